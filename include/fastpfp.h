@@ -1,0 +1,212 @@
+/*
+ * fastpfp.h -- C ABI of the GB300 FastPFP solver (libfastpfp.so).
+ *
+ * FastPFP (Lu, Huang & Liu, "A Fast Projected Fixed-Point Algorithm for
+ * Large Graph Matching") matches two undirected weighted attributed graphs:
+ *
+ *   max_X 1/2 tr(X^T A X A') + lambda tr(X^T K),  K = B B'^T       (Eq. 3)
+ *   X 1 <= 1, X^T 1 = 1, X in {0,1}^{n x n'}, n >= n'               (Eq. 4)
+ *
+ * relaxed to partial doubly stochastic X and solved by the projected
+ * fixed-point iteration (Eq. fastPFP, Algorithm 1)
+ *
+ *   Y[:, :n'] = A X A' + lambda K
+ *   repeat { Y <- P1(Y) (Eq. P1);  Y <- max(Y, 0) (Eq. P2) } until Y converges
+ *   X <- (1 - alpha) X + alpha Y[:, :n'];  X <- X / max(X)
+ *
+ * until X converges, followed by the greedy discretisation of Section 4.5.
+ *
+ * Conventions for every entry point
+ *   - Matrices are dense, row-major, contiguous, float32.
+ *   - "device" pointers are CUDA global memory on the handle's device; the
+ *     caller owns them.  "host" pointers are ordinary host memory.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; calls that return statistics
+ *     synchronise that stream before returning.
+ *   - Every call returns FASTPFP_OK (0) or a negative FASTPFP_ERR_* code;
+ *     fastpfp_error_string() names it.  On an error no output is valid.
+ *   - Orientation: outputs are in the caller's orientation.  Internally the
+ *     larger graph indexes the rows (Section 3 assumes n >= n'); the swap
+ *     and the transposes are done by the library.
+ *   - A handle is not thread safe: one host thread per handle at a time.
+ */
+#ifndef FASTPFP_H
+#define FASTPFP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FASTPFP_OK 0
+#define FASTPFP_ERR_ARG (-1)         /* null pointer, bad size, alpha outside [0,1] ...  */
+#define FASTPFP_ERR_SIZE (-2)        /* a graph larger than the handle's max_n            */
+#define FASTPFP_ERR_CUDA (-3)        /* a CUDA runtime call failed                        */
+#define FASTPFP_ERR_TIMEOUT (-4)     /* a device-side barrier wait ran out of its budget  */
+#define FASTPFP_ERR_NONFINITE (-5)   /* NaN or Inf met in the iterate                     */
+#define FASTPFP_ERR_UNSUPPORTED (-6) /* option not available on this device / build       */
+
+#define FASTPFP_MAX_N 16384          /* largest graph a handle can be created for         */
+#define FASTPFP_MAX_K 256            /* largest attribute dimension k                     */
+
+enum { FASTPFP_FP32 = 0, FASTPFP_BF16 = 1 };
+
+typedef struct fastpfp_s* fastpfp_t;
+
+/* Parameters of one solve.  Defaults (fastpfp_default_params) follow the
+ * paper where it fixes a value: alpha = 0.5 (Section 5), the uniform start
+ * X = 1 1^T / (n n') and Y = 0 (after Algorithm 1), X <- X / max(X) on
+ * (Remarks after Theorem 1). */
+typedef struct {
+    float lambda;          /* weight of the attribute term, Eq. (3); >= 0                     */
+    float alpha;           /* step size of Eq. (fastPFP), in [0, 1]                           */
+    double tol_outer;      /* eps_1: stop when max|X(t+1) - X(t)| < eps_1 (Section 5)         */
+    double tol_inner;      /* eps_2: stop P_D when max|Y(u+1) - Y(u)| < eps_2 (Section 5)     */
+    int max_outer;         /* I_0: at most this many outer iterations, >= 1                   */
+    int max_inner;         /* I_1: at most this many P1/P2 rounds per outer iteration, >= 1   */
+    int precision;         /* FASTPFP_FP32 or FASTPFP_BF16 for the A X A' products            */
+    int refine_iters;      /* BF16 only: FP32 outer iterations run after the BF16 phase        */
+    double switch_tol;     /* BF16 only: the BF16 phase ends once max|dX| < switch_tol         */
+    int normalize_max;     /* 1: X <- X / max(X) after every outer iteration (Algorithm 1)     */
+    int slack_policy;      /* 0: slack columns of Y carry over between outer iterations
+                              (Algorithm 1 initialises Y once); 1: reset them to 0            */
+    int timeout_ms;        /* budget of every device-side barrier wait; <= 0 means 2000 ms     */
+    int profile;           /* 1: record CUDA events on `stream` around every phase of the first
+                              128 outer iterations and report per-phase times in the stats    */
+    int debug_flags;       /* testing only, 0 in production.  Bit 0: CTA 0 of the first
+                              projection launch skips its arrival at the first grid barrier, so
+                              every wait of that launch runs out after timeout_ms and the call
+                              returns FASTPFP_ERR_TIMEOUT (exercises failure detection without
+                              faulting or hanging the device)                                 */
+} fastpfp_params;
+
+/* Statistics of one solve (in the canonical orientation). */
+typedef struct {
+    int outer_iters;        /* outer iterations run                                          */
+    int inner_iters_total;  /* P1/P2 rounds summed over all outer iterations                 */
+    int inner_iters_max;    /* largest P1/P2 round count of one outer iteration              */
+    int converged;          /* 1 if max|dX| < tol_outer was reached; 0 if I_0 stopped it     */
+    int lowp_iters;         /* outer iterations run with BF16 products                       */
+    int transposed;         /* 1 if the graphs were swapped (n_a < n_b)                      */
+    int status;             /* FASTPFP_OK or the error code of this solve                    */
+    int launches;           /* CUDA kernels this solve enqueued                              */
+    double final_delta;     /* last max|X(t+1) - X(t)|                                       */
+    double objective;       /* Eq. (3) at the returned partial permutation                   */
+    float ms_gemm;          /* profile = 1: summed time of the gradient products             */
+    float ms_proj;          /* profile = 1: summed time of the projection launches           */
+    float ms_disc;          /* profile = 1: time of the discretisation                       */
+} fastpfp_stats;
+
+/* One graph pair of a batch; all pointers are device pointers. */
+typedef struct {
+    const float* A;     /* n_a x n_a symmetric                       */
+    const float* A2;    /* n_b x n_b symmetric                       */
+    const float* B;     /* n_a x k, or NULL when k == 0              */
+    const float* B2;    /* n_b x k, or NULL when k == 0              */
+    int n_a, n_b, k;
+    const float* X0;    /* nullable n_a x n_b start                  */
+    int32_t* perm_out;  /* n_a entries                               */
+    float* X_out;       /* nullable n_a x n_b                        */
+} fastpfp_pair;
+
+/* Fills *p with the defaults: lambda 0, alpha 0.5, tol_outer = tol_inner =
+ * 1e-6, max_outer 100, max_inner 1000, FP32, refine_iters 8, switch_tol
+ * 1e-3, normalize_max 1, slack_policy 0, timeout_ms 2000. */
+void fastpfp_default_params(fastpfp_params* p);
+
+/* Creates a solver on CUDA device `device` for graphs of up to max_n nodes.
+ * All device scratch (the slacked N x N matrix Y of Section 4.3, X, K, the
+ * products, the reduction buffers) is allocated here, sized for max_n;
+ * max_batch bounds the pairs of one fastpfp_match_batched call.  Nothing is
+ * allocated by the solve calls.  Errors: ERR_ARG (max_n < 1, max_batch < 1,
+ * out == NULL), ERR_CUDA (bad device, out of memory). */
+int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch);
+
+/* Releases the handle and all its device memory.  NULL is ignored. */
+void fastpfp_destroy(fastpfp_t h);
+
+/* Solves one pair (Algorithm 1 followed by Section 4.5), all arrays on the
+ * device.
+ *   A   : n_a x n_a symmetric adjacency of graph 1 (Section 3)
+ *   A2  : n_b x n_b symmetric adjacency of graph 2
+ *   B,B2: n_a x k and n_b x k node attributes; may be NULL when k == 0 or
+ *         p->lambda == 0
+ *   X0  : nullable n_a x n_b start; NULL gives the uniform start 1/(n n')
+ *   perm_out : n_a int32; perm_out[i] = node of graph 2 matched to node i of
+ *              graph 1, or -1 when graph 1 is the larger one and i is left
+ *              unmatched (every node of the smaller graph is matched, Eq. 4)
+ *   X_out    : nullable n_a x n_b; receives the final soft assignment X
+ *   st       : nullable host pointer; receives the statistics
+ * Synchronises `stream`.  Errors: ERR_ARG, ERR_SIZE (max(n_a, n_b) > max_n),
+ * ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE. */
+int fastpfp_match(fastpfp_t h, void* stream,
+                  const float* A, int n_a, const float* A2, int n_b,
+                  const float* B, const float* B2, int k,
+                  const fastpfp_params* p, const float* X0,
+                  int32_t* perm_out, float* X_out, fastpfp_stats* st);
+
+/* As fastpfp_match, but every array argument is HOST memory: the library
+ * stages the inputs into its own device buffers, solves, and copies
+ * perm_out (and X_out) back.  Synchronises `stream`. */
+int fastpfp_match_host(fastpfp_t h, void* stream,
+                       const float* A, int n_a, const float* A2, int n_b,
+                       const float* B, const float* B2, int k,
+                       const fastpfp_params* p, const float* X0,
+                       int32_t* perm_out, float* X_out, fastpfp_stats* st);
+
+/* Solves `count` independent pairs with the same parameters (Algorithm 1
+ * per pair).  pairs[] is a host array of device-pointer descriptors; st is
+ * a nullable host array of `count` statistics.  Synchronises `stream`.
+ * Errors as fastpfp_match, plus ERR_ARG when count > max_batch. */
+int fastpfp_match_batched(fastpfp_t h, void* stream, int count, const fastpfp_pair* pairs,
+                          const fastpfp_params* p, fastpfp_stats* st);
+
+/* Copies the per-outer-iteration trace of the last solve on this handle:
+ * inner_counts[t] = P1/P2 rounds of outer iteration t, deltas[t] =
+ * max|X(t+1) - X(t)|.  Either array may be NULL.  Returns the number of
+ * outer iterations (at most cap entries are written), or an error code. */
+int fastpfp_last_trace(fastpfp_t h, int* inner_counts, double* deltas, int cap);
+
+/* ---- single steps of Algorithm 1, for step-by-step checking ------------ */
+
+/* Gradient of Section 4.1 in canonical orientation (N >= m):
+ *   Y[i, j] = sum_l (sum_q A[i,q] X[q,l]) A2[l,j] + lambda * K[i,j]
+ * for i < N, j < m; Y has leading dimension ldy >= m.  A is N x N, X is
+ * N x m, A2 is m x m, K is N x m (nullable when lambda == 0).  precision
+ * selects FP32 or BF16 products (FP32 accumulation).  Device pointers;
+ * asynchronous on `stream`.  Errors: ERR_ARG, ERR_SIZE, ERR_CUDA. */
+int fastpfp_gradient(fastpfp_t h, void* stream, const float* A, const float* X, const float* A2,
+                     const float* K, float lambda, int N, int m, float* Y, int ldy, int precision);
+
+/* K = B B2^T (below Eq. 4): B is N x k, B2 is m x k, K is N x m, 1 <= k <=
+ * 256.  Device pointers; asynchronous.  Errors: ERR_ARG, ERR_SIZE, ERR_CUDA. */
+int fastpfp_affinity(fastpfp_t h, void* stream, const float* B, const float* B2, int N, int m,
+                     int k, float* K);
+
+/* Successive projection P_D of Section 4.3 in place on the N x N device
+ * matrix Y (leading dimension N): rounds of P1 (Eq. P1, total taken over
+ * Y) then P2 (Eq. P2) until max|dY| < tol or max_iter rounds.  *iters and
+ * *last_delta (host, nullable) receive the rounds run and the last
+ * max|dY|.  Synchronises `stream`.  Errors: ERR_ARG, ERR_SIZE, ERR_CUDA,
+ * ERR_TIMEOUT. */
+int fastpfp_project(fastpfp_t h, void* stream, float* Y, int N, double tol, int max_iter,
+                    int* iters, double* last_delta);
+
+/* Greedy discretisation of Section 4.5 of the N x m device matrix X
+ * (N >= m): repeatedly takes the largest remaining entry, ties to the
+ * lowest row-major index, and removes its row and column.  row_of_col
+ * (device, m int32) receives the row matched to each column.  Bit-exact
+ * with the sequential definition for finite X.  Asynchronous.  Errors:
+ * ERR_ARG, ERR_SIZE, ERR_CUDA. */
+int fastpfp_discretize(fastpfp_t h, void* stream, const float* X, int N, int m,
+                       int32_t* row_of_col);
+
+/* Human-readable name of an error code. */
+const char* fastpfp_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASTPFP_H */

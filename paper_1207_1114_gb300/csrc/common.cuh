@@ -1,0 +1,143 @@
+// common.cuh -- device helpers shared by the FastPFP kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/fastpfp.h"
+
+namespace fpfp {
+
+constexpr int kMaxOuterTrace = 4096;  // per-solve trace capacity (outer iterations)
+
+// Device control block of one solve.  Zeroed (except the fields the host
+// sets) before the first outer iteration.
+struct Ctrl {
+    int done;              // 1 once the outer loop has stopped
+    int outer;             // outer iterations completed
+    int error;             // FASTPFP_ERR_* raised on the device, 0 if none
+    int converged;         // 1 if max|dX| < tol_outer was reached
+    int inner_total;       // sum of P1/P2 rounds
+    int inner_max;         // largest round count of one outer iteration
+    int lowp;              // 1 while the BF16 phase runs
+    int lowp_iters;        // outer iterations run in BF16
+    int refine_left;       // FP32 iterations left after the BF16 phase
+    int last_inner;        // rounds of the latest P_D call
+    double last_delta;     // latest max|dX| (outer) or max|dY| (P_D only)
+    double objective;      // Eq. (3) at the discrete result
+    unsigned long long dx_bits;  // max|dX| of the running outer iteration (double bits)
+    unsigned xmax_bits;    // max(X) of the running outer iteration (ordered float bits)
+    unsigned bar;          // grid-barrier arrival counter (grows within a solve)
+    unsigned bar_base;     // counter value at the start of the next cooperative launch
+    int matched;           // discretisation: columns matched so far
+    int inner_trace[kMaxOuterTrace];
+    double delta_trace[kMaxOuterTrace];
+};
+
+// ---------------------------------------------------------------- ordering
+// Order-preserving map of a float onto uint32 (larger float -> larger uint).
+__device__ __forceinline__ unsigned float_to_ordered(float f) {
+    unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ordered_to_float(unsigned u) {
+    unsigned b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+    return __uint_as_float(b);
+}
+
+// --------------------------------------------------------------- reductions
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// ------------------------------------------------------------ memory model
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed_i32(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Vector reduction-add of four floats into global memory (sm_90+).
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a),
+                 "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+// Grid-wide barrier for a cooperative launch.  `counter` only ever grows
+// within a solve: every CTA adds 1 per barrier, and a barrier is passed once
+// the counter reaches `target` (the value after all CTAs of the grid have
+// arrived).  The arrive is a release and the wait an acquire, so writes made
+// by any thread of a CTA before the barrier are visible to every thread of
+// every CTA after it.  The wait is bounded: after `timeout_ns` (or as soon as
+// another CTA has raised an error) it records FASTPFP_ERR_TIMEOUT in *err and
+// returns false; every caller then leaves the kernel.  Must be reached by all
+// threads of the CTA.  `arrive` = false (fault-injection tests only) waits
+// without arriving, so the barrier can never complete and every wait runs out.
+__device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned target, int* err,
+                                             long long timeout_ns, bool arrive = true) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (arrive) red_release_add_u32(counter, 1u);
+        uint64_t t0 = 0;
+        unsigned spins = 0;
+        while (ld_acquire_u32(counter) < target) {
+            if ((++spins & 255u) == 0u) {
+                const uint64_t now = globaltimer_ns();
+                if (t0 == 0) t0 = now;
+                if (ld_relaxed_i32(err) != 0 || (long long)(now - t0) > timeout_ns ||
+                    spins > (1u << 30)) {
+                    atomicCAS(err, 0, FASTPFP_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+}  // namespace fpfp

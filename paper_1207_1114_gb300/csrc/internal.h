@@ -1,0 +1,106 @@
+// internal.h -- launch interfaces between the C ABI (fastpfp_api.cu) and the
+// kernels.  Not installed; not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace fpfp {
+
+struct Ctrl;
+
+// ------------------------------------------------------------ projection
+constexpr int kPdOuterStep = 1;     // P_D rounds + blend/normalise + loop control
+constexpr int kPdProjectOnly = 0;   // P_D rounds only (fastpfp_project)
+constexpr int kPdMaxSmem = 220 * 1024;
+constexpr long long kPdElemsPerCta = 8192;  // target band size of one CTA
+
+struct PdParams {
+    float* Y;           // N x ldy slacked matrix, ldy = round_up(N, 4), pad columns zero
+    int N, ldy;
+    int m;              // columns of X (outer step); m <= N
+    float* X;           // N x ldx master X, ldx = round_up(m, 4), pad columns zero
+    int ldx;
+    __nv_bfloat16* Xt16;  // nullable: BF16 copy of X^T (m x ldxt) for the BF16 products
+    int ldxt;
+    float alpha;
+    int normalize, slack_reset;
+    double tol_inner;
+    int max_inner;
+    double tol_outer;
+    int max_outer;
+    int refine_iters;
+    double switch_tol;
+    float* colbuf;      // 3 x ldy rotating column-sum accumulators, zero between launches
+    double* sbuf;       // 3 rotating totals
+    unsigned* dbuf;     // 3 rotating max|dY| (float bits)
+    Ctrl* ctrl;
+    long long timeout_ns;
+    int rpc;            // rows per CTA
+    int mode;           // kPdOuterStep or kPdProjectOnly
+    int skip_arrive;    // testing only: CTA 0 does not arrive at the first barrier of outer step 0
+};
+
+struct PdLaunch {
+    int grid, block, rpc, ldy;
+    size_t smem;
+    bool resident;
+};
+
+cudaError_t pd_configure();
+void pd_plan(int N, int num_sms, PdLaunch* L);
+size_t pd_smem_bytes(int rpc, int Q, bool res);
+cudaError_t pd_launch(const PdLaunch& L, const PdParams& P, cudaStream_t s);
+
+// ----------------------------------------------------------------- GEMM
+// C[M x Nc] = Aop[M x K] * Bop[K x Nc] (+ lambda * Kmat), row-major FP32.
+// When ctrl is set the kernel does nothing unless the solve is running and
+// its precision phase is `phase` (0 FP32, 1 BF16).
+struct GemmF32Args {
+    const float* A; int lda;
+    const float* B; int ldb;
+    float* C; int ldc;
+    const float* Kmat; int ldk; float lambda;
+    int M, Nc, K;
+    const Ctrl* ctrl;
+};
+cudaError_t gemm_f32(const GemmF32Args& a, cudaStream_t s);
+
+// ----------------------------------------------------------- misc kernels
+cudaError_t init_ctrl(Ctrl* c, int lowp, cudaStream_t s);
+
+// K[i, j] = sum_c B[i, c] * B2[j, c]   (N x m, leading dimension ldk)
+cudaError_t affinity(const float* B, const float* B2, int N, int m, int k, float* K, int ldk,
+                     cudaStream_t s);
+
+// X (N x ldx) = uniform 1/(N m), or X0 (caller orientation; transposed when
+// `transposed`), pad columns zero.  Also writes the BF16 X^T copy if Xt16.
+cudaError_t init_x(float* X, int N, int m, int ldx, const float* X0, int transposed,
+                   __nv_bfloat16* Xt16, int ldxt, cudaStream_t s);
+
+// FP32 -> BF16 copy of an r x c matrix (leading dimensions lds, ldd); the
+// pad columns c..ldd-1 are written as zero.
+cudaError_t to_bf16(const float* src, int r, int c, int lds, __nv_bfloat16* dst, int ldd,
+                    cudaStream_t s);
+
+// Caller-orientation outputs from the canonical result.
+cudaError_t write_outputs(const int32_t* row_of_col, int N, int m, int transposed, int32_t* perm_out,
+                          const float* X, int ldx, float* X_out, cudaStream_t s);
+
+// Eq. (3) at the discrete result, FP64, into ctrl->objective.
+cudaError_t objective(const float* A, int N, const float* A2, int m, const float* K, int ldk,
+                      float lambda, const int32_t* row_of_col, Ctrl* ctrl, cudaStream_t s);
+
+// ------------------------------------------------------- discretisation
+struct DiscBuffers {
+    int32_t* row_match;           // N
+    int32_t* col_match;           // m (the output row_of_col)
+    unsigned long long* row_best; // N
+    unsigned long long* col_best; // 2 x m
+};
+cudaError_t disc_configure();
+cudaError_t discretize(const float* X, int N, int m, int ldx, const DiscBuffers& b, Ctrl* ctrl,
+                       long long timeout_ns, int num_sms, cudaStream_t s);
+
+}  // namespace fpfp

@@ -1,0 +1,176 @@
+// misc.cu -- small kernels around the solve: control-block set-up, the
+// attribute affinity K = B B'^T (below Eq. 4), the initial X (after
+// Algorithm 1), BF16 operand copies, caller-orientation outputs and the
+// objective of Eq. (3) at the discrete result.
+#include "common.cuh"
+#include "internal.h"
+
+namespace fpfp {
+namespace {
+
+__global__ void init_ctrl_kernel(Ctrl* c, int lowp) {
+    c->lowp = lowp;
+    c->refine_left = 0;
+}
+
+// K[i, j] = sum_c B[i, c] B2[j, c]; one thread per entry, attributes of the
+// block's rows staged in shared memory.
+__global__ void affinity_kernel(const float* __restrict__ B, const float* __restrict__ B2, int N,
+                                int m, int k, float* __restrict__ K, int ldk) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    extern __shared__ float brow[];
+    for (int c = threadIdx.x; c < k; c += blockDim.x) brow[c] = B[(size_t)i * k + c];
+    __syncthreads();
+    if (j >= m) return;
+    float acc = 0.f;
+    for (int c = 0; c < k; ++c) acc = fmaf(brow[c], __ldg(B2 + (size_t)j * k + c), acc);
+    K[(size_t)i * ldk + j] = acc;
+}
+
+__global__ void init_x_kernel(float* X, int N, int m, int ldx, const float* X0, int transposed,
+                              __nv_bfloat16* Xt16, int ldxt) {
+    const size_t total = (size_t)N * ldx;
+    const float u = (float)(1.0 / ((double)N * (double)m));
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ldx), j = (int)(e % ldx);
+        float v = 0.f;
+        if (j < m) {
+            if (X0) v = transposed ? X0[(size_t)j * N + i] : X0[(size_t)i * m + j];
+            else v = u;
+        }
+        X[e] = v;
+        if (Xt16 && j < m) Xt16[(size_t)j * ldxt + i] = __float2bfloat16_rn(v);
+    }
+}
+
+__global__ void to_bf16_kernel(const float* src, int r, int c, int lds, __nv_bfloat16* dst,
+                               int ldd) {
+    const size_t total = (size_t)r * ldd;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ldd), j = (int)(e % ldd);
+        dst[e] = __float2bfloat16_rn(j < c ? src[(size_t)i * lds + j] : 0.f);
+    }
+}
+
+__global__ void perm_fill_kernel(int32_t* perm, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) perm[i] = -1;
+}
+
+__global__ void perm_scatter_kernel(const int32_t* row_of_col, int m, int transposed,
+                                    int32_t* perm) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int r = row_of_col[j];
+    if (transposed) perm[j] = r;          // graph 1 indexes the columns
+    else if (r >= 0) perm[r] = j;         // graph 1 indexes the rows
+}
+
+// X_out (caller orientation) from the canonical N x m X.
+__global__ void x_out_kernel(const float* X, int N, int m, int ldx, int transposed, float* out) {
+    __shared__ float tile[32][33];
+    const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int i = bi + r, j = bj + threadIdx.x;
+        if (i < N && j < m) {
+            const float v = X[(size_t)i * ldx + j];
+            if (!transposed) out[(size_t)i * m + j] = v;
+            else tile[r][threadIdx.x] = v;
+        }
+    }
+    if (!transposed) return;
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int j = bj + r, i = bi + threadIdx.x;   // out is m x N
+        if (i < N && j < m) out[(size_t)j * N + i] = tile[threadIdx.x][r];
+    }
+}
+
+// 1/2 sum_{j,l} A[r(j), r(l)] A2[l, j] + lambda sum_j K[r(j), j], in FP64.
+__global__ void objective_kernel(const float* A, int N, const float* A2, int m, const float* K,
+                                 int ldk, float lambda, const int32_t* row_of_col, Ctrl* ctrl) {
+    double acc = 0.0;
+    const size_t total = (size_t)m * m;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int l = (int)(e / m), j = (int)(e % m);
+        const int rj = row_of_col[j], rl = row_of_col[l];
+        if (rj < 0 || rl < 0) continue;   // an aborted discretisation leaves -1 entries
+        acc += 0.5 * (double)A[(size_t)rj * N + rl] * (double)A2[(size_t)l * m + j];
+    }
+    if (K && lambda != 0.f) {
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x)
+            if (row_of_col[j] >= 0) acc += (double)lambda * (double)K[(size_t)row_of_col[j] * ldk + j];
+    }
+    __shared__ double red[32];
+    acc = warp_sum_d(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        atomicAdd(&ctrl->objective, t);
+    }
+}
+
+inline int grid_for(size_t total, int block, int cap = 4096) {
+    size_t g = (total + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > (size_t)cap) g = cap;
+    return (int)g;
+}
+
+}  // namespace
+
+cudaError_t init_ctrl(Ctrl* c, int lowp, cudaStream_t s) {
+    init_ctrl_kernel<<<1, 1, 0, s>>>(c, lowp);
+    return cudaGetLastError();
+}
+
+cudaError_t affinity(const float* B, const float* B2, int N, int m, int k, float* K, int ldk,
+                     cudaStream_t s) {
+    if (N <= 0 || m <= 0) return cudaSuccess;
+    dim3 grid((m + 255) / 256, N);
+    affinity_kernel<<<grid, 256, (size_t)k * sizeof(float), s>>>(B, B2, N, m, k, K, ldk);
+    return cudaGetLastError();
+}
+
+cudaError_t init_x(float* X, int N, int m, int ldx, const float* X0, int transposed,
+                   __nv_bfloat16* Xt16, int ldxt, cudaStream_t s) {
+    const size_t total = (size_t)N * ldx;
+    init_x_kernel<<<grid_for(total, 256), 256, 0, s>>>(X, N, m, ldx, X0, transposed, Xt16, ldxt);
+    return cudaGetLastError();
+}
+
+cudaError_t to_bf16(const float* src, int r, int c, int lds, __nv_bfloat16* dst, int ldd,
+                    cudaStream_t s) {
+    const size_t total = (size_t)r * ldd;
+    to_bf16_kernel<<<grid_for(total, 256), 256, 0, s>>>(src, r, c, lds, dst, ldd);
+    return cudaGetLastError();
+}
+
+cudaError_t write_outputs(const int32_t* row_of_col, int N, int m, int transposed, int32_t* perm_out,
+                          const float* X, int ldx, float* X_out, cudaStream_t s) {
+    if (perm_out) {
+        if (!transposed) perm_fill_kernel<<<(N + 255) / 256, 256, 0, s>>>(perm_out, N);
+        perm_scatter_kernel<<<(m + 255) / 256, 256, 0, s>>>(row_of_col, m, transposed, perm_out);
+    }
+    if (X_out) {
+        dim3 grid((m + 31) / 32, (N + 31) / 32);
+        x_out_kernel<<<grid, dim3(32, 8), 0, s>>>(X, N, m, ldx, transposed, X_out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t objective(const float* A, int N, const float* A2, int m, const float* K, int ldk,
+                      float lambda, const int32_t* row_of_col, Ctrl* ctrl, cudaStream_t s) {
+    const size_t total = (size_t)m * m;
+    objective_kernel<<<grid_for(total, 256, 1024), 256, 0, s>>>(A, N, A2, m, K, ldk, lambda,
+                                                                row_of_col, ctrl);
+    return cudaGetLastError();
+}
+
+}  // namespace fpfp

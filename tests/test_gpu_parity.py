@@ -1,0 +1,280 @@
+"""GPU parity: every CUDA step and the whole solve against the FP64 oracle,
+called through the C ABI (libfastpfp.so) on the same seeded inputs.
+
+Tolerances (FP32 kernels against the FP64 oracle):
+  * gradient entries: |err| <= 1e-5 * (|A| |X| |A'| + lambda |K|) entrywise, the
+    FP32 dot-product bound for sums of <= ~1e4 terms;
+  * P_D after a replayed number of rounds: max-abs 2e-5 (entries of order 1);
+  * final X of a replayed solve: max-abs 1e-4; objective relative 1e-5;
+  * discretisation: bit-exact (both sides compare the same FP32 values).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle
+from paper_1207_1114_gb300 import fastpfp as F
+from paper_1207_1114_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def cu(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=DEV)
+
+
+@pytest.fixture(scope="module")
+def solver():
+    s = F.Solver(max_n=1200, max_batch=8)
+    yield s
+    s.close()
+
+
+def _canon(g):
+    """Canonical orientation: larger graph on the rows."""
+    if g.A.shape[0] >= g.A2.shape[0]:
+        return g.A, g.A2, g.B, g.B2, False
+    return g.A2, g.A, g.B2, g.B, True
+
+
+# --------------------------------------------------------------- single steps
+
+@pytest.mark.parametrize("N,m,k", [(1, 1, 1), (7, 5, 3), (130, 97, 16), (1000, 1000, 16)])
+def test_affinity_matches_oracle(solver, N, m, k):
+    rng = np.random.default_rng(N + m)
+    B = rng.normal(size=(N, k)).astype(np.float32)
+    B2 = rng.normal(size=(m, k)).astype(np.float32)
+    K = solver.affinity(cu(B), cu(B2)).cpu().numpy()
+    ref = oracle.affinity(B, B2)
+    bound = np.abs(B).astype(np.float64) @ np.abs(B2).astype(np.float64).T
+    assert (np.abs(K - ref) <= 1e-6 * bound + 1e-30).all()
+
+
+@pytest.mark.parametrize("N,m", [(1, 1), (5, 3), (129, 100), (300, 300), (1200, 1000)])
+def test_gradient_matches_oracle(solver, N, m):
+    rng = np.random.default_rng(N * 3 + m)
+    A = synth.random_graph(rng, N, 0.2).astype(np.float32)
+    A2 = synth.random_graph(rng, m, 0.2).astype(np.float32)
+    X = rng.random((N, m)).astype(np.float32)
+    K = rng.normal(size=(N, m)).astype(np.float32)
+    lam = 0.7
+    G = solver.gradient(cu(A), cu(X), cu(A2), cu(K), lam).cpu().numpy()
+    ref = oracle.gradient(A, X, A2, K, lam)
+    bound = np.abs(A) @ np.abs(X).astype(np.float64) @ np.abs(A2) + lam * np.abs(K)
+    assert (np.abs(G - ref) <= 1e-5 * bound + 1e-30).all()
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 7, 64, 100, 129, 333, 1000, 1200])
+def test_projection_matches_oracle_fixed_rounds(solver, N):
+    rng = np.random.default_rng(N)
+    Y = (rng.random((N, N)) * 5.0).astype(np.float32)
+    Yg = cu(Y)
+    it, _ = solver.project(Yg, tol=0.0, max_iter=40)
+    assert it == 40
+    ref, _, _ = oracle.pd(Y, fixed_iters=40)
+    assert np.abs(Yg.cpu().numpy() - ref).max() <= 2e-5
+    assert (Yg.cpu().numpy() >= 0).all()
+
+
+@pytest.mark.parametrize("N", [50, 257, 1000])
+def test_projection_tolerance_stop_replays(solver, N):
+    rng = np.random.default_rng(7 * N)
+    Y = (rng.random((N, N)) * rng.random((N, 1)) * 20).astype(np.float32)
+    Yg = cu(Y)
+    it, d = solver.project(Yg, tol=1e-5, max_iter=2000)
+    assert 1 <= it <= 2000
+    assert it == 2000 or d < 1e-5
+    ref, _, _ = oracle.pd(Y, fixed_iters=it)
+    assert np.abs(Yg.cpu().numpy() - ref).max() <= 2e-5
+
+
+def test_projection_streamed_band_large_n():
+    """N = 4000: a CTA's band no longer fits in shared memory, the kernel
+    streams it from global memory."""
+    with F.Solver(max_n=4000) as s:
+        rng = np.random.default_rng(4000)
+        Y = (rng.random((4000, 4000)) * 3.0).astype(np.float32)
+        Yg = cu(Y)
+        it, _ = s.project(Yg, tol=0.0, max_iter=6)
+        assert it == 6
+        ref, _, _ = oracle.pd(Y, fixed_iters=6)
+        assert np.abs(Yg.cpu().numpy() - ref).max() <= 2e-5
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (2, 1), (9, 9), (100, 37), (257, 256), (1200, 1000)])
+@pytest.mark.parametrize("levels", [0, 4])
+def test_discretize_bit_exact(solver, shape, levels):
+    rng = np.random.default_rng(shape[0] * 11 + shape[1] + levels)
+    X = rng.random(shape).astype(np.float32)
+    if levels:
+        X = (np.floor(X * levels) / levels).astype(np.float32)   # heavy ties
+    got = solver.discretize(cu(X)).cpu().numpy()
+    ref = oracle.greedy_sorted(X.astype(np.float64))
+    np.testing.assert_array_equal(got, ref)
+
+
+# ---------------------------------------------------------------- whole solve
+
+def _check_against_replay(g, res, solver, lam, **kw):
+    """X of the GPU solve against the oracle replaying the GPU's iteration counts."""
+    inner, _ = solver.last_trace()
+    st = res.stats
+    assert st.status == 0 and len(inner) == st.outer_iters
+    r = oracle.solve(g.A, g.A2, g.B, g.B2, lam=lam, replay_inner=inner,
+                     replay_outer=st.outer_iters, **kw)
+    Xg = res.X.cpu().numpy()
+    assert np.abs(Xg - r["X"]).max() <= 1e-4
+    # discretisation of the GPU's X is bit-exact with the oracle's greedy
+    A, A2, _, _, tr = _canon(g)
+    Xc = Xg.T if tr else Xg
+    roc = oracle.greedy_sorted(Xc.astype(np.float64))
+    perm = res.perm.cpu().numpy()
+    if tr:
+        np.testing.assert_array_equal(perm, roc)
+    else:
+        want = -np.ones(A.shape[0], dtype=np.int32)
+        want[roc] = np.arange(len(roc), dtype=np.int32)
+        np.testing.assert_array_equal(perm, want)
+    # objective (Eq. 3) of the GPU's permutation, FP64 on both sides
+    Bc, B2c = (g.B2, g.B) if tr else (g.B, g.B2)
+    K = oracle.affinity(Bc, B2c) if g.k and lam else None
+    obj = oracle.qap_objective(A, A2, roc, K, lam)
+    assert abs(st.objective - obj) <= 1e-5 * abs(obj)
+    return r
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_plain_100_matches_oracle(solver, seed):
+    g = synth.plain_100(seed)
+    res = solver.match(cu(g.A), cu(g.A2), params=F.default_params(), want_X=True)
+    r = _check_against_replay(g, res, solver, 0.0)
+    assert (res.perm.cpu().numpy() == g.gt).mean() >= 0.99
+    assert res.stats.converged == int(r["converged"])
+
+
+@pytest.mark.parametrize("n_a,n_b", [(60, 75), (75, 60), (17, 13), (13, 17), (1, 1), (2, 1),
+                                     (1, 3)])
+def test_partial_and_transposed_match_oracle(solver, n_a, n_b):
+    n, n_out = min(n_a, n_b), abs(n_a - n_b)
+    g = synth.graph_pair(n, p=0.3, sigma=0.03, k=4, n_out=n_out, lam=0.5, seed=n_a * 100 + n_b)
+    if n_a > n_b:   # graph 1 is the larger one
+        g = synth.GraphPair(g.A2, g.A, g.B2, g.B, np.argsort(g.gt).astype(np.int32)[:n], g.lam)
+    p = F.default_params(lam=0.5, max_outer=30, max_inner=300)
+    res = solver.match(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2), params=p, want_X=True)
+    assert res.stats.transposed == int(n_a < n_b)
+    _check_against_replay(g, res, solver, 0.5, max_outer=30, max_inner=300)
+
+
+def test_slack_reset_policy_matches_oracle(solver):
+    g = synth.graph_pair(40, p=0.3, sigma=0.03, k=3, n_out=12, lam=0.5, seed=9)
+    p = F.default_params(lam=0.5, max_outer=20, max_inner=200, slack_policy=1)
+    res = solver.match(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2), params=p, want_X=True)
+    _check_against_replay(g, res, solver, 0.5, max_outer=20, max_inner=200, slack_policy=1)
+
+
+def test_no_normalisation_matches_oracle(solver):
+    g = synth.graph_pair(50, p=0.3, sigma=0.02, seed=10)
+    p = F.default_params(max_outer=15, max_inner=200, normalize_max=0)
+    res = solver.match(cu(g.A), cu(g.A2), params=p, want_X=True)
+    _check_against_replay(g, res, solver, 0.0, max_outer=15, max_inner=200, normalize_max=False)
+
+
+def test_warm_start_x0_matches_oracle(solver):
+    g = synth.graph_pair(64, p=0.3, sigma=0.02, n_out=8, seed=11)
+    rng = np.random.default_rng(0)
+    X0 = rng.random((g.n, g.n2)).astype(np.float32)
+    p = F.default_params(max_outer=20, max_inner=200)
+    res = solver.match(cu(g.A), cu(g.A2), params=p, X0=cu(X0), want_X=True)
+    _check_against_replay(g, res, solver, 0.0, max_outer=20, max_inner=200, X0=X0)
+
+
+def test_host_entry_point_equals_device_entry_point(solver):
+    g = synth.graph_pair(90, p=0.2, sigma=0.03, k=5, n_out=10, lam=0.5, seed=12)
+    p = F.default_params(lam=0.5, max_outer=25, max_inner=300)
+    d = solver.match(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2), params=p, want_X=True)
+    h = solver.match_host(g.A, g.A2, g.B, g.B2, params=p, want_X=True)
+    np.testing.assert_array_equal(d.perm.cpu().numpy(), h.perm)
+    assert np.abs(d.X.cpu().numpy() - h.X).max() <= 1e-5
+    assert d.stats.outer_iters == h.stats.outer_iters
+
+
+def test_batched_equals_single(solver):
+    pairs = synth.batch_mixed(count=5, seed=3, n_lo=20, n_hi=90, out_hi=15)
+    p = F.default_params(lam=0.5, max_outer=20, max_inner=200)
+    dev = [(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)) for g in pairs]
+    outs = solver.match_batched(dev, params=p, want_X=True)
+    for (A, A2, B, B2), o in zip(dev, outs):
+        s = solver.match(A, A2, B, B2, params=p, want_X=True)
+        np.testing.assert_array_equal(s.perm.cpu().numpy(), o.perm.cpu().numpy())
+        assert np.abs(s.X.cpu().numpy() - o.X.cpu().numpy()).max() <= 1e-5
+        assert s.stats.outer_iters == o.stats.outer_iters
+
+
+# ------------------------------------------------------------ errors / faults
+
+def test_nonfinite_input_is_reported(solver):
+    g = synth.plain_100(0)
+    A = g.A.copy()
+    A[3, 5] = A[5, 3] = np.nan
+    with pytest.raises(F.FastPFPError) as e:
+        solver.match(cu(A), cu(g.A2))
+    assert e.value.code == F.FASTPFP_ERR_NONFINITE
+    solver.match(cu(g.A), cu(g.A2))     # the handle stays usable
+
+
+def test_argument_errors(solver):
+    g = synth.plain_100(0)
+    with pytest.raises(F.FastPFPError) as e:
+        solver.match(cu(g.A), cu(g.A2), params=F.default_params(alpha=1.5))
+    assert e.value.code == F.FASTPFP_ERR_ARG
+    big = torch.zeros((1300, 1300), device=DEV)
+    with pytest.raises(F.FastPFPError) as e:
+        solver.match(big, cu(g.A2))
+    assert e.value.code == F.FASTPFP_ERR_SIZE
+
+
+def test_barrier_timeout_is_reported_and_handle_recovers(solver):
+    """A lost barrier arrival (test-only flag) makes every wait run out after
+    timeout_ms; the call returns ERR_TIMEOUT and the context stays usable."""
+    g = synth.plain_100(0)
+    p = F.default_params(timeout_ms=200, debug_flags=1, max_outer=3)
+    with pytest.raises(F.FastPFPError) as e:
+        solver.match(cu(g.A), cu(g.A2), params=p)
+    assert e.value.code == F.FASTPFP_ERR_TIMEOUT
+    res = solver.match(cu(g.A), cu(g.A2))
+    assert res.stats.status == 0 and (res.perm.cpu().numpy() == g.gt).mean() >= 0.99
+
+
+# ------------------------------------------------------ full-size workloads
+
+def test_attributed_1000_full_size_properties(solver):
+    """n = n' = 1000 attributed pair at the benchmark's launch configuration:
+    the oracle cannot replay the whole solve in seconds, so check what holds
+    at any size and sample one gradient step."""
+    g = synth.attributed_1000(0)
+    p = F.default_params(lam=1.0)
+    A, A2, B, B2 = cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)
+    res = solver.match(A, A2, B, B2, params=p, want_X=True)
+    st = res.stats
+    assert st.status == 0 and 1 <= st.outer_iters <= 100
+    Xg = res.X.cpu().numpy()
+    assert Xg.min() >= 0 and Xg.max() == 1.0
+    perm = res.perm.cpu().numpy()
+    assert sorted(perm.tolist()) == list(range(1000))
+    roc = oracle.greedy_sorted(Xg.astype(np.float64))
+    np.testing.assert_array_equal(np.argsort(roc), perm)
+    K = oracle.affinity(g.B, g.B2)
+    obj = oracle.qap_objective(g.A, g.A2, roc, K, 1.0)
+    assert abs(st.objective - obj) <= 1e-5 * abs(obj)
+    assert (perm == g.gt).mean() >= 0.98
+    # one gradient step at the final X on sampled rows
+    G = solver.gradient(A, res.X, A2, solver.affinity(B, B2), 1.0).cpu().numpy()
+    rows = np.arange(0, 1000, 97)
+    T = g.A[rows].astype(np.float64) @ Xg.astype(np.float64)
+    ref = T @ g.A2.astype(np.float64) + K[rows]
+    bound = np.abs(g.A[rows]) @ np.abs(Xg).astype(np.float64) @ np.abs(g.A2) + np.abs(K[rows])
+    assert (np.abs(G[rows] - ref) <= 1e-5 * bound).all()
