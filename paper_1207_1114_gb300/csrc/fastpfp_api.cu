@@ -76,6 +76,17 @@ long long timeout_ns(const fastpfp_params* p) {
     return (long long)ms * 1000000ll;
 }
 
+// The projection kernel leaves its rotating accumulators zero when it
+// completes; a launch that stopped on an error may not.  Every solve
+// therefore starts from cleared accumulators.
+cudaError_t clear_accumulators(fastpfp_t h, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(h->colbuf, 0, 3 * (size_t)h->ld * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(h->sbuf, 0, 3 * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(h->dbuf, 0, 3 * sizeof(unsigned), s);
+}
+
 // Arguments of one solve in canonical orientation (N >= m).
 struct Problem {
     const float *A, *A2, *B, *B2;
@@ -125,6 +136,7 @@ int enqueue_solve(fastpfp_t h, cudaStream_t s, const Problem& q, const fastpfp_p
     if (bf16) return FASTPFP_ERR_UNSUPPORTED;
 
     FP_CUDA(cudaMemsetAsync(h->ctrl, 0, kCtrlHeader, s));
+    FP_CUDA(clear_accumulators(h, s));
     FP_CUDA(cudaMemsetAsync(h->Y, 0, (size_t)N * ldy * sizeof(float), s));
     FP_CUDA(init_ctrl(h->ctrl, bf16 ? 1 : 0, s));
     const float* Kp = nullptr;
@@ -492,6 +504,7 @@ int fastpfp_project(fastpfp_t h, void* stream, float* Y, int N, double tol, int 
     cudaStream_t s = (cudaStream_t)stream;
     const int ldy = round4(N);
     FP_CUDA(cudaMemsetAsync(h->ctrl, 0, kCtrlHeader, s));
+    FP_CUDA(clear_accumulators(h, s));
     FP_CUDA(cudaMemsetAsync(h->Y, 0, (size_t)N * ldy * sizeof(float), s));
     FP_CUDA(cudaMemcpy2DAsync(h->Y, (size_t)ldy * 4, Y, (size_t)N * 4, (size_t)N * 4, N,
                               cudaMemcpyDeviceToDevice, s));

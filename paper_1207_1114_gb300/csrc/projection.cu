@@ -26,11 +26,15 @@ constexpr int kQptMax = 4;  // float4 column quads owned by one thread: N <= 4 *
 struct Smem {
     float4* rows;      // RES: rpc x Q quads of the CTA's band
     float* rsum;       // rpc row sums of the previous round
+    float* arow;       // rpc offsets 1/N + s/N^2 - r_i/N of the next round
     float* rowpart;    // rpc x 32 per-warp row partials
     double* dred;      // 32 doubles of block-reduction scratch
     float* fred;       // 32 floats of block-reduction scratch
+    int* ictl;         // [0] non-finite total, [1] stop the rounds
+    float* fctl;       // [0] max|dY| of the last round
 };
 
+// Shared-memory layout; pd_smem_bytes() below must mirror it.
 __device__ __forceinline__ Smem carve(char* base, int rpc, int Q, bool res) {
     Smem s;
     size_t off = 0;
@@ -38,28 +42,23 @@ __device__ __forceinline__ Smem carve(char* base, int rpc, int Q, bool res) {
     off += res ? (size_t)rpc * Q * sizeof(float4) : 0;
     s.rsum = reinterpret_cast<float*>(base + off);
     off += (size_t)rpc * sizeof(float);
+    s.arow = reinterpret_cast<float*>(base + off);
+    off += (size_t)rpc * sizeof(float);
     s.rowpart = reinterpret_cast<float*>(base + off);
     off += (size_t)rpc * 32 * sizeof(float);
     off = (off + 15) & ~size_t(15);
     s.dred = reinterpret_cast<double*>(base + off);
     off += 32 * sizeof(double);
     s.fred = reinterpret_cast<float*>(base + off);
+    off += 32 * sizeof(float);
+    s.ictl = reinterpret_cast<int*>(base + off);
+    off += 4 * sizeof(int);
+    s.fctl = reinterpret_cast<float*>(base + off);
     return s;
 }
 
 __device__ __forceinline__ float sum4(float4 v) { return (v.x + v.y) + (v.z + v.w); }
 
-// Block-wide sum of one double per thread; result valid in every thread.
-__device__ __forceinline__ double block_sum_d(double v, double* scratch) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_sum_d(v);
-    __syncthreads();
-    if (lane == 0) scratch[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += scratch[w];
-    return t;
-}
 __device__ __forceinline__ float block_max_f(float v, float* scratch) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     v = warp_max(v);
@@ -151,6 +150,69 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
     }
     __syncthreads();
 
+    // End of a pass over the band: fold row sums (FP32), publish the CTA's
+    // share of s (FP64, one warp), of max|dY| and of the column sums, wait at
+    // the grid barrier, then let warp 0 turn the new total s into the per-row
+    // offsets a_i = 1/N + s/N^2 - r_i/N of Eq. (P1) for the next pass.  Only
+    // warp 0 touches FP64, once per pass.
+    const double invN_d = 1.0 / (double)N;
+    const double invN2_d = invN_d * invN_d;
+    const float invN = 1.0f / (float)N;
+    auto finish_pass = [&](int cur, float dmax, int u, bool arrive) -> bool {
+        __syncthreads();
+        for (int rr = tid; rr < nr; rr += nthr) {
+            float r = 0.f;
+            for (int w = 0; w < (nthr >> 5); ++w) r += S.rowpart[rr * 32 + w];
+            S.rsum[rr] = r;
+        }
+        dmax = warp_max(dmax);
+        if (lane == 0) S.fred[warp] = dmax;
+        __syncthreads();
+        if (warp == 0) {
+            double sp = 0.0;
+            for (int rr = lane; rr < nr; rr += 32) sp += (double)S.rsum[rr];
+            sp = warp_sum_d(sp);
+            float bm = lane < (nthr >> 5) ? S.fred[lane] : 0.f;
+            bm = warp_max(bm);
+            if (lane == 0) {
+                atomicAdd(&P.sbuf[cur], sp);
+                if (bm > 0.f) atomicMax(&P.dbuf[cur], __float_as_uint(bm));
+            }
+        }
+        float* ccur = P.colbuf + (size_t)cur * ldy;
+#pragma unroll
+        for (int k = 0; k < kQpt; ++k) {
+            const int q = tid + k * nthr;
+            if (q < Q) red_add_v4(ccur + 4 * q, cpart[k].x, cpart[k].y, cpart[k].z, cpart[k].w);
+        }
+        if (!grid_barrier(&C->bar, bar_base + G * (gen + 1), err, P.timeout_ns, arrive)) return false;
+        ++gen;
+        // column sums of this pass, scaled by 1/N, for the next round (issued
+        // together with warp 0's loads of s and max|dY| below)
+#pragma unroll
+        for (int k = 0; k < kQpt; ++k) {
+            const int q = tid + k * nthr;
+            if (q < Q) {
+                const float4 c = __ldcg(reinterpret_cast<const float4*>(ccur) + q);
+                cN[k] = make_float4(c.x * invN, c.y * invN, c.z * invN, c.w * invN);
+            }
+        }
+        if (warp == 0) {
+            const double s = __ldcg(&P.sbuf[cur]);
+            const float d = __uint_as_float(__ldcg(&P.dbuf[cur]));
+            const double a_base = invN_d + s * invN2_d;
+            for (int rr = lane; rr < nr; rr += 32)
+                S.arow[rr] = (float)(a_base - (double)S.rsum[rr] * invN_d);
+            if (lane == 0) {
+                S.ictl[0] = isfinite(s) ? 0 : 1;
+                S.ictl[1] = (u > 0 && ((double)d < P.tol_inner || u >= P.max_inner)) ? 1 : 0;
+                S.fctl[0] = d;
+            }
+        }
+        __syncthreads();
+        return true;
+    };
+
 #pragma unroll
     for (int k = 0; k < kQpt; ++k) cpart[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int rr = 0; rr < nr; ++rr) {
@@ -168,55 +230,21 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
         racc = warp_sum(racc);
         if (lane == 0) S.rowpart[rr * 32 + warp] = racc;
     }
-    __syncthreads();
-    {
-        double sp = 0.0;
-        for (int rr = tid; rr < nr; rr += nthr) {
-            float r = 0.f;
-            for (int w = 0; w < (nthr >> 5); ++w) r += S.rowpart[rr * 32 + w];
-            S.rsum[rr] = r;
-            sp += (double)r;
-        }
-        sp = block_sum_d(sp, S.dred);
-        if (tid == 0) atomicAdd(&P.sbuf[0], sp);
-#pragma unroll
-        for (int k = 0; k < kQpt; ++k) {
-            const int q = tid + k * nthr;
-            if (q < Q) red_add_v4(P.colbuf + 4 * q, cpart[k].x, cpart[k].y, cpart[k].z, cpart[k].w);
-        }
-    }
     const bool arrive0 = !(P.skip_arrive && blockIdx.x == 0 && C->outer == 0);
-    if (!grid_barrier(&C->bar, bar_base + G * (gen + 1), err, P.timeout_ns, arrive0)) return;
-    ++gen;
-    {
-        const double s0 = __ldcg(&P.sbuf[0]);
-        if (!isfinite(s0)) {
-            if (tid == 0) atomicCAS(err, 0, FASTPFP_ERR_NONFINITE);
-            return;
-        }
+    if (!finish_pass(0, 0.f, 0, arrive0)) return;
+    if (S.ictl[0]) {
+        if (tid == 0) atomicCAS(err, 0, FASTPFP_ERR_NONFINITE);
+        return;
     }
 
-    // ---- P1/P2 rounds
-    const float invN = 1.0f / (float)N;
-    const double dN = (double)N;
+    // ---- P1/P2 rounds (cN holds c/N of the previous pass, S.arow its a_i)
     int u = 0;
     float delta = 0.f;
     while (true) {
         ++u;
-        const int prev = (u - 1) % 3, cur = u % 3, nxt = (u + 1) % 3;
-        // sums of the previous round
-        const float* cprev = P.colbuf + (size_t)prev * ldy;
+        const int cur = u % 3, nxt = (u + 1) % 3;
 #pragma unroll
-        for (int k = 0; k < kQpt; ++k) {
-            const int q = tid + k * nthr;
-            if (q < Q) {
-                float4 c = __ldcg(reinterpret_cast<const float4*>(cprev) + q);
-                cN[k] = make_float4(c.x * invN, c.y * invN, c.z * invN, c.w * invN);
-            }
-            cpart[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        const double s = __ldcg(&P.sbuf[prev]);
-        const double a_base = 1.0 / dN + s / (dN * dN);
+        for (int k = 0; k < kQpt; ++k) cpart[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         // clear the accumulator of round u+1 (last read in round u-1)
         {
             float* cn = P.colbuf + (size_t)nxt * ldy;
@@ -228,55 +256,45 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
             }
         }
         float dmax = 0.f;
-        for (int rr = 0; rr < nr; ++rr) {
-            float4* row = row_ptr(rr);
-            const float ai = (float)(a_base - (double)S.rsum[rr] / dN);
-            float racc = 0.f;
+        // rows in groups of four so the four row-sum shuffle chains overlap
+        for (int rg = 0; rg < nr; rg += 4) {
+            float racc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int k = 0; k < kQpt; ++k) {
-                const int q = tid + k * nthr;
-                if (q < Q) {
-                    const float4 y = row[q];
-                    float4 z;
-                    z.x = fmaxf((y.x + ai) - cN[k].x, 0.f);
-                    z.y = fmaxf((y.y + ai) - cN[k].y, 0.f);
-                    z.z = fmaxf((y.z + ai) - cN[k].z, 0.f);
-                    z.w = fmaxf((y.w + ai) - cN[k].w, 0.f);
-                    z = mask_cols(z, q, N);
-                    dmax = fmaxf(dmax, fmaxf(fmaxf(fabsf(z.x - y.x), fabsf(z.y - y.y)),
-                                             fmaxf(fabsf(z.z - y.z), fabsf(z.w - y.w))));
-                    row[q] = z;
-                    racc += sum4(z);
-                    cpart[k].x += z.x; cpart[k].y += z.y; cpart[k].z += z.z; cpart[k].w += z.w;
+            for (int j = 0; j < 4; ++j) {
+                const int rr = rg + j;
+                if (rr >= nr) break;
+                float4* row = row_ptr(rr);
+                const float ai = S.arow[rr];
+#pragma unroll
+                for (int k = 0; k < kQpt; ++k) {
+                    const int q = tid + k * nthr;
+                    if (q < Q) {
+                        const float4 y = row[q];
+                        float4 z;
+                        z.x = fmaxf((y.x + ai) - cN[k].x, 0.f);
+                        z.y = fmaxf((y.y + ai) - cN[k].y, 0.f);
+                        z.z = fmaxf((y.z + ai) - cN[k].z, 0.f);
+                        z.w = fmaxf((y.w + ai) - cN[k].w, 0.f);
+                        z = mask_cols(z, q, N);
+                        dmax = fmaxf(dmax, fmaxf(fmaxf(fabsf(z.x - y.x), fabsf(z.y - y.y)),
+                                                 fmaxf(fabsf(z.z - y.z), fabsf(z.w - y.w))));
+                        row[q] = z;
+                        racc[j] += sum4(z);
+                        cpart[k].x += z.x; cpart[k].y += z.y; cpart[k].z += z.z; cpart[k].w += z.w;
+                    }
                 }
             }
-            racc = warp_sum(racc);
-            if (lane == 0) S.rowpart[rr * 32 + warp] = racc;
-        }
-        __syncthreads();
-        double sp = 0.0;
-        for (int rr = tid; rr < nr; rr += nthr) {
-            float r = 0.f;
-            for (int w = 0; w < (nthr >> 5); ++w) r += S.rowpart[rr * 32 + w];
-            S.rsum[rr] = r;
-            sp += (double)r;
-        }
-        sp = block_sum_d(sp, S.dred);
-        const float bmax = block_max_f(dmax, S.fred);
-        if (tid == 0) {
-            atomicAdd(&P.sbuf[cur], sp);
-            atomicMax(&P.dbuf[cur], __float_as_uint(bmax));
-        }
-        float* ccur = P.colbuf + (size_t)cur * ldy;
 #pragma unroll
-        for (int k = 0; k < kQpt; ++k) {
-            const int q = tid + k * nthr;
-            if (q < Q) red_add_v4(ccur + 4 * q, cpart[k].x, cpart[k].y, cpart[k].z, cpart[k].w);
+            for (int j = 0; j < 4; ++j) racc[j] = warp_sum(racc[j]);
+            if (lane == 0) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (rg + j < nr) S.rowpart[(rg + j) * 32 + warp] = racc[j];
+            }
         }
-        if (!grid_barrier(&C->bar, bar_base + G * (gen + 1), err, P.timeout_ns)) return;
-        ++gen;
-        delta = __uint_as_float(__ldcg(&P.dbuf[cur]));
-        if ((double)delta < P.tol_inner || u >= P.max_inner) break;
+        if (!finish_pass(cur, dmax, u, true)) return;
+        delta = S.fctl[0];
+        if (S.ictl[1]) break;
     }
 
     if (P.mode == kPdProjectOnly) {
@@ -415,10 +433,10 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
 
 size_t pd_smem_bytes(int rpc, int Q, bool res) {
     size_t off = res ? (size_t)rpc * Q * 16 : 0;
-    off += (size_t)rpc * 4;
+    off += (size_t)rpc * 4 * 2;
     off += (size_t)rpc * 32 * 4;
     off = (off + 15) & ~size_t(15);
-    off += 32 * 8 + 32 * 4;
+    off += 32 * 8 + 32 * 4 + 4 * 4 + 4 * 4;
     return off;
 }
 
