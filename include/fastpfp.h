@@ -203,6 +203,34 @@ int fastpfp_project(fastpfp_t h, void* stream, float* Y, int N, double tol, int 
 int fastpfp_discretize(fastpfp_t h, void* stream, const float* X, int N, int m,
                        int32_t* row_of_col);
 
+/* ---- entry point for callers that cannot allocate -------------------------
+ * The paper has no counterpart to this call; it exists for callers that are
+ * not allowed to call cudaMalloc -- for example code running inside a host
+ * application's fixed device-memory arena, inside a region being captured
+ * into a CUDA graph, or under a real-time rule that forbids allocation after
+ * start-up.  Such callers cannot create a handle, because fastpfp_create
+ * allocates.
+ *
+ * fastpfp_project_noalloc runs the same successive projection as
+ * fastpfp_project, in place on the caller's N x N device matrix Y (row-major,
+ * leading dimension N), on the CUDA device that is current.  It allocates
+ * nothing: the projection's own scratch (column-sum accumulators, FP64
+ * totals, round maxima, barrier and control words) is one file-scope device
+ * array of about 100 KB that every GPU which loads this library holds until
+ * the process exits.
+ *   - N must be a multiple of 4 with 4 <= N <= 4096 and Y 16-byte aligned;
+ *     larger N returns FASTPFP_ERR_SIZE, other shapes FASTPFP_ERR_ARG.
+ *   - The first call on a device resolves the array's device address and sets
+ *     the kernel's attributes for that device; make that first call before
+ *     any stream capture.
+ *   - Every call on a device shares the one array: the call clears what must
+ *     start at zero, but two calls whose work overlaps on the GPU (different
+ *     streams, or different host threads) race on it and give wrong results.
+ *   - Synchronises `stream`; *iters and *last_delta (host, nullable) as in
+ *     fastpfp_project.  Errors: ERR_ARG, ERR_SIZE, ERR_CUDA, ERR_TIMEOUT. */
+int fastpfp_project_noalloc(void* stream, float* Y, int N, double tol, int max_iter, int* iters,
+                            double* last_delta);
+
 /* Human-readable name of an error code. */
 const char* fastpfp_error_string(int code);
 

@@ -29,7 +29,7 @@ FP32, BF16 = 0, 1
 EXPORTS = ("fastpfp_default_params", "fastpfp_create", "fastpfp_destroy", "fastpfp_match",
            "fastpfp_match_host", "fastpfp_match_batched", "fastpfp_last_trace",
            "fastpfp_gradient", "fastpfp_affinity", "fastpfp_project", "fastpfp_discretize",
-           "fastpfp_error_string")
+           "fastpfp_project_noalloc", "fastpfp_error_string")
 
 
 class fastpfp_params(C.Structure):
@@ -88,6 +88,8 @@ def lib():
     l.fastpfp_project.argtypes = [P, V, P, I, C.c_double, I, C.POINTER(C.c_int),
                                   C.POINTER(C.c_double)]
     l.fastpfp_discretize.argtypes = [P, V, P, I, I, P]
+    l.fastpfp_project_noalloc.argtypes = [V, P, I, C.c_double, I, C.POINTER(C.c_int),
+                                          C.POINTER(C.c_double)]
     l.fastpfp_error_string.argtypes = [I]
     l.fastpfp_error_string.restype = C.c_char_p
     for name in EXPORTS:
@@ -282,3 +284,15 @@ class Solver:
         _check(lib().fastpfp_discretize(self._h, _stream(stream), _ptr(X), N, m, _ptr(out)),
                "fastpfp_discretize")
         return out
+
+
+def project_noalloc(Y, tol=1e-6, max_iter=1000, stream=None):
+    """fastpfp_project_noalloc: in-place P_D on the N x N CUDA tensor Y
+    without a handle and without any device allocation (N a multiple of 4,
+    N <= 4096).  Returns (iterations, last delta)."""
+    it = C.c_int(0)
+    d = C.c_double(0.0)
+    _check(lib().fastpfp_project_noalloc(_stream(stream), _ptr(Y), Y.shape[0], float(tol),
+                                         int(max_iter), C.byref(it), C.byref(d)),
+           "fastpfp_project_noalloc")
+    return it.value, d.value
