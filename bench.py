@@ -54,15 +54,15 @@ def pd_source_hash() -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def ncu_traffic_per_unit():
-    """DRAM bytes per projection round from the committed ncu summary, or None
-    when the projection kernel changed since the counters were taken."""
+def ncu_traffic_per_launch():
+    """DRAM bytes of one projection launch from the committed ncu summary, or
+    None when the projection kernel changed since the counters were taken."""
     try:
         text = open(PROFILE_SUMMARY).read()
     except OSError:
         return None
     h = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
-    t = re.search(r"dram_bytes_per_round:\s*([0-9.eE+-]+)", text)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+-]+)", text)
     if not h or not t or h.group(1) != pd_source_hash():
         return None
     return float(t.group(1))
@@ -274,8 +274,7 @@ def main():
     alg_bytes = inner * bytes_round + outer * bytes_blend
     achieved = alg_bytes / (ms_proj / 1e3) / 1e9 if ms_proj > 0 else None
     peak, peak_kind = peaks()
-    tr_round = ncu_traffic_per_unit()
-    traffic = (tr_round * inner / outer + 0.0) if (tr_round is not None and outer) else None
+    traffic = ncu_traffic_per_launch()
     launches = sum(s.launches for s in flat)
 
     # end to end through the public host-memory entry point
