@@ -198,7 +198,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=4, help="pairs per step and rank")
+    ap.add_argument("--batch", type=int, default=7, help="pairs per step and rank")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-budget", type=float, default=10.0, dest="ref_budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")

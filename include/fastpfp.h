@@ -158,16 +158,23 @@ int fastpfp_match_host(fastpfp_t h, void* stream,
 
 /* Solves `count` independent pairs with the same parameters (Algorithm 1
  * per pair).  pairs[] is a host array of device-pointer descriptors; st is
- * a nullable host array of `count` statistics.  Synchronises `stream`.
+ * a nullable host array of `count` statistics.  Pairs are solved in waves:
+ * consecutive pairs whose slacked matrices fit in shared memory together
+ * (N <= 4096 each, at most 64 and at most max_batch per wave) share one
+ * projection launch per outer iteration; with profile = 1 a wave's phase
+ * times are split equally between its pairs.  Synchronises `stream`.
  * Errors as fastpfp_match, plus ERR_ARG when count > max_batch. */
 int fastpfp_match_batched(fastpfp_t h, void* stream, int count, const fastpfp_pair* pairs,
                           const fastpfp_params* p, fastpfp_stats* st);
 
-/* Copies the per-outer-iteration trace of the last solve on this handle:
- * inner_counts[t] = P1/P2 rounds of outer iteration t, deltas[t] =
- * max|X(t+1) - X(t)|.  Either array may be NULL.  Returns the number of
- * outer iterations (at most cap entries are written), or an error code. */
-int fastpfp_last_trace(fastpfp_t h, int* inner_counts, double* deltas, int cap);
+/* Copies the per-outer-iteration trace of a pair of the last call on this
+ * handle: inner_counts[t] = P1/P2 rounds of outer iteration t, deltas[t] =
+ * max|X(t+1) - X(t)|.  `pair` is 0 after fastpfp_match / _host, and after
+ * fastpfp_match_batched the index within that call of a pair of its last
+ * wave.  Either array may be NULL.  Returns the number of outer iterations
+ * (at most cap entries are written), or ERR_ARG for a pair whose trace is no
+ * longer held. */
+int fastpfp_last_trace(fastpfp_t h, int pair, int* inner_counts, double* deltas, int cap);
 
 /* ---- single steps of Algorithm 1, for step-by-step checking ------------ */
 

@@ -1,18 +1,27 @@
 // fastpfp_api.cu -- the C ABI declared in include/fastpfp.h.
 //
 // A handle owns every device buffer the solver touches, allocated once in
-// fastpfp_create for graphs of up to max_n nodes.  A solve enqueues, on the
-// caller's stream, the whole of Algorithm 1 without host round trips: for
-// every outer iteration the two products of the gradient and one cooperative
-// launch of the projection kernel, which also blends, normalises and decides
-// (on the device) whether the loop continues.  Launches after the decision
-// to stop return at once.  The greedy discretisation and the objective
-// follow, and the control block is copied back once at the end.
+// fastpfp_create: one "slot" of per-pair scratch (Y, X, T, K, accumulators,
+// control block, discretisation buffers) for each pair that can be solved at
+// the same time, sized for graphs of up to max_n nodes.
+//
+// One pair (fastpfp_match) runs Algorithm 1 with pd_kernel: per outer
+// iteration the two gradient products and one cooperative launch that runs
+// every P1/P2 round, blends, normalises and decides on the device whether
+// the loop continues.  A batch (fastpfp_match_batched) is cut into waves of
+// pairs whose slacked matrices fit in shared memory together; per outer
+// iteration a wave runs every pair's products and one launch of pdb_kernel,
+// which shares each grid barrier between all pairs of the wave.  Outer
+// iterations are enqueued in chunks: after each chunk the host checks (one
+// chunk behind, so the GPU never idles) whether every pair has stopped, and
+// stops enqueueing.  Launches after a pair's stop return at once.
+#include <algorithm>
 #include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -26,29 +35,46 @@ constexpr int kMaxK = 256;       // attribute dimension staged by fastpfp_match_
 constexpr size_t kCtrlHeader = offsetof(Ctrl, inner_trace);
 constexpr int kProfIters = 128;                   // outer iterations timed when profile = 1
 constexpr int kProfEvents = 2 * kProfIters + 3;   // iteration boundaries + discretisation
+constexpr int kChunk = 4;                         // outer iterations enqueued between checks
+constexpr long long kMinElemsPerCta = 8192;       // smallest band worth a CTA of its own
 
 inline int round4(int x) { return (x + 3) & ~3; }
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Per-pair device scratch.
+struct Slot {
+    float *Y, *X, *T, *K;
+    __nv_bfloat16 *A16, *A216, *Xt16, *T16;
+    float* colbuf;
+    double* sbuf;
+    unsigned* dbuf;
+    Ctrl* ctrl;
+    DiscBuffers disc;
+};
+
 }  // namespace
 
 struct fastpfp_s {
-    int device = 0, max_n = 0, max_batch = 0, num_sms = 0, ld = 0;
+    int device = 0, max_n = 0, max_batch = 0, num_sms = 0, ld = 0, nslots = 0;
     char* pool = nullptr;
     size_t pool_bytes = 0;
-    float *Y = nullptr, *X = nullptr, *T = nullptr, *K = nullptr;
-    __nv_bfloat16 *A16 = nullptr, *A216 = nullptr, *Xt16 = nullptr, *T16 = nullptr;
-    float* colbuf = nullptr;
-    double* sbuf = nullptr;
-    unsigned* dbuf = nullptr;
-    Ctrl* ctrl = nullptr;
-    DiscBuffers disc{};
+    std::vector<Slot> slots;
+    // wave tables (device) and their pinned staging
+    PairDesc* d_pairs = nullptr;
+    int* d_band = nullptr;
+    WaveCtrl* d_wave = nullptr;
+    PairDesc* h_pairs = nullptr;
+    int* h_band = nullptr;
+    int* h_done = nullptr;       // pinned, 2 entries: stop flags read one chunk behind
     // staging for fastpfp_match_host
     float *sA = nullptr, *sA2 = nullptr, *sB = nullptr, *sB2 = nullptr, *sX0 = nullptr, *sXout = nullptr;
     int32_t* sperm = nullptr;
     Ctrl* host_ctrl = nullptr;   // pinned, max_batch control-block headers
-    int last_outer = 0;
+    int last_first = 0;          // pairs [last_first, last_first + last_count) of the last call
+    int last_count = 0;          // still hold their traces in slots 0, 1, ...
+
     cudaEvent_t ev[kProfEvents] = {};
+    cudaEvent_t chunk_ev[2] = {};
 };
 
 namespace {
@@ -74,17 +100,6 @@ bool params_ok(const fastpfp_params* p) {
 long long timeout_ns(const fastpfp_params* p) {
     const int ms = (p && p->timeout_ms > 0) ? p->timeout_ms : 2000;
     return (long long)ms * 1000000ll;
-}
-
-// The projection kernel leaves its rotating accumulators zero when it
-// completes; a launch that stopped on an error may not.  Every solve
-// therefore starts from cleared accumulators.
-cudaError_t clear_accumulators(fastpfp_t h, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(h->colbuf, 0, 3 * (size_t)h->ld * sizeof(float), s);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(h->sbuf, 0, 3 * sizeof(double), s);
-    if (e != cudaSuccess) return e;
-    return cudaMemsetAsync(h->dbuf, 0, 3 * sizeof(unsigned), s);
 }
 
 // Arguments of one solve in canonical orientation (N >= m).
@@ -124,38 +139,101 @@ Problem canonical(const float* A, int n_a, const float* A2, int n_b, const float
     return q;
 }
 
-// Enqueues one whole solve on stream s.  The control-block header lands in
-// *host_slot (pinned) once the stream reaches the end of the solve.  With
-// p->profile the handle's events bracket every phase; *launches receives the
-// number of kernels enqueued.
-int enqueue_solve(fastpfp_t h, cudaStream_t s, const Problem& q, const fastpfp_params* p,
-                  Ctrl* host_slot, int* launches) {
+// ---- the per-pair pieces of a solve ---------------------------------------
+
+// Control block, accumulators and Y cleared; K and the initial X written.
+// A solve that stopped on an error may leave the accumulators dirty, so every
+// solve starts from cleared ones.  Returns the kernels launched or < 0.
+int enqueue_setup(const Slot& sl, cudaStream_t s, const Problem& q, const fastpfp_params* p,
+                  int ld) {
+    const int ldy = round4(q.N), ldx = round4(q.m);
+    const bool bf16 = p->precision == FASTPFP_BF16;
+    FP_CUDA(cudaMemsetAsync(sl.ctrl, 0, kCtrlHeader, s));
+    FP_CUDA(cudaMemsetAsync(sl.colbuf, 0, 3 * (size_t)ld * sizeof(float), s));
+    FP_CUDA(cudaMemsetAsync(sl.sbuf, 0, 3 * sizeof(double), s));
+    FP_CUDA(cudaMemsetAsync(sl.dbuf, 0, 3 * sizeof(unsigned), s));
+    FP_CUDA(cudaMemsetAsync(sl.Y, 0, (size_t)q.N * ldy * sizeof(float), s));
+    FP_CUDA(init_ctrl(sl.ctrl, bf16 ? 1 : 0, s));
+    int nl = 2;
+    if (q.k > 0) {
+        FP_CUDA(affinity(q.B, q.B2, q.N, q.m, q.k, sl.K, ldx, s));
+        ++nl;
+    }
+    FP_CUDA(init_x(sl.X, q.N, q.m, ldx, q.X0, q.transposed, bf16 ? sl.Xt16 : nullptr, ldy, s));
+    return nl;
+}
+
+// The gradient of Section 4.1: T = A X, then Y[:, :m] = T A' + lambda K.
+int enqueue_gradient(const Slot& sl, cudaStream_t s, const Problem& q, const fastpfp_params* p) {
+    const int ldy = round4(q.N), ldx = round4(q.m);
+    GemmF32Args g1{q.A, q.N, sl.X, ldx, sl.T, ldx, nullptr, 0, 0.f, q.N, q.m, q.N, sl.ctrl};
+    GemmF32Args g2{sl.T, ldx, q.A2, q.m, sl.Y, ldy, q.k ? sl.K : nullptr, ldx,
+                   q.k ? (float)p->lambda : 0.f, q.N, q.m, q.m, sl.ctrl};
+    FP_CUDA(gemm_f32(g1, s));
+    FP_CUDA(gemm_f32(g2, s));
+    return 2;
+}
+
+// Discretisation, objective, caller-orientation outputs, control header.
+int enqueue_finish(const Slot& sl, cudaStream_t s, const Problem& q, const fastpfp_params* p,
+                   int num_sms, Ctrl* host_slot) {
+    const int ldx = round4(q.m);
+    FP_CUDA(discretize(sl.X, q.N, q.m, ldx, sl.disc, sl.ctrl, timeout_ns(p), num_sms, s));
+    FP_CUDA(objective(q.A, q.N, q.A2, q.m, q.k ? sl.K : nullptr, ldx, q.k ? (float)p->lambda : 0.f,
+                      sl.disc.col_match, sl.ctrl, s));
+    FP_CUDA(write_outputs(sl.disc.col_match, q.N, q.m, q.transposed, q.perm_out, sl.X, ldx, q.X_out, s));
+    FP_CUDA(cudaMemcpyAsync(host_slot, sl.ctrl, kCtrlHeader, cudaMemcpyDeviceToHost, s));
+    return 2 + (q.perm_out ? (q.transposed ? 1 : 2) : 0) + (q.X_out ? 1 : 0);
+}
+
+// Enqueues outer iterations in chunks of kChunk; `step(t)` enqueues outer
+// iteration t and returns the kernels it launched (or < 0).  After every
+// chunk four ints of the device control word at `d_words` are copied to
+// pinned memory behind an event; the host checks the previous chunk's copy
+// (words done_idx and err_idx), so one chunk is always queued ahead.
+template <typename Step>
+int run_outer(fastpfp_t h, cudaStream_t s, const int* d_words, int done_idx, int err_idx,
+              int max_outer, Step step) {
+    int t = 0, chunk = 0, nl = 0;
+    while (t < max_outer) {
+        const int tc = std::min(kChunk, max_outer - t);
+        for (int i = 0; i < tc; ++i, ++t) {
+            const int r = step(t);
+            if (r < 0) return r;
+            nl += r;
+        }
+        if (t >= max_outer) break;
+        const int slot = chunk & 1;
+        FP_CUDA(cudaMemcpyAsync(&h->h_done[4 * slot], d_words, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        FP_CUDA(cudaEventRecord(h->chunk_ev[slot], s));
+        if (chunk >= 1) {
+            FP_CUDA(cudaEventSynchronize(h->chunk_ev[slot ^ 1]));
+            const int* w = &h->h_done[4 * (slot ^ 1)];
+            if (w[done_idx] || w[err_idx]) break;
+        }
+        ++chunk;
+    }
+    return nl;
+}
+
+// One pair through pd_kernel.  Returns the kernels launched or < 0.
+int enqueue_single(fastpfp_t h, cudaStream_t s, const Slot& sl, const Problem& q,
+                   const fastpfp_params* p, Ctrl* host_slot) {
     const int N = q.N, m = q.m;
     const int ldy = round4(N), ldx = round4(m);
-    const bool bf16 = p->precision == FASTPFP_BF16;
-    if (bf16) return FASTPFP_ERR_UNSUPPORTED;
-
-    FP_CUDA(cudaMemsetAsync(h->ctrl, 0, kCtrlHeader, s));
-    FP_CUDA(clear_accumulators(h, s));
-    FP_CUDA(cudaMemsetAsync(h->Y, 0, (size_t)N * ldy * sizeof(float), s));
-    FP_CUDA(init_ctrl(h->ctrl, bf16 ? 1 : 0, s));
-    const float* Kp = nullptr;
-    if (q.k > 0) {
-        FP_CUDA(affinity(q.B, q.B2, N, m, q.k, h->K, ldx, s));
-        Kp = h->K;
-    }
-    FP_CUDA(init_x(h->X, N, m, ldx, q.X0, q.transposed, bf16 ? h->Xt16 : nullptr, ldy, s));
-
+    if (p->precision == FASTPFP_BF16) return FASTPFP_ERR_UNSUPPORTED;
+    int nl = enqueue_setup(sl, s, q, p, h->ld);
+    if (nl < 0) return nl;
     PdLaunch L;
     pd_plan(N, h->num_sms, &L);
     PdParams P{};
-    P.Y = h->Y;
+    P.Y = sl.Y;
     P.N = N;
     P.ldy = ldy;
     P.m = m;
-    P.X = h->X;
+    P.X = sl.X;
     P.ldx = ldx;
-    P.Xt16 = bf16 ? h->Xt16 : nullptr;
+    P.Xt16 = nullptr;
     P.ldxt = ldy;
     P.alpha = p->alpha;
     P.normalize = p->normalize_max ? 1 : 0;
@@ -166,56 +244,48 @@ int enqueue_solve(fastpfp_t h, cudaStream_t s, const Problem& q, const fastpfp_p
     P.max_outer = p->max_outer;
     P.refine_iters = p->refine_iters;
     P.switch_tol = p->switch_tol;
-    P.colbuf = h->colbuf;
-    P.sbuf = h->sbuf;
-    P.dbuf = h->dbuf;
-    P.ctrl = h->ctrl;
+    P.colbuf = sl.colbuf;
+    P.sbuf = sl.sbuf;
+    P.dbuf = sl.dbuf;
+    P.ctrl = sl.ctrl;
     P.timeout_ns = timeout_ns(p);
     P.rpc = L.rpc;
     P.mode = kPdOuterStep;
     P.skip_arrive = (p->debug_flags & 1) ? 1 : 0;
-
-    GemmF32Args g1{q.A, N, h->X, ldx, h->T, ldx, nullptr, 0, 0.f, N, m, N, h->ctrl};
-    GemmF32Args g2{h->T, ldx, q.A2, m, h->Y, ldy, Kp, ldx, q.k ? (float)p->lambda : 0.f, N, m, m,
-                   h->ctrl};
     const bool prof = p->profile != 0;
-    int nl = 2 + (q.k > 0 ? 1 : 0);   // init_ctrl, init_x, affinity
-    for (int t = 0; t < p->max_outer; ++t) {
+    static_assert(offsetof(Ctrl, done) == 0 && offsetof(Ctrl, error) == 8, "Ctrl head layout");
+    const int r = run_outer(h, s, &sl.ctrl->done, 0, 2, p->max_outer, [&](int t) -> int {
         const bool pt = prof && t < kProfIters;
         if (pt && t == 0) FP_CUDA(cudaEventRecord(h->ev[0], s));
-        FP_CUDA(gemm_f32(g1, s));   // T = A X
-        FP_CUDA(gemm_f32(g2, s));   // Y[:, :m] = T A' + lambda K
+        const int g = enqueue_gradient(sl, s, q, p);
+        if (g < 0) return g;
         if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 1], s));
         FP_CUDA(pd_launch(L, P, s));
         if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 2], s));
-        nl += 3;
-    }
+        return g + 1;
+    });
+    if (r < 0) return r;
+    nl += r;
     if (prof) FP_CUDA(cudaEventRecord(h->ev[kProfEvents - 2], s));
-    FP_CUDA(discretize(h->X, N, m, ldx, h->disc, h->ctrl, timeout_ns(p), h->num_sms, s));
+    const int f = enqueue_finish(sl, s, q, p, h->num_sms, host_slot);
+    if (f < 0) return f;
     if (prof) FP_CUDA(cudaEventRecord(h->ev[kProfEvents - 1], s));
-    FP_CUDA(objective(q.A, N, q.A2, m, Kp, ldx, q.k ? (float)p->lambda : 0.f, h->disc.col_match,
-                      h->ctrl, s));
-    FP_CUDA(write_outputs(h->disc.col_match, N, m, q.transposed, q.perm_out, h->X, ldx, q.X_out, s));
-    nl += 2 + (q.perm_out ? (q.transposed ? 1 : 2) : 0) + (q.X_out ? 1 : 0);
-    FP_CUDA(cudaMemcpyAsync(host_slot, h->ctrl, kCtrlHeader, cudaMemcpyDeviceToHost, s));
-    if (launches) *launches = nl;
-    return FASTPFP_OK;
+    return nl + f;
 }
 
-// Per-phase times of the last profiled solve (call after the stream synced).
-void read_profile(fastpfp_t h, int outer, int max_outer, fastpfp_stats* st) {
+// Per-phase times of the last profiled solve (after the stream synced).
+void read_profile(fastpfp_t h, int outer, float share, fastpfp_stats* st) {
     if (!st) return;
     float g = 0.f, pr = 0.f, d = 0.f, x = 0.f;
     const int T = outer < kProfIters ? outer : kProfIters;
-    (void)max_outer;
     for (int t = 0; t < T; ++t) {
         if (cudaEventElapsedTime(&x, h->ev[2 * t], h->ev[2 * t + 1]) == cudaSuccess) g += x;
         if (cudaEventElapsedTime(&x, h->ev[2 * t + 1], h->ev[2 * t + 2]) == cudaSuccess) pr += x;
     }
     if (cudaEventElapsedTime(&x, h->ev[kProfEvents - 2], h->ev[kProfEvents - 1]) == cudaSuccess) d = x;
-    st->ms_gemm = g;
-    st->ms_proj = pr;
-    st->ms_disc = d;
+    st->ms_gemm = g * share;
+    st->ms_proj = pr * share;
+    st->ms_disc = d * share;
 }
 
 int fill_stats(const Ctrl& c, int transposed, int launches, fastpfp_stats* st) {
@@ -234,6 +304,164 @@ int fill_stats(const Ctrl& c, int transposed, int launches, fastpfp_stats* st) {
         st->objective = c.objective;
     }
     return status;
+}
+
+// ---- waves of the batched path ---------------------------------------------
+
+struct Wave {
+    int first = 0, count = 0, grid = 0;
+    size_t smem = 0;
+    PdbLayout layout{};
+    std::vector<int> band;   // grid + 1 boundaries
+};
+
+// Splits the concatenated rows of pairs [first, first + count) into at most
+// num_sms bands of about equal entry counts; fills the layout maxima.
+// Returns false when a band would not fit in shared memory.
+bool plan_bands(const std::vector<Problem>& qs, int first, int count, int num_sms, Wave* w) {
+    long long E = 0;
+    int rows = 0;
+    for (int i = 0; i < count; ++i) {
+        E += (long long)qs[first + i].N * round4(qs[first + i].N);
+        rows += qs[first + i].N;
+    }
+    long long gl = (E + kMinElemsPerCta - 1) / kMinElemsPerCta;
+    int G = (int)std::min<long long>(num_sms, std::max<long long>(1, gl));
+    G = std::min(G, rows);
+    w->band.assign(G + 1, rows);
+    w->band[0] = 0;
+    int b = 0;
+    long long cum = 0;
+    int gr = 0;
+    PdbLayout L{0, 0, 0};
+    int cur_rows = 0, cur_cols = 0, cur_elems = 0, cur_segs = 0, last_pair = -1;
+    bool ok = true;
+    auto close_band = [&]() {
+        L.max_band_rows = std::max(L.max_band_rows, cur_rows);
+        L.max_band_cols = std::max(L.max_band_cols, cur_cols);
+        L.max_band_elems = std::max(L.max_band_elems, cur_elems);
+        if (cur_segs > kMaxSeg) ok = false;
+        cur_rows = cur_cols = cur_elems = cur_segs = 0;
+        last_pair = -1;
+    };
+    for (int i = 0; i < count; ++i) {
+        const int N = qs[first + i].N, ldy = round4(N);
+        for (int r = 0; r < N; ++r, ++gr) {
+            if (b < G - 1 && cum >= E * (b + 1) / G && cur_rows > 0) {
+                close_band();
+                ++b;
+                w->band[b] = gr;
+            }
+            if (last_pair != i) {
+                cur_cols += ldy;
+                ++cur_segs;
+                last_pair = i;
+            }
+            ++cur_rows;
+            cur_elems += ldy;
+            cum += ldy;
+        }
+    }
+    close_band();
+    for (int c = b + 1; c <= G; ++c) w->band[c] = rows;
+    w->first = first;
+    w->count = count;
+    w->grid = G;
+    w->layout = L;
+    w->smem = pdb_smem_bytes(L, kPdbThreads);
+    return ok && w->smem <= (size_t)kPdMaxSmem;
+}
+
+// Largest wave starting at `first` (at least one pair when it fits at all).
+bool plan_wave(const std::vector<Problem>& qs, int first, int nslots, int num_sms, Wave* w) {
+    int best = 0;
+    Wave cand;
+    const int limit = std::min<int>({(int)qs.size() - first, nslots, kMaxWavePairs});
+    for (int c = 1; c <= limit; ++c) {
+        if (qs[first + c - 1].N > kPdbMaxN) break;
+        if (!plan_bands(qs, first, c, num_sms, &cand)) break;
+        *w = cand;
+        best = c;
+    }
+    return best > 0;
+}
+
+// One wave through pdb_kernel.  Returns the kernels launched or < 0.
+int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, const Wave& w,
+                 const fastpfp_params* p, Ctrl* host_slots) {
+    int nl = 0;
+    int row0 = 0;
+    for (int i = 0; i < w.count; ++i) {
+        const Problem& q = qs[w.first + i];
+        const Slot& sl = h->slots[i];
+        const int r = enqueue_setup(sl, s, q, p, h->ld);
+        if (r < 0) return r;
+        nl += r;
+        PairDesc d{};
+        d.Y = sl.Y;
+        d.X = sl.X;
+        d.Xt16 = nullptr;
+        d.colbuf = sl.colbuf;
+        d.sbuf = sl.sbuf;
+        d.dbuf = sl.dbuf;
+        d.ctrl = sl.ctrl;
+        d.N = q.N;
+        d.ldy = round4(q.N);
+        d.m = q.m;
+        d.ldx = round4(q.m);
+        d.ldxt = d.ldy;
+        d.row0 = row0;
+        row0 += q.N;
+        h->h_pairs[i] = d;
+    }
+    for (int b = 0; b <= w.grid; ++b) h->h_band[b] = w.band[b];
+    FP_CUDA(cudaMemcpyAsync(h->d_pairs, h->h_pairs, sizeof(PairDesc) * w.count, cudaMemcpyHostToDevice, s));
+    FP_CUDA(cudaMemcpyAsync(h->d_band, h->h_band, sizeof(int) * (w.grid + 1), cudaMemcpyHostToDevice, s));
+    FP_CUDA(cudaMemsetAsync(h->d_wave, 0, sizeof(WaveCtrl), s));
+    PdbParams P{};
+    P.pairs = h->d_pairs;
+    P.npairs = w.count;
+    P.band_row = h->d_band;
+    P.wave = h->d_wave;
+    P.layout = w.layout;
+    P.alpha = p->alpha;
+    P.normalize = p->normalize_max ? 1 : 0;
+    P.slack_reset = p->slack_policy == 1 ? 1 : 0;
+    P.tol_inner = p->tol_inner;
+    P.max_inner = p->max_inner;
+    P.tol_outer = p->tol_outer;
+    P.max_outer = p->max_outer;
+    P.refine_iters = p->refine_iters;
+    P.switch_tol = p->switch_tol;
+    P.timeout_ns = timeout_ns(p);
+    const bool prof = p->profile != 0;
+    static_assert(offsetof(WaveCtrl, error) == 8 && offsetof(WaveCtrl, all_done) == 12,
+                  "WaveCtrl layout");
+    const int r = run_outer(h, s, reinterpret_cast<const int*>(h->d_wave), 3, 2, p->max_outer,
+                            [&](int t) -> int {
+        const bool pt = prof && t < kProfIters;
+        if (pt && t == 0) FP_CUDA(cudaEventRecord(h->ev[0], s));
+        int n = 0;
+        for (int i = 0; i < w.count; ++i) {
+            const int g = enqueue_gradient(h->slots[i], s, qs[w.first + i], p);
+            if (g < 0) return g;
+            n += g;
+        }
+        if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 1], s));
+        FP_CUDA(pdb_launch(P, w.grid, w.smem, s));
+        if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 2], s));
+        return n + 1;
+    });
+    if (r < 0) return r;
+    nl += r;
+    if (prof) FP_CUDA(cudaEventRecord(h->ev[kProfEvents - 2], s));
+    for (int i = 0; i < w.count; ++i) {
+        const int f = enqueue_finish(h->slots[i], s, qs[w.first + i], p, h->num_sms, &host_slots[i]);
+        if (f < 0) return f;
+        nl += f;
+    }
+    if (prof) FP_CUDA(cudaEventRecord(h->ev[kProfEvents - 1], s));
+    return nl;
 }
 
 }  // namespace
@@ -255,6 +483,7 @@ void fastpfp_default_params(fastpfp_params* p) {
     p->normalize_max = 1;
     p->slack_policy = 0;
     p->timeout_ms = 2000;
+    p->profile = 0;
     p->debug_flags = 0;
 }
 
@@ -283,8 +512,10 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     h->max_n = max_n;
     h->max_batch = max_batch;
     h->ld = round4(max_n);
+    h->nslots = std::min(max_batch, kMaxWavePairs);
     if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        pd_configure() != cudaSuccess || disc_configure() != cudaSuccess) {
+        pd_configure() != cudaSuccess || pdb_configure() != cudaSuccess ||
+        disc_configure() != cudaSuccess) {
         delete h;
         return FASTPFP_ERR_CUDA;
     }
@@ -293,41 +524,66 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     const size_t b16mat = align256(n * ld * sizeof(__nv_bfloat16));
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
-    const size_t oY = take(f32mat), oX = take(f32mat), oT = take(f32mat), oK = take(f32mat);
-    const size_t oA16 = take(b16mat), oA216 = take(b16mat), oXt16 = take(b16mat), oT16 = take(b16mat);
-    const size_t ocol = take(3 * ld * sizeof(float)), os = take(3 * sizeof(double)),
-                 od = take(3 * sizeof(unsigned)), octrl = take(sizeof(Ctrl));
-    const size_t orm = take(n * 4), ocm = take(n * 4), orb = take(n * 8), ocb = take(2 * n * 8);
+    struct SlotOff { size_t Y, X, T, K, A16, A216, Xt16, T16, col, s, d, ctrl, rm, cm, rb, cb; };
+    std::vector<SlotOff> so(h->nslots);
+    for (auto& o : so) {
+        o.Y = take(f32mat); o.X = take(f32mat); o.T = take(f32mat); o.K = take(f32mat);
+        o.A16 = take(b16mat); o.A216 = take(b16mat); o.Xt16 = take(b16mat); o.T16 = take(b16mat);
+        o.col = take(3 * ld * sizeof(float)); o.s = take(3 * sizeof(double));
+        o.d = take(3 * sizeof(unsigned)); o.ctrl = take(sizeof(Ctrl));
+        o.rm = take(n * 4); o.cm = take(n * 4); o.rb = take(n * 8); o.cb = take(2 * n * 8);
+    }
+    const size_t opairs = take(sizeof(PairDesc) * kMaxWavePairs);
+    const size_t oband = take(sizeof(int) * (h->num_sms + 1));
+    const size_t owave = take(sizeof(WaveCtrl));
     const size_t osA = take(n * n * 4), osA2 = take(n * n * 4), osB = take(n * kMaxK * 4),
                  osB2 = take(n * kMaxK * 4), osX0 = take(n * n * 4), osXo = take(n * n * 4),
                  osp = take(n * 4);
     h->pool_bytes = off;
-    if (cudaMalloc(&h->pool, off) != cudaSuccess) {
+    auto fail = [&](int code) {
+        for (int e = 0; e < kProfEvents; ++e)
+            if (h->ev[e]) cudaEventDestroy(h->ev[e]);
+        for (int e = 0; e < 2; ++e)
+            if (h->chunk_ev[e]) cudaEventDestroy(h->chunk_ev[e]);
+        if (h->host_ctrl) cudaFreeHost(h->host_ctrl);
+        if (h->h_pairs) cudaFreeHost(h->h_pairs);
+        if (h->h_band) cudaFreeHost(h->h_band);
+        if (h->h_done) cudaFreeHost(h->h_done);
+        if (h->pool) cudaFree(h->pool);
         delete h;
-        return FASTPFP_ERR_CUDA;
-    }
-    if (cudaMallocHost(&h->host_ctrl, sizeof(Ctrl) * (size_t)max_batch) != cudaSuccess) {
-        cudaFree(h->pool);
-        delete h;
-        return FASTPFP_ERR_CUDA;
-    }
+        return code;
+    };
+    if (cudaMalloc(&h->pool, off) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
+    if (cudaMallocHost(&h->host_ctrl, sizeof(Ctrl) * (size_t)max_batch) != cudaSuccess ||
+        cudaMallocHost(&h->h_pairs, sizeof(PairDesc) * kMaxWavePairs) != cudaSuccess ||
+        cudaMallocHost(&h->h_band, sizeof(int) * (h->num_sms + 1)) != cudaSuccess ||
+        cudaMallocHost(&h->h_done, sizeof(int) * 8) != cudaSuccess)
+        return fail(FASTPFP_ERR_CUDA);
     char* b = h->pool;
-    h->Y = (float*)(b + oY);
-    h->X = (float*)(b + oX);
-    h->T = (float*)(b + oT);
-    h->K = (float*)(b + oK);
-    h->A16 = (__nv_bfloat16*)(b + oA16);
-    h->A216 = (__nv_bfloat16*)(b + oA216);
-    h->Xt16 = (__nv_bfloat16*)(b + oXt16);
-    h->T16 = (__nv_bfloat16*)(b + oT16);
-    h->colbuf = (float*)(b + ocol);
-    h->sbuf = (double*)(b + os);
-    h->dbuf = (unsigned*)(b + od);
-    h->ctrl = (Ctrl*)(b + octrl);
-    h->disc.row_match = (int32_t*)(b + orm);
-    h->disc.col_match = (int32_t*)(b + ocm);
-    h->disc.row_best = (unsigned long long*)(b + orb);
-    h->disc.col_best = (unsigned long long*)(b + ocb);
+    h->slots.resize(h->nslots);
+    for (int i = 0; i < h->nslots; ++i) {
+        const SlotOff& o = so[i];
+        Slot& sl = h->slots[i];
+        sl.Y = (float*)(b + o.Y);
+        sl.X = (float*)(b + o.X);
+        sl.T = (float*)(b + o.T);
+        sl.K = (float*)(b + o.K);
+        sl.A16 = (__nv_bfloat16*)(b + o.A16);
+        sl.A216 = (__nv_bfloat16*)(b + o.A216);
+        sl.Xt16 = (__nv_bfloat16*)(b + o.Xt16);
+        sl.T16 = (__nv_bfloat16*)(b + o.T16);
+        sl.colbuf = (float*)(b + o.col);
+        sl.sbuf = (double*)(b + o.s);
+        sl.dbuf = (unsigned*)(b + o.d);
+        sl.ctrl = (Ctrl*)(b + o.ctrl);
+        sl.disc.row_match = (int32_t*)(b + o.rm);
+        sl.disc.col_match = (int32_t*)(b + o.cm);
+        sl.disc.row_best = (unsigned long long*)(b + o.rb);
+        sl.disc.col_best = (unsigned long long*)(b + o.cb);
+    }
+    h->d_pairs = (PairDesc*)(b + opairs);
+    h->d_band = (int*)(b + oband);
+    h->d_wave = (WaveCtrl*)(b + owave);
     h->sA = (float*)(b + osA);
     h->sA2 = (float*)(b + osA2);
     h->sB = (float*)(b + osB);
@@ -335,22 +591,13 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     h->sX0 = (float*)(b + osX0);
     h->sXout = (float*)(b + osXo);
     h->sperm = (int32_t*)(b + osp);
-    for (int e = 0; e < kProfEvents; ++e) {
-        if (cudaEventCreate(&h->ev[e]) != cudaSuccess) {
-            for (int f = 0; f < e; ++f) cudaEventDestroy(h->ev[f]);
-            cudaFreeHost(h->host_ctrl);
-            cudaFree(h->pool);
-            delete h;
-            return FASTPFP_ERR_CUDA;
-        }
-    }
-    if (cudaMemset(h->pool, 0, off) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
-        for (int e = 0; e < kProfEvents; ++e) cudaEventDestroy(h->ev[e]);
-        cudaFreeHost(h->host_ctrl);
-        cudaFree(h->pool);
-        delete h;
-        return FASTPFP_ERR_CUDA;
-    }
+    for (int e = 0; e < kProfEvents; ++e)
+        if (cudaEventCreate(&h->ev[e]) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
+    for (int e = 0; e < 2; ++e)
+        if (cudaEventCreateWithFlags(&h->chunk_ev[e], cudaEventDisableTiming) != cudaSuccess)
+            return fail(FASTPFP_ERR_CUDA);
+    if (cudaMemset(h->pool, 0, off) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return fail(FASTPFP_ERR_CUDA);
     *out = h;
     return FASTPFP_OK;
 }
@@ -361,7 +608,12 @@ void fastpfp_destroy(fastpfp_t h) {
     cudaDeviceSynchronize();
     for (int e = 0; e < kProfEvents; ++e)
         if (h->ev[e]) cudaEventDestroy(h->ev[e]);
+    for (int e = 0; e < 2; ++e)
+        if (h->chunk_ev[e]) cudaEventDestroy(h->chunk_ev[e]);
     if (h->host_ctrl) cudaFreeHost(h->host_ctrl);
+    if (h->h_pairs) cudaFreeHost(h->h_pairs);
+    if (h->h_band) cudaFreeHost(h->h_band);
+    if (h->h_done) cudaFreeHost(h->h_done);
     if (h->pool) cudaFree(h->pool);
     delete h;
 }
@@ -374,13 +626,16 @@ int fastpfp_match(fastpfp_t h, void* stream, const float* A, int n_a, const floa
     if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     const Problem q = canonical(A, n_a, A2, n_b, B, B2, k, p->lambda, X0, perm_out, X_out);
-    int nl = 0;
-    rc = enqueue_solve(h, s, q, p, &h->host_ctrl[0], &nl);
-    if (rc != FASTPFP_OK) return rc;
+    const int nl = enqueue_single(h, s, h->slots[0], q, p, &h->host_ctrl[0]);
+    if (nl < 0) {
+        cudaStreamSynchronize(s);
+        return nl;
+    }
     if (cudaStreamSynchronize(s) != cudaSuccess) return FASTPFP_ERR_CUDA;
-    h->last_outer = h->host_ctrl[0].outer;
+    h->last_first = 0;
+    h->last_count = 1;
     rc = fill_stats(h->host_ctrl[0], q.transposed, nl, st);
-    if (p->profile) read_profile(h, h->host_ctrl[0].outer, p->max_outer, st);
+    if (p->profile) read_profile(h, h->host_ctrl[0].outer, 1.0f, st);
     return rc;
 }
 
@@ -390,7 +645,6 @@ int fastpfp_match_host(fastpfp_t h, void* stream, const float* A, int n_a, const
     int rc = check_pair(h, A, n_a, A2, n_b, B, B2, k, p, perm_out);
     if (rc != FASTPFP_OK) return rc;
     const int kk = (k > 0 && p->lambda != 0.f) ? k : 0;
-    if (kk > kMaxK) return FASTPFP_ERR_SIZE;
     if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     FP_CUDA(cudaMemcpyAsync(h->sA, A, (size_t)n_a * n_a * 4, cudaMemcpyHostToDevice, s));
@@ -403,16 +657,19 @@ int fastpfp_match_host(fastpfp_t h, void* stream, const float* A, int n_a, const
     const Problem q = canonical(h->sA, n_a, h->sA2, n_b, kk ? h->sB : nullptr, kk ? h->sB2 : nullptr,
                                 kk, p->lambda, X0 ? h->sX0 : nullptr, h->sperm,
                                 X_out ? h->sXout : nullptr);
-    int nl = 0;
-    rc = enqueue_solve(h, s, q, p, &h->host_ctrl[0], &nl);
-    if (rc != FASTPFP_OK) return rc;
+    const int nl = enqueue_single(h, s, h->slots[0], q, p, &h->host_ctrl[0]);
+    if (nl < 0) {
+        cudaStreamSynchronize(s);
+        return nl;
+    }
     FP_CUDA(cudaMemcpyAsync(perm_out, h->sperm, (size_t)n_a * 4, cudaMemcpyDeviceToHost, s));
     if (X_out)
         FP_CUDA(cudaMemcpyAsync(X_out, h->sXout, (size_t)n_a * n_b * 4, cudaMemcpyDeviceToHost, s));
     if (cudaStreamSynchronize(s) != cudaSuccess) return FASTPFP_ERR_CUDA;
-    h->last_outer = h->host_ctrl[0].outer;
+    h->last_first = 0;
+    h->last_count = 1;
     rc = fill_stats(h->host_ctrl[0], q.transposed, nl, st);
-    if (p->profile) read_profile(h, h->host_ctrl[0].outer, p->max_outer, st);
+    if (p->profile) read_profile(h, h->host_ctrl[0].outer, 1.0f, st);
     return rc;
 }
 
@@ -425,51 +682,68 @@ int fastpfp_match_batched(fastpfp_t h, void* stream, int count, const fastpfp_pa
         int rc = check_pair(h, q.A, q.n_a, q.A2, q.n_b, q.B, q.B2, q.k, p, q.perm_out);
         if (rc != FASTPFP_OK) return rc;
     }
+    if (p->precision == FASTPFP_BF16) return FASTPFP_ERR_UNSUPPORTED;
     if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    int worst = FASTPFP_OK;
+    std::vector<Problem> qs(count);
     for (int b = 0; b < count; ++b) {
         const fastpfp_pair& x = pairs[b];
-        const Problem q = canonical(x.A, x.n_a, x.A2, x.n_b, x.B, x.B2, x.k, p->lambda, x.X0,
-                                    x.perm_out, x.X_out);
-        int nl = 0;
-        int rc = enqueue_solve(h, s, q, p, &h->host_ctrl[b], &nl);
-        if (rc != FASTPFP_OK) return rc;
-        if (p->profile || b + 1 == count) {
-            // profiled batches read each pair's events before they are reused
-            if (cudaStreamSynchronize(s) != cudaSuccess) return FASTPFP_ERR_CUDA;
-        }
-        if (p->profile) {
-            rc = fill_stats(h->host_ctrl[b], q.transposed, nl, st ? &st[b] : nullptr);
-            if (st) read_profile(h, h->host_ctrl[b].outer, p->max_outer, &st[b]);
-            if (rc != FASTPFP_OK && worst == FASTPFP_OK) worst = rc;
-        } else if (st) {
-            st[b].launches = nl;
-        }
+        qs[b] = canonical(x.A, x.n_a, x.A2, x.n_b, x.B, x.B2, x.k, p->lambda, x.X0, x.perm_out,
+                          x.X_out);
     }
-    if (!p->profile) {
-        for (int b = 0; b < count; ++b) {
-            const int tr = pairs[b].n_a < pairs[b].n_b;
-            const int nl = st ? st[b].launches : 0;
-            int rc = fill_stats(h->host_ctrl[b], tr, nl, st ? &st[b] : nullptr);
+    int worst = FASTPFP_OK;
+    int b = 0;
+    while (b < count) {
+        Wave w;
+        const bool batched = plan_wave(qs, b, h->nslots, h->num_sms, &w);
+        const int cnt = batched ? w.count : 1;
+        const int nl = batched ? enqueue_wave(h, s, qs, w, p, &h->host_ctrl[b])
+                               : enqueue_single(h, s, h->slots[0], qs[b], p, &h->host_ctrl[b]);
+        if (nl < 0) {
+            cudaStreamSynchronize(s);
+            return nl;
+        }
+        // the wave tables and the profiling events are reused by the next wave
+        if (cudaStreamSynchronize(s) != cudaSuccess) return FASTPFP_ERR_CUDA;
+        if (batched) {
+            // an error of the shared projection launch belongs to every pair of the wave
+            WaveCtrl wc{};
+            FP_CUDA(cudaMemcpy(&wc, h->d_wave, sizeof(WaveCtrl), cudaMemcpyDeviceToHost));
+            if (wc.error != 0)
+                for (int i = 0; i < cnt; ++i)
+                    if (h->host_ctrl[b + i].error == 0) h->host_ctrl[b + i].error = wc.error;
+        }
+        for (int i = 0; i < cnt; ++i) {
+            const int launches = nl / cnt + (i == 0 ? nl % cnt : 0);
+            int rc = fill_stats(h->host_ctrl[b + i], qs[b + i].transposed, launches,
+                                st ? &st[b + i] : nullptr);
+            if (st && p->profile) {
+                int outer = 0;
+                for (int j = 0; j < cnt; ++j) outer = std::max(outer, h->host_ctrl[b + j].outer);
+                read_profile(h, outer, 1.0f / (float)cnt, &st[b + i]);
+            }
             if (rc != FASTPFP_OK && worst == FASTPFP_OK) worst = rc;
         }
+        h->last_first = b;
+        h->last_count = cnt;
+        b += cnt;
     }
-    if (count > 0) h->last_outer = h->host_ctrl[count - 1].outer;
     return worst;
 }
 
-int fastpfp_last_trace(fastpfp_t h, int* inner_counts, double* deltas, int cap) {
+int fastpfp_last_trace(fastpfp_t h, int pair, int* inner_counts, double* deltas, int cap) {
     if (!h || cap < 0) return FASTPFP_ERR_ARG;
+    const int i = pair - h->last_first;
+    if (i < 0 || i >= h->last_count) return FASTPFP_ERR_ARG;
     if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
-    const int n = h->last_outer < cap ? h->last_outer : cap;
+    const int outer = h->host_ctrl[pair].outer;
+    const int n = outer < cap ? outer : cap;
+    const Ctrl* c = h->slots[i].ctrl;
     if (n > 0 && inner_counts)
-        FP_CUDA(cudaMemcpy(inner_counts, h->ctrl->inner_trace, (size_t)n * sizeof(int),
-                           cudaMemcpyDeviceToHost));
+        FP_CUDA(cudaMemcpy(inner_counts, c->inner_trace, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost));
     if (n > 0 && deltas)
-        FP_CUDA(cudaMemcpy(deltas, h->ctrl->delta_trace, (size_t)n * sizeof(double),
-                           cudaMemcpyDeviceToHost));
-    return h->last_outer;
+        FP_CUDA(cudaMemcpy(deltas, c->delta_trace, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost));
+    return outer;
 }
 
 int fastpfp_gradient(fastpfp_t h, void* stream, const float* A, const float* X, const float* A2,
@@ -480,8 +754,9 @@ int fastpfp_gradient(fastpfp_t h, void* stream, const float* A, const float* X, 
     if (precision != FASTPFP_FP32) return FASTPFP_ERR_UNSUPPORTED;
     if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    GemmF32Args g1{A, N, X, m, h->T, m, nullptr, 0, 0.f, N, m, N, nullptr};
-    GemmF32Args g2{h->T, m, A2, m, Y, ldy, lambda != 0.f ? K : nullptr, m, lambda, N, m, m, nullptr};
+    const Slot& sl = h->slots[0];
+    GemmF32Args g1{A, N, X, m, sl.T, m, nullptr, 0, 0.f, N, m, N, nullptr};
+    GemmF32Args g2{sl.T, m, A2, m, Y, ldy, lambda != 0.f ? K : nullptr, m, lambda, N, m, m, nullptr};
     FP_CUDA(gemm_f32(g1, s));
     FP_CUDA(gemm_f32(g2, s));
     return FASTPFP_OK;
@@ -502,32 +777,35 @@ int fastpfp_project(fastpfp_t h, void* stream, float* Y, int N, double tol, int 
     if (N > h->max_n) return FASTPFP_ERR_SIZE;
     if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
+    const Slot& sl = h->slots[0];
     const int ldy = round4(N);
-    FP_CUDA(cudaMemsetAsync(h->ctrl, 0, kCtrlHeader, s));
-    FP_CUDA(clear_accumulators(h, s));
-    FP_CUDA(cudaMemsetAsync(h->Y, 0, (size_t)N * ldy * sizeof(float), s));
-    FP_CUDA(cudaMemcpy2DAsync(h->Y, (size_t)ldy * 4, Y, (size_t)N * 4, (size_t)N * 4, N,
+    FP_CUDA(cudaMemsetAsync(sl.ctrl, 0, kCtrlHeader, s));
+    FP_CUDA(cudaMemsetAsync(sl.colbuf, 0, 3 * (size_t)h->ld * sizeof(float), s));
+    FP_CUDA(cudaMemsetAsync(sl.sbuf, 0, 3 * sizeof(double), s));
+    FP_CUDA(cudaMemsetAsync(sl.dbuf, 0, 3 * sizeof(unsigned), s));
+    FP_CUDA(cudaMemsetAsync(sl.Y, 0, (size_t)N * ldy * sizeof(float), s));
+    FP_CUDA(cudaMemcpy2DAsync(sl.Y, (size_t)ldy * 4, Y, (size_t)N * 4, (size_t)N * 4, N,
                               cudaMemcpyDeviceToDevice, s));
     PdLaunch L;
     pd_plan(N, h->num_sms, &L);
     PdParams P{};
-    P.Y = h->Y;
+    P.Y = sl.Y;
     P.N = N;
     P.ldy = ldy;
     P.m = N;
     P.tol_inner = tol;
     P.max_inner = max_iter;
-    P.colbuf = h->colbuf;
-    P.sbuf = h->sbuf;
-    P.dbuf = h->dbuf;
-    P.ctrl = h->ctrl;
+    P.colbuf = sl.colbuf;
+    P.sbuf = sl.sbuf;
+    P.dbuf = sl.dbuf;
+    P.ctrl = sl.ctrl;
     P.timeout_ns = 2000ll * 1000000ll;
     P.rpc = L.rpc;
     P.mode = kPdProjectOnly;
     FP_CUDA(pd_launch(L, P, s));
-    FP_CUDA(cudaMemcpy2DAsync(Y, (size_t)N * 4, h->Y, (size_t)ldy * 4, (size_t)N * 4, N,
+    FP_CUDA(cudaMemcpy2DAsync(Y, (size_t)N * 4, sl.Y, (size_t)ldy * 4, (size_t)N * 4, N,
                               cudaMemcpyDeviceToDevice, s));
-    FP_CUDA(cudaMemcpyAsync(&h->host_ctrl[0], h->ctrl, kCtrlHeader, cudaMemcpyDeviceToHost, s));
+    FP_CUDA(cudaMemcpyAsync(&h->host_ctrl[0], sl.ctrl, kCtrlHeader, cudaMemcpyDeviceToHost, s));
     if (cudaStreamSynchronize(s) != cudaSuccess) return FASTPFP_ERR_CUDA;
     const Ctrl& c = h->host_ctrl[0];
     if (iters) *iters = c.last_inner;
@@ -541,9 +819,10 @@ int fastpfp_discretize(fastpfp_t h, void* stream, const float* X, int N, int m,
     if (N > h->max_n) return FASTPFP_ERR_SIZE;
     if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    FP_CUDA(cudaMemsetAsync(h->ctrl, 0, kCtrlHeader, s));
-    FP_CUDA(discretize(X, N, m, m, h->disc, h->ctrl, 2000ll * 1000000ll, h->num_sms, s));
-    FP_CUDA(cudaMemcpyAsync(row_of_col, h->disc.col_match, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
+    const Slot& sl = h->slots[0];
+    FP_CUDA(cudaMemsetAsync(sl.ctrl, 0, kCtrlHeader, s));
+    FP_CUDA(discretize(X, N, m, m, sl.disc, sl.ctrl, 2000ll * 1000000ll, h->num_sms, s));
+    FP_CUDA(cudaMemcpyAsync(row_of_col, sl.disc.col_match, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
     return FASTPFP_OK;
 }
 

@@ -53,6 +53,61 @@ void pd_plan(int N, int num_sms, PdLaunch* L);
 size_t pd_smem_bytes(int rpc, int Q, bool res);
 cudaError_t pd_launch(const PdLaunch& L, const PdParams& P, cudaStream_t s);
 
+// -------------------------------------------------- batched projection
+constexpr int kPdbThreads = 512;     // CTA size of the batched kernel
+constexpr int kMaxSeg = 32;          // pairs one CTA band may span
+constexpr int kMaxWavePairs = 64;    // pairs of one cooperative launch
+constexpr int kPdbMaxN = 4096;       // widest pair (two column quads per thread)
+
+// One pair of a wave (device-resident table, read-only in the kernel).
+struct PairDesc {
+    float* Y;             // N x ldy slacked matrix
+    float* X;             // N x ldx master X
+    __nv_bfloat16* Xt16;  // nullable BF16 copy of X^T (m x ldxt)
+    float* colbuf;        // 3 x ldy column-sum accumulators
+    double* sbuf;         // 3 totals
+    unsigned* dbuf;       // 3 round maxima
+    Ctrl* ctrl;           // the pair's control block
+    int N, ldy, m, ldx, ldxt;
+    int row0;             // first row of the pair in the wave's concatenated rows
+};
+
+// Wave-level state: barrier counter, error word, "every pair done".
+struct WaveCtrl {
+    unsigned bar;
+    unsigned bar_base;
+    int error;
+    int all_done;
+};
+
+// Shared-memory sizing of the batched kernel (maxima over the CTAs' bands).
+struct PdbLayout {
+    int max_band_rows;    // rows of the largest band
+    int max_band_cols;    // sum of ldy over the segments of one band
+    int max_band_elems;   // floats of the largest band
+};
+
+struct PdbParams {
+    const PairDesc* pairs;
+    int npairs;
+    const int* band_row;  // grid + 1 row boundaries in the concatenated row space
+    WaveCtrl* wave;
+    PdbLayout layout;
+    float alpha;
+    int normalize, slack_reset;
+    double tol_inner;
+    int max_inner;
+    double tol_outer;
+    int max_outer;
+    int refine_iters;
+    double switch_tol;
+    long long timeout_ns;
+};
+
+cudaError_t pdb_configure();
+size_t pdb_smem_bytes(const PdbLayout& L, int nthr);
+cudaError_t pdb_launch(const PdbParams& P, int grid, size_t smem, cudaStream_t s);
+
 // ----------------------------------------------------------------- GEMM
 // C[M x Nc] = Aop[M x K] * Bop[K x Nc] (+ lambda * Kmat), row-major FP32.
 // When ctrl is set the kernel does nothing unless the solve is running and

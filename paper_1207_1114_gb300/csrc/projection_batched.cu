@@ -1,0 +1,589 @@
+// projection_batched.cu -- one cooperative launch runs the successive
+// projection (Section 4.3) and the blend / normalisation / loop control of
+// Algorithm 1 for a whole wave of graph pairs at once.
+//
+// The projection rounds are bound by grid-synchronisation latency, not by
+// bandwidth: one pair leaves the SMs idle while they wait for the barrier.  A
+// wave therefore shares every barrier between many pairs.  All rows of all
+// pairs of the wave are concatenated and cut into one band per CTA with about
+// the same number of matrix entries; a band may span several pairs ("segments")
+// and stays in shared memory for all rounds.  Each round, for every segment of
+// its band, a CTA applies Eq. (P1) and Eq. (P2) elementwise, measures max|dY|,
+// and publishes that pair's column partials (vector red.add), FP64 share of
+// the total s and round maximum; one bounded grid barrier ends the round for
+// every pair.  After the barrier every CTA reads every pair's round maximum,
+// so all CTAs take the same stop decision for each pair (a pair stops when
+// max|dY| < eps_2 or after I_1 rounds) and leave the round loop together once
+// no pair is active.  Pairs whose outer loop has finished are skipped.
+#include <type_traits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace fpfp {
+namespace {
+
+struct Seg {
+    int pair;       // index into the wave's pair table
+    int lr0;        // first row of the segment inside its pair
+    int nrows;      // rows of the segment
+    int brow0;      // first row of the segment inside the band (rsum/arow index)
+    int soff;       // float offset of the segment's rows in the band storage
+    int coff;       // float offset of the segment's c/N vector
+};
+
+// Per-pair fields used every round, copied to shared memory once per launch.
+struct PairS {
+    float* colbuf;
+    double* sbuf;
+    unsigned* dbuf;
+    double s;       // total of the last finished pass
+    int N, ldy;
+};
+
+struct Shared {
+    Seg* seg;            // kMaxSeg
+    PairS* pair;         // kMaxWavePairs
+    int* pstate;         // kMaxWavePairs: bit0 active this launch, bit1 stopped
+    int* pstop;          // kMaxWavePairs: round at which the pair stopped
+    int* ictl;           // [0] any active, [1] non-finite, [2] n segments
+    float* fred;         // kMaxSeg x 32 per-warp maxima
+    float* rsum;         // band rows
+    float* arow;         // band rows
+    float* rowpart;      // band rows x 32
+    float4* cred;        // nthr float4: column-partial reduction across row groups
+    float* cN;           // sum over segments of ldy floats
+    float* band;         // band rows of every segment (16-byte aligned)
+};
+
+__device__ __forceinline__ Shared carve_b(char* base, const PdbLayout& L, int nthr) {
+    Shared s;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* p = base + off;
+        off = (off + bytes + 15) & ~size_t(15);
+        return p;
+    };
+    s.seg = reinterpret_cast<Seg*>(take(sizeof(Seg) * kMaxSeg));
+    s.pair = reinterpret_cast<PairS*>(take(sizeof(PairS) * kMaxWavePairs));
+    s.pstate = reinterpret_cast<int*>(take(sizeof(int) * kMaxWavePairs));
+    s.pstop = reinterpret_cast<int*>(take(sizeof(int) * kMaxWavePairs));
+    s.ictl = reinterpret_cast<int*>(take(sizeof(int) * 4));
+    s.fred = reinterpret_cast<float*>(take(sizeof(float) * kMaxSeg * 32));
+    s.rsum = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_rows));
+    s.arow = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_rows));
+    s.rowpart = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_rows * 32));
+    s.cred = reinterpret_cast<float4*>(take(sizeof(float4) * nthr));
+    s.cN = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_cols));
+    s.band = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_elems));
+    return s;
+}
+
+// Thread -> (row group, quad) mapping of one segment.  QP = quads per row
+// padded to a warp multiple.  When QP <= nthr, RP = nthr / QP row groups work
+// on different rows at once and each thread owns one quad; otherwise one
+// group covers a row with kq (<= 2) quads per thread.
+struct Map {
+    int QP, RP, grp, q0, kq;
+};
+__device__ __forceinline__ Map make_map(int Q, int nthr, int tid) {
+    Map m;
+    m.QP = (Q + 31) & ~31;
+    if (m.QP <= nthr) {
+        m.RP = nthr / m.QP;
+        m.grp = tid / m.QP;
+        m.q0 = tid % m.QP;
+        m.kq = 1;
+    } else {
+        m.RP = 1;
+        m.grp = 0;
+        m.q0 = tid;
+        m.kq = 2;
+    }
+    return m;
+}
+
+// One column quad of one row: Eq. (P1) with the row offset ai and the
+// column offset c (= c_j / N), then Eq. (P2); columns >= N stay zero.
+// Returns the quad's contribution to the row sum.
+template <bool UPDATE>
+__device__ __forceinline__ float quad_step(float4* __restrict__ p, float ai, float4 c, int c0, int N,
+                                           float4& cp, float& dmax) {
+    float4 y = *p;
+    if (UPDATE) {
+        float4 z;
+        z.x = fmaxf((y.x + ai) - c.x, 0.f);
+        z.y = fmaxf((y.y + ai) - c.y, 0.f);
+        z.z = fmaxf((y.z + ai) - c.z, 0.f);
+        z.w = fmaxf((y.w + ai) - c.w, 0.f);
+        if (c0 + 4 > N) {
+            if (c0 + 1 >= N) z.y = 0.f;
+            if (c0 + 2 >= N) z.z = 0.f;
+            if (c0 + 3 >= N) z.w = 0.f;
+        }
+        dmax = fmaxf(dmax, fmaxf(fmaxf(fabsf(z.x - y.x), fabsf(z.y - y.y)),
+                                 fmaxf(fabsf(z.z - y.z), fabsf(z.w - y.w))));
+        *p = z;
+        y = z;
+    }
+    cp.x += y.x;
+    cp.y += y.y;
+    cp.z += y.z;
+    cp.w += y.w;
+    return (y.x + y.y) + (y.z + y.w);
+}
+
+// All rows of one segment handled by this thread's row group, two rows in
+// flight.  Must be called by whole warps (a row group is whole warps).
+template <bool UPDATE>
+__device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, int Q, int N,
+                                         const Map& mp, int nthr, int lane,
+                                         const float* __restrict__ arow, float* __restrict__ rowpart,
+                                         float4 c0v, float4 c1v, float4& cp0, float4& cp1,
+                                         float& dmax) {
+    const bool h0 = mp.q0 < Q;
+    const bool h1 = mp.kq > 1 && mp.q0 + nthr < Q;
+    const int c00 = 4 * mp.q0, c01 = 4 * (mp.q0 + nthr);
+    const int stride = mp.RP * Q;
+    int r = mp.grp;
+    float4* p = band + (size_t)mp.grp * Q + mp.q0;
+    for (; r + mp.RP < nrows; r += 2 * mp.RP, p += 2 * stride) {
+        const float a0 = UPDATE ? arow[r] : 0.f;
+        const float a1 = UPDATE ? arow[r + mp.RP] : 0.f;
+        float s0 = 0.f, s1 = 0.f;
+        if (h0) {
+            s0 += quad_step<UPDATE>(p, a0, c0v, c00, N, cp0, dmax);
+            s1 += quad_step<UPDATE>(p + stride, a1, c0v, c00, N, cp0, dmax);
+        }
+        if (h1) {
+            s0 += quad_step<UPDATE>(p + nthr, a0, c1v, c01, N, cp1, dmax);
+            s1 += quad_step<UPDATE>(p + stride + nthr, a1, c1v, c01, N, cp1, dmax);
+        }
+        s0 = warp_sum(s0);
+        s1 = warp_sum(s1);
+        if (lane == 0) {
+            rowpart[(size_t)r * 32] = s0;
+            rowpart[(size_t)(r + mp.RP) * 32] = s1;
+        }
+    }
+    if (r < nrows) {
+        const float a0 = UPDATE ? arow[r] : 0.f;
+        float s0 = 0.f;
+        if (h0) s0 += quad_step<UPDATE>(p, a0, c0v, c00, N, cp0, dmax);
+        if (h1) s0 += quad_step<UPDATE>(p + nthr, a0, c1v, c01, N, cp1, dmax);
+        s0 = warp_sum(s0);
+        if (lane == 0) rowpart[(size_t)r * 32] = s0;
+    }
+}
+
+__global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) {
+    extern __shared__ __align__(16) char smem_raw[];
+    WaveCtrl* W = P.wave;
+    if (ld_relaxed_i32(&W->all_done) != 0 || ld_relaxed_i32(&W->error) != 0) return;
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned G = gridDim.x;
+    Shared S = carve_b(smem_raw, P.layout, nthr);
+    int* err = &W->error;
+    const unsigned bar_base = W->bar_base;
+    unsigned gen = 0;
+    const int npairs = P.npairs;
+
+    // ---- band -> segments, pair states and per-pair fields
+    const int b0 = P.band_row[blockIdx.x], b1 = P.band_row[blockIdx.x + 1];
+    if (tid == 0) {
+        int nseg = 0, brow = 0, soff = 0, coff = 0;
+        for (int p = 0; p < npairs && nseg < kMaxSeg; ++p) {
+            const PairDesc& d = P.pairs[p];
+            const int lo = max(b0, d.row0), hi = min(b1, d.row0 + d.N);
+            if (lo >= hi) continue;
+            Seg s;
+            s.pair = p;
+            s.lr0 = lo - d.row0;
+            s.nrows = hi - lo;
+            s.brow0 = brow;
+            s.soff = soff;
+            s.coff = coff;
+            S.seg[nseg++] = s;
+            brow += s.nrows;
+            soff += s.nrows * d.ldy;
+            coff += d.ldy;
+        }
+        S.ictl[2] = nseg;
+        S.ictl[1] = 0;
+    }
+    for (int p = tid; p < npairs; p += nthr) {
+        const PairDesc& d = P.pairs[p];
+        const int done = ld_relaxed_i32(&d.ctrl->done);
+        S.pstate[p] = done ? 0 : 1;
+        S.pstop[p] = 0;
+        PairS ps;
+        ps.colbuf = d.colbuf;
+        ps.sbuf = d.sbuf;
+        ps.dbuf = d.dbuf;
+        ps.s = 0.0;
+        ps.N = d.N;
+        ps.ldy = d.ldy;
+        S.pair[p] = ps;
+    }
+    __syncthreads();
+    const int nseg = S.ictl[2];
+
+    // ---- prologue: load the band (optional slack reset)
+    for (int si = 0; si < nseg; ++si) {
+        const Seg sg = S.seg[si];
+        const PairDesc& d = P.pairs[sg.pair];
+        if (!(S.pstate[sg.pair] & 1)) continue;
+        const int Q = d.ldy >> 2, m = d.m;
+        const bool reset = P.slack_reset && m < d.N;
+        const float4* src = reinterpret_cast<const float4*>(d.Y) + (size_t)sg.lr0 * Q;
+        float4* dst = reinterpret_cast<float4*>(S.band + sg.soff);
+        for (int e = tid; e < sg.nrows * Q; e += nthr) {
+            float4 v = src[e];
+            if (reset) {
+                const int c0 = 4 * (e % Q);
+                if (c0 + 0 >= m) v.x = 0.f;
+                if (c0 + 1 >= m) v.y = 0.f;
+                if (c0 + 2 >= m) v.z = 0.f;
+                if (c0 + 3 >= m) v.w = 0.f;
+            }
+            dst[e] = v;
+        }
+    }
+    __syncthreads();
+
+    // One pass over every active segment.  UPDATE = false only sums.
+    // Row partials go to rowpart, per-segment maxima to fred, column partials
+    // to the pairs' accumulator `cur`.
+    auto pass = [&](auto update_tag, int cur) {
+        constexpr bool UPDATE = decltype(update_tag)::value;
+        for (int si = 0; si < nseg; ++si) {
+            const Seg sg = S.seg[si];
+            const int pst = S.pstate[sg.pair];
+            if (!(pst & 1) || (pst & 2)) continue;   // inactive or stopped pair
+            const PairS pr = S.pair[sg.pair];
+            const int N = pr.N, Q = pr.ldy >> 2;
+            const Map mp = make_map(Q, nthr, tid);
+            const bool in_grp = mp.grp < mp.RP;
+            float4 c0v = make_float4(0.f, 0.f, 0.f, 0.f), c1v = c0v;
+            if (UPDATE && in_grp) {
+                const float4* cN = reinterpret_cast<const float4*>(S.cN + sg.coff);
+                if (mp.q0 < Q) c0v = cN[mp.q0];
+                if (mp.kq > 1 && mp.q0 + nthr < Q) c1v = cN[mp.q0 + nthr];
+            }
+            float4 cp0 = make_float4(0.f, 0.f, 0.f, 0.f), cp1 = cp0;
+            float dmax = 0.f;
+            if (in_grp) {
+                const int wig = (mp.QP <= nthr) ? ((tid % mp.QP) >> 5) : warp;
+                seg_rows<UPDATE>(reinterpret_cast<float4*>(S.band + sg.soff), sg.nrows, Q, N, mp, nthr,
+                                 lane, S.arow + sg.brow0, S.rowpart + (size_t)sg.brow0 * 32 + wig, c0v,
+                                 c1v, cp0, cp1, dmax);
+            }
+            dmax = warp_max(dmax);
+            if (lane == 0) S.fred[si * 32 + warp] = dmax;
+            // column partials: fold the row groups, then one red.v4 per quad
+            float* acc = pr.colbuf + (size_t)cur * pr.ldy;
+            if (mp.RP > 1) {
+                S.cred[tid] = (in_grp && mp.q0 < Q) ? cp0 : make_float4(0.f, 0.f, 0.f, 0.f);
+                __syncthreads();
+                if (tid < Q) {
+                    float4 t = S.cred[tid];
+                    for (int g = 1; g < mp.RP; ++g) {
+                        const float4 v = S.cred[g * mp.QP + tid];
+                        t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
+                    }
+                    red_add_v4(acc + 4 * tid, t.x, t.y, t.z, t.w);
+                }
+                __syncthreads();
+            } else {
+                if (mp.q0 < Q) red_add_v4(acc + 4 * mp.q0, cp0.x, cp0.y, cp0.z, cp0.w);
+                if (mp.kq > 1 && mp.q0 + nthr < Q)
+                    red_add_v4(acc + 4 * (mp.q0 + nthr), cp1.x, cp1.y, cp1.z, cp1.w);
+            }
+        }
+    };
+
+    // End of a pass: row sums, FP64 totals and maxima per segment, grid
+    // barrier, then every pair's stop decision and the next offsets a_i.
+    auto finish = [&](int cur, int u, bool check_stop) -> bool {
+        __syncthreads();
+        for (int si = 0; si < nseg; ++si) {
+            const Seg sg = S.seg[si];
+            const int pst = S.pstate[sg.pair];
+            if (!(pst & 1) || (pst & 2)) continue;
+            const int QP = ((S.pair[sg.pair].ldy >> 2) + 31) & ~31;
+            const int nw = (QP <= nthr ? QP : nthr) >> 5;
+            for (int r = tid; r < sg.nrows; r += nthr) {
+                const float* rp = S.rowpart + (size_t)(sg.brow0 + r) * 32;
+                float t = 0.f;
+                for (int w = 0; w < nw; ++w) t += rp[w];
+                S.rsum[sg.brow0 + r] = t;
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            for (int si = 0; si < nseg; ++si) {
+                const Seg sg = S.seg[si];
+                const int pst = S.pstate[sg.pair];
+                if (!(pst & 1) || (pst & 2)) continue;
+                double sp = 0.0;
+                for (int r = lane; r < sg.nrows; r += 32) sp += (double)S.rsum[sg.brow0 + r];
+                sp = warp_sum_d(sp);
+                float bm = lane < (nthr >> 5) ? S.fred[si * 32 + lane] : 0.f;
+                bm = warp_max(bm);
+                if (lane == 0) {
+                    const PairS& pr = S.pair[sg.pair];
+                    atomicAdd(pr.sbuf + cur, sp);
+                    if (bm > 0.f) atomicMax(pr.dbuf + cur, __float_as_uint(bm));
+                }
+            }
+        }
+        if (!grid_barrier(&W->bar, bar_base + G * (gen + 1), err, P.timeout_ns)) return false;
+        ++gen;
+        // c/N of every active segment for the next round
+        for (int si = 0; si < nseg; ++si) {
+            const Seg sg = S.seg[si];
+            const int pst = S.pstate[sg.pair];
+            if (!(pst & 1) || (pst & 2)) continue;
+            const PairS pr = S.pair[sg.pair];
+            const float invN = 1.0f / (float)pr.N;
+            const float4* c = reinterpret_cast<const float4*>(pr.colbuf + (size_t)cur * pr.ldy);
+            float4* dst = reinterpret_cast<float4*>(S.cN + sg.coff);
+            for (int q = tid; q < (pr.ldy >> 2); q += nthr) {
+                const float4 v = __ldcg(c + q);
+                dst[q] = make_float4(v.x * invN, v.y * invN, v.z * invN, v.w * invN);
+            }
+        }
+        if (warp == 0) {
+            // stop decisions of every pair of the wave (identical in every CTA)
+            int any = 0;
+            for (int p = lane; p < npairs; p += 32) {
+                int ps = S.pstate[p];
+                if ((ps & 1) && !(ps & 2)) {
+                    PairS& pr = S.pair[p];
+                    const double s = __ldcg(pr.sbuf + cur);
+                    const float dd = __uint_as_float(__ldcg(pr.dbuf + cur));
+                    pr.s = s;
+                    if (!isfinite(s)) S.ictl[1] = 1;
+                    if (check_stop && ((double)dd < P.tol_inner || u >= P.max_inner)) {
+                        ps |= 2;
+                        S.pstop[p] = u;
+                    }
+                    S.pstate[p] = ps;
+                    any |= !(ps & 2);
+                }
+            }
+            any = __any_sync(0xffffffffu, any);
+            __syncwarp();
+            if (lane == 0) S.ictl[0] = any;
+            // offsets a_i = 1/N + s/N^2 - r_i/N of the band's rows
+            for (int si = 0; si < nseg; ++si) {
+                const Seg sg = S.seg[si];
+                if ((S.pstate[sg.pair] & 3) != 1) continue;
+                const PairS& pr = S.pair[sg.pair];
+                const double invN = 1.0 / (double)pr.N;
+                const double a_base = invN + pr.s * invN * invN;
+                for (int r = lane; r < sg.nrows; r += 32)
+                    S.arow[sg.brow0 + r] = (float)(a_base - (double)S.rsum[sg.brow0 + r] * invN);
+            }
+        }
+        __syncthreads();
+        return true;
+    };
+
+    // Zero the accumulator `which` of every active pair (distributed over CTAs).
+    auto clear_acc = [&](int which) {
+        for (int p = 0; p < npairs; ++p) {
+            const PairS& pr = S.pair[p];
+            const int Q = pr.ldy >> 2;
+            float4* cb = reinterpret_cast<float4*>(pr.colbuf + (size_t)which * pr.ldy);
+            for (int q = blockIdx.x * nthr + tid; q < Q; q += G * nthr) cb[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (blockIdx.x == 0 && tid == 0) {
+                pr.sbuf[which] = 0.0;
+                pr.dbuf[which] = 0u;
+            }
+        }
+    };
+
+    // ---- sums of the input, then the rounds
+    clear_acc(1);
+    pass(std::false_type{}, 0);
+    if (!finish(0, 0, false)) return;
+    if (S.ictl[1]) {
+        if (tid == 0) atomicCAS(err, 0, FASTPFP_ERR_NONFINITE);
+        return;
+    }
+    int u = 0;
+    while (S.ictl[0]) {
+        ++u;
+        const int cur = u % 3;
+        clear_acc((u + 1) % 3);
+        pass(std::true_type{}, cur);
+        if (!finish(cur, u, true)) return;
+    }
+    // ---- blend and normalise every active pair
+    const float alpha = P.alpha, beta = 1.0f - P.alpha;
+    if (P.normalize) {
+        for (int si = 0; si < nseg; ++si) {
+            const Seg sg = S.seg[si];
+            if (!(S.pstate[sg.pair] & 1)) continue;
+            const PairDesc& d = P.pairs[sg.pair];
+            const int Qy = d.ldy >> 2, Qx = d.ldx >> 2, m = d.m;
+            const float4* band = reinterpret_cast<const float4*>(S.band + sg.soff);
+            const float4* X = reinterpret_cast<const float4*>(d.X) + (size_t)sg.lr0 * Qx;
+            float lmax = -INFINITY;
+            for (int e = tid; e < sg.nrows * Qx; e += nthr) {
+                const int r = e / Qx, q = e % Qx;
+                const float4 x = X[(size_t)r * Qx + q], y = band[(size_t)r * Qy + q];
+                const int c0 = 4 * q;
+                lmax = fmaxf(lmax, beta * x.x + alpha * y.x);
+                if (c0 + 1 < m) lmax = fmaxf(lmax, beta * x.y + alpha * y.y);
+                if (c0 + 2 < m) lmax = fmaxf(lmax, beta * x.z + alpha * y.z);
+                if (c0 + 3 < m) lmax = fmaxf(lmax, beta * x.w + alpha * y.w);
+            }
+            lmax = warp_max(lmax);
+            if (lane == 0) S.fred[si * 32 + warp] = lmax;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            for (int si = 0; si < nseg; ++si) {
+                const Seg sg = S.seg[si];
+                if (!(S.pstate[sg.pair] & 1)) continue;
+                float bm = lane < (nthr >> 5) ? S.fred[si * 32 + lane] : -INFINITY;
+                bm = warp_max(bm);
+                if (lane == 0) atomicMax(&P.pairs[sg.pair].ctrl->xmax_bits, float_to_ordered(bm));
+            }
+        }
+        if (!grid_barrier(&W->bar, bar_base + G * (gen + 1), err, P.timeout_ns)) return;
+        ++gen;
+    }
+    for (int si = 0; si < nseg; ++si) {
+        const Seg sg = S.seg[si];
+        if (!(S.pstate[sg.pair] & 1)) continue;
+        const PairDesc& d = P.pairs[sg.pair];
+        const int Qy = d.ldy >> 2, Qx = d.ldx >> 2, m = d.m, N = d.N;
+        const float mx = P.normalize ? ordered_to_float(__ldcg(&d.ctrl->xmax_bits)) : 1.0f;
+        const float4* band = reinterpret_cast<const float4*>(S.band + sg.soff);
+        float4* X = reinterpret_cast<float4*>(d.X) + (size_t)sg.lr0 * Qx;
+        __nv_bfloat16* Xt16 = d.Xt16;
+        const int ldxt = d.ldxt;
+        double dx = 0.0;
+        for (int e = tid; e < sg.nrows * Qx; e += nthr) {
+            const int r = e / Qx, q = e % Qx;
+            const float4 x = X[(size_t)r * Qx + q], y = band[(size_t)r * Qy + q];
+            float4 v = make_float4(beta * x.x + alpha * y.x, beta * x.y + alpha * y.y,
+                                   beta * x.z + alpha * y.z, beta * x.w + alpha * y.w);
+            if (P.normalize) { v.x /= mx; v.y /= mx; v.z /= mx; v.w /= mx; }
+            const int c0 = 4 * q;
+            if (c0 + 4 > m) {
+                if (c0 + 1 >= m) v.y = 0.f;
+                if (c0 + 2 >= m) v.z = 0.f;
+                if (c0 + 3 >= m) v.w = 0.f;
+            }
+            dx = fmax(dx, fmax(fmax(fabs((double)v.x - (double)x.x), fabs((double)v.y - (double)x.y)),
+                               fmax(fabs((double)v.z - (double)x.z), fabs((double)v.w - (double)x.w))));
+            X[(size_t)r * Qx + q] = v;
+            if (Xt16) {
+                const int i = sg.lr0 + r;
+                Xt16[(size_t)c0 * ldxt + i] = __float2bfloat16_rn(v.x);
+                if (c0 + 1 < m) Xt16[(size_t)(c0 + 1) * ldxt + i] = __float2bfloat16_rn(v.y);
+                if (c0 + 2 < m) Xt16[(size_t)(c0 + 2) * ldxt + i] = __float2bfloat16_rn(v.z);
+                if (c0 + 3 < m) Xt16[(size_t)(c0 + 3) * ldxt + i] = __float2bfloat16_rn(v.w);
+            }
+        }
+        // the slack columns m..N-1 carry over to the next outer iteration
+        if (m < N) {
+            const int qs = m >> 2;
+            float4* Yg = reinterpret_cast<float4*>(d.Y) + (size_t)sg.lr0 * Qy;
+            for (int e = tid; e < sg.nrows * (Qy - qs); e += nthr) {
+                const int r = e / (Qy - qs), q = qs + e % (Qy - qs);
+                Yg[(size_t)r * Qy + q] = band[(size_t)r * Qy + q];
+            }
+        }
+        // per-warp max|dX| of the segment, folded at L2 by the atomic
+        dx = warp_max_d(dx);
+        if (lane == 0 && dx > 0.0) atomicMax(&d.ctrl->dx_bits, (unsigned long long)__double_as_longlong(dx));
+    }
+    if (!grid_barrier(&W->bar, bar_base + G * (gen + 1), err, P.timeout_ns)) return;
+    ++gen;
+
+    // ---- per-pair loop control, accumulator clean-up
+    for (int b = 0; b < 3; ++b) clear_acc(b);
+    if (blockIdx.x == 0) {
+        for (int p = tid; p < npairs; p += nthr) {
+            if (!(S.pstate[p] & 1)) continue;
+            Ctrl* C = P.pairs[p].ctrl;
+            const int ui = S.pstop[p];
+            const double d = __longlong_as_double((long long)__ldcg(&C->dx_bits));
+            if (!isfinite(d)) atomicCAS(err, 0, FASTPFP_ERR_NONFINITE);
+            C->dx_bits = 0ull;
+            C->xmax_bits = 0u;
+            const int t = C->outer;
+            if (t < kMaxOuterTrace) {
+                C->inner_trace[t] = ui;
+                C->delta_trace[t] = d;
+            }
+            C->outer = t + 1;
+            C->inner_total += ui;
+            C->inner_max = max(C->inner_max, ui);
+            C->last_inner = ui;
+            C->last_delta = d;
+            if (C->lowp) {
+                C->lowp_iters += 1;
+                if (d < P.switch_tol || t + 1 >= P.max_outer - P.refine_iters) {
+                    C->lowp = 0;
+                    C->refine_left = P.refine_iters;
+                }
+            } else {
+                if (d < P.tol_outer) {
+                    C->converged = 1;
+                    C->done = 1;
+                }
+                if (C->refine_left > 0) {
+                    C->refine_left -= 1;
+                    if (C->refine_left == 0) C->done = 1;
+                }
+            }
+            if (t + 1 >= P.max_outer) C->done = 1;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int all = 1;
+            for (int p = 0; p < npairs; ++p) all &= (P.pairs[p].ctrl->done != 0);
+            W->all_done = all;
+            W->bar_base = bar_base + G * gen;
+        }
+    }
+}
+
+}  // namespace
+
+size_t pdb_smem_bytes(const PdbLayout& L, int nthr) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) { off = (off + bytes + 15) & ~size_t(15); };
+    take(24 * kMaxSeg);               // Seg is six ints
+    take(40 * kMaxWavePairs);         // PairS: three pointers, a double, two ints
+    take(4 * kMaxWavePairs);
+    take(4 * kMaxWavePairs);
+    take(4 * 4);
+    take(4 * kMaxSeg * 32);
+    take(4 * (size_t)L.max_band_rows);
+    take(4 * (size_t)L.max_band_rows);
+    take(4 * (size_t)L.max_band_rows * 32);
+    take(16 * (size_t)nthr);
+    take(4 * (size_t)L.max_band_cols);
+    take(4 * (size_t)L.max_band_elems);
+    return off;
+}
+
+cudaError_t pdb_configure() {
+    return cudaFuncSetAttribute((const void*)pdb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kPdMaxSmem);
+}
+
+cudaError_t pdb_launch(const PdbParams& P, int grid, size_t smem, cudaStream_t s) {
+    void* args[] = {const_cast<PdbParams*>(&P)};
+    return cudaLaunchCooperativeKernel((const void*)pdb_kernel, dim3(grid), dim3(kPdbThreads), args, smem,
+                                       s);
+}
+
+}  // namespace fpfp

@@ -82,7 +82,7 @@ def lib():
     l.fastpfp_match_host.argtypes = sig
     l.fastpfp_match_batched.argtypes = [P, V, I, C.POINTER(fastpfp_pair), C.POINTER(fastpfp_params),
                                         C.POINTER(fastpfp_stats)]
-    l.fastpfp_last_trace.argtypes = [P, P, P, I]
+    l.fastpfp_last_trace.argtypes = [P, I, P, P, I]
     l.fastpfp_gradient.argtypes = [P, V, P, P, P, P, C.c_float, I, I, P, I, I]
     l.fastpfp_affinity.argtypes = [P, V, P, P, I, I, I, P]
     l.fastpfp_project.argtypes = [P, V, P, I, C.c_double, I, C.POINTER(C.c_int),
@@ -240,10 +240,12 @@ class Solver:
         _check(rc, "fastpfp_match_batched")
         return [MatchResult(perm, X, sts[b]) for b, (perm, X) in enumerate(outs)]
 
-    def last_trace(self, cap: int = 4096):
+    def last_trace(self, pair: int = 0, cap: int = 4096):
+        """(inner counts, max|dX|) per outer iteration of pair `pair` of the
+        last call (0 after match; a pair of the last wave after a batch)."""
         inner = np.zeros(cap, dtype=np.int32)
         delta = np.zeros(cap, dtype=np.float64)
-        n = lib().fastpfp_last_trace(self._h, C.c_void_p(inner.ctypes.data),
+        n = lib().fastpfp_last_trace(self._h, int(pair), C.c_void_p(inner.ctypes.data),
                                      C.c_void_p(delta.ctypes.data), cap)
         if n < 0:
             raise FastPFPError(n, "fastpfp_last_trace")

@@ -201,16 +201,46 @@ def test_host_entry_point_equals_device_entry_point(solver):
     assert d.stats.outer_iters == h.stats.outer_iters
 
 
-def test_batched_equals_single(solver):
-    pairs = synth.batch_mixed(count=5, seed=3, n_lo=20, n_hi=90, out_hi=15)
-    p = F.default_params(lam=0.5, max_outer=20, max_inner=200)
-    dev = [(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)) for g in pairs]
+def _check_batch(solver, pairs, lam, **kw):
+    """Every pair of one wave against the oracle replaying that pair's trace."""
+    p = F.default_params(lam=lam, **kw)
+    dev = [(cu(g.A), cu(g.A2), cu(g.B) if g.k else None, cu(g.B2) if g.k else None) for g in pairs]
     outs = solver.match_batched(dev, params=p, want_X=True)
-    for (A, A2, B, B2), o in zip(dev, outs):
-        s = solver.match(A, A2, B, B2, params=p, want_X=True)
-        np.testing.assert_array_equal(s.perm.cpu().numpy(), o.perm.cpu().numpy())
-        assert np.abs(s.X.cpu().numpy() - o.X.cpu().numpy()).max() <= 1e-5
-        assert s.stats.outer_iters == o.stats.outer_iters
+    for i, (g, o) in enumerate(zip(pairs, outs)):
+        inner, _ = solver.last_trace(pair=i)
+        assert o.stats.status == 0 and len(inner) == o.stats.outer_iters
+        r = oracle.solve(g.A, g.A2, g.B, g.B2, lam=lam, replay_inner=inner,
+                         replay_outer=o.stats.outer_iters, **kw)
+        Xg = o.X.cpu().numpy()
+        assert np.abs(Xg - r["X"]).max() <= 1e-4
+        A, A2, Bc, B2c, tr = _canon(g)
+        roc = oracle.greedy_sorted((Xg.T if tr else Xg).astype(np.float64))
+        K = oracle.affinity(Bc, B2c) if g.k and lam else None
+        obj = oracle.qap_objective(A, A2, roc, K, lam)
+        assert abs(o.stats.objective - obj) <= 1e-5 * abs(obj)
+    return outs
+
+
+def test_batched_wave_of_uneven_pairs_matches_oracle(solver):
+    """Six pairs of uneven sizes (outliers on either side) share one wave."""
+    pairs = synth.batch_mixed(count=6, seed=3, n_lo=20, n_hi=160, out_hi=25)
+    pairs[1] = synth.GraphPair(pairs[1].A2, pairs[1].A, pairs[1].B2, pairs[1].B, pairs[1].gt, 0.5)
+    _check_batch(solver, pairs, 0.5, max_outer=25, max_inner=250)
+
+
+def test_batched_wave_at_full_size_matches_oracle(solver):
+    """Three n = 1000 attributed pairs in one wave, a few outer iterations."""
+    pairs = [synth.attributed_1000(seed=s) for s in range(3)]
+    _check_batch(solver, pairs, 1.0, max_outer=3, max_inner=150)
+
+
+def test_batched_mixed_small_pairs_plain(solver):
+    """Pairs without attributes and exact-size matches in one wave."""
+    pairs = [synth.plain_100(seed=s) for s in range(4)] + [synth.graph_pair(7, p=0.5, sigma=0.0,
+                                                                             seed=9)]
+    outs = _check_batch(solver, pairs, 0.0, max_outer=40, max_inner=400)
+    for g, o in zip(pairs[:4], outs):
+        assert (o.perm.cpu().numpy() == g.gt).mean() >= 0.99
 
 
 # ------------------------------------------------------------ errors / faults
