@@ -123,11 +123,14 @@ def make_pairs(rank: int, batch: int):
     return [synth.attributed_1000(seed=rank * 1000 + b) for b in range(batch)]
 
 
-def params(F, profile=0):
+def params(F, profile=0, precision="fp32"):
+    """The workload's parameters.  bf16: tensor-core products until
+    max|dX| < 1e-3, then FP32 iterations (at most 30) to convergence."""
     w = WORKLOAD
+    extra = dict(precision=F.BF16, refine_iters=30, switch_tol=1e-3) if precision == "bf16" else {}
     return F.default_params(lam=w["lam"], alpha=w["alpha"], tol_outer=w["tol_outer"],
                             tol_inner=w["tol_inner"], max_outer=w["max_outer"],
-                            max_inner=w["max_inner"], profile=profile)
+                            max_inner=w["max_inner"], profile=profile, **extra)
 
 
 def cpu_oracle_sample(g, outer_per_pair, inner_per_pair, budget_s=12.0):
@@ -202,6 +205,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-budget", type=float, default=10.0, dest="ref_budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
+                    help="gradient products: plain FP32, or BF16 tensor cores + FP32 refinement")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -233,8 +238,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    p_plain = params(F)
-    p_prof = params(F, profile=1)
+    p_plain = params(F, precision=args.precision)
+    p_prof = params(F, profile=1, precision=args.precision)
     for _ in range(args.warmup):
         solver.match_batched(dpairs, params=p_plain)
     # timed region: per-step CUDA events, L2 flushed (untimed) before every step
@@ -309,8 +314,9 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(WORKLOAD, pairs_per_step=args.batch, precision="fp32",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "bf16+f32", "data": "synthetic",
+            "config": dict(WORKLOAD, pairs_per_step=args.batch, precision=args.precision,
                            l2="flushed (512 MB write) before every timed step",
                            parallelism=f"pairs sharded over {world} rank(s)"),
             "accuracy": float(np.mean(accs)),

@@ -39,6 +39,7 @@ constexpr int kChunk = 4;                         // outer iterations enqueued b
 constexpr long long kMinElemsPerCta = 8192;       // smallest band worth a CTA of its own
 
 inline int round4(int x) { return (x + 3) & ~3; }
+inline int round8(int x) { return (x + 7) & ~7; }   // BF16 rows: 16-byte TMA strides
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Per-pair device scratch.
@@ -159,11 +160,18 @@ int enqueue_setup(const Slot& sl, cudaStream_t s, const Problem& q, const fastpf
         FP_CUDA(affinity(q.B, q.B2, q.N, q.m, q.k, sl.K, ldx, s));
         ++nl;
     }
-    FP_CUDA(init_x(sl.X, q.N, q.m, ldx, q.X0, q.transposed, bf16 ? sl.Xt16 : nullptr, ldy, s));
+    FP_CUDA(init_x(sl.X, q.N, q.m, ldx, q.X0, q.transposed, bf16 ? sl.Xt16 : nullptr, round8(q.N), s));
+    if (bf16) {
+        // BF16 operand copies of A and A' for the tensor-core products
+        FP_CUDA(to_bf16(q.A, q.N, q.N, q.N, sl.A16, round8(q.N), s));
+        FP_CUDA(to_bf16(q.A2, q.m, q.m, q.m, sl.A216, round8(q.m), s));
+        nl += 2;
+    }
     return nl;
 }
 
-// The gradient of Section 4.1: T = A X, then Y[:, :m] = T A' + lambda K.
+// The gradient of Section 4.1 in FP32: T = A X, then Y[:, :m] = T A' + lambda K.
+// Skipped on the device while the solve runs its BF16 phase.
 int enqueue_gradient(const Slot& sl, cudaStream_t s, const Problem& q, const fastpfp_params* p) {
     const int ldy = round4(q.N), ldx = round4(q.m);
     GemmF32Args g1{q.A, q.N, sl.X, ldx, sl.T, ldx, nullptr, 0, 0.f, q.N, q.m, q.N, sl.ctrl};
@@ -172,6 +180,48 @@ int enqueue_gradient(const Slot& sl, cudaStream_t s, const Problem& q, const fas
     FP_CUDA(gemm_f32(g1, s));
     FP_CUDA(gemm_f32(g2, s));
     return 2;
+}
+
+// The same gradient on the tensor cores for pairs in slots 0..count-1: one
+// grouped launch for T = A X (BF16 out) and one for Y = T A' + lambda K (FP32
+// out), each covering up to kTcMaxGroup pairs.  The tensor maps describe the
+// slots' BF16 buffers and are built once per solve.
+struct TcPlan {
+    std::vector<TcGroup> g1, g2;
+};
+
+bool plan_tc(fastpfp_t h, const Problem* qs, int count, const fastpfp_params* p, TcPlan* plan) {
+    plan->g1.clear();
+    plan->g2.clear();
+    for (int b = 0; b < count; b += kTcMaxGroup) {
+        TcGroup a{}, c{};
+        const int n = std::min(kTcMaxGroup, count - b);
+        a.count = c.count = n;
+        a.mode = kTcOutBf16;
+        c.mode = kTcOutF32;
+        for (int i = 0; i < n; ++i) {
+            const Problem& q = qs[b + i];
+            const Slot& sl = h->slots[b + i];
+            const int l16N = round8(q.N), l16m = round8(q.m);
+            if (!tc_make_map(&a.map_a[i], sl.A16, q.N, q.N, l16N) ||
+                !tc_make_map(&a.map_b[i], sl.Xt16, q.m, q.N, l16N) ||
+                !tc_make_map(&c.map_a[i], sl.T16, q.N, q.m, l16m) ||
+                !tc_make_map(&c.map_b[i], sl.A216, q.m, q.m, l16m))
+                return false;
+            a.prob[i] = TcProblem{q.N, q.m, q.N, sl.T16, l16m, nullptr, 0, 0.f, sl.ctrl, &sl.ctrl->error};
+            c.prob[i] = TcProblem{q.N, q.m, q.m, sl.Y, round4(q.N), q.k ? sl.K : nullptr, round4(q.m),
+                                  q.k ? (float)p->lambda : 0.f, sl.ctrl, &sl.ctrl->error};
+        }
+        plan->g1.push_back(a);
+        plan->g2.push_back(c);
+    }
+    return true;
+}
+
+int enqueue_tc(const TcPlan& plan, cudaStream_t s) {
+    for (const TcGroup& g : plan.g1) FP_CUDA(tc_gemm(g, s));
+    for (const TcGroup& g : plan.g2) FP_CUDA(tc_gemm(g, s));
+    return (int)(plan.g1.size() + plan.g2.size());
 }
 
 // Discretisation, objective, caller-orientation outputs, control header.
@@ -221,7 +271,9 @@ int enqueue_single(fastpfp_t h, cudaStream_t s, const Slot& sl, const Problem& q
                    const fastpfp_params* p, Ctrl* host_slot) {
     const int N = q.N, m = q.m;
     const int ldy = round4(N), ldx = round4(m);
-    if (p->precision == FASTPFP_BF16) return FASTPFP_ERR_UNSUPPORTED;
+    const bool bf16 = p->precision == FASTPFP_BF16;
+    TcPlan tc;
+    if (bf16 && !plan_tc(h, &q, 1, p, &tc)) return FASTPFP_ERR_UNSUPPORTED;
     int nl = enqueue_setup(sl, s, q, p, h->ld);
     if (nl < 0) return nl;
     PdLaunch L;
@@ -233,8 +285,8 @@ int enqueue_single(fastpfp_t h, cudaStream_t s, const Slot& sl, const Problem& q
     P.m = m;
     P.X = sl.X;
     P.ldx = ldx;
-    P.Xt16 = nullptr;
-    P.ldxt = ldy;
+    P.Xt16 = bf16 ? sl.Xt16 : nullptr;
+    P.ldxt = round8(N);
     P.alpha = p->alpha;
     P.normalize = p->normalize_max ? 1 : 0;
     P.slack_reset = p->slack_policy == 1 ? 1 : 0;
@@ -257,12 +309,17 @@ int enqueue_single(fastpfp_t h, cudaStream_t s, const Slot& sl, const Problem& q
     const int r = run_outer(h, s, &sl.ctrl->done, 0, 2, p->max_outer, [&](int t) -> int {
         const bool pt = prof && t < kProfIters;
         if (pt && t == 0) FP_CUDA(cudaEventRecord(h->ev[0], s));
-        const int g = enqueue_gradient(sl, s, q, p);
-        if (g < 0) return g;
+        int g = 0;
+        if (bf16) {
+            g = enqueue_tc(tc, s);
+            if (g < 0) return g;
+        }
+        const int g32 = enqueue_gradient(sl, s, q, p);
+        if (g32 < 0) return g32;
         if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 1], s));
         FP_CUDA(pd_launch(L, P, s));
         if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 2], s));
-        return g + 1;
+        return g + g32 + 1;
     });
     if (r < 0) return r;
     nl += r;
@@ -391,6 +448,9 @@ int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, co
                  const fastpfp_params* p, Ctrl* host_slots) {
     int nl = 0;
     int row0 = 0;
+    const bool bf16 = p->precision == FASTPFP_BF16;
+    TcPlan tc;
+    if (bf16 && !plan_tc(h, &qs[w.first], w.count, p, &tc)) return FASTPFP_ERR_UNSUPPORTED;
     for (int i = 0; i < w.count; ++i) {
         const Problem& q = qs[w.first + i];
         const Slot& sl = h->slots[i];
@@ -400,7 +460,7 @@ int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, co
         PairDesc d{};
         d.Y = sl.Y;
         d.X = sl.X;
-        d.Xt16 = nullptr;
+        d.Xt16 = bf16 ? sl.Xt16 : nullptr;
         d.colbuf = sl.colbuf;
         d.sbuf = sl.sbuf;
         d.dbuf = sl.dbuf;
@@ -409,7 +469,7 @@ int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, co
         d.ldy = round4(q.N);
         d.m = q.m;
         d.ldx = round4(q.m);
-        d.ldxt = d.ldy;
+        d.ldxt = round8(q.N);
         d.row0 = row0;
         row0 += q.N;
         h->h_pairs[i] = d;
@@ -442,6 +502,10 @@ int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, co
         const bool pt = prof && t < kProfIters;
         if (pt && t == 0) FP_CUDA(cudaEventRecord(h->ev[0], s));
         int n = 0;
+        if (bf16) {
+            n = enqueue_tc(tc, s);
+            if (n < 0) return n;
+        }
         for (int i = 0; i < w.count; ++i) {
             const int g = enqueue_gradient(h->slots[i], s, qs[w.first + i], p);
             if (g < 0) return g;
@@ -514,14 +578,14 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     h->ld = round4(max_n);
     h->nslots = std::min(max_batch, kMaxWavePairs);
     if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        pd_configure() != cudaSuccess || pdb_configure() != cudaSuccess ||
+        pd_configure() != cudaSuccess || pdb_configure() != cudaSuccess || tc_configure() != cudaSuccess ||
         disc_configure() != cudaSuccess) {
         delete h;
         return FASTPFP_ERR_CUDA;
     }
     const size_t n = (size_t)max_n, ld = (size_t)h->ld;
     const size_t f32mat = align256(n * ld * sizeof(float));
-    const size_t b16mat = align256(n * ld * sizeof(__nv_bfloat16));
+    const size_t b16mat = align256(n * (size_t)round8(max_n) * sizeof(__nv_bfloat16));
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
     struct SlotOff { size_t Y, X, T, K, A16, A216, Xt16, T16, col, s, d, ctrl, rm, cm, rb, cb; };
@@ -682,7 +746,6 @@ int fastpfp_match_batched(fastpfp_t h, void* stream, int count, const fastpfp_pa
         int rc = check_pair(h, q.A, q.n_a, q.A2, q.n_b, q.B, q.B2, q.k, p, q.perm_out);
         if (rc != FASTPFP_OK) return rc;
     }
-    if (p->precision == FASTPFP_BF16) return FASTPFP_ERR_UNSUPPORTED;
     if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<Problem> qs(count);
@@ -751,10 +814,35 @@ int fastpfp_gradient(fastpfp_t h, void* stream, const float* A, const float* X, 
     if (!h || !A || !X || !A2 || !Y || N < 1 || m < 1 || m > N || ldy < m) return FASTPFP_ERR_ARG;
     if (lambda != 0.f && !K) return FASTPFP_ERR_ARG;
     if (N > h->max_n) return FASTPFP_ERR_SIZE;
-    if (precision != FASTPFP_FP32) return FASTPFP_ERR_UNSUPPORTED;
+    if (precision != FASTPFP_FP32 && precision != FASTPFP_BF16) return FASTPFP_ERR_ARG;
     if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     const Slot& sl = h->slots[0];
+    if (precision == FASTPFP_BF16) {
+        // BF16 operand copies in the slot, products on the tensor cores; Y and
+        // K go through the slot's padded FP32 buffers (16-byte aligned rows)
+        const int l16N = round8(N), l16m = round8(m), l4m = round4(m);
+        FP_CUDA(to_bf16(A, N, N, N, sl.A16, l16N, s));
+        FP_CUDA(to_bf16(A2, m, m, m, sl.A216, l16m, s));
+        FP_CUDA(transpose_to_bf16(X, N, m, m, sl.Xt16, l16N, s));
+        if (lambda != 0.f)
+            FP_CUDA(cudaMemcpy2DAsync(sl.K, (size_t)l4m * 4, K, (size_t)m * 4, (size_t)m * 4, N,
+                                      cudaMemcpyDeviceToDevice, s));
+        TcGroup a{}, c{};
+        a.count = c.count = 1;
+        a.mode = kTcOutBf16;
+        c.mode = kTcOutF32;
+        if (!tc_make_map(&a.map_a[0], sl.A16, N, N, l16N) || !tc_make_map(&a.map_b[0], sl.Xt16, m, N, l16N) ||
+            !tc_make_map(&c.map_a[0], sl.T16, N, m, l16m) || !tc_make_map(&c.map_b[0], sl.A216, m, m, l16m))
+            return FASTPFP_ERR_UNSUPPORTED;
+        a.prob[0] = TcProblem{N, m, N, sl.T16, l16m, nullptr, 0, 0.f, nullptr, nullptr};
+        c.prob[0] = TcProblem{N, m, m, sl.Y, l4m, lambda != 0.f ? sl.K : nullptr, l4m, lambda, nullptr, nullptr};
+        FP_CUDA(tc_gemm(a, s));
+        FP_CUDA(tc_gemm(c, s));
+        FP_CUDA(cudaMemcpy2DAsync(Y, (size_t)ldy * 4, sl.Y, (size_t)l4m * 4, (size_t)m * 4, N,
+                                  cudaMemcpyDeviceToDevice, s));
+        return FASTPFP_OK;
+    }
     GemmF32Args g1{A, N, X, m, sl.T, m, nullptr, 0, 0.f, N, m, N, nullptr};
     GemmF32Args g2{sl.T, m, A2, m, Y, ldy, lambda != 0.f ? K : nullptr, m, lambda, N, m, m, nullptr};
     FP_CUDA(gemm_f32(g1, s));

@@ -1,0 +1,323 @@
+// gemm_tc.cu -- BF16 products of the gradient (Section 4.1) on the sm_103a
+// tensor cores: tcgen05.mma with the accumulator in tensor memory, operands
+// staged into shared memory by TMA (cp.async.bulk.tensor, 128-byte swizzle).
+//
+// Both products are "TN": C[i, j] = sum_k A[i, k] * B[j, k] with A and B
+// stored K-major (row-major with the reduction index contiguous):
+//   T = A X        A: adjacency (N x N), B: X^T (m x N), written by the blend
+//   Y = T A' + lK  A: T (N x m),         B: A' itself (m x m) -- A' is
+//                  symmetric, so its rows are the K-major columns and no
+//                  transpose is ever formed.
+// FP32 accumulation in TMEM; the epilogue writes T as BF16 for the second
+// product, or Y as FP32 with lambda K added.
+//
+// One CTA computes one 128 x 128 output tile of one problem of a group
+// (blockIdx.z): warp 0 issues the TMA loads of a 4-stage ring, warp 1 owns
+// the TMEM allocation and one lane issues the MMAs (K = 16 each, four per
+// 64-wide stage), warps 2..5 drain the accumulator with tcgen05.ld.  Every
+// mbarrier wait is bounded: on expiry the CTA records FASTPFP_ERR_TIMEOUT,
+// stops issuing work, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace fpfp {
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int kTileBytesA = BM * BK * 2;
+constexpr int kTileBytesB = BN * BK * 2;
+constexpr int kStageBytes = kTileBytesA + kTileBytesB;
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 128;
+constexpr long long kWaitNs = 2000ll * 1000000ll;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait on phase `parity`; false (and *abort set) on expiry or when
+// another role of the CTA has already given up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 63u) == 0u) {
+            if (*abort) return false;
+            if ((long long)(globaltimer_ns() - t0) > kWaitNs) {
+                *abort = 1;
+                return false;
+            }
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): K-major operand, 128-byte
+// swizzle, 8-row core groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused with this swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
+    d |= (uint64_t)1 << 46;                     // fixed 0b001
+    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, both
+// K-major, M = 128, N = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcGroup G) {
+    const int g = blockIdx.z;
+    if (g >= G.count) return;
+    const TcProblem& pr = G.prob[g];
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    if (m0 >= pr.M || n0 >= pr.N) return;
+    if (pr.ctrl) {
+        if (ld_relaxed_i32(&pr.ctrl->done) != 0 || ld_relaxed_i32(&pr.ctrl->error) != 0) return;
+        if (ld_relaxed_i32(&pr.ctrl->lowp) == 0) return;
+    }
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte alignment of the tile ring (required by the 128-byte swizzle)
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* tiles = base;
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * kStageBytes);
+    uint64_t* empty = full + STAGES;
+    uint64_t* acc_full = empty + STAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = (pr.K + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(acc_full, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+            if (!mbar_wait(&empty[s], ph ^ 1u, abort)) break;
+            unsigned char* a = tiles + s * kStageBytes;
+            unsigned char* b = a + kTileBytesA;
+            mbar_expect_tx(&full[s], kStageBytes);
+            tma_load_2d(a, &G.map_a[g], kb * BK, m0, &full[s]);
+            tma_load_2d(b, &G.map_b[g], kb * BK, n0, &full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+            if (!mbar_wait(&full[s], ph, abort)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a = smem_u32(tiles + s * kStageBytes);
+            const uint32_t b = a + kTileBytesA;
+            const uint64_t ad = smem_desc(a), bd = smem_desc(b);
+#pragma unroll
+            for (int j = 0; j < BK / 16; ++j)   // K = 16 per MMA: 32 bytes along the swizzled row
+                mma_bf16(tmem, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), (kb > 0 || j > 0) ? 1u : 0u);
+            mma_commit(&empty[s]);
+        }
+        mma_commit(acc_full);
+    } else if (warp >= 2) {
+        // epilogue: warp w reads TMEM lanes 32 * (w % 4) .. + 31 = tile rows
+        const int quarter = warp & 3;
+        const int row = m0 + quarter * 32 + lane;
+        // one lane waits; tcgen05.ld is warp-collective, so the outcome is broadcast
+        int okl = 0;
+        if (lane == 0) okl = mbar_wait(acc_full, 0u, abort) ? 1 : 0;
+        const bool ok = __shfl_sync(0xffffffffu, okl, 0) != 0;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok) {
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c, r);
+                const int col = n0 + c;
+                if (row >= pr.M || col >= pr.N) continue;
+                const int nv = min(32, pr.N - col);
+                if (G.mode == kTcOutBf16) {
+                    __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(pr.out) + (size_t)row * pr.ldo + col;
+                    if (nv == 32) {
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            uint4 pk;
+                            __nv_bfloat162 h0 = __floats2bfloat162_rn(__uint_as_float(r[8 * v + 0]), __uint_as_float(r[8 * v + 1]));
+                            __nv_bfloat162 h1 = __floats2bfloat162_rn(__uint_as_float(r[8 * v + 2]), __uint_as_float(r[8 * v + 3]));
+                            __nv_bfloat162 h2 = __floats2bfloat162_rn(__uint_as_float(r[8 * v + 4]), __uint_as_float(r[8 * v + 5]));
+                            __nv_bfloat162 h3 = __floats2bfloat162_rn(__uint_as_float(r[8 * v + 6]), __uint_as_float(r[8 * v + 7]));
+                            pk.x = *reinterpret_cast<uint32_t*>(&h0);
+                            pk.y = *reinterpret_cast<uint32_t*>(&h1);
+                            pk.z = *reinterpret_cast<uint32_t*>(&h2);
+                            pk.w = *reinterpret_cast<uint32_t*>(&h3);
+                            reinterpret_cast<uint4*>(out)[v] = pk;
+                        }
+                    } else {
+                        for (int v = 0; v < nv; ++v) out[v] = __float2bfloat16_rn(__uint_as_float(r[v]));
+                    }
+                } else {
+                    float* out = reinterpret_cast<float*>(pr.out) + (size_t)row * pr.ldo + col;
+                    const float* kk = pr.Kmat ? pr.Kmat + (size_t)row * pr.ldk + col : nullptr;
+                    if (nv == 32) {
+#pragma unroll
+                        for (int v = 0; v < 8; ++v) {
+                            float4 o = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                                                   __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
+                            if (kk) {
+                                const float4 kv = __ldg(reinterpret_cast<const float4*>(kk) + v);
+                                o.x = fmaf(pr.lambda, kv.x, o.x);
+                                o.y = fmaf(pr.lambda, kv.y, o.y);
+                                o.z = fmaf(pr.lambda, kv.z, o.z);
+                                o.w = fmaf(pr.lambda, kv.w, o.w);
+                            }
+                            reinterpret_cast<float4*>(out)[v] = o;
+                        }
+                    } else {
+                        for (int v = 0; v < nv; ++v) {
+                            float o = __uint_as_float(r[v]);
+                            if (kk) o = fmaf(pr.lambda, kk[v], o);
+                            out[v] = o;
+                        }
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    if (*abort && threadIdx.x == 0) {
+        int* err = pr.err;
+        if (err) atomicCAS(err, 0, FASTPFP_ERR_TIMEOUT);
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+size_t tc_smem_bytes() { return (size_t)STAGES * kStageBytes + 1024 + 256; }
+
+cudaError_t tc_configure() {
+    return cudaFuncSetAttribute((const void*)tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tc_smem_bytes());
+}
+
+// rows x cols BF16 matrix, row-major with leading dimension ld (elements,
+// a multiple of 8), read as 128-row x 64-column boxes with 128-byte swizzle.
+bool tc_make_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int cols, int ld) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn || (ld % 8) != 0 || (reinterpret_cast<uintptr_t>(ptr) & 15) != 0) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+cudaError_t tc_gemm(const TcGroup& G, cudaStream_t s) {
+    int mt = 1, nt = 1;
+    for (int i = 0; i < G.count; ++i) {
+        mt = max(mt, (G.prob[i].M + BM - 1) / BM);
+        nt = max(nt, (G.prob[i].N + BN - 1) / BN);
+    }
+    if (G.count <= 0) return cudaSuccess;
+    tc_gemm_kernel<<<dim3(nt, mt, G.count), kThreads, tc_smem_bytes(), s>>>(G);
+    return cudaGetLastError();
+}
+
+}  // namespace fpfp

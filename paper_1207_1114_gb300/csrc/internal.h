@@ -2,6 +2,7 @@
 // kernels.  Not installed; not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -108,6 +109,34 @@ cudaError_t pdb_configure();
 size_t pdb_smem_bytes(const PdbLayout& L, int nthr);
 cudaError_t pdb_launch(const PdbParams& P, int grid, size_t smem, cudaStream_t s);
 
+// ------------------------------------------------- tensor-core products
+constexpr int kTcMaxGroup = 8;       // problems of one grouped launch
+constexpr int kTcOutBf16 = 0;        // epilogue writes BF16 (T = A X)
+constexpr int kTcOutF32 = 1;         // epilogue writes FP32 + lambda K (Y = T A' + lambda K)
+
+// C[M x N] = A[M x K] B[N x K]^T, both operands BF16 K-major (tensor maps).
+struct TcProblem {
+    int M, N, K;
+    void* out;            // BF16 or FP32 row-major, leading dimension ldo
+    int ldo;
+    const float* Kmat;    // FP32 mode: nullable lambda * K addend, leading dimension ldk
+    int ldk;
+    float lambda;
+    const Ctrl* ctrl;     // nullable: skip unless the solve runs its BF16 phase
+    int* err;             // nullable: receives FASTPFP_ERR_TIMEOUT
+};
+struct TcGroup {
+    CUtensorMap map_a[kTcMaxGroup];
+    CUtensorMap map_b[kTcMaxGroup];
+    TcProblem prob[kTcMaxGroup];
+    int count;
+    int mode;
+};
+size_t tc_smem_bytes();
+cudaError_t tc_configure();
+bool tc_make_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int cols, int ld);
+cudaError_t tc_gemm(const TcGroup& G, cudaStream_t s);
+
 // ----------------------------------------------------------------- GEMM
 // C[M x Nc] = Aop[M x K] * Bop[K x Nc] (+ lambda * Kmat), row-major FP32.
 // When ctrl is set the kernel does nothing unless the solve is running and
@@ -138,6 +167,10 @@ cudaError_t init_x(float* X, int N, int m, int ldx, const float* X0, int transpo
 // pad columns c..ldd-1 are written as zero.
 cudaError_t to_bf16(const float* src, int r, int c, int lds, __nv_bfloat16* dst, int ldd,
                     cudaStream_t s);
+
+// dst (c x ldd, BF16) = src^T for an r x c FP32 src with leading dimension lds.
+cudaError_t transpose_to_bf16(const float* src, int r, int c, int lds, __nv_bfloat16* dst, int ldd,
+                              cudaStream_t s);
 
 // Caller-orientation outputs from the canonical result.
 cudaError_t write_outputs(const int32_t* row_of_col, int N, int m, int transposed, int32_t* perm_out,

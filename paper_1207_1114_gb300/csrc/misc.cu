@@ -55,6 +55,21 @@ __global__ void to_bf16_kernel(const float* src, int r, int c, int lds, __nv_bfl
     }
 }
 
+// dst (c x ldd, BF16) = src^T for an r x c FP32 src (leading dimension lds).
+__global__ void transpose_bf16_kernel(const float* src, int r, int c, int lds, __nv_bfloat16* dst, int ldd) {
+    __shared__ float tile[32][33];
+    const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int i = bi + y, j = bj + threadIdx.x;
+        tile[y][threadIdx.x] = (i < r && j < c) ? src[(size_t)i * lds + j] : 0.f;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int j = bj + y, i = bi + threadIdx.x;
+        if (j < c && i < r) dst[(size_t)j * ldd + i] = __float2bfloat16_rn(tile[threadIdx.x][y]);
+    }
+}
+
 __global__ void perm_fill_kernel(int32_t* perm, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) perm[i] = -1;
@@ -149,6 +164,13 @@ cudaError_t to_bf16(const float* src, int r, int c, int lds, __nv_bfloat16* dst,
                     cudaStream_t s) {
     const size_t total = (size_t)r * ldd;
     to_bf16_kernel<<<grid_for(total, 256), 256, 0, s>>>(src, r, c, lds, dst, ldd);
+    return cudaGetLastError();
+}
+
+cudaError_t transpose_to_bf16(const float* src, int r, int c, int lds, __nv_bfloat16* dst, int ldd,
+                              cudaStream_t s) {
+    dim3 grid((c + 31) / 32, (r + 31) / 32);
+    transpose_bf16_kernel<<<grid, dim3(32, 8), 0, s>>>(src, r, c, lds, dst, ldd);
     return cudaGetLastError();
 }
 

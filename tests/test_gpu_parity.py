@@ -68,6 +68,32 @@ def test_gradient_matches_oracle(solver, N, m):
     assert (np.abs(G - ref) <= 1e-5 * bound + 1e-30).all()
 
 
+def _bf16(a):
+    """Round to bfloat16 (nearest even) and back, as the tensor-core path does."""
+    t = torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16)
+    return t.to(torch.float32).numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("N,m", [(5, 3), (129, 100), (300, 300), (1000, 1000), (1200, 1000)])
+def test_gradient_bf16_tensor_cores_matches_oracle(solver, N, m):
+    """tcgen05 BF16 products: A, X, A' and T are rounded to BF16 (unit roundoff
+    2^-9), accumulation is FP32.  Against the oracle on the same BF16-rounded
+    operands only T's rounding remains: |err| <= 3e-3 * |A||X||A'| (+ the FP32
+    term); against the unrounded oracle four roundings: 1e-2 * the bound."""
+    rng = np.random.default_rng(N * 5 + m)
+    A = synth.random_graph(rng, N, 0.2).astype(np.float32)
+    A2 = synth.random_graph(rng, m, 0.2).astype(np.float32)
+    X = rng.random((N, m)).astype(np.float32)
+    K = rng.normal(size=(N, m)).astype(np.float32)
+    lam = 0.7
+    G = solver.gradient(cu(A), cu(X), cu(A2), cu(K), lam, precision=F.BF16).cpu().numpy()
+    bound = np.abs(A) @ np.abs(X).astype(np.float64) @ np.abs(A2) + lam * np.abs(K)
+    ref = oracle.gradient(A, X, A2, K, lam)
+    assert (np.abs(G - ref) <= 1e-2 * bound + 1e-30).all()
+    ref16 = oracle.gradient(_bf16(A), _bf16(X), _bf16(A2), K, lam)
+    assert (np.abs(G - ref16) <= 3e-3 * bound + 1e-30).all()
+
+
 @pytest.mark.parametrize("N", [1, 2, 3, 7, 64, 100, 129, 333, 1000, 1200])
 def test_projection_matches_oracle_fixed_rounds(solver, N):
     rng = np.random.default_rng(N)
@@ -232,6 +258,39 @@ def test_batched_wave_at_full_size_matches_oracle(solver):
     """Three n = 1000 attributed pairs in one wave, a few outer iterations."""
     pairs = [synth.attributed_1000(seed=s) for s in range(3)]
     _check_batch(solver, pairs, 1.0, max_outer=3, max_inner=150)
+
+
+def test_bf16_phase_then_fp32_refinement(solver):
+    """Precision policy: BF16 tensor-core products until max|dX| < switch_tol,
+    then FP32 iterations.  The refined result matches the plain FP32 solve's
+    permutation and objective; the refinement's X matches the oracle replaying
+    the FP32 iterations from the X the BF16 phase reached."""
+    g = synth.attributed_1000(seed=1)
+    A, A2, B, B2 = cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)
+    p32 = F.default_params(lam=1.0)
+    r32 = solver.match(A, A2, B, B2, params=p32, want_X=True)
+    p16 = F.default_params(lam=1.0, precision=F.BF16, refine_iters=30, switch_tol=1e-3)
+    r16 = solver.match(A, A2, B, B2, params=p16, want_X=True)
+    st = r16.stats
+    assert st.status == 0 and st.lowp_iters >= 1 and st.outer_iters > st.lowp_iters
+    assert st.converged == 1
+    np.testing.assert_array_equal(r16.perm.cpu().numpy(), r32.perm.cpu().numpy())
+    assert abs(st.objective - r32.stats.objective) <= 1e-5 * abs(r32.stats.objective)
+    assert np.abs(r16.X.cpu().numpy() - r32.X.cpu().numpy()).max() <= 1e-3
+
+
+def test_bf16_batched_wave(solver):
+    """A wave of pairs with the BF16 phase: every pair converges in FP32 and
+    recovers the ground truth like the FP32 solve."""
+    pairs = synth.batch_mixed(count=5, seed=11, n_lo=100, n_hi=400, out_hi=40)
+    dev = [(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)) for g in pairs]
+    p16 = F.default_params(lam=0.5, precision=F.BF16, refine_iters=30)
+    p32 = F.default_params(lam=0.5)
+    o16 = solver.match_batched(dev, params=p16)
+    o32 = solver.match_batched(dev, params=p32)
+    for a, b in zip(o16, o32):
+        assert a.stats.status == 0 and a.stats.lowp_iters >= 1
+        assert abs(a.stats.objective - b.stats.objective) <= 1e-4 * abs(b.stats.objective)
 
 
 def test_batched_mixed_small_pairs_plain(solver):
