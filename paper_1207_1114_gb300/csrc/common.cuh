@@ -140,4 +140,36 @@ __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned target,
     return s_ok != 0;
 }
 
+// Split-phase form of grid_barrier: grid_arrive publishes the CTA's prior
+// writes and counts it in; grid_wait (later, after unrelated work) waits until
+// the counter reaches `target`.  Same bounds and error handling as above.
+__device__ __forceinline__ void grid_arrive(unsigned* counter) {
+    __syncthreads();
+    if (threadIdx.x == 0) red_release_add_u32(counter, 1u);
+}
+__device__ __forceinline__ bool grid_wait(unsigned* counter, unsigned target, int* err,
+                                          long long timeout_ns) {
+    __shared__ int s_ok_w;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        uint64_t t0 = 0;
+        unsigned spins = 0;
+        while (ld_acquire_u32(counter) < target) {
+            if ((++spins & 255u) == 0u) {
+                const uint64_t now = globaltimer_ns();
+                if (t0 == 0) t0 = now;
+                if (ld_relaxed_i32(err) != 0 || (long long)(now - t0) > timeout_ns ||
+                    spins > (1u << 30)) {
+                    atomicCAS(err, 0, FASTPFP_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        s_ok_w = ok;
+    }
+    __syncthreads();
+    return s_ok_w != 0;
+}
+
 }  // namespace fpfp

@@ -37,6 +37,10 @@ constexpr int kProfIters = 128;                   // outer iterations timed when
 constexpr int kProfEvents = 2 * kProfIters + 3;   // iteration boundaries + discretisation
 constexpr int kChunk = 4;                         // outer iterations enqueued between checks
 constexpr long long kMinElemsPerCta = 8192;       // smallest band worth a CTA of its own
+// Two interleaved pair groups per wave (one group's barrier hidden behind the
+// other's round).  Measured slower on GB300 at n = 1000 (17.3 vs 11.8 us per
+// 7-pair round): a round's fixed cost is serial latency, not barrier waiting.
+constexpr bool kInterleaveGroups = false;
 
 inline int round4(int x) { return (x + 3) & ~3; }
 inline int round8(int x) { return (x + 7) & ~7; }   // BF16 rows: 16-byte TMA strides
@@ -366,63 +370,84 @@ int fill_stats(const Ctrl& c, int transposed, int launches, fastpfp_stats* st) {
 // ---- waves of the batched path ---------------------------------------------
 
 struct Wave {
-    int first = 0, count = 0, grid = 0;
+    int first = 0, count = 0, split = 0, grid = 0;
     size_t smem = 0;
     PdbLayout layout{};
-    std::vector<int> band;   // grid + 1 boundaries
+    std::vector<int> band;   // 2 x (grid + 1) boundaries: group 0, then group 1
 };
 
-// Splits the concatenated rows of pairs [first, first + count) into at most
-// num_sms bands of about equal entry counts; fills the layout maxima.
-// Returns false when a band would not fit in shared memory.
-bool plan_bands(const std::vector<Problem>& qs, int first, int count, int num_sms, Wave* w) {
+struct BandStats {
+    int rows = 0, cols = 0, elems = 0, segs = 0;
+};
+
+// Cuts the concatenated rows of pairs [first, first + count) into G bands of
+// about equal entry counts: band[0..G] row boundaries, per-band statistics.
+void split_group(const std::vector<Problem>& qs, int first, int count, int G, int* band,
+                 std::vector<BandStats>& st) {
     long long E = 0;
     int rows = 0;
     for (int i = 0; i < count; ++i) {
         E += (long long)qs[first + i].N * round4(qs[first + i].N);
         rows += qs[first + i].N;
     }
-    long long gl = (E + kMinElemsPerCta - 1) / kMinElemsPerCta;
-    int G = (int)std::min<long long>(num_sms, std::max<long long>(1, gl));
-    G = std::min(G, rows);
-    w->band.assign(G + 1, rows);
-    w->band[0] = 0;
-    int b = 0;
+    for (int c = 0; c <= G; ++c) band[c] = rows;
+    band[0] = 0;
+    int b = 0, gr = 0, last_pair = -1;
     long long cum = 0;
-    int gr = 0;
-    PdbLayout L{0, 0, 0};
-    int cur_rows = 0, cur_cols = 0, cur_elems = 0, cur_segs = 0, last_pair = -1;
-    bool ok = true;
-    auto close_band = [&]() {
-        L.max_band_rows = std::max(L.max_band_rows, cur_rows);
-        L.max_band_cols = std::max(L.max_band_cols, cur_cols);
-        L.max_band_elems = std::max(L.max_band_elems, cur_elems);
-        if (cur_segs > kMaxSeg) ok = false;
-        cur_rows = cur_cols = cur_elems = cur_segs = 0;
-        last_pair = -1;
-    };
     for (int i = 0; i < count; ++i) {
         const int N = qs[first + i].N, ldy = round4(N);
         for (int r = 0; r < N; ++r, ++gr) {
-            if (b < G - 1 && cum >= E * (b + 1) / G && cur_rows > 0) {
-                close_band();
+            if (b < G - 1 && cum >= E * (b + 1) / G && st[b].rows > 0) {
                 ++b;
-                w->band[b] = gr;
+                band[b] = gr;
+                last_pair = -1;
             }
             if (last_pair != i) {
-                cur_cols += ldy;
-                ++cur_segs;
+                st[b].cols += ldy;
+                ++st[b].segs;
                 last_pair = i;
             }
-            ++cur_rows;
-            cur_elems += ldy;
+            ++st[b].rows;
+            st[b].elems += ldy;
             cum += ldy;
         }
     }
-    close_band();
-    for (int c = b + 1; c <= G; ++c) w->band[c] = rows;
+}
+
+// Plans one wave of pairs [first, first + count): two groups of about equal
+// entry counts (group 1 one half-step behind group 0), each cut into at most
+// num_sms bands; a CTA holds one band of each group.  Returns false when a
+// CTA's bands would not fit in shared memory.
+bool plan_bands(const std::vector<Problem>& qs, int first, int count, int num_sms, Wave* w) {
+    long long E = 0;
+    for (int i = 0; i < count; ++i) E += (long long)qs[first + i].N * round4(qs[first + i].N);
+    int split = count;
+    if (kInterleaveGroups && count > 1) {
+        long long pre = 0;
+        split = 1;
+        for (int i = 0; i < count - 1; ++i) {
+            pre += (long long)qs[first + i].N * round4(qs[first + i].N);
+            split = i + 1;
+            if (2 * pre >= E) break;
+        }
+    }
+    const long long gl = (E + kMinElemsPerCta - 1) / kMinElemsPerCta;
+    const int G = (int)std::min<long long>(num_sms, std::max<long long>(1, gl));
+    w->band.assign(2 * (G + 1), 0);
+    std::vector<BandStats> s0(G), s1(G);
+    split_group(qs, first, split, G, w->band.data(), s0);
+    split_group(qs, first + split, count - split, G, w->band.data() + G + 1, s1);
+    PdbLayout L{0, 0, 0};
+    bool ok = true;
+    for (int b = 0; b < G; ++b) {
+        L.max_band_rows = std::max(L.max_band_rows, s0[b].rows + s1[b].rows);
+        L.max_band_cols = std::max(L.max_band_cols, s0[b].cols + s1[b].cols);
+        L.max_band_elems = std::max(L.max_band_elems, s0[b].elems + s1[b].elems);
+        if (s0[b].segs + s1[b].segs > kMaxSeg) ok = false;
+    }
     w->first = first;
     w->count = count;
+    w->split = split;
     w->grid = G;
     w->layout = L;
     w->smem = pdb_smem_bytes(L, kPdbThreads);
@@ -470,17 +495,19 @@ int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, co
         d.m = q.m;
         d.ldx = round4(q.m);
         d.ldxt = round8(q.N);
+        if (i == w.split) row0 = 0;   // rows are counted per group
         d.row0 = row0;
         row0 += q.N;
         h->h_pairs[i] = d;
     }
-    for (int b = 0; b <= w.grid; ++b) h->h_band[b] = w.band[b];
+    for (int b = 0; b < 2 * (w.grid + 1); ++b) h->h_band[b] = w.band[b];
     FP_CUDA(cudaMemcpyAsync(h->d_pairs, h->h_pairs, sizeof(PairDesc) * w.count, cudaMemcpyHostToDevice, s));
-    FP_CUDA(cudaMemcpyAsync(h->d_band, h->h_band, sizeof(int) * (w.grid + 1), cudaMemcpyHostToDevice, s));
+    FP_CUDA(cudaMemcpyAsync(h->d_band, h->h_band, sizeof(int) * 2 * (w.grid + 1), cudaMemcpyHostToDevice, s));
     FP_CUDA(cudaMemsetAsync(h->d_wave, 0, sizeof(WaveCtrl), s));
     PdbParams P{};
     P.pairs = h->d_pairs;
     P.npairs = w.count;
+    P.split = w.split;
     P.band_row = h->d_band;
     P.wave = h->d_wave;
     P.layout = w.layout;
@@ -494,10 +521,26 @@ int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, co
     P.refine_iters = p->refine_iters;
     P.switch_tol = p->switch_tol;
     P.timeout_ns = timeout_ns(p);
+    // FP32 products of every pair of the wave: one grouped launch per product
+    std::vector<GemmF32Group> f32a, f32b;
+    for (int b = 0; b < w.count; b += kF32MaxGroup) {
+        GemmF32Group ga{}, gb{};
+        ga.count = gb.count = std::min(kF32MaxGroup, w.count - b);
+        for (int i = 0; i < ga.count; ++i) {
+            const Problem& q = qs[w.first + b + i];
+            const Slot& sl = h->slots[b + i];
+            const int ldy = round4(q.N), ldx = round4(q.m);
+            ga.a[i] = GemmF32Args{q.A, q.N, sl.X, ldx, sl.T, ldx, nullptr, 0, 0.f, q.N, q.m, q.N, sl.ctrl};
+            gb.a[i] = GemmF32Args{sl.T, ldx, q.A2, q.m, sl.Y, ldy, q.k ? sl.K : nullptr, ldx,
+                                  q.k ? (float)p->lambda : 0.f, q.N, q.m, q.m, sl.ctrl};
+        }
+        f32a.push_back(ga);
+        f32b.push_back(gb);
+    }
     const bool prof = p->profile != 0;
-    static_assert(offsetof(WaveCtrl, error) == 8 && offsetof(WaveCtrl, all_done) == 12,
+    static_assert(offsetof(WaveCtrl, error) == 0 && offsetof(WaveCtrl, all_done) == 4,
                   "WaveCtrl layout");
-    const int r = run_outer(h, s, reinterpret_cast<const int*>(h->d_wave), 3, 2, p->max_outer,
+    const int r = run_outer(h, s, reinterpret_cast<const int*>(h->d_wave), 1, 0, p->max_outer,
                             [&](int t) -> int {
         const bool pt = prof && t < kProfIters;
         if (pt && t == 0) FP_CUDA(cudaEventRecord(h->ev[0], s));
@@ -506,11 +549,9 @@ int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, co
             n = enqueue_tc(tc, s);
             if (n < 0) return n;
         }
-        for (int i = 0; i < w.count; ++i) {
-            const int g = enqueue_gradient(h->slots[i], s, qs[w.first + i], p);
-            if (g < 0) return g;
-            n += g;
-        }
+        for (const GemmF32Group& g : f32a) FP_CUDA(gemm_f32_group(g, s));   // T = A X
+        for (const GemmF32Group& g : f32b) FP_CUDA(gemm_f32_group(g, s));   // Y = T A' + lambda K
+        n += (int)(f32a.size() + f32b.size());
         if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 1], s));
         FP_CUDA(pdb_launch(P, w.grid, w.smem, s));
         if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 2], s));
@@ -598,7 +639,7 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
         o.rm = take(n * 4); o.cm = take(n * 4); o.rb = take(n * 8); o.cb = take(2 * n * 8);
     }
     const size_t opairs = take(sizeof(PairDesc) * kMaxWavePairs);
-    const size_t oband = take(sizeof(int) * (h->num_sms + 1));
+    const size_t oband = take(sizeof(int) * 2 * (h->num_sms + 1));
     const size_t owave = take(sizeof(WaveCtrl));
     const size_t osA = take(n * n * 4), osA2 = take(n * n * 4), osB = take(n * kMaxK * 4),
                  osB2 = take(n * kMaxK * 4), osX0 = take(n * n * 4), osXo = take(n * n * 4),
@@ -620,7 +661,7 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     if (cudaMalloc(&h->pool, off) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
     if (cudaMallocHost(&h->host_ctrl, sizeof(Ctrl) * (size_t)max_batch) != cudaSuccess ||
         cudaMallocHost(&h->h_pairs, sizeof(PairDesc) * kMaxWavePairs) != cudaSuccess ||
-        cudaMallocHost(&h->h_band, sizeof(int) * (h->num_sms + 1)) != cudaSuccess ||
+        cudaMallocHost(&h->h_band, sizeof(int) * 2 * (h->num_sms + 1)) != cudaSuccess ||
         cudaMallocHost(&h->h_done, sizeof(int) * 8) != cudaSuccess)
         return fail(FASTPFP_ERR_CUDA);
     char* b = h->pool;

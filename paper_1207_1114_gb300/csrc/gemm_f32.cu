@@ -12,7 +12,10 @@ namespace {
 constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
 constexpr int kThreads = (BM / TM) * (BN / TN);  // 256
 
-__global__ void __launch_bounds__(kThreads) gemm_f32_kernel(const GemmF32Args g) {
+__global__ void __launch_bounds__(kThreads) gemm_f32_kernel(const __grid_constant__ GemmF32Group grp) {
+    if ((int)blockIdx.z >= grp.count) return;
+    const GemmF32Args& g = grp.a[blockIdx.z];
+    if ((int)blockIdx.y * BM >= g.M || (int)blockIdx.x * BN >= g.Nc) return;
     if (g.ctrl) {
         if (ld_relaxed_i32(&g.ctrl->done) != 0 || ld_relaxed_i32(&g.ctrl->error) != 0) return;
         if (ld_relaxed_i32(&g.ctrl->lowp) != 0) return;
@@ -104,11 +107,22 @@ __global__ void __launch_bounds__(kThreads) gemm_f32_kernel(const GemmF32Args g)
 
 }  // namespace
 
-cudaError_t gemm_f32(const GemmF32Args& a, cudaStream_t s) {
-    if (a.M <= 0 || a.Nc <= 0) return cudaSuccess;
-    dim3 grid((a.Nc + BN - 1) / BN, (a.M + BM - 1) / BM);
-    gemm_f32_kernel<<<grid, kThreads, 0, s>>>(a);
+cudaError_t gemm_f32_group(const GemmF32Group& g, cudaStream_t s) {
+    int mt = 0, nt = 0;
+    for (int i = 0; i < g.count; ++i) {
+        mt = max(mt, (g.a[i].M + BM - 1) / BM);
+        nt = max(nt, (g.a[i].Nc + BN - 1) / BN);
+    }
+    if (g.count <= 0 || mt == 0 || nt == 0) return cudaSuccess;
+    gemm_f32_kernel<<<dim3(nt, mt, g.count), kThreads, 0, s>>>(g);
     return cudaGetLastError();
+}
+
+cudaError_t gemm_f32(const GemmF32Args& a, cudaStream_t s) {
+    GemmF32Group g{};
+    g.a[0] = a;
+    g.count = 1;
+    return gemm_f32_group(g, s);
 }
 
 }  // namespace fpfp

@@ -70,15 +70,16 @@ struct PairDesc {
     unsigned* dbuf;       // 3 round maxima
     Ctrl* ctrl;           // the pair's control block
     int N, ldy, m, ldx, ldxt;
-    int row0;             // first row of the pair in the wave's concatenated rows
+    int row0;             // first row of the pair in its group's concatenated rows
 };
 
-// Wave-level state: barrier counter, error word, "every pair done".
+// Wave-level state: error word, "every pair done", and one grid-barrier
+// counter per pair group (the two groups' rounds are interleaved).
 struct WaveCtrl {
-    unsigned bar;
-    unsigned bar_base;
     int error;
     int all_done;
+    unsigned bar[2];
+    unsigned bar_base[2];
 };
 
 // Shared-memory sizing of the batched kernel (maxima over the CTAs' bands).
@@ -91,7 +92,8 @@ struct PdbLayout {
 struct PdbParams {
     const PairDesc* pairs;
     int npairs;
-    const int* band_row;  // grid + 1 row boundaries in the concatenated row space
+    int split;            // pairs [0, split) form group 0, [split, npairs) group 1
+    const int* band_row;  // 2 x (grid + 1) row boundaries, per group, in its concatenated rows
     WaveCtrl* wave;
     PdbLayout layout;
     float alpha;
@@ -150,6 +152,14 @@ struct GemmF32Args {
     const Ctrl* ctrl;
 };
 cudaError_t gemm_f32(const GemmF32Args& a, cudaStream_t s);
+
+// Up to kF32MaxGroup independent products in one launch (blockIdx.z).
+constexpr int kF32MaxGroup = 8;
+struct GemmF32Group {
+    GemmF32Args a[kF32MaxGroup];
+    int count;
+};
+cudaError_t gemm_f32_group(const GemmF32Group& g, cudaStream_t s);
 
 // ----------------------------------------------------------- misc kernels
 cudaError_t init_ctrl(Ctrl* c, int lowp, cudaStream_t s);

@@ -3,18 +3,20 @@
 // Algorithm 1 for a whole wave of graph pairs at once.
 //
 // The projection rounds are bound by grid-synchronisation latency, not by
-// bandwidth: one pair leaves the SMs idle while they wait for the barrier.  A
-// wave therefore shares every barrier between many pairs.  All rows of all
-// pairs of the wave are concatenated and cut into one band per CTA with about
-// the same number of matrix entries; a band may span several pairs ("segments")
-// and stays in shared memory for all rounds.  Each round, for every segment of
-// its band, a CTA applies Eq. (P1) and Eq. (P2) elementwise, measures max|dY|,
-// and publishes that pair's column partials (vector red.add), FP64 share of
-// the total s and round maximum; one bounded grid barrier ends the round for
-// every pair.  After the barrier every CTA reads every pair's round maximum,
-// so all CTAs take the same stop decision for each pair (a pair stops when
-// max|dY| < eps_2 or after I_1 rounds) and leave the round loop together once
-// no pair is active.  Pairs whose outer loop has finished are skipped.
+// bandwidth.  A wave therefore shares every barrier between many pairs.  The
+// kernel can also split a wave into two groups with their own barrier
+// counters and compute one group's round while the other's barrier completes
+//     arrive(A,u) -> wait(B,u-1) -> round B(u) -> arrive(B,u) -> wait(A,u) -> round A(u+1) ...
+// (the host chooses; with one group, group 1 is empty).
+// Within a group all rows of all pairs are concatenated and cut into one band
+// per CTA with about the same number of entries; a band may span several
+// pairs ("segments") and stays in shared memory for all rounds.  A round
+// applies Eq. (P1) and Eq. (P2) elementwise to every segment of the group,
+// measures max|dY|, and publishes the pairs' column partials (vector
+// red.add), FP64 shares of the totals s and round maxima.  After the group's
+// barrier every CTA reads every pair's round maximum, so all CTAs take the
+// same stop decision for each pair (max|dY| < eps_2 or I_1 rounds) and leave
+// the loop together.  Pairs whose outer loop has finished are skipped.
 #include <type_traits>
 
 #include "common.cuh"
@@ -25,11 +27,13 @@ namespace {
 
 struct Seg {
     int pair;       // index into the wave's pair table
+    int group;      // 0 or 1
     int lr0;        // first row of the segment inside its pair
     int nrows;      // rows of the segment
     int brow0;      // first row of the segment inside the band (rsum/arow index)
     int soff;       // float offset of the segment's rows in the band storage
     int coff;       // float offset of the segment's c/N vector
+    int pad;
 };
 
 // Per-pair fields used every round, copied to shared memory once per launch.
@@ -46,7 +50,7 @@ struct Shared {
     PairS* pair;         // kMaxWavePairs
     int* pstate;         // kMaxWavePairs: bit0 active this launch, bit1 stopped
     int* pstop;          // kMaxWavePairs: round at which the pair stopped
-    int* ictl;           // [0] any active, [1] non-finite, [2] n segments
+    int* ictl;           // [0],[1] group has an active pair, [2] n segments, [3] non-finite
     float* fred;         // kMaxSeg x 32 per-warp maxima
     float* rsum;         // band rows
     float* arow;         // band rows
@@ -184,32 +188,38 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     const unsigned G = gridDim.x;
     Shared S = carve_b(smem_raw, P.layout, nthr);
     int* err = &W->error;
-    const unsigned bar_base = W->bar_base;
-    unsigned gen = 0;
-    const int npairs = P.npairs;
+    const unsigned base0 = W->bar_base[0], base1 = W->bar_base[1];
+    unsigned gen[2] = {0u, 0u};
+    const int npairs = P.npairs, split = P.split;
 
-    // ---- band -> segments, pair states and per-pair fields
-    const int b0 = P.band_row[blockIdx.x], b1 = P.band_row[blockIdx.x + 1];
+    // ---- bands of both groups -> segments, pair states and per-pair fields
     if (tid == 0) {
         int nseg = 0, brow = 0, soff = 0, coff = 0;
-        for (int p = 0; p < npairs && nseg < kMaxSeg; ++p) {
-            const PairDesc& d = P.pairs[p];
-            const int lo = max(b0, d.row0), hi = min(b1, d.row0 + d.N);
-            if (lo >= hi) continue;
-            Seg s;
-            s.pair = p;
-            s.lr0 = lo - d.row0;
-            s.nrows = hi - lo;
-            s.brow0 = brow;
-            s.soff = soff;
-            s.coff = coff;
-            S.seg[nseg++] = s;
-            brow += s.nrows;
-            soff += s.nrows * d.ldy;
-            coff += d.ldy;
+        for (int g = 0; g < 2; ++g) {
+            const int* band = P.band_row + g * (G + 1);
+            const int b0 = band[blockIdx.x], b1 = band[blockIdx.x + 1];
+            const int p0 = g == 0 ? 0 : split, p1 = g == 0 ? split : npairs;
+            for (int p = p0; p < p1 && nseg < kMaxSeg; ++p) {
+                const PairDesc& d = P.pairs[p];
+                const int lo = max(b0, d.row0), hi = min(b1, d.row0 + d.N);
+                if (lo >= hi) continue;
+                Seg s;
+                s.pair = p;
+                s.group = g;
+                s.lr0 = lo - d.row0;
+                s.nrows = hi - lo;
+                s.brow0 = brow;
+                s.soff = soff;
+                s.coff = coff;
+                s.pad = 0;
+                S.seg[nseg++] = s;
+                brow += s.nrows;
+                soff += s.nrows * d.ldy;
+                coff += d.ldy;
+            }
         }
         S.ictl[2] = nseg;
-        S.ictl[1] = 0;
+        S.ictl[3] = 0;
     }
     for (int p = tid; p < npairs; p += nthr) {
         const PairDesc& d = P.pairs[p];
@@ -251,13 +261,14 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     }
     __syncthreads();
 
-    // One pass over every active segment.  UPDATE = false only sums.
+    // One pass over the active segments of group g.  UPDATE = false only sums.
     // Row partials go to rowpart, per-segment maxima to fred, column partials
     // to the pairs' accumulator `cur`.
-    auto pass = [&](auto update_tag, int cur) {
+    auto pass = [&](int g, auto update_tag, int cur) {
         constexpr bool UPDATE = decltype(update_tag)::value;
         for (int si = 0; si < nseg; ++si) {
             const Seg sg = S.seg[si];
+            if (sg.group != g) continue;
             const int pst = S.pstate[sg.pair];
             if (!(pst & 1) || (pst & 2)) continue;   // inactive or stopped pair
             const PairS pr = S.pair[sg.pair];
@@ -287,8 +298,8 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 __syncthreads();
                 if (tid < Q) {
                     float4 t = S.cred[tid];
-                    for (int g = 1; g < mp.RP; ++g) {
-                        const float4 v = S.cred[g * mp.QP + tid];
+                    for (int gg = 1; gg < mp.RP; ++gg) {
+                        const float4 v = S.cred[gg * mp.QP + tid];
                         t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
                     }
                     red_add_v4(acc + 4 * tid, t.x, t.y, t.z, t.w);
@@ -302,12 +313,13 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         }
     };
 
-    // End of a pass: row sums, FP64 totals and maxima per segment, grid
-    // barrier, then every pair's stop decision and the next offsets a_i.
-    auto finish = [&](int cur, int u, bool check_stop) -> bool {
+    // End of group g's pass: row sums, FP64 totals and maxima of its
+    // segments, then arrive at the group's barrier.
+    auto publish = [&](int g, int cur) {
         __syncthreads();
         for (int si = 0; si < nseg; ++si) {
             const Seg sg = S.seg[si];
+            if (sg.group != g) continue;
             const int pst = S.pstate[sg.pair];
             if (!(pst & 1) || (pst & 2)) continue;
             const int QP = ((S.pair[sg.pair].ldy >> 2) + 31) & ~31;
@@ -323,6 +335,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         if (warp == 0) {
             for (int si = 0; si < nseg; ++si) {
                 const Seg sg = S.seg[si];
+                if (sg.group != g) continue;
                 const int pst = S.pstate[sg.pair];
                 if (!(pst & 1) || (pst & 2)) continue;
                 double sp = 0.0;
@@ -337,11 +350,19 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 }
             }
         }
-        if (!grid_barrier(&W->bar, bar_base + G * (gen + 1), err, P.timeout_ns)) return false;
-        ++gen;
-        // c/N of every active segment for the next round
+        grid_arrive(&W->bar[g]);
+    };
+
+    // Wait for group g's barrier of pass `cur` (round u), then take every
+    // stop decision of the group's pairs (identical in every CTA), load c/N
+    // of its segments and turn the new totals into the next offsets a_i.
+    auto wait_post = [&](int g, int cur, int u, bool check_stop) -> bool {
+        const unsigned target = (g == 0 ? base0 : base1) + G * (gen[g] + 1u);
+        if (!grid_wait(&W->bar[g], target, err, P.timeout_ns)) return false;
+        ++gen[g];
         for (int si = 0; si < nseg; ++si) {
             const Seg sg = S.seg[si];
+            if (sg.group != g) continue;
             const int pst = S.pstate[sg.pair];
             if (!(pst & 1) || (pst & 2)) continue;
             const PairS pr = S.pair[sg.pair];
@@ -354,16 +375,16 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             }
         }
         if (warp == 0) {
-            // stop decisions of every pair of the wave (identical in every CTA)
+            const int p0 = g == 0 ? 0 : split, p1 = g == 0 ? split : npairs;
             int any = 0;
-            for (int p = lane; p < npairs; p += 32) {
+            for (int p = p0 + lane; p < p1; p += 32) {
                 int ps = S.pstate[p];
                 if ((ps & 1) && !(ps & 2)) {
                     PairS& pr = S.pair[p];
                     const double s = __ldcg(pr.sbuf + cur);
                     const float dd = __uint_as_float(__ldcg(pr.dbuf + cur));
                     pr.s = s;
-                    if (!isfinite(s)) S.ictl[1] = 1;
+                    if (!isfinite(s)) S.ictl[3] = 1;
                     if (check_stop && ((double)dd < P.tol_inner || u >= P.max_inner)) {
                         ps |= 2;
                         S.pstop[p] = u;
@@ -374,11 +395,11 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             }
             any = __any_sync(0xffffffffu, any);
             __syncwarp();
-            if (lane == 0) S.ictl[0] = any;
-            // offsets a_i = 1/N + s/N^2 - r_i/N of the band's rows
+            if (lane == 0) S.ictl[g] = any;
+            // offsets a_i = 1/N + s/N^2 - r_i/N of the group's band rows
             for (int si = 0; si < nseg; ++si) {
                 const Seg sg = S.seg[si];
-                if ((S.pstate[sg.pair] & 3) != 1) continue;
+                if (sg.group != g || (S.pstate[sg.pair] & 3) != 1) continue;
                 const PairS& pr = S.pair[sg.pair];
                 const double invN = 1.0 / (double)pr.N;
                 const double a_base = invN + pr.s * invN * invN;
@@ -390,9 +411,10 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         return true;
     };
 
-    // Zero the accumulator `which` of every active pair (distributed over CTAs).
-    auto clear_acc = [&](int which) {
-        for (int p = 0; p < npairs; ++p) {
+    // Zero accumulator `which` of group g's pairs (distributed over CTAs).
+    auto clear_acc = [&](int g, int which) {
+        const int p0 = g == 0 ? 0 : split, p1 = g == 0 ? split : npairs;
+        for (int p = p0; p < p1; ++p) {
             const PairS& pr = S.pair[p];
             const int Q = pr.ldy >> 2;
             float4* cb = reinterpret_cast<float4*>(pr.colbuf + (size_t)which * pr.ldy);
@@ -404,23 +426,49 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         }
     };
 
-    // ---- sums of the input, then the rounds
-    clear_acc(1);
-    pass(std::false_type{}, 0);
-    if (!finish(0, 0, false)) return;
-    if (S.ictl[1]) {
+    // ---- sums of the input of both groups
+    const bool has1 = split < npairs;
+    pass(0, std::false_type{}, 0);
+    publish(0, 0);
+    if (has1) {
+        pass(1, std::false_type{}, 0);
+        publish(1, 0);
+    }
+    if (!wait_post(0, 0, 0, false)) return;
+    if (has1 && !wait_post(1, 0, 0, false)) return;
+    if (S.ictl[3]) {
         if (tid == 0) atomicCAS(err, 0, FASTPFP_ERR_NONFINITE);
         return;
     }
+    bool act0 = S.ictl[0] != 0, act1 = has1 && S.ictl[1] != 0, pend1 = false;
+
+    // ---- the rounds, group 1 one half-step behind group 0
     int u = 0;
-    while (S.ictl[0]) {
+    while (act0 || act1 || pend1) {
         ++u;
-        const int cur = u % 3;
-        clear_acc((u + 1) % 3);
-        pass(std::true_type{}, cur);
-        if (!finish(cur, u, true)) return;
+        if (act0) {
+            clear_acc(0, (u + 1) % 3);
+            pass(0, std::true_type{}, u % 3);
+            publish(0, u % 3);
+        }
+        if (pend1) {
+            if (!wait_post(1, (u - 1) % 3, u - 1, true)) return;
+            act1 = S.ictl[1] != 0;
+            pend1 = false;
+        }
+        if (act1) {
+            clear_acc(1, (u + 1) % 3);
+            pass(1, std::true_type{}, u % 3);
+            publish(1, u % 3);
+            pend1 = true;
+        }
+        if (act0) {
+            if (!wait_post(0, u % 3, u, true)) return;
+            act0 = S.ictl[0] != 0;
+        }
     }
-    // ---- blend and normalise every active pair
+
+    // ---- blend and normalise every active pair (barriers on counter 0)
     const float alpha = P.alpha, beta = 1.0f - P.alpha;
     if (P.normalize) {
         for (int si = 0; si < nseg; ++si) {
@@ -453,8 +501,9 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 if (lane == 0) atomicMax(&P.pairs[sg.pair].ctrl->xmax_bits, float_to_ordered(bm));
             }
         }
-        if (!grid_barrier(&W->bar, bar_base + G * (gen + 1), err, P.timeout_ns)) return;
-        ++gen;
+        grid_arrive(&W->bar[0]);
+        if (!grid_wait(&W->bar[0], base0 + G * (gen[0] + 1u), err, P.timeout_ns)) return;
+        ++gen[0];
     }
     for (int si = 0; si < nseg; ++si) {
         const Seg sg = S.seg[si];
@@ -503,11 +552,15 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         dx = warp_max_d(dx);
         if (lane == 0 && dx > 0.0) atomicMax(&d.ctrl->dx_bits, (unsigned long long)__double_as_longlong(dx));
     }
-    if (!grid_barrier(&W->bar, bar_base + G * (gen + 1), err, P.timeout_ns)) return;
-    ++gen;
+    grid_arrive(&W->bar[0]);
+    if (!grid_wait(&W->bar[0], base0 + G * (gen[0] + 1u), err, P.timeout_ns)) return;
+    ++gen[0];
 
     // ---- per-pair loop control, accumulator clean-up
-    for (int b = 0; b < 3; ++b) clear_acc(b);
+    for (int b = 0; b < 3; ++b) {
+        clear_acc(0, b);
+        clear_acc(1, b);
+    }
     if (blockIdx.x == 0) {
         for (int p = tid; p < npairs; p += nthr) {
             if (!(S.pstate[p] & 1)) continue;
@@ -550,7 +603,8 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             int all = 1;
             for (int p = 0; p < npairs; ++p) all &= (P.pairs[p].ctrl->done != 0);
             W->all_done = all;
-            W->bar_base = bar_base + G * gen;
+            W->bar_base[0] = base0 + G * gen[0];
+            W->bar_base[1] = base1 + G * gen[1];
         }
     }
 }
@@ -560,7 +614,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
 size_t pdb_smem_bytes(const PdbLayout& L, int nthr) {
     size_t off = 0;
     auto take = [&](size_t bytes) { off = (off + bytes + 15) & ~size_t(15); };
-    take(24 * kMaxSeg);               // Seg is six ints
+    take(32 * kMaxSeg);               // Seg is eight ints
     take(40 * kMaxWavePairs);         // PairS: three pointers, a double, two ints
     take(4 * kMaxWavePairs);
     take(4 * kMaxWavePairs);
