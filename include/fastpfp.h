@@ -210,6 +210,47 @@ int fastpfp_project(fastpfp_t h, void* stream, float* Y, int N, double tol, int 
 int fastpfp_discretize(fastpfp_t h, void* stream, const float* X, int N, int m,
                        int32_t* row_of_col);
 
+/* ---- learned warm start ----------------------------------------------------
+ * The paper recommends the uniform start X = 1 1^T / (n n') and notes that
+ * the result depends on the initialisation (discussion after Algorithm 1).
+ * These calls build a learned start instead (not part of the paper):
+ *   features  F_i = [zscore(deg)_i, hist_i[0..15], zscore(B)_i[0..14]] (32 per
+ *             node): weighted degree, histogram of the node's nonzero
+ *             incident weights in 16 bins of [0, 1] (clamped) divided by their
+ *             count, the first 15 attributes; z-scores over the graph's nodes
+ *   MLP       H = relu(F W1 + b1) (128), E = H W2 + b2 (64), one set of weights
+ *             for both graphs
+ *   start     S = E_big E_small^T / 8; X0 = sinkhorn_iters alternations of
+ *             row and column normalisation of exp(S - max S)
+ * params is a device array of FASTPFP_MLP_NPARAMS floats: W1 (32 x 128,
+ * row-major), b1 (128), W2 (128 x 64), b2 (64). */
+#define FASTPFP_MLP_NPARAMS (32 * 128 + 128 + 128 * 64 + 64)
+
+/* X0_out (device, n_a x n_b, caller orientation) = the learned start of the
+ * pair; use it as fastpfp_match's X0.  B/B2 may be NULL when k == 0.  Device
+ * pointers; asynchronous on `stream`.  Errors: ERR_ARG, ERR_SIZE, ERR_CUDA. */
+int fastpfp_warmstart(fastpfp_t h, void* stream, const float* A, int n_a, const float* A2, int n_b,
+                      const float* B, const float* B2, int k, const float* params, int sinkhorn_iters,
+                      float* X0_out);
+
+/* One training step on a pair whose matching `perm` (device, n_a entries,
+ * as fastpfp_match returns it; every node of the smaller graph matched) is
+ * the target.  Loss, with t(j) the row matched to column j in canonical
+ * orientation and m the smaller graph's size:
+ *   L = -(1/m) sum_j [S(t(j), j) - logsumexp_i S(i, j)]
+ *       -(1/m) sum_j [S(t(j), j) - logsumexp_j' S(t(j), j')]
+ * The gradient of L w.r.t. params is computed by hand-written backward
+ * kernels; when step >= 1 an Adam update (beta 0.9 / 0.999, eps 1e-8, bias
+ * correction for `step`) with learning rate lr is applied to params using
+ * the device moments adam_m / adam_v (FASTPFP_MLP_NPARAMS floats each, start
+ * at zero).  step == 0 only evaluates.  *loss_out (host, nullable; the call
+ * then synchronises) receives L before the update; grad_out (device,
+ * nullable) the gradient.  Errors: ERR_ARG, ERR_SIZE, ERR_CUDA. */
+int fastpfp_warmstart_train_step(fastpfp_t h, void* stream, const float* A, int n_a, const float* A2,
+                                 int n_b, const float* B, const float* B2, int k, const int32_t* perm,
+                                 float* params, float* adam_m, float* adam_v, int step, float lr,
+                                 double* loss_out, float* grad_out);
+
 /* ---- entry point for callers that cannot allocate -------------------------
  * The paper has no counterpart to this call; it exists for callers that are
  * not allowed to call cudaMalloc -- for example code running inside a host

@@ -80,6 +80,15 @@ struct fastpfp_s {
 
     cudaEvent_t ev[kProfEvents] = {};
     cudaEvent_t chunk_ev[2] = {};
+    // learned warm start: features, activations, embeddings and gradients of
+    // both graphs (big = canonical rows, small = columns)
+    struct {
+        float *Fb, *Fs, *Hb, *Hs, *Eb, *Es, *Eb8, *Es8, *EsT, *dEb, *dEs, *dH, *grad, *scalar;
+        float *lse_c, *lse_r;
+        float2* part;
+        int32_t *t, *tinv;
+        double* loss;
+    } ws{};
 };
 
 namespace {
@@ -644,6 +653,13 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     const size_t osA = take(n * n * 4), osA2 = take(n * n * 4), osB = take(n * kMaxK * 4),
                  osB2 = take(n * kMaxK * 4), osX0 = take(n * n * 4), osXo = take(n * n * 4),
                  osp = take(n * 4);
+    const size_t nch = (n + 63) / 64;
+    const size_t wFb = take(n * kMlpIn * 4), wFs = take(n * kMlpIn * 4), wHb = take(n * kMlpHidden * 4),
+                 wHs = take(n * kMlpHidden * 4), wEb = take(n * kMlpOut * 4), wEs = take(n * kMlpOut * 4),
+                 wEb8 = take(n * kMlpOut * 4), wEs8 = take(n * kMlpOut * 4), wEsT = take(kMlpOut * ld * 4),
+                 wdEb = take(n * kMlpOut * 4), wdEs = take(n * kMlpOut * 4), wdH = take(n * kMlpHidden * 4),
+                 wgrad = take(kMlpParams * 4), wscal = take(16), wlc = take(n * 4), wlr = take(n * 4),
+                 wpart = take(nch * n * 8), wt = take(n * 4), wtinv = take(n * 4), wloss = take(16);
     h->pool_bytes = off;
     auto fail = [&](int code) {
         for (int e = 0; e < kProfEvents; ++e)
@@ -696,6 +712,26 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     h->sX0 = (float*)(b + osX0);
     h->sXout = (float*)(b + osXo);
     h->sperm = (int32_t*)(b + osp);
+    h->ws.Fb = (float*)(b + wFb);
+    h->ws.Fs = (float*)(b + wFs);
+    h->ws.Hb = (float*)(b + wHb);
+    h->ws.Hs = (float*)(b + wHs);
+    h->ws.Eb = (float*)(b + wEb);
+    h->ws.Es = (float*)(b + wEs);
+    h->ws.Eb8 = (float*)(b + wEb8);
+    h->ws.Es8 = (float*)(b + wEs8);
+    h->ws.EsT = (float*)(b + wEsT);
+    h->ws.dEb = (float*)(b + wdEb);
+    h->ws.dEs = (float*)(b + wdEs);
+    h->ws.dH = (float*)(b + wdH);
+    h->ws.grad = (float*)(b + wgrad);
+    h->ws.scalar = (float*)(b + wscal);
+    h->ws.lse_c = (float*)(b + wlc);
+    h->ws.lse_r = (float*)(b + wlr);
+    h->ws.part = (float2*)(b + wpart);
+    h->ws.t = (int32_t*)(b + wt);
+    h->ws.tinv = (int32_t*)(b + wtinv);
+    h->ws.loss = (double*)(b + wloss);
     for (int e = 0; e < kProfEvents; ++e)
         if (cudaEventCreate(&h->ev[e]) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
     for (int e = 0; e < 2; ++e)
@@ -952,6 +988,99 @@ int fastpfp_discretize(fastpfp_t h, void* stream, const float* X, int N, int m,
     FP_CUDA(cudaMemsetAsync(sl.ctrl, 0, kCtrlHeader, s));
     FP_CUDA(discretize(X, N, m, m, sl.disc, sl.ctrl, 2000ll * 1000000ll, h->num_sms, s));
     FP_CUDA(cudaMemcpyAsync(row_of_col, sl.disc.col_match, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
+    return FASTPFP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Features, MLP and S = E_big E_small^T / 8 of a canonical pair into slot 0's
+// Y (leading dimension round4(m)); keeps the activations for the backward.
+int ws_forward(fastpfp_t h, cudaStream_t s, const Problem& q, int kk, const float* params) {
+    const Slot& sl = h->slots[0];
+    const int N = q.N, m = q.m, ldS = round4(m);
+    auto& w = h->ws;
+    FP_CUDA(ws_features(q.A, N, kk ? q.B : nullptr, kk, w.Fb, s));
+    FP_CUDA(ws_features(q.A2, m, kk ? q.B2 : nullptr, kk, w.Fs, s));
+    FP_CUDA(ws_mlp_forward(w.Fb, N, params, w.Hb, w.Eb, 1.0f, s));
+    FP_CUDA(ws_mlp_forward(w.Fs, m, params, w.Hs, w.Es, 1.0f, s));
+    // E_big / 8 (exact) so that the product is S; E_small / 8 for dE_big
+    FP_CUDA(cudaMemcpyAsync(w.Eb8, w.Eb, (size_t)N * kMlpOut * 4, cudaMemcpyDeviceToDevice, s));
+    FP_CUDA(ws_scale(w.Eb8, (size_t)N * kMlpOut, 0.125f, s));
+    FP_CUDA(cudaMemcpyAsync(w.Es8, w.Es, (size_t)m * kMlpOut * 4, cudaMemcpyDeviceToDevice, s));
+    FP_CUDA(ws_scale(w.Es8, (size_t)m * kMlpOut, 0.125f, s));
+    FP_CUDA(ws_transpose(w.Es, m, kMlpOut, kMlpOut, w.EsT, ldS, s));
+    GemmF32Args g{w.Eb8, kMlpOut, w.EsT, ldS, sl.Y, ldS, nullptr, 0, 0.f, N, m, kMlpOut, nullptr};
+    FP_CUDA(gemm_f32(g, s));
+    return FASTPFP_OK;
+}
+
+int ws_check(fastpfp_t h, const float* A, int n_a, const float* A2, int n_b, const float* B, const float* B2,
+             int k, const float* params) {
+    if (!h || !A || !A2 || !params || n_a < 1 || n_b < 1 || k < 0) return FASTPFP_ERR_ARG;
+    if (k > 0 && (!B || !B2)) return FASTPFP_ERR_ARG;
+    if (n_a > h->max_n || n_b > h->max_n) return FASTPFP_ERR_SIZE;
+    return FASTPFP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fastpfp_warmstart(fastpfp_t h, void* stream, const float* A, int n_a, const float* A2, int n_b,
+                      const float* B, const float* B2, int k, const float* params, int sinkhorn_iters,
+                      float* X0_out) {
+    int rc = ws_check(h, A, n_a, A2, n_b, B, B2, k, params);
+    if (rc != FASTPFP_OK) return rc;
+    if (!X0_out || sinkhorn_iters < 0) return FASTPFP_ERR_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int kk = k < 15 ? k : 15;
+    const Problem q = canonical(A, n_a, A2, n_b, B, B2, kk, 1.0f, nullptr, nullptr, X0_out);
+    rc = ws_forward(h, s, q, kk, params);
+    if (rc != FASTPFP_OK) return rc;
+    const Slot& sl = h->slots[0];
+    const int ldS = round4(q.m);
+    FP_CUDA(ws_sinkhorn(sl.Y, q.N, q.m, ldS, sinkhorn_iters, reinterpret_cast<float*>(h->ws.part),
+                        h->ws.scalar, s));
+    FP_CUDA(write_outputs(nullptr, q.N, q.m, q.transposed, nullptr, sl.Y, ldS, X0_out, s));
+    return FASTPFP_OK;
+}
+
+int fastpfp_warmstart_train_step(fastpfp_t h, void* stream, const float* A, int n_a, const float* A2,
+                                 int n_b, const float* B, const float* B2, int k, const int32_t* perm,
+                                 float* params, float* adam_m, float* adam_v, int step, float lr,
+                                 double* loss_out, float* grad_out) {
+    int rc = ws_check(h, A, n_a, A2, n_b, B, B2, k, params);
+    if (rc != FASTPFP_OK) return rc;
+    if (!perm || step < 0 || (step > 0 && (!adam_m || !adam_v)) || !(lr >= 0.f)) return FASTPFP_ERR_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int kk = k < 15 ? k : 15;
+    const Problem q = canonical(A, n_a, A2, n_b, B, B2, kk, 1.0f, nullptr, nullptr, nullptr);
+    const int N = q.N, m = q.m, ldS = round4(m);
+    auto& w = h->ws;
+    const Slot& sl = h->slots[0];
+    rc = ws_forward(h, s, q, kk, params);
+    if (rc != FASTPFP_OK) return rc;
+    FP_CUDA(ws_targets(perm, n_a, q.transposed, N, m, w.t, w.tinv, s));
+    // dL/dS into slot 0's T (N x ldS), its transpose into slot 0's K (m x round4(N))
+    FP_CUDA(ws_loss_grad_S(sl.Y, N, m, ldS, w.t, w.tinv, w.lse_c, w.lse_r, w.part, sl.T, ldS, w.loss, s));
+    FP_CUDA(ws_transpose(sl.T, N, m, ldS, sl.K, round4(N), s));
+    GemmF32Args gb{sl.T, ldS, w.Es8, kMlpOut, w.dEb, kMlpOut, nullptr, 0, 0.f, N, kMlpOut, m, nullptr};
+    GemmF32Args gs{sl.K, round4(N), w.Eb8, kMlpOut, w.dEs, kMlpOut, nullptr, 0, 0.f, m, kMlpOut, N, nullptr};
+    FP_CUDA(gemm_f32(gb, s));   // dE_big = dS E_small / 8
+    FP_CUDA(gemm_f32(gs, s));   // dE_small = dS^T E_big / 8
+    FP_CUDA(ws_mlp_backward(w.Fb, w.Hb, w.dEb, N, params, w.dH, w.grad, 0, s));
+    FP_CUDA(ws_mlp_backward(w.Fs, w.Hs, w.dEs, m, params, w.dH, w.grad, 1, s));
+    if (grad_out)
+        FP_CUDA(cudaMemcpyAsync(grad_out, w.grad, kMlpParams * 4, cudaMemcpyDeviceToDevice, s));
+    if (step > 0) FP_CUDA(ws_adam(params, adam_m, adam_v, w.grad, step, lr, s));
+    if (loss_out) {
+        FP_CUDA(cudaMemcpyAsync(loss_out, w.loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (cudaStreamSynchronize(s) != cudaSuccess) return FASTPFP_ERR_CUDA;
+    }
     return FASTPFP_OK;
 }
 

@@ -190,6 +190,32 @@ cudaError_t write_outputs(const int32_t* row_of_col, int N, int m, int transpose
 cudaError_t objective(const float* A, int N, const float* A2, int m, const float* K, int ldk,
                       float lambda, const int32_t* row_of_col, Ctrl* ctrl, cudaStream_t s);
 
+// ------------------------------------------------------- learned warm start
+constexpr int kMlpIn = 32, kMlpHidden = 128, kMlpOut = 64;
+constexpr int kMlpParams = kMlpIn * kMlpHidden + kMlpHidden + kMlpHidden * kMlpOut + kMlpOut;
+
+cudaError_t ws_features(const float* W, int n, const float* B, int k, float* F, cudaStream_t s);
+// E = (relu(F W1 + b1) W2 + b2) * escale; H keeps the hidden activations.
+cudaError_t ws_mlp_forward(const float* F, int n, const float* params, float* H, float* E, float escale,
+                           cudaStream_t s);
+cudaError_t ws_transpose(const float* src, int r, int c, int lds, float* dst, int ldd, cudaStream_t s);
+cudaError_t ws_scale(float* x, size_t n, float v, cudaStream_t s);
+// In place: S <- exp(S - max S), then `iters` row and column normalisations.
+cudaError_t ws_sinkhorn(float* S, int r, int c, int ld, int iters, float* part, float* scalar,
+                        cudaStream_t s);
+// Loss of Section "learned warm start" and dL/dS (ld ldd); part holds
+// ceil(r / 64) x c float2 partials.
+cudaError_t ws_loss_grad_S(const float* S, int r, int c, int ld, const int32_t* t, const int32_t* tinv,
+                           float* lse_c, float* lse_r, float2* part, float* dS, int ldd, double* loss,
+                           cudaStream_t s);
+// Parameter gradient of one graph's MLP pass, written or accumulated into grad.
+cudaError_t ws_mlp_backward(const float* F, const float* H, const float* dE, int n, const float* params,
+                            float* dH, float* grad, int accumulate, cudaStream_t s);
+cudaError_t ws_adam(float* p, float* m, float* v, const float* g, int step, float lr, cudaStream_t s);
+// t[j] = canonical row matched to column j, tinv[i] = column of row i or -1.
+cudaError_t ws_targets(const int32_t* perm, int n_a, int transposed, int N, int m, int32_t* t,
+                       int32_t* tinv, cudaStream_t s);
+
 // ------------------------------------------------------- discretisation
 struct DiscBuffers {
     int32_t* row_match;           // N

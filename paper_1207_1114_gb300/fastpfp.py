@@ -29,7 +29,9 @@ FP32, BF16 = 0, 1
 EXPORTS = ("fastpfp_default_params", "fastpfp_create", "fastpfp_destroy", "fastpfp_match",
            "fastpfp_match_host", "fastpfp_match_batched", "fastpfp_last_trace",
            "fastpfp_gradient", "fastpfp_affinity", "fastpfp_project", "fastpfp_discretize",
-           "fastpfp_project_noalloc", "fastpfp_error_string")
+           "fastpfp_project_noalloc", "fastpfp_warmstart", "fastpfp_warmstart_train_step",
+           "fastpfp_error_string")
+MLP_NPARAMS = 32 * 128 + 128 + 128 * 64 + 64
 
 
 class fastpfp_params(C.Structure):
@@ -90,6 +92,9 @@ def lib():
     l.fastpfp_discretize.argtypes = [P, V, P, I, I, P]
     l.fastpfp_project_noalloc.argtypes = [V, P, I, C.c_double, I, C.POINTER(C.c_int),
                                           C.POINTER(C.c_double)]
+    l.fastpfp_warmstart.argtypes = [P, V, P, I, P, I, P, P, I, P, I, P]
+    l.fastpfp_warmstart_train_step.argtypes = [P, V, P, I, P, I, P, P, I, P, P, P, P, I, C.c_float,
+                                               C.POINTER(C.c_double), P]
     l.fastpfp_error_string.argtypes = [I]
     l.fastpfp_error_string.restype = C.c_char_p
     for name in EXPORTS:
@@ -278,6 +283,32 @@ class Solver:
         _check(lib().fastpfp_project(self._h, _stream(stream), _ptr(Y), Y.shape[0], float(tol),
                                      int(max_iter), C.byref(it), C.byref(d)), "fastpfp_project")
         return it.value, d.value
+
+    # ---------------------------------------------------- learned start
+    def warmstart(self, A, A2, B, B2, params, iters=20, stream=None):
+        """fastpfp_warmstart: the learned X0 (n_a x n_b CUDA tensor)."""
+        import torch
+        n_a, n_b = A.shape[0], A2.shape[0]
+        k = 0 if B is None else B.shape[1]
+        X0 = torch.empty((n_a, n_b), dtype=torch.float32, device=A.device)
+        _check(lib().fastpfp_warmstart(self._h, _stream(stream), _ptr(A), n_a, _ptr(A2), n_b,
+                                       _ptr(B) if k else None, _ptr(B2) if k else None, k,
+                                       _ptr(params), int(iters), _ptr(X0)), "fastpfp_warmstart")
+        return X0
+
+    def train_step(self, A, A2, B, B2, perm, params, adam_m=None, adam_v=None, step=0, lr=0.0,
+                   want_grad=False, stream=None):
+        """fastpfp_warmstart_train_step; returns (loss, grad or None)."""
+        import torch
+        n_a, n_b = A.shape[0], A2.shape[0]
+        k = 0 if B is None else B.shape[1]
+        grad = torch.empty(MLP_NPARAMS, dtype=torch.float32, device=A.device) if want_grad else None
+        loss = C.c_double(0.0)
+        _check(lib().fastpfp_warmstart_train_step(
+            self._h, _stream(stream), _ptr(A), n_a, _ptr(A2), n_b, _ptr(B) if k else None,
+            _ptr(B2) if k else None, k, _ptr(perm), _ptr(params), _ptr(adam_m), _ptr(adam_v),
+            int(step), float(lr), C.byref(loss), _ptr(grad)), "fastpfp_warmstart_train_step")
+        return loss.value, grad
 
     def discretize(self, X, stream=None):
         import torch
