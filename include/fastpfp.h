@@ -167,6 +167,12 @@ int fastpfp_match_host(fastpfp_t h, void* stream,
 int fastpfp_match_batched(fastpfp_t h, void* stream, int count, const fastpfp_pair* pairs,
                           const fastpfp_params* p, fastpfp_stats* st);
 
+/* As fastpfp_match_batched, but every pointer of every descriptor is HOST
+ * memory: each wave's inputs are copied into the handle's device staging,
+ * solved, and perm_out (and X_out) copied back.  Synchronises `stream`. */
+int fastpfp_match_batched_host(fastpfp_t h, void* stream, int count, const fastpfp_pair* pairs,
+                               const fastpfp_params* p, fastpfp_stats* st);
+
 /* Copies the per-outer-iteration trace of a pair of the last call on this
  * handle: inner_counts[t] = P1/P2 rounds of outer iteration t, deltas[t] =
  * max|X(t+1) - X(t)|.  `pair` is 0 after fastpfp_match / _host, and after

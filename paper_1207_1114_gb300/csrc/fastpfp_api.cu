@@ -55,6 +55,9 @@ struct Slot {
     unsigned* dbuf;
     Ctrl* ctrl;
     DiscBuffers disc;
+    // device staging of host-memory inputs and outputs (the *_host calls)
+    float *sA, *sA2, *sB, *sB2, *sX0, *sXout;
+    int32_t* sperm;
 };
 
 }  // namespace
@@ -70,10 +73,7 @@ struct fastpfp_s {
     WaveCtrl* d_wave = nullptr;
     PairDesc* h_pairs = nullptr;
     int* h_band = nullptr;
-    int* h_done = nullptr;       // pinned, 2 entries: stop flags read one chunk behind
-    // staging for fastpfp_match_host
-    float *sA = nullptr, *sA2 = nullptr, *sB = nullptr, *sB2 = nullptr, *sX0 = nullptr, *sXout = nullptr;
-    int32_t* sperm = nullptr;
+    int* h_done = nullptr;       // pinned, 2 x 4 words: stop flags read one chunk behind
     Ctrl* host_ctrl = nullptr;   // pinned, max_batch control-block headers
     int last_first = 0;          // pairs [last_first, last_first + last_count) of the last call
     int last_count = 0;          // still hold their traces in slots 0, 1, ...
@@ -578,6 +578,9 @@ int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, co
     return nl;
 }
 
+int solve_batch(fastpfp_t h, cudaStream_t s, int count, const fastpfp_pair* pairs,
+                const fastpfp_params* p, fastpfp_stats* st, bool host);
+
 }  // namespace
 
 extern "C" {
@@ -638,7 +641,10 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     const size_t b16mat = align256(n * (size_t)round8(max_n) * sizeof(__nv_bfloat16));
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
-    struct SlotOff { size_t Y, X, T, K, A16, A216, Xt16, T16, col, s, d, ctrl, rm, cm, rb, cb; };
+    struct SlotOff {
+        size_t Y, X, T, K, A16, A216, Xt16, T16, col, s, d, ctrl, rm, cm, rb, cb, sA, sA2, sB, sB2, sX0,
+            sXo, sp;
+    };
     std::vector<SlotOff> so(h->nslots);
     for (auto& o : so) {
         o.Y = take(f32mat); o.X = take(f32mat); o.T = take(f32mat); o.K = take(f32mat);
@@ -646,13 +652,12 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
         o.col = take(3 * ld * sizeof(float)); o.s = take(3 * sizeof(double));
         o.d = take(3 * sizeof(unsigned)); o.ctrl = take(sizeof(Ctrl));
         o.rm = take(n * 4); o.cm = take(n * 4); o.rb = take(n * 8); o.cb = take(2 * n * 8);
+        o.sA = take(n * n * 4); o.sA2 = take(n * n * 4); o.sB = take(n * kMaxK * 4);
+        o.sB2 = take(n * kMaxK * 4); o.sX0 = take(n * n * 4); o.sXo = take(n * n * 4); o.sp = take(n * 4);
     }
     const size_t opairs = take(sizeof(PairDesc) * kMaxWavePairs);
     const size_t oband = take(sizeof(int) * 2 * (h->num_sms + 1));
     const size_t owave = take(sizeof(WaveCtrl));
-    const size_t osA = take(n * n * 4), osA2 = take(n * n * 4), osB = take(n * kMaxK * 4),
-                 osB2 = take(n * kMaxK * 4), osX0 = take(n * n * 4), osXo = take(n * n * 4),
-                 osp = take(n * 4);
     const size_t nch = (n + 63) / 64;
     const size_t wFb = take(n * kMlpIn * 4), wFs = take(n * kMlpIn * 4), wHb = take(n * kMlpHidden * 4),
                  wHs = take(n * kMlpHidden * 4), wEb = take(n * kMlpOut * 4), wEs = take(n * kMlpOut * 4),
@@ -701,17 +706,17 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
         sl.disc.col_match = (int32_t*)(b + o.cm);
         sl.disc.row_best = (unsigned long long*)(b + o.rb);
         sl.disc.col_best = (unsigned long long*)(b + o.cb);
+        sl.sA = (float*)(b + o.sA);
+        sl.sA2 = (float*)(b + o.sA2);
+        sl.sB = (float*)(b + o.sB);
+        sl.sB2 = (float*)(b + o.sB2);
+        sl.sX0 = (float*)(b + o.sX0);
+        sl.sXout = (float*)(b + o.sXo);
+        sl.sperm = (int32_t*)(b + o.sp);
     }
     h->d_pairs = (PairDesc*)(b + opairs);
     h->d_band = (int*)(b + oband);
     h->d_wave = (WaveCtrl*)(b + owave);
-    h->sA = (float*)(b + osA);
-    h->sA2 = (float*)(b + osA2);
-    h->sB = (float*)(b + osB);
-    h->sB2 = (float*)(b + osB2);
-    h->sX0 = (float*)(b + osX0);
-    h->sXout = (float*)(b + osXo);
-    h->sperm = (int32_t*)(b + osp);
     h->ws.Fb = (float*)(b + wFb);
     h->ws.Fs = (float*)(b + wFs);
     h->ws.Hb = (float*)(b + wHb);
@@ -785,32 +790,10 @@ int fastpfp_match_host(fastpfp_t h, void* stream, const float* A, int n_a, const
                        const float* X0, int32_t* perm_out, float* X_out, fastpfp_stats* st) {
     int rc = check_pair(h, A, n_a, A2, n_b, B, B2, k, p, perm_out);
     if (rc != FASTPFP_OK) return rc;
-    const int kk = (k > 0 && p->lambda != 0.f) ? k : 0;
     if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    FP_CUDA(cudaMemcpyAsync(h->sA, A, (size_t)n_a * n_a * 4, cudaMemcpyHostToDevice, s));
-    FP_CUDA(cudaMemcpyAsync(h->sA2, A2, (size_t)n_b * n_b * 4, cudaMemcpyHostToDevice, s));
-    if (kk) {
-        FP_CUDA(cudaMemcpyAsync(h->sB, B, (size_t)n_a * kk * 4, cudaMemcpyHostToDevice, s));
-        FP_CUDA(cudaMemcpyAsync(h->sB2, B2, (size_t)n_b * kk * 4, cudaMemcpyHostToDevice, s));
-    }
-    if (X0) FP_CUDA(cudaMemcpyAsync(h->sX0, X0, (size_t)n_a * n_b * 4, cudaMemcpyHostToDevice, s));
-    const Problem q = canonical(h->sA, n_a, h->sA2, n_b, kk ? h->sB : nullptr, kk ? h->sB2 : nullptr,
-                                kk, p->lambda, X0 ? h->sX0 : nullptr, h->sperm,
-                                X_out ? h->sXout : nullptr);
-    const int nl = enqueue_single(h, s, h->slots[0], q, p, &h->host_ctrl[0]);
-    if (nl < 0) {
-        cudaStreamSynchronize(s);
-        return nl;
-    }
-    FP_CUDA(cudaMemcpyAsync(perm_out, h->sperm, (size_t)n_a * 4, cudaMemcpyDeviceToHost, s));
-    if (X_out)
-        FP_CUDA(cudaMemcpyAsync(X_out, h->sXout, (size_t)n_a * n_b * 4, cudaMemcpyDeviceToHost, s));
-    if (cudaStreamSynchronize(s) != cudaSuccess) return FASTPFP_ERR_CUDA;
-    h->last_first = 0;
-    h->last_count = 1;
-    rc = fill_stats(h->host_ctrl[0], q.transposed, nl, st);
-    if (p->profile) read_profile(h, h->host_ctrl[0].outer, 1.0f, st);
+    const fastpfp_pair pr{A, A2, B, B2, n_a, n_b, k, X0, perm_out, X_out};
+    rc = solve_batch(h, s, 1, &pr, p, st, true);
     return rc;
 }
 
@@ -824,7 +807,31 @@ int fastpfp_match_batched(fastpfp_t h, void* stream, int count, const fastpfp_pa
         if (rc != FASTPFP_OK) return rc;
     }
     if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
-    cudaStream_t s = (cudaStream_t)stream;
+    return solve_batch(h, (cudaStream_t)stream, count, pairs, p, st, false);
+}
+
+int fastpfp_match_batched_host(fastpfp_t h, void* stream, int count, const fastpfp_pair* pairs,
+                               const fastpfp_params* p, fastpfp_stats* st) {
+    if (!h || count < 0 || (count > 0 && !pairs)) return FASTPFP_ERR_ARG;
+    if (count > h->max_batch) return FASTPFP_ERR_ARG;
+    for (int b = 0; b < count; ++b) {
+        const fastpfp_pair& q = pairs[b];
+        int rc = check_pair(h, q.A, q.n_a, q.A2, q.n_b, q.B, q.B2, q.k, p, q.perm_out);
+        if (rc != FASTPFP_OK) return rc;
+    }
+    if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
+    return solve_batch(h, (cudaStream_t)stream, count, pairs, p, st, true);
+}
+
+}  // extern "C"
+
+namespace {
+
+// The batch driver of fastpfp_match_batched (device memory) and of the
+// *_host calls (host memory: each wave's inputs are staged into its slots
+// and the outputs copied back before the next wave).
+int solve_batch(fastpfp_t h, cudaStream_t s, int count, const fastpfp_pair* pairs,
+                const fastpfp_params* p, fastpfp_stats* st, bool host) {
     std::vector<Problem> qs(count);
     for (int b = 0; b < count; ++b) {
         const fastpfp_pair& x = pairs[b];
@@ -835,13 +842,42 @@ int fastpfp_match_batched(fastpfp_t h, void* stream, int count, const fastpfp_pa
     int b = 0;
     while (b < count) {
         Wave w;
-        const bool batched = plan_wave(qs, b, h->nslots, h->num_sms, &w);
+        // a lone pair takes the single-pair kernel, as fastpfp_match does
+        const bool batched = count > 1 && plan_wave(qs, b, h->nslots, h->num_sms, &w);
         const int cnt = batched ? w.count : 1;
+        if (host) {
+            for (int i = 0; i < cnt; ++i) {
+                const fastpfp_pair& x = pairs[b + i];
+                const Slot& sl = h->slots[i];
+                const int kk = (x.k > 0 && p->lambda != 0.f) ? x.k : 0;
+                FP_CUDA(cudaMemcpyAsync(sl.sA, x.A, (size_t)x.n_a * x.n_a * 4, cudaMemcpyHostToDevice, s));
+                FP_CUDA(cudaMemcpyAsync(sl.sA2, x.A2, (size_t)x.n_b * x.n_b * 4, cudaMemcpyHostToDevice, s));
+                if (kk) {
+                    FP_CUDA(cudaMemcpyAsync(sl.sB, x.B, (size_t)x.n_a * kk * 4, cudaMemcpyHostToDevice, s));
+                    FP_CUDA(cudaMemcpyAsync(sl.sB2, x.B2, (size_t)x.n_b * kk * 4, cudaMemcpyHostToDevice, s));
+                }
+                if (x.X0)
+                    FP_CUDA(cudaMemcpyAsync(sl.sX0, x.X0, (size_t)x.n_a * x.n_b * 4, cudaMemcpyHostToDevice, s));
+                qs[b + i] = canonical(sl.sA, x.n_a, sl.sA2, x.n_b, kk ? sl.sB : nullptr, kk ? sl.sB2 : nullptr,
+                                      kk, p->lambda, x.X0 ? sl.sX0 : nullptr, sl.sperm,
+                                      x.X_out ? sl.sXout : nullptr);
+            }
+        }
         const int nl = batched ? enqueue_wave(h, s, qs, w, p, &h->host_ctrl[b])
                                : enqueue_single(h, s, h->slots[0], qs[b], p, &h->host_ctrl[b]);
         if (nl < 0) {
             cudaStreamSynchronize(s);
             return nl;
+        }
+        if (host) {
+            for (int i = 0; i < cnt; ++i) {
+                const fastpfp_pair& x = pairs[b + i];
+                const Slot& sl = h->slots[i];
+                FP_CUDA(cudaMemcpyAsync(x.perm_out, sl.sperm, (size_t)x.n_a * 4, cudaMemcpyDeviceToHost, s));
+                if (x.X_out)
+                    FP_CUDA(cudaMemcpyAsync(x.X_out, sl.sXout, (size_t)x.n_a * x.n_b * 4,
+                                            cudaMemcpyDeviceToHost, s));
+            }
         }
         // the wave tables and the profiling events are reused by the next wave
         if (cudaStreamSynchronize(s) != cudaSuccess) return FASTPFP_ERR_CUDA;
@@ -870,6 +906,10 @@ int fastpfp_match_batched(fastpfp_t h, void* stream, int count, const fastpfp_pa
     }
     return worst;
 }
+
+}  // namespace
+
+extern "C" {
 
 int fastpfp_last_trace(fastpfp_t h, int pair, int* inner_counts, double* deltas, int cap) {
     if (!h || cap < 0) return FASTPFP_ERR_ARG;

@@ -27,7 +27,8 @@ FP32, BF16 = 0, 1
 
 # Every symbol include/fastpfp.h declares.
 EXPORTS = ("fastpfp_default_params", "fastpfp_create", "fastpfp_destroy", "fastpfp_match",
-           "fastpfp_match_host", "fastpfp_match_batched", "fastpfp_last_trace",
+           "fastpfp_match_host", "fastpfp_match_batched", "fastpfp_match_batched_host",
+           "fastpfp_last_trace",
            "fastpfp_gradient", "fastpfp_affinity", "fastpfp_project", "fastpfp_discretize",
            "fastpfp_project_noalloc", "fastpfp_warmstart", "fastpfp_warmstart_train_step",
            "fastpfp_error_string")
@@ -82,6 +83,8 @@ def lib():
     sig = [P, V, P, I, P, I, P, P, I, C.POINTER(fastpfp_params), P, P, P, C.POINTER(fastpfp_stats)]
     l.fastpfp_match.argtypes = sig
     l.fastpfp_match_host.argtypes = sig
+    l.fastpfp_match_batched_host.argtypes = [P, V, I, C.POINTER(fastpfp_pair),
+                                             C.POINTER(fastpfp_params), C.POINTER(fastpfp_stats)]
     l.fastpfp_match_batched.argtypes = [P, V, I, C.POINTER(fastpfp_pair), C.POINTER(fastpfp_params),
                                         C.POINTER(fastpfp_stats)]
     l.fastpfp_last_trace.argtypes = [P, I, P, P, I]
@@ -243,6 +246,41 @@ class Solver:
         sts = (fastpfp_stats * max(1, n))()
         rc = lib().fastpfp_match_batched(self._h, _stream(stream), n, arr, C.byref(p), sts)
         _check(rc, "fastpfp_match_batched")
+        return [MatchResult(perm, X, sts[b]) for b, (perm, X) in enumerate(outs)]
+
+    def match_batched_host(self, pairs, params=None, want_X=False, stream=None):
+        """fastpfp_match_batched_host: pairs of host float32 arrays (numpy, or
+        pinned torch CPU tensors passed without a copy); returns host results."""
+        p = params if params is not None else default_params()
+        n = len(pairs)
+        arr = (fastpfp_pair * max(1, n))()
+        keep, outs = [], []
+
+        def host(a):
+            if a is None or (hasattr(a, "data_ptr") and not a.is_cuda and a.is_contiguous()
+                             and str(a.dtype) == "torch.float32"):
+                return a
+            return np.ascontiguousarray(a, dtype=np.float32)
+
+        def addr(a):
+            if a is None:
+                return None
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+        for b, (A, A2, B, B2) in enumerate(pairs):
+            A, A2, B, B2 = host(A), host(A2), host(B), host(B2)
+            n_a, n_b = A.shape[0], A2.shape[0]
+            k = 0 if B is None else B.shape[1]
+            perm = np.empty(n_a, dtype=np.int32)
+            X = np.empty((n_a, n_b), dtype=np.float32) if want_X else None
+            arr[b] = fastpfp_pair(addr(A), addr(A2), addr(B) if k else None, addr(B2) if k else None,
+                                  n_a, n_b, k, None, perm.ctypes.data,
+                                  X.ctypes.data if X is not None else None)
+            keep.append((A, A2, B, B2))
+            outs.append((perm, X))
+        sts = (fastpfp_stats * max(1, n))()
+        rc = lib().fastpfp_match_batched_host(self._h, _stream(stream), n, arr, C.byref(p), sts)
+        _check(rc, "fastpfp_match_batched_host")
         return [MatchResult(perm, X, sts[b]) for b, (perm, X) in enumerate(outs)]
 
     def last_trace(self, pair: int = 0, cap: int = 4096):

@@ -227,6 +227,20 @@ def test_host_entry_point_equals_device_entry_point(solver):
     assert d.stats.outer_iters == h.stats.outer_iters
 
 
+def test_batched_host_entry_point_equals_device_batch(solver):
+    """fastpfp_match_batched_host stages every wave from host memory; it must
+    give what fastpfp_match_batched gives on device copies of the same pairs."""
+    pairs = synth.batch_mixed(count=6, seed=21, n_lo=40, n_hi=200, out_hi=30)
+    p = F.default_params(lam=0.5, max_outer=25, max_inner=250)
+    dev = [(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)) for g in pairs]
+    d = solver.match_batched(dev, params=p, want_X=True)
+    h = solver.match_batched_host([(g.A, g.A2, g.B, g.B2) for g in pairs], params=p, want_X=True)
+    for a, b in zip(d, h):
+        np.testing.assert_array_equal(a.perm.cpu().numpy(), b.perm)
+        assert np.abs(a.X.cpu().numpy() - b.X).max() <= 1e-5
+        assert a.stats.outer_iters == b.stats.outer_iters
+
+
 def _check_batch(solver, pairs, lam, **kw):
     """Every pair of one wave against the oracle replaying that pair's trace."""
     p = F.default_params(lam=lam, **kw)
