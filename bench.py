@@ -33,12 +33,25 @@ import numpy as np  # noqa: E402
 
 METRIC = "fastpfp_pair_solves_per_s_n1000"
 UNIT = "pair-solves/s"
-WORKLOAD = dict(workload="attributed_1000", n=1000, n2=1000, p=0.1, sigma=0.05, k=16,
-                attr_sigma=0.05, lam=1.0, alpha=0.5, tol_outer=1e-6, tol_inner=1e-6,
-                max_outer=100, max_inner=1000)
-# The dominant kernel of a batched step: the wave projection kernel.
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pdb_kernel_attributed_1000.md")
-PD_SOURCE = os.path.join(ROOT, "paper_1207_1114_gb300", "csrc", "projection_batched.cu")
+SOLVER = dict(alpha=0.5, tol_outer=1e-6, tol_inner=1e-6, max_outer=100, max_inner=1000)
+# Workloads (synthetic, seeded; paper_1207_1114_gb300/synth.py draws them).
+# attributed_1000 is the headline: pair-solves/s at n = n' = 1000.
+WORKLOADS = {
+    "attributed_1000": dict(n=1000, n2=1000, p=0.1, sigma=0.05, k=16, attr_sigma=0.05, lam=1.0,
+                            batch=7, metric=METRIC),
+    "partial_1000_1200": dict(n=1000, n2=1200, outliers=200, p=0.1, sigma=0.03, k=16,
+                              attr_sigma=0.05, lam=0.5, batch=5,
+                              metric="fastpfp_pair_solves_per_s_partial_1000_1200"),
+    "batch_mixed_512": dict(n="U{50..600}", n2="n+U{0..100}", p=0.15, sigma=0.03, k=8,
+                            attr_sigma=0.05, lam=0.5, batch=512,
+                            metric="fastpfp_pair_solves_per_s_batch_mixed"),
+    "large_4000": dict(n=4000, n2=4000, p=0.05, sigma=0.05, k=15, attr_sigma=0.05, lam=0.5,
+                       batch=1, metric="fastpfp_pair_solves_per_s_n4000"),
+}
+KERNEL_SOURCE = {
+    "pdb_kernel": os.path.join(ROOT, "paper_1207_1114_gb300", "csrc", "projection_batched.cu"),
+    "pd_kernel": os.path.join(ROOT, "paper_1207_1114_gb300", "csrc", "projection.cu"),
+}
 
 
 def peaks():
@@ -50,21 +63,27 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def pd_source_hash() -> str:
-    with open(PD_SOURCE, "rb") as f:
+def source_hash(kernel: str) -> str:
+    with open(KERNEL_SOURCE[kernel], "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def ncu_traffic_per_launch():
-    """DRAM bytes of one projection launch from the committed ncu summary, or
-    None when the projection kernel changed since the counters were taken."""
+def ncu_traffic_per_launch(kernel: str, workload: str, rounds_per_launch: float):
+    """DRAM bytes of one projection launch from the committed ncu summary
+    profiles/<kernel>_<workload>.md; None when the kernel source changed
+    since the counters were taken, or when the captured launch ran a
+    different number of rounds than this run's launches do on average."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload.replace('_512', '')}.md")
     try:
-        text = open(PROFILE_SUMMARY).read()
+        text = open(path).read()
     except OSError:
         return None
     h = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
     t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+-]+)", text)
-    if not h or not t or h.group(1) != pd_source_hash():
+    r = re.search(r"rounds_per_launch:\s*([0-9.eE+-]+)", text)
+    if not h or not t or h.group(1) != source_hash(kernel):
+        return None
+    if r and abs(float(r.group(1)) - rounds_per_launch) > 0.05 * rounds_per_launch:
         return None
     return float(t.group(1))
 
@@ -119,35 +138,78 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def make_pairs(rank: int, batch: int):
+def max_over_ranks(x: float, device) -> float:
+    """The largest of every rank's x (the slowest rank's time); x itself on
+    one process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, seconds: float, device) -> float:
+    """Whole-job throughput: the units all ranks processed divided by the
+    slowest rank's time (every rank processes units_per_rank)."""
+    import torch.distributed as dist
+    world = dist.get_world_size() if (dist.is_available() and dist.is_initialized()) else 1
+    return units_per_rank * world / max_over_ranks(seconds, device)
+
+
+def make_pairs(workload: str, rank: int, batch: int):
     from paper_1207_1114_gb300 import synth
-    return [synth.attributed_1000(seed=rank * 1000 + b) for b in range(batch)]
+    if workload == "attributed_1000":
+        return [synth.attributed_1000(seed=rank * 1000 + b) for b in range(batch)]
+    if workload == "partial_1000_1200":
+        return [synth.partial_1000_1200(seed=rank * 1000 + b) for b in range(batch)]
+    if workload == "batch_mixed_512":
+        return synth.batch_mixed(count=batch, seed=rank + 1)
+    if workload == "large_4000":
+        return [synth.large_4000(seed=rank * 1000 + b) for b in range(batch)]
+    raise ValueError(workload)
 
 
-def params(F, profile=0, precision="fp32"):
+def params(F, lam, profile=0, precision="fp32", loop_mode=0):
     """The workload's parameters.  bf16: tensor-core products until
     max|dX| < 1e-3, then FP32 iterations (at most 30) to convergence."""
-    w = WORKLOAD
     extra = dict(precision=F.BF16, refine_iters=30, switch_tol=1e-3) if precision == "bf16" else {}
-    return F.default_params(lam=w["lam"], alpha=w["alpha"], tol_outer=w["tol_outer"],
-                            tol_inner=w["tol_inner"], max_outer=w["max_outer"],
-                            max_inner=w["max_inner"], profile=profile, **extra)
+    return F.default_params(lam=lam, profile=profile, loop_mode=loop_mode, **SOLVER, **extra)
 
 
-def cpu_oracle_sample(g, outer_per_pair, inner_per_pair, budget_s=12.0):
-    """Times the oracle on one gradient, one blend and a bounded number of
-    projection rounds of one pair, and extrapolates to one whole solve with
-    the given per-pair iteration counts."""
+def canon_shape(g):
+    n, n2 = g.A.shape[0], g.A2.shape[0]
+    return max(n, n2), min(n, n2)
+
+
+def cpu_oracle_sample(g, budget_s=12.0):
+    """Times the oracle as it stands on one pair: one gradient, one blend and
+    a bounded number of projection rounds.  Returns per-unit costs (seconds
+    per gradient flop, per projection entry-round, per blend entry) that
+    extrapolate to any pair and iteration count, the sample's description and
+    the CPU seconds spent."""
     import oracle
     A = g.A.astype(np.float64)
     A2 = g.A2.astype(np.float64)
-    K = oracle.affinity(g.B, g.B2)
-    N = A.shape[0]
-    X = np.full((N, N), 1.0 / (N * N))
+    K = oracle.affinity(g.B, g.B2) if g.k else None
+    tr = A.shape[0] < A2.shape[0]
+    if tr:
+        A, A2 = A2, A
+        K = K.T if K is not None else None
+    N, m = A.shape[0], A2.shape[0]
+    X = np.full((N, m), 1.0 / (N * m))
+    lam = g.lam if K is not None else 0.0
+    # the gradient's cost per flop is taken on the leading 1000 x 1000 block
+    # when the whole product would take minutes
+    ng, mg = (N, m) if N <= 1200 else (1000, 1000)
     t0 = time.perf_counter()
-    G = oracle.gradient(A, X, A2, K, g.lam)
+    Gs = oracle.gradient(A[:ng, :ng], X[:ng, :mg], A2[:mg, :mg],
+                         K[:ng, :mg] if K is not None else None, lam)
     t_grad = time.perf_counter() - t0
-    Y = G
+    G = Gs if (ng, mg) == (N, m) else np.full((N, m), Gs.mean())
+    Y = np.zeros((N, N))
+    Y[:, :m] = G
     t0 = time.perf_counter()
     Y, _, _ = oracle.pd(Y, fixed_iters=2)
     t_round = (time.perf_counter() - t0) / 2
@@ -156,42 +218,57 @@ def cpu_oracle_sample(g, outer_per_pair, inner_per_pair, budget_s=12.0):
     Y, _, _ = oracle.pd(Y, fixed_iters=rounds)
     t_round = (time.perf_counter() - t0) / rounds
     t0 = time.perf_counter()
-    oracle.blend(X, np.pad(G, ((0, 0), (0, 0))), 0.5, True)
+    oracle.blend(X, Y, 0.5, True)
     t_blend = time.perf_counter() - t0
-    t_solve = outer_per_pair * (t_grad + t_blend) + inner_per_pair * t_round
-    sample = (f"1 pair of the n=1000 workload: 1 gradient ({t_grad:.2f}s) + {rounds} projection "
-              f"rounds ({t_round * 1e3:.2f} ms/round) + 1 blend, extrapolated to "
-              f"{outer_per_pair:.1f} outer / {inner_per_pair:.0f} inner iterations per pair")
-    return 1.0 / t_solve, sample, t_grad + rounds * t_round + t_blend
+    unit = dict(grad=t_grad / (2.0 * ng * mg * (ng + mg)), round=t_round / (N * N),
+                blend=t_blend / (N * m))
+    sample = (f"1 pair (N={N}, m={m}): 1 gradient of {ng}x{mg} ({t_grad:.2f}s) + {rounds} "
+              f"projection rounds ({t_round * 1e3:.2f} ms/round) + 1 blend")
+    return unit, sample, t_grad + rounds * t_round + t_blend
+
+
+def oracle_solve_seconds(unit, N, m, outer, inner):
+    """Oracle time of one whole solve from the per-unit costs."""
+    return (outer * (unit["grad"] * 2.0 * N * m * (N + m) + unit["blend"] * N * m)
+            + inner * unit["round"] * N * N)
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the FP64 CPU oracle as it stands, on the host cores."""
+    """--impl reference: the FP64 CPU oracle as it stands, on the host cores.
+    Each step is a bounded sample of the n = 1000 workload, extrapolated with
+    the oracle's own iteration counts of its full solve of seed 0."""
     import oracle
     if rank != 0:
+        return
+    if args.workload != "attributed_1000":
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the oracle's own iteration counts are stored for attributed_1000 only"}))
         return
     golden = os.path.join(ROOT, "tests", "golden", "attributed_1000_seed0.json")
     with open(golden) as f:
         gold = json.load(f)
     outer = gold["outer_iters"]
     inner = sum(gold["inner"])
-    g = make_pairs(0, 1)[0]
+    g = make_pairs("attributed_1000", 0, 1)[0]
+    N, m = canon_shape(g)
     vals, samples = [], []
     for i in range(args.warmup + args.steps):
-        v, sample, _ = cpu_oracle_sample(g, outer, inner, budget_s=args.ref_budget)
+        unit, sample, _ = cpu_oracle_sample(g, budget_s=args.ref_budget)
         if i >= args.warmup:
-            vals.append(v)
+            vals.append(1.0 / oracle_solve_seconds(unit, N, m, outer, inner))
             samples.append(sample)
     value = float(np.median(vals))
+    wl = {k: v for k, v in WORKLOADS["attributed_1000"].items() if k not in ("metric", "batch")}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": dict(WORKLOAD, pairs_per_step=1),
+        "data": "synthetic",
+        "config": dict(workload="attributed_1000", **wl, **SOLVER, pairs_per_step=1),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                          "kind": "oracle", "sample": samples[-1] +
-                         f"; iteration counts are the oracle's own full solve of seed 0 "
-                         f"({outer} outer, {inner} inner)"},
+                         f", extrapolated to the oracle's own full solve of seed 0 "
+                         f"({outer} outer, {inner} inner iterations)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -202,13 +279,19 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=7, help="pairs per step and rank")
+    ap.add_argument("--workload", default="attributed_1000", choices=sorted(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=None, help="pairs per step and rank")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-budget", type=float, default=10.0, dest="ref_budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
                     help="gradient products: plain FP32, or BF16 tensor cores + FP32 refinement")
+    ap.add_argument("--loop", default="graph", choices=["graph", "host"],
+                    help="outer loop: CUDA-graph while node (default) or host-polled chunks")
     args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.batch is None:
+        args.batch = wl["batch"]
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -226,11 +309,13 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    pairs = make_pairs(rank, args.batch)
-    n = WORKLOAD["n"]
+    pairs = make_pairs(args.workload, rank, args.batch)
+    shapes = [canon_shape(g) for g in pairs]
+    max_n = max(max(g.A.shape[0], g.A2.shape[0]) for g in pairs)
+    lam = pairs[0].lam
     dpairs = [(torch.as_tensor(g.A, device=dev), torch.as_tensor(g.A2, device=dev),
                torch.as_tensor(g.B, device=dev), torch.as_tensor(g.B2, device=dev)) for g in pairs]
-    solver = F.Solver(max_n=n, max_batch=args.batch, device=local)
+    solver = F.Solver(max_n=max_n, max_batch=args.batch, device=local)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -239,8 +324,13 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    p_plain = params(F, precision=args.precision)
-    p_prof = params(F, profile=1, precision=args.precision)
+    loop_mode = 0 if args.loop == "graph" else 1
+    p_plain = params(F, lam, precision=args.precision, loop_mode=loop_mode)
+    p_prof = params(F, lam, profile=1, precision=args.precision)
+    # host loop: the timed steps carry the per-launch CUDA events themselves;
+    # graph loop: the timed steps run the graph, and one instrumented pass of
+    # the same batch right after them times every projection launch
+    p_timed = p_prof if args.loop == "host" else p_plain
     for _ in range(args.warmup):
         solver.match_batched(dpairs, params=p_plain)
     # timed region: per-step CUDA events, L2 flushed (untimed) before every step
@@ -252,47 +342,60 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            outs = solver.match_batched(dpairs, params=p_prof)
+            outs = solver.match_batched(dpairs, params=p_timed)
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
             stats_all.append([o.stats for o in outs])
             accs = [float((o.perm.cpu().numpy() == g.gt).mean()) for o, g in zip(outs, pairs)]
         barrier()
-    total_ms = float(sum(step_ms))
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    pairs_done = args.batch * args.steps * world
-    value = pairs_done / (total_ms / 1e3)
+    value = whole_job_rate(args.batch * args.steps, float(sum(step_ms)) / 1e3, dev)
+    total_ms = max_over_ranks(float(sum(step_ms)), dev)
+    launches = sum(s.launches for step in stats_all for s in step)
 
-    # roofline of the dominant kernel (projection): algorithmic bytes of all
-    # its launches / their summed CUDA-event time
-    flat = [s for step in stats_all for s in step]
-    outer = sum(s.outer_iters for s in flat)
-    inner = sum(s.inner_iters_total for s in flat)
+    # roofline of the dominant kernel (the projection): algorithmic bytes of
+    # all its launches / their summed CUDA-event time
+    if args.loop == "host":
+        prof_steps = stats_all
+        timing = "CUDA events on the launching stream around every projection launch of the timed steps"
+    else:
+        flush.zero_()
+        prof_steps = [[o.stats for o in solver.match_batched(dpairs, params=p_prof)]]
+        timing = ("CUDA events on the launching stream around every projection launch of one "
+                  "instrumented pass (host-enqueued loop) of the timed batch, run after the timed steps")
+    flat = [s for step in prof_steps for s in step]
+    alg_bytes = 0.0
+    for step in prof_steps:
+        for s_, (N, m) in zip(step, shapes):
+            # per P1/P2 round: read + write the FP32 N x N slacked matrix;
+            # per blend: read X and Y[:, :m], write X
+            alg_bytes += s_.inner_iters_total * 8.0 * N * N + s_.outer_iters * 12.0 * N * m
     ms_proj = sum(s.ms_proj for s in flat)
     ms_gemm = sum(s.ms_gemm for s in flat)
     ms_disc = sum(s.ms_disc for s in flat)
-    bytes_round = 8.0 * n * n              # read + write the FP32 N x N slacked matrix
-    bytes_blend = 12.0 * n * n             # read X, read Y[:, :m], write X
-    alg_bytes = inner * bytes_round + outer * bytes_blend
     achieved = alg_bytes / (ms_proj / 1e3) / 1e9 if ms_proj > 0 else None
     peak, peak_kind = peaks()
-    traffic = ncu_traffic_per_launch()
-    launches = sum(s.launches for s in flat)
-    # one projection launch per outer iteration of a wave (a step is one wave)
-    proj_launches = sum(max(s.outer_iters for s in step) for step in stats_all)
+    kernel = "pdb_kernel" if flat[0].wave_pairs > 0 else "pd_kernel"
+    # one projection launch per outer iteration of a wave (or of a lone pair)
+    # and, about, as many rounds per launch as the wave's slowest pair runs
+    proj_launches, wave_rounds = 0, 0
+    for step in prof_steps:
+        i = 0
+        while i < len(step):
+            w = max(step[i].wave_pairs, 1)
+            proj_launches += max(s.outer_iters for s in step[i:i + w])
+            wave_rounds += max(s.inner_iters_total for s in step[i:i + w])
+            i += w
+    rounds_per_launch = wave_rounds / max(proj_launches, 1)
+    traffic = ncu_traffic_per_launch(kernel, args.workload, rounds_per_launch)
 
     # end to end through the public host-memory batch entry point: every step
     # copies its pairs from pinned host memory and reads the permutations back
-    e2e_value = None
     h2d = d2h = 0
     host = [tuple(torch.as_tensor(a).pin_memory() for a in (g.A, g.A2, g.B, g.B2)) for g in pairs]
     for hp in host:
         h2d += sum(x.numel() * x.element_size() for x in hp)
-    d2h = args.batch * n * 4
+    d2h = sum(g.A.shape[0] * 4 for g in pairs)
     solver.match_batched_host(host, params=p_plain)   # warm
     e2e_steps = max(1, min(args.steps, 3))
     barrier()
@@ -300,36 +403,42 @@ def main():
     for _ in range(e2e_steps):
         solver.match_batched_host(host, params=p_plain)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    e2e_value = args.batch * e2e_steps * world / float(tt.item())
+    e2e_value = whole_job_rate(args.batch * e2e_steps, time.perf_counter() - t0, dev)
 
+    flat_t = [s for step in stats_all for s in step]
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
-        v, sample, _ = cpu_oracle_sample(pairs[0], outer / len(flat), inner / len(flat))
-        cpu = {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": sample}
+        unit, sample, _ = cpu_oracle_sample(pairs[0])
+        last = stats_all[-1]
+        t_cpu = sum(oracle_solve_seconds(unit, N, m, s_.outer_iters, s_.inner_iters_total)
+                    for s_, (N, m) in zip(last, shapes))
+        cpu = {"value": len(last) / t_cpu, "unit": UNIT, "cores": oracle.num_threads(),
+               "kind": "oracle",
+               "sample": sample + f", per-unit costs extrapolated to the {len(last)} pairs of one "
+                                  f"step with the GPU's per-pair iteration counts"}
 
     if rank == 0:
+        cfg = {k: v for k, v in wl.items() if k not in ("metric", "batch")}
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "metric": wl["metric"], "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "bf16+f32", "data": "synthetic",
-            "config": dict(WORKLOAD, pairs_per_step=args.batch, precision=args.precision,
+            "config": dict(workload=args.workload, **cfg, **SOLVER, pairs_per_step=args.batch,
+                           precision=args.precision, loop=args.loop,
                            l2="flushed (512 MB write) before every timed step",
                            parallelism=f"pairs sharded over {world} rank(s)"),
             "accuracy": float(np.mean(accs)),
-            "iterations": {"outer_per_pair": outer / len(flat), "inner_per_pair": inner / len(flat)},
-            "phase_ms": {"gemm": ms_gemm, "projection": ms_proj, "discretize": ms_disc},
-            "roofline": {"kernel": "pdb_kernel (wave projection rounds + blend)", "bound": "hbm",
+            "iterations": {"outer_per_pair": sum(s.outer_iters for s in flat_t) / len(flat_t),
+                           "inner_per_pair": sum(s.inner_iters_total for s in flat_t) / len(flat_t)},
+            "phase_ms_instrumented": {"gemm": ms_gemm, "projection": ms_proj, "discretize": ms_disc},
+            "roofline": {"kernel": f"{kernel} (projection rounds + blend)", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                          "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                          "traffic": traffic,
-                         "alg_bytes_per_launch": alg_bytes / max(proj_launches, 1)},
+                         "alg_bytes_per_launch": alg_bytes / max(proj_launches, 1),
+                         "launches": proj_launches, "timing": timing},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

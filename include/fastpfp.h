@@ -74,7 +74,14 @@ typedef struct {
                               (Algorithm 1 initialises Y once); 1: reset them to 0            */
     int timeout_ms;        /* budget of every device-side barrier wait; <= 0 means 2000 ms     */
     int profile;           /* 1: record CUDA events on `stream` around every phase of the first
-                              128 outer iterations and report per-phase times in the stats    */
+                              128 outer iterations and report per-phase times in the stats;
+                              implies loop_mode 1                                            */
+    int loop_mode;         /* control of the repeat loop of Algorithm 1.  0: one CUDA graph per
+                              solve (or wave), a while node around the outer iteration whose
+                              condition a device kernel sets from the stop word after every
+                              iteration (no host round trip inside a solve); 1: the host
+                              enqueues outer iterations in chunks of 4 and polls the stop word
+                              one chunk behind                                               */
     int debug_flags;       /* testing only, 0 in production.  Bit 0: CTA 0 of the first
                               projection launch skips its arrival at the first grid barrier, so
                               every wait of that launch runs out after timeout_ms and the call
@@ -92,6 +99,8 @@ typedef struct {
     int transposed;         /* 1 if the graphs were swapped (n_a < n_b)                      */
     int status;             /* FASTPFP_OK or the error code of this solve                    */
     int launches;           /* CUDA kernels this solve enqueued                              */
+    int wave_pairs;         /* pairs that shared this solve's pdb_kernel launches (a wave of a
+                               batched call); 0 when it ran alone through pd_kernel           */
     double final_delta;     /* last max|X(t+1) - X(t)|                                       */
     double objective;       /* Eq. (3) at the returned partial permutation                   */
     float ms_gemm;          /* profile = 1: summed time of the gradient products             */

@@ -11,10 +11,16 @@
 // the loop continues.  A batch (fastpfp_match_batched) is cut into waves of
 // pairs whose slacked matrices fit in shared memory together; per outer
 // iteration a wave runs every pair's products and one launch of pdb_kernel,
-// which shares each grid barrier between all pairs of the wave.  Outer
-// iterations are enqueued in chunks: after each chunk the host checks (one
-// chunk behind, so the GPU never idles) whether every pair has stopped, and
-// stops enqueueing.  Launches after a pair's stop return at once.
+// which shares each grid barrier between all pairs of the wave.
+//
+// The repeat loop of Algorithm 1 runs in one of two ways.  By default one
+// outer iteration is captured into the body of a CUDA-graph while node whose
+// condition a one-thread kernel sets after every iteration from the device
+// stop word, so a solve (or wave) is one graph launch with no host round
+// trip until its end.  With loop_mode = 1 (and always with profile = 1) the
+// host enqueues outer iterations in chunks and checks, one chunk behind so
+// the GPU never idles, whether every pair has stopped; launches after a
+// pair's stop return at once.
 #include <algorithm>
 #include <cstddef>
 #include <cstdio>
@@ -80,6 +86,14 @@ struct fastpfp_s {
 
     cudaEvent_t ev[kProfEvents] = {};
     cudaEvent_t chunk_ev[2] = {};
+    // graph-controlled outer loop: a capture stream, the loop's iteration
+    // counter (device), and the graphs of the current call, released after
+    // the call has synchronised
+    cudaStream_t cap = nullptr;
+    int* d_loop = nullptr;
+    int loop_body = 0;          // kernels per iteration of the last graph loop (0: host loop)
+    std::vector<cudaGraph_t> graphs;
+    std::vector<cudaGraphExec_t> execs;
     // learned warm start: features, activations, embeddings and gradients of
     // both graphs (big = canonical rows, small = columns)
     struct {
@@ -108,6 +122,7 @@ bool params_ok(const fastpfp_params* p) {
     if (!(p->tol_outer >= 0.0) || !(p->tol_inner >= 0.0)) return false;
     if (p->precision != FASTPFP_FP32 && p->precision != FASTPFP_BF16) return false;
     if (p->refine_iters < 0) return false;
+    if (p->loop_mode != 0 && p->loop_mode != 1) return false;
     return true;
 }
 
@@ -249,19 +264,87 @@ int enqueue_finish(const Slot& sl, cudaStream_t s, const Problem& q, const fastp
     return 2 + (q.perm_out ? (q.transposed ? 1 : 2) : 0) + (q.X_out ? 1 : 0);
 }
 
-// Enqueues outer iterations in chunks of kChunk; `step(t)` enqueues outer
-// iteration t and returns the kernels it launched (or < 0).  After every
-// chunk four ints of the device control word at `d_words` are copied to
-// pinned memory behind an event; the host checks the previous chunk's copy
-// (words done_idx and err_idx), so one chunk is always queued ahead.
+void release_graphs(fastpfp_t h) {
+    for (cudaGraphExec_t e : h->execs) cudaGraphExecDestroy(e);
+    for (cudaGraph_t g : h->graphs) cudaGraphDestroy(g);
+    h->execs.clear();
+    h->graphs.clear();
+}
+
+// The outer loop as a graph: loop_init (clears the iteration count in
+// h->d_loop, opens the loop), then a while node whose body is one outer
+// iteration (`step(0, cap)` captured on the handle's capture stream)
+// followed by loop_cond, which reads the stop and error words at d_words and
+// closes the loop when either is set or after max_outer iterations.  The
+// condition's default is "closed", so the body can only repeat while device
+// code keeps it open.  The graph is launched on `s`; it and its executable
+// live until release_graphs.  Returns the kernels of one iteration (also
+// stored in h->loop_body) or < 0.
 template <typename Step>
-int run_outer(fastpfp_t h, cudaStream_t s, const int* d_words, int done_idx, int err_idx,
-              int max_outer, Step step) {
+int run_outer_graph(fastpfp_t h, cudaStream_t s, const int* d_words, int done_idx, int err_idx,
+                    int max_outer, Step step) {
+    cudaGraph_t g = nullptr;
+    FP_CUDA(cudaGraphCreate(&g, 0));
+    h->graphs.push_back(g);
+    cudaGraphConditionalHandle hc;
+    FP_CUDA(cudaGraphConditionalHandleCreate(&hc, g, 0, cudaGraphCondAssignDefault));
+    FP_CUDA(cudaStreamBeginCaptureToGraph(h->cap, g, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    const cudaError_t ei = loop_init(h->d_loop, hc, h->cap);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t e0 = cudaStreamEndCapture(h->cap, &captured);
+    FP_CUDA(ei);
+    FP_CUDA(e0);
+    cudaGraphNode_t init = nullptr;
+    size_t nn = 1;
+    FP_CUDA(cudaGraphGetNodes(g, &init, &nn));
+    if (nn != 1 || !init) return FASTPFP_ERR_CUDA;
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hc;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    FP_CUDA(cudaGraphAddNode(&node, g, &init, nullptr, 1, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    FP_CUDA(cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    int r = step(0, h->cap);
+    if (r >= 0)
+        r = loop_cond(d_words, done_idx, err_idx, h->d_loop, max_outer, hc, h->cap) == cudaSuccess
+                ? r + 1 : FASTPFP_ERR_CUDA;
+    const cudaError_t ec = cudaStreamEndCapture(h->cap, &captured);
+    if (r < 0) return r;
+    FP_CUDA(ec);
+    cudaGraphExec_t ex = nullptr;
+    FP_CUDA(cudaGraphInstantiate(&ex, g, 0));
+    h->execs.push_back(ex);
+    FP_CUDA(cudaGraphLaunch(ex, s));
+    h->loop_body = r;
+    return r;
+}
+
+// Enqueues the outer loop; `step(t, stream)` enqueues outer iteration t on
+// `stream` and returns the kernels it launched (or < 0).  Graph mode (see
+// run_outer_graph) returns 0 here; the kernels it ran are counted after the
+// call synchronised.  Host mode enqueues chunks of kChunk iterations: after
+// every chunk four ints of the device control word at `d_words` are copied
+// to pinned memory behind an event; the host checks the previous chunk's
+// copy (words done_idx and err_idx), so one chunk is always queued ahead.
+template <typename Step>
+int run_outer(fastpfp_t h, cudaStream_t s, const fastpfp_params* p, const int* d_words, int done_idx,
+              int err_idx, Step step) {
+    const int max_outer = p->max_outer;
+    h->loop_body = 0;
+    if (p->loop_mode == 0 && !p->profile) {
+        const int r = run_outer_graph(h, s, d_words, done_idx, err_idx, max_outer, step);
+        return r < 0 ? r : 0;
+    }
     int t = 0, chunk = 0, nl = 0;
     while (t < max_outer) {
         const int tc = std::min(kChunk, max_outer - t);
         for (int i = 0; i < tc; ++i, ++t) {
-            const int r = step(t);
+            const int r = step(t, s);
             if (r < 0) return r;
             nl += r;
         }
@@ -319,19 +402,19 @@ int enqueue_single(fastpfp_t h, cudaStream_t s, const Slot& sl, const Problem& q
     P.skip_arrive = (p->debug_flags & 1) ? 1 : 0;
     const bool prof = p->profile != 0;
     static_assert(offsetof(Ctrl, done) == 0 && offsetof(Ctrl, error) == 8, "Ctrl head layout");
-    const int r = run_outer(h, s, &sl.ctrl->done, 0, 2, p->max_outer, [&](int t) -> int {
+    const int r = run_outer(h, s, p, &sl.ctrl->done, 0, 2, [&](int t, cudaStream_t st) -> int {
         const bool pt = prof && t < kProfIters;
-        if (pt && t == 0) FP_CUDA(cudaEventRecord(h->ev[0], s));
+        if (pt && t == 0) FP_CUDA(cudaEventRecord(h->ev[0], st));
         int g = 0;
         if (bf16) {
-            g = enqueue_tc(tc, s);
+            g = enqueue_tc(tc, st);
             if (g < 0) return g;
         }
-        const int g32 = enqueue_gradient(sl, s, q, p);
+        const int g32 = enqueue_gradient(sl, st, q, p);
         if (g32 < 0) return g32;
-        if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 1], s));
-        FP_CUDA(pd_launch(L, P, s));
-        if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 2], s));
+        if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 1], st));
+        FP_CUDA(pd_launch(L, P, st));
+        if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 2], st));
         return g + g32 + 1;
     });
     if (r < 0) return r;
@@ -358,10 +441,11 @@ void read_profile(fastpfp_t h, int outer, float share, fastpfp_stats* st) {
     st->ms_disc = d * share;
 }
 
-int fill_stats(const Ctrl& c, int transposed, int launches, fastpfp_stats* st) {
+int fill_stats(const Ctrl& c, int transposed, int launches, int wave_pairs, fastpfp_stats* st) {
     const int status = c.error != 0 ? c.error : FASTPFP_OK;
     if (st) {
         st->launches = launches;
+        st->wave_pairs = wave_pairs;
         st->ms_gemm = st->ms_proj = st->ms_disc = 0.f;
         st->outer_iters = c.outer;
         st->inner_iters_total = c.inner_total;
@@ -549,21 +633,21 @@ int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, co
     const bool prof = p->profile != 0;
     static_assert(offsetof(WaveCtrl, error) == 0 && offsetof(WaveCtrl, all_done) == 4,
                   "WaveCtrl layout");
-    const int r = run_outer(h, s, reinterpret_cast<const int*>(h->d_wave), 1, 0, p->max_outer,
-                            [&](int t) -> int {
+    const int r = run_outer(h, s, p, reinterpret_cast<const int*>(h->d_wave), 1, 0,
+                            [&](int t, cudaStream_t st) -> int {
         const bool pt = prof && t < kProfIters;
-        if (pt && t == 0) FP_CUDA(cudaEventRecord(h->ev[0], s));
+        if (pt && t == 0) FP_CUDA(cudaEventRecord(h->ev[0], st));
         int n = 0;
         if (bf16) {
-            n = enqueue_tc(tc, s);
+            n = enqueue_tc(tc, st);
             if (n < 0) return n;
         }
-        for (const GemmF32Group& g : f32a) FP_CUDA(gemm_f32_group(g, s));   // T = A X
-        for (const GemmF32Group& g : f32b) FP_CUDA(gemm_f32_group(g, s));   // Y = T A' + lambda K
+        for (const GemmF32Group& g : f32a) FP_CUDA(gemm_f32_group(g, st));   // T = A X
+        for (const GemmF32Group& g : f32b) FP_CUDA(gemm_f32_group(g, st));   // Y = T A' + lambda K
         n += (int)(f32a.size() + f32b.size());
-        if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 1], s));
-        FP_CUDA(pdb_launch(P, w.grid, w.smem, s));
-        if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 2], s));
+        if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 1], st));
+        FP_CUDA(pdb_launch(P, w.grid, w.smem, st));
+        if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 2], st));
         return n + 1;
     });
     if (r < 0) return r;
@@ -601,6 +685,7 @@ void fastpfp_default_params(fastpfp_params* p) {
     p->slack_policy = 0;
     p->timeout_ms = 2000;
     p->profile = 0;
+    p->loop_mode = 0;
     p->debug_flags = 0;
 }
 
@@ -658,6 +743,7 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     const size_t opairs = take(sizeof(PairDesc) * kMaxWavePairs);
     const size_t oband = take(sizeof(int) * 2 * (h->num_sms + 1));
     const size_t owave = take(sizeof(WaveCtrl));
+    const size_t oloop = take(sizeof(int));
     const size_t nch = (n + 63) / 64;
     const size_t wFb = take(n * kMlpIn * 4), wFs = take(n * kMlpIn * 4), wHb = take(n * kMlpHidden * 4),
                  wHs = take(n * kMlpHidden * 4), wEb = take(n * kMlpOut * 4), wEs = take(n * kMlpOut * 4),
@@ -675,6 +761,7 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
         if (h->h_pairs) cudaFreeHost(h->h_pairs);
         if (h->h_band) cudaFreeHost(h->h_band);
         if (h->h_done) cudaFreeHost(h->h_done);
+        if (h->cap) cudaStreamDestroy(h->cap);
         if (h->pool) cudaFree(h->pool);
         delete h;
         return code;
@@ -683,7 +770,8 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     if (cudaMallocHost(&h->host_ctrl, sizeof(Ctrl) * (size_t)max_batch) != cudaSuccess ||
         cudaMallocHost(&h->h_pairs, sizeof(PairDesc) * kMaxWavePairs) != cudaSuccess ||
         cudaMallocHost(&h->h_band, sizeof(int) * 2 * (h->num_sms + 1)) != cudaSuccess ||
-        cudaMallocHost(&h->h_done, sizeof(int) * 8) != cudaSuccess)
+        cudaMallocHost(&h->h_done, sizeof(int) * 8) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
         return fail(FASTPFP_ERR_CUDA);
     char* b = h->pool;
     h->slots.resize(h->nslots);
@@ -717,6 +805,7 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     h->d_pairs = (PairDesc*)(b + opairs);
     h->d_band = (int*)(b + oband);
     h->d_wave = (WaveCtrl*)(b + owave);
+    h->d_loop = (int*)(b + oloop);
     h->ws.Fb = (float*)(b + wFb);
     h->ws.Fs = (float*)(b + wFs);
     h->ws.Hb = (float*)(b + wHb);
@@ -752,6 +841,7 @@ void fastpfp_destroy(fastpfp_t h) {
     if (!h) return;
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
+    release_graphs(h);
     for (int e = 0; e < kProfEvents; ++e)
         if (h->ev[e]) cudaEventDestroy(h->ev[e]);
     for (int e = 0; e < 2; ++e)
@@ -760,6 +850,7 @@ void fastpfp_destroy(fastpfp_t h) {
     if (h->h_pairs) cudaFreeHost(h->h_pairs);
     if (h->h_band) cudaFreeHost(h->h_band);
     if (h->h_done) cudaFreeHost(h->h_done);
+    if (h->cap) cudaStreamDestroy(h->cap);
     if (h->pool) cudaFree(h->pool);
     delete h;
 }
@@ -770,19 +861,8 @@ int fastpfp_match(fastpfp_t h, void* stream, const float* A, int n_a, const floa
     int rc = check_pair(h, A, n_a, A2, n_b, B, B2, k, p, perm_out);
     if (rc != FASTPFP_OK) return rc;
     if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
-    cudaStream_t s = (cudaStream_t)stream;
-    const Problem q = canonical(A, n_a, A2, n_b, B, B2, k, p->lambda, X0, perm_out, X_out);
-    const int nl = enqueue_single(h, s, h->slots[0], q, p, &h->host_ctrl[0]);
-    if (nl < 0) {
-        cudaStreamSynchronize(s);
-        return nl;
-    }
-    if (cudaStreamSynchronize(s) != cudaSuccess) return FASTPFP_ERR_CUDA;
-    h->last_first = 0;
-    h->last_count = 1;
-    rc = fill_stats(h->host_ctrl[0], q.transposed, nl, st);
-    if (p->profile) read_profile(h, h->host_ctrl[0].outer, 1.0f, st);
-    return rc;
+    fastpfp_pair x{A, A2, B, B2, n_a, n_b, k, X0, perm_out, X_out};
+    return solve_batch(h, (cudaStream_t)stream, 1, &x, p, st, false);
 }
 
 int fastpfp_match_host(fastpfp_t h, void* stream, const float* A, int n_a, const float* A2, int n_b,
@@ -863,10 +943,11 @@ int solve_batch(fastpfp_t h, cudaStream_t s, int count, const fastpfp_pair* pair
                                       x.X_out ? sl.sXout : nullptr);
             }
         }
-        const int nl = batched ? enqueue_wave(h, s, qs, w, p, &h->host_ctrl[b])
+        int nl = batched ? enqueue_wave(h, s, qs, w, p, &h->host_ctrl[b])
                                : enqueue_single(h, s, h->slots[0], qs[b], p, &h->host_ctrl[b]);
         if (nl < 0) {
             cudaStreamSynchronize(s);
+            release_graphs(h);
             return nl;
         }
         if (host) {
@@ -880,7 +961,13 @@ int solve_batch(fastpfp_t h, cudaStream_t s, int count, const fastpfp_pair* pair
             }
         }
         // the wave tables and the profiling events are reused by the next wave
-        if (cudaStreamSynchronize(s) != cudaSuccess) return FASTPFP_ERR_CUDA;
+        const cudaError_t es = cudaStreamSynchronize(s);
+        int loop_iters = 0;
+        if (es == cudaSuccess && h->loop_body > 0)
+            FP_CUDA(cudaMemcpy(&loop_iters, h->d_loop, sizeof(int), cudaMemcpyDeviceToHost));
+        release_graphs(h);
+        if (es != cudaSuccess) return FASTPFP_ERR_CUDA;
+        if (h->loop_body > 0) nl += 1 + h->loop_body * loop_iters;   // loop_init + iterations
         if (batched) {
             // an error of the shared projection launch belongs to every pair of the wave
             WaveCtrl wc{};
@@ -892,7 +979,7 @@ int solve_batch(fastpfp_t h, cudaStream_t s, int count, const fastpfp_pair* pair
         for (int i = 0; i < cnt; ++i) {
             const int launches = nl / cnt + (i == 0 ? nl % cnt : 0);
             int rc = fill_stats(h->host_ctrl[b + i], qs[b + i].transposed, launches,
-                                st ? &st[b + i] : nullptr);
+                                batched ? cnt : 0, st ? &st[b + i] : nullptr);
             if (st && p->profile) {
                 int outer = 0;
                 for (int j = 0; j < cnt; ++j) outer = std::max(outer, h->host_ctrl[b + j].outer);

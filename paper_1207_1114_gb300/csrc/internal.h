@@ -164,6 +164,14 @@ cudaError_t gemm_f32_group(const GemmF32Group& g, cudaStream_t s);
 // ----------------------------------------------------------- misc kernels
 cudaError_t init_ctrl(Ctrl* c, int lowp, cudaStream_t s);
 
+// Condition kernel of the outer loop's graph while node: sets `handle` to
+// continue while words[done_idx] == 0, words[err_idx] == 0 and the count in
+// *iter (incremented here) is below max_iter.
+cudaError_t loop_cond(const int* words, int done_idx, int err_idx, int* iter, int max_iter,
+                      cudaGraphConditionalHandle handle, cudaStream_t s);
+// Clears *iter and sets `handle` to 1; runs before the while node.
+cudaError_t loop_init(int* iter, cudaGraphConditionalHandle handle, cudaStream_t s);
+
 // K[i, j] = sum_c B[i, c] * B2[j, c]   (N x m, leading dimension ldk)
 cudaError_t affinity(const float* B, const float* B2, int N, int m, int k, float* K, int ldk,
                      cudaStream_t s);

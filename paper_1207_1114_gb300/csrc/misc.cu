@@ -131,6 +131,28 @@ __global__ void objective_kernel(const float* A, int N, const float* A2, int m, 
     }
 }
 
+// Condition of the outer loop's CUDA-graph while node, run after every outer
+// iteration: continue while neither the stop word (words[done_idx]) nor the
+// error word (words[err_idx]) is set and fewer than max_iter iterations have
+// run.  The iteration count in *iter bounds the loop even if no kernel of the
+// body ever sets the stop word.
+__global__ void loop_cond_kernel(const int* words, int done_idx, int err_idx, int* iter, int max_iter,
+                                 cudaGraphConditionalHandle handle) {
+    const int t = *iter + 1;
+    *iter = t;
+    const volatile int* w = words;
+    const bool go = w[done_idx] == 0 && w[err_idx] == 0 && t < max_iter;
+    cudaGraphSetConditional(handle, go ? 1u : 0u);
+}
+
+// Runs once before the while node: clears the iteration count and opens the
+// loop.  The handle's default is 0 (closed), so the body runs only if device
+// code set the condition; a condition that never gets set cannot loop.
+__global__ void loop_init_kernel(int* iter, cudaGraphConditionalHandle handle) {
+    *iter = 0;
+    cudaGraphSetConditional(handle, 1u);
+}
+
 inline int grid_for(size_t total, int block, int cap = 4096) {
     size_t g = (total + block - 1) / block;
     if (g < 1) g = 1;
@@ -142,6 +164,17 @@ inline int grid_for(size_t total, int block, int cap = 4096) {
 
 cudaError_t init_ctrl(Ctrl* c, int lowp, cudaStream_t s) {
     init_ctrl_kernel<<<1, 1, 0, s>>>(c, lowp);
+    return cudaGetLastError();
+}
+
+cudaError_t loop_cond(const int* words, int done_idx, int err_idx, int* iter, int max_iter,
+                      cudaGraphConditionalHandle handle, cudaStream_t s) {
+    loop_cond_kernel<<<1, 1, 0, s>>>(words, done_idx, err_idx, iter, max_iter, handle);
+    return cudaGetLastError();
+}
+
+cudaError_t loop_init(int* iter, cudaGraphConditionalHandle handle, cudaStream_t s) {
+    loop_init_kernel<<<1, 1, 0, s>>>(iter, handle);
     return cudaGetLastError();
 }
 

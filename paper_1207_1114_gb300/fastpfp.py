@@ -40,13 +40,14 @@ class fastpfp_params(C.Structure):
                 ("tol_inner", C.c_double), ("max_outer", C.c_int), ("max_inner", C.c_int),
                 ("precision", C.c_int), ("refine_iters", C.c_int), ("switch_tol", C.c_double),
                 ("normalize_max", C.c_int), ("slack_policy", C.c_int), ("timeout_ms", C.c_int),
-                ("profile", C.c_int), ("debug_flags", C.c_int)]
+                ("profile", C.c_int), ("loop_mode", C.c_int), ("debug_flags", C.c_int)]
 
 
 class fastpfp_stats(C.Structure):
     _fields_ = [("outer_iters", C.c_int), ("inner_iters_total", C.c_int),
                 ("inner_iters_max", C.c_int), ("converged", C.c_int), ("lowp_iters", C.c_int),
                 ("transposed", C.c_int), ("status", C.c_int), ("launches", C.c_int),
+                ("wave_pairs", C.c_int),
                 ("final_delta", C.c_double), ("objective", C.c_double), ("ms_gemm", C.c_float),
                 ("ms_proj", C.c_float), ("ms_disc", C.c_float)]
 

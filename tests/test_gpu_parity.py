@@ -241,6 +241,55 @@ def test_batched_host_entry_point_equals_device_batch(solver):
         assert a.stats.outer_iters == b.stats.outer_iters
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_graph_loop_equals_host_loop_single(solver, precision):
+    """Algorithm 1's repeat loop as a CUDA-graph while node (loop_mode 0)
+    and as host-polled chunks (loop_mode 1) run the same kernels: same
+    permutation, same iteration counts, X within FP32 reduction-order noise."""
+    g = synth.graph_pair(300, p=0.1, sigma=0.03, k=8, n_out=20, lam=0.5, seed=31)
+    prec = F.BF16 if precision == "bf16" else F.FP32
+    args = (cu(g.A), cu(g.A2), cu(g.B), cu(g.B2))
+    out = []
+    for mode in (0, 1):
+        p = F.default_params(lam=0.5, loop_mode=mode, precision=prec, refine_iters=10)
+        out.append(solver.match(*args, params=p, want_X=True))
+    a, b = out
+    np.testing.assert_array_equal(a.perm.cpu().numpy(), b.perm.cpu().numpy())
+    assert a.stats.outer_iters == b.stats.outer_iters
+    assert a.stats.lowp_iters == b.stats.lowp_iters
+    assert np.abs(a.X.cpu().numpy() - b.X.cpu().numpy()).max() <= 1e-5
+    # the graph loop adds one condition kernel per iteration but runs no
+    # product or projection launch after the stop; the host loop may
+    assert 0 < a.stats.launches <= b.stats.launches + a.stats.outer_iters + 1
+
+
+def test_graph_loop_equals_host_loop_batched(solver):
+    pairs = synth.batch_mixed(count=8, seed=32, n_lo=30, n_hi=250, out_hi=40)
+    dev = [(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)) for g in pairs]
+    res = [solver.match_batched(dev, params=F.default_params(lam=0.5, loop_mode=mode), want_X=True)
+           for mode in (0, 1)]
+    for a, b in zip(*res):
+        np.testing.assert_array_equal(a.perm.cpu().numpy(), b.perm.cpu().numpy())
+        assert a.stats.outer_iters == b.stats.outer_iters
+        assert np.abs(a.X.cpu().numpy() - b.X.cpu().numpy()).max() <= 1e-5
+
+
+@pytest.mark.parametrize("max_outer", [1, 2, 5])
+def test_graph_loop_stops_at_the_outer_cap(solver, max_outer):
+    """The while node ends after exactly I_0 iterations when X has not
+    converged (a normal stop: converged = 0)."""
+    g = synth.plain_100(1)
+    for batched in (False, True):
+        p = F.default_params(max_outer=max_outer, loop_mode=0)
+        if batched:
+            outs = solver.match_batched([(cu(g.A), cu(g.A2), None, None)] * 2, params=p)
+        else:
+            outs = [solver.match(cu(g.A), cu(g.A2), params=p)]
+        for o in outs:
+            assert o.stats.outer_iters == max_outer and o.stats.converged == 0
+            assert o.stats.status == 0
+
+
 def _check_batch(solver, pairs, lam, **kw):
     """Every pair of one wave against the oracle replaying that pair's trace."""
     p = F.default_params(lam=lam, **kw)
@@ -339,11 +388,13 @@ def test_argument_errors(solver):
     assert e.value.code == F.FASTPFP_ERR_SIZE
 
 
-def test_barrier_timeout_is_reported_and_handle_recovers(solver):
+@pytest.mark.parametrize("loop_mode", [0, 1])
+def test_barrier_timeout_is_reported_and_handle_recovers(solver, loop_mode):
     """A lost barrier arrival (test-only flag) makes every wait run out after
-    timeout_ms; the call returns ERR_TIMEOUT and the context stays usable."""
+    timeout_ms; the call returns ERR_TIMEOUT (the graph loop's condition sees
+    the error word and ends) and the context stays usable."""
     g = synth.plain_100(0)
-    p = F.default_params(timeout_ms=200, debug_flags=1, max_outer=3)
+    p = F.default_params(timeout_ms=200, debug_flags=1, max_outer=3, loop_mode=loop_mode)
     with pytest.raises(F.FastPFPError) as e:
         solver.match(cu(g.A), cu(g.A2), params=p)
     assert e.value.code == F.FASTPFP_ERR_TIMEOUT
