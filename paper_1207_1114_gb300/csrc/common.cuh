@@ -102,6 +102,17 @@ __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, 
                  : "memory");
 }
 
+// Asynchronous 16-byte global -> shared copy through L2 only (the source is
+// written by other CTAs' reductions, so L1 must not hold a stale copy), and
+// the wait for all of this thread's copies.  Both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async_cg16(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // Grid-wide barrier for a cooperative launch.  `counter` only ever grows
 // within a solve: every CTA adds 1 per barrier, and a barrier is passed once
 // the counter reaches `target` (the value after all CTAs of the grid have

@@ -473,26 +473,82 @@ struct BandStats {
     int rows = 0, cols = 0, elems = 0, segs = 0;
 };
 
-// Cuts the concatenated rows of pairs [first, first + count) into G bands of
-// about equal entry counts: band[0..G] row boundaries, per-band statistics.
-void split_group(const std::vector<Problem>& qs, int first, int count, int G, int* band,
-                 std::vector<BandStats>& st) {
-    long long E = 0;
+// Band cost model of pdb_kernel, in entry equivalents: a band costs its
+// entries plus kSegCost for every pair it spans (a segment brings its own
+// column fold, reductions and read-back; measured on GB300 at about 3500
+// cycles against 0.12 cycles per entry).
+constexpr long long kSegCost = 24576;
+
+// Greedy cut of the concatenated rows of pairs [first, first + count) into
+// consecutive bands of cost at most C: each band takes as many rows as fit.
+// Writes the boundaries to band[0..] (when band != nullptr) and returns the
+// number of bands, or max_bands + 1 as soon as more would be needed.  For a
+// cost that only grows as rows are added, the greedy uses the fewest bands.
+int cut_rows(const std::vector<Problem>& qs, int first, int count, long long C, long long seg_cost,
+             int max_bands, int* band) {
+    int b = 0, gr = 0, rows_in = 0, last = -1;
+    long long cur = 0;
+    if (band) band[0] = 0;
+    for (int i = 0; i < count; ++i) {
+        const int N = qs[first + i].N;
+        const long long ldy = round4(N);
+        int r = 0;
+        while (r < N) {
+            const long long seg = last != i ? seg_cost : 0;
+            const long long avail = C - cur - seg;
+            long long k = avail >= ldy ? std::min<long long>(N - r, avail / ldy) : 0;
+            if (k == 0) {
+                if (rows_in > 0) {
+                    if (++b >= max_bands) return max_bands + 1;
+                    if (band) band[b] = gr;
+                    cur = 0;
+                    rows_in = 0;
+                    last = -1;
+                    continue;
+                }
+                k = 1;   // C below one row's cost: the row goes alone
+            }
+            cur += seg + k * ldy;
+            rows_in += (int)k;
+            r += (int)k;
+            gr += (int)k;
+            last = i;
+        }
+    }
+    return rows_in > 0 || b == 0 ? b + 1 : b;
+}
+
+// Cuts pairs [first, first + count) into at most G bands minimising the
+// largest band cost (binary search on the cost bound over cut_rows).
+// band[0..used] holds the row boundaries, band[used..G] = total rows.
+// Returns the number of bands used.
+int split_group(const std::vector<Problem>& qs, int first, int count, int G, long long seg_cost,
+                int* band, std::vector<BandStats>& st) {
+    long long lo = 1, hi = 0;
     int rows = 0;
     for (int i = 0; i < count; ++i) {
-        E += (long long)qs[first + i].N * round4(qs[first + i].N);
+        const long long ldy = round4(qs[first + i].N);
+        lo = std::max(lo, seg_cost + ldy);
+        hi += (long long)qs[first + i].N * ldy + seg_cost;
         rows += qs[first + i].N;
     }
     for (int c = 0; c <= G; ++c) band[c] = rows;
-    band[0] = 0;
+    st.assign(G, BandStats{});
+    if (count == 0) return 0;
+    while (lo < hi) {
+        const long long mid = lo + (hi - lo) / 2;
+        if (cut_rows(qs, first, count, mid, seg_cost, G, nullptr) <= G) hi = mid;
+        else lo = mid + 1;
+    }
+    const int used = cut_rows(qs, first, count, lo, seg_cost, G, band);
+    for (int c = used; c <= G; ++c) band[c] = rows;
+    // per-band statistics
     int b = 0, gr = 0, last_pair = -1;
-    long long cum = 0;
     for (int i = 0; i < count; ++i) {
         const int N = qs[first + i].N, ldy = round4(N);
         for (int r = 0; r < N; ++r, ++gr) {
-            if (b < G - 1 && cum >= E * (b + 1) / G && st[b].rows > 0) {
+            while (b + 1 < used && gr >= band[b + 1]) {
                 ++b;
-                band[b] = gr;
                 last_pair = -1;
             }
             if (last_pair != i) {
@@ -502,15 +558,18 @@ void split_group(const std::vector<Problem>& qs, int first, int count, int G, in
             }
             ++st[b].rows;
             st[b].elems += ldy;
-            cum += ldy;
         }
     }
+    return used;
 }
 
 // Plans one wave of pairs [first, first + count): two groups of about equal
-// entry counts (group 1 one half-step behind group 0), each cut into at most
-// num_sms bands; a CTA holds one band of each group.  Returns false when a
-// CTA's bands would not fit in shared memory.
+// entry counts (group 1 one half-step behind group 0; with kInterleaveGroups
+// off group 1 is empty), each cut into at most num_sms cost-balanced bands;
+// a CTA holds one band of each group.  Bands first try to respect the
+// per-segment cost (pair-aligned where possible), then fall back to pure
+// entry balance if that does not fit in shared memory.  Returns false when a
+// CTA's bands would not fit.
 bool plan_bands(const std::vector<Problem>& qs, int first, int count, int num_sms, Wave* w) {
     long long E = 0;
     for (int i = 0; i < count; ++i) E += (long long)qs[first + i].N * round4(qs[first + i].N);
@@ -525,26 +584,37 @@ bool plan_bands(const std::vector<Problem>& qs, int first, int count, int num_sm
         }
     }
     const long long gl = (E + kMinElemsPerCta - 1) / kMinElemsPerCta;
-    const int G = (int)std::min<long long>(num_sms, std::max<long long>(1, gl));
-    w->band.assign(2 * (G + 1), 0);
-    std::vector<BandStats> s0(G), s1(G);
-    split_group(qs, first, split, G, w->band.data(), s0);
-    split_group(qs, first + split, count - split, G, w->band.data() + G + 1, s1);
-    PdbLayout L{0, 0, 0};
-    bool ok = true;
-    for (int b = 0; b < G; ++b) {
-        L.max_band_rows = std::max(L.max_band_rows, s0[b].rows + s1[b].rows);
-        L.max_band_cols = std::max(L.max_band_cols, s0[b].cols + s1[b].cols);
-        L.max_band_elems = std::max(L.max_band_elems, s0[b].elems + s1[b].elems);
-        if (s0[b].segs + s1[b].segs > kMaxSeg) ok = false;
+    const int Gmax = (int)std::min<long long>(num_sms, std::max<long long>(1, gl));
+    for (const long long seg_cost : {kSegCost, 0ll}) {
+        std::vector<int> b0(Gmax + 1), b1(Gmax + 1);
+        std::vector<BandStats> s0, s1;
+        const int u0 = split_group(qs, first, split, Gmax, seg_cost, b0.data(), s0);
+        const int u1 = split_group(qs, first + split, count - split, Gmax, seg_cost, b1.data(), s1);
+        const int G = std::max(1, std::max(u0, u1));
+        PdbLayout L{0, 0, 0};
+        bool ok = true;
+        for (int b = 0; b < G; ++b) {
+            L.max_band_rows = std::max(L.max_band_rows, s0[b].rows + s1[b].rows);
+            L.max_band_cols = std::max(L.max_band_cols, s0[b].cols + s1[b].cols);
+            L.max_band_elems = std::max(L.max_band_elems, s0[b].elems + s1[b].elems);
+            if (s0[b].segs + s1[b].segs > kMaxSeg) ok = false;
+        }
+        const size_t smem = pdb_smem_bytes(L, kPdbThreads);
+        if (!ok || smem > (size_t)kPdMaxSmem) continue;
+        w->band.assign(2 * (G + 1), 0);
+        for (int c = 0; c <= G; ++c) {
+            w->band[c] = b0[c];
+            w->band[G + 1 + c] = b1[c];
+        }
+        w->first = first;
+        w->count = count;
+        w->split = split;
+        w->grid = G;
+        w->layout = L;
+        w->smem = smem;
+        return true;
     }
-    w->first = first;
-    w->count = count;
-    w->split = split;
-    w->grid = G;
-    w->layout = L;
-    w->smem = pdb_smem_bytes(L, kPdbThreads);
-    return ok && w->smem <= (size_t)kPdMaxSmem;
+    return false;
 }
 
 // Largest wave starting at `first` (at least one pair when it fits at all).

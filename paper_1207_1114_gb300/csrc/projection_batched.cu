@@ -51,12 +51,13 @@ struct Shared {
     int* pstate;         // kMaxWavePairs: bit0 active this launch, bit1 stopped
     int* pstop;          // kMaxWavePairs: round at which the pair stopped
     int* ictl;           // [0],[1] group has an active pair, [2] n segments, [3] non-finite
+    int* qpref;          // 2 x (kMaxWavePairs + 1): per group, prefix sums of the pairs' column quads
     float* fred;         // kMaxSeg x 32 per-warp maxima
     float* rsum;         // band rows
     float* arow;         // band rows
     float* rowpart;      // band rows x 32
     float4* cred;        // nthr float4: column-partial reduction across row groups
-    float* cN;           // sum over segments of ldy floats
+    float* cN;           // sum over segments of ldy floats: the column sums c_j of the last round
     float* band;         // band rows of every segment (16-byte aligned)
 };
 
@@ -73,6 +74,7 @@ __device__ __forceinline__ Shared carve_b(char* base, const PdbLayout& L, int nt
     s.pstate = reinterpret_cast<int*>(take(sizeof(int) * kMaxWavePairs));
     s.pstop = reinterpret_cast<int*>(take(sizeof(int) * kMaxWavePairs));
     s.ictl = reinterpret_cast<int*>(take(sizeof(int) * 4));
+    s.qpref = reinterpret_cast<int*>(take(sizeof(int) * 2 * (kMaxWavePairs + 1)));
     s.fred = reinterpret_cast<float*>(take(sizeof(float) * kMaxSeg * 32));
     s.rsum = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_rows));
     s.arow = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_rows));
@@ -108,18 +110,19 @@ __device__ __forceinline__ Map make_map(int Q, int nthr, int tid) {
 }
 
 // One column quad of one row: Eq. (P1) with the row offset ai and the
-// column offset c (= c_j / N), then Eq. (P2); columns >= N stay zero.
-// Returns the quad's contribution to the row sum.
+// column sums c (the offset is c_j / N, folded into one FMA with ninvN =
+// -1/N), then Eq. (P2); columns >= N stay zero.  Returns the quad's
+// contribution to the row sum.
 template <bool UPDATE>
-__device__ __forceinline__ float quad_step(float4* __restrict__ p, float ai, float4 c, int c0, int N,
-                                           float4& cp, float& dmax) {
+__device__ __forceinline__ float quad_step(float4* __restrict__ p, float ai, float4 c, float ninvN, int c0,
+                                           int N, float4& cp, float& dmax) {
     float4 y = *p;
     if (UPDATE) {
         float4 z;
-        z.x = fmaxf((y.x + ai) - c.x, 0.f);
-        z.y = fmaxf((y.y + ai) - c.y, 0.f);
-        z.z = fmaxf((y.z + ai) - c.z, 0.f);
-        z.w = fmaxf((y.w + ai) - c.w, 0.f);
+        z.x = fmaxf(fmaf(ninvN, c.x, y.x + ai), 0.f);
+        z.y = fmaxf(fmaf(ninvN, c.y, y.y + ai), 0.f);
+        z.z = fmaxf(fmaf(ninvN, c.z, y.z + ai), 0.f);
+        z.w = fmaxf(fmaf(ninvN, c.w, y.w + ai), 0.f);
         if (c0 + 4 > N) {
             if (c0 + 1 >= N) z.y = 0.f;
             if (c0 + 2 >= N) z.z = 0.f;
@@ -143,7 +146,7 @@ template <bool UPDATE>
 __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, int Q, int N,
                                          const Map& mp, int nthr, int lane,
                                          const float* __restrict__ arow, float* __restrict__ rowpart,
-                                         float4 c0v, float4 c1v, float4& cp0, float4& cp1,
+                                         float4 c0v, float4 c1v, float ninvN, float4& cp0, float4& cp1,
                                          float& dmax) {
     const bool h0 = mp.q0 < Q;
     const bool h1 = mp.kq > 1 && mp.q0 + nthr < Q;
@@ -156,25 +159,30 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
         const float a1 = UPDATE ? arow[r + mp.RP] : 0.f;
         float s0 = 0.f, s1 = 0.f;
         if (h0) {
-            s0 += quad_step<UPDATE>(p, a0, c0v, c00, N, cp0, dmax);
-            s1 += quad_step<UPDATE>(p + stride, a1, c0v, c00, N, cp0, dmax);
+            s0 += quad_step<UPDATE>(p, a0, c0v, ninvN, c00, N, cp0, dmax);
+            s1 += quad_step<UPDATE>(p + stride, a1, c0v, ninvN, c00, N, cp0, dmax);
         }
         if (h1) {
-            s0 += quad_step<UPDATE>(p + nthr, a0, c1v, c01, N, cp1, dmax);
-            s1 += quad_step<UPDATE>(p + stride + nthr, a1, c1v, c01, N, cp1, dmax);
+            s0 += quad_step<UPDATE>(p + nthr, a0, c1v, ninvN, c01, N, cp1, dmax);
+            s1 += quad_step<UPDATE>(p + stride + nthr, a1, c1v, ninvN, c01, N, cp1, dmax);
         }
-        s0 = warp_sum(s0);
-        s1 = warp_sum(s1);
-        if (lane == 0) {
-            rowpart[(size_t)r * 32] = s0;
-            rowpart[(size_t)(r + mp.RP) * 32] = s1;
-        }
+        // both rows' warp sums in five shuffles: the lower half-warp folds
+        // row r, the upper half row r + RP
+        const bool hi = (lane & 16) != 0;
+        float keep = hi ? s1 : s0;
+        keep += __shfl_xor_sync(0xffffffffu, hi ? s0 : s1, 16);
+        keep += __shfl_xor_sync(0xffffffffu, keep, 8);
+        keep += __shfl_xor_sync(0xffffffffu, keep, 4);
+        keep += __shfl_xor_sync(0xffffffffu, keep, 2);
+        keep += __shfl_xor_sync(0xffffffffu, keep, 1);
+        if (lane == 0) rowpart[(size_t)r * 32] = keep;
+        if (lane == 16) rowpart[(size_t)(r + mp.RP) * 32] = keep;
     }
     if (r < nrows) {
         const float a0 = UPDATE ? arow[r] : 0.f;
         float s0 = 0.f;
-        if (h0) s0 += quad_step<UPDATE>(p, a0, c0v, c00, N, cp0, dmax);
-        if (h1) s0 += quad_step<UPDATE>(p + nthr, a0, c1v, c01, N, cp1, dmax);
+        if (h0) s0 += quad_step<UPDATE>(p, a0, c0v, ninvN, c00, N, cp0, dmax);
+        if (h1) s0 += quad_step<UPDATE>(p + nthr, a0, c1v, ninvN, c01, N, cp1, dmax);
         s0 = warp_sum(s0);
         if (lane == 0) rowpart[(size_t)r * 32] = s0;
     }
@@ -220,6 +228,12 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         }
         S.ictl[2] = nseg;
         S.ictl[3] = 0;
+        for (int g = 0; g < 2; ++g) {
+            const int p0 = g == 0 ? 0 : split, p1 = g == 0 ? split : npairs;
+            int* qp = S.qpref + g * (kMaxWavePairs + 1);
+            qp[0] = 0;
+            for (int p = p0; p < p1; ++p) qp[p - p0 + 1] = qp[p - p0] + (P.pairs[p].ldy >> 2);
+        }
     }
     for (int p = tid; p < npairs; p += nthr) {
         const PairDesc& d = P.pairs[p];
@@ -287,7 +301,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 const int wig = (mp.QP <= nthr) ? ((tid % mp.QP) >> 5) : warp;
                 seg_rows<UPDATE>(reinterpret_cast<float4*>(S.band + sg.soff), sg.nrows, Q, N, mp, nthr,
                                  lane, S.arow + sg.brow0, S.rowpart + (size_t)sg.brow0 * 32 + wig, c0v,
-                                 c1v, cp0, cp1, dmax);
+                                 c1v, -1.0f / (float)N, cp0, cp1, dmax);
             }
             dmax = warp_max(dmax);
             if (lane == 0) S.fred[si * 32 + warp] = dmax;
@@ -360,19 +374,17 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         const unsigned target = (g == 0 ? base0 : base1) + G * (gen[g] + 1u);
         if (!grid_wait(&W->bar[g], target, err, P.timeout_ns)) return false;
         ++gen[g];
+        // every segment's column sums in flight at once (copied, not loaded
+        // and stored, so no segment waits for the previous one's latency)
         for (int si = 0; si < nseg; ++si) {
             const Seg sg = S.seg[si];
             if (sg.group != g) continue;
             const int pst = S.pstate[sg.pair];
             if (!(pst & 1) || (pst & 2)) continue;
             const PairS pr = S.pair[sg.pair];
-            const float invN = 1.0f / (float)pr.N;
             const float4* c = reinterpret_cast<const float4*>(pr.colbuf + (size_t)cur * pr.ldy);
             float4* dst = reinterpret_cast<float4*>(S.cN + sg.coff);
-            for (int q = tid; q < (pr.ldy >> 2); q += nthr) {
-                const float4 v = __ldcg(c + q);
-                dst[q] = make_float4(v.x * invN, v.y * invN, v.z * invN, v.w * invN);
-            }
+            for (int q = tid; q < (pr.ldy >> 2); q += nthr) cp_async_cg16(dst + q, c + q);
         }
         if (warp == 0) {
             const int p0 = g == 0 ? 0 : split, p1 = g == 0 ? split : npairs;
@@ -407,19 +419,28 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                     S.arow[sg.brow0 + r] = (float)(a_base - (double)S.rsum[sg.brow0 + r] * invN);
             }
         }
+        cp_async_wait_all();
         __syncthreads();
         return true;
     };
 
-    // Zero accumulator `which` of group g's pairs (distributed over CTAs).
+    // Zero accumulator `which` of group g's pairs.  The group's column quads
+    // are numbered consecutively over its pairs and dealt round-robin over
+    // the CTAs, so every CTA zeroes about the same few quads.
     auto clear_acc = [&](int g, int which) {
-        const int p0 = g == 0 ? 0 : split, p1 = g == 0 ? split : npairs;
-        for (int p = p0; p < p1; ++p) {
-            const PairS& pr = S.pair[p];
-            const int Q = pr.ldy >> 2;
-            float4* cb = reinterpret_cast<float4*>(pr.colbuf + (size_t)which * pr.ldy);
-            for (int q = blockIdx.x * nthr + tid; q < Q; q += G * nthr) cb[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (blockIdx.x == 0 && tid == 0) {
+        const int p0 = g == 0 ? 0 : split, np = (g == 0 ? split : npairs) - p0;
+        const int* qp = S.qpref + g * (kMaxWavePairs + 1);
+        const int total = qp[np];
+        for (int f = tid * (int)G + (int)blockIdx.x; f < total; f += nthr * (int)G) {
+            int lo = 0, hi = np;   // the pair whose quads hold f: qp[lo] <= f < qp[lo + 1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (qp[mid] <= f) lo = mid; else hi = mid;
+            }
+            const PairS& pr = S.pair[p0 + lo];
+            const int q = f - qp[lo];
+            reinterpret_cast<float4*>(pr.colbuf + (size_t)which * pr.ldy)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q == 0) {
                 pr.sbuf[which] = 0.0;
                 pr.dbuf[which] = 0u;
             }
@@ -619,6 +640,7 @@ size_t pdb_smem_bytes(const PdbLayout& L, int nthr) {
     take(4 * kMaxWavePairs);
     take(4 * kMaxWavePairs);
     take(4 * 4);
+    take(4 * 2 * (kMaxWavePairs + 1));
     take(4 * kMaxSeg * 32);
     take(4 * (size_t)L.max_band_rows);
     take(4 * (size_t)L.max_band_rows);
