@@ -140,29 +140,57 @@ __device__ __forceinline__ float quad_step(float4* __restrict__ p, float ai, flo
     return (y.x + y.y) + (y.z + y.w);
 }
 
-// All rows of one segment handled by this thread's row group, two rows in
-// flight.  Must be called by whole warps (a row group is whole warps).
-template <bool UPDATE>
+// All rows of one segment handled by this thread's row group: four rows in
+// flight, then two, then one.  KQ = column quads per thread (1 or 2).  Must
+// be called by whole warps (a row group is whole warps).
+template <bool UPDATE, int KQ>
 __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, int Q, int N,
                                          const Map& mp, int nthr, int lane,
                                          const float* __restrict__ arow, float* __restrict__ rowpart,
                                          float4 c0v, float4 c1v, float ninvN, float4& cp0, float4& cp1,
                                          float& dmax) {
     const bool h0 = mp.q0 < Q;
-    const bool h1 = mp.kq > 1 && mp.q0 + nthr < Q;
+    const bool h1 = KQ > 1 && mp.q0 + nthr < Q;
     const int c00 = 4 * mp.q0, c01 = 4 * (mp.q0 + nthr);
-    const int stride = mp.RP * Q;
+    const int RP = mp.RP;
+    const int stride = RP * Q;
     int r = mp.grp;
     float4* p = band + (size_t)mp.grp * Q + mp.q0;
-    for (; r + mp.RP < nrows; r += 2 * mp.RP, p += 2 * stride) {
+    for (; r + 3 * RP < nrows; r += 4 * RP, p += 4 * stride) {
+        float a[4], s[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] = UPDATE ? arow[r + k * RP] : 0.f;
+        if (h0) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s[k] += quad_step<UPDATE>(p + k * stride, a[k], c0v, ninvN, c00, N, cp0, dmax);
+        }
+        if (KQ > 1 && h1) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                s[k] += quad_step<UPDATE>(p + k * stride + nthr, a[k], c1v, ninvN, c01, N, cp1, dmax);
+        }
+        // four rows' warp sums in one shuffle tree: bit 4 of the lane picks
+        // rows {0,1} or {2,3}, bit 3 the row within the pair
+        const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
+        float x0 = b4 ? s[2] : s[0], x1 = b4 ? s[3] : s[1];
+        x0 += __shfl_xor_sync(0xffffffffu, b4 ? s[0] : s[2], 16);
+        x1 += __shfl_xor_sync(0xffffffffu, b4 ? s[1] : s[3], 16);
+        float z = b3 ? x1 : x0;
+        z += __shfl_xor_sync(0xffffffffu, b3 ? x0 : x1, 8);
+        z += __shfl_xor_sync(0xffffffffu, z, 4);
+        z += __shfl_xor_sync(0xffffffffu, z, 2);
+        z += __shfl_xor_sync(0xffffffffu, z, 1);
+        if ((lane & 7) == 0) rowpart[(size_t)(r + (2 * (lane >> 4) + ((lane >> 3) & 1)) * RP) * 32] = z;
+    }
+    for (; r + RP < nrows; r += 2 * RP, p += 2 * stride) {
         const float a0 = UPDATE ? arow[r] : 0.f;
-        const float a1 = UPDATE ? arow[r + mp.RP] : 0.f;
+        const float a1 = UPDATE ? arow[r + RP] : 0.f;
         float s0 = 0.f, s1 = 0.f;
         if (h0) {
             s0 += quad_step<UPDATE>(p, a0, c0v, ninvN, c00, N, cp0, dmax);
             s1 += quad_step<UPDATE>(p + stride, a1, c0v, ninvN, c00, N, cp0, dmax);
         }
-        if (h1) {
+        if (KQ > 1 && h1) {
             s0 += quad_step<UPDATE>(p + nthr, a0, c1v, ninvN, c01, N, cp1, dmax);
             s1 += quad_step<UPDATE>(p + stride + nthr, a1, c1v, ninvN, c01, N, cp1, dmax);
         }
@@ -176,13 +204,13 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
         keep += __shfl_xor_sync(0xffffffffu, keep, 2);
         keep += __shfl_xor_sync(0xffffffffu, keep, 1);
         if (lane == 0) rowpart[(size_t)r * 32] = keep;
-        if (lane == 16) rowpart[(size_t)(r + mp.RP) * 32] = keep;
+        if (lane == 16) rowpart[(size_t)(r + RP) * 32] = keep;
     }
     if (r < nrows) {
         const float a0 = UPDATE ? arow[r] : 0.f;
         float s0 = 0.f;
         if (h0) s0 += quad_step<UPDATE>(p, a0, c0v, ninvN, c00, N, cp0, dmax);
-        if (h1) s0 += quad_step<UPDATE>(p + nthr, a0, c1v, ninvN, c01, N, cp1, dmax);
+        if (KQ > 1 && h1) s0 += quad_step<UPDATE>(p + nthr, a0, c1v, ninvN, c01, N, cp1, dmax);
         s0 = warp_sum(s0);
         if (lane == 0) rowpart[(size_t)r * 32] = s0;
     }
@@ -299,9 +327,14 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             float dmax = 0.f;
             if (in_grp) {
                 const int wig = (mp.QP <= nthr) ? ((tid % mp.QP) >> 5) : warp;
-                seg_rows<UPDATE>(reinterpret_cast<float4*>(S.band + sg.soff), sg.nrows, Q, N, mp, nthr,
-                                 lane, S.arow + sg.brow0, S.rowpart + (size_t)sg.brow0 * 32 + wig, c0v,
-                                 c1v, -1.0f / (float)N, cp0, cp1, dmax);
+                float4* bp = reinterpret_cast<float4*>(S.band + sg.soff);
+                float* rp = S.rowpart + (size_t)sg.brow0 * 32 + wig;
+                if (mp.kq == 1)
+                    seg_rows<UPDATE, 1>(bp, sg.nrows, Q, N, mp, nthr, lane, S.arow + sg.brow0, rp, c0v, c1v,
+                                        -1.0f / (float)N, cp0, cp1, dmax);
+                else
+                    seg_rows<UPDATE, 2>(bp, sg.nrows, Q, N, mp, nthr, lane, S.arow + sg.brow0, rp, c0v, c1v,
+                                        -1.0f / (float)N, cp0, cp1, dmax);
             }
             dmax = warp_max(dmax);
             if (lane == 0) S.fred[si * 32 + warp] = dmax;
