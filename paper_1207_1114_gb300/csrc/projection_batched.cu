@@ -30,7 +30,7 @@ struct Seg {
     int group;      // 0 or 1
     int lr0;        // first row of the segment inside its pair
     int nrows;      // rows of the segment
-    int brow0;      // first row of the segment inside the band (rsum/arow index)
+    int brow0;      // first row of the segment inside the band (rsum/rowpart index)
     int soff;       // float offset of the segment's rows in the band storage
     int coff;       // float offset of the segment's c/N vector
     int pad;
@@ -43,7 +43,13 @@ struct PairS {
     unsigned* dbuf;
     double s;       // total of the last finished pass
     int N, ldy;
+    float abase;    // 1/N + s/N^2 of the last finished pass (the row offset is abase - r_i/N)
+    int pad;
+    double invN;    // 1/N
 };
+
+static_assert(sizeof(Seg) == 32, "pdb_smem_bytes assumes 32-byte segments");
+static_assert(sizeof(PairS) == 56, "pdb_smem_bytes assumes 56-byte pair records");
 
 struct Shared {
     Seg* seg;            // kMaxSeg
@@ -54,7 +60,6 @@ struct Shared {
     int* qpref;          // 2 x (kMaxWavePairs + 1): per group, prefix sums of the pairs' column quads
     float* fred;         // kMaxSeg x 32 per-warp maxima
     float* rsum;         // band rows
-    float* arow;         // band rows
     float* rowpart;      // band rows x 32
     float4* cred;        // nthr float4: column-partial reduction across row groups
     float* cN;           // sum over segments of ldy floats: the column sums c_j of the last round
@@ -77,7 +82,6 @@ __device__ __forceinline__ Shared carve_b(char* base, const PdbLayout& L, int nt
     s.qpref = reinterpret_cast<int*>(take(sizeof(int) * 2 * (kMaxWavePairs + 1)));
     s.fred = reinterpret_cast<float*>(take(sizeof(float) * kMaxSeg * 32));
     s.rsum = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_rows));
-    s.arow = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_rows));
     s.rowpart = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_rows * 32));
     s.cred = reinterpret_cast<float4*>(take(sizeof(float4) * nthr));
     s.cN = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_cols));
@@ -109,46 +113,84 @@ __device__ __forceinline__ Map make_map(int Q, int nthr, int tid) {
     return m;
 }
 
+// Two-lane FP32 arithmetic (sm_100 packed f32x2): one instruction updates
+// two floats held in a register pair.
+__device__ __forceinline__ unsigned long long pk(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 upk(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // One column quad of one row: Eq. (P1) with the row offset ai and the
 // column sums c (the offset is c_j / N, folded into one FMA with ninvN =
 // -1/N), then Eq. (P2); columns >= N stay zero.  Returns the quad's
-// contribution to the row sum.
+// contribution to the row sum.  Packed f32x2 arithmetic, two lanes per op.
 template <bool UPDATE>
 __device__ __forceinline__ float quad_step(float4* __restrict__ p, float ai, float4 c, float ninvN, int c0,
                                            int N, float4& cp, float& dmax) {
     float4 y = *p;
     if (UPDATE) {
-        float4 z;
-        z.x = fmaxf(fmaf(ninvN, c.x, y.x + ai), 0.f);
-        z.y = fmaxf(fmaf(ninvN, c.y, y.y + ai), 0.f);
-        z.z = fmaxf(fmaf(ninvN, c.z, y.z + ai), 0.f);
-        z.w = fmaxf(fmaf(ninvN, c.w, y.w + ai), 0.f);
+        const unsigned long long A = pk(ai, ai), NI = pk(ninvN, ninvN);
+        const unsigned long long y01 = pk(y.x, y.y), y23 = pk(y.z, y.w);
+        const float2 u01 = upk(fma2(NI, pk(c.x, c.y), add2(y01, A)));
+        const float2 u23 = upk(fma2(NI, pk(c.z, c.w), add2(y23, A)));
+        float4 z = make_float4(fmaxf(u01.x, 0.f), fmaxf(u01.y, 0.f), fmaxf(u23.x, 0.f), fmaxf(u23.y, 0.f));
         if (c0 + 4 > N) {
             if (c0 + 1 >= N) z.y = 0.f;
             if (c0 + 2 >= N) z.z = 0.f;
             if (c0 + 3 >= N) z.w = 0.f;
         }
-        dmax = fmaxf(dmax, fmaxf(fmaxf(fabsf(z.x - y.x), fabsf(z.y - y.y)),
-                                 fmaxf(fabsf(z.z - y.z), fabsf(z.w - y.w))));
+        const float2 d01 = upk(sub2(pk(z.x, z.y), y01));
+        const float2 d23 = upk(sub2(pk(z.z, z.w), y23));
+        dmax = max3f(dmax, fabsf(d01.x), fabsf(d01.y));
+        dmax = max3f(dmax, fabsf(d23.x), fabsf(d23.y));
         *p = z;
         y = z;
     }
-    cp.x += y.x;
-    cp.y += y.y;
-    cp.z += y.z;
-    cp.w += y.w;
-    return (y.x + y.y) + (y.z + y.w);
+    const float2 c01 = upk(add2(pk(cp.x, cp.y), pk(y.x, y.y)));
+    const float2 c23 = upk(add2(pk(cp.z, cp.w), pk(y.z, y.w)));
+    cp = make_float4(c01.x, c01.y, c23.x, c23.y);
+    const float2 r = upk(add2(pk(y.x, y.y), pk(y.z, y.w)));
+    return r.x + r.y;
 }
 
 // All rows of one segment handled by this thread's row group: four rows in
-// flight, then two, then one.  KQ = column quads per thread (1 or 2).  Must
-// be called by whole warps (a row group is whole warps).
+// flight, then two, then one.  KQ = column quads per thread (1 or 2).  The
+// row offset of Eq. (P1) is abase - r_i / N (one FMA from the row sums of
+// the last pass; abase = 1/N + s/N^2 is formed in FP64 once per pair).
+// Must be called by whole warps (a row group is whole warps).
 template <bool UPDATE, int KQ>
 __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, int Q, int N,
                                          const Map& mp, int nthr, int lane,
-                                         const float* __restrict__ arow, float* __restrict__ rowpart,
-                                         float4 c0v, float4 c1v, float ninvN, float4& cp0, float4& cp1,
-                                         float& dmax) {
+                                         const float* __restrict__ rsum, float abase,
+                                         float* __restrict__ rowpart, float4 c0v, float4 c1v, float ninvN,
+                                         float4& cp0, float4& cp1, float& dmax) {
     const bool h0 = mp.q0 < Q;
     const bool h1 = KQ > 1 && mp.q0 + nthr < Q;
     const int c00 = 4 * mp.q0, c01 = 4 * (mp.q0 + nthr);
@@ -159,7 +201,7 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
     for (; r + 3 * RP < nrows; r += 4 * RP, p += 4 * stride) {
         float a[4], s[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int k = 0; k < 4; ++k) a[k] = UPDATE ? arow[r + k * RP] : 0.f;
+        for (int k = 0; k < 4; ++k) a[k] = UPDATE ? fmaf(ninvN, rsum[r + k * RP], abase) : 0.f;
         if (h0) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) s[k] += quad_step<UPDATE>(p + k * stride, a[k], c0v, ninvN, c00, N, cp0, dmax);
@@ -183,8 +225,8 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
         if ((lane & 7) == 0) rowpart[(size_t)(r + (2 * (lane >> 4) + ((lane >> 3) & 1)) * RP) * 32] = z;
     }
     for (; r + RP < nrows; r += 2 * RP, p += 2 * stride) {
-        const float a0 = UPDATE ? arow[r] : 0.f;
-        const float a1 = UPDATE ? arow[r + RP] : 0.f;
+        const float a0 = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
+        const float a1 = UPDATE ? fmaf(ninvN, rsum[r + RP], abase) : 0.f;
         float s0 = 0.f, s1 = 0.f;
         if (h0) {
             s0 += quad_step<UPDATE>(p, a0, c0v, ninvN, c00, N, cp0, dmax);
@@ -207,7 +249,7 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
         if (lane == 16) rowpart[(size_t)(r + RP) * 32] = keep;
     }
     if (r < nrows) {
-        const float a0 = UPDATE ? arow[r] : 0.f;
+        const float a0 = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
         float s0 = 0.f;
         if (h0) s0 += quad_step<UPDATE>(p, a0, c0v, ninvN, c00, N, cp0, dmax);
         if (KQ > 1 && h1) s0 += quad_step<UPDATE>(p + nthr, a0, c1v, ninvN, c01, N, cp1, dmax);
@@ -275,6 +317,9 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         ps.s = 0.0;
         ps.N = d.N;
         ps.ldy = d.ldy;
+        ps.abase = 0.f;
+        ps.pad = 0;
+        ps.invN = 1.0 / (double)d.N;
         S.pair[p] = ps;
     }
     __syncthreads();
@@ -329,11 +374,12 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 const int wig = (mp.QP <= nthr) ? ((tid % mp.QP) >> 5) : warp;
                 float4* bp = reinterpret_cast<float4*>(S.band + sg.soff);
                 float* rp = S.rowpart + (size_t)sg.brow0 * 32 + wig;
+                const float* rs = S.rsum + sg.brow0;
                 if (mp.kq == 1)
-                    seg_rows<UPDATE, 1>(bp, sg.nrows, Q, N, mp, nthr, lane, S.arow + sg.brow0, rp, c0v, c1v,
+                    seg_rows<UPDATE, 1>(bp, sg.nrows, Q, N, mp, nthr, lane, rs, pr.abase, rp, c0v, c1v,
                                         -1.0f / (float)N, cp0, cp1, dmax);
                 else
-                    seg_rows<UPDATE, 2>(bp, sg.nrows, Q, N, mp, nthr, lane, S.arow + sg.brow0, rp, c0v, c1v,
+                    seg_rows<UPDATE, 2>(bp, sg.nrows, Q, N, mp, nthr, lane, rs, pr.abase, rp, c0v, c1v,
                                         -1.0f / (float)N, cp0, cp1, dmax);
             }
             dmax = warp_max(dmax);
@@ -362,7 +408,34 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
 
     // End of group g's pass: row sums, FP64 totals and maxima of its
     // segments, then arrive at the group's barrier.
-    auto publish = [&](int g, int cur) {
+    // Zero accumulator `which` of group g's pairs with threads t of nt.  The
+    // group's column quads are numbered consecutively over its pairs and
+    // dealt round-robin over the CTAs, so every CTA zeroes about the same few.
+    auto clear_acc = [&](int g, int which, int t, int nt) {
+        const int p0 = g == 0 ? 0 : split, np = (g == 0 ? split : npairs) - p0;
+        const int* qp = S.qpref + g * (kMaxWavePairs + 1);
+        const int total = qp[np];
+        for (int f = t * (int)G + (int)blockIdx.x; f < total; f += nt * (int)G) {
+            int lo = 0, hi = np;   // the pair whose quads hold f: qp[lo] <= f < qp[lo + 1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (qp[mid] <= f) lo = mid; else hi = mid;
+            }
+            const PairS& pr = S.pair[p0 + lo];
+            const int q = f - qp[lo];
+            reinterpret_cast<float4*>(pr.colbuf + (size_t)which * pr.ldy)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q == 0) {
+                pr.sbuf[which] = 0.0;
+                pr.dbuf[which] = 0u;
+            }
+        }
+    };
+
+    // Warps 0 and 1 publish the segments' FP64 totals and round maxima
+    // (alternate segments), while warps 2.. zero accumulator `clear_which`
+    // (>= 0) of the group's pairs; all of it precedes the arrival, so the
+    // zeros are visible before any CTA's next-round reductions.
+    auto publish = [&](int g, int cur, int clear_which) {
         __syncthreads();
         for (int si = 0; si < nseg; ++si) {
             const Seg sg = S.seg[si];
@@ -379,8 +452,8 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             }
         }
         __syncthreads();
-        if (warp == 0) {
-            for (int si = 0; si < nseg; ++si) {
+        if (warp < 2) {
+            for (int si = warp; si < nseg; si += 2) {
                 const Seg sg = S.seg[si];
                 if (sg.group != g) continue;
                 const int pst = S.pstate[sg.pair];
@@ -396,6 +469,8 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                     if (bm > 0.f) atomicMax(pr.dbuf + cur, __float_as_uint(bm));
                 }
             }
+        } else if (clear_which >= 0) {
+            clear_acc(g, clear_which, tid - 64, nthr - 64);
         }
         grid_arrive(&W->bar[g]);
     };
@@ -428,7 +503,9 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                     PairS& pr = S.pair[p];
                     const double s = __ldcg(pr.sbuf + cur);
                     const float dd = __uint_as_float(__ldcg(pr.dbuf + cur));
+                    const double invN = pr.invN;
                     pr.s = s;
+                    pr.abase = (float)(invN + s * invN * invN);
                     if (!isfinite(s)) S.ictl[3] = 1;
                     if (check_stop && ((double)dd < P.tol_inner || u >= P.max_inner)) {
                         ps |= 2;
@@ -441,52 +518,19 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             any = __any_sync(0xffffffffu, any);
             __syncwarp();
             if (lane == 0) S.ictl[g] = any;
-            // offsets a_i = 1/N + s/N^2 - r_i/N of the group's band rows
-            for (int si = 0; si < nseg; ++si) {
-                const Seg sg = S.seg[si];
-                if (sg.group != g || (S.pstate[sg.pair] & 3) != 1) continue;
-                const PairS& pr = S.pair[sg.pair];
-                const double invN = 1.0 / (double)pr.N;
-                const double a_base = invN + pr.s * invN * invN;
-                for (int r = lane; r < sg.nrows; r += 32)
-                    S.arow[sg.brow0 + r] = (float)(a_base - (double)S.rsum[sg.brow0 + r] * invN);
-            }
         }
         cp_async_wait_all();
         __syncthreads();
         return true;
     };
 
-    // Zero accumulator `which` of group g's pairs.  The group's column quads
-    // are numbered consecutively over its pairs and dealt round-robin over
-    // the CTAs, so every CTA zeroes about the same few quads.
-    auto clear_acc = [&](int g, int which) {
-        const int p0 = g == 0 ? 0 : split, np = (g == 0 ? split : npairs) - p0;
-        const int* qp = S.qpref + g * (kMaxWavePairs + 1);
-        const int total = qp[np];
-        for (int f = tid * (int)G + (int)blockIdx.x; f < total; f += nthr * (int)G) {
-            int lo = 0, hi = np;   // the pair whose quads hold f: qp[lo] <= f < qp[lo + 1]
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (qp[mid] <= f) lo = mid; else hi = mid;
-            }
-            const PairS& pr = S.pair[p0 + lo];
-            const int q = f - qp[lo];
-            reinterpret_cast<float4*>(pr.colbuf + (size_t)which * pr.ldy)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (q == 0) {
-                pr.sbuf[which] = 0.0;
-                pr.dbuf[which] = 0u;
-            }
-        }
-    };
-
     // ---- sums of the input of both groups
     const bool has1 = split < npairs;
     pass(0, std::false_type{}, 0);
-    publish(0, 0);
+    publish(0, 0, -1);
     if (has1) {
         pass(1, std::false_type{}, 0);
-        publish(1, 0);
+        publish(1, 0, -1);
     }
     if (!wait_post(0, 0, 0, false)) return;
     if (has1 && !wait_post(1, 0, 0, false)) return;
@@ -501,9 +545,8 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     while (act0 || act1 || pend1) {
         ++u;
         if (act0) {
-            clear_acc(0, (u + 1) % 3);
             pass(0, std::true_type{}, u % 3);
-            publish(0, u % 3);
+            publish(0, u % 3, (u + 1) % 3);
         }
         if (pend1) {
             if (!wait_post(1, (u - 1) % 3, u - 1, true)) return;
@@ -511,9 +554,8 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             pend1 = false;
         }
         if (act1) {
-            clear_acc(1, (u + 1) % 3);
             pass(1, std::true_type{}, u % 3);
-            publish(1, u % 3);
+            publish(1, u % 3, (u + 1) % 3);
             pend1 = true;
         }
         if (act0) {
@@ -612,8 +654,8 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
 
     // ---- per-pair loop control, accumulator clean-up
     for (int b = 0; b < 3; ++b) {
-        clear_acc(0, b);
-        clear_acc(1, b);
+        clear_acc(0, b, tid, nthr);
+        clear_acc(1, b, tid, nthr);
     }
     if (blockIdx.x == 0) {
         for (int p = tid; p < npairs; p += nthr) {
@@ -669,13 +711,12 @@ size_t pdb_smem_bytes(const PdbLayout& L, int nthr) {
     size_t off = 0;
     auto take = [&](size_t bytes) { off = (off + bytes + 15) & ~size_t(15); };
     take(32 * kMaxSeg);               // Seg is eight ints
-    take(40 * kMaxWavePairs);         // PairS: three pointers, a double, two ints
+    take(56 * kMaxWavePairs);         // PairS: three pointers, a double, two ints, a float, pad, a double
     take(4 * kMaxWavePairs);
     take(4 * kMaxWavePairs);
     take(4 * 4);
     take(4 * 2 * (kMaxWavePairs + 1));
     take(4 * kMaxSeg * 32);
-    take(4 * (size_t)L.max_band_rows);
     take(4 * (size_t)L.max_band_rows);
     take(4 * (size_t)L.max_band_rows * 32);
     take(16 * (size_t)nthr);
