@@ -42,6 +42,7 @@ constexpr size_t kCtrlHeader = offsetof(Ctrl, inner_trace);
 constexpr int kProfIters = 128;                   // outer iterations timed when profile = 1
 constexpr int kProfEvents = 2 * kProfIters + 3;   // iteration boundaries + discretisation
 constexpr int kChunk = 4;                         // outer iterations enqueued between checks
+constexpr size_t kTraceBytes = (size_t)kMaxOuterTrace * (sizeof(int) + sizeof(double));
 constexpr long long kMinElemsPerCta = 8192;       // smallest band worth a CTA of its own
 // Two interleaved pair groups per wave (one group's barrier hidden behind the
 // other's round).  Measured slower on GB300 at n = 1000 (17.3 vs 11.8 us per
@@ -81,8 +82,10 @@ struct fastpfp_s {
     int* h_band = nullptr;
     int* h_done = nullptr;       // pinned, 2 x 4 words: stop flags read one chunk behind
     Ctrl* host_ctrl = nullptr;   // pinned, max_batch control-block headers
-    int last_first = 0;          // pairs [last_first, last_first + last_count) of the last call
-    int last_count = 0;          // still hold their traces in slots 0, 1, ...
+    int last_count = 0;          // pairs of the last call; their traces are in trace_store
+    char* trace_store = nullptr; // device, max_batch x kTraceBytes: per-pair inner counts and deltas
+    int* d_flags = nullptr;      // device, kMaxWavePairs + 1 stop/error words of a streamed wave
+    int* h_flags = nullptr;      // pinned copy of d_flags
 
     cudaEvent_t ev[kProfEvents] = {};
     cudaEvent_t chunk_ev[2] = {};
@@ -218,7 +221,8 @@ struct TcPlan {
     std::vector<TcGroup> g1, g2;
 };
 
-bool plan_tc(fastpfp_t h, const Problem* qs, int count, const fastpfp_params* p, TcPlan* plan) {
+bool plan_tc(fastpfp_t h, const Problem* qs, int count, const fastpfp_params* p, TcPlan* plan,
+             const int* slot_of = nullptr) {
     plan->g1.clear();
     plan->g2.clear();
     for (int b = 0; b < count; b += kTcMaxGroup) {
@@ -229,7 +233,7 @@ bool plan_tc(fastpfp_t h, const Problem* qs, int count, const fastpfp_params* p,
         c.mode = kTcOutF32;
         for (int i = 0; i < n; ++i) {
             const Problem& q = qs[b + i];
-            const Slot& sl = h->slots[b + i];
+            const Slot& sl = h->slots[slot_of ? slot_of[b + i] : b + i];
             const int l16N = round8(q.N), l16m = round8(q.m);
             if (!tc_make_map(&a.map_a[i], sl.A16, q.N, q.N, l16N) ||
                 !tc_make_map(&a.map_b[i], sl.Xt16, q.m, q.N, l16N) ||
@@ -591,7 +595,9 @@ bool plan_bands(const std::vector<Problem>& qs, int first, int count, int num_sm
         const int u0 = split_group(qs, first, split, Gmax, seg_cost, b0.data(), s0);
         const int u1 = split_group(qs, first + split, count - split, Gmax, seg_cost, b1.data(), s1);
         const int G = std::max(1, std::max(u0, u1));
-        PdbLayout L{0, 0, 0};
+        PdbLayout L{0, 0, 0, 1};
+        for (int i = 0; i < count; ++i)
+            L.rp_stride = std::max(L.rp_stride, pdb_row_warps(round4(qs[first + i].N), kPdbThreads));
         bool ok = true;
         for (int b = 0; b < G; ++b) {
             L.max_band_rows = std::max(L.max_band_rows, s0[b].rows + s1[b].rows);
@@ -631,20 +637,22 @@ bool plan_wave(const std::vector<Problem>& qs, int first, int nslots, int num_sm
     return best > 0;
 }
 
-// One wave through pdb_kernel.  Returns the kernels launched or < 0.
-int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, const Wave& w,
-                 const fastpfp_params* p, Ctrl* host_slots) {
-    int nl = 0;
+// A pair of a wave and the slot whose buffers it uses.
+struct Member {
+    int pair;
+    int slot;
+    int last = -1;   // streamed waves: the launch that last ran the pair
+};
+
+// Wave tables of members mem (pair table in member order, band table of w)
+// staged through pinned memory, the wave control word cleared.  The pinned
+// staging is reused by the next wave, so callers synchronise in between.
+int write_wave_tables(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs,
+                      const std::vector<Member>& mem, const Wave& w, bool bf16) {
     int row0 = 0;
-    const bool bf16 = p->precision == FASTPFP_BF16;
-    TcPlan tc;
-    if (bf16 && !plan_tc(h, &qs[w.first], w.count, p, &tc)) return FASTPFP_ERR_UNSUPPORTED;
-    for (int i = 0; i < w.count; ++i) {
-        const Problem& q = qs[w.first + i];
-        const Slot& sl = h->slots[i];
-        const int r = enqueue_setup(sl, s, q, p, h->ld);
-        if (r < 0) return r;
-        nl += r;
+    for (int i = 0; i < (int)mem.size(); ++i) {
+        const Problem& q = qs[mem[i].pair];
+        const Slot& sl = h->slots[mem[i].slot];
         PairDesc d{};
         d.Y = sl.Y;
         d.X = sl.X;
@@ -664,12 +672,16 @@ int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, co
         h->h_pairs[i] = d;
     }
     for (int b = 0; b < 2 * (w.grid + 1); ++b) h->h_band[b] = w.band[b];
-    FP_CUDA(cudaMemcpyAsync(h->d_pairs, h->h_pairs, sizeof(PairDesc) * w.count, cudaMemcpyHostToDevice, s));
+    FP_CUDA(cudaMemcpyAsync(h->d_pairs, h->h_pairs, sizeof(PairDesc) * mem.size(), cudaMemcpyHostToDevice, s));
     FP_CUDA(cudaMemcpyAsync(h->d_band, h->h_band, sizeof(int) * 2 * (w.grid + 1), cudaMemcpyHostToDevice, s));
     FP_CUDA(cudaMemsetAsync(h->d_wave, 0, sizeof(WaveCtrl), s));
+    return 0;
+}
+
+PdbParams wave_params(fastpfp_t h, const Wave& w, int npairs, const fastpfp_params* p) {
     PdbParams P{};
     P.pairs = h->d_pairs;
-    P.npairs = w.count;
+    P.npairs = npairs;
     P.split = w.split;
     P.band_row = h->d_band;
     P.wave = h->d_wave;
@@ -684,22 +696,63 @@ int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, co
     P.refine_iters = p->refine_iters;
     P.switch_tol = p->switch_tol;
     P.timeout_ns = timeout_ns(p);
-    // FP32 products of every pair of the wave: one grouped launch per product
-    std::vector<GemmF32Group> f32a, f32b;
-    for (int b = 0; b < w.count; b += kF32MaxGroup) {
+    return P;
+}
+
+// FP32 products of every member: one grouped launch per product and
+// kF32MaxGroup members.
+void f32_groups(fastpfp_t h, const std::vector<Problem>& qs, const std::vector<Member>& mem,
+                const fastpfp_params* p, std::vector<GemmF32Group>& ga_out, std::vector<GemmF32Group>& gb_out) {
+    ga_out.clear();
+    gb_out.clear();
+    for (int b = 0; b < (int)mem.size(); b += kF32MaxGroup) {
         GemmF32Group ga{}, gb{};
-        ga.count = gb.count = std::min(kF32MaxGroup, w.count - b);
+        ga.count = gb.count = std::min(kF32MaxGroup, (int)mem.size() - b);
         for (int i = 0; i < ga.count; ++i) {
-            const Problem& q = qs[w.first + b + i];
-            const Slot& sl = h->slots[b + i];
+            const Problem& q = qs[mem[b + i].pair];
+            const Slot& sl = h->slots[mem[b + i].slot];
             const int ldy = round4(q.N), ldx = round4(q.m);
             ga.a[i] = GemmF32Args{q.A, q.N, sl.X, ldx, sl.T, ldx, nullptr, 0, 0.f, q.N, q.m, q.N, sl.ctrl};
             gb.a[i] = GemmF32Args{sl.T, ldx, q.A2, q.m, sl.Y, ldy, q.k ? sl.K : nullptr, ldx,
                                   q.k ? (float)p->lambda : 0.f, q.N, q.m, q.m, sl.ctrl};
         }
-        f32a.push_back(ga);
-        f32b.push_back(gb);
+        ga_out.push_back(ga);
+        gb_out.push_back(gb);
     }
+}
+
+// The inner-round counts and deltas of the pair in `slot`, kept per pair
+// of the call (the slot may be reused by a later pair).
+int save_trace(fastpfp_t h, cudaStream_t s, int slot, int pair, int max_outer) {
+    const Ctrl* c = h->slots[slot].ctrl;
+    char* dst = h->trace_store + (size_t)pair * kTraceBytes;
+    const size_t n = (size_t)std::min(max_outer, kMaxOuterTrace);
+    FP_CUDA(cudaMemcpyAsync(dst, c->inner_trace, n * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    FP_CUDA(cudaMemcpyAsync(dst + (size_t)kMaxOuterTrace * sizeof(int), c->delta_trace, n * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s));
+    return 0;
+}
+
+// One wave through pdb_kernel, the loop controlled as run_outer says; pair
+// w.first + i uses slot i.  Returns the kernels launched or < 0.
+int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, const Wave& w,
+                 const fastpfp_params* p, Ctrl* host_slots) {
+    int nl = 0;
+    const bool bf16 = p->precision == FASTPFP_BF16;
+    std::vector<Member> mem(w.count);
+    for (int i = 0; i < w.count; ++i) mem[i] = Member{w.first + i, i};
+    TcPlan tc;
+    if (bf16 && !plan_tc(h, &qs[w.first], w.count, p, &tc)) return FASTPFP_ERR_UNSUPPORTED;
+    for (int i = 0; i < w.count; ++i) {
+        const int r = enqueue_setup(h->slots[i], s, qs[w.first + i], p, h->ld);
+        if (r < 0) return r;
+        nl += r;
+    }
+    const int wt = write_wave_tables(h, s, qs, mem, w, bf16);
+    if (wt < 0) return wt;
+    const PdbParams P = wave_params(h, w, w.count, p);
+    std::vector<GemmF32Group> f32a, f32b;
+    f32_groups(h, qs, mem, p, f32a, f32b);
     const bool prof = p->profile != 0;
     static_assert(offsetof(WaveCtrl, error) == 0 && offsetof(WaveCtrl, all_done) == 4,
                   "WaveCtrl layout");
@@ -727,6 +780,8 @@ int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, co
         const int f = enqueue_finish(h->slots[i], s, qs[w.first + i], p, h->num_sms, &host_slots[i]);
         if (f < 0) return f;
         nl += f;
+        const int tr = save_trace(h, s, i, w.first + i, p->max_outer);
+        if (tr < 0) return tr;
     }
     if (prof) FP_CUDA(cudaEventRecord(h->ev[kProfEvents - 1], s));
     return nl;
@@ -814,6 +869,8 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     const size_t oband = take(sizeof(int) * 2 * (h->num_sms + 1));
     const size_t owave = take(sizeof(WaveCtrl));
     const size_t oloop = take(sizeof(int));
+    const size_t oflags = take(sizeof(int) * (kMaxWavePairs + 1));
+    const size_t otrace = take((size_t)max_batch * kTraceBytes);
     const size_t nch = (n + 63) / 64;
     const size_t wFb = take(n * kMlpIn * 4), wFs = take(n * kMlpIn * 4), wHb = take(n * kMlpHidden * 4),
                  wHs = take(n * kMlpHidden * 4), wEb = take(n * kMlpOut * 4), wEs = take(n * kMlpOut * 4),
@@ -831,6 +888,7 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
         if (h->h_pairs) cudaFreeHost(h->h_pairs);
         if (h->h_band) cudaFreeHost(h->h_band);
         if (h->h_done) cudaFreeHost(h->h_done);
+        if (h->h_flags) cudaFreeHost(h->h_flags);
         if (h->cap) cudaStreamDestroy(h->cap);
         if (h->pool) cudaFree(h->pool);
         delete h;
@@ -841,6 +899,7 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
         cudaMallocHost(&h->h_pairs, sizeof(PairDesc) * kMaxWavePairs) != cudaSuccess ||
         cudaMallocHost(&h->h_band, sizeof(int) * 2 * (h->num_sms + 1)) != cudaSuccess ||
         cudaMallocHost(&h->h_done, sizeof(int) * 8) != cudaSuccess ||
+        cudaMallocHost(&h->h_flags, sizeof(int) * (kMaxWavePairs + 1)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
         return fail(FASTPFP_ERR_CUDA);
     char* b = h->pool;
@@ -876,6 +935,8 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     h->d_band = (int*)(b + oband);
     h->d_wave = (WaveCtrl*)(b + owave);
     h->d_loop = (int*)(b + oloop);
+    h->d_flags = (int*)(b + oflags);
+    h->trace_store = b + otrace;
     h->ws.Fb = (float*)(b + wFb);
     h->ws.Fs = (float*)(b + wFs);
     h->ws.Hb = (float*)(b + wHb);
@@ -920,6 +981,7 @@ void fastpfp_destroy(fastpfp_t h) {
     if (h->h_pairs) cudaFreeHost(h->h_pairs);
     if (h->h_band) cudaFreeHost(h->h_band);
     if (h->h_done) cudaFreeHost(h->h_done);
+    if (h->h_flags) cudaFreeHost(h->h_flags);
     if (h->cap) cudaStreamDestroy(h->cap);
     if (h->pool) cudaFree(h->pool);
     delete h;
@@ -980,87 +1042,280 @@ namespace {
 // The batch driver of fastpfp_match_batched (device memory) and of the
 // *_host calls (host memory: each wave's inputs are staged into its slots
 // and the outputs copied back before the next wave).
+// Host-memory inputs of pair x staged into `slot`; *q is rewritten to
+// point at the staged copies (caller orientation preserved).
+int stage_in(fastpfp_t h, cudaStream_t s, const fastpfp_pair& x, const fastpfp_params* p, int slot,
+             Problem* q) {
+    const Slot& sl = h->slots[slot];
+    const int kk = (x.k > 0 && p->lambda != 0.f) ? x.k : 0;
+    FP_CUDA(cudaMemcpyAsync(sl.sA, x.A, (size_t)x.n_a * x.n_a * 4, cudaMemcpyHostToDevice, s));
+    FP_CUDA(cudaMemcpyAsync(sl.sA2, x.A2, (size_t)x.n_b * x.n_b * 4, cudaMemcpyHostToDevice, s));
+    if (kk) {
+        FP_CUDA(cudaMemcpyAsync(sl.sB, x.B, (size_t)x.n_a * kk * 4, cudaMemcpyHostToDevice, s));
+        FP_CUDA(cudaMemcpyAsync(sl.sB2, x.B2, (size_t)x.n_b * kk * 4, cudaMemcpyHostToDevice, s));
+    }
+    if (x.X0) FP_CUDA(cudaMemcpyAsync(sl.sX0, x.X0, (size_t)x.n_a * x.n_b * 4, cudaMemcpyHostToDevice, s));
+    *q = canonical(sl.sA, x.n_a, sl.sA2, x.n_b, kk ? sl.sB : nullptr, kk ? sl.sB2 : nullptr, kk, p->lambda,
+                   x.X0 ? sl.sX0 : nullptr, sl.sperm, x.X_out ? sl.sXout : nullptr);
+    return 0;
+}
+
+// Staged outputs of the pair in `slot` copied back to host memory.
+int stage_out(fastpfp_t h, cudaStream_t s, const fastpfp_pair& x, int slot) {
+    const Slot& sl = h->slots[slot];
+    FP_CUDA(cudaMemcpyAsync(x.perm_out, sl.sperm, (size_t)x.n_a * 4, cudaMemcpyDeviceToHost, s));
+    if (x.X_out)
+        FP_CUDA(cudaMemcpyAsync(x.X_out, sl.sXout, (size_t)x.n_a * x.n_b * 4, cudaMemcpyDeviceToHost, s));
+    return 0;
+}
+
+// Continuous batching for batches that do not fit in one wave.  A wave is
+// kept full: after every outer iteration (one pdb_kernel launch over the
+// wave's active pairs and their grouped products) the host reads the pairs'
+// stop words, finishes the pairs that stopped (discretisation, objective,
+// outputs) and admits waiting pairs into the freed slots while the wave's
+// band plan still fits on chip.  Each pair's iterations are independent of
+// its wave-mates, so the result of a pair does not depend on the schedule
+// beyond FP32 summation order.  Returns the worst status.
+int solve_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, const fastpfp_pair* pairs,
+                 const fastpfp_params* p, fastpfp_stats* st, bool host) {
+    const int count = (int)qs.size();
+    const bool bf16 = p->precision == FASTPFP_BF16;
+    const bool prof = p->profile != 0;
+    std::vector<int> free_slots;
+    for (int i = h->nslots - 1; i >= 0; --i) free_slots.push_back(i);
+    std::vector<Member> act;
+    std::vector<int> nl(count, 0), wave_of(count, 0), werr_of(count, 0);
+    std::vector<float> ms_g(count, 0.f), ms_p(count, 0.f);
+    int next = 0;
+    auto fail = [&](int code) {
+        cudaStreamSynchronize(s);
+        return code;
+    };
+    auto problems_of = [&](const std::vector<Member>& m, std::vector<Problem>& out, std::vector<int>& slots) {
+        out.clear();
+        slots.clear();
+        for (const Member& x : m) {
+            out.push_back(qs[x.pair]);
+            slots.push_back(x.slot);
+        }
+    };
+    std::vector<Problem> cand;
+    std::vector<int> cand_slots;
+    std::vector<GemmF32Group> f32a, f32b;
+    int launch_no = 0;
+    while (true) {
+        // admit waiting pairs while the wave still fits on chip
+        Wave w;
+        bool planned = false;
+        while (next < count && !free_slots.empty() && (int)act.size() < kMaxWavePairs &&
+               qs[next].N <= kPdbMaxN) {
+            problems_of(act, cand, cand_slots);
+            cand.push_back(qs[next]);
+            Wave cw;
+            if (!plan_bands(cand, 0, (int)cand.size(), h->num_sms, &cw)) break;
+            const int slot = free_slots.back();
+            free_slots.pop_back();
+            if (host) {
+                const int r = stage_in(h, s, pairs[next], p, slot, &qs[next]);
+                if (r < 0) return fail(r);
+            }
+            const int r = enqueue_setup(h->slots[slot], s, qs[next], p, h->ld);
+            if (r < 0) return fail(r);
+            nl[next] += r;
+            act.push_back(Member{next, slot, -1});
+            ++next;
+            w = cw;
+            planned = true;
+        }
+        if (act.empty()) {
+            if (next >= count) break;
+            // a pair that fits in no wave runs alone through pd_kernel
+            const int slot = free_slots.back();
+            if (host) {
+                const int r = stage_in(h, s, pairs[next], p, slot, &qs[next]);
+                if (r < 0) return fail(r);
+            }
+            const int r = enqueue_single(h, s, h->slots[slot], qs[next], p, &h->host_ctrl[next]);
+            if (r < 0) return fail(r);
+            nl[next] += r;
+            if (save_trace(h, s, slot, next, p->max_outer) < 0) return fail(FASTPFP_ERR_CUDA);
+            if (host && stage_out(h, s, pairs[next], slot) < 0) return fail(FASTPFP_ERR_CUDA);
+            if (cudaStreamSynchronize(s) != cudaSuccess) return FASTPFP_ERR_CUDA;
+            if (h->loop_body > 0) {
+                int it = 0;
+                FP_CUDA(cudaMemcpy(&it, h->d_loop, sizeof(int), cudaMemcpyDeviceToHost));
+                nl[next] += 1 + h->loop_body * it;
+            }
+            release_graphs(h);
+            ++next;
+            continue;
+        }
+        // the pairs of this launch: every active pair when they fit on chip
+        // together, else as many as fit, least recently run first (a pair
+        // left out simply waits: its state is in its slot)
+        std::vector<Member> run;
+        problems_of(act, cand, cand_slots);
+        if (planned || plan_bands(cand, 0, (int)cand.size(), h->num_sms, &w)) {
+            run = act;
+        } else {
+            std::vector<Member> order = act;
+            std::stable_sort(order.begin(), order.end(),
+                             [](const Member& a, const Member& b) { return a.last < b.last; });
+            std::vector<Member> trial;
+            for (const Member& m : order) {
+                trial = run;
+                trial.push_back(m);
+                problems_of(trial, cand, cand_slots);
+                Wave tw;
+                if (!plan_bands(cand, 0, (int)cand.size(), h->num_sms, &tw)) continue;
+                run = trial;
+                w = tw;
+            }
+            if (run.empty()) return fail(FASTPFP_ERR_UNSUPPORTED);
+            problems_of(run, cand, cand_slots);
+        }
+        ++launch_no;
+        // one outer iteration of the wave
+        const int n = (int)run.size();
+        if (write_wave_tables(h, s, qs, run, w, bf16) < 0) return fail(FASTPFP_ERR_CUDA);
+        const PdbParams P = wave_params(h, w, n, p);
+        TcPlan tc;
+        if (bf16 && !plan_tc(h, cand.data(), n, p, &tc, cand_slots.data())) return fail(FASTPFP_ERR_UNSUPPORTED);
+        f32_groups(h, qs, run, p, f32a, f32b);
+        int kl = 0;
+        if (prof && cudaEventRecord(h->ev[0], s) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
+        if (bf16) {
+            const int r = enqueue_tc(tc, s);
+            if (r < 0) return fail(r);
+            kl += r;
+        }
+        for (const GemmF32Group& g : f32a)
+            if (gemm_f32_group(g, s) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
+        for (const GemmF32Group& g : f32b)
+            if (gemm_f32_group(g, s) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
+        kl += (int)(f32a.size() + f32b.size());
+        if (prof && cudaEventRecord(h->ev[1], s) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
+        if (pdb_launch(P, w.grid, w.smem, s) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
+        if (prof && cudaEventRecord(h->ev[2], s) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
+        FlagList fl{};
+        for (int i = 0; i < n; ++i) fl.ctrl[i] = h->slots[run[i].slot].ctrl;
+        fl.wave = h->d_wave;
+        fl.n = n;
+        if (gather_flags(fl, h->d_flags, s) != cudaSuccess ||
+            cudaMemcpyAsync(h->h_flags, h->d_flags, sizeof(int) * (kMaxWavePairs + 1), cudaMemcpyDeviceToHost,
+                            s) != cudaSuccess)
+            return fail(FASTPFP_ERR_CUDA);
+        kl += 2;   // the flag gather and the pdb launch
+        if (cudaStreamSynchronize(s) != cudaSuccess) return FASTPFP_ERR_CUDA;
+        float tg = 0.f, tp = 0.f;
+        if (prof) {
+            cudaEventElapsedTime(&tg, h->ev[0], h->ev[1]);
+            cudaEventElapsedTime(&tp, h->ev[1], h->ev[2]);
+        }
+        const int werr = h->h_flags[kMaxWavePairs];
+        std::vector<int> stopped(count, 0);
+        for (int i = 0; i < n; ++i) {
+            const Member& m = run[i];
+            nl[m.pair] += kl / n + (i < kl % n ? 1 : 0);
+            ms_g[m.pair] += tg / (float)n;
+            ms_p[m.pair] += tp / (float)n;
+            wave_of[m.pair] = std::max(wave_of[m.pair], n);
+            if ((h->h_flags[i] & 3) == 0 && werr == 0) continue;
+            stopped[m.pair] = 1;
+            // an error of the shared launch belongs to every pair of the wave
+            if (werr != 0) werr_of[m.pair] = werr;
+            const int f = enqueue_finish(h->slots[m.slot], s, qs[m.pair], p, h->num_sms, &h->host_ctrl[m.pair]);
+            if (f < 0) return fail(f);
+            nl[m.pair] += f;
+            if (save_trace(h, s, m.slot, m.pair, p->max_outer) < 0) return fail(FASTPFP_ERR_CUDA);
+            if (host && stage_out(h, s, pairs[m.pair], m.slot) < 0) return fail(FASTPFP_ERR_CUDA);
+            free_slots.push_back(m.slot);
+        }
+        std::vector<Member> keep;
+        for (Member m : act) {
+            if (stopped[m.pair]) continue;
+            for (const Member& r : run)
+                if (r.pair == m.pair) m.last = launch_no;
+            keep.push_back(m);
+        }
+        act.swap(keep);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FASTPFP_ERR_CUDA;
+    int worst = FASTPFP_OK;
+    for (int b = 0; b < count; ++b) {
+        if (werr_of[b] != 0 && h->host_ctrl[b].error == 0) h->host_ctrl[b].error = werr_of[b];
+        fastpfp_stats* sb = st ? &st[b] : nullptr;
+        const int rc = fill_stats(h->host_ctrl[b], qs[b].transposed, nl[b], wave_of[b], sb);
+        if (sb && prof) {
+            sb->ms_gemm = ms_g[b];
+            sb->ms_proj = ms_p[b];
+            sb->ms_disc = 0.f;
+        }
+        if (rc != FASTPFP_OK && worst == FASTPFP_OK) worst = rc;
+    }
+    h->last_count = count;
+    return worst;
+}
+
 int solve_batch(fastpfp_t h, cudaStream_t s, int count, const fastpfp_pair* pairs,
                 const fastpfp_params* p, fastpfp_stats* st, bool host) {
     std::vector<Problem> qs(count);
     for (int b = 0; b < count; ++b) {
         const fastpfp_pair& x = pairs[b];
-        qs[b] = canonical(x.A, x.n_a, x.A2, x.n_b, x.B, x.B2, x.k, p->lambda, x.X0, x.perm_out,
-                          x.X_out);
+        qs[b] = canonical(x.A, x.n_a, x.A2, x.n_b, x.B, x.B2, x.k, p->lambda, x.X0, x.perm_out, x.X_out);
+    }
+    // a batch that fits in one wave runs as one wave (its loop on the device);
+    // a larger one is streamed through waves kept full by the host
+    Wave w;
+    const bool batched = count > 1 && plan_wave(qs, 0, h->nslots, h->num_sms, &w);
+    if (count > 1 && (!batched || w.count < count)) return solve_stream(h, s, qs, pairs, p, st, host);
+    const int cnt = batched ? w.count : 1;
+    if (host)
+        for (int i = 0; i < cnt; ++i) {
+            const int r = stage_in(h, s, pairs[i], p, i, &qs[i]);
+            if (r < 0) return r;
+        }
+    int nl = batched ? enqueue_wave(h, s, qs, w, p, h->host_ctrl)
+                     : enqueue_single(h, s, h->slots[0], qs[0], p, &h->host_ctrl[0]);
+    if (nl >= 0 && !batched) {
+        const int r = save_trace(h, s, 0, 0, p->max_outer);
+        if (r < 0) nl = r;
+    }
+    if (nl < 0) {
+        cudaStreamSynchronize(s);
+        release_graphs(h);
+        return nl;
+    }
+    if (host)
+        for (int i = 0; i < cnt; ++i)
+            if (stage_out(h, s, pairs[i], i) < 0) return FASTPFP_ERR_CUDA;
+    const cudaError_t es = cudaStreamSynchronize(s);
+    int loop_iters = 0;
+    if (es == cudaSuccess && h->loop_body > 0)
+        FP_CUDA(cudaMemcpy(&loop_iters, h->d_loop, sizeof(int), cudaMemcpyDeviceToHost));
+    release_graphs(h);
+    if (es != cudaSuccess) return FASTPFP_ERR_CUDA;
+    if (h->loop_body > 0) nl += 1 + h->loop_body * loop_iters;   // loop_init + iterations
+    if (batched) {
+        // an error of the shared projection launch belongs to every pair of the wave
+        WaveCtrl wc{};
+        FP_CUDA(cudaMemcpy(&wc, h->d_wave, sizeof(WaveCtrl), cudaMemcpyDeviceToHost));
+        if (wc.error != 0)
+            for (int i = 0; i < cnt; ++i)
+                if (h->host_ctrl[i].error == 0) h->host_ctrl[i].error = wc.error;
     }
     int worst = FASTPFP_OK;
-    int b = 0;
-    while (b < count) {
-        Wave w;
-        // a lone pair takes the single-pair kernel, as fastpfp_match does
-        const bool batched = count > 1 && plan_wave(qs, b, h->nslots, h->num_sms, &w);
-        const int cnt = batched ? w.count : 1;
-        if (host) {
-            for (int i = 0; i < cnt; ++i) {
-                const fastpfp_pair& x = pairs[b + i];
-                const Slot& sl = h->slots[i];
-                const int kk = (x.k > 0 && p->lambda != 0.f) ? x.k : 0;
-                FP_CUDA(cudaMemcpyAsync(sl.sA, x.A, (size_t)x.n_a * x.n_a * 4, cudaMemcpyHostToDevice, s));
-                FP_CUDA(cudaMemcpyAsync(sl.sA2, x.A2, (size_t)x.n_b * x.n_b * 4, cudaMemcpyHostToDevice, s));
-                if (kk) {
-                    FP_CUDA(cudaMemcpyAsync(sl.sB, x.B, (size_t)x.n_a * kk * 4, cudaMemcpyHostToDevice, s));
-                    FP_CUDA(cudaMemcpyAsync(sl.sB2, x.B2, (size_t)x.n_b * kk * 4, cudaMemcpyHostToDevice, s));
-                }
-                if (x.X0)
-                    FP_CUDA(cudaMemcpyAsync(sl.sX0, x.X0, (size_t)x.n_a * x.n_b * 4, cudaMemcpyHostToDevice, s));
-                qs[b + i] = canonical(sl.sA, x.n_a, sl.sA2, x.n_b, kk ? sl.sB : nullptr, kk ? sl.sB2 : nullptr,
-                                      kk, p->lambda, x.X0 ? sl.sX0 : nullptr, sl.sperm,
-                                      x.X_out ? sl.sXout : nullptr);
-            }
-        }
-        int nl = batched ? enqueue_wave(h, s, qs, w, p, &h->host_ctrl[b])
-                               : enqueue_single(h, s, h->slots[0], qs[b], p, &h->host_ctrl[b]);
-        if (nl < 0) {
-            cudaStreamSynchronize(s);
-            release_graphs(h);
-            return nl;
-        }
-        if (host) {
-            for (int i = 0; i < cnt; ++i) {
-                const fastpfp_pair& x = pairs[b + i];
-                const Slot& sl = h->slots[i];
-                FP_CUDA(cudaMemcpyAsync(x.perm_out, sl.sperm, (size_t)x.n_a * 4, cudaMemcpyDeviceToHost, s));
-                if (x.X_out)
-                    FP_CUDA(cudaMemcpyAsync(x.X_out, sl.sXout, (size_t)x.n_a * x.n_b * 4,
-                                            cudaMemcpyDeviceToHost, s));
-            }
-        }
-        // the wave tables and the profiling events are reused by the next wave
-        const cudaError_t es = cudaStreamSynchronize(s);
-        int loop_iters = 0;
-        if (es == cudaSuccess && h->loop_body > 0)
-            FP_CUDA(cudaMemcpy(&loop_iters, h->d_loop, sizeof(int), cudaMemcpyDeviceToHost));
-        release_graphs(h);
-        if (es != cudaSuccess) return FASTPFP_ERR_CUDA;
-        if (h->loop_body > 0) nl += 1 + h->loop_body * loop_iters;   // loop_init + iterations
-        if (batched) {
-            // an error of the shared projection launch belongs to every pair of the wave
-            WaveCtrl wc{};
-            FP_CUDA(cudaMemcpy(&wc, h->d_wave, sizeof(WaveCtrl), cudaMemcpyDeviceToHost));
-            if (wc.error != 0)
-                for (int i = 0; i < cnt; ++i)
-                    if (h->host_ctrl[b + i].error == 0) h->host_ctrl[b + i].error = wc.error;
-        }
-        for (int i = 0; i < cnt; ++i) {
-            const int launches = nl / cnt + (i == 0 ? nl % cnt : 0);
-            int rc = fill_stats(h->host_ctrl[b + i], qs[b + i].transposed, launches,
-                                batched ? cnt : 0, st ? &st[b + i] : nullptr);
-            if (st && p->profile) {
-                int outer = 0;
-                for (int j = 0; j < cnt; ++j) outer = std::max(outer, h->host_ctrl[b + j].outer);
-                read_profile(h, outer, 1.0f / (float)cnt, &st[b + i]);
-            }
-            if (rc != FASTPFP_OK && worst == FASTPFP_OK) worst = rc;
-        }
-        h->last_first = b;
-        h->last_count = cnt;
-        b += cnt;
+    int outer = 0;
+    for (int j = 0; j < cnt; ++j) outer = std::max(outer, h->host_ctrl[j].outer);
+    for (int i = 0; i < cnt; ++i) {
+        const int launches = nl / cnt + (i == 0 ? nl % cnt : 0);
+        const int rc = fill_stats(h->host_ctrl[i], qs[i].transposed, launches, batched ? cnt : 0,
+                                  st ? &st[i] : nullptr);
+        if (st && p->profile) read_profile(h, outer, 1.0f / (float)cnt, &st[i]);
+        if (rc != FASTPFP_OK && worst == FASTPFP_OK) worst = rc;
     }
+    h->last_count = cnt;
     return worst;
 }
 
@@ -1070,16 +1325,16 @@ extern "C" {
 
 int fastpfp_last_trace(fastpfp_t h, int pair, int* inner_counts, double* deltas, int cap) {
     if (!h || cap < 0) return FASTPFP_ERR_ARG;
-    const int i = pair - h->last_first;
-    if (i < 0 || i >= h->last_count) return FASTPFP_ERR_ARG;
+    if (pair < 0 || pair >= h->last_count) return FASTPFP_ERR_ARG;
     if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
     const int outer = h->host_ctrl[pair].outer;
-    const int n = outer < cap ? outer : cap;
-    const Ctrl* c = h->slots[i].ctrl;
+    const int n = std::min(std::min(outer, cap), kMaxOuterTrace);
+    const char* src = h->trace_store + (size_t)pair * kTraceBytes;
     if (n > 0 && inner_counts)
-        FP_CUDA(cudaMemcpy(inner_counts, c->inner_trace, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost));
+        FP_CUDA(cudaMemcpy(inner_counts, src, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost));
     if (n > 0 && deltas)
-        FP_CUDA(cudaMemcpy(deltas, c->delta_trace, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost));
+        FP_CUDA(cudaMemcpy(deltas, src + (size_t)kMaxOuterTrace * sizeof(int), (size_t)n * sizeof(double),
+                           cudaMemcpyDeviceToHost));
     return outer;
 }
 

@@ -87,7 +87,16 @@ struct PdbLayout {
     int max_band_rows;    // rows of the largest band
     int max_band_cols;    // sum of ldy over the segments of one band
     int max_band_elems;   // floats of the largest band
+    int rp_stride;        // row-partial slots per row: the most warps sharing one row, <= 16
 };
+
+// Warps sharing one row of a pair whose slacked rows hold ldy floats, in a
+// CTA of nthr threads (one column quad per thread, or two when a row has
+// more quads than threads).
+inline int pdb_row_warps(int ldy, int nthr) {
+    const int QP = ((ldy >> 2) + 31) & ~31;
+    return (QP <= nthr ? QP : nthr) >> 5;
+}
 
 struct PdbParams {
     const PairDesc* pairs;
@@ -171,6 +180,15 @@ cudaError_t loop_cond(const int* words, int done_idx, int err_idx, int* iter, in
                       cudaGraphConditionalHandle handle, cudaStream_t s);
 // Clears *iter and sets `handle` to 1; runs before the while node.
 cudaError_t loop_init(int* iter, cudaGraphConditionalHandle handle, cudaStream_t s);
+
+// Stop/error words of the pairs of a streamed wave: out[i] = 1 (done) | 2
+// (error) for ctrl[i], out[kMaxWavePairs] = the wave's error word.
+struct FlagList {
+    const Ctrl* ctrl[kMaxWavePairs];
+    const WaveCtrl* wave;
+    int n;
+};
+cudaError_t gather_flags(const FlagList& f, int* out, cudaStream_t s);
 
 // K[i, j] = sum_c B[i, c] * B2[j, c]   (N x m, leading dimension ldk)
 cudaError_t affinity(const float* B, const float* B2, int N, int m, int k, float* K, int ldk,

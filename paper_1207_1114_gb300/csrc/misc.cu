@@ -153,6 +153,12 @@ __global__ void loop_init_kernel(int* iter, cudaGraphConditionalHandle handle) {
     cudaGraphSetConditional(handle, 1u);
 }
 
+__global__ void flags_kernel(const FlagList f, int* out) {
+    const int i = threadIdx.x;
+    if (i < f.n) out[i] = (f.ctrl[i]->done != 0 ? 1 : 0) | (f.ctrl[i]->error != 0 ? 2 : 0);
+    if (i == 0) out[kMaxWavePairs] = f.wave->error;
+}
+
 inline int grid_for(size_t total, int block, int cap = 4096) {
     size_t g = (total + block - 1) / block;
     if (g < 1) g = 1;
@@ -175,6 +181,11 @@ cudaError_t loop_cond(const int* words, int done_idx, int err_idx, int* iter, in
 
 cudaError_t loop_init(int* iter, cudaGraphConditionalHandle handle, cudaStream_t s) {
     loop_init_kernel<<<1, 1, 0, s>>>(iter, handle);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_flags(const FlagList& f, int* out, cudaStream_t s) {
+    flags_kernel<<<1, kMaxWavePairs, 0, s>>>(f, out);
     return cudaGetLastError();
 }
 

@@ -56,11 +56,12 @@ struct Shared {
     PairS* pair;         // kMaxWavePairs
     int* pstate;         // kMaxWavePairs: bit0 active this launch, bit1 stopped
     int* pstop;          // kMaxWavePairs: round at which the pair stopped
-    int* ictl;           // [0],[1] group has an active pair, [2] n segments, [3] non-finite
+    int* ictl;           // [0],[1] group has an active pair, [2] n segments, [3] non-finite,
+                         // [4],[5] group has a segment whose row sums are folded in publish
     int* qpref;          // 2 x (kMaxWavePairs + 1): per group, prefix sums of the pairs' column quads
     float* fred;         // kMaxSeg x 32 per-warp maxima
     float* rsum;         // band rows
-    float* rowpart;      // band rows x 32
+    float* rowpart;      // band rows x rp_stride per-warp row partials
     float4* cred;        // nthr float4: column-partial reduction across row groups
     float* cN;           // sum over segments of ldy floats: the column sums c_j of the last round
     float* band;         // band rows of every segment (16-byte aligned)
@@ -78,11 +79,11 @@ __device__ __forceinline__ Shared carve_b(char* base, const PdbLayout& L, int nt
     s.pair = reinterpret_cast<PairS*>(take(sizeof(PairS) * kMaxWavePairs));
     s.pstate = reinterpret_cast<int*>(take(sizeof(int) * kMaxWavePairs));
     s.pstop = reinterpret_cast<int*>(take(sizeof(int) * kMaxWavePairs));
-    s.ictl = reinterpret_cast<int*>(take(sizeof(int) * 4));
+    s.ictl = reinterpret_cast<int*>(take(sizeof(int) * 8));
     s.qpref = reinterpret_cast<int*>(take(sizeof(int) * 2 * (kMaxWavePairs + 1)));
     s.fred = reinterpret_cast<float*>(take(sizeof(float) * kMaxSeg * 32));
     s.rsum = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_rows));
-    s.rowpart = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_rows * 32));
+    s.rowpart = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_rows * L.rp_stride));
     s.cred = reinterpret_cast<float4*>(take(sizeof(float4) * nthr));
     s.cN = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_cols));
     s.band = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_elems));
@@ -189,7 +190,7 @@ template <bool UPDATE, int KQ>
 __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, int Q, int N,
                                          const Map& mp, int nthr, int lane,
                                          const float* __restrict__ rsum, float abase,
-                                         float* __restrict__ rowpart, float4 c0v, float4 c1v, float ninvN,
+                                         float* __restrict__ rowpart, int rps, float4 c0v, float4 c1v, float ninvN,
                                          float4& cp0, float4& cp1, float& dmax) {
     const bool h0 = mp.q0 < Q;
     const bool h1 = KQ > 1 && mp.q0 + nthr < Q;
@@ -222,7 +223,7 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
         z += __shfl_xor_sync(0xffffffffu, z, 4);
         z += __shfl_xor_sync(0xffffffffu, z, 2);
         z += __shfl_xor_sync(0xffffffffu, z, 1);
-        if ((lane & 7) == 0) rowpart[(size_t)(r + (2 * (lane >> 4) + ((lane >> 3) & 1)) * RP) * 32] = z;
+        if ((lane & 7) == 0) rowpart[(size_t)(r + (2 * (lane >> 4) + ((lane >> 3) & 1)) * RP) * rps] = z;
     }
     for (; r + RP < nrows; r += 2 * RP, p += 2 * stride) {
         const float a0 = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
@@ -245,8 +246,8 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
         keep += __shfl_xor_sync(0xffffffffu, keep, 4);
         keep += __shfl_xor_sync(0xffffffffu, keep, 2);
         keep += __shfl_xor_sync(0xffffffffu, keep, 1);
-        if (lane == 0) rowpart[(size_t)r * 32] = keep;
-        if (lane == 16) rowpart[(size_t)(r + RP) * 32] = keep;
+        if (lane == 0) rowpart[(size_t)r * rps] = keep;
+        if (lane == 16) rowpart[(size_t)(r + RP) * rps] = keep;
     }
     if (r < nrows) {
         const float a0 = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
@@ -254,7 +255,7 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
         if (h0) s0 += quad_step<UPDATE>(p, a0, c0v, ninvN, c00, N, cp0, dmax);
         if (KQ > 1 && h1) s0 += quad_step<UPDATE>(p + nthr, a0, c1v, ninvN, c01, N, cp1, dmax);
         s0 = warp_sum(s0);
-        if (lane == 0) rowpart[(size_t)r * 32] = s0;
+        if (lane == 0) rowpart[(size_t)r * rps] = s0;
     }
 }
 
@@ -269,6 +270,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     const unsigned base0 = W->bar_base[0], base1 = W->bar_base[1];
     unsigned gen[2] = {0u, 0u};
     const int npairs = P.npairs, split = P.split;
+    const int RPS = P.layout.rp_stride;
 
     // ---- bands of both groups -> segments, pair states and per-pair fields
     if (tid == 0) {
@@ -298,6 +300,11 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         }
         S.ictl[2] = nseg;
         S.ictl[3] = 0;
+        S.ictl[4] = S.ictl[5] = 0;
+        for (int si = 0; si < nseg; ++si) {
+            const int QP = ((P.pairs[S.seg[si].pair].ldy >> 2) + 31) & ~31;
+            if (QP > (nthr >> 1)) S.ictl[4 + S.seg[si].group] = 1;
+        }
         for (int g = 0; g < 2; ++g) {
             const int p0 = g == 0 ? 0 : split, p1 = g == 0 ? split : npairs;
             int* qp = S.qpref + g * (kMaxWavePairs + 1);
@@ -373,22 +380,24 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             if (in_grp) {
                 const int wig = (mp.QP <= nthr) ? ((tid % mp.QP) >> 5) : warp;
                 float4* bp = reinterpret_cast<float4*>(S.band + sg.soff);
-                float* rp = S.rowpart + (size_t)sg.brow0 * 32 + wig;
+                float* rp = S.rowpart + (size_t)sg.brow0 * RPS + wig;
                 const float* rs = S.rsum + sg.brow0;
                 if (mp.kq == 1)
-                    seg_rows<UPDATE, 1>(bp, sg.nrows, Q, N, mp, nthr, lane, rs, pr.abase, rp, c0v, c1v,
+                    seg_rows<UPDATE, 1>(bp, sg.nrows, Q, N, mp, nthr, lane, rs, pr.abase, rp, RPS, c0v, c1v,
                                         -1.0f / (float)N, cp0, cp1, dmax);
                 else
-                    seg_rows<UPDATE, 2>(bp, sg.nrows, Q, N, mp, nthr, lane, rs, pr.abase, rp, c0v, c1v,
+                    seg_rows<UPDATE, 2>(bp, sg.nrows, Q, N, mp, nthr, lane, rs, pr.abase, rp, RPS, c0v, c1v,
                                         -1.0f / (float)N, cp0, cp1, dmax);
             }
             dmax = warp_max(dmax);
             if (lane == 0) S.fred[si * 32 + warp] = dmax;
-            // column partials: fold the row groups, then one red.v4 per quad
+            // column partials: fold the row groups, then one red.v4 per quad;
+            // meanwhile the warps past the quads fold the row sums
             float* acc = pr.colbuf + (size_t)cur * pr.ldy;
             if (mp.RP > 1) {
                 S.cred[tid] = (in_grp && mp.q0 < Q) ? cp0 : make_float4(0.f, 0.f, 0.f, 0.f);
                 __syncthreads();
+                const int QW = (Q + 31) & ~31;
                 if (tid < Q) {
                     float4 t = S.cred[tid];
                     for (int gg = 1; gg < mp.RP; ++gg) {
@@ -396,6 +405,14 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                         t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
                     }
                     red_add_v4(acc + 4 * tid, t.x, t.y, t.z, t.w);
+                } else if (tid >= QW) {
+                    const int nw = mp.QP >> 5;
+                    for (int r = tid - QW; r < sg.nrows; r += nthr - QW) {
+                        const float* rpp = S.rowpart + (size_t)(sg.brow0 + r) * RPS;
+                        float t = 0.f;
+                        for (int w = 0; w < nw; ++w) t += rpp[w];
+                        S.rsum[sg.brow0 + r] = t;
+                    }
                 }
                 __syncthreads();
             } else {
@@ -406,8 +423,6 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         }
     };
 
-    // End of group g's pass: row sums, FP64 totals and maxima of its
-    // segments, then arrive at the group's barrier.
     // Zero accumulator `which` of group g's pairs with threads t of nt.  The
     // group's column quads are numbered consecutively over its pairs and
     // dealt round-robin over the CTAs, so every CTA zeroes about the same few.
@@ -431,24 +446,30 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         }
     };
 
-    // Warps 0 and 1 publish the segments' FP64 totals and round maxima
-    // (alternate segments), while warps 2.. zero accumulator `clear_which`
-    // (>= 0) of the group's pairs; all of it precedes the arrival, so the
-    // zeros are visible before any CTA's next-round reductions.
+    // End of group g's pass: the row sums of segments whose rows span the
+    // whole CTA (the others were folded in the pass), then warps 0 and 1
+    // publish the segments' totals and round maxima (alternate segments)
+    // while warps 2.. zero accumulator `clear_which` (>= 0) of the group's
+    // pairs; all of it precedes the arrival, so the zeros are visible before
+    // any CTA's next-round reductions.  A band's total (at most a few dozen
+    // FP32 row sums) is added in FP32 and accumulated over the CTAs in FP64.
     auto publish = [&](int g, int cur, int clear_which) {
-        __syncthreads();
-        for (int si = 0; si < nseg; ++si) {
-            const Seg sg = S.seg[si];
-            if (sg.group != g) continue;
-            const int pst = S.pstate[sg.pair];
-            if (!(pst & 1) || (pst & 2)) continue;
-            const int QP = ((S.pair[sg.pair].ldy >> 2) + 31) & ~31;
-            const int nw = (QP <= nthr ? QP : nthr) >> 5;
-            for (int r = tid; r < sg.nrows; r += nthr) {
-                const float* rp = S.rowpart + (size_t)(sg.brow0 + r) * 32;
-                float t = 0.f;
-                for (int w = 0; w < nw; ++w) t += rp[w];
-                S.rsum[sg.brow0 + r] = t;
+        if (S.ictl[4 + g] != 0) {   // some segment of the group folds its rows here
+            __syncthreads();
+            for (int si = 0; si < nseg; ++si) {
+                const Seg sg = S.seg[si];
+                if (sg.group != g) continue;
+                const int pst = S.pstate[sg.pair];
+                if (!(pst & 1) || (pst & 2)) continue;
+                const int QP = ((S.pair[sg.pair].ldy >> 2) + 31) & ~31;
+                if (QP <= (nthr >> 1)) continue;   // folded in the pass
+                const int nw = (QP <= nthr ? QP : nthr) >> 5;
+                for (int r = tid; r < sg.nrows; r += nthr) {
+                    const float* rp = S.rowpart + (size_t)(sg.brow0 + r) * RPS;
+                    float t = 0.f;
+                    for (int w = 0; w < nw; ++w) t += rp[w];
+                    S.rsum[sg.brow0 + r] = t;
+                }
             }
         }
         __syncthreads();
@@ -458,14 +479,14 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 if (sg.group != g) continue;
                 const int pst = S.pstate[sg.pair];
                 if (!(pst & 1) || (pst & 2)) continue;
-                double sp = 0.0;
-                for (int r = lane; r < sg.nrows; r += 32) sp += (double)S.rsum[sg.brow0 + r];
-                sp = warp_sum_d(sp);
+                float sp = 0.f;
+                for (int r = lane; r < sg.nrows; r += 32) sp += S.rsum[sg.brow0 + r];
+                sp = warp_sum(sp);
                 float bm = lane < (nthr >> 5) ? S.fred[si * 32 + lane] : 0.f;
                 bm = warp_max(bm);
                 if (lane == 0) {
                     const PairS& pr = S.pair[sg.pair];
-                    atomicAdd(pr.sbuf + cur, sp);
+                    atomicAdd(pr.sbuf + cur, (double)sp);
                     if (bm > 0.f) atomicMax(pr.dbuf + cur, __float_as_uint(bm));
                 }
             }
@@ -714,11 +735,11 @@ size_t pdb_smem_bytes(const PdbLayout& L, int nthr) {
     take(56 * kMaxWavePairs);         // PairS: three pointers, a double, two ints, a float, pad, a double
     take(4 * kMaxWavePairs);
     take(4 * kMaxWavePairs);
-    take(4 * 4);
+    take(4 * 8);
     take(4 * 2 * (kMaxWavePairs + 1));
     take(4 * kMaxSeg * 32);
     take(4 * (size_t)L.max_band_rows);
-    take(4 * (size_t)L.max_band_rows * 32);
+    take(4 * (size_t)L.max_band_rows * L.rp_stride);
     take(16 * (size_t)nthr);
     take(4 * (size_t)L.max_band_cols);
     take(4 * (size_t)L.max_band_elems);

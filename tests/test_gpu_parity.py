@@ -365,6 +365,85 @@ def test_batched_mixed_small_pairs_plain(solver):
         assert (o.perm.cpu().numpy() == g.gt).mean() >= 0.99
 
 
+# ------------------------------------------------- streamed (continuous) batches
+
+@pytest.fixture(scope="module")
+def stream_solver():
+    s = F.Solver(max_n=1000, max_batch=128)
+    yield s
+    s.close()
+
+
+def _replay_check(solver, g, o, i, lam, **kw):
+    inner, _ = solver.last_trace(pair=i)
+    assert o.stats.status == 0 and len(inner) == o.stats.outer_iters
+    r = oracle.solve(g.A, g.A2, g.B, g.B2, lam=lam, replay_inner=inner,
+                     replay_outer=o.stats.outer_iters, **kw)
+    Xg = o.X.cpu().numpy()
+    assert np.abs(Xg - r["X"]).max() <= 1e-4
+    A, A2, Bc, B2c, tr = _canon(g)
+    roc = oracle.greedy_sorted((Xg.T if tr else Xg).astype(np.float64))
+    K = oracle.affinity(Bc, B2c) if g.k and lam else None
+    obj = oracle.qap_objective(A, A2, roc, K, lam)
+    assert abs(o.stats.objective - obj) <= 1e-5 * abs(obj)
+
+
+def test_streamed_batch_refills_waves_and_matches_oracle(stream_solver):
+    """Twelve pairs of 850..1000 nodes do not fit in one wave (shared memory):
+    the batch is streamed, finished pairs leaving and waiting pairs entering
+    between outer iterations.  A loose outer tolerance makes the pairs stop
+    at different iterations.  Every pair matches the oracle replaying its
+    own inner counts."""
+    rng = np.random.default_rng(40)
+    pairs = [synth.graph_pair(int(rng.integers(850, 1001)), p=0.1, sigma=0.05, k=8, lam=0.5,
+                              seed=400 + i) for i in range(12)]
+    kw = dict(max_outer=12, max_inner=80, tol_outer=1e-3)
+    p = F.default_params(lam=0.5, **kw)
+    dev = [(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)) for g in pairs]
+    outs = stream_solver.match_batched(dev, params=p, want_X=True)
+    waves = [o.stats.wave_pairs for o in outs]
+    assert 0 < max(waves) < len(pairs)
+    assert len({o.stats.outer_iters for o in outs}) > 1   # pairs left at different times
+    for i, (g, o) in enumerate(zip(pairs, outs)):
+        _replay_check(stream_solver, g, o, i, 0.5, **kw)
+
+
+def test_streamed_host_batch_equals_device_batch(stream_solver):
+    rng = np.random.default_rng(41)
+    pairs = [synth.graph_pair(int(rng.integers(850, 1001)), p=0.1, sigma=0.05, k=8, lam=0.5,
+                              seed=500 + i) for i in range(11)]
+    p = F.default_params(lam=0.5, max_outer=8, max_inner=60, tol_outer=1e-3)
+    d = stream_solver.match_batched([(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)) for g in pairs], params=p,
+                                    want_X=True)
+    assert max(o.stats.wave_pairs for o in d) < len(pairs)
+    h = stream_solver.match_batched_host([(g.A, g.A2, g.B, g.B2) for g in pairs], params=p, want_X=True)
+    for a, b in zip(d, h):
+        assert a.stats.outer_iters == b.stats.outer_iters
+        np.testing.assert_array_equal(a.perm.cpu().numpy(), b.perm)
+        assert np.abs(a.X.cpu().numpy() - b.X).max() <= 1e-5
+
+
+def test_streamed_mixed_batch_of_100(stream_solver):
+    """100 mixed pairs (n in 50..600, up to 100 outliers): more pairs than
+    one wave holds.  Every pair returns a valid partial permutation; sampled
+    pairs match the oracle replay."""
+    pairs = synth.batch_mixed(count=100, seed=7, n_lo=50, n_hi=600, out_hi=100)
+    kw = dict(max_outer=30, max_inner=200)
+    p = F.default_params(lam=0.5, **kw)
+    dev = [(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)) for g in pairs]
+    outs = stream_solver.match_batched(dev, params=p, want_X=True)
+    assert max(o.stats.wave_pairs for o in outs) < len(pairs)
+    for g, o in zip(pairs, outs):
+        assert o.stats.status == 0
+        perm = o.perm.cpu().numpy()
+        n_a, n_b = g.A.shape[0], g.A2.shape[0]
+        used = perm[perm >= 0]
+        assert len(np.unique(used)) == len(used) and (used < n_b).all()
+        assert len(used) == min(n_a, n_b)
+    for i in (0, 37, 99):
+        _replay_check(stream_solver, pairs[i], outs[i], i, 0.5, **kw)
+
+
 # ------------------------------------------------------------ errors / faults
 
 def test_nonfinite_input_is_reported(solver):
