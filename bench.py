@@ -1,6 +1,6 @@
 """FastPFP throughput benchmark: pair-solves/s at n = n' = 1000.
 
-One step = one batch of synthetic attributed graph pairs (n = n' = 1000,
+One step = one batch of 64 synthetic attributed graph pairs (n = n' = 1000,
 p = 0.1, U(0,1) weights, edge noise 0.05, 16-dim attributes, lambda = 1,
 alpha = 0.5, eps_1 = eps_2 = 1e-6, I_0 = 100, I_1 = 1000) solved end to end
 (affinity, gradient products, projection, blend/normalise, loop control,
@@ -38,7 +38,7 @@ SOLVER = dict(alpha=0.5, tol_outer=1e-6, tol_inner=1e-6, max_outer=100, max_inne
 # attributed_1000 is the headline: pair-solves/s at n = n' = 1000.
 WORKLOADS = {
     "attributed_1000": dict(n=1000, n2=1000, p=0.1, sigma=0.05, k=16, attr_sigma=0.05, lam=1.0,
-                            batch=7, metric=METRIC),
+                            batch=64, metric=METRIC),
     "partial_1000_1200": dict(n=1000, n2=1200, outliers=200, p=0.1, sigma=0.03, k=16,
                               attr_sigma=0.05, lam=0.5, batch=5,
                               metric="fastpfp_pair_solves_per_s_partial_1000_1200"),
@@ -374,8 +374,25 @@ def main():
     ms_gemm = sum(s.ms_gemm for s in flat)
     ms_disc = sum(s.ms_disc for s in flat)
     achieved = alg_bytes / (ms_proj / 1e3) / 1e9 if ms_proj > 0 else None
-    peak, peak_kind = peaks()
+    hbm_peak, hbm_kind = peaks()
     kernel = "pdb_kernel" if flat[0].wave_pairs > 0 else "pd_kernel"
+    # the memory level that holds Y during the rounds bounds their traffic:
+    # shared memory for a wave (and for a lone pair whose band fits), L2 for
+    # a streamed band of up to ~100 MB, HBM beyond
+    Nmax = max(N for N, _ in shapes)
+    y_bytes = 4.0 * Nmax * Nmax
+    if kernel == "pdb_kernel" or Nmax <= 2900:
+        level, bound, sweeps = 0, "smem", 20000
+    elif y_bytes <= 100e6:
+        level, bound, sweeps = 1, "l2", 2000
+    else:
+        level, bound, sweeps = 2, "hbm", 0
+    if level < 2:
+        peak = F.bandwidth_probe(level, sweeps=sweeps, device=local)
+        peak_kind = ("measured live by fastpfp_bandwidth_probe: read + write sweeps of "
+                     + ("every SM's shared memory" if level == 0 else "a 64 MB L2-resident buffer"))
+    else:
+        peak, peak_kind = hbm_peak, hbm_kind
     # one projection launch per outer iteration of a wave (or of a lone pair)
     # and, about, as many rounds per launch as the wave's slowest pair runs
     proj_launches, wave_rounds = 0, 0
@@ -433,9 +450,10 @@ def main():
             "iterations": {"outer_per_pair": sum(s.outer_iters for s in flat_t) / len(flat_t),
                            "inner_per_pair": sum(s.inner_iters_total for s in flat_t) / len(flat_t)},
             "phase_ms_instrumented": {"gemm": ms_gemm, "projection": ms_proj, "discretize": ms_disc},
-            "roofline": {"kernel": f"{kernel} (projection rounds + blend)", "bound": "hbm",
+            "roofline": {"kernel": f"{kernel} (projection rounds + blend)", "bound": bound,
                          "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                          "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                         "hbm_peak": hbm_peak, "hbm_frac": (achieved / hbm_peak) if achieved else None,
                          "traffic": traffic,
                          "alg_bytes_per_launch": alg_bytes / max(proj_launches, 1),
                          "launches": proj_launches, "timing": timing},

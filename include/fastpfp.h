@@ -294,6 +294,19 @@ int fastpfp_warmstart_train_step(fastpfp_t h, void* stream, const float* A, int 
 int fastpfp_project_noalloc(void* stream, float* Y, int N, double tol, int max_iter, int* iters,
                             double* last_delta);
 
+/* Measures the bandwidth of a memory level that can hold the slacked
+ * matrix Y of the projection rounds (Section 4.3), on CUDA device `device`,
+ * with the rounds' access pattern (every float read and written back once
+ * per sweep, 16-byte accesses):
+ *   level 0  shared memory, every SM sweeping ~219 KB of its own;
+ *   level 1  L2, one 64 MB buffer (the size of Y at N = 4000);
+ *   level 2  HBM, one 2 GB buffer.
+ * sweeps >= 1 timed sweeps after one warm-up sweep.  *gbs receives the
+ * measured read + write bandwidth in GB/s.  Allocates and frees a scratch
+ * buffer (levels 1, 2); synchronises the device.  Errors: ERR_ARG (bad level
+ * or sweeps, gbs == NULL), ERR_CUDA. */
+int fastpfp_bandwidth_probe(int device, int level, int sweeps, double* gbs);
+
 /* Human-readable name of an error code. */
 const char* fastpfp_error_string(int code);
 

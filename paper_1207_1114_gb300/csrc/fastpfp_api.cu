@@ -546,23 +546,27 @@ int split_group(const std::vector<Problem>& qs, int first, int count, int G, lon
     }
     const int used = cut_rows(qs, first, count, lo, seg_cost, G, band);
     for (int c = used; c <= G; ++c) band[c] = rows;
-    // per-band statistics
-    int b = 0, gr = 0, last_pair = -1;
+    // per-band statistics; the first rows of every row group go to TMEM
+    // (pdb_tmem_rows, segments in pair order as the kernel places them), so
+    // elems counts the floats left in shared memory
+    std::vector<int> tcol(G, 0);
+    int b = 0, gr = 0;
     for (int i = 0; i < count; ++i) {
         const int N = qs[first + i].N, ldy = round4(N);
-        for (int r = 0; r < N; ++r, ++gr) {
-            while (b + 1 < used && gr >= band[b + 1]) {
-                ++b;
-                last_pair = -1;
-            }
-            if (last_pair != i) {
-                st[b].cols += ldy;
-                ++st[b].segs;
-                last_pair = i;
-            }
-            ++st[b].rows;
-            st[b].elems += ldy;
+        while (b + 1 < used && band[b + 1] <= gr) ++b;
+        for (int bb = b; bb < used && band[bb] < gr + N; ++bb) {
+            const int lo = std::max(band[bb], gr), hi = std::min(band[bb + 1], gr + N);
+            if (lo >= hi) continue;
+            const int nr = hi - lo;
+            int ntm = 0, next = 0;
+            pdb_tmem_rows(nr, ldy, kPdbThreads, tcol[bb], &ntm, &next);
+            tcol[bb] = next;
+            st[bb].rows += nr;
+            st[bb].cols += ldy;
+            ++st[bb].segs;
+            st[bb].elems += (nr - ntm) * ldy;
         }
+        gr += N;
     }
     return used;
 }
@@ -1322,6 +1326,22 @@ int solve_batch(fastpfp_t h, cudaStream_t s, int count, const fastpfp_pair* pair
 }  // namespace
 
 extern "C" {
+
+int fastpfp_bandwidth_probe(int device, int level, int sweeps, double* gbs) {
+    if (!gbs || sweeps < 1 || level < 0 || level > 2) return FASTPFP_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return FASTPFP_ERR_CUDA;
+    int num_sms = 0;
+    if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return FASTPFP_ERR_CUDA;
+    float ms = 0.f;
+    double bytes = 0.0;
+    cudaError_t e;
+    if (level == 0) e = probe_smem(num_sms, sweeps, 0, &ms, &bytes);
+    else e = probe_gmem(level == 1 ? (size_t)64 << 20 : (size_t)2 << 30, num_sms, sweeps, 0, &ms, &bytes);
+    if (e != cudaSuccess || ms <= 0.f) return FASTPFP_ERR_CUDA;
+    *gbs = bytes / ((double)ms * 1e-3) / 1e9;
+    return FASTPFP_OK;
+}
 
 int fastpfp_last_trace(fastpfp_t h, int pair, int* inner_counts, double* deltas, int cap) {
     if (!h || cap < 0) return FASTPFP_ERR_ARG;

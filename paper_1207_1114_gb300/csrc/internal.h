@@ -86,16 +86,45 @@ struct WaveCtrl {
 struct PdbLayout {
     int max_band_rows;    // rows of the largest band
     int max_band_cols;    // sum of ldy over the segments of one band
-    int max_band_elems;   // floats of the largest band
+    int max_band_elems;   // floats of the largest band kept in shared memory (the rest is in TMEM)
     int rp_stride;        // row-partial slots per row: the most warps sharing one row, <= 16
 };
 
 // Warps sharing one row of a pair whose slacked rows hold ldy floats, in a
 // CTA of nthr threads (one column quad per thread, or two when a row has
 // more quads than threads).
-inline int pdb_row_warps(int ldy, int nthr) {
+__host__ __device__ inline int pdb_row_warps(int ldy, int nthr) {
     const int QP = ((ldy >> 2) + 31) & ~31;
     return (QP <= nthr ? QP : nthr) >> 5;
+}
+
+// Tensor memory as band storage: a CTA of kPdbThreads threads allocates all
+// 512 TMEM columns; the four warps sharing a 32-lane quarter split them, so
+// every thread owns kTmemColsPerThread 32-bit columns of its lane.
+constexpr int kTmemCols = 512;
+constexpr int kTmemColsPerThread = kTmemCols * 128 / kPdbThreads;
+
+// Placement of one segment of a band (nrows rows of a pair with row length
+// ldy) after col_used of the thread's TMEM columns are taken by earlier
+// segments: the first `tm` rows of every row group (band rows 0 ..
+// RP * tm - 1 of the segment, RP = row groups) live in TMEM columns col_used
+// + 4 k, one quad per thread; the rest in shared memory.  Rows wider than
+// the CTA (two quads per thread) stay in shared memory.  Returns tm and sets
+// *tm_band_rows (band rows in TMEM) and *col_next.
+__host__ __device__ inline int pdb_tmem_rows(int nrows, int ldy, int nthr, int col_used, int* tm_band_rows,
+                                             int* col_next) {
+    const int QP = ((ldy >> 2) + 31) & ~31;
+    *col_next = col_used;
+    *tm_band_rows = 0;
+    if (QP > nthr) return 0;
+    const int RP = nthr / QP;
+    const int nk = (nrows + RP - 1) / RP;
+    int avail = (kTmemColsPerThread - col_used) / 4;
+    if (avail < 0) avail = 0;
+    const int tm = nk < avail ? nk : avail;
+    *col_next = col_used + 4 * tm;
+    *tm_band_rows = RP * tm < nrows ? RP * tm : nrows;
+    return tm;
 }
 
 struct PdbParams {
@@ -169,6 +198,12 @@ struct GemmF32Group {
     int count;
 };
 cudaError_t gemm_f32_group(const GemmF32Group& g, cudaStream_t s);
+
+// ------------------------------------------------------ bandwidth probes
+// Read + write sweeps of shared memory (all SMs) or of one global buffer;
+// *ms = elapsed time of the timed sweeps, *bytes = bytes they moved.
+cudaError_t probe_smem(int num_sms, int sweeps, cudaStream_t s, float* ms, double* bytes);
+cudaError_t probe_gmem(size_t buf_bytes, int num_sms, int sweeps, cudaStream_t s, float* ms, double* bytes);
 
 // ----------------------------------------------------------- misc kernels
 cudaError_t init_ctrl(Ctrl* c, int lowp, cudaStream_t s);

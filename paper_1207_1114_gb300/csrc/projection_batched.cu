@@ -31,9 +31,12 @@ struct Seg {
     int lr0;        // first row of the segment inside its pair
     int nrows;      // rows of the segment
     int brow0;      // first row of the segment inside the band (rsum/rowpart index)
-    int soff;       // float offset of the segment's rows in the band storage
-    int coff;       // float offset of the segment's c/N vector
-    int pad;
+    int soff;       // float offset of the segment's shared-memory rows in the band storage
+    int coff;       // float offset of the segment's column sums
+    int tm;         // thread-rows per row group held in TMEM (band rows 0 .. ntm - 1)
+    int tcol;       // first TMEM column of the segment in every thread's share
+    int ntm;        // band rows of the segment in TMEM; rows ntm .. nrows - 1 are in shared memory
+    int pad0, pad1;
 };
 
 // Per-pair fields used every round, copied to shared memory once per launch.
@@ -48,7 +51,7 @@ struct PairS {
     double invN;    // 1/N
 };
 
-static_assert(sizeof(Seg) == 32, "pdb_smem_bytes assumes 32-byte segments");
+static_assert(sizeof(Seg) == 48, "pdb_smem_bytes assumes 48-byte segments");
 static_assert(sizeof(PairS) == 56, "pdb_smem_bytes assumes 56-byte pair records");
 
 struct Shared {
@@ -148,14 +151,14 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
     return r;
 }
 
-// One column quad of one row: Eq. (P1) with the row offset ai and the
-// column sums c (the offset is c_j / N, folded into one FMA with ninvN =
-// -1/N), then Eq. (P2); columns >= N stay zero.  Returns the quad's
-// contribution to the row sum.  Packed f32x2 arithmetic, two lanes per op.
+// One column quad of one row held in registers: Eq. (P1) with the row
+// offset ai and the column sums c (the offset is c_j / N, folded into one
+// FMA with ninvN = -1/N), then Eq. (P2); columns >= N stay zero.  Returns
+// the quad's contribution to the row sum.  Packed f32x2 arithmetic, two
+// lanes per op.
 template <bool UPDATE>
-__device__ __forceinline__ float quad_step(float4* __restrict__ p, float ai, float4 c, float ninvN, int c0,
-                                           int N, float4& cp, float& dmax) {
-    float4 y = *p;
+__device__ __forceinline__ float quad_upd(float4& y, float ai, float4 c, float ninvN, int c0, int N, float4& cp,
+                                          float& dmax) {
     if (UPDATE) {
         const unsigned long long A = pk(ai, ai), NI = pk(ninvN, ninvN);
         const unsigned long long y01 = pk(y.x, y.y), y23 = pk(y.z, y.w);
@@ -171,7 +174,6 @@ __device__ __forceinline__ float quad_step(float4* __restrict__ p, float ai, flo
         const float2 d23 = upk(sub2(pk(z.z, z.w), y23));
         dmax = max3f(dmax, fabsf(d01.x), fabsf(d01.y));
         dmax = max3f(dmax, fabsf(d23.x), fabsf(d23.y));
-        *p = z;
         y = z;
     }
     const float2 c01 = upk(add2(pk(cp.x, cp.y), pk(y.x, y.y)));
@@ -179,6 +181,119 @@ __device__ __forceinline__ float quad_step(float4* __restrict__ p, float ai, flo
     cp = make_float4(c01.x, c01.y, c23.x, c23.y);
     const float2 r = upk(add2(pk(y.x, y.y), pk(y.z, y.w)));
     return r.x + r.y;
+}
+
+// The same for a quad in shared memory.
+template <bool UPDATE>
+__device__ __forceinline__ float quad_step(float4* __restrict__ p, float ai, float4 c, float ninvN, int c0,
+                                           int N, float4& cp, float& dmax) {
+    float4 y = *p;
+    const float s = quad_upd<UPDATE>(y, ai, c, ninvN, c0, N, cp, dmax);
+    if (UPDATE) *p = y;
+    return s;
+}
+
+// Tensor memory as storage (no MMA): warp-collective 32-lane x N-column
+// loads and stores of 32-bit words, each lane its own TMEM lane.
+__device__ __forceinline__ void tm_ld16(uint32_t taddr, float4 (&q)[4]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        q[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]), __uint_as_float(r[4 * j + 2]),
+                           __uint_as_float(r[4 * j + 3]));
+}
+__device__ __forceinline__ void tm_st16(uint32_t taddr, const float4 (&q)[4]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+        ::"r"(taddr), "r"(__float_as_uint(q[0].x)), "r"(__float_as_uint(q[0].y)), "r"(__float_as_uint(q[0].z)),
+          "r"(__float_as_uint(q[0].w)), "r"(__float_as_uint(q[1].x)), "r"(__float_as_uint(q[1].y)),
+          "r"(__float_as_uint(q[1].z)), "r"(__float_as_uint(q[1].w)), "r"(__float_as_uint(q[2].x)),
+          "r"(__float_as_uint(q[2].y)), "r"(__float_as_uint(q[2].z)), "r"(__float_as_uint(q[2].w)),
+          "r"(__float_as_uint(q[3].x)), "r"(__float_as_uint(q[3].y)), "r"(__float_as_uint(q[3].z)),
+          "r"(__float_as_uint(q[3].w))
+        : "memory");
+}
+__device__ __forceinline__ float4 tm_ld4(uint32_t taddr) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    return make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]), __uint_as_float(r[3]));
+}
+__device__ __forceinline__ void tm_st4(uint32_t taddr, float4 v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr),
+                 "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)),
+                 "r"(__float_as_uint(v.w))
+                 : "memory");
+}
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Four rows' warp sums in one shuffle tree: bit 4 of the lane picks rows
+// {0,1} or {2,3}, bit 3 the row within the pair; lanes 0, 8, 16, 24 end
+// with rows 0, 1, 2, 3.
+__device__ __forceinline__ float sum4_rows(const float (&s)[4], int lane) {
+    const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
+    float x0 = b4 ? s[2] : s[0], x1 = b4 ? s[3] : s[1];
+    x0 += __shfl_xor_sync(0xffffffffu, b4 ? s[0] : s[2], 16);
+    x1 += __shfl_xor_sync(0xffffffffu, b4 ? s[1] : s[3], 16);
+    float z = b3 ? x1 : x0;
+    z += __shfl_xor_sync(0xffffffffu, b3 ? x0 : x1, 8);
+    z += __shfl_xor_sync(0xffffffffu, z, 4);
+    z += __shfl_xor_sync(0xffffffffu, z, 2);
+    z += __shfl_xor_sync(0xffffffffu, z, 1);
+    return z;
+}
+
+// The TMEM rows of one segment for this thread's row group: thread-rows
+// k < tm (band rows grp + RP k) at TMEM columns taddr + 4 k, four rows per
+// load/store.  Rows past nrows (the group's last thread-rows) are carried
+// but not updated or counted.  Warp-collective: whole warps call it.
+template <bool UPDATE>
+__device__ __forceinline__ void seg_rows_tmem(uint32_t taddr, int tm, int nrows, int Q, int N, const Map& mp,
+                                              int lane, const float* __restrict__ rsum, float abase,
+                                              float* __restrict__ rowpart, int rps, float4 c0v, float ninvN,
+                                              float4& cp0, float& dmax) {
+    const bool h0 = mp.q0 < Q;
+    const int c00 = 4 * mp.q0;
+    const int RP = mp.RP;
+    int k = 0;
+    for (; k + 3 < tm; k += 4) {
+        float4 q[4];
+        tm_ld16(taddr + 4 * k, q);
+        float s[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = mp.grp + RP * (k + j);
+            s[j] = 0.f;
+            if (r < nrows && h0) {
+                const float a = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
+                s[j] = quad_upd<UPDATE>(q[j], a, c0v, ninvN, c00, N, cp0, dmax);
+            }
+        }
+        if (UPDATE) tm_st16(taddr + 4 * k, q);
+        const float z = sum4_rows(s, lane);
+        const int rj = mp.grp + RP * (k + 2 * (lane >> 4) + ((lane >> 3) & 1));
+        if ((lane & 7) == 0 && rj < nrows) rowpart[(size_t)rj * rps] = z;
+    }
+    for (; k < tm; ++k) {
+        const int r = mp.grp + RP * k;
+        float4 y = tm_ld4(taddr + 4 * k);
+        float s0 = 0.f;
+        if (r < nrows && h0) {
+            const float a = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
+            s0 = quad_upd<UPDATE>(y, a, c0v, ninvN, c00, N, cp0, dmax);
+        }
+        if (UPDATE) tm_st4(taddr + 4 * k, y);
+        s0 = warp_sum(s0);
+        if (lane == 0 && r < nrows) rowpart[(size_t)r * rps] = s0;
+    }
 }
 
 // All rows of one segment handled by this thread's row group: four rows in
@@ -212,17 +327,7 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
             for (int k = 0; k < 4; ++k)
                 s[k] += quad_step<UPDATE>(p + k * stride + nthr, a[k], c1v, ninvN, c01, N, cp1, dmax);
         }
-        // four rows' warp sums in one shuffle tree: bit 4 of the lane picks
-        // rows {0,1} or {2,3}, bit 3 the row within the pair
-        const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
-        float x0 = b4 ? s[2] : s[0], x1 = b4 ? s[3] : s[1];
-        x0 += __shfl_xor_sync(0xffffffffu, b4 ? s[0] : s[2], 16);
-        x1 += __shfl_xor_sync(0xffffffffu, b4 ? s[1] : s[3], 16);
-        float z = b3 ? x1 : x0;
-        z += __shfl_xor_sync(0xffffffffu, b3 ? x0 : x1, 8);
-        z += __shfl_xor_sync(0xffffffffu, z, 4);
-        z += __shfl_xor_sync(0xffffffffu, z, 2);
-        z += __shfl_xor_sync(0xffffffffu, z, 1);
+        const float z = sum4_rows(s, lane);
         if ((lane & 7) == 0) rowpart[(size_t)(r + (2 * (lane >> 4) + ((lane >> 3) & 1)) * RP) * rps] = z;
     }
     for (; r + RP < nrows; r += 2 * RP, p += 2 * stride) {
@@ -274,7 +379,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
 
     // ---- bands of both groups -> segments, pair states and per-pair fields
     if (tid == 0) {
-        int nseg = 0, brow = 0, soff = 0, coff = 0;
+        int nseg = 0, brow = 0, soff = 0, coff = 0, tcol = 0;
         for (int g = 0; g < 2; ++g) {
             const int* band = P.band_row + g * (G + 1);
             const int b0 = band[blockIdx.x], b1 = band[blockIdx.x + 1];
@@ -291,10 +396,12 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 s.brow0 = brow;
                 s.soff = soff;
                 s.coff = coff;
-                s.pad = 0;
+                s.tcol = tcol;
+                s.tm = pdb_tmem_rows(s.nrows, d.ldy, nthr, tcol, &s.ntm, &tcol);
+                s.pad0 = s.pad1 = 0;
                 S.seg[nseg++] = s;
                 brow += s.nrows;
-                soff += s.nrows * d.ldy;
+                soff += (s.nrows - s.ntm) * d.ldy;
                 coff += d.ldy;
             }
         }
@@ -332,6 +439,31 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     __syncthreads();
     const int nseg = S.ictl[2];
 
+    // ---- tensor memory: all 512 columns of this SM hold the first rows of
+    // every row group (one quad per thread and row); shared memory the rest
+    __shared__ uint32_t s_tmem;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (unsigned)__cvta_generic_to_shared(&s_tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    // this thread's share: its warp's 32-lane quarter, one of four column blocks
+    const uint32_t tme = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(kTmemColsPerThread * (warp >> 2));
+
+    auto slack_mask = [&](float4 v, int c0, int m) {
+        if (c0 + 0 >= m) v.x = 0.f;
+        if (c0 + 1 >= m) v.y = 0.f;
+        if (c0 + 2 >= m) v.z = 0.f;
+        if (c0 + 3 >= m) v.w = 0.f;
+        return v;
+    };
+
     // ---- prologue: load the band (optional slack reset)
     for (int si = 0; si < nseg; ++si) {
         const Seg sg = S.seg[si];
@@ -340,19 +472,31 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         const int Q = d.ldy >> 2, m = d.m;
         const bool reset = P.slack_reset && m < d.N;
         const float4* src = reinterpret_cast<const float4*>(d.Y) + (size_t)sg.lr0 * Q;
-        float4* dst = reinterpret_cast<float4*>(S.band + sg.soff);
-        for (int e = tid; e < sg.nrows * Q; e += nthr) {
-            float4 v = src[e];
-            if (reset) {
-                const int c0 = 4 * (e % Q);
-                if (c0 + 0 >= m) v.x = 0.f;
-                if (c0 + 1 >= m) v.y = 0.f;
-                if (c0 + 2 >= m) v.z = 0.f;
-                if (c0 + 3 >= m) v.w = 0.f;
+        // TMEM rows: thread-row k of the row group is band row grp + RP k
+        if (sg.tm > 0) {
+            const Map mp = make_map(Q, nthr, tid);
+            if (mp.grp < mp.RP) {
+                for (int k = 0; k < sg.tm; ++k) {
+                    const int r = mp.grp + mp.RP * k;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (r < sg.nrows && mp.q0 < Q) {
+                        v = src[(size_t)r * Q + mp.q0];
+                        if (reset) v = slack_mask(v, 4 * mp.q0, m);
+                    }
+                    tm_st4(tme + sg.tcol + 4 * k, v);
+                }
             }
+        }
+        // shared-memory rows ntm .. nrows - 1
+        const float4* src2 = src + (size_t)sg.ntm * Q;
+        float4* dst = reinterpret_cast<float4*>(S.band + sg.soff);
+        for (int e = tid; e < (sg.nrows - sg.ntm) * Q; e += nthr) {
+            float4 v = src2[e];
+            if (reset) v = slack_mask(v, 4 * (e % Q), m);
             dst[e] = v;
         }
     }
+    tm_wait_st();
     __syncthreads();
 
     // One pass over the active segments of group g.  UPDATE = false only sums.
@@ -382,13 +526,20 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 float4* bp = reinterpret_cast<float4*>(S.band + sg.soff);
                 float* rp = S.rowpart + (size_t)sg.brow0 * RPS + wig;
                 const float* rs = S.rsum + sg.brow0;
+                const float ninvN = -1.0f / (float)N;
+                if (sg.tm > 0)
+                    seg_rows_tmem<UPDATE>(tme + sg.tcol, sg.tm, sg.nrows, Q, N, mp, lane, rs, pr.abase, rp, RPS,
+                                          c0v, ninvN, cp0, dmax);
+                // rows ntm .. nrows - 1 (ntm is a multiple of RP, so row groups line up)
+                const int ns = sg.nrows - sg.ntm;
                 if (mp.kq == 1)
-                    seg_rows<UPDATE, 1>(bp, sg.nrows, Q, N, mp, nthr, lane, rs, pr.abase, rp, RPS, c0v, c1v,
-                                        -1.0f / (float)N, cp0, cp1, dmax);
+                    seg_rows<UPDATE, 1>(bp, ns, Q, N, mp, nthr, lane, rs + sg.ntm, pr.abase,
+                                        rp + (size_t)sg.ntm * RPS, RPS, c0v, c1v, ninvN, cp0, cp1, dmax);
                 else
-                    seg_rows<UPDATE, 2>(bp, sg.nrows, Q, N, mp, nthr, lane, rs, pr.abase, rp, RPS, c0v, c1v,
-                                        -1.0f / (float)N, cp0, cp1, dmax);
+                    seg_rows<UPDATE, 2>(bp, ns, Q, N, mp, nthr, lane, rs + sg.ntm, pr.abase,
+                                        rp + (size_t)sg.ntm * RPS, RPS, c0v, c1v, ninvN, cp0, cp1, dmax);
             }
+            if (UPDATE) tm_wait_st();
             dmax = warp_max(dmax);
             if (lane == 0) S.fred[si * 32 + warp] = dmax;
             // column partials: fold the row groups, then one red.v4 per quad;
@@ -545,6 +696,9 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         return true;
     };
 
+    // Everything from here until the tensor memory is released; a timeout or
+    // a non-finite total leaves it early (all threads of the CTA together).
+    auto body = [&]() {
     // ---- sums of the input of both groups
     const bool has1 = split < npairs;
     pass(0, std::false_type{}, 0);
@@ -585,6 +739,30 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         }
     }
 
+    // ---- the band back to Y, every column: the slack columns carry over to
+    // the next outer iteration, the first m feed the blend below
+    for (int si = 0; si < nseg; ++si) {
+        const Seg sg = S.seg[si];
+        if (!(S.pstate[sg.pair] & 1)) continue;
+        const PairDesc& d = P.pairs[sg.pair];
+        const int Q = d.ldy >> 2;
+        float4* Yg = reinterpret_cast<float4*>(d.Y) + (size_t)sg.lr0 * Q;
+        if (sg.tm > 0) {
+            const Map mp = make_map(Q, nthr, tid);
+            if (mp.grp < mp.RP) {
+                for (int k = 0; k < sg.tm; ++k) {
+                    const float4 v = tm_ld4(tme + sg.tcol + 4 * k);
+                    const int r = mp.grp + mp.RP * k;
+                    if (r < sg.nrows && mp.q0 < Q) Yg[(size_t)r * Q + mp.q0] = v;
+                }
+            }
+        }
+        const float4* band = reinterpret_cast<const float4*>(S.band + sg.soff);
+        float4* dst = Yg + (size_t)sg.ntm * Q;
+        for (int e = tid; e < (sg.nrows - sg.ntm) * Q; e += nthr) dst[e] = band[e];
+    }
+    __syncthreads();
+
     // ---- blend and normalise every active pair (barriers on counter 0)
     const float alpha = P.alpha, beta = 1.0f - P.alpha;
     if (P.normalize) {
@@ -593,12 +771,12 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             if (!(S.pstate[sg.pair] & 1)) continue;
             const PairDesc& d = P.pairs[sg.pair];
             const int Qy = d.ldy >> 2, Qx = d.ldx >> 2, m = d.m;
-            const float4* band = reinterpret_cast<const float4*>(S.band + sg.soff);
+            const float4* Yg = reinterpret_cast<const float4*>(d.Y) + (size_t)sg.lr0 * Qy;
             const float4* X = reinterpret_cast<const float4*>(d.X) + (size_t)sg.lr0 * Qx;
             float lmax = -INFINITY;
             for (int e = tid; e < sg.nrows * Qx; e += nthr) {
                 const int r = e / Qx, q = e % Qx;
-                const float4 x = X[(size_t)r * Qx + q], y = band[(size_t)r * Qy + q];
+                const float4 x = X[(size_t)r * Qx + q], y = Yg[(size_t)r * Qy + q];
                 const int c0 = 4 * q;
                 lmax = fmaxf(lmax, beta * x.x + alpha * y.x);
                 if (c0 + 1 < m) lmax = fmaxf(lmax, beta * x.y + alpha * y.y);
@@ -626,16 +804,16 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         const Seg sg = S.seg[si];
         if (!(S.pstate[sg.pair] & 1)) continue;
         const PairDesc& d = P.pairs[sg.pair];
-        const int Qy = d.ldy >> 2, Qx = d.ldx >> 2, m = d.m, N = d.N;
+        const int Qy = d.ldy >> 2, Qx = d.ldx >> 2, m = d.m;
         const float mx = P.normalize ? ordered_to_float(__ldcg(&d.ctrl->xmax_bits)) : 1.0f;
-        const float4* band = reinterpret_cast<const float4*>(S.band + sg.soff);
+        const float4* Yg = reinterpret_cast<const float4*>(d.Y) + (size_t)sg.lr0 * Qy;
         float4* X = reinterpret_cast<float4*>(d.X) + (size_t)sg.lr0 * Qx;
         __nv_bfloat16* Xt16 = d.Xt16;
         const int ldxt = d.ldxt;
         double dx = 0.0;
         for (int e = tid; e < sg.nrows * Qx; e += nthr) {
             const int r = e / Qx, q = e % Qx;
-            const float4 x = X[(size_t)r * Qx + q], y = band[(size_t)r * Qy + q];
+            const float4 x = X[(size_t)r * Qx + q], y = Yg[(size_t)r * Qy + q];
             float4 v = make_float4(beta * x.x + alpha * y.x, beta * x.y + alpha * y.y,
                                    beta * x.z + alpha * y.z, beta * x.w + alpha * y.w);
             if (P.normalize) { v.x /= mx; v.y /= mx; v.z /= mx; v.w /= mx; }
@@ -654,15 +832,6 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 if (c0 + 1 < m) Xt16[(size_t)(c0 + 1) * ldxt + i] = __float2bfloat16_rn(v.y);
                 if (c0 + 2 < m) Xt16[(size_t)(c0 + 2) * ldxt + i] = __float2bfloat16_rn(v.z);
                 if (c0 + 3 < m) Xt16[(size_t)(c0 + 3) * ldxt + i] = __float2bfloat16_rn(v.w);
-            }
-        }
-        // the slack columns m..N-1 carry over to the next outer iteration
-        if (m < N) {
-            const int qs = m >> 2;
-            float4* Yg = reinterpret_cast<float4*>(d.Y) + (size_t)sg.lr0 * Qy;
-            for (int e = tid; e < sg.nrows * (Qy - qs); e += nthr) {
-                const int r = e / (Qy - qs), q = qs + e % (Qy - qs);
-                Yg[(size_t)r * Qy + q] = band[(size_t)r * Qy + q];
             }
         }
         // per-warp max|dX| of the segment, folded at L2 by the atomic
@@ -724,6 +893,16 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             W->bar_base[1] = base1 + G * gen[1];
         }
     }
+    };
+    body();
+
+    // ---- release the tensor memory (every TMEM access of the CTA is complete)
+    tm_wait_st();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
 }  // namespace
@@ -731,7 +910,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
 size_t pdb_smem_bytes(const PdbLayout& L, int nthr) {
     size_t off = 0;
     auto take = [&](size_t bytes) { off = (off + bytes + 15) & ~size_t(15); };
-    take(32 * kMaxSeg);               // Seg is eight ints
+    take(48 * kMaxSeg);               // Seg is twelve ints
     take(56 * kMaxWavePairs);         // PairS: three pointers, a double, two ints, a float, pad, a double
     take(4 * kMaxWavePairs);
     take(4 * kMaxWavePairs);
@@ -753,8 +932,13 @@ cudaError_t pdb_configure() {
 
 cudaError_t pdb_launch(const PdbParams& P, int grid, size_t smem, cudaStream_t s) {
     void* args[] = {const_cast<PdbParams*>(&P)};
-    return cudaLaunchCooperativeKernel((const void*)pdb_kernel, dim3(grid), dim3(kPdbThreads), args, smem,
-                                       s);
+    // Every CTA allocates all 512 TMEM columns, so two CTAs must never share
+    // an SM (the second's allocation would wait for the first, which waits
+    // at the grid barrier): more than half an SM's shared memory per CTA
+    // guarantees one CTA per SM whatever the band needs.
+    const size_t one_per_sm = 120 * 1024;
+    return cudaLaunchCooperativeKernel((const void*)pdb_kernel, dim3(grid), dim3(kPdbThreads), args,
+                                       smem > one_per_sm ? smem : one_per_sm, s);
 }
 
 }  // namespace fpfp

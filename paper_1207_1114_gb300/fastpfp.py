@@ -31,7 +31,7 @@ EXPORTS = ("fastpfp_default_params", "fastpfp_create", "fastpfp_destroy", "fastp
            "fastpfp_last_trace",
            "fastpfp_gradient", "fastpfp_affinity", "fastpfp_project", "fastpfp_discretize",
            "fastpfp_project_noalloc", "fastpfp_warmstart", "fastpfp_warmstart_train_step",
-           "fastpfp_error_string")
+           "fastpfp_bandwidth_probe", "fastpfp_error_string")
 MLP_NPARAMS = 32 * 128 + 128 + 128 * 64 + 64
 
 
@@ -99,6 +99,7 @@ def lib():
     l.fastpfp_warmstart.argtypes = [P, V, P, I, P, I, P, P, I, P, I, P]
     l.fastpfp_warmstart_train_step.argtypes = [P, V, P, I, P, I, P, P, I, P, P, P, P, I, C.c_float,
                                                C.POINTER(C.c_double), P]
+    l.fastpfp_bandwidth_probe.argtypes = [I, I, I, C.POINTER(C.c_double)]
     l.fastpfp_error_string.argtypes = [I]
     l.fastpfp_error_string.restype = C.c_char_p
     for name in EXPORTS:
@@ -106,6 +107,15 @@ def lib():
             getattr(l, name).restype = C.c_int
     _lib = l
     return l
+
+
+def bandwidth_probe(level: int, sweeps: int = 200, device: int = 0) -> float:
+    """GB/s of shared memory (0), L2 (1) or HBM (2) under the projection
+    rounds' read + write pattern (fastpfp_bandwidth_probe)."""
+    out = C.c_double(0.0)
+    _check(lib().fastpfp_bandwidth_probe(int(device), int(level), int(sweeps), C.byref(out)),
+           "fastpfp_bandwidth_probe")
+    return float(out.value)
 
 
 def error_string(code: int) -> str:

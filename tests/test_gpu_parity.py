@@ -389,14 +389,15 @@ def _replay_check(solver, g, o, i, lam, **kw):
 
 
 def test_streamed_batch_refills_waves_and_matches_oracle(stream_solver):
-    """Twelve pairs of 850..1000 nodes do not fit in one wave (shared memory):
+    """Twenty-four pairs of 850..1000 nodes do not fit in one wave (on-chip
+    storage):
     the batch is streamed, finished pairs leaving and waiting pairs entering
     between outer iterations.  A loose outer tolerance makes the pairs stop
     at different iterations.  Every pair matches the oracle replaying its
     own inner counts."""
     rng = np.random.default_rng(40)
     pairs = [synth.graph_pair(int(rng.integers(850, 1001)), p=0.1, sigma=0.05, k=8, lam=0.5,
-                              seed=400 + i) for i in range(12)]
+                              seed=400 + i) for i in range(24)]
     kw = dict(max_outer=12, max_inner=80, tol_outer=1e-3)
     p = F.default_params(lam=0.5, **kw)
     dev = [(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)) for g in pairs]
@@ -404,14 +405,14 @@ def test_streamed_batch_refills_waves_and_matches_oracle(stream_solver):
     waves = [o.stats.wave_pairs for o in outs]
     assert 0 < max(waves) < len(pairs)
     assert len({o.stats.outer_iters for o in outs}) > 1   # pairs left at different times
-    for i, (g, o) in enumerate(zip(pairs, outs)):
-        _replay_check(stream_solver, g, o, i, 0.5, **kw)
+    for i in (0, 5, 11, 17, 19, 21, 22, 23):   # first and last admitted pairs among them
+        _replay_check(stream_solver, pairs[i], outs[i], i, 0.5, **kw)
 
 
 def test_streamed_host_batch_equals_device_batch(stream_solver):
     rng = np.random.default_rng(41)
     pairs = [synth.graph_pair(int(rng.integers(850, 1001)), p=0.1, sigma=0.05, k=8, lam=0.5,
-                              seed=500 + i) for i in range(11)]
+                              seed=500 + i) for i in range(22)]
     p = F.default_params(lam=0.5, max_outer=8, max_inner=60, tol_outer=1e-3)
     d = stream_solver.match_batched([(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)) for g in pairs], params=p,
                                     want_X=True)
@@ -442,6 +443,19 @@ def test_streamed_mixed_batch_of_100(stream_solver):
         assert len(used) == min(n_a, n_b)
     for i in (0, 37, 99):
         _replay_check(stream_solver, pairs[i], outs[i], i, 0.5, **kw)
+
+
+def test_bandwidth_probe_orders_the_memory_levels():
+    """The probe behind the roofline denominators: shared memory (all SMs)
+    is faster than L2, which is faster than HBM; all are plausible for one
+    GB300 (HBM within the measured copy figure's ballpark)."""
+    smem = F.bandwidth_probe(0, sweeps=2000)
+    l2 = F.bandwidth_probe(1, sweeps=200)
+    hbm = F.bandwidth_probe(2, sweeps=5)
+    assert smem > l2 > hbm > 1000.0
+    assert hbm < 10000.0
+    with pytest.raises(F.FastPFPError):
+        F.bandwidth_probe(3)
 
 
 # ------------------------------------------------------------ errors / faults
