@@ -65,6 +65,9 @@ struct Slot {
     // device staging of host-memory inputs and outputs (the *_host calls)
     float *sA, *sA2, *sB, *sB2, *sX0, *sXout;
     int32_t* sperm;
+    // 16-byte-row copies of A and A' for the FP32 products when the caller's
+    // rows are not 16-byte aligned
+    float *A32, *A232;
 };
 
 }  // namespace
@@ -173,6 +176,20 @@ Problem canonical(const float* A, int n_a, const float* A2, int n_b, const float
 
 // ---- the per-pair pieces of a solve ---------------------------------------
 
+// An n x n adjacency as an operand of the FP32 products: the caller's
+// matrix when its rows start on 16-byte boundaries, else the padded copy
+// made by enqueue_setup.
+inline bool rows16(const float* p, int n) { return ((uintptr_t)p & 15u) == 0 && (n & 3) == 0; }
+inline const float* f32_operand(const float* A, int n, float* padded, int* ld) {
+    if (rows16(A, n)) {
+        *ld = n;
+        return A;
+    }
+    *ld = round4(n);
+    return padded;
+}
+
+
 // Control block, accumulators and Y cleared; K and the initial X written.
 // A solve that stopped on an error may leave the accumulators dirty, so every
 // solve starts from cleared ones.  Returns the kernels launched or < 0.
@@ -192,6 +209,13 @@ int enqueue_setup(const Slot& sl, cudaStream_t s, const Problem& q, const fastpf
         ++nl;
     }
     FP_CUDA(init_x(sl.X, q.N, q.m, ldx, q.X0, q.transposed, bf16 ? sl.Xt16 : nullptr, round8(q.N), s));
+    // 16-byte rows of A and A' for the FP32 products (only when the caller's are not)
+    if (!rows16(q.A, q.N))
+        FP_CUDA(cudaMemcpy2DAsync(sl.A32, (size_t)round4(q.N) * 4, q.A, (size_t)q.N * 4, (size_t)q.N * 4, q.N,
+                                  cudaMemcpyDeviceToDevice, s));
+    if (!rows16(q.A2, q.m))
+        FP_CUDA(cudaMemcpy2DAsync(sl.A232, (size_t)round4(q.m) * 4, q.A2, (size_t)q.m * 4, (size_t)q.m * 4, q.m,
+                                  cudaMemcpyDeviceToDevice, s));
     if (bf16) {
         // BF16 operand copies of A and A' for the tensor-core products
         FP_CUDA(to_bf16(q.A, q.N, q.N, q.N, sl.A16, round8(q.N), s));
@@ -201,15 +225,27 @@ int enqueue_setup(const Slot& sl, cudaStream_t s, const Problem& q, const fastpf
     return nl;
 }
 
-// The gradient of Section 4.1 in FP32: T = A X, then Y[:, :m] = T A' + lambda K.
+// The gradient products of Section 4.1 in FP32 for one pair, as the
+// transposed-operand GEMM consumes them:
+//   T^T (m x N, in slot T, ld round4(N)) = X^T A
+//   Y[:, :m] = (T^T)^T A' + lambda K.
 // Skipped on the device while the solve runs its BF16 phase.
+void f32_products(const Slot& sl, const Problem& q, const fastpfp_params* p, GemmF32TArgs* g1, GemmF32TArgs* g2) {
+    const int ldy = round4(q.N), ldx = round4(q.m), ldt = round4(q.N);
+    int lda = 0, lda2 = 0;
+    const float* A = f32_operand(q.A, q.N, sl.A32, &lda);
+    const float* A2 = f32_operand(q.A2, q.m, sl.A232, &lda2);
+    *g1 = GemmF32TArgs{sl.X, ldx, A, lda, sl.T, ldt, nullptr, 0, 0.f, q.m, q.N, q.N, sl.ctrl};
+    *g2 = GemmF32TArgs{sl.T, ldt, A2, lda2, sl.Y, ldy, q.k ? sl.K : nullptr, ldx,
+                       q.k ? (float)p->lambda : 0.f, q.N, q.m, q.m, sl.ctrl};
+}
+
 int enqueue_gradient(const Slot& sl, cudaStream_t s, const Problem& q, const fastpfp_params* p) {
-    const int ldy = round4(q.N), ldx = round4(q.m);
-    GemmF32Args g1{q.A, q.N, sl.X, ldx, sl.T, ldx, nullptr, 0, 0.f, q.N, q.m, q.N, sl.ctrl};
-    GemmF32Args g2{sl.T, ldx, q.A2, q.m, sl.Y, ldy, q.k ? sl.K : nullptr, ldx,
-                   q.k ? (float)p->lambda : 0.f, q.N, q.m, q.m, sl.ctrl};
-    FP_CUDA(gemm_f32(g1, s));
-    FP_CUDA(gemm_f32(g2, s));
+    GemmF32TGroup g1{}, g2{};
+    g1.count = g2.count = 1;
+    f32_products(sl, q, p, &g1.a[0], &g2.a[0]);
+    FP_CUDA(gemm_f32t_group(g1, s));
+    FP_CUDA(gemm_f32t_group(g2, s));
     return 2;
 }
 
@@ -706,20 +742,14 @@ PdbParams wave_params(fastpfp_t h, const Wave& w, int npairs, const fastpfp_para
 // FP32 products of every member: one grouped launch per product and
 // kF32MaxGroup members.
 void f32_groups(fastpfp_t h, const std::vector<Problem>& qs, const std::vector<Member>& mem,
-                const fastpfp_params* p, std::vector<GemmF32Group>& ga_out, std::vector<GemmF32Group>& gb_out) {
+                const fastpfp_params* p, std::vector<GemmF32TGroup>& ga_out, std::vector<GemmF32TGroup>& gb_out) {
     ga_out.clear();
     gb_out.clear();
     for (int b = 0; b < (int)mem.size(); b += kF32MaxGroup) {
-        GemmF32Group ga{}, gb{};
+        GemmF32TGroup ga{}, gb{};
         ga.count = gb.count = std::min(kF32MaxGroup, (int)mem.size() - b);
-        for (int i = 0; i < ga.count; ++i) {
-            const Problem& q = qs[mem[b + i].pair];
-            const Slot& sl = h->slots[mem[b + i].slot];
-            const int ldy = round4(q.N), ldx = round4(q.m);
-            ga.a[i] = GemmF32Args{q.A, q.N, sl.X, ldx, sl.T, ldx, nullptr, 0, 0.f, q.N, q.m, q.N, sl.ctrl};
-            gb.a[i] = GemmF32Args{sl.T, ldx, q.A2, q.m, sl.Y, ldy, q.k ? sl.K : nullptr, ldx,
-                                  q.k ? (float)p->lambda : 0.f, q.N, q.m, q.m, sl.ctrl};
-        }
+        for (int i = 0; i < ga.count; ++i)
+            f32_products(h->slots[mem[b + i].slot], qs[mem[b + i].pair], p, &ga.a[i], &gb.a[i]);
         ga_out.push_back(ga);
         gb_out.push_back(gb);
     }
@@ -755,7 +785,7 @@ int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, co
     const int wt = write_wave_tables(h, s, qs, mem, w, bf16);
     if (wt < 0) return wt;
     const PdbParams P = wave_params(h, w, w.count, p);
-    std::vector<GemmF32Group> f32a, f32b;
+    std::vector<GemmF32TGroup> f32a, f32b;
     f32_groups(h, qs, mem, p, f32a, f32b);
     const bool prof = p->profile != 0;
     static_assert(offsetof(WaveCtrl, error) == 0 && offsetof(WaveCtrl, all_done) == 4,
@@ -769,8 +799,8 @@ int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, co
             n = enqueue_tc(tc, st);
             if (n < 0) return n;
         }
-        for (const GemmF32Group& g : f32a) FP_CUDA(gemm_f32_group(g, st));   // T = A X
-        for (const GemmF32Group& g : f32b) FP_CUDA(gemm_f32_group(g, st));   // Y = T A' + lambda K
+        for (const GemmF32TGroup& g : f32a) FP_CUDA(gemm_f32t_group(g, st));   // T^T = X^T A
+        for (const GemmF32TGroup& g : f32b) FP_CUDA(gemm_f32t_group(g, st));   // Y = T A' + lambda K
         n += (int)(f32a.size() + f32b.size());
         if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 1], st));
         FP_CUDA(pdb_launch(P, w.grid, w.smem, st));
@@ -846,6 +876,7 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     h->nslots = std::min(max_batch, kMaxWavePairs);
     if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         pd_configure() != cudaSuccess || pdb_configure() != cudaSuccess || tc_configure() != cudaSuccess ||
+        gemm_f32t_configure() != cudaSuccess ||
         disc_configure() != cudaSuccess) {
         delete h;
         return FASTPFP_ERR_CUDA;
@@ -857,7 +888,7 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
     struct SlotOff {
         size_t Y, X, T, K, A16, A216, Xt16, T16, col, s, d, ctrl, rm, cm, rb, cb, sA, sA2, sB, sB2, sX0,
-            sXo, sp;
+            sXo, sp, A32, A232;
     };
     std::vector<SlotOff> so(h->nslots);
     for (auto& o : so) {
@@ -868,6 +899,7 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
         o.rm = take(n * 4); o.cm = take(n * 4); o.rb = take(n * 8); o.cb = take(2 * n * 8);
         o.sA = take(n * n * 4); o.sA2 = take(n * n * 4); o.sB = take(n * kMaxK * 4);
         o.sB2 = take(n * kMaxK * 4); o.sX0 = take(n * n * 4); o.sXo = take(n * n * 4); o.sp = take(n * 4);
+        o.A32 = take(f32mat); o.A232 = take(f32mat);
     }
     const size_t opairs = take(sizeof(PairDesc) * kMaxWavePairs);
     const size_t oband = take(sizeof(int) * 2 * (h->num_sms + 1));
@@ -933,6 +965,8 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
         sl.sB2 = (float*)(b + o.sB2);
         sl.sX0 = (float*)(b + o.sX0);
         sl.sXout = (float*)(b + o.sXo);
+        sl.A32 = (float*)(b + o.A32);
+        sl.A232 = (float*)(b + o.A232);
         sl.sperm = (int32_t*)(b + o.sp);
     }
     h->d_pairs = (PairDesc*)(b + opairs);
@@ -1106,7 +1140,7 @@ int solve_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, const fa
     };
     std::vector<Problem> cand;
     std::vector<int> cand_slots;
-    std::vector<GemmF32Group> f32a, f32b;
+    std::vector<GemmF32TGroup> f32a, f32b;
     int launch_no = 0;
     while (true) {
         // admit waiting pairs while the wave still fits on chip
@@ -1194,10 +1228,10 @@ int solve_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, const fa
             if (r < 0) return fail(r);
             kl += r;
         }
-        for (const GemmF32Group& g : f32a)
-            if (gemm_f32_group(g, s) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
-        for (const GemmF32Group& g : f32b)
-            if (gemm_f32_group(g, s) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
+        for (const GemmF32TGroup& g : f32a)
+            if (gemm_f32t_group(g, s) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
+        for (const GemmF32TGroup& g : f32b)
+            if (gemm_f32t_group(g, s) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
         kl += (int)(f32a.size() + f32b.size());
         if (prof && cudaEventRecord(h->ev[1], s) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
         if (pdb_launch(P, w.grid, w.smem, s) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
@@ -1392,10 +1426,25 @@ int fastpfp_gradient(fastpfp_t h, void* stream, const float* A, const float* X, 
                                   cudaMemcpyDeviceToDevice, s));
         return FASTPFP_OK;
     }
-    GemmF32Args g1{A, N, X, m, sl.T, m, nullptr, 0, 0.f, N, m, N, nullptr};
-    GemmF32Args g2{sl.T, m, A2, m, Y, ldy, lambda != 0.f ? K : nullptr, m, lambda, N, m, m, nullptr};
-    FP_CUDA(gemm_f32(g1, s));
-    FP_CUDA(gemm_f32(g2, s));
+    // the solve's FP32 products: X staged with 16-byte rows, A and A' used
+    // in place when their rows are 16-byte aligned
+    const int ldx = round4(m), ldt = round4(N);
+    FP_CUDA(cudaMemcpy2DAsync(sl.X, (size_t)ldx * 4, X, (size_t)m * 4, (size_t)m * 4, N, cudaMemcpyDeviceToDevice, s));
+    if (!rows16(A, N))
+        FP_CUDA(cudaMemcpy2DAsync(sl.A32, (size_t)ldt * 4, A, (size_t)N * 4, (size_t)N * 4, N,
+                                  cudaMemcpyDeviceToDevice, s));
+    if (!rows16(A2, m))
+        FP_CUDA(cudaMemcpy2DAsync(sl.A232, (size_t)ldx * 4, A2, (size_t)m * 4, (size_t)m * 4, m,
+                                  cudaMemcpyDeviceToDevice, s));
+    int lda = 0, lda2 = 0;
+    const float* Aop = f32_operand(A, N, sl.A32, &lda);
+    const float* A2op = f32_operand(A2, m, sl.A232, &lda2);
+    GemmF32TGroup g1{}, g2{};
+    g1.count = g2.count = 1;
+    g1.a[0] = GemmF32TArgs{sl.X, ldx, Aop, lda, sl.T, ldt, nullptr, 0, 0.f, m, N, N, nullptr};
+    g2.a[0] = GemmF32TArgs{sl.T, ldt, A2op, lda2, Y, ldy, lambda != 0.f ? K : nullptr, m, lambda, N, m, m, nullptr};
+    FP_CUDA(gemm_f32t_group(g1, s));
+    FP_CUDA(gemm_f32t_group(g2, s));
     return FASTPFP_OK;
 }
 

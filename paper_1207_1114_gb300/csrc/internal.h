@@ -150,7 +150,7 @@ size_t pdb_smem_bytes(const PdbLayout& L, int nthr);
 cudaError_t pdb_launch(const PdbParams& P, int grid, size_t smem, cudaStream_t s);
 
 // ------------------------------------------------- tensor-core products
-constexpr int kTcMaxGroup = 8;       // problems of one grouped launch
+constexpr int kTcMaxGroup = 32;      // problems of one grouped launch (a whole wave)
 constexpr int kTcOutBf16 = 0;        // epilogue writes BF16 (T = A X)
 constexpr int kTcOutF32 = 1;         // epilogue writes FP32 + lambda K (Y = T A' + lambda K)
 
@@ -192,12 +192,30 @@ struct GemmF32Args {
 cudaError_t gemm_f32(const GemmF32Args& a, cudaStream_t s);
 
 // Up to kF32MaxGroup independent products in one launch (blockIdx.z).
-constexpr int kF32MaxGroup = 8;
+constexpr int kF32MaxGroup = 32;   // a whole wave in one launch per product
 struct GemmF32Group {
     GemmF32Args a[kF32MaxGroup];
     int count;
 };
 cudaError_t gemm_f32_group(const GemmF32Group& g, cudaStream_t s);
+
+// C[M x Nc] = AT^T B (+ lambda * Kmat): the left operand supplied transposed
+// (AT is K x M row-major), B is K x Nc row-major.  AT, B 16-byte aligned,
+// lda, ldb multiples of 4.  Same control gating as GemmF32Args.
+struct GemmF32TArgs {
+    const float* AT; int lda;
+    const float* B; int ldb;
+    float* C; int ldc;
+    const float* Kmat; int ldk; float lambda;
+    int M, Nc, K;
+    const Ctrl* ctrl;
+};
+struct GemmF32TGroup {
+    GemmF32TArgs a[kF32MaxGroup];
+    int count;
+};
+cudaError_t gemm_f32t_configure();
+cudaError_t gemm_f32t_group(const GemmF32TGroup& g, cudaStream_t s);
 
 // ------------------------------------------------------ bandwidth probes
 // Read + write sweeps of shared memory (all SMs) or of one global buffer;
