@@ -515,9 +515,9 @@ struct BandStats {
 
 // Band cost model of pdb_kernel, in entry equivalents: a band costs its
 // entries plus kSegCost for every pair it spans (a segment brings its own
-// column fold, reductions and read-back; measured on GB300 at about 3500
-// cycles against 0.12 cycles per entry).
-constexpr long long kSegCost = 24576;
+// loop tails, reductions and read-back; measured on GB300 at about 1800
+// cycles against 0.115 cycles per entry).
+constexpr long long kSegCost = 16384;
 
 // Greedy cut of the concatenated rows of pairs [first, first + count) into
 // consecutive bands of cost at most C: each band takes as many rows as fit.

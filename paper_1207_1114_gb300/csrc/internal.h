@@ -14,7 +14,7 @@ struct Ctrl;
 // ------------------------------------------------------------ projection
 constexpr int kPdOuterStep = 1;     // P_D rounds + blend/normalise + loop control
 constexpr int kPdProjectOnly = 0;   // P_D rounds only (fastpfp_project)
-constexpr int kPdMaxSmem = 220 * 1024;
+constexpr int kPdMaxSmem = 226 * 1024;   // dynamic shared memory per CTA (the opt-in limit is 227 KB)
 constexpr long long kPdElemsPerCta = 8192;  // target band size of one CTA
 
 struct PdParams {

@@ -59,13 +59,11 @@ struct Shared {
     PairS* pair;         // kMaxWavePairs
     int* pstate;         // kMaxWavePairs: bit0 active this launch, bit1 stopped
     int* pstop;          // kMaxWavePairs: round at which the pair stopped
-    int* ictl;           // [0],[1] group has an active pair, [2] n segments, [3] non-finite,
-                         // [4],[5] group has a segment whose row sums are folded in publish
+    int* ictl;           // [0],[1] group has an active pair, [2] n segments, [3] non-finite
     int* qpref;          // 2 x (kMaxWavePairs + 1): per group, prefix sums of the pairs' column quads
     float* fred;         // kMaxSeg x 32 per-warp maxima
     float* rsum;         // band rows
     float* rowpart;      // band rows x rp_stride per-warp row partials
-    float4* cred;        // nthr float4: column-partial reduction across row groups
     float* cN;           // sum over segments of ldy floats: the column sums c_j of the last round
     float* band;         // band rows of every segment (16-byte aligned)
 };
@@ -87,7 +85,6 @@ __device__ __forceinline__ Shared carve_b(char* base, const PdbLayout& L, int nt
     s.fred = reinterpret_cast<float*>(take(sizeof(float) * kMaxSeg * 32));
     s.rsum = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_rows));
     s.rowpart = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_rows * L.rp_stride));
-    s.cred = reinterpret_cast<float4*>(take(sizeof(float4) * nthr));
     s.cN = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_cols));
     s.band = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_elems));
     return s;
@@ -407,11 +404,6 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         }
         S.ictl[2] = nseg;
         S.ictl[3] = 0;
-        S.ictl[4] = S.ictl[5] = 0;
-        for (int si = 0; si < nseg; ++si) {
-            const int QP = ((P.pairs[S.seg[si].pair].ldy >> 2) + 31) & ~31;
-            if (QP > (nthr >> 1)) S.ictl[4 + S.seg[si].group] = 1;
-        }
         for (int g = 0; g < 2; ++g) {
             const int p0 = g == 0 ? 0 : split, p1 = g == 0 ? split : npairs;
             int* qp = S.qpref + g * (kMaxWavePairs + 1);
@@ -542,34 +534,28 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             if (UPDATE) tm_wait_st();
             dmax = warp_max(dmax);
             if (lane == 0) S.fred[si * 32 + warp] = dmax;
-            // column partials: fold the row groups, then one red.v4 per quad;
-            // meanwhile the warps past the quads fold the row sums
+            // column partials: every row group adds its own, one red.v4 per
+            // quad (L2 folds the row groups; no block-wide fold, no barrier)
             float* acc = pr.colbuf + (size_t)cur * pr.ldy;
-            if (mp.RP > 1) {
-                S.cred[tid] = (in_grp && mp.q0 < Q) ? cp0 : make_float4(0.f, 0.f, 0.f, 0.f);
-                __syncthreads();
-                const int QW = (Q + 31) & ~31;
-                if (tid < Q) {
-                    float4 t = S.cred[tid];
-                    for (int gg = 1; gg < mp.RP; ++gg) {
-                        const float4 v = S.cred[gg * mp.QP + tid];
-                        t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
-                    }
-                    red_add_v4(acc + 4 * tid, t.x, t.y, t.z, t.w);
-                } else if (tid >= QW) {
-                    const int nw = mp.QP >> 5;
-                    for (int r = tid - QW; r < sg.nrows; r += nthr - QW) {
-                        const float* rpp = S.rowpart + (size_t)(sg.brow0 + r) * RPS;
-                        float t = 0.f;
-                        for (int w = 0; w < nw; ++w) t += rpp[w];
-                        S.rsum[sg.brow0 + r] = t;
-                    }
-                }
-                __syncthreads();
-            } else {
+            if (in_grp) {
                 if (mp.q0 < Q) red_add_v4(acc + 4 * mp.q0, cp0.x, cp0.y, cp0.z, cp0.w);
                 if (mp.kq > 1 && mp.q0 + nthr < Q)
                     red_add_v4(acc + 4 * (mp.q0 + nthr), cp1.x, cp1.y, cp1.z, cp1.w);
+            }
+        }
+        // the row sums of the group's segments, once every warp's partials are in
+        __syncthreads();
+        for (int si = 0; si < nseg; ++si) {
+            const Seg sg = S.seg[si];
+            if (sg.group != g) continue;
+            const int pst = S.pstate[sg.pair];
+            if (!(pst & 1) || (pst & 2)) continue;
+            const int nw = pdb_row_warps(S.pair[sg.pair].ldy, nthr);
+            for (int r = tid; r < sg.nrows; r += nthr) {
+                const float* rpp = S.rowpart + (size_t)(sg.brow0 + r) * RPS;
+                float t = 0.f;
+                for (int w = 0; w < nw; ++w) t += rpp[w];
+                S.rsum[sg.brow0 + r] = t;
             }
         }
     };
@@ -597,32 +583,13 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         }
     };
 
-    // End of group g's pass: the row sums of segments whose rows span the
-    // whole CTA (the others were folded in the pass), then warps 0 and 1
-    // publish the segments' totals and round maxima (alternate segments)
-    // while warps 2.. zero accumulator `clear_which` (>= 0) of the group's
-    // pairs; all of it precedes the arrival, so the zeros are visible before
-    // any CTA's next-round reductions.  A band's total (at most a few dozen
-    // FP32 row sums) is added in FP32 and accumulated over the CTAs in FP64.
+    // End of group g's pass: warps 0 and 1 publish the segments' totals and
+    // round maxima (alternate segments) while warps 2.. zero accumulator
+    // `clear_which` (>= 0) of the group's pairs; all of it precedes the
+    // arrival, so the zeros are visible before any CTA's next-round
+    // reductions.  A band's total (at most a few dozen FP32 row sums) is
+    // added in FP32 and accumulated over the CTAs in FP64.
     auto publish = [&](int g, int cur, int clear_which) {
-        if (S.ictl[4 + g] != 0) {   // some segment of the group folds its rows here
-            __syncthreads();
-            for (int si = 0; si < nseg; ++si) {
-                const Seg sg = S.seg[si];
-                if (sg.group != g) continue;
-                const int pst = S.pstate[sg.pair];
-                if (!(pst & 1) || (pst & 2)) continue;
-                const int QP = ((S.pair[sg.pair].ldy >> 2) + 31) & ~31;
-                if (QP <= (nthr >> 1)) continue;   // folded in the pass
-                const int nw = (QP <= nthr ? QP : nthr) >> 5;
-                for (int r = tid; r < sg.nrows; r += nthr) {
-                    const float* rp = S.rowpart + (size_t)(sg.brow0 + r) * RPS;
-                    float t = 0.f;
-                    for (int w = 0; w < nw; ++w) t += rp[w];
-                    S.rsum[sg.brow0 + r] = t;
-                }
-            }
-        }
         __syncthreads();
         if (warp < 2) {
             for (int si = warp; si < nseg; si += 2) {
@@ -919,7 +886,6 @@ size_t pdb_smem_bytes(const PdbLayout& L, int nthr) {
     take(4 * kMaxSeg * 32);
     take(4 * (size_t)L.max_band_rows);
     take(4 * (size_t)L.max_band_rows * L.rp_stride);
-    take(16 * (size_t)nthr);
     take(4 * (size_t)L.max_band_cols);
     take(4 * (size_t)L.max_band_elems);
     return off;
