@@ -40,7 +40,7 @@ WORKLOADS = {
     "attributed_1000": dict(n=1000, n2=1000, p=0.1, sigma=0.05, k=16, attr_sigma=0.05, lam=1.0,
                             batch=64, metric=METRIC),
     "partial_1000_1200": dict(n=1000, n2=1200, outliers=200, p=0.1, sigma=0.03, k=16,
-                              attr_sigma=0.05, lam=0.5, batch=5,
+                              attr_sigma=0.05, lam=0.5, batch=64,
                               metric="fastpfp_pair_solves_per_s_partial_1000_1200"),
     "batch_mixed_512": dict(n="U{50..600}", n2="n+U{0..100}", p=0.15, sigma=0.03, k=8,
                             attr_sigma=0.05, lam=0.5, batch=512,
@@ -233,6 +233,47 @@ def oracle_solve_seconds(unit, N, m, outer, inner):
             + inner * unit["round"] * N * N)
 
 
+def train_warm_start(F, torch, dev, local, count, seed):
+    """The learned warm start of the large workload: `count` pairs shaped
+    like the partial workload (n in 200..800, up to n/5 outliers, 15-dim
+    attributes) are solved by the plain FP32 solver; their matchings are
+    the targets of one Adam pass (row + column softmax cross-entropy of
+    the similarity S, all on the GPU through fastpfp_warmstart_train_step).
+    Returns the trained parameters and a summary."""
+    from paper_1207_1114_gb300 import synth
+    t0 = time.perf_counter()
+    train = synth.warm_start_train(count, seed=seed)
+    t_gen = time.perf_counter() - t0
+    max_n = max(max(g.A.shape[0], g.A2.shape[0]) for g in train)
+    ts = F.Solver(max_n=max_n, max_batch=64, device=local)
+    prm = F.default_params(lam=0.5, **SOLVER)
+    t0 = time.perf_counter()
+    solved = []
+    for c in range(0, count, 64):
+        chunk = train[c:c + 64]
+        dev_chunk = [(torch.as_tensor(g.A, device=dev), torch.as_tensor(g.A2, device=dev),
+                      torch.as_tensor(g.B, device=dev), torch.as_tensor(g.B2, device=dev)) for g in chunk]
+        outs = ts.match_batched(dev_chunk, params=prm)
+        solved += [(d, o.perm) for d, o in zip(dev_chunk, outs)]
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    params = torch.as_tensor(F.init_mlp_params(seed), device=dev)
+    m = torch.zeros(F.MLP_NPARAMS, device=dev)
+    v = torch.zeros(F.MLP_NPARAMS, device=dev)
+    t0 = time.perf_counter()
+    losses = []
+    for step, (d, perm) in enumerate(solved, start=1):
+        loss, _ = ts.train_step(*d, perm, params, m, v, step=step, lr=3e-3)
+        losses.append(loss)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    ts.close()
+    k = max(1, min(50, len(losses) // 10))
+    return params, {"train_pairs": count, "train_shape": "n in 200..800, up to n/5 outliers, k=15, lambda=0.5",
+                    "seconds": {"generate_cpu": t_gen, "solve_gpu": t_solve, "train_gpu": t_train},
+                    "loss_first": float(np.mean(losses[:k])), "loss_last": float(np.mean(losses[-k:]))}
+
+
 def run_reference(args, rank, world):
     """--impl reference: the FP64 CPU oracle as it stands, on the host cores.
     Each step is a bounded sample of the n = 1000 workload, extrapolated with
@@ -286,6 +327,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
                     help="gradient products: plain FP32, or BF16 tensor cores + FP32 refinement")
+    ap.add_argument("--init", default="uniform", choices=["uniform", "learned"],
+                    help="X(0): the paper's uniform start, or the learned warm start (trained first, "
+                         "on --train-pairs pairs solved by the plain solver)")
+    ap.add_argument("--train-pairs", type=int, default=2000, dest="train_pairs")
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="outer loop: CUDA-graph while node (default) or host-polled chunks")
     args = ap.parse_args()
@@ -324,6 +369,18 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    # learned warm start: train the MLP on pairs solved by the plain solver,
+    # then every step computes X(0) for its pairs before solving them
+    ws_info, mlp = None, None
+    if args.init == "learned":
+        mlp, ws_info = train_warm_start(F, torch, dev, local, args.train_pairs, seed=rank + 11)
+
+    def solve(prm):
+        if mlp is None:
+            return solver.match_batched(dpairs, params=prm)
+        x0 = [solver.warmstart(*dp, mlp, iters=20) for dp in dpairs]
+        return solver.match_batched([dp + (x,) for dp, x in zip(dpairs, x0)], params=prm)
+
     loop_mode = 0 if args.loop == "graph" else 1
     p_plain = params(F, lam, precision=args.precision, loop_mode=loop_mode)
     p_prof = params(F, lam, profile=1, precision=args.precision)
@@ -332,7 +389,7 @@ def main():
     # the same batch right after them times every projection launch
     p_timed = p_prof if args.loop == "host" else p_plain
     for _ in range(args.warmup):
-        solver.match_batched(dpairs, params=p_plain)
+        solve(p_plain)
     # timed region: per-step CUDA events, L2 flushed (untimed) before every step
     step_ms, stats_all = [], []
     barrier()
@@ -342,7 +399,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            outs = solver.match_batched(dpairs, params=p_timed)
+            outs = solve(p_timed)
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
@@ -360,7 +417,7 @@ def main():
         timing = "CUDA events on the launching stream around every projection launch of the timed steps"
     else:
         flush.zero_()
-        prof_steps = [[o.stats for o in solver.match_batched(dpairs, params=p_prof)]]
+        prof_steps = [[o.stats for o in solve(p_prof)]]
         timing = ("CUDA events on the launching stream around every projection launch of one "
                   "instrumented pass (host-enqueued loop) of the timed batch, run after the timed steps")
     flat = [s for step in prof_steps for s in step]
@@ -422,6 +479,26 @@ def main():
     barrier()
     e2e_value = whole_job_rate(args.batch * e2e_steps, time.perf_counter() - t0, dev)
 
+    if ws_info is not None:
+        # the same pairs from the uniform start, same timing rules
+        u_ms, u_outer, u_acc = [], [], []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            uo = solver.match_batched(dpairs, params=p_plain)
+            e1.record(stream)
+            e1.synchronize()
+            u_ms.append(e0.elapsed_time(e1))
+            u_outer += [o.stats.outer_iters for o in uo]
+            u_acc += [float((o.perm.cpu().numpy() == g.gt).mean()) for o, g in zip(uo, pairs)]
+        ws_info["uniform"] = {"value": whole_job_rate(args.batch * args.steps, sum(u_ms) / 1e3, dev),
+                              "outer_per_pair": float(np.mean(u_outer)), "accuracy": float(np.mean(u_acc))}
+        ws_info["learned"] = {"value": value,
+                              "outer_per_pair": float(np.mean([s.outer_iters for st in stats_all for s in st])),
+                              "accuracy": float(np.mean(accs))}
+
     flat_t = [s for step in stats_all for s in step]
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -443,7 +520,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "bf16+f32", "data": "synthetic",
             "config": dict(workload=args.workload, **cfg, **SOLVER, pairs_per_step=args.batch,
-                           precision=args.precision, loop=args.loop,
+                           precision=args.precision, loop=args.loop, init=args.init,
                            l2="flushed (512 MB write) before every timed step",
                            parallelism=f"pairs sharded over {world} rank(s)"),
             "accuracy": float(np.mean(accs)),
@@ -463,6 +540,8 @@ def main():
             "gpu_launches": launches,
             "clocks": clk.summary(),
         }
+        if ws_info is not None:
+            line["warm_start"] = ws_info
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:

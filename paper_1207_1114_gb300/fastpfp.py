@@ -118,6 +118,19 @@ def bandwidth_probe(level: int, sweeps: int = 200, device: int = 0) -> float:
     return float(out.value)
 
 
+def init_mlp_params(seed: int = 0):
+    """Initial weights of the warm-start MLP (32 -> 128 -> 64) as one flat
+    float32 array in the library's packing [W1 (32x128), b1, W2 (128x64),
+    b2]: Glorot-uniform weights, zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_in, fan_out in ((32, 128), (128, 64)):
+        lim = np.sqrt(6.0 / (fan_in + fan_out))
+        parts.append(rng.uniform(-lim, lim, size=fan_in * fan_out))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
+
+
 def error_string(code: int) -> str:
     return lib().fastpfp_error_string(int(code)).decode()
 
@@ -237,23 +250,27 @@ class Solver:
         return MatchResult(perm, X, st)
 
     def match_batched(self, pairs, params=None, want_X=False, stream=None):
-        """pairs: list of (A, A2, B, B2) CUDA tensors (B/B2 may be None)."""
+        """pairs: list of (A, A2, B, B2) or (A, A2, B, B2, X0) CUDA tensors
+        (B/B2 may be None; X0, an n_a x n_b start, may be None)."""
         import torch
         p = params if params is not None else default_params()
         n = len(pairs)
         arr = (fastpfp_pair * max(1, n))()
         outs = []
         keep = []
-        for b, (A, A2, B, B2) in enumerate(pairs):
+        for b, pr in enumerate(pairs):
+            A, A2, B, B2 = pr[:4]
+            X0 = pr[4] if len(pr) > 4 else None
             n_a, n_b = A.shape[0], A2.shape[0]
             k = 0 if B is None else B.shape[1]
             perm = torch.empty(n_a, dtype=torch.int32, device=A.device)
             X = torch.empty((n_a, n_b), dtype=torch.float32, device=A.device) if want_X else None
             arr[b] = fastpfp_pair(A.data_ptr(), A2.data_ptr(), B.data_ptr() if k else None,
-                                  B2.data_ptr() if k else None, n_a, n_b, k, None, perm.data_ptr(),
+                                  B2.data_ptr() if k else None, n_a, n_b, k,
+                                  X0.data_ptr() if X0 is not None else None, perm.data_ptr(),
                                   X.data_ptr() if X is not None else None)
             outs.append((perm, X))
-            keep.append((A, A2, B, B2))
+            keep.append(pr)
         sts = (fastpfp_stats * max(1, n))()
         rc = lib().fastpfp_match_batched(self._h, _stream(stream), n, arr, C.byref(p), sts)
         _check(rc, "fastpfp_match_batched")

@@ -125,3 +125,14 @@ def batch_mixed(count: int = 512, seed: int = 0, n_lo: int = 50, n_hi: int = 600
 def large_4000(seed: int = 0, n: int = 4000) -> GraphPair:
     """n = n' = 4000, p = 0.05, edge noise 0.05, 15-dim attributes, lambda = 0.5."""
     return graph_pair(n, p=0.05, sigma=0.05, k=15, attr_sigma=0.05, lam=0.5, seed=seed)
+
+
+def warm_start_train(count: int, seed: int = 0, n_lo: int = 200, n_hi: int = 800) -> list[GraphPair]:
+    """Training pairs for the learned warm start, shaped like the partial
+    workload: n ~ U{n_lo..n_hi} inliers plus up to n/5 outliers, p = 0.1,
+    sigma = 0.03, 15-dim attributes, lambda = 0.5."""
+    rng = np.random.default_rng(seed)
+    ns = rng.integers(n_lo, n_hi + 1, size=count)
+    return [graph_pair(int(n), p=0.1, sigma=0.03, k=15, attr_sigma=0.05,
+                       n_out=int(rng.integers(0, int(n) // 5 + 1)), lam=0.5,
+                       seed=seed * 1000003 + b + 1) for b, n in enumerate(ns)]
