@@ -271,10 +271,10 @@ bool plan_tc(fastpfp_t h, const Problem* qs, int count, const fastpfp_params* p,
             const Problem& q = qs[b + i];
             const Slot& sl = h->slots[slot_of ? slot_of[b + i] : b + i];
             const int l16N = round8(q.N), l16m = round8(q.m);
-            if (!tc_make_map(&a.map_a[i], sl.A16, q.N, q.N, l16N) ||
-                !tc_make_map(&a.map_b[i], sl.Xt16, q.m, q.N, l16N) ||
-                !tc_make_map(&c.map_a[i], sl.T16, q.N, q.m, l16m) ||
-                !tc_make_map(&c.map_b[i], sl.A216, q.m, q.m, l16m))
+            if (!tc_make_map(&a.map_a[i], sl.A16, q.N, q.N, l16N, false) ||
+                !tc_make_map(&a.map_b[i], sl.Xt16, q.m, q.N, l16N, true) ||
+                !tc_make_map(&c.map_a[i], sl.T16, q.N, q.m, l16m, false) ||
+                !tc_make_map(&c.map_b[i], sl.A216, q.m, q.m, l16m, true))
                 return false;
             a.prob[i] = TcProblem{q.N, q.m, q.N, sl.T16, l16m, nullptr, 0, 0.f, sl.ctrl, &sl.ctrl->error};
             c.prob[i] = TcProblem{q.N, q.m, q.m, sl.Y, round4(q.N), q.k ? sl.K : nullptr, round4(q.m),
@@ -1415,8 +1415,8 @@ int fastpfp_gradient(fastpfp_t h, void* stream, const float* A, const float* X, 
         a.count = c.count = 1;
         a.mode = kTcOutBf16;
         c.mode = kTcOutF32;
-        if (!tc_make_map(&a.map_a[0], sl.A16, N, N, l16N) || !tc_make_map(&a.map_b[0], sl.Xt16, m, N, l16N) ||
-            !tc_make_map(&c.map_a[0], sl.T16, N, m, l16m) || !tc_make_map(&c.map_b[0], sl.A216, m, m, l16m))
+        if (!tc_make_map(&a.map_a[0], sl.A16, N, N, l16N, false) || !tc_make_map(&a.map_b[0], sl.Xt16, m, N, l16N, true) ||
+            !tc_make_map(&c.map_a[0], sl.T16, N, m, l16m, false) || !tc_make_map(&c.map_b[0], sl.A216, m, m, l16m, true))
             return FASTPFP_ERR_UNSUPPORTED;
         a.prob[0] = TcProblem{N, m, N, sl.T16, l16m, nullptr, 0, 0.f, nullptr, nullptr};
         c.prob[0] = TcProblem{N, m, m, sl.Y, l4m, lambda != 0.f ? sl.K : nullptr, l4m, lambda, nullptr, nullptr};

@@ -11,12 +11,17 @@
 // FP32 accumulation in TMEM; the epilogue writes T as BF16 for the second
 // product, or Y as FP32 with lambda K added.
 //
-// One CTA computes one 128 x 128 output tile of one problem of a group
-// (blockIdx.z): warp 0 issues the TMA loads of a 4-stage ring, warp 1 owns
-// the TMEM allocation and one lane issues the MMAs (K = 16 each, four per
-// 64-wide stage), warps 2..5 drain the accumulator with tcgen05.ld.  Every
-// mbarrier wait is bounded: on expiry the CTA records FASTPFP_ERR_TIMEOUT,
-// stops issuing work, frees its TMEM and returns.
+// Persistent: one CTA per SM walks the 128 x 256 output tiles of every
+// problem of the group (N = 256 per MMA halves the shared-memory operand
+// bytes per flop of a 128 x 128 tile, which would otherwise saturate shared
+// memory).  Warp 0 issues the TMA loads of a 4-stage ring continuously
+// across tiles, warp 1 owns the TMEM allocation (two 256-column
+// accumulators, all 512 columns) and one lane issues the MMAs (K = 16 each,
+// four per 64-wide stage) into one accumulator while warps 2..5 drain the
+// other with tcgen05.ld, so a tile's epilogue overlaps the next tile's main
+// loop.
+// Every mbarrier wait is bounded: on expiry the CTA records
+// FASTPFP_ERR_TIMEOUT, every role stops, the TMEM is freed and it returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -26,12 +31,12 @@
 namespace fpfp {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int kTileBytesA = BM * BK * 2;
 constexpr int kTileBytesB = BN * BK * 2;
 constexpr int kStageBytes = kTileBytesA + kTileBytesB;
 constexpr int kThreads = 192;
-constexpr uint32_t kTmemCols = 128;
+constexpr uint32_t kTmemCols = 512;   // two 256-column FP32 accumulators
 constexpr long long kWaitNs = 2000ll * 1000000ll;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -90,7 +95,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     return d;
 }
 // Instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, both
-// K-major, M = 128, N = 128.
+// K-major, M = 128, N = 256.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                             ((uint32_t)(BM >> 4) << 24);
 
@@ -122,16 +127,86 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcGroup G) {
-    const int g = blockIdx.z;
-    if (g >= G.count) return;
-    const TcProblem& pr = G.prob[g];
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    if (m0 >= pr.M || n0 >= pr.N) return;
+// Output tile t of the group: problem g, tile row / column, or false when
+// the solve that owns the problem is not in its BF16 phase (every role of
+// every CTA decides the same way: the flags do not change during a launch).
+__device__ __forceinline__ bool tile_of(const TcGroup& G, int t, int* g, int* m0, int* n0) {
+    int p = 0;
+    while (p + 1 < G.count && G.tile0[p + 1] <= t) ++p;
+    const int local = t - G.tile0[p];
+    *g = p;
+    *m0 = (local / G.ntn[p]) * BM;
+    *n0 = (local % G.ntn[p]) * BN;
+    const TcProblem& pr = G.prob[p];
     if (pr.ctrl) {
-        if (ld_relaxed_i32(&pr.ctrl->done) != 0 || ld_relaxed_i32(&pr.ctrl->error) != 0) return;
-        if (ld_relaxed_i32(&pr.ctrl->lowp) == 0) return;
+        if (ld_relaxed_i32(&pr.ctrl->done) != 0 || ld_relaxed_i32(&pr.ctrl->error) != 0) return false;
+        if (ld_relaxed_i32(&pr.ctrl->lowp) == 0) return false;
     }
+    return true;
+}
+
+// Epilogue of one tile: warp `quarter` of the four epilogue warps drains TMEM
+// lanes 32 * quarter .. + 31 (tile rows) of accumulator column base `tcol`.
+__device__ __forceinline__ void drain_tile(const TcGroup& G, const TcProblem& pr, uint32_t tmem, uint32_t tcol,
+                                           int quarter, int lane, int m0, int n0) {
+    const int row = m0 + quarter * 32 + lane;
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + tcol + (uint32_t)c, r);
+        const int col = n0 + c;
+        if (row >= pr.M || col >= pr.N) continue;
+        const int nv = min(32, pr.N - col);
+        if (G.mode == kTcOutBf16) {
+            __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(pr.out) + (size_t)row * pr.ldo + col;
+            if (nv == 32) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    uint4 pk;
+                    __nv_bfloat162 h0 = __floats2bfloat162_rn(__uint_as_float(r[8 * v + 0]), __uint_as_float(r[8 * v + 1]));
+                    __nv_bfloat162 h1 = __floats2bfloat162_rn(__uint_as_float(r[8 * v + 2]), __uint_as_float(r[8 * v + 3]));
+                    __nv_bfloat162 h2 = __floats2bfloat162_rn(__uint_as_float(r[8 * v + 4]), __uint_as_float(r[8 * v + 5]));
+                    __nv_bfloat162 h3 = __floats2bfloat162_rn(__uint_as_float(r[8 * v + 6]), __uint_as_float(r[8 * v + 7]));
+                    pk.x = *reinterpret_cast<uint32_t*>(&h0);
+                    pk.y = *reinterpret_cast<uint32_t*>(&h1);
+                    pk.z = *reinterpret_cast<uint32_t*>(&h2);
+                    pk.w = *reinterpret_cast<uint32_t*>(&h3);
+                    reinterpret_cast<uint4*>(out)[v] = pk;
+                }
+            } else {
+                for (int v = 0; v < nv; ++v) out[v] = __float2bfloat16_rn(__uint_as_float(r[v]));
+            }
+        } else {
+            float* out = reinterpret_cast<float*>(pr.out) + (size_t)row * pr.ldo + col;
+            const float* kk = pr.Kmat ? pr.Kmat + (size_t)row * pr.ldk + col : nullptr;
+            if (nv == 32) {
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    float4 o = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                                           __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
+                    if (kk) {
+                        const float4 kv = __ldg(reinterpret_cast<const float4*>(kk) + v);
+                        o.x = fmaf(pr.lambda, kv.x, o.x);
+                        o.y = fmaf(pr.lambda, kv.y, o.y);
+                        o.z = fmaf(pr.lambda, kv.z, o.z);
+                        o.w = fmaf(pr.lambda, kv.w, o.w);
+                    }
+                    reinterpret_cast<float4*>(out)[v] = o;
+                }
+            } else {
+                for (int v = 0; v < nv; ++v) {
+                    float o = __uint_as_float(r[v]);
+                    if (kk) o = fmaf(pr.lambda, kk[v], o);
+                    out[v] = o;
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcGroup G) {
+    const int ntiles = G.tile0[G.count];
+    if ((int)blockIdx.x >= ntiles) return;
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment of the tile ring (required by the 128-byte swizzle)
@@ -140,19 +215,22 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     unsigned char* tiles = base;
     uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * kStageBytes);
     uint64_t* empty = full + STAGES;
-    uint64_t* acc_full = empty + STAGES;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 1);
+    uint64_t* acc_full = empty + STAGES;   // [2]
+    uint64_t* acc_empty = acc_full + 2;    // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = (pr.K + BK - 1) / BK;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(acc_full, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);   // one arrival per epilogue warp
+        }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -168,102 +246,83 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        // TMA producer
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % STAGES;
-            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-            if (!mbar_wait(&empty[s], ph ^ 1u, abort)) break;
-            unsigned char* a = tiles + s * kStageBytes;
-            unsigned char* b = a + kTileBytesA;
-            mbar_expect_tx(&full[s], kStageBytes);
-            tma_load_2d(a, &G.map_a[g], kb * BK, m0, &full[s]);
-            tma_load_2d(b, &G.map_b[g], kb * BK, n0, &full[s]);
-        }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % STAGES;
-            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-            if (!mbar_wait(&full[s], ph, abort)) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a = smem_u32(tiles + s * kStageBytes);
-            const uint32_t b = a + kTileBytesA;
-            const uint64_t ad = smem_desc(a), bd = smem_desc(b);
-#pragma unroll
-            for (int j = 0; j < BK / 16; ++j)   // K = 16 per MMA: 32 bytes along the swizzled row
-                mma_bf16(tmem, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), (kb > 0 || j > 0) ? 1u : 0u);
-            mma_commit(&empty[s]);
-        }
-        mma_commit(acc_full);
-    } else if (warp >= 2) {
-        // epilogue: warp w reads TMEM lanes 32 * (w % 4) .. + 31 = tile rows
-        const int quarter = warp & 3;
-        const int row = m0 + quarter * 32 + lane;
-        // one lane waits; tcgen05.ld is warp-collective, so the outcome is broadcast
-        int okl = 0;
-        if (lane == 0) okl = mbar_wait(acc_full, 0u, abort) ? 1 : 0;
-        const bool ok = __shfl_sync(0xffffffffu, okl, 0) != 0;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok) {
-#pragma unroll 1
-            for (int c = 0; c < BN; c += 32) {
-                uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c, r);
-                const int col = n0 + c;
-                if (row >= pr.M || col >= pr.N) continue;
-                const int nv = min(32, pr.N - col);
-                if (G.mode == kTcOutBf16) {
-                    __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(pr.out) + (size_t)row * pr.ldo + col;
-                    if (nv == 32) {
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) {
-                            uint4 pk;
-                            __nv_bfloat162 h0 = __floats2bfloat162_rn(__uint_as_float(r[8 * v + 0]), __uint_as_float(r[8 * v + 1]));
-                            __nv_bfloat162 h1 = __floats2bfloat162_rn(__uint_as_float(r[8 * v + 2]), __uint_as_float(r[8 * v + 3]));
-                            __nv_bfloat162 h2 = __floats2bfloat162_rn(__uint_as_float(r[8 * v + 4]), __uint_as_float(r[8 * v + 5]));
-                            __nv_bfloat162 h3 = __floats2bfloat162_rn(__uint_as_float(r[8 * v + 6]), __uint_as_float(r[8 * v + 7]));
-                            pk.x = *reinterpret_cast<uint32_t*>(&h0);
-                            pk.y = *reinterpret_cast<uint32_t*>(&h1);
-                            pk.z = *reinterpret_cast<uint32_t*>(&h2);
-                            pk.w = *reinterpret_cast<uint32_t*>(&h3);
-                            reinterpret_cast<uint4*>(out)[v] = pk;
-                        }
-                    } else {
-                        for (int v = 0; v < nv; ++v) out[v] = __float2bfloat16_rn(__uint_as_float(r[v]));
-                    }
-                } else {
-                    float* out = reinterpret_cast<float*>(pr.out) + (size_t)row * pr.ldo + col;
-                    const float* kk = pr.Kmat ? pr.Kmat + (size_t)row * pr.ldk + col : nullptr;
-                    if (nv == 32) {
-#pragma unroll
-                        for (int v = 0; v < 8; ++v) {
-                            float4 o = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
-                                                   __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
-                            if (kk) {
-                                const float4 kv = __ldg(reinterpret_cast<const float4*>(kk) + v);
-                                o.x = fmaf(pr.lambda, kv.x, o.x);
-                                o.y = fmaf(pr.lambda, kv.y, o.y);
-                                o.z = fmaf(pr.lambda, kv.z, o.z);
-                                o.w = fmaf(pr.lambda, kv.w, o.w);
-                            }
-                            reinterpret_cast<float4*>(out)[v] = o;
-                        }
-                    } else {
-                        for (int v = 0; v < nv; ++v) {
-                            float o = __uint_as_float(r[v]);
-                            if (kk) o = fmaf(pr.lambda, kk[v], o);
-                            out[v] = o;
-                        }
-                    }
-                }
+        // TMA producer: the k-blocks of this CTA's tiles, one ring across tiles
+        uint32_t it = 0;
+        for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
+            int g, m0, n0;
+            if (!tile_of(G, t, &g, &m0, &n0)) continue;
+            const int nk = (G.prob[g].K + BK - 1) / BK;
+            for (int kb = 0; kb < nk; ++kb, ++it) {
+                const int s = it % STAGES;
+                const uint32_t ph = (it / STAGES) & 1u;
+                if (!mbar_wait(&empty[s], ph ^ 1u, abort)) break;
+                unsigned char* a = tiles + s * kStageBytes;
+                unsigned char* b = a + kTileBytesA;
+                mbar_expect_tx(&full[s], kStageBytes);
+                tma_load_2d(a, &G.map_a[g], kb * BK, m0, &full[s]);
+                tma_load_2d(b, &G.map_b[g], kb * BK, n0, &full[s]);
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: accumulator tc & 1 of the CTA's tc-th tile
+        uint32_t it = 0, tc = 0;
+        for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
+            int g, m0, n0;
+            if (!tile_of(G, t, &g, &m0, &n0)) continue;
+            const int nk = (G.prob[g].K + BK - 1) / BK;
+            const uint32_t buf = tc & 1u, aph = (tc >> 1) & 1u;
+            if (!mbar_wait(&acc_empty[buf], aph ^ 1u, abort)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acc = tmem + buf * (uint32_t)BN;
+            bool ok = true;
+            for (int kb = 0; kb < nk; ++kb, ++it) {
+                const int s = it % STAGES;
+                const uint32_t ph = (it / STAGES) & 1u;
+                if (!mbar_wait(&full[s], ph, abort)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a = smem_u32(tiles + s * kStageBytes);
+                const uint32_t b = a + kTileBytesA;
+                const uint64_t ad = smem_desc(a), bd = smem_desc(b);
+#pragma unroll
+                for (int j = 0; j < BK / 16; ++j)   // K = 16 per MMA: 32 bytes along the swizzled row
+                    mma_bf16(acc, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), (kb > 0 || j > 0) ? 1u : 0u);
+                mma_commit(&empty[s]);
+            }
+            if (!ok) break;
+            mma_commit(&acc_full[buf]);
+            ++tc;
+        }
+    } else if (warp >= 2) {
+        // epilogue: warp w drains TMEM lanes 32 * (w % 4) .. + 31 = tile rows
+        const int quarter = warp & 3;
+        uint32_t tc = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            int g, m0, n0;
+            if (!tile_of(G, t, &g, &m0, &n0)) continue;
+            const uint32_t buf = tc & 1u, aph = (tc >> 1) & 1u;
+            // one lane waits; tcgen05.ld is warp-collective, so the outcome is broadcast
+            int okl = 0;
+            if (lane == 0) okl = mbar_wait(&acc_full[buf], aph, abort) ? 1 : 0;
+            if (__shfl_sync(0xffffffffu, okl, 0) == 0) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            drain_tile(G, G.prob[g], tmem, buf * (uint32_t)BN, quarter, lane, m0, n0);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[buf]))
+                             : "memory");
+            }
+            ++tc;
+        }
     }
     __syncthreads();
     if (*abort && threadIdx.x == 0) {
-        int* err = pr.err;
-        if (err) atomicCAS(err, 0, FASTPFP_ERR_TIMEOUT);
+        // every problem of the group gets the timeout (their solves stop)
+        for (int g = 0; g < G.count; ++g)
+            if (G.prob[g].err) atomicCAS(G.prob[g].err, 0, FASTPFP_ERR_TIMEOUT);
     }
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -289,19 +348,26 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 size_t tc_smem_bytes() { return (size_t)STAGES * kStageBytes + 1024 + 256; }
 
+static int g_tc_sms = 0;
+
 cudaError_t tc_configure() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute((const void*)tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)tc_smem_bytes());
 }
 
 // rows x cols BF16 matrix, row-major with leading dimension ld (elements,
-// a multiple of 8), read as 128-row x 64-column boxes with 128-byte swizzle.
-bool tc_make_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int cols, int ld) {
+// a multiple of 8), read as 64-column boxes of 128 rows (A operand) or 256
+// rows (B operand) with 128-byte swizzle.
+bool tc_make_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int cols, int ld, bool b_operand) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn || (ld % 8) != 0 || (reinterpret_cast<uintptr_t>(ptr) & 15) != 0) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)(b_operand ? BN : BM)};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), dims,
                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -309,14 +375,18 @@ bool tc_make_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int cols,
     return r == CUDA_SUCCESS;
 }
 
-cudaError_t tc_gemm(const TcGroup& G, cudaStream_t s) {
-    int mt = 1, nt = 1;
+cudaError_t tc_gemm(const TcGroup& G0, cudaStream_t s) {
+    if (G0.count <= 0) return cudaSuccess;
+    TcGroup G = G0;
+    G.tile0[0] = 0;
     for (int i = 0; i < G.count; ++i) {
-        mt = max(mt, (G.prob[i].M + BM - 1) / BM);
-        nt = max(nt, (G.prob[i].N + BN - 1) / BN);
+        G.ntn[i] = (G.prob[i].N + BN - 1) / BN;
+        G.tile0[i + 1] = G.tile0[i] + ((G.prob[i].M + BM - 1) / BM) * G.ntn[i];
     }
-    if (G.count <= 0) return cudaSuccess;
-    tc_gemm_kernel<<<dim3(nt, mt, G.count), kThreads, tc_smem_bytes(), s>>>(G);
+    const int ntiles = G.tile0[G.count];
+    if (ntiles <= 0) return cudaSuccess;
+    const int grid = min(ntiles, g_tc_sms > 0 ? g_tc_sms : 148);
+    tc_gemm_kernel<<<grid, kThreads, tc_smem_bytes(), s>>>(G);
     return cudaGetLastError();
 }
 

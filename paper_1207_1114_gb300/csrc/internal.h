@@ -171,10 +171,16 @@ struct TcGroup {
     TcProblem prob[kTcMaxGroup];
     int count;
     int mode;
+    // filled by tc_gemm: output tiles of problems before i (tile0[count] =
+    // all tiles) and tiles per row of tiles of problem i
+    int tile0[kTcMaxGroup + 1];
+    int ntn[kTcMaxGroup];
 };
 size_t tc_smem_bytes();
 cudaError_t tc_configure();
-bool tc_make_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int cols, int ld);
+// TMA map of a rows x cols BF16 operand (ld elements, a multiple of 8) for
+// tc_gemm: b_operand selects the B-operand box (256 rows) over A's (128).
+bool tc_make_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int cols, int ld, bool b_operand);
 cudaError_t tc_gemm(const TcGroup& G, cudaStream_t s);
 
 // ----------------------------------------------------------------- GEMM
