@@ -93,10 +93,27 @@ struct PdbLayout {
 // Warps sharing one row of a pair whose slacked rows hold ldy floats, in a
 // CTA of nthr threads (one column quad per thread, or two when a row has
 // more quads than threads).
-__host__ __device__ inline int pdb_row_warps(int ldy, int nthr) {
-    const int QP = ((ldy >> 2) + 31) & ~31;
-    return (QP <= nthr ? QP : nthr) >> 5;
+// Thread layout of one pair's rows in a CTA of nthr threads: qpg threads (a
+// multiple of 32) cover a row, each owning kq column quads (kq = 1 or 2,
+// qpg apart), and rp = nthr / qpg row groups work on different rows.  kq
+// maximises rp / kq, the rows a pass advances per quad a thread handles
+// (ties to one quad): a 1200-node row (300 quads) takes 3 groups of 160
+// threads with two quads each rather than one group of 320.
+struct PdbShape {
+    int kq, qpg, rp;
+};
+__host__ __device__ inline PdbShape pdb_shape(int ldy, int nthr) {
+    const int Q = ldy >> 2;
+    PdbShape best{0, 0, 0};
+    for (int kq = 1; kq <= 2; ++kq) {
+        const int qpg = ((Q + kq - 1) / kq + 31) & ~31;
+        if (qpg > nthr) continue;
+        const int rp = nthr / qpg;
+        if (best.kq == 0 || rp * best.kq > best.rp * kq) best = PdbShape{kq, qpg, rp};
+    }
+    return best;   // kq == 0: rows too wide for one CTA (more than 2 * nthr quads)
 }
+__host__ __device__ inline int pdb_row_warps(int ldy, int nthr) { return pdb_shape(ldy, nthr).qpg >> 5; }
 
 // Tensor memory as band storage: a CTA of kPdbThreads threads allocates all
 // 512 TMEM columns; the four warps sharing a 32-lane quarter split them, so
@@ -107,23 +124,21 @@ constexpr int kTmemColsPerThread = kTmemCols * 128 / kPdbThreads;
 // Placement of one segment of a band (nrows rows of a pair with row length
 // ldy) after col_used of the thread's TMEM columns are taken by earlier
 // segments: the first `tm` rows of every row group (band rows 0 ..
-// RP * tm - 1 of the segment, RP = row groups) live in TMEM columns col_used
-// + 4 k, one quad per thread; the rest in shared memory.  Rows wider than
-// the CTA (two quads per thread) stay in shared memory.  Returns tm and sets
-// *tm_band_rows (band rows in TMEM) and *col_next.
+// rp * tm - 1 of the segment) live in TMEM columns col_used + 4 kq k (the
+// thread's kq quads of its k-th row); the rest in shared memory.  Returns tm
+// and sets *tm_band_rows (band rows in TMEM) and *col_next.
 __host__ __device__ inline int pdb_tmem_rows(int nrows, int ldy, int nthr, int col_used, int* tm_band_rows,
                                              int* col_next) {
-    const int QP = ((ldy >> 2) + 31) & ~31;
+    const PdbShape sh = pdb_shape(ldy, nthr);
     *col_next = col_used;
     *tm_band_rows = 0;
-    if (QP > nthr) return 0;
-    const int RP = nthr / QP;
-    const int nk = (nrows + RP - 1) / RP;
-    int avail = (kTmemColsPerThread - col_used) / 4;
+    if (sh.kq == 0) return 0;
+    const int nk = (nrows + sh.rp - 1) / sh.rp;
+    int avail = (kTmemColsPerThread - col_used) / (4 * sh.kq);
     if (avail < 0) avail = 0;
     const int tm = nk < avail ? nk : avail;
-    *col_next = col_used + 4 * tm;
-    *tm_band_rows = RP * tm < nrows ? RP * tm : nrows;
+    *col_next = col_used + 4 * sh.kq * tm;
+    *tm_band_rows = sh.rp * tm < nrows ? sh.rp * tm : nrows;
     return tm;
 }
 

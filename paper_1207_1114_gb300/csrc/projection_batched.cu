@@ -36,7 +36,8 @@ struct Seg {
     int tm;         // thread-rows per row group held in TMEM (band rows 0 .. ntm - 1)
     int tcol;       // first TMEM column of the segment in every thread's share
     int ntm;        // band rows of the segment in TMEM; rows ntm .. nrows - 1 are in shared memory
-    int pad0, pad1;
+    int qpg;        // thread layout of the pair (pdb_shape): threads per row,
+    int rpkq;       // row groups * 4 + quads per thread
 };
 
 // Per-pair fields used every round, copied to shared memory once per launch.
@@ -90,27 +91,20 @@ __device__ __forceinline__ Shared carve_b(char* base, const PdbLayout& L, int nt
     return s;
 }
 
-// Thread -> (row group, quad) mapping of one segment.  QP = quads per row
-// padded to a warp multiple.  When QP <= nthr, RP = nthr / QP row groups work
-// on different rows at once and each thread owns one quad; otherwise one
-// group covers a row with kq (<= 2) quads per thread.
+// Thread -> (row group, quads) mapping of one segment (pdb_shape): QP
+// threads cover a row, RP row groups work on different rows at once, and a
+// thread owns quads q0 and (kq = 2) q0 + QP of its group's rows.  Threads
+// past RP * QP have no rows (grp >= RP).
 struct Map {
     int QP, RP, grp, q0, kq;
 };
-__device__ __forceinline__ Map make_map(int Q, int nthr, int tid) {
+__device__ __forceinline__ Map make_map(int qpg, int rpkq, int tid) {
     Map m;
-    m.QP = (Q + 31) & ~31;
-    if (m.QP <= nthr) {
-        m.RP = nthr / m.QP;
-        m.grp = tid / m.QP;
-        m.q0 = tid % m.QP;
-        m.kq = 1;
-    } else {
-        m.RP = 1;
-        m.grp = 0;
-        m.q0 = tid;
-        m.kq = 2;
-    }
+    m.QP = qpg;
+    m.RP = rpkq >> 2;
+    m.kq = rpkq & 3;
+    m.grp = tid / qpg;
+    m.q0 = tid - m.grp * qpg;
     return m;
 }
 
@@ -293,6 +287,63 @@ __device__ __forceinline__ void seg_rows_tmem(uint32_t taddr, int tm, int nrows,
     }
 }
 
+// The TMEM rows of a segment whose threads own two quads per row (kq = 2):
+// thread-row k holds quads q0 and q0 + QP at TMEM columns taddr + 8 k and
+// + 8 k + 4, two rows per 16-column load/store.  Warp-collective.
+template <bool UPDATE>
+__device__ __forceinline__ void seg_rows_tmem2(uint32_t taddr, int tm, int nrows, int Q, int N, const Map& mp,
+                                               int lane, const float* __restrict__ rsum, float abase,
+                                               float* __restrict__ rowpart, int rps, float4 c0v, float4 c1v,
+                                               float ninvN, float4& cp0, float4& cp1, float& dmax) {
+    const int q1 = mp.q0 + mp.QP;
+    const bool h0 = mp.q0 < Q, h1 = q1 < Q;
+    const int c00 = 4 * mp.q0, c01 = 4 * q1;
+    const int RP = mp.RP;
+    int k = 0;
+    for (; k + 1 < tm; k += 2) {
+        float4 q[4];   // row k: quads 0, 1; row k + 1: quads 0, 1
+        tm_ld16(taddr + 8 * k, q);
+        float s[2] = {0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int r = mp.grp + RP * (k + j);
+            if (r < nrows) {
+                const float a = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
+                if (h0) s[j] += quad_upd<UPDATE>(q[2 * j], a, c0v, ninvN, c00, N, cp0, dmax);
+                if (h1) s[j] += quad_upd<UPDATE>(q[2 * j + 1], a, c1v, ninvN, c01, N, cp1, dmax);
+            }
+        }
+        if (UPDATE) tm_st16(taddr + 8 * k, q);
+        // both rows' warp sums in five shuffles (lower half-warp row k)
+        const bool hi = (lane & 16) != 0;
+        float keep = hi ? s[1] : s[0];
+        keep += __shfl_xor_sync(0xffffffffu, hi ? s[0] : s[1], 16);
+        keep += __shfl_xor_sync(0xffffffffu, keep, 8);
+        keep += __shfl_xor_sync(0xffffffffu, keep, 4);
+        keep += __shfl_xor_sync(0xffffffffu, keep, 2);
+        keep += __shfl_xor_sync(0xffffffffu, keep, 1);
+        const int r0 = mp.grp + RP * k, r1 = r0 + RP;
+        if (lane == 0 && r0 < nrows) rowpart[(size_t)r0 * rps] = keep;
+        if (lane == 16 && r1 < nrows) rowpart[(size_t)r1 * rps] = keep;
+    }
+    if (k < tm) {
+        const int r = mp.grp + RP * k;
+        float4 y0 = tm_ld4(taddr + 8 * k), y1 = tm_ld4(taddr + 8 * k + 4);
+        float s0 = 0.f;
+        if (r < nrows) {
+            const float a = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
+            if (h0) s0 += quad_upd<UPDATE>(y0, a, c0v, ninvN, c00, N, cp0, dmax);
+            if (h1) s0 += quad_upd<UPDATE>(y1, a, c1v, ninvN, c01, N, cp1, dmax);
+        }
+        if (UPDATE) {
+            tm_st4(taddr + 8 * k, y0);
+            tm_st4(taddr + 8 * k + 4, y1);
+        }
+        s0 = warp_sum(s0);
+        if (lane == 0 && r < nrows) rowpart[(size_t)r * rps] = s0;
+    }
+}
+
 // All rows of one segment handled by this thread's row group: four rows in
 // flight, then two, then one.  KQ = column quads per thread (1 or 2).  The
 // row offset of Eq. (P1) is abase - r_i / N (one FMA from the row sums of
@@ -305,8 +356,9 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
                                          float* __restrict__ rowpart, int rps, float4 c0v, float4 c1v, float ninvN,
                                          float4& cp0, float4& cp1, float& dmax) {
     const bool h0 = mp.q0 < Q;
-    const bool h1 = KQ > 1 && mp.q0 + nthr < Q;
-    const int c00 = 4 * mp.q0, c01 = 4 * (mp.q0 + nthr);
+    const int q1 = mp.q0 + mp.QP;   // the second quad (kq = 2)
+    const bool h1 = KQ > 1 && q1 < Q;
+    const int c00 = 4 * mp.q0, c01 = 4 * q1;
     const int RP = mp.RP;
     const int stride = RP * Q;
     int r = mp.grp;
@@ -322,7 +374,7 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
         if (KQ > 1 && h1) {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                s[k] += quad_step<UPDATE>(p + k * stride + nthr, a[k], c1v, ninvN, c01, N, cp1, dmax);
+                s[k] += quad_step<UPDATE>(p + k * stride + mp.QP, a[k], c1v, ninvN, c01, N, cp1, dmax);
         }
         const float z = sum4_rows(s, lane);
         if ((lane & 7) == 0) rowpart[(size_t)(r + (2 * (lane >> 4) + ((lane >> 3) & 1)) * RP) * rps] = z;
@@ -336,8 +388,8 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
             s1 += quad_step<UPDATE>(p + stride, a1, c0v, ninvN, c00, N, cp0, dmax);
         }
         if (KQ > 1 && h1) {
-            s0 += quad_step<UPDATE>(p + nthr, a0, c1v, ninvN, c01, N, cp1, dmax);
-            s1 += quad_step<UPDATE>(p + stride + nthr, a1, c1v, ninvN, c01, N, cp1, dmax);
+            s0 += quad_step<UPDATE>(p + mp.QP, a0, c1v, ninvN, c01, N, cp1, dmax);
+            s1 += quad_step<UPDATE>(p + stride + mp.QP, a1, c1v, ninvN, c01, N, cp1, dmax);
         }
         // both rows' warp sums in five shuffles: the lower half-warp folds
         // row r, the upper half row r + RP
@@ -355,7 +407,7 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
         const float a0 = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
         float s0 = 0.f;
         if (h0) s0 += quad_step<UPDATE>(p, a0, c0v, ninvN, c00, N, cp0, dmax);
-        if (KQ > 1 && h1) s0 += quad_step<UPDATE>(p + nthr, a0, c1v, ninvN, c01, N, cp1, dmax);
+        if (KQ > 1 && h1) s0 += quad_step<UPDATE>(p + mp.QP, a0, c1v, ninvN, c01, N, cp1, dmax);
         s0 = warp_sum(s0);
         if (lane == 0) rowpart[(size_t)r * rps] = s0;
     }
@@ -395,7 +447,9 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 s.coff = coff;
                 s.tcol = tcol;
                 s.tm = pdb_tmem_rows(s.nrows, d.ldy, nthr, tcol, &s.ntm, &tcol);
-                s.pad0 = s.pad1 = 0;
+                const PdbShape sh = pdb_shape(d.ldy, nthr);
+                s.qpg = sh.qpg;
+                s.rpkq = 4 * sh.rp + sh.kq;
                 S.seg[nseg++] = s;
                 brow += s.nrows;
                 soff += (s.nrows - s.ntm) * d.ldy;
@@ -466,16 +520,19 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         const float4* src = reinterpret_cast<const float4*>(d.Y) + (size_t)sg.lr0 * Q;
         // TMEM rows: thread-row k of the row group is band row grp + RP k
         if (sg.tm > 0) {
-            const Map mp = make_map(Q, nthr, tid);
+            const Map mp = make_map(sg.qpg, sg.rpkq, tid);
             if (mp.grp < mp.RP) {
                 for (int k = 0; k < sg.tm; ++k) {
                     const int r = mp.grp + mp.RP * k;
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (r < sg.nrows && mp.q0 < Q) {
-                        v = src[(size_t)r * Q + mp.q0];
-                        if (reset) v = slack_mask(v, 4 * mp.q0, m);
+                    for (int j = 0; j < mp.kq; ++j) {   // the thread's quads of its k-th row
+                        const int q = mp.q0 + j * mp.QP;
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (r < sg.nrows && q < Q) {
+                            v = src[(size_t)r * Q + q];
+                            if (reset) v = slack_mask(v, 4 * q, m);
+                        }
+                        tm_st4(tme + sg.tcol + 4 * (mp.kq * k + j), v);
                     }
-                    tm_st4(tme + sg.tcol + 4 * k, v);
                 }
             }
         }
@@ -503,25 +560,28 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             if (!(pst & 1) || (pst & 2)) continue;   // inactive or stopped pair
             const PairS pr = S.pair[sg.pair];
             const int N = pr.N, Q = pr.ldy >> 2;
-            const Map mp = make_map(Q, nthr, tid);
+            const Map mp = make_map(sg.qpg, sg.rpkq, tid);
             const bool in_grp = mp.grp < mp.RP;
             float4 c0v = make_float4(0.f, 0.f, 0.f, 0.f), c1v = c0v;
             if (UPDATE && in_grp) {
                 const float4* cN = reinterpret_cast<const float4*>(S.cN + sg.coff);
                 if (mp.q0 < Q) c0v = cN[mp.q0];
-                if (mp.kq > 1 && mp.q0 + nthr < Q) c1v = cN[mp.q0 + nthr];
+                if (mp.kq > 1 && mp.q0 + mp.QP < Q) c1v = cN[mp.q0 + mp.QP];
             }
             float4 cp0 = make_float4(0.f, 0.f, 0.f, 0.f), cp1 = cp0;
             float dmax = 0.f;
             if (in_grp) {
-                const int wig = (mp.QP <= nthr) ? ((tid % mp.QP) >> 5) : warp;
+                const int wig = (tid % mp.QP) >> 5;
                 float4* bp = reinterpret_cast<float4*>(S.band + sg.soff);
                 float* rp = S.rowpart + (size_t)sg.brow0 * RPS + wig;
                 const float* rs = S.rsum + sg.brow0;
                 const float ninvN = -1.0f / (float)N;
-                if (sg.tm > 0)
+                if (sg.tm > 0 && mp.kq == 1)
                     seg_rows_tmem<UPDATE>(tme + sg.tcol, sg.tm, sg.nrows, Q, N, mp, lane, rs, pr.abase, rp, RPS,
                                           c0v, ninvN, cp0, dmax);
+                else if (sg.tm > 0)
+                    seg_rows_tmem2<UPDATE>(tme + sg.tcol, sg.tm, sg.nrows, Q, N, mp, lane, rs, pr.abase, rp, RPS,
+                                           c0v, c1v, ninvN, cp0, cp1, dmax);
                 // rows ntm .. nrows - 1 (ntm is a multiple of RP, so row groups line up)
                 const int ns = sg.nrows - sg.ntm;
                 if (mp.kq == 1)
@@ -539,8 +599,8 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             float* acc = pr.colbuf + (size_t)cur * pr.ldy;
             if (in_grp) {
                 if (mp.q0 < Q) red_add_v4(acc + 4 * mp.q0, cp0.x, cp0.y, cp0.z, cp0.w);
-                if (mp.kq > 1 && mp.q0 + nthr < Q)
-                    red_add_v4(acc + 4 * (mp.q0 + nthr), cp1.x, cp1.y, cp1.z, cp1.w);
+                if (mp.kq > 1 && mp.q0 + mp.QP < Q)
+                    red_add_v4(acc + 4 * (mp.q0 + mp.QP), cp1.x, cp1.y, cp1.z, cp1.w);
             }
         }
         // the row sums of the group's segments, once every warp's partials are in
@@ -715,12 +775,15 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         const int Q = d.ldy >> 2;
         float4* Yg = reinterpret_cast<float4*>(d.Y) + (size_t)sg.lr0 * Q;
         if (sg.tm > 0) {
-            const Map mp = make_map(Q, nthr, tid);
+            const Map mp = make_map(sg.qpg, sg.rpkq, tid);
             if (mp.grp < mp.RP) {
                 for (int k = 0; k < sg.tm; ++k) {
-                    const float4 v = tm_ld4(tme + sg.tcol + 4 * k);
                     const int r = mp.grp + mp.RP * k;
-                    if (r < sg.nrows && mp.q0 < Q) Yg[(size_t)r * Q + mp.q0] = v;
+                    for (int j = 0; j < mp.kq; ++j) {
+                        const int q = mp.q0 + j * mp.QP;
+                        const float4 v = tm_ld4(tme + sg.tcol + 4 * (mp.kq * k + j));
+                        if (r < sg.nrows && q < Q) Yg[(size_t)r * Q + q] = v;
+                    }
                 }
             }
         }

@@ -323,6 +323,27 @@ def test_batched_wave_at_full_size_matches_oracle(solver):
     _check_batch(solver, pairs, 1.0, max_outer=3, max_inner=150)
 
 
+def test_batched_wave_with_two_quads_per_thread_matches_oracle(solver):
+    """1000-into-1200 pairs: a 1200-wide row is covered by three row groups
+    of 160 threads with two column quads each (TMEM rows of eight columns)."""
+    pairs = [synth.partial_1000_1200(seed=s) for s in range(3)]
+    _check_batch(solver, pairs, 0.5, max_outer=3, max_inner=100)
+
+
+def test_batched_wave_of_wide_rows_matches_oracle(stream_solver_wide):
+    """Rows of 2100 nodes: one row group of 288 threads with two quads each."""
+    pairs = [synth.graph_pair(2100, p=0.05, sigma=0.05, k=8, lam=0.5, seed=70 + s) for s in range(2)]
+    outs = _check_batch(stream_solver_wide, pairs, 0.5, max_outer=2, max_inner=30)
+    assert all(o.stats.wave_pairs == 2 for o in outs)
+
+
+@pytest.fixture(scope="module")
+def stream_solver_wide():
+    s = F.Solver(max_n=2100, max_batch=2)
+    yield s
+    s.close()
+
+
 def test_bf16_phase_then_fp32_refinement(solver):
     """Precision policy: BF16 tensor-core products until max|dX| < switch_tol,
     then FP32 iterations.  The refined result matches the plain FP32 solve's
