@@ -5,13 +5,15 @@
 // control block, discretisation buffers) for each pair that can be solved at
 // the same time, sized for graphs of up to max_n nodes.
 //
-// One pair (fastpfp_match) runs Algorithm 1 with pd_kernel: per outer
-// iteration the two gradient products and one cooperative launch that runs
-// every P1/P2 round, blends, normalises and decides on the device whether
-// the loop continues.  A batch (fastpfp_match_batched) is cut into waves of
-// pairs whose slacked matrices fit in shared memory together; per outer
-// iteration a wave runs every pair's products and one launch of pdb_kernel,
-// which shares each grid barrier between all pairs of the wave.
+// Pairs run Algorithm 1 in waves: pairs whose slacked matrices fit on chip
+// together (TMEM + shared memory of all SMs) share one cooperative launch of
+// pdb_kernel per outer iteration, which runs every P1/P2 round of every pair
+// with one grid barrier per round, blends, normalises and decides on the
+// device whether each pair's loop continues; the pairs' gradient products
+// are grouped launches.  A lone pair is a wave of one.  A batch larger than
+// one wave is streamed (solve_stream): finished pairs leave and waiting pairs
+// enter between outer iterations.  A pair too large for any wave runs
+// through pd_kernel, which streams its band through L2.
 //
 // The repeat loop of Algorithm 1 runs in one of two ways.  By default one
 // outer iteration is captured into the body of a CUDA-graph while node whose
@@ -736,6 +738,7 @@ PdbParams wave_params(fastpfp_t h, const Wave& w, int npairs, const fastpfp_para
     P.refine_iters = p->refine_iters;
     P.switch_tol = p->switch_tol;
     P.timeout_ns = timeout_ns(p);
+    P.skip_arrive = (p->debug_flags & 1) ? 1 : 0;
     return P;
 }
 
@@ -1303,10 +1306,13 @@ int solve_batch(fastpfp_t h, cudaStream_t s, int count, const fastpfp_pair* pair
         const fastpfp_pair& x = pairs[b];
         qs[b] = canonical(x.A, x.n_a, x.A2, x.n_b, x.B, x.B2, x.k, p->lambda, x.X0, x.perm_out, x.X_out);
     }
-    // a batch that fits in one wave runs as one wave (its loop on the device);
-    // a larger one is streamed through waves kept full by the host
+    // a batch that fits in one wave runs as one wave (its loop on the
+    // device), a lone pair included: its slacked matrix then stays on chip
+    // (TMEM + shared memory) instead of streaming through L2; a larger batch
+    // is streamed through waves kept full by the host; a pair that fits in
+    // no wave runs through pd_kernel
     Wave w;
-    const bool batched = count > 1 && plan_wave(qs, 0, h->nslots, h->num_sms, &w);
+    const bool batched = plan_wave(qs, 0, h->nslots, h->num_sms, &w);
     if (count > 1 && (!batched || w.count < count)) return solve_stream(h, s, qs, pairs, p, st, host);
     const int cnt = batched ? w.count : 1;
     if (host)

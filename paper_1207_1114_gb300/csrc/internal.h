@@ -158,6 +158,7 @@ struct PdbParams {
     int refine_iters;
     double switch_tol;
     long long timeout_ns;
+    int skip_arrive;      // testing only: CTA 0 does not arrive at the first barrier of a solve's first launch
 };
 
 cudaError_t pdb_configure();

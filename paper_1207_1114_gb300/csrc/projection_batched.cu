@@ -425,6 +425,9 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     unsigned gen[2] = {0u, 0u};
     const int npairs = P.npairs, split = P.split;
     const int RPS = P.layout.rp_stride;
+    // testing only (debug_flags bit 0): CTA 0 skips its first arrival of the
+    // first launch of a solve, so every wait of that launch runs out
+    bool skip_first = P.skip_arrive && blockIdx.x == 0 && ld_relaxed_i32(&P.pairs[0].ctrl->outer) == 0;
 
     // ---- bands of both groups -> segments, pair states and per-pair fields
     if (tid == 0) {
@@ -671,7 +674,12 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         } else if (clear_which >= 0) {
             clear_acc(g, clear_which, tid - 64, nthr - 64);
         }
-        grid_arrive(&W->bar[g]);
+        if (skip_first) {   // fault-injection test: this arrival is lost
+            skip_first = false;
+            __syncthreads();
+        } else {
+            grid_arrive(&W->bar[g]);
+        }
     };
 
     // Wait for group g's barrier of pass `cur` (round u), then take every
