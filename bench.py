@@ -333,6 +333,8 @@ def main():
     ap.add_argument("--train-pairs", type=int, default=2000, dest="train_pairs")
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="outer loop: CUDA-graph while node (default) or host-polled chunks")
+    ap.add_argument("--no-autotune", action="store_true", dest="no_autotune",
+                    help="keep the default GEMM tiles instead of timing both per size class")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.batch is None:
@@ -362,6 +364,13 @@ def main():
                torch.as_tensor(g.B, device=dev), torch.as_tensor(g.B2, device=dev)) for g in pairs]
     solver = F.Solver(max_n=max_n, max_batch=args.batch, device=local)
     stream = torch.cuda.current_stream()
+    # GEMM tile shapes per size class, timed once before anything is measured
+    if not args.no_autotune:
+        solver.autotune(reps=3, stream=stream)
+    tiles = {}
+    for lo, hi in ((1, 1), (2, 4), (5, 16), (17, 32)):
+        f32_m, tc_n = solver.get_tiles(max(N for N, _ in shapes), hi)
+        tiles[f"groups_of_{lo}-{hi}"] = f"f32 {f32_m}x128, bf16 128x{tc_n}"
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -521,6 +530,7 @@ def main():
             "dtype": "f32" if args.precision == "fp32" else "bf16+f32", "data": "synthetic",
             "config": dict(workload=args.workload, **cfg, **SOLVER, pairs_per_step=args.batch,
                            precision=args.precision, loop=args.loop, init=args.init,
+                           gemm_tiles=dict(tiles, source="default" if args.no_autotune else "autotuned"),
                            l2="flushed (512 MB write) before every timed step",
                            parallelism=f"pairs sharded over {world} rank(s)"),
             "accuracy": float(np.mean(accs)),

@@ -298,7 +298,7 @@ int fastpfp_project_noalloc(void* stream, float* Y, int N, double tol, int max_i
  * matrix Y of the projection rounds (Section 4.3), on CUDA device `device`,
  * with the rounds' access pattern (every float read and written back once
  * per sweep, 16-byte accesses):
- *   level 0  shared memory, every SM sweeping ~219 KB of its own;
+ *   level 0  shared memory, every SM sweeping ~225 KB of its own;
  *   level 1  L2, one 64 MB buffer (the size of Y at N = 4000);
  *   level 2  HBM, one 2 GB buffer.
  * sweeps >= 1 timed sweeps after one warm-up sweep.  *gbs receives the
@@ -306,6 +306,42 @@ int fastpfp_project_noalloc(void* stream, float* Y, int N, double tol, int max_i
  * buffer (levels 1, 2); synchronises the device.  Errors: ERR_ARG (bad level
  * or sweeps, gbs == NULL), ERR_CUDA. */
 int fastpfp_bandwidth_probe(int device, int level, int sweeps, double* gbs);
+
+/* Tile shapes of the gradient products A X A' + lambda K (Section 4.1).
+ * Each solve picks, per grouped launch, the CTA tile of its FP32 products
+ * (128 or 64 output rows) and of its BF16 tensor-core products (128 x 256 or
+ * 128 x 128 outputs) from a table kept in the handle, indexed by a size
+ * class of the group's largest canonical N (class c covers
+ * 2^(c+6) < N <= 2^(c+7); class 0 also N <= 128) and a count class of the
+ * group's pairs (1; 2-4; 5-16; 17-32).  The table starts at 128 / 256 in
+ * every class.  Results do not depend on the choice: every output is
+ * accumulated in the same order whatever the tile. */
+#define FASTPFP_TUNE_SIZES 8
+#define FASTPFP_TUNE_COUNTS 4
+
+/* Fills the table by timing both tiles of both products for every class
+ * the handle can meet (N up to max_n, counts up to min(max_batch, 32)), on
+ * problems of the class's largest N (square, N = m) in the handle's own
+ * scratch, on `stream`: one untimed launch pair, then `reps` (1..100) timed
+ * ones; the faster tile (minimum over reps) wins.  A class whose smallest
+ * group already holds four times as many large tiles as the device has SMs,
+ * in both products, keeps 128 / 256 unmeasured.  Must not overlap a solve
+ * on the same handle.  times_ms (host, nullable) receives
+ * FASTPFP_TUNE_SIZES x FASTPFP_TUNE_COUNTS x 4 doubles, row-major: the best
+ * time of FP32 tile 128, FP32 tile 64, BF16 tile 256 and BF16 tile 128 of
+ * each class (0 where the class was not measured).  Synchronises `stream`.
+ * Errors: ERR_ARG, ERR_CUDA, ERR_TIMEOUT (a tensor-core launch gave up). */
+int fastpfp_autotune(fastpfp_t h, void* stream, int reps, double* times_ms);
+
+/* The table entry of size class n and count class count (the classes that
+ * contain these values): *f32_tile_m (128 or 64) and *tc_tile_n (256 or
+ * 128), each nullable.  Errors: ERR_ARG (n < 1, count < 1). */
+int fastpfp_get_tiles(fastpfp_t h, int n, int count, int* f32_tile_m, int* tc_tile_n);
+
+/* Sets the table entry of the classes that contain n and count; n <= 0
+ * means every size class, count <= 0 every count class.  f32_tile_m must be
+ * 128 or 64 and tc_tile_n 256 or 128.  Errors: ERR_ARG. */
+int fastpfp_set_tiles(fastpfp_t h, int n, int count, int f32_tile_m, int tc_tile_n);
 
 /* Human-readable name of an error code. */
 const char* fastpfp_error_string(int code);

@@ -102,6 +102,9 @@ struct fastpfp_s {
     int loop_body = 0;          // kernels per iteration of the last graph loop (0: host loop)
     std::vector<cudaGraph_t> graphs;
     std::vector<cudaGraphExec_t> execs;
+    // tile shapes of the gradient products per size and count class
+    int tile_f32[FASTPFP_TUNE_SIZES][FASTPFP_TUNE_COUNTS];
+    int tile_tc[FASTPFP_TUNE_SIZES][FASTPFP_TUNE_COUNTS];
     // learned warm start: features, activations, embeddings and gradients of
     // both graphs (big = canonical rows, small = columns)
     struct {
@@ -114,6 +117,18 @@ struct fastpfp_s {
 };
 
 namespace {
+
+// Size class of a canonical N (2^(c+6) < N <= 2^(c+7)) and count class of a
+// group of pairs, the indices of the handle's tile table.
+int size_class(int N) {
+    int c = 0;
+    for (int u = 128; u < N && c < FASTPFP_TUNE_SIZES - 1; u <<= 1) ++c;
+    return c;
+}
+int count_class(int count) { return count <= 1 ? 0 : count <= 4 ? 1 : count <= 16 ? 2 : 3; }
+constexpr int kCountClassHi[FASTPFP_TUNE_COUNTS] = {1, 4, 16, 32};
+int f32_tile(fastpfp_t h, int N, int count) { return h->tile_f32[size_class(N)][count_class(count)]; }
+int tc_tile(fastpfp_t h, int N, int count) { return h->tile_tc[size_class(N)][count_class(count)]; }
 
 #define FP_CUDA(x)                                         \
     do {                                                   \
@@ -242,9 +257,10 @@ void f32_products(const Slot& sl, const Problem& q, const fastpfp_params* p, Gem
                        q.k ? (float)p->lambda : 0.f, q.N, q.m, q.m, sl.ctrl};
 }
 
-int enqueue_gradient(const Slot& sl, cudaStream_t s, const Problem& q, const fastpfp_params* p) {
+int enqueue_gradient(const Slot& sl, cudaStream_t s, const Problem& q, const fastpfp_params* p, int tile_m) {
     GemmF32TGroup g1{}, g2{};
     g1.count = g2.count = 1;
+    g1.tile_m = g2.tile_m = tile_m;
     f32_products(sl, q, p, &g1.a[0], &g2.a[0]);
     FP_CUDA(gemm_f32t_group(g1, s));
     FP_CUDA(gemm_f32t_group(g2, s));
@@ -266,17 +282,21 @@ bool plan_tc(fastpfp_t h, const Problem* qs, int count, const fastpfp_params* p,
     for (int b = 0; b < count; b += kTcMaxGroup) {
         TcGroup a{}, c{};
         const int n = std::min(kTcMaxGroup, count - b);
+        int nmax = 0;
+        for (int i = 0; i < n; ++i) nmax = std::max(nmax, qs[b + i].N);
+        const int bn = tc_tile(h, nmax, n);
         a.count = c.count = n;
         a.mode = kTcOutBf16;
         c.mode = kTcOutF32;
+        a.bn = c.bn = bn;
         for (int i = 0; i < n; ++i) {
             const Problem& q = qs[b + i];
             const Slot& sl = h->slots[slot_of ? slot_of[b + i] : b + i];
             const int l16N = round8(q.N), l16m = round8(q.m);
-            if (!tc_make_map(&a.map_a[i], sl.A16, q.N, q.N, l16N, false) ||
-                !tc_make_map(&a.map_b[i], sl.Xt16, q.m, q.N, l16N, true) ||
-                !tc_make_map(&c.map_a[i], sl.T16, q.N, q.m, l16m, false) ||
-                !tc_make_map(&c.map_b[i], sl.A216, q.m, q.m, l16m, true))
+            if (!tc_make_map(&a.map_a[i], sl.A16, q.N, q.N, l16N, kTcTileM) ||
+                !tc_make_map(&a.map_b[i], sl.Xt16, q.m, q.N, l16N, bn) ||
+                !tc_make_map(&c.map_a[i], sl.T16, q.N, q.m, l16m, kTcTileM) ||
+                !tc_make_map(&c.map_b[i], sl.A216, q.m, q.m, l16m, bn))
                 return false;
             a.prob[i] = TcProblem{q.N, q.m, q.N, sl.T16, l16m, nullptr, 0, 0.f, sl.ctrl, &sl.ctrl->error};
             c.prob[i] = TcProblem{q.N, q.m, q.m, sl.Y, round4(q.N), q.k ? sl.K : nullptr, round4(q.m),
@@ -452,7 +472,7 @@ int enqueue_single(fastpfp_t h, cudaStream_t s, const Slot& sl, const Problem& q
             g = enqueue_tc(tc, st);
             if (g < 0) return g;
         }
-        const int g32 = enqueue_gradient(sl, st, q, p);
+        const int g32 = enqueue_gradient(sl, st, q, p, f32_tile(h, q.N, 1));
         if (g32 < 0) return g32;
         if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 1], st));
         FP_CUDA(pd_launch(L, P, st));
@@ -751,8 +771,12 @@ void f32_groups(fastpfp_t h, const std::vector<Problem>& qs, const std::vector<M
     for (int b = 0; b < (int)mem.size(); b += kF32MaxGroup) {
         GemmF32TGroup ga{}, gb{};
         ga.count = gb.count = std::min(kF32MaxGroup, (int)mem.size() - b);
-        for (int i = 0; i < ga.count; ++i)
+        int nmax = 0;
+        for (int i = 0; i < ga.count; ++i) {
             f32_products(h->slots[mem[b + i].slot], qs[mem[b + i].pair], p, &ga.a[i], &gb.a[i]);
+            nmax = std::max(nmax, qs[mem[b + i].pair].N);
+        }
+        ga.tile_m = gb.tile_m = f32_tile(h, nmax, ga.count);
         ga_out.push_back(ga);
         gb_out.push_back(gb);
     }
@@ -877,6 +901,11 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     h->max_batch = max_batch;
     h->ld = round4(max_n);
     h->nslots = std::min(max_batch, kMaxWavePairs);
+    for (int c = 0; c < FASTPFP_TUNE_SIZES; ++c)
+        for (int k = 0; k < FASTPFP_TUNE_COUNTS; ++k) {
+            h->tile_f32[c][k] = 128;
+            h->tile_tc[c][k] = 256;
+        }
     if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         pd_configure() != cudaSuccess || pdb_configure() != cudaSuccess || tc_configure() != cudaSuccess ||
         gemm_f32t_configure() != cudaSuccess ||
@@ -1383,6 +1412,120 @@ int fastpfp_bandwidth_probe(int device, int level, int sweeps, double* gbs) {
     return FASTPFP_OK;
 }
 
+int fastpfp_autotune(fastpfp_t h, void* stream, int reps, double* times_ms) {
+    if (!h || reps < 1 || reps > 100) return FASTPFP_ERR_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    constexpr int kSlotsPerClass = 4;
+    if (times_ms)
+        for (int i = 0; i < FASTPFP_TUNE_SIZES * FASTPFP_TUNE_COUNTS * kSlotsPerClass; ++i) times_ms[i] = 0.0;
+    int* d_err = h->d_flags;   // free between solves; receives a tensor-core timeout
+    FP_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+    cudaEvent_t e0 = h->ev[0], e1 = h->ev[1];
+    // best time of `launch` (one product pair) over reps, after one untimed run
+    auto best_of = [&](auto&& launch, double* out) -> int {
+        FP_CUDA(launch());
+        float best = 0.f;
+        for (int r = 0; r < reps; ++r) {
+            FP_CUDA(cudaEventRecord(e0, s));
+            FP_CUDA(launch());
+            FP_CUDA(cudaEventRecord(e1, s));
+            FP_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            FP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (r == 0 || ms < best) best = ms;
+        }
+        *out = best;
+        return 0;
+    };
+    for (int sc = 0; sc < FASTPFP_TUNE_SIZES; ++sc) {
+        const int lo = sc == 0 ? 1 : (64 << sc) + 1;
+        if (lo > h->max_n) break;
+        const int N = std::min(128 << sc, h->max_n), m = N;
+        const int ld4 = round4(N), ld8 = round8(N);
+        for (int cc = 0; cc < FASTPFP_TUNE_COUNTS; ++cc) {
+            const int clo = cc == 0 ? 1 : kCountClassHi[cc - 1] + 1;
+            if (clo > h->nslots) break;
+            // a class whose smallest group already fills every SM four times
+            // over with the large tiles of both products keeps them unmeasured
+            const int tiles32 = ((N + 127) / 128) * ((m + 127) / 128);
+            const int tiles16 = ((N + kTcTileM - 1) / kTcTileM) * ((m + 255) / 256);
+            if ((long long)clo * std::min(tiles32, tiles16) >= 4ll * h->num_sms) continue;
+            const int cnt = std::min(kCountClassHi[cc], h->nslots);
+            double t[kSlotsPerClass] = {0, 0, 0, 0};
+            // FP32 products T^T = X^T A, Y = T A' in the slots' scratch
+            for (int v = 0; v < 2; ++v) {
+                GemmF32TGroup g1{}, g2{};
+                g1.count = g2.count = cnt;
+                g1.tile_m = g2.tile_m = v == 0 ? 128 : 64;
+                for (int i = 0; i < cnt; ++i) {
+                    const Slot& sl = h->slots[i];
+                    g1.a[i] = GemmF32TArgs{sl.X, ld4, sl.A32, ld4, sl.T, ld4, nullptr, 0, 0.f, m, N, N, nullptr};
+                    g2.a[i] = GemmF32TArgs{sl.T, ld4, sl.A232, ld4, sl.Y, ld4, nullptr, 0, 0.f, N, m, m, nullptr};
+                }
+                const int r = best_of([&]() {
+                    cudaError_t e = gemm_f32t_group(g1, s);
+                    return e == cudaSuccess ? gemm_f32t_group(g2, s) : e;
+                }, &t[v]);
+                if (r < 0) return r;
+            }
+            // BF16 products T = A X, Y = T A' on the tensor cores
+            for (int v = 0; v < 2; ++v) {
+                const int bn = v == 0 ? 256 : 128;
+                TcGroup a{}, c{};
+                a.count = c.count = cnt;
+                a.mode = kTcOutBf16;
+                c.mode = kTcOutF32;
+                a.bn = c.bn = bn;
+                for (int i = 0; i < cnt; ++i) {
+                    const Slot& sl = h->slots[i];
+                    if (!tc_make_map(&a.map_a[i], sl.A16, N, N, ld8, kTcTileM) ||
+                        !tc_make_map(&a.map_b[i], sl.Xt16, m, N, ld8, bn) ||
+                        !tc_make_map(&c.map_a[i], sl.T16, N, m, ld8, kTcTileM) ||
+                        !tc_make_map(&c.map_b[i], sl.A216, m, m, ld8, bn))
+                        return FASTPFP_ERR_UNSUPPORTED;
+                    a.prob[i] = TcProblem{N, m, N, sl.T16, ld8, nullptr, 0, 0.f, nullptr, d_err};
+                    c.prob[i] = TcProblem{N, m, m, sl.Y, ld4, nullptr, 0, 0.f, nullptr, d_err};
+                }
+                const int r = best_of([&]() {
+                    cudaError_t e = tc_gemm(a, s);
+                    return e == cudaSuccess ? tc_gemm(c, s) : e;
+                }, &t[2 + v]);
+                if (r < 0) return r;
+            }
+            int err = 0;
+            FP_CUDA(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            FP_CUDA(cudaStreamSynchronize(s));
+            if (err != 0) return err;
+            h->tile_f32[sc][cc] = t[1] < t[0] ? 64 : 128;
+            h->tile_tc[sc][cc] = t[3] < t[2] ? 128 : 256;
+            if (times_ms)
+                for (int k = 0; k < kSlotsPerClass; ++k)
+                    times_ms[(sc * FASTPFP_TUNE_COUNTS + cc) * kSlotsPerClass + k] = t[k];
+        }
+    }
+    return FASTPFP_OK;
+}
+
+int fastpfp_get_tiles(fastpfp_t h, int n, int count, int* f32_tile_m, int* tc_tile_n) {
+    if (!h || n < 1 || count < 1) return FASTPFP_ERR_ARG;
+    if (f32_tile_m) *f32_tile_m = f32_tile(h, n, count);
+    if (tc_tile_n) *tc_tile_n = tc_tile(h, n, count);
+    return FASTPFP_OK;
+}
+
+int fastpfp_set_tiles(fastpfp_t h, int n, int count, int f32_tile_m, int tc_tile_n) {
+    if (!h || (f32_tile_m != 128 && f32_tile_m != 64) || (tc_tile_n != 256 && tc_tile_n != 128))
+        return FASTPFP_ERR_ARG;
+    for (int c = 0; c < FASTPFP_TUNE_SIZES; ++c)
+        for (int k = 0; k < FASTPFP_TUNE_COUNTS; ++k)
+            if ((n <= 0 || c == size_class(n)) && (count <= 0 || k == count_class(count))) {
+                h->tile_f32[c][k] = f32_tile_m;
+                h->tile_tc[c][k] = tc_tile_n;
+            }
+    return FASTPFP_OK;
+}
+
 int fastpfp_last_trace(fastpfp_t h, int pair, int* inner_counts, double* deltas, int cap) {
     if (!h || cap < 0) return FASTPFP_ERR_ARG;
     if (pair < 0 || pair >= h->last_count) return FASTPFP_ERR_ARG;
@@ -1421,8 +1564,10 @@ int fastpfp_gradient(fastpfp_t h, void* stream, const float* A, const float* X, 
         a.count = c.count = 1;
         a.mode = kTcOutBf16;
         c.mode = kTcOutF32;
-        if (!tc_make_map(&a.map_a[0], sl.A16, N, N, l16N, false) || !tc_make_map(&a.map_b[0], sl.Xt16, m, N, l16N, true) ||
-            !tc_make_map(&c.map_a[0], sl.T16, N, m, l16m, false) || !tc_make_map(&c.map_b[0], sl.A216, m, m, l16m, true))
+        const int bn = tc_tile(h, N, 1);
+        a.bn = c.bn = bn;
+        if (!tc_make_map(&a.map_a[0], sl.A16, N, N, l16N, kTcTileM) || !tc_make_map(&a.map_b[0], sl.Xt16, m, N, l16N, bn) ||
+            !tc_make_map(&c.map_a[0], sl.T16, N, m, l16m, kTcTileM) || !tc_make_map(&c.map_b[0], sl.A216, m, m, l16m, bn))
             return FASTPFP_ERR_UNSUPPORTED;
         a.prob[0] = TcProblem{N, m, N, sl.T16, l16m, nullptr, 0, 0.f, nullptr, nullptr};
         c.prob[0] = TcProblem{N, m, m, sl.Y, l4m, lambda != 0.f ? sl.K : nullptr, l4m, lambda, nullptr, nullptr};
@@ -1447,6 +1592,7 @@ int fastpfp_gradient(fastpfp_t h, void* stream, const float* A, const float* X, 
     const float* A2op = f32_operand(A2, m, sl.A232, &lda2);
     GemmF32TGroup g1{}, g2{};
     g1.count = g2.count = 1;
+    g1.tile_m = g2.tile_m = f32_tile(h, N, 1);
     g1.a[0] = GemmF32TArgs{sl.X, ldx, Aop, lda, sl.T, ldt, nullptr, 0, 0.f, m, N, N, nullptr};
     g2.a[0] = GemmF32TArgs{sl.T, ldt, A2op, lda2, Y, ldy, lambda != 0.f ? K : nullptr, m, lambda, N, m, m, nullptr};
     FP_CUDA(gemm_f32t_group(g1, s));

@@ -109,11 +109,14 @@ __global__ void __launch_bounds__(kThreads) gemm_f32_kernel(const __grid_constan
 // The solve's products with the left operand supplied transposed (K x M
 // row-major) and both operands 16-byte aligned with leading dimensions that
 // are multiples of 4: every shared-memory tile row is a contiguous run of
-// global memory, copied with cp.async into a three-stage ring.  128 x 128 x
-// 16 tiles, 8 x 8 outputs per thread, packed f32x2 FMAs (two accumulators
-// per instruction), FP32 accumulation in a fixed order per output.
+// global memory, copied with cp.async into a three-stage ring.  BMT x 128 x
+// 16 tiles (BMT = 128 or 64, picked per problem size by fastpfp_autotune),
+// 256 threads, (BMT / 16) x 8 outputs per thread, packed f32x2 FMAs (two
+// accumulators per instruction), FP32 accumulation in a fixed order per
+// output.
 constexpr int TBK = 16, TSTAGES = 3;
-constexpr size_t kTileStageFloats = (size_t)TBK * (BM + BN);
+template <int BMT>
+constexpr size_t tile_stage_floats() { return (size_t)TBK * (BMT + BN); }
 
 __device__ __forceinline__ void cp_async16_zfill(void* smem_dst, const void* gmem_src, bool valid) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -132,10 +135,13 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
     return r;
 }
 
+template <int BMT>
 __global__ void __launch_bounds__(kThreads) gemm_f32t_kernel(const __grid_constant__ GemmF32TGroup grp) {
+    constexpr int TMT = BMT / 16;                                // rows per thread: 8 or 4
+    constexpr size_t kStage = tile_stage_floats<BMT>();
     if ((int)blockIdx.z >= grp.count) return;
     const GemmF32TArgs& g = grp.a[blockIdx.z];
-    if ((int)blockIdx.y * BM >= g.M || (int)blockIdx.x * BN >= g.Nc) return;
+    if ((int)blockIdx.y * BMT >= g.M || (int)blockIdx.x * BN >= g.Nc) return;
     if (g.ctrl) {
         if (ld_relaxed_i32(&g.ctrl->done) != 0 || ld_relaxed_i32(&g.ctrl->error) != 0) return;
         if (ld_relaxed_i32(&g.ctrl->lowp) != 0) return;
@@ -143,29 +149,33 @@ __global__ void __launch_bounds__(kThreads) gemm_f32t_kernel(const __grid_consta
     extern __shared__ __align__(16) float tsm[];
     const int tid = threadIdx.x;
     const int tr = tid / (BN / TN), tc = tid % (BN / TN);
-    const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+    const int row0 = blockIdx.y * BMT, col0 = blockIdx.x * BN;
     const int KT = (g.K + TBK - 1) / TBK;
 
-    // stage st: As = tsm + st * stage (TBK x BM), Bs = As + TBK * BM (TBK x BN)
+    // stage st: As = tsm + st * stage (TBK x BMT), Bs = As + TBK * BMT (TBK x BN)
     auto issue = [&](int st, int kt) {
-        float* As = tsm + (size_t)st * kTileStageFloats;
-        float* Bs = As + TBK * BM;
+        float* As = tsm + (size_t)st * kStage;
+        float* Bs = As + TBK * BMT;
         const int k0 = kt * TBK;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int idx = tid + h * kThreads;            // 0 .. 511
-            const int kk = idx >> 5, c4 = (idx & 31) * 4;  // tile row, first column of the chunk
+        for (int idx = tid; idx < TBK * BMT / 4; idx += kThreads) {
+            const int kk = idx / (BMT / 4), c4 = (idx % (BMT / 4)) * 4;
             const int gk = k0 + kk;
             const bool va = gk < g.K && row0 + c4 < g.M;
-            cp_async16_zfill(As + kk * BM + c4, va ? g.AT + (size_t)gk * g.lda + row0 + c4 : g.AT, va);
+            cp_async16_zfill(As + kk * BMT + c4, va ? g.AT + (size_t)gk * g.lda + row0 + c4 : g.AT, va);
+        }
+#pragma unroll
+        for (int idx = tid; idx < TBK * BN / 4; idx += kThreads) {
+            const int kk = idx >> 5, c4 = (idx & 31) * 4;
+            const int gk = k0 + kk;
             const bool vb = gk < g.K && col0 + c4 < g.Nc;
             cp_async16_zfill(Bs + kk * BN + c4, vb ? g.B + (size_t)gk * g.ldb + col0 + c4 : g.B, vb);
         }
     };
 
-    unsigned long long acc[TM][TN / 2];
+    unsigned long long acc[TMT][TN / 2];
 #pragma unroll
-    for (int i = 0; i < TM; ++i)
+    for (int i = 0; i < TMT; ++i)
 #pragma unroll
         for (int j = 0; j < TN / 2; ++j) acc[i][j] = 0ull;   // (+0.0f, +0.0f)
 
@@ -179,19 +189,24 @@ __global__ void __launch_bounds__(kThreads) gemm_f32t_kernel(const __grid_consta
         __syncthreads();   // tile kt is in place; every thread is done with tile kt - 1
         if (kt + TSTAGES - 1 < KT) issue((kt + TSTAGES - 1) % TSTAGES, kt + TSTAGES - 1);
         asm volatile("cp.async.commit_group;" ::: "memory");
-        const float* As = tsm + (size_t)(kt % TSTAGES) * kTileStageFloats;
-        const float* Bs = As + TBK * BM;
+        const float* As = tsm + (size_t)(kt % TSTAGES) * kStage;
+        const float* Bs = As + TBK * BMT;
 #pragma unroll
         for (int kk = 0; kk < TBK; ++kk) {
-            const float4 a0 = *reinterpret_cast<const float4*>(As + kk * BM + tr * 4);
-            const float4 a1 = *reinterpret_cast<const float4*>(As + kk * BM + 64 + tr * 4);
+            float a[TMT];
+            const float4 a0 = *reinterpret_cast<const float4*>(As + kk * BMT + tr * 4);
+            a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
+            if (TMT == 8) {
+                const float4 a1 = *reinterpret_cast<const float4*>(As + kk * BMT + 64 + tr * 4);
+                a[TMT > 4 ? 4 : 0] = a1.x; a[TMT > 5 ? 5 : 0] = a1.y;
+                a[TMT > 6 ? 6 : 0] = a1.z; a[TMT > 7 ? 7 : 0] = a1.w;
+            }
             const float4 b0 = *reinterpret_cast<const float4*>(Bs + kk * BN + tc * 4);
             const float4 b1 = *reinterpret_cast<const float4*>(Bs + kk * BN + 64 + tc * 4);
-            const float a[TM] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const unsigned long long b[TN / 2] = {pk2(b0.x, b0.y), pk2(b0.z, b0.w), pk2(b1.x, b1.y),
                                                   pk2(b1.z, b1.w)};
 #pragma unroll
-            for (int i = 0; i < TM; ++i) {
+            for (int i = 0; i < TMT; ++i) {
                 const unsigned long long ai = pk2(a[i], a[i]);
 #pragma unroll
                 for (int j = 0; j < TN / 2; ++j) acc[i][j] = ffma2(ai, b[j], acc[i][j]);
@@ -201,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) gemm_f32t_kernel(const __grid_consta
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 
 #pragma unroll
-    for (int i = 0; i < TM; ++i) {
+    for (int i = 0; i < TMT; ++i) {
         const int r = row0 + (i < 4 ? tr * 4 + i : 64 + tr * 4 + (i - 4));
         if (r >= g.M) continue;
 #pragma unroll
@@ -218,21 +233,29 @@ __global__ void __launch_bounds__(kThreads) gemm_f32t_kernel(const __grid_consta
 
 }  // namespace
 
-size_t gemm_f32t_smem_bytes() { return (size_t)TSTAGES * kTileStageFloats * sizeof(float); }
+template <int BMT>
+static size_t f32t_smem() { return (size_t)TSTAGES * tile_stage_floats<BMT>() * sizeof(float); }
 
 cudaError_t gemm_f32t_configure() {
-    return cudaFuncSetAttribute((const void*)gemm_f32t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)gemm_f32t_smem_bytes());
+    cudaError_t e = cudaFuncSetAttribute((const void*)gemm_f32t_kernel<128>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f32t_smem<128>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void*)gemm_f32t_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)f32t_smem<64>());
 }
 
 cudaError_t gemm_f32t_group(const GemmF32TGroup& g, cudaStream_t s) {
+    const int bm = g.tile_m == 64 ? 64 : 128;
     int mt = 0, nt = 0;
     for (int i = 0; i < g.count; ++i) {
-        mt = max(mt, (g.a[i].M + BM - 1) / BM);
+        mt = max(mt, (g.a[i].M + bm - 1) / bm);
         nt = max(nt, (g.a[i].Nc + BN - 1) / BN);
     }
     if (g.count <= 0 || mt == 0 || nt == 0) return cudaSuccess;
-    gemm_f32t_kernel<<<dim3(nt, mt, g.count), kThreads, gemm_f32t_smem_bytes(), s>>>(g);
+    if (bm == 64)
+        gemm_f32t_kernel<64><<<dim3(nt, mt, g.count), kThreads, f32t_smem<64>(), s>>>(g);
+    else
+        gemm_f32t_kernel<128><<<dim3(nt, mt, g.count), kThreads, f32t_smem<128>(), s>>>(g);
     return cudaGetLastError();
 }
 

@@ -11,15 +11,16 @@
 // FP32 accumulation in TMEM; the epilogue writes T as BF16 for the second
 // product, or Y as FP32 with lambda K added.
 //
-// Persistent: one CTA per SM walks the 128 x 256 output tiles of every
-// problem of the group (N = 256 per MMA halves the shared-memory operand
-// bytes per flop of a 128 x 128 tile, which would otherwise saturate shared
-// memory).  Warp 0 issues the TMA loads of a 4-stage ring continuously
-// across tiles, warp 1 owns the TMEM allocation (two 256-column
-// accumulators, all 512 columns) and one lane issues the MMAs (K = 16 each,
-// four per 64-wide stage) into one accumulator while warps 2..5 drain the
-// other with tcgen05.ld, so a tile's epilogue overlaps the next tile's main
-// loop.
+// Persistent: one CTA per SM walks the 128 x BN output tiles of every
+// problem of the group.  BN = 256 (the default) halves the shared-memory
+// operand bytes per flop of a 128 x 128 tile, which would otherwise saturate
+// shared memory; BN = 128 doubles the tile count, which keeps more SMs busy
+// when a group has few small problems (fastpfp_autotune picks per size
+// class).  Warp 0 issues the TMA loads of a 4-stage ring continuously across
+// tiles, warp 1 owns the TMEM allocation (two BN-column accumulators) and one
+// lane issues the MMAs (K = 16 each, four per 64-wide stage) into one
+// accumulator while warps 2..5 drain the other with tcgen05.ld, so a tile's
+// epilogue overlaps the next tile's main loop.
 // Every mbarrier wait is bounded: on expiry the CTA records
 // FASTPFP_ERR_TIMEOUT, every role stops, the TMEM is freed and it returns.
 #include <cuda.h>
@@ -31,12 +32,20 @@
 namespace fpfp {
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int BM = kTcTileM, BK = 64, STAGES = 4;
 constexpr int kTileBytesA = BM * BK * 2;
-constexpr int kTileBytesB = BN * BK * 2;
-constexpr int kStageBytes = kTileBytesA + kTileBytesB;
 constexpr int kThreads = 192;
-constexpr uint32_t kTmemCols = 512;   // two 256-column FP32 accumulators
+// Shapes that depend on the tile width BN (128 or 256).
+template <int BN>
+struct TcShape {
+    static constexpr int kTileBytesB = BN * BK * 2;
+    static constexpr int kStageBytes = kTileBytesA + kTileBytesB;
+    static constexpr uint32_t kTmemCols = 2 * BN;   // two BN-column FP32 accumulators
+    // Instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, both
+    // K-major, M = 128, N = BN.
+    static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                       ((uint32_t)(BM >> 4) << 24);
+};
 constexpr long long kWaitNs = 2000ll * 1000000ll;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -94,17 +103,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     d |= (uint64_t)2 << 61;                     // 128-byte swizzle
     return d;
 }
-// Instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, both
-// K-major, M = 128, N = 256.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc)
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -130,6 +135,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 // Output tile t of the group: problem g, tile row / column, or false when
 // the solve that owns the problem is not in its BF16 phase (every role of
 // every CTA decides the same way: the flags do not change during a launch).
+template <int BN>
 __device__ __forceinline__ bool tile_of(const TcGroup& G, int t, int* g, int* m0, int* n0) {
     int p = 0;
     while (p + 1 < G.count && G.tile0[p + 1] <= t) ++p;
@@ -147,6 +153,7 @@ __device__ __forceinline__ bool tile_of(const TcGroup& G, int t, int* g, int* m0
 
 // Epilogue of one tile: warp `quarter` of the four epilogue warps drains TMEM
 // lanes 32 * quarter .. + 31 (tile rows) of accumulator column base `tcol`.
+template <int BN>
 __device__ __forceinline__ void drain_tile(const TcGroup& G, const TcProblem& pr, uint32_t tmem, uint32_t tcol,
                                            int quarter, int lane, int m0, int n0) {
     const int row = m0 + quarter * 32 + lane;
@@ -204,7 +211,11 @@ __device__ __forceinline__ void drain_tile(const TcGroup& G, const TcProblem& pr
     }
 }
 
+template <int BN>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcGroup G) {
+    using S = TcShape<BN>;
+    constexpr int kStageBytes = S::kStageBytes;
+    constexpr uint32_t kTmemCols = S::kTmemCols;
     const int ntiles = G.tile0[G.count];
     if ((int)blockIdx.x >= ntiles) return;
 
@@ -250,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         uint32_t it = 0;
         for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
             int g, m0, n0;
-            if (!tile_of(G, t, &g, &m0, &n0)) continue;
+            if (!tile_of<BN>(G, t, &g, &m0, &n0)) continue;
             const int nk = (G.prob[g].K + BK - 1) / BK;
             for (int kb = 0; kb < nk; ++kb, ++it) {
                 const int s = it % STAGES;
@@ -268,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         uint32_t it = 0, tc = 0;
         for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
             int g, m0, n0;
-            if (!tile_of(G, t, &g, &m0, &n0)) continue;
+            if (!tile_of<BN>(G, t, &g, &m0, &n0)) continue;
             const int nk = (G.prob[g].K + BK - 1) / BK;
             const uint32_t buf = tc & 1u, aph = (tc >> 1) & 1u;
             if (!mbar_wait(&acc_empty[buf], aph ^ 1u, abort)) break;
@@ -288,7 +299,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 const uint64_t ad = smem_desc(a), bd = smem_desc(b);
 #pragma unroll
                 for (int j = 0; j < BK / 16; ++j)   // K = 16 per MMA: 32 bytes along the swizzled row
-                    mma_bf16(acc, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), (kb > 0 || j > 0) ? 1u : 0u);
+                    mma_bf16(acc, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), S::kIdesc,
+                             (kb > 0 || j > 0) ? 1u : 0u);
                 mma_commit(&empty[s]);
             }
             if (!ok) break;
@@ -301,14 +313,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         uint32_t tc = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             int g, m0, n0;
-            if (!tile_of(G, t, &g, &m0, &n0)) continue;
+            if (!tile_of<BN>(G, t, &g, &m0, &n0)) continue;
             const uint32_t buf = tc & 1u, aph = (tc >> 1) & 1u;
             // one lane waits; tcgen05.ld is warp-collective, so the outcome is broadcast
             int okl = 0;
             if (lane == 0) okl = mbar_wait(&acc_full[buf], aph, abort) ? 1 : 0;
             if (__shfl_sync(0xffffffffu, okl, 0) == 0) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            drain_tile(G, G.prob[g], tmem, buf * (uint32_t)BN, quarter, lane, m0, n0);
+            drain_tile<BN>(G, G.prob[g], tmem, buf * (uint32_t)BN, quarter, lane, m0, n0);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) {
@@ -346,7 +358,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-size_t tc_smem_bytes() { return (size_t)STAGES * kStageBytes + 1024 + 256; }
+size_t tc_smem_bytes(int bn) {
+    return (size_t)STAGES * (bn == 128 ? TcShape<128>::kStageBytes : TcShape<256>::kStageBytes) + 1024 + 256;
+}
 
 static int g_tc_sms = 0;
 
@@ -355,19 +369,23 @@ cudaError_t tc_configure() {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute((const void*)tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tc_smem_bytes());
+    e = cudaFuncSetAttribute((const void*)tc_gemm_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc_smem_bytes(256));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void*)tc_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tc_smem_bytes(128));
 }
 
 // rows x cols BF16 matrix, row-major with leading dimension ld (elements,
-// a multiple of 8), read as 64-column boxes of 128 rows (A operand) or 256
-// rows (B operand) with 128-byte swizzle.
-bool tc_make_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int cols, int ld, bool b_operand) {
+// a multiple of 8), read as 64-column boxes of box_rows rows (128 for the A
+// operand, the group's tile width for B) with 128-byte swizzle.
+bool tc_make_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int cols, int ld, int box_rows) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn || (ld % 8) != 0 || (reinterpret_cast<uintptr_t>(ptr) & 15) != 0) return false;
+    if (box_rows != 128 && box_rows != 256) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)(b_operand ? BN : BM)};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), dims,
                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -378,15 +396,19 @@ bool tc_make_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int cols,
 cudaError_t tc_gemm(const TcGroup& G0, cudaStream_t s) {
     if (G0.count <= 0) return cudaSuccess;
     TcGroup G = G0;
+    const int bn = G.bn == 128 ? 128 : 256;
     G.tile0[0] = 0;
     for (int i = 0; i < G.count; ++i) {
-        G.ntn[i] = (G.prob[i].N + BN - 1) / BN;
+        G.ntn[i] = (G.prob[i].N + bn - 1) / bn;
         G.tile0[i + 1] = G.tile0[i] + ((G.prob[i].M + BM - 1) / BM) * G.ntn[i];
     }
     const int ntiles = G.tile0[G.count];
     if (ntiles <= 0) return cudaSuccess;
     const int grid = min(ntiles, g_tc_sms > 0 ? g_tc_sms : 148);
-    tc_gemm_kernel<<<grid, kThreads, tc_smem_bytes(), s>>>(G);
+    if (bn == 128)
+        tc_gemm_kernel<128><<<grid, kThreads, tc_smem_bytes(128), s>>>(G);
+    else
+        tc_gemm_kernel<256><<<grid, kThreads, tc_smem_bytes(256), s>>>(G);
     return cudaGetLastError();
 }
 

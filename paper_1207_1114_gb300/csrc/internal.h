@@ -187,16 +187,19 @@ struct TcGroup {
     TcProblem prob[kTcMaxGroup];
     int count;
     int mode;
+    int bn;   // output tile columns: 256 (0 reads as 256) or 128; map_b's box has bn rows
     // filled by tc_gemm: output tiles of problems before i (tile0[count] =
     // all tiles) and tiles per row of tiles of problem i
     int tile0[kTcMaxGroup + 1];
     int ntn[kTcMaxGroup];
 };
-size_t tc_smem_bytes();
+constexpr int kTcTileM = 128;   // output tile rows of tc_gemm (the A operand's box)
+size_t tc_smem_bytes(int bn);
 cudaError_t tc_configure();
 // TMA map of a rows x cols BF16 operand (ld elements, a multiple of 8) for
-// tc_gemm: b_operand selects the B-operand box (256 rows) over A's (128).
-bool tc_make_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int cols, int ld, bool b_operand);
+// tc_gemm, read in boxes of box_rows rows: kTcTileM for an A operand, the
+// group's bn for a B operand.  False if the layout does not suit TMA.
+bool tc_make_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int cols, int ld, int box_rows);
 cudaError_t tc_gemm(const TcGroup& G, cudaStream_t s);
 
 // ----------------------------------------------------------------- GEMM
@@ -235,6 +238,7 @@ struct GemmF32TArgs {
 struct GemmF32TGroup {
     GemmF32TArgs a[kF32MaxGroup];
     int count;
+    int tile_m;   // output rows per CTA tile: 128 (0 reads as 128) or 64
 };
 cudaError_t gemm_f32t_configure();
 cudaError_t gemm_f32t_group(const GemmF32TGroup& g, cudaStream_t s);

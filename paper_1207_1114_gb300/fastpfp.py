@@ -31,7 +31,9 @@ EXPORTS = ("fastpfp_default_params", "fastpfp_create", "fastpfp_destroy", "fastp
            "fastpfp_last_trace",
            "fastpfp_gradient", "fastpfp_affinity", "fastpfp_project", "fastpfp_discretize",
            "fastpfp_project_noalloc", "fastpfp_warmstart", "fastpfp_warmstart_train_step",
-           "fastpfp_bandwidth_probe", "fastpfp_error_string")
+           "fastpfp_bandwidth_probe", "fastpfp_autotune", "fastpfp_get_tiles", "fastpfp_set_tiles",
+           "fastpfp_error_string")
+TUNE_SIZES, TUNE_COUNTS = 8, 4
 MLP_NPARAMS = 32 * 128 + 128 + 128 * 64 + 64
 
 
@@ -100,6 +102,9 @@ def lib():
     l.fastpfp_warmstart_train_step.argtypes = [P, V, P, I, P, I, P, P, I, P, P, P, P, I, C.c_float,
                                                C.POINTER(C.c_double), P]
     l.fastpfp_bandwidth_probe.argtypes = [I, I, I, C.POINTER(C.c_double)]
+    l.fastpfp_autotune.argtypes = [P, V, I, P]
+    l.fastpfp_get_tiles.argtypes = [P, I, I, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    l.fastpfp_set_tiles.argtypes = [P, I, I, I, I]
     l.fastpfp_error_string.argtypes = [I]
     l.fastpfp_error_string.restype = C.c_char_p
     for name in EXPORTS:
@@ -322,6 +327,30 @@ class Solver:
             raise FastPFPError(n, "fastpfp_last_trace")
         n = min(n, cap)
         return inner[:n].copy(), delta[:n].copy()
+
+    # ------------------------------------------------------- tile shapes
+    def autotune(self, reps: int = 3, stream=None):
+        """fastpfp_autotune: times both tiles of both gradient products per
+        size and count class and keeps the faster.  Returns the best times
+        (ms) as a (TUNE_SIZES, TUNE_COUNTS, 4) array: FP32 tile 128, FP32
+        tile 64, BF16 tile 256, BF16 tile 128 (0 = class not measured)."""
+        t = np.zeros((TUNE_SIZES, TUNE_COUNTS, 4), dtype=np.float64)
+        _check(lib().fastpfp_autotune(self._h, _stream(stream), int(reps), C.c_void_p(t.ctypes.data)),
+               "fastpfp_autotune")
+        return t
+
+    def get_tiles(self, n: int, count: int = 1):
+        """(FP32 tile rows, BF16 tile columns) used for a group of `count`
+        pairs whose largest canonical size is n."""
+        a, b = C.c_int(0), C.c_int(0)
+        _check(lib().fastpfp_get_tiles(self._h, int(n), int(count), C.byref(a), C.byref(b)),
+               "fastpfp_get_tiles")
+        return a.value, b.value
+
+    def set_tiles(self, f32_tile_m: int, tc_tile_n: int, n: int = 0, count: int = 0):
+        """Sets the tiles of the classes of n and count (0 = every class)."""
+        _check(lib().fastpfp_set_tiles(self._h, int(n), int(count), int(f32_tile_m), int(tc_tile_n)),
+               "fastpfp_set_tiles")
 
     # ------------------------------------------------------- single steps
     def gradient(self, A, X, A2, K=None, lam=0.0, precision=FP32, stream=None):

@@ -549,3 +549,78 @@ def test_attributed_1000_full_size_properties(solver):
     ref = T @ g.A2.astype(np.float64) + K[rows]
     bound = np.abs(g.A[rows]) @ np.abs(Xg).astype(np.float64) @ np.abs(g.A2) + np.abs(K[rows])
     assert (np.abs(G[rows] - ref) <= 1e-5 * bound).all()
+
+
+# ------------------------------------------------------------ tile shapes
+
+@pytest.mark.parametrize("N,m", [(129, 100), (1000, 900), (1200, 1000)])
+def test_gradient_tiles_give_identical_products(solver, N, m):
+    """Both CTA tiles of each product accumulate every output in the same
+    order: FP32 tile 64 equals tile 128 bit for bit; the BF16 128-column tile
+    matches the 256-column one to FP32 rounding and the oracle to the BF16
+    bound."""
+    rng = np.random.default_rng(N + 17 * m)
+    A = synth.random_graph(rng, N, 0.2).astype(np.float32)
+    A2 = synth.random_graph(rng, m, 0.2).astype(np.float32)
+    X = rng.random((N, m)).astype(np.float32)
+    K = rng.normal(size=(N, m)).astype(np.float32)
+    lam = 0.7
+    bound = np.abs(A) @ np.abs(X).astype(np.float64) @ np.abs(A2) + lam * np.abs(K)
+    args = (cu(A), cu(X), cu(A2), cu(K), lam)
+    try:
+        assert solver.get_tiles(N, 1) == (128, 256)
+        g128 = solver.gradient(*args).cpu().numpy()
+        t256 = solver.gradient(*args, precision=F.BF16).cpu().numpy()
+        solver.set_tiles(64, 128, n=N, count=1)
+        assert solver.get_tiles(N, 1) == (64, 128)
+        g64 = solver.gradient(*args).cpu().numpy()
+        t128 = solver.gradient(*args, precision=F.BF16).cpu().numpy()
+    finally:
+        solver.set_tiles(128, 256)
+    np.testing.assert_array_equal(g64, g128)
+    assert (np.abs(t128 - t256) <= 1e-6 * bound + 1e-30).all()
+    ref16 = oracle.gradient(_bf16(A), _bf16(X), _bf16(A2), K, lam)
+    assert (np.abs(t128 - ref16) <= 3e-3 * bound + 1e-30).all()
+
+
+def test_batched_wave_with_small_tiles_matches_oracle(solver):
+    """A wave whose grouped products run on the small tiles (FP32 64 rows,
+    BF16 128 columns) against the oracle's replay, and its BF16 phase
+    against the FP32 solve."""
+    pairs = synth.batch_mixed(count=5, seed=21, n_lo=100, n_hi=400, out_hi=40)
+    try:
+        solver.set_tiles(64, 128)
+        _check_batch(solver, pairs, 0.5, max_outer=20, max_inner=200)
+        dev = [(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)) for g in pairs]
+        o16 = solver.match_batched(dev, params=F.default_params(lam=0.5, precision=F.BF16, refine_iters=30))
+    finally:
+        solver.set_tiles(128, 256)
+    o32 = solver.match_batched(dev, params=F.default_params(lam=0.5))
+    for a, b in zip(o16, o32):
+        assert a.stats.status == 0 and a.stats.lowp_iters >= 1
+        assert abs(a.stats.objective - b.stats.objective) <= 1e-4 * abs(b.stats.objective)
+
+
+def test_autotune_fills_the_table_for_every_reachable_class():
+    s = F.Solver(max_n=1000, max_batch=32)
+    try:
+        t = s.autotune(reps=2)
+        assert t.shape == (F.TUNE_SIZES, F.TUNE_COUNTS, 4)
+        # size classes up to N = 1000 (0..3) and every count class are timed
+        assert (t[:4] > 0).all() and (t[4:] == 0).all()
+        for n in (50, 200, 400, 1000):
+            for c in (1, 3, 10, 32):
+                f, b = s.get_tiles(n, c)
+                assert f in (64, 128) and b in (128, 256)
+                sc = {50: 0, 200: 1, 400: 2, 1000: 3}[n]
+                cc = {1: 0, 3: 1, 10: 2, 32: 3}[c]
+                assert f == (64 if t[sc, cc, 1] < t[sc, cc, 0] else 128)
+                assert b == (128 if t[sc, cc, 3] < t[sc, cc, 2] else 256)
+        pairs = synth.batch_mixed(count=4, seed=23, n_lo=60, n_hi=300, out_hi=30)
+        _check_batch(s, pairs, 0.5, max_outer=15, max_inner=200)
+        with pytest.raises(F.FastPFPError):
+            s.set_tiles(96, 256)
+        with pytest.raises(F.FastPFPError):
+            s.autotune(reps=0)
+    finally:
+        s.close()
