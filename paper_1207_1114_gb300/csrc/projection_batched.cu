@@ -142,30 +142,31 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
     return r;
 }
 
-// One column quad of one row held in registers: Eq. (P1) with the row
-// offset ai and the column sums c (the offset is c_j / N, folded into one
-// FMA with ninvN = -1/N), then Eq. (P2); columns >= N stay zero.  Returns
-// the quad's contribution to the row sum.  Packed f32x2 arithmetic, two
-// lanes per op.
+// One column quad of one row held in registers: Eq. (P1) then Eq. (P2).
+// With t = a_i + b_j the offset P1 adds (a_i = 1/N + s/N^2 - r_i/N per row,
+// b = -c_j/N per column, passed in `b`), max(y + t, 0) = y + max(t, -y)
+// exactly (an FP32 y - y is +0), so the round's change d = max(t, -y) comes
+// out of the update itself and max|dY| costs one three-way max per two
+// entries.  Columns >= N keep y = 0 (d = 0).  Returns the quad's
+// contribution to the row sum and adds the new y to the column partials cp.
+// Packed f32x2 additions, two lanes per op.
 template <bool UPDATE>
-__device__ __forceinline__ float quad_upd(float4& y, float ai, float4 c, float ninvN, int c0, int N, float4& cp,
-                                          float& dmax) {
+__device__ __forceinline__ float quad_upd(float4& y, float ai, float4 b, int c0, int N, float4& cp, float& dmax) {
     if (UPDATE) {
-        const unsigned long long A = pk(ai, ai), NI = pk(ninvN, ninvN);
-        const unsigned long long y01 = pk(y.x, y.y), y23 = pk(y.z, y.w);
-        const float2 u01 = upk(fma2(NI, pk(c.x, c.y), add2(y01, A)));
-        const float2 u23 = upk(fma2(NI, pk(c.z, c.w), add2(y23, A)));
-        float4 z = make_float4(fmaxf(u01.x, 0.f), fmaxf(u01.y, 0.f), fmaxf(u23.x, 0.f), fmaxf(u23.y, 0.f));
+        const unsigned long long A = pk(ai, ai);
+        const float2 t01 = upk(add2(A, pk(b.x, b.y)));
+        const float2 t23 = upk(add2(A, pk(b.z, b.w)));
+        float4 d = make_float4(fmaxf(t01.x, -y.x), fmaxf(t01.y, -y.y), fmaxf(t23.x, -y.z), fmaxf(t23.y, -y.w));
         if (c0 + 4 > N) {
-            if (c0 + 1 >= N) z.y = 0.f;
-            if (c0 + 2 >= N) z.z = 0.f;
-            if (c0 + 3 >= N) z.w = 0.f;
+            if (c0 + 1 >= N) d.y = 0.f;
+            if (c0 + 2 >= N) d.z = 0.f;
+            if (c0 + 3 >= N) d.w = 0.f;
         }
-        const float2 d01 = upk(sub2(pk(z.x, z.y), y01));
-        const float2 d23 = upk(sub2(pk(z.z, z.w), y23));
-        dmax = max3f(dmax, fabsf(d01.x), fabsf(d01.y));
-        dmax = max3f(dmax, fabsf(d23.x), fabsf(d23.y));
-        y = z;
+        dmax = max3f(dmax, fabsf(d.x), fabsf(d.y));
+        dmax = max3f(dmax, fabsf(d.z), fabsf(d.w));
+        const float2 z01 = upk(add2(pk(y.x, y.y), pk(d.x, d.y)));
+        const float2 z23 = upk(add2(pk(y.z, y.w), pk(d.z, d.w)));
+        y = make_float4(z01.x, z01.y, z23.x, z23.y);
     }
     const float2 c01 = upk(add2(pk(cp.x, cp.y), pk(y.x, y.y)));
     const float2 c23 = upk(add2(pk(cp.z, cp.w), pk(y.z, y.w)));
@@ -176,10 +177,10 @@ __device__ __forceinline__ float quad_upd(float4& y, float ai, float4 c, float n
 
 // The same for a quad in shared memory.
 template <bool UPDATE>
-__device__ __forceinline__ float quad_step(float4* __restrict__ p, float ai, float4 c, float ninvN, int c0,
-                                           int N, float4& cp, float& dmax) {
+__device__ __forceinline__ float quad_step(float4* __restrict__ p, float ai, float4 b, int c0, int N, float4& cp,
+                                           float& dmax) {
     float4 y = *p;
-    const float s = quad_upd<UPDATE>(y, ai, c, ninvN, c0, N, cp, dmax);
+    const float s = quad_upd<UPDATE>(y, ai, b, c0, N, cp, dmax);
     if (UPDATE) *p = y;
     return s;
 }
@@ -265,7 +266,7 @@ __device__ __forceinline__ void seg_rows_tmem(uint32_t taddr, int tm, int nrows,
             s[j] = 0.f;
             if (r < nrows && h0) {
                 const float a = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
-                s[j] = quad_upd<UPDATE>(q[j], a, c0v, ninvN, c00, N, cp0, dmax);
+                s[j] = quad_upd<UPDATE>(q[j], a, c0v, c00, N, cp0, dmax);
             }
         }
         if (UPDATE) tm_st16(taddr + 4 * k, q);
@@ -279,7 +280,7 @@ __device__ __forceinline__ void seg_rows_tmem(uint32_t taddr, int tm, int nrows,
         float s0 = 0.f;
         if (r < nrows && h0) {
             const float a = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
-            s0 = quad_upd<UPDATE>(y, a, c0v, ninvN, c00, N, cp0, dmax);
+            s0 = quad_upd<UPDATE>(y, a, c0v, c00, N, cp0, dmax);
         }
         if (UPDATE) tm_st4(taddr + 4 * k, y);
         s0 = warp_sum(s0);
@@ -309,8 +310,8 @@ __device__ __forceinline__ void seg_rows_tmem2(uint32_t taddr, int tm, int nrows
             const int r = mp.grp + RP * (k + j);
             if (r < nrows) {
                 const float a = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
-                if (h0) s[j] += quad_upd<UPDATE>(q[2 * j], a, c0v, ninvN, c00, N, cp0, dmax);
-                if (h1) s[j] += quad_upd<UPDATE>(q[2 * j + 1], a, c1v, ninvN, c01, N, cp1, dmax);
+                if (h0) s[j] += quad_upd<UPDATE>(q[2 * j], a, c0v, c00, N, cp0, dmax);
+                if (h1) s[j] += quad_upd<UPDATE>(q[2 * j + 1], a, c1v, c01, N, cp1, dmax);
             }
         }
         if (UPDATE) tm_st16(taddr + 8 * k, q);
@@ -332,8 +333,8 @@ __device__ __forceinline__ void seg_rows_tmem2(uint32_t taddr, int tm, int nrows
         float s0 = 0.f;
         if (r < nrows) {
             const float a = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
-            if (h0) s0 += quad_upd<UPDATE>(y0, a, c0v, ninvN, c00, N, cp0, dmax);
-            if (h1) s0 += quad_upd<UPDATE>(y1, a, c1v, ninvN, c01, N, cp1, dmax);
+            if (h0) s0 += quad_upd<UPDATE>(y0, a, c0v, c00, N, cp0, dmax);
+            if (h1) s0 += quad_upd<UPDATE>(y1, a, c1v, c01, N, cp1, dmax);
         }
         if (UPDATE) {
             tm_st4(taddr + 8 * k, y0);
@@ -369,12 +370,12 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
         for (int k = 0; k < 4; ++k) a[k] = UPDATE ? fmaf(ninvN, rsum[r + k * RP], abase) : 0.f;
         if (h0) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) s[k] += quad_step<UPDATE>(p + k * stride, a[k], c0v, ninvN, c00, N, cp0, dmax);
+            for (int k = 0; k < 4; ++k) s[k] += quad_step<UPDATE>(p + k * stride, a[k], c0v, c00, N, cp0, dmax);
         }
         if (KQ > 1 && h1) {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                s[k] += quad_step<UPDATE>(p + k * stride + mp.QP, a[k], c1v, ninvN, c01, N, cp1, dmax);
+                s[k] += quad_step<UPDATE>(p + k * stride + mp.QP, a[k], c1v, c01, N, cp1, dmax);
         }
         const float z = sum4_rows(s, lane);
         if ((lane & 7) == 0) rowpart[(size_t)(r + (2 * (lane >> 4) + ((lane >> 3) & 1)) * RP) * rps] = z;
@@ -384,12 +385,12 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
         const float a1 = UPDATE ? fmaf(ninvN, rsum[r + RP], abase) : 0.f;
         float s0 = 0.f, s1 = 0.f;
         if (h0) {
-            s0 += quad_step<UPDATE>(p, a0, c0v, ninvN, c00, N, cp0, dmax);
-            s1 += quad_step<UPDATE>(p + stride, a1, c0v, ninvN, c00, N, cp0, dmax);
+            s0 += quad_step<UPDATE>(p, a0, c0v, c00, N, cp0, dmax);
+            s1 += quad_step<UPDATE>(p + stride, a1, c0v, c00, N, cp0, dmax);
         }
         if (KQ > 1 && h1) {
-            s0 += quad_step<UPDATE>(p + mp.QP, a0, c1v, ninvN, c01, N, cp1, dmax);
-            s1 += quad_step<UPDATE>(p + stride + mp.QP, a1, c1v, ninvN, c01, N, cp1, dmax);
+            s0 += quad_step<UPDATE>(p + mp.QP, a0, c1v, c01, N, cp1, dmax);
+            s1 += quad_step<UPDATE>(p + stride + mp.QP, a1, c1v, c01, N, cp1, dmax);
         }
         // both rows' warp sums in five shuffles: the lower half-warp folds
         // row r, the upper half row r + RP
@@ -406,8 +407,8 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
     if (r < nrows) {
         const float a0 = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
         float s0 = 0.f;
-        if (h0) s0 += quad_step<UPDATE>(p, a0, c0v, ninvN, c00, N, cp0, dmax);
-        if (KQ > 1 && h1) s0 += quad_step<UPDATE>(p + mp.QP, a0, c1v, ninvN, c01, N, cp1, dmax);
+        if (h0) s0 += quad_step<UPDATE>(p, a0, c0v, c00, N, cp0, dmax);
+        if (KQ > 1 && h1) s0 += quad_step<UPDATE>(p + mp.QP, a0, c1v, c01, N, cp1, dmax);
         s0 = warp_sum(s0);
         if (lane == 0) rowpart[(size_t)r * rps] = s0;
     }
@@ -565,11 +566,14 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             const int N = pr.N, Q = pr.ldy >> 2;
             const Map mp = make_map(sg.qpg, sg.rpkq, tid);
             const bool in_grp = mp.grp < mp.RP;
+            // b = -c_j / N of this thread's column quads (the column term of P1)
             float4 c0v = make_float4(0.f, 0.f, 0.f, 0.f), c1v = c0v;
             if (UPDATE && in_grp) {
                 const float4* cN = reinterpret_cast<const float4*>(S.cN + sg.coff);
-                if (mp.q0 < Q) c0v = cN[mp.q0];
-                if (mp.kq > 1 && mp.q0 + mp.QP < Q) c1v = cN[mp.q0 + mp.QP];
+                const float ni = -1.0f / (float)N;
+                auto scale = [ni](float4 v) { return make_float4(ni * v.x, ni * v.y, ni * v.z, ni * v.w); };
+                if (mp.q0 < Q) c0v = scale(cN[mp.q0]);
+                if (mp.kq > 1 && mp.q0 + mp.QP < Q) c1v = scale(cN[mp.q0 + mp.QP]);
             }
             float4 cp0 = make_float4(0.f, 0.f, 0.f, 0.f), cp1 = cp0;
             float dmax = 0.f;
