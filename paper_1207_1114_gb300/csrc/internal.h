@@ -109,7 +109,10 @@ __host__ __device__ inline PdbShape pdb_shape(int ldy, int nthr) {
         const int qpg = ((Q + kq - 1) / kq + 31) & ~31;
         if (qpg > nthr) continue;
         const int rp = nthr / qpg;
-        if (best.kq == 0 || rp * best.kq > best.rp * kq) best = PdbShape{kq, qpg, rp};
+        // the layout that keeps more threads busy; on a tie two quads per
+        // thread, whose per-row work (row offset, row-sum shuffles) then
+        // serves twice the entries
+        if (best.kq == 0 || rp * best.kq >= best.rp * kq) best = PdbShape{kq, qpg, rp};
     }
     return best;   // kq == 0: rows too wide for one CTA (more than 2 * nthr quads)
 }

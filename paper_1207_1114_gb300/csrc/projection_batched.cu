@@ -108,6 +108,10 @@ __device__ __forceinline__ Map make_map(int qpg, int rpkq, int tid) {
     return m;
 }
 
+// The column term of P1 on padding columns: far below any offset a_i, so
+// their update max(a_i - kPadB, -0) is -0 (finite: no infinity enters).
+constexpr float kPadB = 1.0e30f;
+
 // Two-lane FP32 arithmetic (sm_100 packed f32x2): one instruction updates
 // two floats held in a register pair.
 __device__ __forceinline__ unsigned long long pk(float a, float b) {
@@ -125,17 +129,6 @@ __device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigne
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
-__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
-    unsigned long long r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
-                                                   unsigned long long c) {
-    unsigned long long r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
 __device__ __forceinline__ float max3f(float a, float b, float c) {
     float r;
     asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
@@ -147,21 +140,19 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
 // b = -c_j/N per column, passed in `b`), max(y + t, 0) = y + max(t, -y)
 // exactly (an FP32 y - y is +0), so the round's change d = max(t, -y) comes
 // out of the update itself and max|dY| costs one three-way max per two
-// entries.  Columns >= N keep y = 0 (d = 0).  Returns the quad's
-// contribution to the row sum and adds the new y to the column partials cp.
-// Packed f32x2 additions, two lanes per op.
+// entries.  Padding columns (>= N) hold y = 0 and b = -kPadB, so t is
+// hugely negative there and d = max(t, -0) = -0: they stay zero with no
+// test in the loop.  Returns the quad's contribution to the row sum and adds
+// the new y to the column partials cp.  Packed f32x2 additions, two lanes
+// per op.
 template <bool UPDATE>
-__device__ __forceinline__ float quad_upd(float4& y, float ai, float4 b, int c0, int N, float4& cp, float& dmax) {
+__device__ __forceinline__ float quad_upd(float4& y, float ai, float4 b, float4& cp, float& dmax) {
     if (UPDATE) {
         const unsigned long long A = pk(ai, ai);
         const float2 t01 = upk(add2(A, pk(b.x, b.y)));
         const float2 t23 = upk(add2(A, pk(b.z, b.w)));
-        float4 d = make_float4(fmaxf(t01.x, -y.x), fmaxf(t01.y, -y.y), fmaxf(t23.x, -y.z), fmaxf(t23.y, -y.w));
-        if (c0 + 4 > N) {
-            if (c0 + 1 >= N) d.y = 0.f;
-            if (c0 + 2 >= N) d.z = 0.f;
-            if (c0 + 3 >= N) d.w = 0.f;
-        }
+        const float4 d =
+            make_float4(fmaxf(t01.x, -y.x), fmaxf(t01.y, -y.y), fmaxf(t23.x, -y.z), fmaxf(t23.y, -y.w));
         dmax = max3f(dmax, fabsf(d.x), fabsf(d.y));
         dmax = max3f(dmax, fabsf(d.z), fabsf(d.w));
         const float2 z01 = upk(add2(pk(y.x, y.y), pk(d.x, d.y)));
@@ -177,10 +168,9 @@ __device__ __forceinline__ float quad_upd(float4& y, float ai, float4 b, int c0,
 
 // The same for a quad in shared memory.
 template <bool UPDATE>
-__device__ __forceinline__ float quad_step(float4* __restrict__ p, float ai, float4 b, int c0, int N, float4& cp,
-                                           float& dmax) {
+__device__ __forceinline__ float quad_step(float4* __restrict__ p, float ai, float4 b, float4& cp, float& dmax) {
     float4 y = *p;
-    const float s = quad_upd<UPDATE>(y, ai, b, c0, N, cp, dmax);
+    const float s = quad_upd<UPDATE>(y, ai, b, cp, dmax);
     if (UPDATE) *p = y;
     return s;
 }
@@ -253,7 +243,6 @@ __device__ __forceinline__ void seg_rows_tmem(uint32_t taddr, int tm, int nrows,
                                               float* __restrict__ rowpart, int rps, float4 c0v, float ninvN,
                                               float4& cp0, float& dmax) {
     const bool h0 = mp.q0 < Q;
-    const int c00 = 4 * mp.q0;
     const int RP = mp.RP;
     int k = 0;
     for (; k + 3 < tm; k += 4) {
@@ -266,7 +255,7 @@ __device__ __forceinline__ void seg_rows_tmem(uint32_t taddr, int tm, int nrows,
             s[j] = 0.f;
             if (r < nrows && h0) {
                 const float a = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
-                s[j] = quad_upd<UPDATE>(q[j], a, c0v, c00, N, cp0, dmax);
+                s[j] = quad_upd<UPDATE>(q[j], a, c0v, cp0, dmax);
             }
         }
         if (UPDATE) tm_st16(taddr + 4 * k, q);
@@ -280,7 +269,7 @@ __device__ __forceinline__ void seg_rows_tmem(uint32_t taddr, int tm, int nrows,
         float s0 = 0.f;
         if (r < nrows && h0) {
             const float a = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
-            s0 = quad_upd<UPDATE>(y, a, c0v, c00, N, cp0, dmax);
+            s0 = quad_upd<UPDATE>(y, a, c0v, cp0, dmax);
         }
         if (UPDATE) tm_st4(taddr + 4 * k, y);
         s0 = warp_sum(s0);
@@ -298,7 +287,6 @@ __device__ __forceinline__ void seg_rows_tmem2(uint32_t taddr, int tm, int nrows
                                                float ninvN, float4& cp0, float4& cp1, float& dmax) {
     const int q1 = mp.q0 + mp.QP;
     const bool h0 = mp.q0 < Q, h1 = q1 < Q;
-    const int c00 = 4 * mp.q0, c01 = 4 * q1;
     const int RP = mp.RP;
     int k = 0;
     for (; k + 1 < tm; k += 2) {
@@ -310,8 +298,8 @@ __device__ __forceinline__ void seg_rows_tmem2(uint32_t taddr, int tm, int nrows
             const int r = mp.grp + RP * (k + j);
             if (r < nrows) {
                 const float a = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
-                if (h0) s[j] += quad_upd<UPDATE>(q[2 * j], a, c0v, c00, N, cp0, dmax);
-                if (h1) s[j] += quad_upd<UPDATE>(q[2 * j + 1], a, c1v, c01, N, cp1, dmax);
+                if (h0) s[j] += quad_upd<UPDATE>(q[2 * j], a, c0v, cp0, dmax);
+                if (h1) s[j] += quad_upd<UPDATE>(q[2 * j + 1], a, c1v, cp1, dmax);
             }
         }
         if (UPDATE) tm_st16(taddr + 8 * k, q);
@@ -333,8 +321,8 @@ __device__ __forceinline__ void seg_rows_tmem2(uint32_t taddr, int tm, int nrows
         float s0 = 0.f;
         if (r < nrows) {
             const float a = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
-            if (h0) s0 += quad_upd<UPDATE>(y0, a, c0v, c00, N, cp0, dmax);
-            if (h1) s0 += quad_upd<UPDATE>(y1, a, c1v, c01, N, cp1, dmax);
+            if (h0) s0 += quad_upd<UPDATE>(y0, a, c0v, cp0, dmax);
+            if (h1) s0 += quad_upd<UPDATE>(y1, a, c1v, cp1, dmax);
         }
         if (UPDATE) {
             tm_st4(taddr + 8 * k, y0);
@@ -359,7 +347,6 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
     const bool h0 = mp.q0 < Q;
     const int q1 = mp.q0 + mp.QP;   // the second quad (kq = 2)
     const bool h1 = KQ > 1 && q1 < Q;
-    const int c00 = 4 * mp.q0, c01 = 4 * q1;
     const int RP = mp.RP;
     const int stride = RP * Q;
     int r = mp.grp;
@@ -368,14 +355,24 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
         float a[4], s[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < 4; ++k) a[k] = UPDATE ? fmaf(ninvN, rsum[r + k * RP], abase) : 0.f;
-        if (h0) {
+        // per column quad, every load of the four rows before any store (the
+        // rows are distinct, which the compiler cannot prove), so their
+        // latencies overlap
 #pragma unroll
-            for (int k = 0; k < 4; ++k) s[k] += quad_step<UPDATE>(p + k * stride, a[k], c0v, c00, N, cp0, dmax);
-        }
-        if (KQ > 1 && h1) {
+        for (int j = 0; j < KQ; ++j) {
+            if (!(j == 0 ? h0 : h1)) continue;
+            float4* pj = p + j * mp.QP;
+            const float4 cv = j == 0 ? c0v : c1v;
+            float4& cpj = j == 0 ? cp0 : cp1;
+            float4 y[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                s[k] += quad_step<UPDATE>(p + k * stride + mp.QP, a[k], c1v, c01, N, cp1, dmax);
+            for (int k = 0; k < 4; ++k) y[k] = pj[k * stride];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s[k] += quad_upd<UPDATE>(y[k], a[k], cv, cpj, dmax);
+            if (UPDATE) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) pj[k * stride] = y[k];
+            }
         }
         const float z = sum4_rows(s, lane);
         if ((lane & 7) == 0) rowpart[(size_t)(r + (2 * (lane >> 4) + ((lane >> 3) & 1)) * RP) * rps] = z;
@@ -385,12 +382,12 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
         const float a1 = UPDATE ? fmaf(ninvN, rsum[r + RP], abase) : 0.f;
         float s0 = 0.f, s1 = 0.f;
         if (h0) {
-            s0 += quad_step<UPDATE>(p, a0, c0v, c00, N, cp0, dmax);
-            s1 += quad_step<UPDATE>(p + stride, a1, c0v, c00, N, cp0, dmax);
+            s0 += quad_step<UPDATE>(p, a0, c0v, cp0, dmax);
+            s1 += quad_step<UPDATE>(p + stride, a1, c0v, cp0, dmax);
         }
         if (KQ > 1 && h1) {
-            s0 += quad_step<UPDATE>(p + mp.QP, a0, c1v, c01, N, cp1, dmax);
-            s1 += quad_step<UPDATE>(p + stride + mp.QP, a1, c1v, c01, N, cp1, dmax);
+            s0 += quad_step<UPDATE>(p + mp.QP, a0, c1v, cp1, dmax);
+            s1 += quad_step<UPDATE>(p + stride + mp.QP, a1, c1v, cp1, dmax);
         }
         // both rows' warp sums in five shuffles: the lower half-warp folds
         // row r, the upper half row r + RP
@@ -407,8 +404,8 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
     if (r < nrows) {
         const float a0 = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
         float s0 = 0.f;
-        if (h0) s0 += quad_step<UPDATE>(p, a0, c0v, c00, N, cp0, dmax);
-        if (KQ > 1 && h1) s0 += quad_step<UPDATE>(p + mp.QP, a0, c1v, c01, N, cp1, dmax);
+        if (h0) s0 += quad_step<UPDATE>(p, a0, c0v, cp0, dmax);
+        if (KQ > 1 && h1) s0 += quad_step<UPDATE>(p + mp.QP, a0, c1v, cp1, dmax);
         s0 = warp_sum(s0);
         if (lane == 0) rowpart[(size_t)r * rps] = s0;
     }
@@ -566,14 +563,18 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             const int N = pr.N, Q = pr.ldy >> 2;
             const Map mp = make_map(sg.qpg, sg.rpkq, tid);
             const bool in_grp = mp.grp < mp.RP;
-            // b = -c_j / N of this thread's column quads (the column term of P1)
+            // b = -c_j / N of this thread's column quads (the column term of
+            // P1), -kPadB on padding columns
             float4 c0v = make_float4(0.f, 0.f, 0.f, 0.f), c1v = c0v;
             if (UPDATE && in_grp) {
                 const float4* cN = reinterpret_cast<const float4*>(S.cN + sg.coff);
                 const float ni = -1.0f / (float)N;
-                auto scale = [ni](float4 v) { return make_float4(ni * v.x, ni * v.y, ni * v.z, ni * v.w); };
-                if (mp.q0 < Q) c0v = scale(cN[mp.q0]);
-                if (mp.kq > 1 && mp.q0 + mp.QP < Q) c1v = scale(cN[mp.q0 + mp.QP]);
+                auto scale = [ni, N](float4 v, int c) {
+                    return make_float4(ni * v.x, c + 1 < N ? ni * v.y : -kPadB, c + 2 < N ? ni * v.z : -kPadB,
+                                       c + 3 < N ? ni * v.w : -kPadB);
+                };
+                if (mp.q0 < Q) c0v = scale(cN[mp.q0], 4 * mp.q0);
+                if (mp.kq > 1 && mp.q0 + mp.QP < Q) c1v = scale(cN[mp.q0 + mp.QP], 4 * (mp.q0 + mp.QP));
             }
             float4 cp0 = make_float4(0.f, 0.f, 0.f, 0.f), cp1 = cp0;
             float dmax = 0.f;
