@@ -174,7 +174,8 @@ def make_pairs(workload: str, rank: int, batch: int):
 def params(F, lam, profile=0, precision="fp32", loop_mode=0):
     """The workload's parameters.  bf16: tensor-core products until
     max|dX| < 1e-3, then FP32 iterations (at most 30) to convergence."""
-    extra = dict(precision=F.BF16, refine_iters=30, switch_tol=1e-3) if precision == "bf16" else {}
+    low = {"bf16": F.BF16, "fp8": F.FP8}.get(precision)
+    extra = dict(precision=low, refine_iters=30, switch_tol=1e-3) if low is not None else {}
     return F.default_params(lam=lam, profile=profile, loop_mode=loop_mode, **SOLVER, **extra)
 
 
@@ -325,8 +326,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-budget", type=float, default=10.0, dest="ref_budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
-                    help="gradient products: plain FP32, or BF16 tensor cores + FP32 refinement")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"],
+                    help="gradient products: plain FP32, or BF16 / E4M3 tensor cores + FP32 refinement")
     ap.add_argument("--init", default="uniform", choices=["uniform", "learned"],
                     help="X(0): the paper's uniform start, or the learned warm start (trained first, "
                          "on --train-pairs pairs solved by the plain solver)")
@@ -527,7 +528,7 @@ def main():
             "metric": wl["metric"], "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "bf16+f32", "data": "synthetic",
+            "dtype": {"fp32": "f32", "bf16": "bf16+f32", "fp8": "e4m3+f32"}[args.precision], "data": "synthetic",
             "config": dict(workload=args.workload, **cfg, **SOLVER, pairs_per_step=args.batch,
                            precision=args.precision, loop=args.loop, init=args.init,
                            gemm_tiles=dict(tiles, source="default" if args.no_autotune else "autotuned"),

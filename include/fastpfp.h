@@ -51,7 +51,14 @@ extern "C" {
 #define FASTPFP_MAX_N 16384          /* largest graph a handle can be created for         */
 #define FASTPFP_MAX_K 256            /* largest attribute dimension k                     */
 
-enum { FASTPFP_FP32 = 0, FASTPFP_BF16 = 1 };
+/* Precision of the A X A' products (FP32 accumulation throughout).  BF16:
+ * both operands of both products rounded to BF16.  FP8: both operands E4M3
+ * (round to nearest even, saturating) with one power-of-two scale per
+ * operand row, chosen so the row's largest magnitude maps to at most 448,
+ * and both scales applied to the FP32 accumulator: A and A' are quantised
+ * once per solve, X^T (through a BF16 copy) and T = A X (through its BF16
+ * result) before each product. */
+enum { FASTPFP_FP32 = 0, FASTPFP_BF16 = 1, FASTPFP_FP8 = 2 };
 
 typedef struct fastpfp_s* fastpfp_t;
 
@@ -66,9 +73,13 @@ typedef struct {
     double tol_inner;      /* eps_2: stop P_D when max|Y(u+1) - Y(u)| < eps_2 (Section 5)     */
     int max_outer;         /* I_0: at most this many outer iterations, >= 1                   */
     int max_inner;         /* I_1: at most this many P1/P2 rounds per outer iteration, >= 1   */
-    int precision;         /* FASTPFP_FP32 or FASTPFP_BF16 for the A X A' products            */
-    int refine_iters;      /* BF16 only: FP32 outer iterations run after the BF16 phase        */
-    double switch_tol;     /* BF16 only: the BF16 phase ends once max|dX| < switch_tol         */
+    int precision;         /* FASTPFP_FP32, FASTPFP_BF16 or FASTPFP_FP8 for the A X A' products */
+    int refine_iters;      /* BF16 / FP8: FP32 outer iterations run after the low-precision
+                              phase                                                          */
+    double switch_tol;     /* BF16 / FP8: the low-precision phase ends once max|dX| <
+                              switch_tol, or once max|dX| shrinks by less than half in an
+                              iteration (from its fourth iteration on: the products' rounding
+                              noise is near)                                                 */
     int normalize_max;     /* 1: X <- X / max(X) after every outer iteration (Algorithm 1)     */
     int slack_policy;      /* 0: slack columns of Y carry over between outer iterations
                               (Algorithm 1 initialises Y once); 1: reset them to 0            */
@@ -197,7 +208,8 @@ int fastpfp_last_trace(fastpfp_t h, int pair, int* inner_counts, double* deltas,
  *   Y[i, j] = sum_l (sum_q A[i,q] X[q,l]) A2[l,j] + lambda * K[i,j]
  * for i < N, j < m; Y has leading dimension ldy >= m.  A is N x N, X is
  * N x m, A2 is m x m, K is N x m (nullable when lambda == 0).  precision
- * selects FP32 or BF16 products (FP32 accumulation).  Device pointers;
+ * selects FP32, BF16 or FP8 products (FP32 accumulation; FP8 quantises as
+ * the solve does, T through a BF16 copy).  Device pointers;
  * asynchronous on `stream`.  Errors: ERR_ARG, ERR_SIZE, ERR_CUDA. */
 int fastpfp_gradient(fastpfp_t h, void* stream, const float* A, const float* X, const float* A2,
                      const float* K, float lambda, int N, int m, float* Y, int ldy, int precision);

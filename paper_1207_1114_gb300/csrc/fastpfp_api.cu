@@ -46,6 +46,10 @@ constexpr int kProfEvents = 2 * kProfIters + 3;   // iteration boundaries + disc
 constexpr int kChunk = 4;                         // outer iterations enqueued between checks
 constexpr size_t kTraceBytes = (size_t)kMaxOuterTrace * (sizeof(int) + sizeof(double));
 constexpr long long kMinElemsPerCta = 8192;       // smallest band worth a CTA of its own
+// Waves with at least this many rows per CTA lay out tied pairs with two
+// column quads per thread (pdb_shape): measured +7 % at 112 rows per CTA
+// (17 pairs of n = 1000), -25 % at 7 (one pair of n = 1000).
+constexpr int kTwoQuadRowsPerCta = 32;
 // Two interleaved pair groups per wave (one group's barrier hidden behind the
 // other's round).  Measured slower on GB300 at n = 1000 (17.3 vs 11.8 us per
 // 7-pair round): a round's fixed cost is serial latency, not barrier waiting.
@@ -53,6 +57,7 @@ constexpr bool kInterleaveGroups = false;
 
 inline int round4(int x) { return (x + 3) & ~3; }
 inline int round8(int x) { return (x + 7) & ~7; }   // BF16 rows: 16-byte TMA strides
+inline int round16(int x) { return (x + 15) & ~15; }   // E4M3 rows: 16-byte TMA strides
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Per-pair device scratch.
@@ -70,6 +75,10 @@ struct Slot {
     // 16-byte-row copies of A and A' for the FP32 products when the caller's
     // rows are not 16-byte aligned
     float *A32, *A232;
+    // FP8 products: E4M3 copies of A, A', X^T and T (leading dimension
+    // round16 of the row length) and their per-row scales
+    uint8_t *qA, *qA2, *qXt, *qT;
+    float *scA, *scA2, *scX, *scT;
 };
 
 }  // namespace
@@ -143,7 +152,8 @@ bool params_ok(const fastpfp_params* p) {
     if (p->max_outer < 1 || p->max_inner < 1) return false;
     if (p->max_outer > kMaxOuterTrace) return false;
     if (!(p->tol_outer >= 0.0) || !(p->tol_inner >= 0.0)) return false;
-    if (p->precision != FASTPFP_FP32 && p->precision != FASTPFP_BF16) return false;
+    if (p->precision != FASTPFP_FP32 && p->precision != FASTPFP_BF16 && p->precision != FASTPFP_FP8)
+        return false;
     if (p->refine_iters < 0) return false;
     if (p->loop_mode != 0 && p->loop_mode != 1) return false;
     return true;
@@ -213,19 +223,19 @@ inline const float* f32_operand(const float* A, int n, float* padded, int* ld) {
 int enqueue_setup(const Slot& sl, cudaStream_t s, const Problem& q, const fastpfp_params* p,
                   int ld) {
     const int ldy = round4(q.N), ldx = round4(q.m);
-    const bool bf16 = p->precision == FASTPFP_BF16;
+    const bool lowp = p->precision != FASTPFP_FP32;   // a BF16 or FP8 phase
     FP_CUDA(cudaMemsetAsync(sl.ctrl, 0, kCtrlHeader, s));
     FP_CUDA(cudaMemsetAsync(sl.colbuf, 0, 3 * (size_t)ld * sizeof(float), s));
     FP_CUDA(cudaMemsetAsync(sl.sbuf, 0, 3 * sizeof(double), s));
     FP_CUDA(cudaMemsetAsync(sl.dbuf, 0, 3 * sizeof(unsigned), s));
     FP_CUDA(cudaMemsetAsync(sl.Y, 0, (size_t)q.N * ldy * sizeof(float), s));
-    FP_CUDA(init_ctrl(sl.ctrl, bf16 ? 1 : 0, s));
+    FP_CUDA(init_ctrl(sl.ctrl, lowp ? 1 : 0, s));
     int nl = 2;
     if (q.k > 0) {
         FP_CUDA(affinity(q.B, q.B2, q.N, q.m, q.k, sl.K, ldx, s));
         ++nl;
     }
-    FP_CUDA(init_x(sl.X, q.N, q.m, ldx, q.X0, q.transposed, bf16 ? sl.Xt16 : nullptr, round8(q.N), s));
+    FP_CUDA(init_x(sl.X, q.N, q.m, ldx, q.X0, q.transposed, lowp ? sl.Xt16 : nullptr, round8(q.N), s));
     // 16-byte rows of A and A' for the FP32 products (only when the caller's are not)
     if (!rows16(q.A, q.N))
         FP_CUDA(cudaMemcpy2DAsync(sl.A32, (size_t)round4(q.N) * 4, q.A, (size_t)q.N * 4, (size_t)q.N * 4, q.N,
@@ -233,11 +243,19 @@ int enqueue_setup(const Slot& sl, cudaStream_t s, const Problem& q, const fastpf
     if (!rows16(q.A2, q.m))
         FP_CUDA(cudaMemcpy2DAsync(sl.A232, (size_t)round4(q.m) * 4, q.A2, (size_t)q.m * 4, (size_t)q.m * 4, q.m,
                                   cudaMemcpyDeviceToDevice, s));
-    if (bf16) {
+    if (p->precision == FASTPFP_BF16) {
         // BF16 operand copies of A and A' for the tensor-core products
         FP_CUDA(to_bf16(q.A, q.N, q.N, q.N, sl.A16, round8(q.N), s));
         FP_CUDA(to_bf16(q.A2, q.m, q.m, q.m, sl.A216, round8(q.m), s));
         nl += 2;
+    } else if (p->precision == FASTPFP_FP8) {
+        // E4M3 copies of A and A' with per-row scales, once per solve
+        QuantGroup g{};
+        g.count = 2;
+        g.q[0] = QuantRows{q.A, 0, q.N, q.N, q.N, sl.qA, round16(q.N), sl.scA, nullptr};
+        g.q[1] = QuantRows{q.A2, 0, q.m, q.m, q.m, sl.qA2, round16(q.m), sl.scA2, nullptr};
+        FP_CUDA(quant_fp8_group(g, s));
+        ++nl;
     }
     return nl;
 }
@@ -270,17 +288,25 @@ int enqueue_gradient(const Slot& sl, cudaStream_t s, const Problem& q, const fas
 // The same gradient on the tensor cores for pairs in slots 0..count-1: one
 // grouped launch for T = A X (BF16 out) and one for Y = T A' + lambda K (FP32
 // out), each covering up to kTcMaxGroup pairs.  The tensor maps describe the
-// slots' BF16 buffers and are built once per solve.
+// slots' BF16 buffers and are built once per solve.  FP8 runs the same two
+// launches on E4M3 copies: X^T (written in BF16 by the blend) and T are
+// quantised per row just before the product that reads them (qx, qt), A and
+// A' once at set-up, and the epilogues scale by the two operands' row scales.
 struct TcPlan {
     std::vector<TcGroup> g1, g2;
+    std::vector<QuantGroup> qx, qt;
 };
 
 bool plan_tc(fastpfp_t h, const Problem* qs, int count, const fastpfp_params* p, TcPlan* plan,
              const int* slot_of = nullptr) {
     plan->g1.clear();
     plan->g2.clear();
+    plan->qx.clear();
+    plan->qt.clear();
+    const bool fp8 = p->precision == FASTPFP_FP8;
     for (int b = 0; b < count; b += kTcMaxGroup) {
         TcGroup a{}, c{};
+        QuantGroup qx{}, qt{};
         const int n = std::min(kTcMaxGroup, count - b);
         int nmax = 0;
         for (int i = 0; i < n; ++i) nmax = std::max(nmax, qs[b + i].N);
@@ -289,10 +315,27 @@ bool plan_tc(fastpfp_t h, const Problem* qs, int count, const fastpfp_params* p,
         a.mode = kTcOutBf16;
         c.mode = kTcOutF32;
         a.bn = c.bn = bn;
+        a.fp8 = c.fp8 = fp8 ? 1 : 0;
+        qx.count = qt.count = fp8 ? n : 0;
         for (int i = 0; i < n; ++i) {
             const Problem& q = qs[b + i];
             const Slot& sl = h->slots[slot_of ? slot_of[b + i] : b + i];
             const int l16N = round8(q.N), l16m = round8(q.m);
+            if (fp8) {
+                const int l8N = round16(q.N), l8m = round16(q.m);
+                if (!tc_make_map(&a.map_a[i], sl.qA, q.N, q.N, l8N, kTcTileM, true) ||
+                    !tc_make_map(&a.map_b[i], sl.qXt, q.m, q.N, l8N, bn, true) ||
+                    !tc_make_map(&c.map_a[i], sl.qT, q.N, q.m, l8m, kTcTileM, true) ||
+                    !tc_make_map(&c.map_b[i], sl.qA2, q.m, q.m, l8m, bn, true))
+                    return false;
+                qx.q[i] = QuantRows{sl.Xt16, 1, q.m, q.N, l16N, sl.qXt, l8N, sl.scX, sl.ctrl};
+                qt.q[i] = QuantRows{sl.T16, 1, q.N, q.m, l16m, sl.qT, l8m, sl.scT, sl.ctrl};
+                a.prob[i] = TcProblem{q.N, q.m, q.N, sl.T16, l16m, nullptr, 0, 0.f, sl.ctrl, &sl.ctrl->error,
+                                      sl.scA, sl.scX};
+                c.prob[i] = TcProblem{q.N, q.m, q.m, sl.Y, round4(q.N), q.k ? sl.K : nullptr, round4(q.m),
+                                      q.k ? (float)p->lambda : 0.f, sl.ctrl, &sl.ctrl->error, sl.scT, sl.scA2};
+                continue;
+            }
             if (!tc_make_map(&a.map_a[i], sl.A16, q.N, q.N, l16N, kTcTileM) ||
                 !tc_make_map(&a.map_b[i], sl.Xt16, q.m, q.N, l16N, bn) ||
                 !tc_make_map(&c.map_a[i], sl.T16, q.N, q.m, l16m, kTcTileM) ||
@@ -304,14 +347,20 @@ bool plan_tc(fastpfp_t h, const Problem* qs, int count, const fastpfp_params* p,
         }
         plan->g1.push_back(a);
         plan->g2.push_back(c);
+        if (fp8) {
+            plan->qx.push_back(qx);
+            plan->qt.push_back(qt);
+        }
     }
     return true;
 }
 
 int enqueue_tc(const TcPlan& plan, cudaStream_t s) {
+    for (const QuantGroup& g : plan.qx) FP_CUDA(quant_fp8_group(g, s));
     for (const TcGroup& g : plan.g1) FP_CUDA(tc_gemm(g, s));
+    for (const QuantGroup& g : plan.qt) FP_CUDA(quant_fp8_group(g, s));
     for (const TcGroup& g : plan.g2) FP_CUDA(tc_gemm(g, s));
-    return (int)(plan.g1.size() + plan.g2.size());
+    return (int)(plan.g1.size() + plan.g2.size() + plan.qx.size() + plan.qt.size());
 }
 
 // Discretisation, objective, caller-orientation outputs, control header.
@@ -429,9 +478,9 @@ int enqueue_single(fastpfp_t h, cudaStream_t s, const Slot& sl, const Problem& q
                    const fastpfp_params* p, Ctrl* host_slot) {
     const int N = q.N, m = q.m;
     const int ldy = round4(N), ldx = round4(m);
-    const bool bf16 = p->precision == FASTPFP_BF16;
+    const bool lowp = p->precision != FASTPFP_FP32;   // a BF16 or FP8 phase
     TcPlan tc;
-    if (bf16 && !plan_tc(h, &q, 1, p, &tc)) return FASTPFP_ERR_UNSUPPORTED;
+    if (lowp && !plan_tc(h, &q, 1, p, &tc)) return FASTPFP_ERR_UNSUPPORTED;
     int nl = enqueue_setup(sl, s, q, p, h->ld);
     if (nl < 0) return nl;
     PdLaunch L;
@@ -443,7 +492,7 @@ int enqueue_single(fastpfp_t h, cudaStream_t s, const Slot& sl, const Problem& q
     P.m = m;
     P.X = sl.X;
     P.ldx = ldx;
-    P.Xt16 = bf16 ? sl.Xt16 : nullptr;
+    P.Xt16 = lowp ? sl.Xt16 : nullptr;
     P.ldxt = round8(N);
     P.alpha = p->alpha;
     P.normalize = p->normalize_max ? 1 : 0;
@@ -468,7 +517,7 @@ int enqueue_single(fastpfp_t h, cudaStream_t s, const Slot& sl, const Problem& q
         const bool pt = prof && t < kProfIters;
         if (pt && t == 0) FP_CUDA(cudaEventRecord(h->ev[0], st));
         int g = 0;
-        if (bf16) {
+        if (lowp) {
             g = enqueue_tc(tc, st);
             if (g < 0) return g;
         }
@@ -585,7 +634,7 @@ int cut_rows(const std::vector<Problem>& qs, int first, int count, long long C, 
 // band[0..used] holds the row boundaries, band[used..G] = total rows.
 // Returns the number of bands used.
 int split_group(const std::vector<Problem>& qs, int first, int count, int G, long long seg_cost,
-                int* band, std::vector<BandStats>& st) {
+                int two_quad_ties, int* band, std::vector<BandStats>& st) {
     long long lo = 1, hi = 0;
     int rows = 0;
     for (int i = 0; i < count; ++i) {
@@ -617,7 +666,7 @@ int split_group(const std::vector<Problem>& qs, int first, int count, int G, lon
             if (lo >= hi) continue;
             const int nr = hi - lo;
             int ntm = 0, next = 0;
-            pdb_tmem_rows(nr, ldy, kPdbThreads, tcol[bb], &ntm, &next);
+            pdb_tmem_rows(nr, ldy, kPdbThreads, tcol[bb], &ntm, &next, two_quad_ties);
             tcol[bb] = next;
             st[bb].rows += nr;
             st[bb].cols += ldy;
@@ -651,15 +700,18 @@ bool plan_bands(const std::vector<Problem>& qs, int first, int count, int num_sm
     }
     const long long gl = (E + kMinElemsPerCta - 1) / kMinElemsPerCta;
     const int Gmax = (int)std::min<long long>(num_sms, std::max<long long>(1, gl));
+    long long rows = 0;
+    for (int i = 0; i < count; ++i) rows += qs[first + i].N;
+    const int t2 = rows >= (long long)kTwoQuadRowsPerCta * Gmax ? 1 : 0;
     for (const long long seg_cost : {kSegCost, 0ll}) {
         std::vector<int> b0(Gmax + 1), b1(Gmax + 1);
         std::vector<BandStats> s0, s1;
-        const int u0 = split_group(qs, first, split, Gmax, seg_cost, b0.data(), s0);
-        const int u1 = split_group(qs, first + split, count - split, Gmax, seg_cost, b1.data(), s1);
+        const int u0 = split_group(qs, first, split, Gmax, seg_cost, t2, b0.data(), s0);
+        const int u1 = split_group(qs, first + split, count - split, Gmax, seg_cost, t2, b1.data(), s1);
         const int G = std::max(1, std::max(u0, u1));
-        PdbLayout L{0, 0, 0, 1};
+        PdbLayout L{0, 0, 0, 1, t2};
         for (int i = 0; i < count; ++i)
-            L.rp_stride = std::max(L.rp_stride, pdb_row_warps(round4(qs[first + i].N), kPdbThreads));
+            L.rp_stride = std::max(L.rp_stride, pdb_row_warps(round4(qs[first + i].N), kPdbThreads, t2));
         bool ok = true;
         for (int b = 0; b < G; ++b) {
             L.max_band_rows = std::max(L.max_band_rows, s0[b].rows + s1[b].rows);
@@ -710,7 +762,7 @@ struct Member {
 // staged through pinned memory, the wave control word cleared.  The pinned
 // staging is reused by the next wave, so callers synchronise in between.
 int write_wave_tables(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs,
-                      const std::vector<Member>& mem, const Wave& w, bool bf16) {
+                      const std::vector<Member>& mem, const Wave& w, bool lowp) {
     int row0 = 0;
     for (int i = 0; i < (int)mem.size(); ++i) {
         const Problem& q = qs[mem[i].pair];
@@ -718,7 +770,7 @@ int write_wave_tables(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& q
         PairDesc d{};
         d.Y = sl.Y;
         d.X = sl.X;
-        d.Xt16 = bf16 ? sl.Xt16 : nullptr;
+        d.Xt16 = lowp ? sl.Xt16 : nullptr;
         d.colbuf = sl.colbuf;
         d.sbuf = sl.sbuf;
         d.dbuf = sl.dbuf;
@@ -799,17 +851,17 @@ int save_trace(fastpfp_t h, cudaStream_t s, int slot, int pair, int max_outer) {
 int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, const Wave& w,
                  const fastpfp_params* p, Ctrl* host_slots) {
     int nl = 0;
-    const bool bf16 = p->precision == FASTPFP_BF16;
+    const bool lowp = p->precision != FASTPFP_FP32;   // a BF16 or FP8 phase
     std::vector<Member> mem(w.count);
     for (int i = 0; i < w.count; ++i) mem[i] = Member{w.first + i, i};
     TcPlan tc;
-    if (bf16 && !plan_tc(h, &qs[w.first], w.count, p, &tc)) return FASTPFP_ERR_UNSUPPORTED;
+    if (lowp && !plan_tc(h, &qs[w.first], w.count, p, &tc)) return FASTPFP_ERR_UNSUPPORTED;
     for (int i = 0; i < w.count; ++i) {
         const int r = enqueue_setup(h->slots[i], s, qs[w.first + i], p, h->ld);
         if (r < 0) return r;
         nl += r;
     }
-    const int wt = write_wave_tables(h, s, qs, mem, w, bf16);
+    const int wt = write_wave_tables(h, s, qs, mem, w, lowp);
     if (wt < 0) return wt;
     const PdbParams P = wave_params(h, w, w.count, p);
     std::vector<GemmF32TGroup> f32a, f32b;
@@ -822,7 +874,7 @@ int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, co
         const bool pt = prof && t < kProfIters;
         if (pt && t == 0) FP_CUDA(cudaEventRecord(h->ev[0], st));
         int n = 0;
-        if (bf16) {
+        if (lowp) {
             n = enqueue_tc(tc, st);
             if (n < 0) return n;
         }
@@ -916,11 +968,12 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     const size_t n = (size_t)max_n, ld = (size_t)h->ld;
     const size_t f32mat = align256(n * ld * sizeof(float));
     const size_t b16mat = align256(n * (size_t)round8(max_n) * sizeof(__nv_bfloat16));
+    const size_t f8mat = align256(n * (size_t)round16(max_n));
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
     struct SlotOff {
         size_t Y, X, T, K, A16, A216, Xt16, T16, col, s, d, ctrl, rm, cm, rb, cb, sA, sA2, sB, sB2, sX0,
-            sXo, sp, A32, A232;
+            sXo, sp, A32, A232, qA, qA2, qXt, qT, scA, scA2, scX, scT;
     };
     std::vector<SlotOff> so(h->nslots);
     for (auto& o : so) {
@@ -932,6 +985,8 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
         o.sA = take(n * n * 4); o.sA2 = take(n * n * 4); o.sB = take(n * kMaxK * 4);
         o.sB2 = take(n * kMaxK * 4); o.sX0 = take(n * n * 4); o.sXo = take(n * n * 4); o.sp = take(n * 4);
         o.A32 = take(f32mat); o.A232 = take(f32mat);
+        o.qA = take(f8mat); o.qA2 = take(f8mat); o.qXt = take(f8mat); o.qT = take(f8mat);
+        o.scA = take(n * 4); o.scA2 = take(n * 4); o.scX = take(n * 4); o.scT = take(n * 4);
     }
     const size_t opairs = take(sizeof(PairDesc) * kMaxWavePairs);
     const size_t oband = take(sizeof(int) * 2 * (h->num_sms + 1));
@@ -999,6 +1054,14 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
         sl.sXout = (float*)(b + o.sXo);
         sl.A32 = (float*)(b + o.A32);
         sl.A232 = (float*)(b + o.A232);
+        sl.qA = (uint8_t*)(b + o.qA);
+        sl.qA2 = (uint8_t*)(b + o.qA2);
+        sl.qXt = (uint8_t*)(b + o.qXt);
+        sl.qT = (uint8_t*)(b + o.qT);
+        sl.scA = (float*)(b + o.scA);
+        sl.scA2 = (float*)(b + o.scA2);
+        sl.scX = (float*)(b + o.scX);
+        sl.scT = (float*)(b + o.scT);
         sl.sperm = (int32_t*)(b + o.sp);
     }
     h->d_pairs = (PairDesc*)(b + opairs);
@@ -1150,7 +1213,7 @@ int stage_out(fastpfp_t h, cudaStream_t s, const fastpfp_pair& x, int slot) {
 int solve_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, const fastpfp_pair* pairs,
                  const fastpfp_params* p, fastpfp_stats* st, bool host) {
     const int count = (int)qs.size();
-    const bool bf16 = p->precision == FASTPFP_BF16;
+    const bool lowp = p->precision != FASTPFP_FP32;   // a BF16 or FP8 phase
     const bool prof = p->profile != 0;
     std::vector<int> free_slots;
     for (int i = h->nslots - 1; i >= 0; --i) free_slots.push_back(i);
@@ -1248,14 +1311,14 @@ int solve_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, const fa
         ++launch_no;
         // one outer iteration of the wave
         const int n = (int)run.size();
-        if (write_wave_tables(h, s, qs, run, w, bf16) < 0) return fail(FASTPFP_ERR_CUDA);
+        if (write_wave_tables(h, s, qs, run, w, lowp) < 0) return fail(FASTPFP_ERR_CUDA);
         const PdbParams P = wave_params(h, w, n, p);
         TcPlan tc;
-        if (bf16 && !plan_tc(h, cand.data(), n, p, &tc, cand_slots.data())) return fail(FASTPFP_ERR_UNSUPPORTED);
+        if (lowp && !plan_tc(h, cand.data(), n, p, &tc, cand_slots.data())) return fail(FASTPFP_ERR_UNSUPPORTED);
         f32_groups(h, qs, run, p, f32a, f32b);
         int kl = 0;
         if (prof && cudaEventRecord(h->ev[0], s) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
-        if (bf16) {
+        if (lowp) {
             const int r = enqueue_tc(tc, s);
             if (r < 0) return fail(r);
             kl += r;
@@ -1546,10 +1609,50 @@ int fastpfp_gradient(fastpfp_t h, void* stream, const float* A, const float* X, 
     if (!h || !A || !X || !A2 || !Y || N < 1 || m < 1 || m > N || ldy < m) return FASTPFP_ERR_ARG;
     if (lambda != 0.f && !K) return FASTPFP_ERR_ARG;
     if (N > h->max_n) return FASTPFP_ERR_SIZE;
-    if (precision != FASTPFP_FP32 && precision != FASTPFP_BF16) return FASTPFP_ERR_ARG;
+    if (precision != FASTPFP_FP32 && precision != FASTPFP_BF16 && precision != FASTPFP_FP8)
+        return FASTPFP_ERR_ARG;
     if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     const Slot& sl = h->slots[0];
+    if (precision == FASTPFP_FP8) {
+        // E4M3 copies with per-row scales: A, A' and X^T (through the BF16
+        // transpose the solve's blend writes), then T between the products
+        const int l16N = round8(N), l16m = round8(m), l8N = round16(N), l8m = round16(m), l4m = round4(m);
+        FP_CUDA(transpose_to_bf16(X, N, m, m, sl.Xt16, l16N, s));
+        QuantGroup q1{};
+        q1.count = 3;
+        q1.q[0] = QuantRows{A, 0, N, N, N, sl.qA, l8N, sl.scA, nullptr};
+        q1.q[1] = QuantRows{A2, 0, m, m, m, sl.qA2, l8m, sl.scA2, nullptr};
+        q1.q[2] = QuantRows{sl.Xt16, 1, m, N, l16N, sl.qXt, l8N, sl.scX, nullptr};
+        FP_CUDA(quant_fp8_group(q1, s));
+        if (lambda != 0.f)
+            FP_CUDA(cudaMemcpy2DAsync(sl.K, (size_t)l4m * 4, K, (size_t)m * 4, (size_t)m * 4, N,
+                                      cudaMemcpyDeviceToDevice, s));
+        TcGroup a{}, c{};
+        a.count = c.count = 1;
+        a.mode = kTcOutBf16;
+        c.mode = kTcOutF32;
+        a.fp8 = c.fp8 = 1;
+        const int bn = tc_tile(h, N, 1);
+        a.bn = c.bn = bn;
+        if (!tc_make_map(&a.map_a[0], sl.qA, N, N, l8N, kTcTileM, true) ||
+            !tc_make_map(&a.map_b[0], sl.qXt, m, N, l8N, bn, true) ||
+            !tc_make_map(&c.map_a[0], sl.qT, N, m, l8m, kTcTileM, true) ||
+            !tc_make_map(&c.map_b[0], sl.qA2, m, m, l8m, bn, true))
+            return FASTPFP_ERR_UNSUPPORTED;
+        a.prob[0] = TcProblem{N, m, N, sl.T16, l16m, nullptr, 0, 0.f, nullptr, nullptr, sl.scA, sl.scX};
+        c.prob[0] = TcProblem{N, m, m, sl.Y, l4m, lambda != 0.f ? sl.K : nullptr, l4m, lambda, nullptr, nullptr,
+                              sl.scT, sl.scA2};
+        QuantGroup q2{};
+        q2.count = 1;
+        q2.q[0] = QuantRows{sl.T16, 1, N, m, l16m, sl.qT, l8m, sl.scT, nullptr};
+        FP_CUDA(tc_gemm(a, s));
+        FP_CUDA(quant_fp8_group(q2, s));
+        FP_CUDA(tc_gemm(c, s));
+        FP_CUDA(cudaMemcpy2DAsync(Y, (size_t)ldy * 4, sl.Y, (size_t)l4m * 4, (size_t)m * 4, N,
+                                  cudaMemcpyDeviceToDevice, s));
+        return FASTPFP_OK;
+    }
     if (precision == FASTPFP_BF16) {
         // BF16 operand copies in the slot, products on the tensor cores; Y and
         // K go through the slot's padded FP32 buffers (16-byte aligned rows)

@@ -1,6 +1,12 @@
-// gemm_tc.cu -- BF16 products of the gradient (Section 4.1) on the sm_103a
-// tensor cores: tcgen05.mma with the accumulator in tensor memory, operands
-// staged into shared memory by TMA (cp.async.bulk.tensor, 128-byte swizzle).
+// gemm_tc.cu -- low-precision products of the gradient (Section 4.1) on the
+// sm_103a tensor cores: tcgen05.mma with the accumulator in tensor memory,
+// operands staged into shared memory by TMA (cp.async.bulk.tensor, 128-byte
+// swizzle).  Operands are BF16 (kind::f16, K = 16 per MMA) or E4M3
+// (kind::f8f6f4, K = 32 per MMA) with one scale per operand row, applied to
+// the accumulator in the epilogue.  Either way a K stage is 128 bytes per
+// row, so the shared-memory layout, the descriptors and the ring are the
+// same; only the element count per stage (64 or 128) and the instruction
+// differ.
 //
 // Both products are "TN": C[i, j] = sum_k A[i, k] * B[j, k] with A and B
 // stored K-major (row-major with the reduction index contiguous):
@@ -32,19 +38,22 @@
 namespace fpfp {
 namespace {
 
-constexpr int BM = kTcTileM, BK = 64, STAGES = 4;
-constexpr int kTileBytesA = BM * BK * 2;
+constexpr int BM = kTcTileM, STAGES = 4;
+constexpr int kRowBytes = 128;                 // bytes of one operand row per K stage
+constexpr int kTileBytesA = BM * kRowBytes;
 constexpr int kThreads = 192;
-// Shapes that depend on the tile width BN (128 or 256).
-template <int BN>
+// Shapes that depend on the tile width BN (128 or 256) and the operand type.
+template <int BN, bool F8>
 struct TcShape {
-    static constexpr int kTileBytesB = BN * BK * 2;
+    static constexpr int BK = F8 ? 128 : 64;       // K elements per stage
+    static constexpr int kTileBytesB = BN * kRowBytes;
     static constexpr int kStageBytes = kTileBytesA + kTileBytesB;
     static constexpr uint32_t kTmemCols = 2 * BN;   // two BN-column FP32 accumulators
-    // Instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, both
-    // K-major, M = 128, N = BN.
-    static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                                       ((uint32_t)(BM >> 4) << 24);
+    // Instruction descriptor: FP32 accumulate (bits 4-5), A and B types
+    // (bits 7-9, 10-12: BF16 = 1 for kind::f16, E4M3 = 0 for kind::f8f6f4),
+    // both K-major, N >> 3 (bits 17-22), M >> 4 (bits 24-28).
+    static constexpr uint32_t kIdesc = (1u << 4) | (F8 ? 0u : (1u << 7) | (1u << 10)) |
+                                       ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 };
 constexpr long long kWaitNs = 2000ll * 1000000ll;
 
@@ -103,14 +112,23 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     d |= (uint64_t)2 << 61;                     // 128-byte swizzle
     return d;
 }
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-        : "memory");
+template <bool F8>
+__device__ __forceinline__ void mma_issue(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t acc) {
+    if (F8)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -157,6 +175,7 @@ template <int BN>
 __device__ __forceinline__ void drain_tile(const TcGroup& G, const TcProblem& pr, uint32_t tmem, uint32_t tcol,
                                            int quarter, int lane, int m0, int n0) {
     const int row = m0 + quarter * 32 + lane;
+    const float rsc = (pr.rs && row < pr.M) ? __ldg(pr.rs + row) : 1.f;
 #pragma unroll 1
     for (int c = 0; c < BN; c += 32) {
         uint32_t r[32];
@@ -164,6 +183,13 @@ __device__ __forceinline__ void drain_tile(const TcGroup& G, const TcProblem& pr
         const int col = n0 + c;
         if (row >= pr.M || col >= pr.N) continue;
         const int nv = min(32, pr.N - col);
+        if (pr.rs) {   // dequantisation: rs[row] * cs[col + v]
+#pragma unroll
+            for (int v = 0; v < 32; ++v) {
+                const float cv = (pr.cs && v < nv) ? __ldg(pr.cs + col + v) : 1.f;
+                r[v] = __float_as_uint(__uint_as_float(r[v]) * (rsc * cv));
+            }
+        }
         if (G.mode == kTcOutBf16) {
             __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(pr.out) + (size_t)row * pr.ldo + col;
             if (nv == 32) {
@@ -211,9 +237,10 @@ __device__ __forceinline__ void drain_tile(const TcGroup& G, const TcProblem& pr
     }
 }
 
-template <int BN>
+template <int BN, bool F8>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcGroup G) {
-    using S = TcShape<BN>;
+    using S = TcShape<BN, F8>;
+    constexpr int BK = S::BK;
     constexpr int kStageBytes = S::kStageBytes;
     constexpr uint32_t kTmemCols = S::kTmemCols;
     const int ntiles = G.tile0[G.count];
@@ -298,9 +325,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 const uint32_t b = a + kTileBytesA;
                 const uint64_t ad = smem_desc(a), bd = smem_desc(b);
 #pragma unroll
-                for (int j = 0; j < BK / 16; ++j)   // K = 16 per MMA: 32 bytes along the swizzled row
-                    mma_bf16(acc, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), S::kIdesc,
-                             (kb > 0 || j > 0) ? 1u : 0u);
+                for (int j = 0; j < 4; ++j)   // 32 bytes of K per MMA (16 BF16 or 32 E4M3)
+                    mma_issue<F8>(acc, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), S::kIdesc,
+                                  (kb > 0 || j > 0) ? 1u : 0u);
                 mma_commit(&empty[s]);
             }
             if (!ok) break;
@@ -359,7 +386,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }  // namespace
 
 size_t tc_smem_bytes(int bn) {
-    return (size_t)STAGES * (bn == 128 ? TcShape<128>::kStageBytes : TcShape<256>::kStageBytes) + 1024 + 256;
+    return (size_t)STAGES * (bn == 128 ? TcShape<128, false>::kStageBytes : TcShape<256, false>::kStageBytes) +
+           1024 + 256;
 }
 
 static int g_tc_sms = 0;
@@ -369,25 +397,31 @@ cudaError_t tc_configure() {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute((const void*)tc_gemm_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tc_smem_bytes(256));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute((const void*)tc_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tc_smem_bytes(128));
+    const void* fns[4] = {(const void*)tc_gemm_kernel<256, false>, (const void*)tc_gemm_kernel<128, false>,
+                          (const void*)tc_gemm_kernel<256, true>, (const void*)tc_gemm_kernel<128, true>};
+    for (int i = 0; i < 4; ++i) {
+        e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc_smem_bytes((i & 1) ? 128 : 256));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
-// rows x cols BF16 matrix, row-major with leading dimension ld (elements,
-// a multiple of 8), read as 64-column boxes of box_rows rows (128 for the A
-// operand, the group's tile width for B) with 128-byte swizzle.
-bool tc_make_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int cols, int ld, int box_rows) {
+// rows x cols matrix, row-major with leading dimension ld elements (BF16,
+// ld a multiple of 8; or E4M3 bytes, ld a multiple of 16), read as boxes of
+// 128 bytes along K by box_rows rows (128 for the A operand, the group's
+// tile width for B) with 128-byte swizzle.
+bool tc_make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int box_rows, bool fp8) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
-    if (!fn || (ld % 8) != 0 || (reinterpret_cast<uintptr_t>(ptr) & 15) != 0) return false;
+    const int esize = fp8 ? 1 : 2;
+    if (!fn || ((size_t)ld * esize) % 16 != 0 || (reinterpret_cast<uintptr_t>(ptr) & 15) != 0) return false;
     if (box_rows != 128 && box_rows != 256) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * esize};
+    const cuuint32_t box[2] = {(cuuint32_t)(kRowBytes / esize), (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), dims,
+    const CUresult r = fn(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                          const_cast<void*>(ptr), dims,
                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -405,10 +439,16 @@ cudaError_t tc_gemm(const TcGroup& G0, cudaStream_t s) {
     const int ntiles = G.tile0[G.count];
     if (ntiles <= 0) return cudaSuccess;
     const int grid = min(ntiles, g_tc_sms > 0 ? g_tc_sms : 148);
-    if (bn == 128)
-        tc_gemm_kernel<128><<<grid, kThreads, tc_smem_bytes(128), s>>>(G);
-    else
-        tc_gemm_kernel<256><<<grid, kThreads, tc_smem_bytes(256), s>>>(G);
+    if (G.fp8) {
+        if (bn == 128)
+            tc_gemm_kernel<128, true><<<grid, kThreads, tc_smem_bytes(128), s>>>(G);
+        else
+            tc_gemm_kernel<256, true><<<grid, kThreads, tc_smem_bytes(256), s>>>(G);
+    } else if (bn == 128) {
+        tc_gemm_kernel<128, false><<<grid, kThreads, tc_smem_bytes(128), s>>>(G);
+    } else {
+        tc_gemm_kernel<256, false><<<grid, kThreads, tc_smem_bytes(256), s>>>(G);
+    }
     return cudaGetLastError();
 }
 

@@ -88,6 +88,7 @@ struct PdbLayout {
     int max_band_cols;    // sum of ldy over the segments of one band
     int max_band_elems;   // floats of the largest band kept in shared memory (the rest is in TMEM)
     int rp_stride;        // row-partial slots per row: the most warps sharing one row, <= 16
+    int two_quad_ties;    // pdb_shape's tie rule for this wave (1: two quads per thread)
 };
 
 // Warps sharing one row of a pair whose slacked rows hold ldy floats, in a
@@ -97,26 +98,30 @@ struct PdbLayout {
 // multiple of 32) cover a row, each owning kq column quads (kq = 1 or 2,
 // qpg apart), and rp = nthr / qpg row groups work on different rows.  kq
 // maximises rp / kq, the rows a pass advances per quad a thread handles
-// (ties to one quad): a 1200-node row (300 quads) takes 3 groups of 160
-// threads with two quads each rather than one group of 320.
+// (a 1200-node row, 300 quads, takes 3 groups of 160 threads with two quads
+// each rather than one group of 320).  On a tie, two_quad_ties picks two
+// quads per thread: the per-row work (row offset, row-sum shuffles) then
+// serves twice the entries, which pays when a CTA's band has many rows; a
+// band of a few rows is better spread over more row groups.
 struct PdbShape {
     int kq, qpg, rp;
 };
-__host__ __device__ inline PdbShape pdb_shape(int ldy, int nthr) {
+__host__ __device__ inline PdbShape pdb_shape(int ldy, int nthr, int two_quad_ties) {
     const int Q = ldy >> 2;
     PdbShape best{0, 0, 0};
     for (int kq = 1; kq <= 2; ++kq) {
         const int qpg = ((Q + kq - 1) / kq + 31) & ~31;
         if (qpg > nthr) continue;
         const int rp = nthr / qpg;
-        // the layout that keeps more threads busy; on a tie two quads per
-        // thread, whose per-row work (row offset, row-sum shuffles) then
-        // serves twice the entries
-        if (best.kq == 0 || rp * best.kq >= best.rp * kq) best = PdbShape{kq, qpg, rp};
+        // the layout that keeps more threads busy; ties as the wave says
+        if (best.kq == 0 || rp * best.kq > best.rp * kq || (two_quad_ties && rp * best.kq == best.rp * kq))
+            best = PdbShape{kq, qpg, rp};
     }
     return best;   // kq == 0: rows too wide for one CTA (more than 2 * nthr quads)
 }
-__host__ __device__ inline int pdb_row_warps(int ldy, int nthr) { return pdb_shape(ldy, nthr).qpg >> 5; }
+__host__ __device__ inline int pdb_row_warps(int ldy, int nthr, int two_quad_ties) {
+    return pdb_shape(ldy, nthr, two_quad_ties).qpg >> 5;
+}
 
 // Tensor memory as band storage: a CTA of kPdbThreads threads allocates all
 // 512 TMEM columns; the four warps sharing a 32-lane quarter split them, so
@@ -131,8 +136,8 @@ constexpr int kTmemColsPerThread = kTmemCols * 128 / kPdbThreads;
 // thread's kq quads of its k-th row); the rest in shared memory.  Returns tm
 // and sets *tm_band_rows (band rows in TMEM) and *col_next.
 __host__ __device__ inline int pdb_tmem_rows(int nrows, int ldy, int nthr, int col_used, int* tm_band_rows,
-                                             int* col_next) {
-    const PdbShape sh = pdb_shape(ldy, nthr);
+                                             int* col_next, int two_quad_ties) {
+    const PdbShape sh = pdb_shape(ldy, nthr, two_quad_ties);
     *col_next = col_used;
     *tm_band_rows = 0;
     if (sh.kq == 0) return 0;
@@ -173,7 +178,10 @@ constexpr int kTcMaxGroup = 32;      // problems of one grouped launch (a whole 
 constexpr int kTcOutBf16 = 0;        // epilogue writes BF16 (T = A X)
 constexpr int kTcOutF32 = 1;         // epilogue writes FP32 + lambda K (Y = T A' + lambda K)
 
-// C[M x N] = A[M x K] B[N x K]^T, both operands BF16 K-major (tensor maps).
+// C[M x N] = A[M x K] B[N x K]^T, both operands K-major (tensor maps),
+// both BF16 or both E4M3 (the group's fp8 flag).  With rs / cs set the
+// accumulator is scaled by rs[i] * cs[j] before the epilogue adds lambda K:
+// the dequantisation of operands stored as E4M3 with one scale per row.
 struct TcProblem {
     int M, N, K;
     void* out;            // BF16 or FP32 row-major, leading dimension ldo
@@ -181,8 +189,10 @@ struct TcProblem {
     const float* Kmat;    // FP32 mode: nullable lambda * K addend, leading dimension ldk
     int ldk;
     float lambda;
-    const Ctrl* ctrl;     // nullable: skip unless the solve runs its BF16 phase
+    const Ctrl* ctrl;     // nullable: skip unless the solve runs its low-precision phase
     int* err;             // nullable: receives FASTPFP_ERR_TIMEOUT
+    const float* rs;      // nullable: per-row output scale (M entries)
+    const float* cs;      // nullable: per-column output scale (N entries)
 };
 struct TcGroup {
     CUtensorMap map_a[kTcMaxGroup];
@@ -191,6 +201,7 @@ struct TcGroup {
     int count;
     int mode;
     int bn;   // output tile columns: 256 (0 reads as 256) or 128; map_b's box has bn rows
+    int fp8;  // operands E4M3 (kind::f8f6f4, 128-element K stages) instead of BF16
     // filled by tc_gemm: output tiles of problems before i (tile0[count] =
     // all tiles) and tiles per row of tiles of problem i
     int tile0[kTcMaxGroup + 1];
@@ -199,10 +210,11 @@ struct TcGroup {
 constexpr int kTcTileM = 128;   // output tile rows of tc_gemm (the A operand's box)
 size_t tc_smem_bytes(int bn);
 cudaError_t tc_configure();
-// TMA map of a rows x cols BF16 operand (ld elements, a multiple of 8) for
-// tc_gemm, read in boxes of box_rows rows: kTcTileM for an A operand, the
-// group's bn for a B operand.  False if the layout does not suit TMA.
-bool tc_make_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int cols, int ld, int box_rows);
+// TMA map of a rows x cols operand for tc_gemm, BF16 (ld elements, a
+// multiple of 8) or E4M3 bytes (fp8; ld a multiple of 16), read in boxes of
+// 128 bytes along K by box_rows rows: kTcTileM for an A operand, the group's
+// bn for a B operand.  False if the layout does not suit TMA.
+bool tc_make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int box_rows, bool fp8 = false);
 cudaError_t tc_gemm(const TcGroup& G, cudaStream_t s);
 
 // ----------------------------------------------------------------- GEMM
@@ -287,6 +299,28 @@ cudaError_t to_bf16(const float* src, int r, int c, int lds, __nv_bfloat16* dst,
                     cudaStream_t s);
 
 // dst (c x ldd, BF16) = src^T for an r x c FP32 src with leading dimension lds.
+// E4M3 copies with one power-of-two scale per row, for the FP8 products:
+// row r of src (BF16 or FP32, rows x cols, leading dimension lds) becomes
+// dst[r] = E4M3(src[r] * 2^e_r) (round to nearest even, saturating) with the
+// largest e_r that keeps max |src[r]| * 2^e_r <= 448 (e_r = 0 for a zero
+// row), and scale[r] = 2^-e_r.  Up to kTcMaxGroup matrices per launch; an
+// entry with ctrl set does nothing unless that solve is running its
+// low-precision phase.
+struct QuantRows {
+    const void* src;
+    int src_bf16;
+    int rows, cols, lds;
+    uint8_t* dst;
+    int ldd;
+    float* scale;
+    const Ctrl* ctrl;
+};
+struct QuantGroup {
+    QuantRows q[kTcMaxGroup];
+    int count;
+};
+cudaError_t quant_fp8_group(const QuantGroup& g, cudaStream_t s);
+
 cudaError_t transpose_to_bf16(const float* src, int r, int c, int lds, __nv_bfloat16* dst, int ldd,
                               cudaStream_t s);
 

@@ -1,7 +1,7 @@
 // misc.cu -- small kernels around the solve: control-block set-up, the
 // attribute affinity K = B B'^T (below Eq. 4), the initial X (after
-// Algorithm 1), BF16 operand copies, caller-orientation outputs and the
-// objective of Eq. (3) at the discrete result.
+// Algorithm 1), BF16 and E4M3 operand copies, caller-orientation outputs and
+// the objective of Eq. (3) at the discrete result.
 #include "common.cuh"
 #include "internal.h"
 
@@ -52,6 +52,56 @@ __global__ void to_bf16_kernel(const float* src, int r, int c, int lds, __nv_bfl
          e += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(e / ldd), j = (int)(e % ldd);
         dst[e] = __float2bfloat16_rn(j < c ? src[(size_t)i * lds + j] : 0.f);
+    }
+}
+
+// Two floats to two E4M3 bytes (round to nearest even, saturating at
+// +-448): the lower byte holds lo.
+__device__ __forceinline__ unsigned short e4m3x2(float lo, float hi) {
+    unsigned short r;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// One warp per row of one matrix of the group (blockIdx.y): the row's
+// largest magnitude, its power-of-two scale, then the E4M3 bytes, four per
+// lane and store.
+__global__ void __launch_bounds__(256) quant_fp8_kernel(const __grid_constant__ QuantGroup G) {
+    if ((int)blockIdx.y >= G.count) return;
+    const QuantRows& q = G.q[blockIdx.y];
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (row >= q.rows) return;
+    if (q.ctrl) {
+        if (ld_relaxed_i32(&q.ctrl->done) != 0 || ld_relaxed_i32(&q.ctrl->error) != 0) return;
+        if (ld_relaxed_i32(&q.ctrl->lowp) == 0) return;
+    }
+    const float* f = q.src_bf16 ? nullptr : reinterpret_cast<const float*>(q.src) + (size_t)row * q.lds;
+    const __nv_bfloat16* h = q.src_bf16 ? reinterpret_cast<const __nv_bfloat16*>(q.src) + (size_t)row * q.lds
+                                        : nullptr;
+    auto at = [&](int c) { return c < q.cols ? (h ? __bfloat162float(h[c]) : f[c]) : 0.f; };
+    float mx = 0.f;
+    for (int c = lane; c < q.cols; c += 32) mx = fmaxf(mx, fabsf(at(c)));
+    mx = warp_max(mx);
+    // the largest e with mx * 2^e <= 448 = 0.875 * 2^9 (mx = fr * 2^ex, fr in [0.5, 1))
+    int e = 0;
+    if (mx > 0.f && isfinite(mx)) {
+        int ex;
+        const float fr = frexpf(mx, &ex);
+        e = (fr <= 0.875f ? 9 : 8) - ex;
+        e = max(-126, min(126, e));
+    }
+    const float up = ldexpf(1.f, e);
+    if (lane == 0) q.scale[row] = ldexpf(1.f, -e);
+    uint8_t* d = q.dst + (size_t)row * q.ldd;
+    for (int c = 4 * lane; c < q.cols; c += 128) {
+        const unsigned lo = e4m3x2(at(c) * up, at(c + 1) * up);
+        const unsigned hi = e4m3x2(at(c + 2) * up, at(c + 3) * up);
+        if (c + 3 < q.cols) {
+            *reinterpret_cast<unsigned*>(d + c) = lo | (hi << 16);
+        } else {
+            const unsigned w = lo | (hi << 16);
+            for (int t = 0; c + t < q.cols; ++t) d[c + t] = (uint8_t)(w >> (8 * t));
+        }
     }
 }
 
@@ -208,6 +258,14 @@ cudaError_t to_bf16(const float* src, int r, int c, int lds, __nv_bfloat16* dst,
                     cudaStream_t s) {
     const size_t total = (size_t)r * ldd;
     to_bf16_kernel<<<grid_for(total, 256), 256, 0, s>>>(src, r, c, lds, dst, ldd);
+    return cudaGetLastError();
+}
+
+cudaError_t quant_fp8_group(const QuantGroup& g, cudaStream_t s) {
+    int rows = 0;
+    for (int i = 0; i < g.count; ++i) rows = max(rows, g.q[i].rows);
+    if (g.count <= 0 || rows <= 0) return cudaSuccess;
+    quant_fp8_kernel<<<dim3((rows + 7) / 8, g.count), 256, 0, s>>>(g);
     return cudaGetLastError();
 }
 

@@ -410,7 +410,11 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
         C->last_delta = d;
         if (C->lowp) {
             C->lowp_iters += 1;
-            if (d < P.switch_tol || t + 1 >= P.max_outer - P.refine_iters) {
+            // the phase ends at switch_tol, when max|dX| shrinks by less than half
+            // (the products' rounding noise is near; from the fourth iteration on) or
+            // when only the refinement iterations are left
+            const double dprev = (t >= 1 && t - 1 < kMaxOuterTrace) ? C->delta_trace[t - 1] : d;
+            if (d < P.switch_tol || (t >= 3 && d > 0.5 * dprev) || t + 1 >= P.max_outer - P.refine_iters) {
                 C->lowp = 0;
                 C->refine_left = P.refine_iters;
             }

@@ -447,8 +447,8 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 s.soff = soff;
                 s.coff = coff;
                 s.tcol = tcol;
-                s.tm = pdb_tmem_rows(s.nrows, d.ldy, nthr, tcol, &s.ntm, &tcol);
-                const PdbShape sh = pdb_shape(d.ldy, nthr);
+                s.tm = pdb_tmem_rows(s.nrows, d.ldy, nthr, tcol, &s.ntm, &tcol, P.layout.two_quad_ties);
+                const PdbShape sh = pdb_shape(d.ldy, nthr, P.layout.two_quad_ties);
                 s.qpg = sh.qpg;
                 s.rpkq = 4 * sh.rp + sh.kq;
                 S.seg[nseg++] = s;
@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             if (sg.group != g) continue;
             const int pst = S.pstate[sg.pair];
             if (!(pst & 1) || (pst & 2)) continue;
-            const int nw = pdb_row_warps(S.pair[sg.pair].ldy, nthr);
+            const int nw = pdb_row_warps(S.pair[sg.pair].ldy, nthr, P.layout.two_quad_ties);
             for (int r = tid; r < sg.nrows; r += nthr) {
                 const float* rpp = S.rowpart + (size_t)(sg.brow0 + r) * RPS;
                 float t = 0.f;
@@ -911,7 +911,11 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             C->last_delta = d;
             if (C->lowp) {
                 C->lowp_iters += 1;
-                if (d < P.switch_tol || t + 1 >= P.max_outer - P.refine_iters) {
+                // the phase ends at switch_tol, when max|dX| shrinks by less than half
+                // (the products' rounding noise is near; from the fourth iteration on) or
+                // when only the refinement iterations are left
+                const double dprev = (t >= 1 && t - 1 < kMaxOuterTrace) ? C->delta_trace[t - 1] : d;
+                if (d < P.switch_tol || (t >= 3 && d > 0.5 * dprev) || t + 1 >= P.max_outer - P.refine_iters) {
                     C->lowp = 0;
                     C->refine_left = P.refine_iters;
                 }

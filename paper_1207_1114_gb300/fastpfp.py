@@ -23,7 +23,7 @@ FASTPFP_ERR_CUDA = -3
 FASTPFP_ERR_TIMEOUT = -4
 FASTPFP_ERR_NONFINITE = -5
 FASTPFP_ERR_UNSUPPORTED = -6
-FP32, BF16 = 0, 1
+FP32, BF16, FP8 = 0, 1, 2
 
 # Every symbol include/fastpfp.h declares.
 EXPORTS = ("fastpfp_default_params", "fastpfp_create", "fastpfp_destroy", "fastpfp_match",

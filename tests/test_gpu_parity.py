@@ -624,3 +624,86 @@ def test_autotune_fills_the_table_for_every_reachable_class():
             s.autotune(reps=0)
     finally:
         s.close()
+
+
+# ------------------------------------------------------------ FP8 products
+
+def _e4m3_rows(a):
+    """Per-row power-of-two scaling and E4M3 rounding as the FP8 products do
+    (the largest e with max|row| * 2^e <= 448, round to nearest even), then
+    back to float64: the operand the tensor cores effectively multiply."""
+    a = np.asarray(a, dtype=np.float32)
+    mx = np.abs(a).max(axis=1).astype(np.float64)
+    e = np.zeros(len(a), dtype=np.int64)
+    nz = mx > 0
+    fr, ex = np.frexp(mx[nz])
+    e[nz] = np.where(fr <= 0.875, 9, 8) - ex
+    up = np.ldexp(1.0, e)[:, None]
+    q = torch.as_tensor((a * up).astype(np.float32)).to(torch.float8_e4m3fn).to(torch.float32).numpy()
+    return q.astype(np.float64) / up
+
+
+def test_e4m3_emulation_rounds_like_the_format():
+    """The test-side emulation itself: E4M3 keeps 3 mantissa bits (relative
+    spacing 2^-3), so after scaling every normal value is within 2^-4 of
+    itself, the row maximum lands in (224, 448], and exact grid points
+    survive unchanged."""
+    rng = np.random.default_rng(3)
+    a = rng.random((7, 50)).astype(np.float32) * np.logspace(-3, 3, 7, dtype=np.float32)[:, None]
+    q = _e4m3_rows(a)
+    assert (np.abs(q - a) <= 2.0 ** -4 * np.abs(a) + 1e-12).all()
+    grid = np.array([[0.0, 1.0, 1.125, 448.0, 0.015625]], dtype=np.float32)
+    np.testing.assert_array_equal(_e4m3_rows(grid), grid.astype(np.float64))
+
+
+@pytest.mark.parametrize("N,m", [(5, 3), (129, 100), (300, 300), (1000, 1000), (1200, 1000)])
+def test_gradient_fp8_tensor_cores_matches_oracle(solver, N, m):
+    """tcgen05 E4M3 products with per-row scales.  Against the oracle on the
+    operands as the kernels quantise them (A and A' per row from FP32, X per
+    column through its BF16 copy) only T's quantisation remains: E4M3 after
+    BF16, |err| <= (2^-4 + 2^-8) |A||X||A'| (+ FP32 terms); against the
+    unquantised oracle four E4M3 roundings: 0.3 * the bound."""
+    rng = np.random.default_rng(N * 7 + m)
+    A = synth.random_graph(rng, N, 0.2).astype(np.float32)
+    A2 = synth.random_graph(rng, m, 0.2).astype(np.float32)
+    X = rng.random((N, m)).astype(np.float32)
+    K = rng.normal(size=(N, m)).astype(np.float32)
+    lam = 0.7
+    G = solver.gradient(cu(A), cu(X), cu(A2), cu(K), lam, precision=F.FP8).cpu().numpy()
+    bound = np.abs(A) @ np.abs(X).astype(np.float64) @ np.abs(A2) + lam * np.abs(K)
+    ref = oracle.gradient(A, X, A2, K, lam)
+    assert (np.abs(G - ref) <= 0.3 * bound + 1e-30).all()
+    Aq, A2q = _e4m3_rows(A), _e4m3_rows(A2).T
+    Xq = _e4m3_rows(_bf16(X).T).T
+    ref8 = oracle.gradient(Aq, Xq, A2q, K, lam)
+    bound8 = np.abs(Aq) @ np.abs(Xq) @ np.abs(A2q) + lam * np.abs(K)
+    assert (np.abs(G - ref8) <= (2.0 ** -4 + 2.0 ** -8) * bound8 + 1e-5 * bound8 + 1e-30).all()
+
+
+def test_fp8_phase_then_fp32_refinement(solver):
+    """The precision policy with E4M3 products: the FP8 phase runs until
+    max|dX| < switch_tol, then FP32 iterations; the refined result matches
+    the plain FP32 solve's permutation and objective."""
+    g = synth.attributed_1000(seed=2)
+    A, A2, B, B2 = cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)
+    r32 = solver.match(A, A2, B, B2, params=F.default_params(lam=1.0), want_X=True)
+    p8 = F.default_params(lam=1.0, precision=F.FP8, refine_iters=30, switch_tol=1e-3)
+    r8 = solver.match(A, A2, B, B2, params=p8, want_X=True)
+    st = r8.stats
+    assert st.status == 0 and st.lowp_iters >= 1 and st.outer_iters > st.lowp_iters
+    assert st.converged == 1
+    np.testing.assert_array_equal(r8.perm.cpu().numpy(), r32.perm.cpu().numpy())
+    assert abs(st.objective - r32.stats.objective) <= 1e-5 * abs(r32.stats.objective)
+    assert np.abs(r8.X.cpu().numpy() - r32.X.cpu().numpy()).max() <= 1e-3
+
+
+def test_fp8_batched_wave(solver):
+    """A wave of uneven pairs with the FP8 phase: every pair ends in FP32 at
+    the plain solve's objective."""
+    pairs = synth.batch_mixed(count=5, seed=13, n_lo=100, n_hi=400, out_hi=40)
+    dev = [(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)) for g in pairs]
+    o8 = solver.match_batched(dev, params=F.default_params(lam=0.5, precision=F.FP8, refine_iters=30))
+    o32 = solver.match_batched(dev, params=F.default_params(lam=0.5))
+    for a, b in zip(o8, o32):
+        assert a.stats.status == 0 and a.stats.lowp_iters >= 1
+        assert abs(a.stats.objective - b.stats.objective) <= 1e-4 * abs(b.stats.objective)
