@@ -54,13 +54,39 @@ KERNEL_SOURCE = {
 }
 
 
-def peaks():
+# FP32 SIMT peak of the GB300: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz.
+F32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def load_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+            return json.load(f)
     except Exception:
-        return 6800.0, "fallback"
+        return {}
+
+
+def peaks():
+    d = load_peaks()
+    if "hbm_gbs" in d:
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def gemm_probe_line(F, device: int, n: int = 4096):
+    """The product kernels timed alone at n^3 (fastpfp_gemm_probe) against
+    their peaks: BF16 against the measured cuBLAS burst, E4M3 against twice
+    that (the nominal FP8:BF16 ratio), FP32 SIMT against its derived peak."""
+    bf16_peak = float(load_peaks().get("bf16_tflops") or 1900.0)   # the fallback burst figure
+    f32_peak = F32_SIMT_TFLOPS
+    out = {"n": n, "timing": "best of 10 launches, CUDA events, after one warm-up"}
+    for name, prec, peak, kind in (
+            ("f32", F.FP32, f32_peak, "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"),
+            ("bf16", F.BF16, bf16_peak, "measured cuBLAS BF16 burst (MEASURED_PEAKS.json)"),
+            ("fp8", F.FP8, 2.0 * bf16_peak, "2 x measured BF16 burst (nominal dense FP8:BF16 ratio)")):
+        t = F.gemm_probe(prec, n=n, reps=10, device=device)
+        out[name] = {"tflops": t, "peak": peak, "frac": t / peak, "peak_kind": kind}
+    return out
 
 
 def source_hash(kernel: str) -> str:
@@ -472,6 +498,7 @@ def main():
             i += w
     rounds_per_launch = wave_rounds / max(proj_launches, 1)
     traffic = ncu_traffic_per_launch(kernel, args.workload, rounds_per_launch)
+    gemm = gemm_probe_line(F, local) if rank == 0 else None
 
     # end to end through the public host-memory batch entry point: every step
     # copies its pairs from pinned host memory and reads the permutations back
@@ -545,6 +572,7 @@ def main():
                          "traffic": traffic,
                          "alg_bytes_per_launch": alg_bytes / max(proj_launches, 1),
                          "launches": proj_launches, "timing": timing},
+            "gemm_probe": gemm,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -319,6 +319,16 @@ int fastpfp_project_noalloc(void* stream, float* Y, int N, double tol, int max_i
  * or sweeps, gbs == NULL), ERR_CUDA. */
 int fastpfp_bandwidth_probe(int device, int level, int sweeps, double* gbs);
 
+/* Throughput of the gradient's product kernels on CUDA device `device`: one
+ * n x n x n product C = A B^T (both operands K-major, values pseudo-random
+ * in [-1, 1)) with the kernel `precision` selects (FASTPFP_FP32: the SIMT
+ * kernel; FASTPFP_BF16 / FASTPFP_FP8: the tensor-core kernel, 128 x 256
+ * tiles, E4M3 with per-row scales), timed alone with CUDA events after one
+ * warm-up launch; *tflops = 2 n^3 / (best of reps) in TFLOP/s.  n a multiple
+ * of 16 in [256, 16384], reps in [1, 1000].  Allocates and frees about
+ * 16 n^2 bytes; synchronises the device.  Errors: ERR_ARG, ERR_CUDA. */
+int fastpfp_gemm_probe(int device, int precision, int n, int reps, double* tflops);
+
 /* Tile shapes of the gradient products A X A' + lambda K (Section 4.1).
  * Each solve picks, per grouped launch, the CTA tile of its FP32 products
  * (128 or 64 output rows) and of its BF16 tensor-core products (128 x 256 or

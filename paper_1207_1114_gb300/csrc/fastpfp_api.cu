@@ -1475,6 +1475,17 @@ int fastpfp_bandwidth_probe(int device, int level, int sweeps, double* gbs) {
     return FASTPFP_OK;
 }
 
+int fastpfp_gemm_probe(int device, int precision, int n, int reps, double* tflops) {
+    if (!tflops || reps < 1 || reps > 1000 || n < 256 || n > 16384 || (n % 16) != 0) return FASTPFP_ERR_ARG;
+    if (precision != FASTPFP_FP32 && precision != FASTPFP_BF16 && precision != FASTPFP_FP8) return FASTPFP_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return FASTPFP_ERR_CUDA;
+    if (tc_configure() != cudaSuccess || gemm_f32t_configure() != cudaSuccess) return FASTPFP_ERR_CUDA;
+    float ms = 0.f;
+    if (probe_gemm(precision, n, reps, 0, &ms) != cudaSuccess || ms <= 0.f) return FASTPFP_ERR_CUDA;
+    *tflops = 2.0 * (double)n * n * n / ((double)ms * 1e-3) / 1e12;
+    return FASTPFP_OK;
+}
+
 int fastpfp_autotune(fastpfp_t h, void* stream, int reps, double* times_ms) {
     if (!h || reps < 1 || reps > 100) return FASTPFP_ERR_ARG;
     if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;

@@ -263,6 +263,9 @@ cudaError_t gemm_f32t_group(const GemmF32TGroup& g, cudaStream_t s);
 // *ms = elapsed time of the timed sweeps, *bytes = bytes they moved.
 cudaError_t probe_smem(int num_sms, int sweeps, cudaStream_t s, float* ms, double* bytes);
 cudaError_t probe_gmem(size_t buf_bytes, int num_sms, int sweeps, cudaStream_t s, float* ms, double* bytes);
+// Best time of one n x n x n product C = A B^T on the solver's kernels
+// (FP32 SIMT, BF16 or E4M3 tensor cores) over reps timed launches.
+cudaError_t probe_gemm(int precision, int n, int reps, cudaStream_t s, float* best_ms);
 
 // ----------------------------------------------------------- misc kernels
 cudaError_t init_ctrl(Ctrl* c, int lowp, cudaStream_t s);

@@ -1,5 +1,6 @@
 // probe.cu -- bandwidth of the memory levels that hold the slacked matrix Y
-// during the projection rounds, measured on the device the solver runs on.
+// during the projection rounds, and throughput of the gradient's product
+// kernels, measured on the device the solver runs on.
 //
 // The P1/P2 rounds read and write every entry of Y once per round.  When a
 // wave's matrices fit in shared memory they never leave it, so the level
@@ -46,7 +47,85 @@ __global__ void __launch_bounds__(kProbeThreads) gmem_probe_kernel(float4* buf, 
     }
 }
 
+// Pseudo-random values in [-1, 1) (a 32-bit integer hash of the index), so
+// the timed products see data-dependent switching like real operands.
+__global__ void fill_kernel(float* p, size_t n, unsigned seed) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        unsigned h = (unsigned)i * 0x9E3779B1u ^ seed;
+        h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
+        p[i] = (float)(h >> 8) * (2.0f / 16777216.0f) - 1.0f;
+    }
+}
+
 }  // namespace
+
+cudaError_t probe_gemm(int precision, int n, int reps, cudaStream_t s, float* best_ms) {
+    const size_t nn = (size_t)n * n;
+    float *a = nullptr, *b = nullptr, *c = nullptr;
+    void *a16 = nullptr, *b16 = nullptr;
+    float *sa = nullptr, *sb = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto check = [&](cudaError_t r) { if (e == cudaSuccess) e = r; return e == cudaSuccess; };
+    check(cudaMalloc(&a, nn * 4));
+    check(cudaMalloc(&b, nn * 4));
+    check(cudaMalloc(&c, nn * 4));
+    check(cudaMalloc(&a16, nn * 2));
+    check(cudaMalloc(&b16, nn * 2));
+    check(cudaMalloc(&sa, (size_t)n * 4));
+    check(cudaMalloc(&sb, (size_t)n * 4));
+    check(cudaEventCreate(&e0));
+    check(cudaEventCreate(&e1));
+    if (e == cudaSuccess) {
+        fill_kernel<<<1024, 256, 0, s>>>(a, nn, 1u);
+        fill_kernel<<<1024, 256, 0, s>>>(b, nn, 2u);
+        check(cudaGetLastError());
+    }
+    // one product C = A B^T (TN, both K-major) of the precision under test
+    TcGroup g{};
+    GemmF32TGroup f{};
+    if (e == cudaSuccess && precision == FASTPFP_FP32) {
+        f.count = 1;
+        f.a[0] = GemmF32TArgs{a, n, b, n, c, n, nullptr, 0, 0.f, n, n, n, nullptr};
+    } else if (e == cudaSuccess) {
+        const bool fp8 = precision == FASTPFP_FP8;
+        if (fp8) {
+            QuantGroup q{};
+            q.count = 2;
+            q.q[0] = QuantRows{a, 0, n, n, n, (uint8_t*)a16, n, sa, nullptr};
+            q.q[1] = QuantRows{b, 0, n, n, n, (uint8_t*)b16, n, sb, nullptr};
+            check(quant_fp8_group(q, s));
+        } else {
+            check(to_bf16(a, n, n, n, (__nv_bfloat16*)a16, n, s));
+            check(to_bf16(b, n, n, n, (__nv_bfloat16*)b16, n, s));
+        }
+        g.count = 1;
+        g.mode = kTcOutF32;
+        g.bn = 256;
+        g.fp8 = fp8 ? 1 : 0;
+        if (!tc_make_map(&g.map_a[0], a16, n, n, n, kTcTileM, fp8) ||
+            !tc_make_map(&g.map_b[0], b16, n, n, n, 256, fp8))
+            e = cudaErrorInvalidValue;
+        g.prob[0] = TcProblem{n, n, n, c, n, nullptr, 0, 0.f, nullptr, nullptr, fp8 ? sa : nullptr,
+                              fp8 ? sb : nullptr};
+    }
+    auto launch = [&]() { return precision == FASTPFP_FP32 ? gemm_f32t_group(f, s) : tc_gemm(g, s); };
+    if (e == cudaSuccess) check(launch());   // warm-up
+    *best_ms = 0.f;
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        check(cudaEventRecord(e0, s));
+        check(launch());
+        check(cudaEventRecord(e1, s));
+        check(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        check(cudaEventElapsedTime(&ms, e0, e1));
+        if (r == 0 || ms < *best_ms) *best_ms = ms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(a); cudaFree(b); cudaFree(c); cudaFree(a16); cudaFree(b16); cudaFree(sa); cudaFree(sb);
+    return e;
+}
 
 cudaError_t probe_smem(int num_sms, int sweeps, cudaStream_t s, float* ms, double* bytes) {
     const int floats = (int)((kPdMaxSmem - 1024) / sizeof(float)) & ~3;

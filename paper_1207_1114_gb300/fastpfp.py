@@ -31,7 +31,7 @@ EXPORTS = ("fastpfp_default_params", "fastpfp_create", "fastpfp_destroy", "fastp
            "fastpfp_last_trace",
            "fastpfp_gradient", "fastpfp_affinity", "fastpfp_project", "fastpfp_discretize",
            "fastpfp_project_noalloc", "fastpfp_warmstart", "fastpfp_warmstart_train_step",
-           "fastpfp_bandwidth_probe", "fastpfp_autotune", "fastpfp_get_tiles", "fastpfp_set_tiles",
+           "fastpfp_bandwidth_probe", "fastpfp_gemm_probe", "fastpfp_autotune", "fastpfp_get_tiles", "fastpfp_set_tiles",
            "fastpfp_error_string")
 TUNE_SIZES, TUNE_COUNTS = 8, 4
 MLP_NPARAMS = 32 * 128 + 128 + 128 * 64 + 64
@@ -102,6 +102,7 @@ def lib():
     l.fastpfp_warmstart_train_step.argtypes = [P, V, P, I, P, I, P, P, I, P, P, P, P, I, C.c_float,
                                                C.POINTER(C.c_double), P]
     l.fastpfp_bandwidth_probe.argtypes = [I, I, I, C.POINTER(C.c_double)]
+    l.fastpfp_gemm_probe.argtypes = [I, I, I, I, C.POINTER(C.c_double)]
     l.fastpfp_autotune.argtypes = [P, V, I, P]
     l.fastpfp_get_tiles.argtypes = [P, I, I, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     l.fastpfp_set_tiles.argtypes = [P, I, I, I, I]
@@ -120,6 +121,15 @@ def bandwidth_probe(level: int, sweeps: int = 200, device: int = 0) -> float:
     out = C.c_double(0.0)
     _check(lib().fastpfp_bandwidth_probe(int(device), int(level), int(sweeps), C.byref(out)),
            "fastpfp_bandwidth_probe")
+    return float(out.value)
+
+
+def gemm_probe(precision: int, n: int = 4096, reps: int = 10, device: int = 0) -> float:
+    """TFLOP/s of one n^3 product on the solver's FP32, BF16 or FP8 kernel
+    (fastpfp_gemm_probe)."""
+    out = C.c_double(0.0)
+    _check(lib().fastpfp_gemm_probe(int(device), int(precision), int(n), int(reps), C.byref(out)),
+           "fastpfp_gemm_probe")
     return float(out.value)
 
 

@@ -707,3 +707,18 @@ def test_fp8_batched_wave(solver):
     for a, b in zip(o8, o32):
         assert a.stats.status == 0 and a.stats.lowp_iters >= 1
         assert abs(a.stats.objective - b.stats.objective) <= 1e-4 * abs(b.stats.objective)
+
+
+def test_gemm_probe_orders_the_product_kernels():
+    """The GEMM throughput probe behind the bench's product fractions: every
+    kernel does real work (FP32 well above 1 TFLOP/s), the tensor cores beat
+    the SIMT kernel, and nothing exceeds its nominal dense peak (FP32 80.5,
+    BF16 2250, FP8 4500 TFLOP/s)."""
+    f32 = F.gemm_probe(F.FP32, n=2048, reps=3)
+    bf16 = F.gemm_probe(F.BF16, n=2048, reps=3)
+    fp8 = F.gemm_probe(F.FP8, n=2048, reps=3)
+    assert 1.0 < f32 < 80.5
+    assert f32 < bf16 < 2250.0
+    assert 1.0 < fp8 < 4500.0
+    with pytest.raises(F.FastPFPError):
+        F.gemm_probe(F.BF16, n=1000)
