@@ -42,7 +42,7 @@ def build(force: bool = False) -> str:
 class orc_params(C.Structure):
     _fields_ = [("lambda_", C.c_double), ("alpha", C.c_double), ("tol_outer", C.c_double),
                 ("tol_inner", C.c_double), ("max_outer", C.c_int), ("max_inner", C.c_int),
-                ("normalize_max", C.c_int), ("slack_policy", C.c_int)]
+                ("normalize_max", C.c_int), ("slack_policy", C.c_int), ("algorithm", C.c_int)]
 
 
 class orc_stats(C.Structure):
@@ -211,8 +211,9 @@ def relaxed_objective(A, A2, X, K=None, lam=0.0):
 
 def solve(A, A2, B=None, B2=None, lam=0.0, alpha=0.5, tol_outer=1e-6, tol_inner=1e-6,
           max_outer=100, max_inner=1000, normalize_max=True, slack_policy=0, X0=None,
-          replay_inner=None, replay_outer=0):
-    """Algorithm 1 end to end in the caller's orientation.
+          replay_inner=None, replay_outer=0, algorithm="fastpfp"):
+    """Algorithm 1 end to end in the caller's orientation (algorithm="pg":
+    the projected gradient method of Eq. (pg) in the same loop).
 
     Returns a dict with ``perm`` (n_a entries, -1 for unmatched), ``X``
     (n_a x n_b), ``inner`` and ``delta`` traces and the stats fields."""
@@ -225,8 +226,11 @@ def solve(A, A2, B=None, B2=None, lam=0.0, alpha=0.5, tol_outer=1e-6, tol_inner=
         B, pb = _d(B)
         B2, pb2 = _d(B2)
         k = B.shape[1]
+    if algorithm not in ("fastpfp", "pg"):
+        raise ValueError("algorithm is 'fastpfp' or 'pg'")
     prm = orc_params(float(lam), float(alpha), float(tol_outer), float(tol_inner), int(max_outer),
-                     int(max_inner), int(bool(normalize_max)), int(slack_policy))
+                     int(max_inner), int(bool(normalize_max)), int(slack_policy),
+                     1 if algorithm == "pg" else 0)
     cap = max(int(max_outer), int(replay_outer))
     X0p = None
     if X0 is not None:

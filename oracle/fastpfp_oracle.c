@@ -21,6 +21,9 @@
  *   orc_greedy_*                 pinned (each other, Hungarian on separable cases)
  *   orc_*_objective              pinned (brute force, Appendix identity)
  *   orc_solve                    pinned (exact recovery, brute force on N<=7)
+ *   orc_solve, algorithm = PG    pinned (a feasible point is fixed at alpha = 0;
+ *                                linear objective -> its assignment optimum;
+ *                                relabelling equivariance)
  * The inner cap I_1, the slack carry-over and the comparison details are
  * readings of an underspecified paper; those choices are "parity unpinned".
  */
@@ -322,7 +325,11 @@ double orc_relaxed_objective(const double* A, const double* A2, const double* K,
 }
 
 /* Algorithm 1 with the initialisation recommended after it
- * (X = 1 1^T / (n n'), Y = 0) and the stopping rules of Section 5. */
+ * (X = 1 1^T / (n n'), Y = 0) and the stopping rules of Section 5.  With
+ * algorithm = 1 the same loop runs the projected gradient method of
+ * Eq. (pg) instead: Y_{1:n,1:n'} = X + alpha (A X A' + lambda K), then
+ * X = P_d(.) = P_D(Y)_{1:n,1:n'} (the slack columns handled as for
+ * FastPFP), optionally normalised by its maximum. */
 int orc_solve(const double* A_in, int n_a, const double* A2_in, int n_b,
               const double* B_in, const double* B2_in, int k,
               const orc_params* p, const double* X0,
@@ -363,16 +370,20 @@ int orc_solve(const double* A_in, int n_a, const double* A2_in, int n_b,
     int t = 0, converged = 0, inner_total = 0, inner_max = 0;
     double delta = 0.0;
     while (t < outer_cap) {
-        /* Y_{1:n,1:n'} = A X A' + lambda K */
+        /* Y_{1:n,1:n'} = A X A' + lambda K (FastPFP) or X + alpha (A X A' + lambda K) (PG) */
         orc_gradient(A, X, A2, K, p->lambda, N, m, G);
+        const int pg = p->algorithm == 1;
         for (int i = 0; i < N; ++i) {
-            for (int j = 0; j < m; ++j) Y[(size_t)i * N + j] = G[(size_t)i * m + j];
+            for (int j = 0; j < m; ++j)
+                Y[(size_t)i * N + j] = pg ? X[(size_t)i * m + j] + p->alpha * G[(size_t)i * m + j]
+                                          : G[(size_t)i * m + j];
             if (p->slack_policy == 1)
                 for (int j = m; j < N; ++j) Y[(size_t)i * N + j] = 0.0;
         }
         const int fixed = replay_inner ? replay_inner[t] : 0;
         const int inner = orc_pd(Y, N, p->tol_inner, p->max_inner, fixed, NULL);
-        delta = orc_blend(X, Y, N, m, p->alpha, p->normalize_max);
+        /* FastPFP blends; PG takes the projection itself (a blend with weight 1) */
+        delta = orc_blend(X, Y, N, m, pg ? 1.0 : p->alpha, p->normalize_max);
         if (inner_trace) inner_trace[t] = inner;
         if (delta_trace) delta_trace[t] = delta;
         inner_total += inner;

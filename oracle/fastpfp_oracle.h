@@ -29,6 +29,8 @@ typedef struct {
     int max_inner;      /* I_1: at most this many inner iterations (Sec. 5)     */
     int normalize_max;  /* 1: X <- X / max(X) each outer iteration (Alg. 1)     */
     int slack_policy;   /* 0: slack columns of Y carry over (Alg. 1), 1: reset  */
+    int algorithm;      /* 0: FastPFP, Eq. (fastPFP); 1: projected gradient,
+                           Eq. (pg): X <- P_d(X + alpha (A X A' + lambda K))  */
 } orc_params;
 
 typedef struct {

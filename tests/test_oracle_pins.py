@@ -350,3 +350,67 @@ def test_thread_count_does_not_change_results():
     finally:
         oracle.set_num_threads(n0)
     np.testing.assert_array_equal(a["X"], b["X"])
+
+
+# ------------------------------------ projected gradient, Eq. (pg)
+
+def _random_doubly_stochastic(rng, n, terms=4):
+    """A convex combination of permutation matrices (Birkhoff)."""
+    w = rng.random(terms)
+    w /= w.sum()
+    X = np.zeros((n, n))
+    for c in w:
+        X[np.arange(n), rng.permutation(n)] += c
+    return X
+
+
+def test_pg_zero_step_keeps_a_feasible_point():
+    """Eq. (pg) with alpha = 0 is X <- P_d(X): a doubly stochastic X is its
+    own projection, so the first iterate equals X(0) (a method that dropped
+    the X term would return the uniform matrix instead)."""
+    rng = np.random.default_rng(31)
+    n = 6
+    A, A2 = _sym(rng, n), _sym(rng, n)
+    X0 = _random_doubly_stochastic(rng, n)
+    r = oracle.solve(A, A2, alpha=0.0, X0=X0, normalize_max=False, max_outer=1, tol_inner=1e-13,
+                     max_inner=50, algorithm="pg")
+    np.testing.assert_allclose(r["X"], X0, atol=1e-12)
+    assert r["delta"][0] <= 1e-12
+
+
+@pytest.mark.parametrize("N,m", [(7, 7), (9, 6)])
+def test_pg_on_a_linear_objective_reaches_the_assignment_optimum(N, m):
+    """With A = A' = 0 the objective is lambda tr(X^T K) and Eq. (pg) is
+    projected gradient ascent of a linear function: its iterates settle on
+    the optimal vertex, the linear assignment maximum (scipy), as a 0/1
+    matrix — FastPFP's blend of the same gradient would settle on the soft
+    projection P_d(lambda K) instead."""
+    from scipy.optimize import linear_sum_assignment
+    rng = np.random.default_rng(N * 10 + m)
+    B, B2 = rng.normal(size=(N, 4)), rng.normal(size=(m, 4))
+    K = B @ B2.T
+    r = oracle.solve(np.zeros((N, N)), np.zeros((m, m)), B, B2, lam=1.0, alpha=1.0, normalize_max=False,
+                     max_outer=300, tol_outer=1e-12, tol_inner=1e-12, max_inner=2000, algorithm="pg")
+    rows, cols = linear_sum_assignment(K, maximize=True)
+    P = np.zeros((N, m))
+    P[rows, cols] = 1.0
+    assert np.abs(r["X"] - P).max() < 1e-6
+    expect = np.full(N, -1, dtype=np.int32)
+    expect[rows] = cols
+    assert (r["perm"] == expect).all()
+
+
+def test_pg_is_equivariant_under_relabelling():
+    """Relabelling graph 2's nodes by q (A2 -> A2[q][:, q], B2 -> B2[q])
+    relabels the columns of every PG iterate the same way (the uniform start
+    is invariant): catches a transposed operand or a mixed-up index."""
+    rng = np.random.default_rng(33)
+    n = 9
+    g = synth.graph_pair(n, p=0.4, sigma=0.05, k=3, lam=0.5, seed=4)
+    q = rng.permutation(n)
+    kw = dict(lam=0.5, alpha=0.02, normalize_max=False, max_outer=6, tol_outer=0.0, tol_inner=1e-12,
+              max_inner=400, algorithm="pg")
+    r = oracle.solve(g.A, g.A2, g.B, g.B2, **kw)
+    rq = oracle.solve(g.A, g.A2[q][:, q], g.B, g.B2[q], **kw)
+    np.testing.assert_allclose(rq["X"], r["X"][:, q], atol=1e-10)
+    np.testing.assert_allclose(rq["delta"], r["delta"], rtol=1e-8, atol=1e-12)
