@@ -197,12 +197,31 @@ def make_pairs(workload: str, rank: int, batch: int):
     raise ValueError(workload)
 
 
-def params(F, lam, profile=0, precision="fp32", loop_mode=0):
+def params(F, lam, profile=0, precision="fp32", loop_mode=0, pg_alpha=None):
     """The workload's parameters.  bf16: tensor-core products until
-    max|dX| < 1e-3, then FP32 iterations (at most 30) to convergence."""
+    max|dX| < 1e-3, then FP32 iterations (at most 30) to convergence.
+    pg_alpha: the projected gradient method of Eq. (pg) with that step and
+    no normalisation instead of FastPFP."""
     low = {"bf16": F.BF16, "fp8": F.FP8}.get(precision)
     extra = dict(precision=low, refine_iters=30, switch_tol=1e-3) if low is not None else {}
-    return F.default_params(lam=lam, profile=profile, loop_mode=loop_mode, **SOLVER, **extra)
+    solver = dict(SOLVER)
+    if pg_alpha is not None:
+        solver.update(alpha=pg_alpha)
+        extra.update(algorithm=F.ALG_PG, normalize_max=0)
+    return F.default_params(lam=lam, profile=profile, loop_mode=loop_mode, **solver, **extra)
+
+
+def pg_step(pairs) -> float:
+    """Step of the projected gradient method: 1 / L with L = ||A||_2 ||A'||_2
+    the Lipschitz constant of the gradient A X A' + lambda K (largest over the
+    pairs; spectral norms by power iteration on the host)."""
+    def norm2(a):
+        v = np.ones(a.shape[0]) / np.sqrt(a.shape[0])
+        for _ in range(60):
+            w = a @ v
+            v = w / np.linalg.norm(w)
+        return float(np.linalg.norm(a @ v))
+    return 1.0 / max(norm2(g.A) * norm2(g.A2) for g in pairs[:4])
 
 
 def canon_shape(g):
@@ -360,6 +379,8 @@ def main():
     ap.add_argument("--train-pairs", type=int, default=2000, dest="train_pairs")
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="outer loop: CUDA-graph while node (default) or host-polled chunks")
+    ap.add_argument("--algorithm", default="fastpfp", choices=["fastpfp", "pg"],
+                    help="FastPFP (Eq. fastPFP), or the projected gradient method of Eq. (pg) with step 1/L")
     ap.add_argument("--no-autotune", action="store_true", dest="no_autotune",
                     help="keep the default GEMM tiles instead of timing both per size class")
     args = ap.parse_args()
@@ -418,8 +439,9 @@ def main():
         return solver.match_batched([dp + (x,) for dp, x in zip(dpairs, x0)], params=prm)
 
     loop_mode = 0 if args.loop == "graph" else 1
-    p_plain = params(F, lam, precision=args.precision, loop_mode=loop_mode)
-    p_prof = params(F, lam, profile=1, precision=args.precision)
+    pg_alpha = pg_step(pairs) if args.algorithm == "pg" else None
+    p_plain = params(F, lam, precision=args.precision, loop_mode=loop_mode, pg_alpha=pg_alpha)
+    p_prof = params(F, lam, profile=1, precision=args.precision, pg_alpha=pg_alpha)
     # host loop: the timed steps carry the per-launch CUDA events themselves;
     # graph loop: the timed steps run the graph, and one instrumented pass of
     # the same batch right after them times every projection launch
@@ -557,6 +579,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "bf16": "bf16+f32", "fp8": "e4m3+f32"}[args.precision], "data": "synthetic",
             "config": dict(workload=args.workload, **cfg, **SOLVER, pairs_per_step=args.batch,
+                           algorithm=args.algorithm if pg_alpha is None else f"pg (alpha = 1/L = {pg_alpha:.3g}, "
+                                                                              "no normalisation)",
                            precision=args.precision, loop=args.loop, init=args.init,
                            gemm_tiles=dict(tiles, source="default" if args.no_autotune else "autotuned"),
                            l2="flushed (512 MB write) before every timed step",

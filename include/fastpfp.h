@@ -59,6 +59,7 @@ extern "C" {
  * once per solve, X^T (through a BF16 copy) and T = A X (through its BF16
  * result) before each product. */
 enum { FASTPFP_FP32 = 0, FASTPFP_BF16 = 1, FASTPFP_FP8 = 2 };
+enum { FASTPFP_ALG_FASTPFP = 0, FASTPFP_ALG_PG = 1 };
 
 typedef struct fastpfp_s* fastpfp_t;
 
@@ -98,6 +99,11 @@ typedef struct {
                               every wait of that launch runs out after timeout_ms and the call
                               returns FASTPFP_ERR_TIMEOUT (exercises failure detection without
                               faulting or hanging the device)                                 */
+    int algorithm;         /* FASTPFP_ALG_FASTPFP (default): Eq. (fastPFP),
+                              X <- (1 - alpha) X + alpha P_d(A X A' + lambda K);
+                              FASTPFP_ALG_PG: the projected gradient method of Eq. (pg),
+                              X <- P_d(X + alpha (A X A' + lambda K)) (normalize_max applies to
+                              both)                                                          */
 } fastpfp_params;
 
 /* Statistics of one solve (in the canonical orientation). */

@@ -156,6 +156,7 @@ bool params_ok(const fastpfp_params* p) {
         return false;
     if (p->refine_iters < 0) return false;
     if (p->loop_mode != 0 && p->loop_mode != 1) return false;
+    if (p->algorithm != FASTPFP_ALG_FASTPFP && p->algorithm != FASTPFP_ALG_PG) return false;
     return true;
 }
 
@@ -273,6 +274,12 @@ void f32_products(const Slot& sl, const Problem& q, const fastpfp_params* p, Gem
     *g1 = GemmF32TArgs{sl.X, ldx, A, lda, sl.T, ldt, nullptr, 0, 0.f, q.m, q.N, q.N, sl.ctrl};
     *g2 = GemmF32TArgs{sl.T, ldt, A2, lda2, sl.Y, ldy, q.k ? sl.K : nullptr, ldx,
                        q.k ? (float)p->lambda : 0.f, q.N, q.m, q.m, sl.ctrl};
+    if (p->algorithm == FASTPFP_ALG_PG) {   // Y[:, :m] = X + alpha (T A' + lambda K), Eq. (pg)
+        g2->addend = sl.X;
+        g2->ld_add = ldx;
+        g2->scale = p->alpha;
+        g2->lambda *= p->alpha;
+    }
 }
 
 int enqueue_gradient(const Slot& sl, cudaStream_t s, const Problem& q, const fastpfp_params* p, int tile_m) {
@@ -344,6 +351,15 @@ bool plan_tc(fastpfp_t h, const Problem* qs, int count, const fastpfp_params* p,
             a.prob[i] = TcProblem{q.N, q.m, q.N, sl.T16, l16m, nullptr, 0, 0.f, sl.ctrl, &sl.ctrl->error};
             c.prob[i] = TcProblem{q.N, q.m, q.m, sl.Y, round4(q.N), q.k ? sl.K : nullptr, round4(q.m),
                                   q.k ? (float)p->lambda : 0.f, sl.ctrl, &sl.ctrl->error};
+        }
+        if (p->algorithm == FASTPFP_ALG_PG) {   // Y[:, :m] = X + alpha (T A' + lambda K), Eq. (pg)
+            for (int i = 0; i < n; ++i) {
+                const Slot& sl = h->slots[slot_of ? slot_of[b + i] : b + i];
+                c.prob[i].addend = sl.X;
+                c.prob[i].ld_add = round4(qs[b + i].m);
+                c.prob[i].scale = p->alpha;
+                c.prob[i].lambda *= p->alpha;
+            }
         }
         plan->g1.push_back(a);
         plan->g2.push_back(c);
@@ -494,7 +510,7 @@ int enqueue_single(fastpfp_t h, cudaStream_t s, const Slot& sl, const Problem& q
     P.ldx = ldx;
     P.Xt16 = lowp ? sl.Xt16 : nullptr;
     P.ldxt = round8(N);
-    P.alpha = p->alpha;
+    P.alpha = p->algorithm == FASTPFP_ALG_PG ? 1.0f : p->alpha;   // PG keeps the projection itself
     P.normalize = p->normalize_max ? 1 : 0;
     P.slack_reset = p->slack_policy == 1 ? 1 : 0;
     P.tol_inner = p->tol_inner;
@@ -800,7 +816,7 @@ PdbParams wave_params(fastpfp_t h, const Wave& w, int npairs, const fastpfp_para
     P.band_row = h->d_band;
     P.wave = h->d_wave;
     P.layout = w.layout;
-    P.alpha = p->alpha;
+    P.alpha = p->algorithm == FASTPFP_ALG_PG ? 1.0f : p->alpha;   // PG keeps the projection itself
     P.normalize = p->normalize_max ? 1 : 0;
     P.slack_reset = p->slack_policy == 1 ? 1 : 0;
     P.tol_inner = p->tol_inner;
@@ -925,6 +941,7 @@ void fastpfp_default_params(fastpfp_params* p) {
     p->profile = 0;
     p->loop_mode = 0;
     p->debug_flags = 0;
+    p->algorithm = FASTPFP_ALG_FASTPFP;
 }
 
 const char* fastpfp_error_string(int code) {

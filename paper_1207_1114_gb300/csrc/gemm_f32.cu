@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(kThreads) gemm_f32t_kernel(const __grid_consta
             if (c >= g.Nc) continue;
             const unsigned long long pr = acc[i][j >> 1];
             float v = __uint_as_float((unsigned)((j & 1) ? (pr >> 32) : (pr & 0xffffffffull)));
+            if (g.addend) v = fmaf(g.scale, v, __ldg(g.addend + (size_t)r * g.ld_add + c));
             if (g.Kmat) v = fmaf(g.lambda, __ldg(g.Kmat + (size_t)r * g.ldk + c), v);
             g.C[(size_t)r * g.ldc + c] = v;
         }

@@ -212,6 +212,12 @@ __device__ __forceinline__ void drain_tile(const TcGroup& G, const TcProblem& pr
         } else {
             float* out = reinterpret_cast<float*>(pr.out) + (size_t)row * pr.ldo + col;
             const float* kk = pr.Kmat ? pr.Kmat + (size_t)row * pr.ldk + col : nullptr;
+            if (pr.addend) {   // projected gradient step: addend + scale * acc
+                const float* ad = pr.addend + (size_t)row * pr.ld_add + col;
+#pragma unroll
+                for (int v = 0; v < 32; ++v)
+                    if (v < nv) r[v] = __float_as_uint(fmaf(pr.scale, __uint_as_float(r[v]), __ldg(ad + v)));
+            }
             if (nv == 32) {
 #pragma unroll
                 for (int v = 0; v < 8; ++v) {

@@ -193,6 +193,11 @@ struct TcProblem {
     int* err;             // nullable: receives FASTPFP_ERR_TIMEOUT
     const float* rs;      // nullable: per-row output scale (M entries)
     const float* cs;      // nullable: per-column output scale (N entries)
+    // FP32 mode, nullable: out = addend + scale * acc + lambda K (the step of
+    // the projected gradient method); leading dimension ld_add
+    const float* addend;
+    int ld_add;
+    float scale;
 };
 struct TcGroup {
     CUtensorMap map_a[kTcMaxGroup];
@@ -249,6 +254,9 @@ struct GemmF32TArgs {
     const float* Kmat; int ldk; float lambda;
     int M, Nc, K;
     const Ctrl* ctrl;
+    // nullable: C = addend + scale * (AT^T B) + lambda * Kmat (the step of
+    // the projected gradient method); leading dimension ld_add
+    const float* addend; int ld_add; float scale;
 };
 struct GemmF32TGroup {
     GemmF32TArgs a[kF32MaxGroup];

@@ -722,3 +722,47 @@ def test_gemm_probe_orders_the_product_kernels():
     assert 1.0 < fp8 < 4500.0
     with pytest.raises(F.FastPFPError):
         F.gemm_probe(F.BF16, n=1000)
+
+
+# ------------------------------------------- projected gradient, Eq. (pg)
+
+def _check_pg(solver, pairs, lam, alpha, **kw):
+    """Every pair of one batched PG solve against the oracle replaying that
+    pair's inner counts (X max-abs 1e-4, objective relative 1e-5)."""
+    p = F.default_params(lam=lam, alpha=alpha, algorithm=F.ALG_PG, **kw)
+    dev = [(cu(g.A), cu(g.A2), cu(g.B) if g.k else None, cu(g.B2) if g.k else None) for g in pairs]
+    outs = solver.match_batched(dev, params=p, want_X=True)
+    for i, (g, o) in enumerate(zip(pairs, outs)):
+        inner, _ = solver.last_trace(pair=i)
+        assert o.stats.status == 0 and len(inner) == o.stats.outer_iters
+        r = oracle.solve(g.A, g.A2, g.B, g.B2, lam=lam, alpha=alpha, replay_inner=inner,
+                         replay_outer=o.stats.outer_iters, algorithm="pg", **kw)
+        assert np.abs(o.X.cpu().numpy() - r["X"]).max() <= 1e-4
+        assert abs(o.stats.objective - r["objective"]) <= 1e-5 * abs(r["objective"])
+    return outs
+
+
+def test_pg_single_pair_matches_oracle(solver):
+    """Eq. (pg) on one attributed pair with outliers: the gradient epilogue
+    forms X + alpha (A X A' + lambda K), the projection keeps P_d of it."""
+    g = synth.graph_pair(60, p=0.3, sigma=0.02, k=3, n_out=8, lam=0.5, seed=5)
+    outs = _check_pg(solver, [g], 0.5, 0.05, normalize_max=False, max_outer=40, max_inner=300)
+    assert outs[0].stats.converged == 1
+
+
+def test_pg_wave_of_uneven_pairs_matches_oracle(solver):
+    pairs = synth.batch_mixed(count=5, seed=17, n_lo=20, n_hi=150, out_hi=20)
+    _check_pg(solver, pairs, 0.5, 0.05, normalize_max=False, max_outer=25, max_inner=250)
+
+
+def test_pg_bf16_phase_then_fp32_refinement(solver):
+    """PG with the BF16 tensor-core products (the epilogue adds X in FP32)
+    and FP32 refinement ends at the plain FP32 PG solve's objective."""
+    pairs = synth.batch_mixed(count=4, seed=19, n_lo=100, n_hi=300, out_hi=30)
+    dev = [(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)) for g in pairs]
+    kw = dict(lam=0.5, alpha=0.01, algorithm=F.ALG_PG, normalize_max=0)
+    o16 = solver.match_batched(dev, params=F.default_params(precision=F.BF16, refine_iters=40, **kw))
+    o32 = solver.match_batched(dev, params=F.default_params(**kw))
+    for a, b in zip(o16, o32):
+        assert a.stats.status == 0 and a.stats.lowp_iters >= 1
+        assert abs(a.stats.objective - b.stats.objective) <= 1e-4 * abs(b.stats.objective)
