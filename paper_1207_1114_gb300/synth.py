@@ -136,3 +136,36 @@ def warm_start_train(count: int, seed: int = 0, n_lo: int = 200, n_hi: int = 800
     return [graph_pair(int(n), p=0.1, sigma=0.03, k=15, attr_sigma=0.05,
                        n_out=int(rng.integers(0, int(n) // 5 + 1)), lam=0.5,
                        seed=seed * 1000003 + b + 1) for b, n in enumerate(ns)]
+
+
+def e1_pair(n: int, case: str, seed: int = 0) -> GraphPair:
+    """Section 5.1's synthetic random graphs: unweighted, each pair {i, j} an
+    edge with probability 1/2, and graph 2 a hidden relabelling of graph 1
+    with (case 'a') no change, ('b') n edge editions — n distinct pairs
+    {i, j} whose edge is flipped (present <-> absent) —, ('c') 10 % of the
+    nodes deleted (floor(n / 10) nodes; subgraph isomorphism), or ('d')
+    both.  gt[i] is node i's label in graph 2, -1 for a deleted node.  No
+    attributes (lambda = 0)."""
+    if case not in ("a", "b", "c", "d"):
+        raise ValueError("case is one of 'a', 'b', 'c', 'd'")
+    rng = np.random.default_rng(seed)
+    up = np.triu(rng.random((n, n)) < 0.5, 1)
+    A = (up | up.T).astype(np.float32)
+    A2 = A.copy()
+    if case in ("b", "d"):
+        iu, ju = np.triu_indices(n, 1)
+        pick = rng.choice(len(iu), size=min(n, len(iu)), replace=False)
+        i, j = iu[pick], ju[pick]
+        A2[i, j] = 1.0 - A2[i, j]
+        A2[j, i] = A2[i, j]
+    keep = np.arange(n)
+    if case in ("c", "d"):
+        keep = np.sort(rng.choice(n, size=n - n // 10, replace=False))
+    A2 = A2[np.ix_(keep, keep)]
+    m = len(keep)
+    label = rng.permutation(m)           # node keep[t] of graph 1 is node label[t] of graph 2
+    A2p = np.zeros_like(A2)
+    A2p[np.ix_(label, label)] = A2
+    gt = np.full(n, -1, dtype=np.int32)
+    gt[keep] = label
+    return GraphPair(A, A2p, np.zeros((n, 0), np.float32), np.zeros((m, 0), np.float32), gt, 0.0)
