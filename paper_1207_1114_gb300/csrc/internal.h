@@ -57,7 +57,7 @@ cudaError_t pd_launch(const PdLaunch& L, const PdParams& P, cudaStream_t s);
 // -------------------------------------------------- batched projection
 constexpr int kPdbThreads = 512;     // CTA size of the batched kernel
 constexpr int kMaxSeg = 32;          // pairs one CTA band may span
-constexpr int kMaxWavePairs = 64;    // pairs of one cooperative launch
+constexpr int kMaxWavePairs = 128;   // pairs of one cooperative launch
 constexpr int kPdbMaxN = 4096;       // widest pair (two column quads per thread)
 
 // One pair of a wave (device-resident table, read-only in the kernel).

@@ -449,11 +449,11 @@ def test_streamed_host_batch_equals_device_batch(stream_solver):
         _same_solve(a, b, a.X.cpu().numpy(), b.X)
 
 
-def test_streamed_mixed_batch_of_100(stream_solver):
-    """100 mixed pairs (n in 50..600, up to 100 outliers): more pairs than
-    one wave holds.  Every pair returns a valid partial permutation; sampled
-    pairs match the oracle replay."""
-    pairs = synth.batch_mixed(count=100, seed=7, n_lo=50, n_hi=600, out_hi=100)
+def test_streamed_mixed_batch_of_120(stream_solver):
+    """120 mixed pairs (n in 200..600, up to 100 outliers): more than one
+    wave holds on chip.  Every pair returns a valid partial permutation;
+    sampled pairs match the oracle replay."""
+    pairs = synth.batch_mixed(count=120, seed=7, n_lo=200, n_hi=600, out_hi=100)
     kw = dict(max_outer=30, max_inner=200)
     p = F.default_params(lam=0.5, **kw)
     dev = [(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)) for g in pairs]
@@ -466,7 +466,7 @@ def test_streamed_mixed_batch_of_100(stream_solver):
         used = perm[perm >= 0]
         assert len(np.unique(used)) == len(used) and (used < n_b).all()
         assert len(used) == min(n_a, n_b)
-    for i in (0, 37, 99):
+    for i in (0, 57, 119):
         _replay_check(stream_solver, pairs[i], outs[i], i, 0.5, **kw)
 
 
