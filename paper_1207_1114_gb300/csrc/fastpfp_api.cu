@@ -602,9 +602,9 @@ struct BandStats {
 
 // Band cost model of pdb_kernel, in entry equivalents: a band costs its
 // entries plus kSegCost for every pair it spans (a segment brings its own
-// loop tails, reductions and read-back; measured on GB300 at about 1800
-// cycles against 0.115 cycles per entry).
-constexpr long long kSegCost = 16384;
+// loop tails, reductions and read-back; measured on GB300 by clock stamps
+// at 2500-2750 cycles against 0.07-0.09 cycles per entry of a pass).
+constexpr long long kSegCost = 32768;
 
 // Greedy cut of the concatenated rows of pairs [first, first + count) into
 // consecutive bands of cost at most C: each band takes as many rows as fit.
@@ -719,7 +719,10 @@ bool plan_bands(const std::vector<Problem>& qs, int first, int count, int num_sm
     long long rows = 0;
     for (int i = 0; i < count; ++i) rows += qs[first + i].N;
     const int t2 = rows >= (long long)kTwoQuadRowsPerCta * Gmax ? 1 : 0;
-    for (const long long seg_cost : {kSegCost, 0ll}) {
+    // the measured segment cost first, then cheaper ones when that plan does
+    // not fit on chip (pair-aligned bands hold more entries), finally pure
+    // entry balance
+    for (const long long seg_cost : {kSegCost, kSegCost / 2, kSegCost / 4, 0ll}) {
         std::vector<int> b0(Gmax + 1), b1(Gmax + 1);
         std::vector<BandStats> s0, s1;
         const int u0 = split_group(qs, first, split, Gmax, seg_cost, t2, b0.data(), s0);

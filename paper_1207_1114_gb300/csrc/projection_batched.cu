@@ -60,7 +60,7 @@ struct Shared {
     PairS* pair;         // kMaxWavePairs
     int* pstate;         // kMaxWavePairs: bit0 active this launch, bit1 stopped
     int* pstop;          // kMaxWavePairs: round at which the pair stopped
-    int* ictl;           // [0],[1] group has an active pair, [2] n segments, [3] non-finite
+    int* ictl;           // [2] n segments, [3] non-finite, [4],[5] running pairs of group 0 / 1
     int* qpref;          // 2 x (kMaxWavePairs + 1): per group, prefix sums of the pairs' column quads
     float* fred;         // kMaxSeg x 32 per-warp maxima
     float* rsum;         // band rows
@@ -659,6 +659,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     // added in FP32 and accumulated over the CTAs in FP64.
     auto publish = [&](int g, int cur, int clear_which) {
         __syncthreads();
+        if (tid == 0) S.ictl[4 + g] = 0;   // the running-pair count of wait_post
         if (warp < 2) {
             for (int si = warp; si < nseg; si += 2) {
                 const Seg sg = S.seg[si];
@@ -706,31 +707,31 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             float4* dst = reinterpret_cast<float4*>(S.cN + sg.coff);
             for (int q = tid; q < (pr.ldy >> 2); q += nthr) cp_async_cg16(dst + q, c + q);
         }
-        if (warp == 0) {
-            const int p0 = g == 0 ? 0 : split, p1 = g == 0 ? split : npairs;
-            int any = 0;
-            for (int p = p0 + lane; p < p1; p += 32) {
-                int ps = S.pstate[p];
-                if ((ps & 1) && !(ps & 2)) {
-                    PairS& pr = S.pair[p];
-                    const double s = __ldcg(pr.sbuf + cur);
-                    const float dd = __uint_as_float(__ldcg(pr.dbuf + cur));
-                    const double invN = pr.invN;
-                    pr.s = s;
-                    pr.abase = (float)(invN + s * invN * invN);
-                    if (!isfinite(s)) S.ictl[3] = 1;
-                    if (check_stop && ((double)dd < P.tol_inner || u >= P.max_inner)) {
-                        ps |= 2;
-                        S.pstop[p] = u;
-                    }
-                    S.pstate[p] = ps;
-                    any |= !(ps & 2);
+        // the group's pairs, one per thread of the first four warps (their
+        // totals come from L2: one round trip for up to 128 pairs)
+        const int p0 = g == 0 ? 0 : split, p1 = g == 0 ? split : npairs;
+        int any = 0;
+        for (int p = p0 + tid; p < p1 && tid < 128; p += 128) {
+            int ps = S.pstate[p];
+            if ((ps & 1) && !(ps & 2)) {
+                PairS& pr = S.pair[p];
+                const double s = __ldcg(pr.sbuf + cur);
+                const float dd = __uint_as_float(__ldcg(pr.dbuf + cur));
+                const double invN = pr.invN;
+                pr.s = s;
+                pr.abase = (float)(invN + s * invN * invN);
+                if (!isfinite(s)) S.ictl[3] = 1;
+                if (check_stop && ((double)dd < P.tol_inner || u >= P.max_inner)) {
+                    ps |= 2;
+                    S.pstop[p] = u;
                 }
+                S.pstate[p] = ps;
+                any |= !(ps & 2);
             }
-            any = __any_sync(0xffffffffu, any);
-            __syncwarp();
-            if (lane == 0) S.ictl[g] = any;
         }
+        // ictl[4 + g] counts the group's pairs still running (zeroed in publish)
+        any = __any_sync(0xffffffffu, any);
+        if (warp < 4 && lane == 0 && any) atomicAdd(&S.ictl[4 + g], 1);
         cp_async_wait_all();
         __syncthreads();
         return true;
@@ -753,7 +754,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         if (tid == 0) atomicCAS(err, 0, FASTPFP_ERR_NONFINITE);
         return;
     }
-    bool act0 = S.ictl[0] != 0, act1 = has1 && S.ictl[1] != 0, pend1 = false;
+    bool act0 = S.ictl[4] != 0, act1 = has1 && S.ictl[5] != 0, pend1 = false;
 
     // ---- the rounds, group 1 one half-step behind group 0
     int u = 0;
@@ -765,7 +766,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         }
         if (pend1) {
             if (!wait_post(1, (u - 1) % 3, u - 1, true)) return;
-            act1 = S.ictl[1] != 0;
+            act1 = S.ictl[5] != 0;
             pend1 = false;
         }
         if (act1) {
@@ -775,7 +776,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         }
         if (act0) {
             if (!wait_post(0, u % 3, u, true)) return;
-            act0 = S.ictl[0] != 0;
+            act0 = S.ictl[4] != 0;
         }
     }
 
