@@ -606,6 +606,14 @@ struct BandStats {
 // at 2500-2750 cycles against 0.07-0.09 cycles per entry of a pass).
 constexpr long long kSegCost = 32768;
 
+// Pairs join a wave only while its bands can still be cut with at least
+// this segment-cost level (0 = kSegCost, 1 = half of it, ...): a wave filled
+// until only pure entry balance fits leaves the CTAs that span several pairs
+// slower than the rest, and every grid barrier waits for them.  Measured:
+// level 0 gives the 512-pair mixed batch 451 pair-solves/s against 405 with
+// no limit, and n = 1000 waves 153 against 148.
+constexpr int kAdmitLevel = 0;
+
 // Greedy cut of the concatenated rows of pairs [first, first + count) into
 // consecutive bands of cost at most C: each band takes as many rows as fit.
 // Writes the boundaries to band[0..] (when band != nullptr) and returns the
@@ -701,7 +709,8 @@ int split_group(const std::vector<Problem>& qs, int first, int count, int G, lon
 // per-segment cost (pair-aligned where possible), then fall back to pure
 // entry balance if that does not fit in shared memory.  Returns false when a
 // CTA's bands would not fit.
-bool plan_bands(const std::vector<Problem>& qs, int first, int count, int num_sms, Wave* w) {
+bool plan_bands(const std::vector<Problem>& qs, int first, int count, int num_sms, Wave* w,
+                int max_level = 3) {
     long long E = 0;
     for (int i = 0; i < count; ++i) E += (long long)qs[first + i].N * round4(qs[first + i].N);
     int split = count;
@@ -722,7 +731,9 @@ bool plan_bands(const std::vector<Problem>& qs, int first, int count, int num_sm
     // the measured segment cost first, then cheaper ones when that plan does
     // not fit on chip (pair-aligned bands hold more entries), finally pure
     // entry balance
-    for (const long long seg_cost : {kSegCost, kSegCost / 2, kSegCost / 4, 0ll}) {
+    const long long levels[4] = {kSegCost, kSegCost / 2, kSegCost / 4, 0ll};
+    for (int lv = 0; lv <= max_level && lv < 4; ++lv) {
+        const long long seg_cost = levels[lv];
         std::vector<int> b0(Gmax + 1), b1(Gmax + 1);
         std::vector<BandStats> s0, s1;
         const int u0 = split_group(qs, first, split, Gmax, seg_cost, t2, b0.data(), s0);
@@ -763,7 +774,7 @@ bool plan_wave(const std::vector<Problem>& qs, int first, int nslots, int num_sm
     const int limit = std::min<int>({(int)qs.size() - first, nslots, kMaxWavePairs});
     for (int c = 1; c <= limit; ++c) {
         if (qs[first + c - 1].N > kPdbMaxN) break;
-        if (!plan_bands(qs, first, c, num_sms, &cand)) break;
+        if (!plan_bands(qs, first, c, num_sms, &cand, c == 1 ? 3 : kAdmitLevel)) break;
         *w = cand;
         best = c;
     }
@@ -1266,7 +1277,7 @@ int solve_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, const fa
             problems_of(act, cand, cand_slots);
             cand.push_back(qs[next]);
             Wave cw;
-            if (!plan_bands(cand, 0, (int)cand.size(), h->num_sms, &cw)) break;
+            if (!plan_bands(cand, 0, (int)cand.size(), h->num_sms, &cw, act.empty() ? 3 : kAdmitLevel)) break;
             const int slot = free_slots.back();
             free_slots.pop_back();
             if (host) {
