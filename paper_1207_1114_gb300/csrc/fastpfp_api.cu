@@ -611,7 +611,10 @@ constexpr long long kSegCost = 32768;
 // until only pure entry balance fits leaves the CTAs that span several pairs
 // slower than the rest, and every grid barrier waits for them.  Measured:
 // level 0 gives the 512-pair mixed batch 451 pair-solves/s against 405 with
-// no limit, and n = 1000 waves 153 against 148.
+// no limit, and streamed n = 1000 batches 153 against 148.  A batch that
+// fits in one wave as a whole (plan_wave) takes any plan instead: splitting
+// it would leave a tail wave of a few pairs (17 pairs of n = 1000: 117
+// against 146 pair-solves/s).
 constexpr int kAdmitLevel = 0;
 
 // Greedy cut of the concatenated rows of pairs [first, first + count) into
@@ -774,7 +777,7 @@ bool plan_wave(const std::vector<Problem>& qs, int first, int nslots, int num_sm
     const int limit = std::min<int>({(int)qs.size() - first, nslots, kMaxWavePairs});
     for (int c = 1; c <= limit; ++c) {
         if (qs[first + c - 1].N > kPdbMaxN) break;
-        if (!plan_bands(qs, first, c, num_sms, &cand, c == 1 ? 3 : kAdmitLevel)) break;
+        if (!plan_bands(qs, first, c, num_sms, &cand)) break;
         *w = cand;
         best = c;
     }
