@@ -659,9 +659,12 @@ int cut_rows(const std::vector<Problem>& qs, int first, int count, long long C, 
 // Cuts pairs [first, first + count) into at most G bands minimising the
 // largest band cost (binary search on the cost bound over cut_rows).
 // band[0..used] holds the row boundaries, band[used..G] = total rows.
-// Returns the number of bands used.
+// tcol[b] (G entries) holds the TMEM columns band b's CTA has already given
+// to earlier segments — the kernel places group 1's segments after group
+// 0's — and receives the columns used after this group.  Returns the number
+// of bands used.
 int split_group(const std::vector<Problem>& qs, int first, int count, int G, long long seg_cost,
-                int two_quad_ties, int* band, std::vector<BandStats>& st) {
+                int two_quad_ties, int* band, std::vector<BandStats>& st, std::vector<int>& tcol) {
     long long lo = 1, hi = 0;
     int rows = 0;
     for (int i = 0; i < count; ++i) {
@@ -683,7 +686,7 @@ int split_group(const std::vector<Problem>& qs, int first, int count, int G, lon
     // per-band statistics; the first rows of every row group go to TMEM
     // (pdb_tmem_rows, segments in pair order as the kernel places them), so
     // elems counts the floats left in shared memory
-    std::vector<int> tcol(G, 0);
+    tcol.resize(G, 0);
     int b = 0, gr = 0;
     for (int i = 0; i < count; ++i) {
         const int N = qs[first + i].N, ldy = round4(N);
@@ -739,8 +742,9 @@ bool plan_bands(const std::vector<Problem>& qs, int first, int count, int num_sm
         const long long seg_cost = levels[lv];
         std::vector<int> b0(Gmax + 1), b1(Gmax + 1);
         std::vector<BandStats> s0, s1;
-        const int u0 = split_group(qs, first, split, Gmax, seg_cost, t2, b0.data(), s0);
-        const int u1 = split_group(qs, first + split, count - split, Gmax, seg_cost, t2, b1.data(), s1);
+        std::vector<int> tcol(Gmax, 0);   // TMEM columns per CTA, group 0's segments first
+        const int u0 = split_group(qs, first, split, Gmax, seg_cost, t2, b0.data(), s0, tcol);
+        const int u1 = split_group(qs, first + split, count - split, Gmax, seg_cost, t2, b1.data(), s1, tcol);
         const int G = std::max(1, std::max(u0, u1));
         PdbLayout L{0, 0, 0, 1, t2};
         for (int i = 0; i < count; ++i)
