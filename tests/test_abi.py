@@ -50,6 +50,7 @@ def test_default_params_and_error_strings(built):
     assert p.alpha == 0.5 and p.max_outer == 100 and p.max_inner == 1000
     assert p.tol_outer == 1e-6 and p.tol_inner == 1e-6 and p.normalize_max == 1
     assert p.slack_policy == 0 and p.precision == F.FP32 and p.debug_flags == 0
+    assert p.algorithm == F.ALG_FASTPFP
     for code in (0, -1, -2, -3, -4, -5, -6):
         assert F.error_string(code) != "unknown error"
 
@@ -61,6 +62,8 @@ def test_struct_layouts_match_header():
 #include "fastpfp.h"
 int main(void) {
   printf("%zu %zu %zu\n", sizeof(fastpfp_params), sizeof(fastpfp_stats), sizeof(fastpfp_pair));
+  printf("%d %d %d %d %d %d %d\n", FASTPFP_FP32, FASTPFP_BF16, FASTPFP_FP8, FASTPFP_ALG_FASTPFP,
+         FASTPFP_ALG_PG, FASTPFP_TUNE_SIZES, FASTPFP_TUNE_COUNTS);
   return 0;
 }'''
     import tempfile
@@ -69,7 +72,9 @@ int main(void) {
         exe = os.path.join(d, "t")
         open(c, "w").write(src)
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
-        sizes = [int(x) for x in subprocess.run([exe], capture_output=True, text=True,
-                                                check=True).stdout.split()]
+        lines = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.splitlines()
+    sizes = [int(x) for x in lines[0].split()]
     assert sizes == [C.sizeof(F.fastpfp_params), C.sizeof(F.fastpfp_stats),
                      C.sizeof(F.fastpfp_pair)]
+    consts = [int(x) for x in lines[1].split()]
+    assert consts == [F.FP32, F.BF16, F.FP8, F.ALG_FASTPFP, F.ALG_PG, F.TUNE_SIZES, F.TUNE_COUNTS]

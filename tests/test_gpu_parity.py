@@ -778,3 +778,31 @@ def test_e1_sweep_recovers_isomorphisms():
     assert a["error"] == 0.0 and a["accuracy"] == 1.0
     for r in rows:
         assert r["seconds"] > 0 and r["outer"] >= 1
+
+
+def test_fp8_transposed_partial_pair(solver):
+    """E4M3 products on a pair whose first graph is the smaller one (the
+    canonical swap transposes every operand) with outliers: the FP8 phase and
+    the FP32 refinement end at the plain FP32 solve's objective."""
+    g = synth.graph_pair(300, p=0.15, sigma=0.03, k=8, n_out=60, lam=0.5, seed=27)
+    A, A2, B, B2 = cu(g.A2), cu(g.A), cu(g.B2), cu(g.B)       # graph 1 is the smaller
+    r32 = solver.match(A, A2, B, B2, params=F.default_params(lam=0.5))
+    r8 = solver.match(A, A2, B, B2, params=F.default_params(lam=0.5, precision=F.FP8, refine_iters=30))
+    assert r8.stats.status == 0 and r8.stats.transposed == 1 and r8.stats.lowp_iters >= 1
+    assert abs(r8.stats.objective - r32.stats.objective) <= 1e-4 * abs(r32.stats.objective)
+    perm = r8.perm.cpu().numpy()
+    assert (perm >= 0).all() and len(np.unique(perm)) == len(perm)
+
+
+def test_pg_fp8_phase_then_fp32_refinement(solver):
+    """The projected gradient step formed in the E4M3 products' epilogue
+    (X + alpha (scaled accumulator) + alpha lambda K) ends, after FP32
+    refinement, at the plain FP32 PG solve's objective."""
+    pairs = synth.batch_mixed(count=3, seed=29, n_lo=100, n_hi=300, out_hi=30)
+    dev = [(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)) for g in pairs]
+    kw = dict(lam=0.5, alpha=0.01, algorithm=F.ALG_PG, normalize_max=0)
+    o8 = solver.match_batched(dev, params=F.default_params(precision=F.FP8, refine_iters=40, **kw))
+    o32 = solver.match_batched(dev, params=F.default_params(**kw))
+    for a, b in zip(o8, o32):
+        assert a.stats.status == 0 and a.stats.lowp_iters >= 1
+        assert abs(a.stats.objective - b.stats.objective) <= 1e-4 * abs(b.stats.objective)
