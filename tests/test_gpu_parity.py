@@ -785,7 +785,7 @@ def test_fp8_transposed_partial_pair(solver):
     canonical swap transposes every operand) with outliers: the FP8 phase and
     the FP32 refinement end at the plain FP32 solve's objective."""
     g = synth.graph_pair(300, p=0.15, sigma=0.03, k=8, n_out=60, lam=0.5, seed=27)
-    A, A2, B, B2 = cu(g.A2), cu(g.A), cu(g.B2), cu(g.B)       # graph 1 is the smaller
+    A, A2, B, B2 = cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)       # graph 1 (300) is the smaller
     r32 = solver.match(A, A2, B, B2, params=F.default_params(lam=0.5))
     r8 = solver.match(A, A2, B, B2, params=F.default_params(lam=0.5, precision=F.FP8, refine_iters=30))
     assert r8.stats.status == 0 and r8.stats.transposed == 1 and r8.stats.lowp_iters >= 1
