@@ -273,6 +273,52 @@ def cpu_oracle_sample(g, budget_s=12.0):
     return unit, sample, t_grad + rounds * t_round + t_blend
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_single_thread_units(g, rounds: int = 12):
+    """Per-unit costs of the oracle on one thread (a shorter sample: the
+    gradient's cost per flop on a 400-node block, `rounds` projection rounds,
+    one blend), to report beside the all-core figure."""
+    import oracle
+    n0 = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        N = max(g.A.shape[0], g.A2.shape[0])
+        ng = min(400, N)
+        A = g.A.astype(np.float64)[:ng, :ng]
+        X = np.full((ng, ng), 1.0 / (ng * ng))
+        t0 = time.perf_counter()
+        oracle.gradient(A, X, A, None, 0.0)
+        t_grad = time.perf_counter() - t0
+        Y = np.full((N, N), 1.0 / N)
+        t0 = time.perf_counter()
+        oracle.pd(Y, fixed_iters=rounds)
+        t_round = (time.perf_counter() - t0) / rounds
+        Xb = np.full((N, N), 1.0 / N)
+        t0 = time.perf_counter()
+        oracle.blend(Xb, Y, 0.5, True)
+        t_blend = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(n0)
+    return dict(grad=t_grad / (2.0 * ng * ng * (2 * ng)), round=t_round / (N * N), blend=t_blend / (N * N))
+
+
 def oracle_solve_seconds(unit, N, m, outer, inner):
     """Oracle time of one whole solve from the per-unit costs."""
     return (outer * (unit["grad"] * 2.0 * N * m * (N + m) + unit["blend"] * N * m)
@@ -353,7 +399,7 @@ def run_reference(args, rank, world):
         "data": "synthetic",
         "config": dict(workload="attributed_1000", **wl, **SOLVER, pairs_per_step=1),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
-                         "kind": "oracle", "sample": samples[-1] +
+                         "kind": "oracle", "cpu_model": cpu_model(), "sample": samples[-1] +
                          f", extrapolated to the oracle's own full solve of seed 0 "
                          f"({outer} outer, {inner} inner iterations)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -566,8 +612,11 @@ def main():
         last = stats_all[-1]
         t_cpu = sum(oracle_solve_seconds(unit, N, m, s_.outer_iters, s_.inner_iters_total)
                     for s_, (N, m) in zip(last, shapes))
+        unit1 = oracle_single_thread_units(pairs[0])
+        t_cpu1 = sum(oracle_solve_seconds(unit1, N, m, s_.outer_iters, s_.inner_iters_total)
+                     for s_, (N, m) in zip(last, shapes))
         cpu = {"value": len(last) / t_cpu, "unit": UNIT, "cores": oracle.num_threads(),
-               "kind": "oracle",
+               "kind": "oracle", "cpu_model": cpu_model(), "value_1_thread": len(last) / t_cpu1,
                "sample": sample + f", per-unit costs extrapolated to the {len(last)} pairs of one "
                                   f"step with the GPU's per-pair iteration counts"}
 
