@@ -746,7 +746,7 @@ bool plan_bands(const std::vector<Problem>& qs, int first, int count, int num_sm
         const int u0 = split_group(qs, first, split, Gmax, seg_cost, t2, b0.data(), s0, tcol);
         const int u1 = split_group(qs, first + split, count - split, Gmax, seg_cost, t2, b1.data(), s1, tcol);
         const int G = std::max(1, std::max(u0, u1));
-        PdbLayout L{0, 0, 0, 1, t2};
+        PdbLayout L{0, 0, 0, 1, t2, 1, count};
         for (int i = 0; i < count; ++i)
             L.rp_stride = std::max(L.rp_stride, pdb_row_warps(round4(qs[first + i].N), kPdbThreads, t2));
         bool ok = true;
@@ -754,6 +754,7 @@ bool plan_bands(const std::vector<Problem>& qs, int first, int count, int num_sm
             L.max_band_rows = std::max(L.max_band_rows, s0[b].rows + s1[b].rows);
             L.max_band_cols = std::max(L.max_band_cols, s0[b].cols + s1[b].cols);
             L.max_band_elems = std::max(L.max_band_elems, s0[b].elems + s1[b].elems);
+            L.max_segs = std::max(L.max_segs, s0[b].segs + s1[b].segs);
             if (s0[b].segs + s1[b].segs > kMaxSeg) ok = false;
         }
         const size_t smem = pdb_smem_bytes(L, kPdbThreads);

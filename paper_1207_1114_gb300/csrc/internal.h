@@ -89,6 +89,8 @@ struct PdbLayout {
     int max_band_elems;   // floats of the largest band kept in shared memory (the rest is in TMEM)
     int rp_stride;        // row-partial slots per row: the most warps sharing one row, <= 16
     int two_quad_ties;    // pdb_shape's tie rule for this wave (1: two quads per thread)
+    int max_segs;         // segments of the band that spans the most pairs (<= kMaxSeg)
+    int npairs;           // pairs of the wave: the per-pair tables are sized for this many
 };
 
 // Warps sharing one row of a pair whose slacked rows hold ldy floats, in a

@@ -56,13 +56,13 @@ static_assert(sizeof(Seg) == 48, "pdb_smem_bytes assumes 48-byte segments");
 static_assert(sizeof(PairS) == 56, "pdb_smem_bytes assumes 56-byte pair records");
 
 struct Shared {
-    Seg* seg;            // kMaxSeg
-    PairS* pair;         // kMaxWavePairs
-    int* pstate;         // kMaxWavePairs: bit0 active this launch, bit1 stopped
-    int* pstop;          // kMaxWavePairs: round at which the pair stopped
+    Seg* seg;            // L.max_segs
+    PairS* pair;         // L.npairs
+    int* pstate;         // L.npairs: bit0 active this launch, bit1 stopped
+    int* pstop;          // L.npairs: round at which the pair stopped
     int* ictl;           // [2] n segments, [3] non-finite, [4],[5] running pairs of group 0 / 1
-    int* qpref;          // 2 x (kMaxWavePairs + 1): per group, prefix sums of the pairs' column quads
-    float* fred;         // kMaxSeg x 32 per-warp maxima
+    int* qpref;          // 2 x (L.npairs + 1): per group, prefix sums of the pairs' column quads
+    float* fred;         // L.max_segs x 32 per-warp maxima
     float* rsum;         // band rows
     float* rowpart;      // band rows x rp_stride per-warp row partials
     float* cN;           // sum over segments of ldy floats: the column sums c_j of the last round
@@ -77,13 +77,13 @@ __device__ __forceinline__ Shared carve_b(char* base, const PdbLayout& L, int nt
         off = (off + bytes + 15) & ~size_t(15);
         return p;
     };
-    s.seg = reinterpret_cast<Seg*>(take(sizeof(Seg) * kMaxSeg));
-    s.pair = reinterpret_cast<PairS*>(take(sizeof(PairS) * kMaxWavePairs));
-    s.pstate = reinterpret_cast<int*>(take(sizeof(int) * kMaxWavePairs));
-    s.pstop = reinterpret_cast<int*>(take(sizeof(int) * kMaxWavePairs));
+    s.seg = reinterpret_cast<Seg*>(take(sizeof(Seg) * L.max_segs));
+    s.pair = reinterpret_cast<PairS*>(take(sizeof(PairS) * L.npairs));
+    s.pstate = reinterpret_cast<int*>(take(sizeof(int) * L.npairs));
+    s.pstop = reinterpret_cast<int*>(take(sizeof(int) * L.npairs));
     s.ictl = reinterpret_cast<int*>(take(sizeof(int) * 8));
-    s.qpref = reinterpret_cast<int*>(take(sizeof(int) * 2 * (kMaxWavePairs + 1)));
-    s.fred = reinterpret_cast<float*>(take(sizeof(float) * kMaxSeg * 32));
+    s.qpref = reinterpret_cast<int*>(take(sizeof(int) * 2 * (L.npairs + 1)));
+    s.fred = reinterpret_cast<float*>(take(sizeof(float) * L.max_segs * 32));
     s.rsum = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_rows));
     s.rowpart = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_rows * L.rp_stride));
     s.cN = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_cols));
@@ -415,6 +415,13 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     extern __shared__ __align__(16) char smem_raw[];
     WaveCtrl* W = P.wave;
     if (ld_relaxed_i32(&W->all_done) != 0 || ld_relaxed_i32(&W->error) != 0) return;
+    // the per-pair tables are sized for layout.npairs pairs: a launch with more
+    // would overrun them, so every CTA leaves (the same decision everywhere,
+    // before any barrier)
+    if (P.npairs > P.layout.npairs || P.layout.max_segs < 1) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) atomicCAS(&W->error, 0, FASTPFP_ERR_ARG);
+        return;
+    }
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const unsigned G = gridDim.x;
     Shared S = carve_b(smem_raw, P.layout, nthr);
@@ -434,7 +441,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             const int* band = P.band_row + g * (G + 1);
             const int b0 = band[blockIdx.x], b1 = band[blockIdx.x + 1];
             const int p0 = g == 0 ? 0 : split, p1 = g == 0 ? split : npairs;
-            for (int p = p0; p < p1 && nseg < kMaxSeg; ++p) {
+            for (int p = p0; p < p1 && nseg < P.layout.max_segs; ++p) {
                 const PairDesc& d = P.pairs[p];
                 const int lo = max(b0, d.row0), hi = min(b1, d.row0 + d.N);
                 if (lo >= hi) continue;
@@ -461,7 +468,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         S.ictl[3] = 0;
         for (int g = 0; g < 2; ++g) {
             const int p0 = g == 0 ? 0 : split, p1 = g == 0 ? split : npairs;
-            int* qp = S.qpref + g * (kMaxWavePairs + 1);
+            int* qp = S.qpref + g * (P.layout.npairs + 1);
             qp[0] = 0;
             for (int p = p0; p < p1; ++p) qp[p - p0 + 1] = qp[p - p0] + (P.pairs[p].ldy >> 2);
         }
@@ -633,7 +640,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     // dealt round-robin over the CTAs, so every CTA zeroes about the same few.
     auto clear_acc = [&](int g, int which, int t, int nt) {
         const int p0 = g == 0 ? 0 : split, np = (g == 0 ? split : npairs) - p0;
-        const int* qp = S.qpref + g * (kMaxWavePairs + 1);
+        const int* qp = S.qpref + g * (P.layout.npairs + 1);
         const int total = qp[np];
         for (int f = t * (int)G + (int)blockIdx.x; f < total; f += nt * (int)G) {
             int lo = 0, hi = np;   // the pair whose quads hold f: qp[lo] <= f < qp[lo + 1]
@@ -958,13 +965,13 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
 size_t pdb_smem_bytes(const PdbLayout& L, int nthr) {
     size_t off = 0;
     auto take = [&](size_t bytes) { off = (off + bytes + 15) & ~size_t(15); };
-    take(48 * kMaxSeg);               // Seg is twelve ints
-    take(56 * kMaxWavePairs);         // PairS: three pointers, a double, two ints, a float, pad, a double
-    take(4 * kMaxWavePairs);
-    take(4 * kMaxWavePairs);
+    take(48 * (size_t)L.max_segs);    // Seg is twelve ints
+    take(56 * (size_t)L.npairs);      // PairS: three pointers, a double, two ints, a float, pad, a double
+    take(4 * (size_t)L.npairs);
+    take(4 * (size_t)L.npairs);
     take(4 * 8);
-    take(4 * 2 * (kMaxWavePairs + 1));
-    take(4 * kMaxSeg * 32);
+    take(4 * 2 * ((size_t)L.npairs + 1));
+    take(4 * (size_t)L.max_segs * 32);
     take(4 * (size_t)L.max_band_rows);
     take(4 * (size_t)L.max_band_rows * L.rp_stride);
     take(4 * (size_t)L.max_band_cols);
