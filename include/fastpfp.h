@@ -112,7 +112,7 @@ typedef struct {
     int inner_iters_total;  /* P1/P2 rounds summed over all outer iterations                 */
     int inner_iters_max;    /* largest P1/P2 round count of one outer iteration              */
     int converged;          /* 1 if max|dX| < tol_outer was reached; 0 if I_0 stopped it     */
-    int lowp_iters;         /* outer iterations run with BF16 products                       */
+    int lowp_iters;         /* outer iterations run with BF16 or FP8 products                */
     int transposed;         /* 1 if the graphs were swapped (n_a < n_b)                      */
     int status;             /* FASTPFP_OK or the error code of this solve                    */
     int launches;           /* CUDA kernels this solve enqueued                              */
@@ -337,8 +337,9 @@ int fastpfp_gemm_probe(int device, int precision, int n, int reps, double* tflop
 
 /* Tile shapes of the gradient products A X A' + lambda K (Section 4.1).
  * Each solve picks, per grouped launch, the CTA tile of its FP32 products
- * (128 or 64 output rows) and of its BF16 tensor-core products (128 x 256 or
- * 128 x 128 outputs) from a table kept in the handle, indexed by a size
+ * (128 or 64 output rows) and of its tensor-core products, BF16 or E4M3
+ * (128 x 256 or 128 x 128 outputs; timed in BF16), from a table kept in the
+ * handle, indexed by a size
  * class of the group's largest canonical N (class c covers
  * 2^(c+6) < N <= 2^(c+7); class 0 also N <= 128) and a count class of the
  * group's pairs (1; 2-4; 5-16; 17-32).  The table starts at 128 / 256 in
