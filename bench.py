@@ -89,9 +89,33 @@ def gemm_probe_line(F, device: int, n: int = 4096):
     return out
 
 
+def code_hash(text: str) -> str:
+    """sha256 (16 hex digits) of C++ source with its comments and blank runs
+    removed: edits to comments do not change it, edits to code do."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        if text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        elif text[i] == '"':                       # string literal, kept verbatim
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(text[i])
+            i += 1
+    code = " ".join("".join(out).split())
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
+
+
 def source_hash(kernel: str) -> str:
-    with open(KERNEL_SOURCE[kernel], "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    with open(KERNEL_SOURCE[kernel]) as f:
+        return code_hash(f.read())
 
 
 def ncu_traffic_per_launch(kernel: str, workload: str, rounds_per_launch: float):

@@ -9,8 +9,11 @@
 //     arrive(A,u) -> wait(B,u-1) -> round B(u) -> arrive(B,u) -> wait(A,u) -> round A(u+1) ...
 // (the host chooses; with one group, group 1 is empty).
 // Within a group all rows of all pairs are concatenated and cut into one band
-// per CTA with about the same number of entries; a band may span several
-// pairs ("segments") and stays in shared memory for all rounds.  A round
+// per CTA of about the same cost (entries plus a measured cost per pair the
+// band spans); a band may span several pairs ("segments") and stays on chip
+// for all rounds: the first rows of every thread in tensor memory (all 512
+// columns of the SM, used as storage through tcgen05.ld/st), the rest in
+// shared memory.  A round
 // applies Eq. (P1) and Eq. (P2) elementwise to every segment of the group,
 // measures max|dY|, and publishes the pairs' column partials (vector
 // red.add), FP64 shares of the totals s and round maxima.  After the group's
@@ -696,8 +699,9 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     };
 
     // Wait for group g's barrier of pass `cur` (round u), then take every
-    // stop decision of the group's pairs (identical in every CTA), load c/N
-    // of its segments and turn the new totals into the next offsets a_i.
+    // stop decision of the group's pairs (identical in every CTA), load the
+    // column sums c_j of its segments and turn the new totals into the next
+    // row-offset bases 1/N + s/N^2.
     auto wait_post = [&](int g, int cur, int u, bool check_stop) -> bool {
         const unsigned target = (g == 0 ? base0 : base1) + G * (gen[g] + 1u);
         if (!grid_wait(&W->bar[g], target, err, P.timeout_ns)) return false;
