@@ -806,3 +806,17 @@ def test_pg_fp8_phase_then_fp32_refinement(solver):
     for a, b in zip(o8, o32):
         assert a.stats.status == 0 and a.stats.lowp_iters >= 1
         assert abs(a.stats.objective - b.stats.objective) <= 1e-4 * abs(b.stats.objective)
+
+
+def test_autotune_on_a_tiny_handle():
+    """Tile timing on the smallest shapes (N = 40: one partial tile, TMA boxes
+    larger than the matrices) and a solve on whatever it picked, against the
+    oracle replay."""
+    s = F.Solver(max_n=40, max_batch=3)
+    try:
+        t = s.autotune(reps=1)
+        assert (t[0, :2] > 0).all() and (t[1:] == 0).all()
+        pairs = [synth.graph_pair(n, p=0.4, sigma=0.02, k=3, lam=0.5, seed=60 + n) for n in (12, 25, 33)]
+        _check_batch(s, pairs, 0.5, max_outer=20, max_inner=200)
+    finally:
+        s.close()
