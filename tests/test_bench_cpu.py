@@ -1,0 +1,54 @@
+"""Host-side pieces of bench.py: the parameters each mode passes to the
+library, the kernel-code hash behind the ncu traffic field, and the oracle
+baseline's unit costs.  CPU only."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_1207_1114_gb300 import fastpfp as F  # noqa: E402
+from paper_1207_1114_gb300 import synth  # noqa: E402
+
+
+def test_code_hash_ignores_comments_but_not_code():
+    a = "int f(int x) { // double it\n  return 2 * x; /* fast */ }\n"
+    b = "int f(int x) {\n  return 2 * x;\n}\n// another note\n"
+    c = "int f(int x) { return 3 * x; }"
+    assert bench.code_hash(a) == bench.code_hash(b)
+    assert bench.code_hash(a) != bench.code_hash(c)
+    # a comment marker inside a string literal is code
+    assert bench.code_hash('const char* s = "//x";') != bench.code_hash('const char* s = "";')
+
+
+def test_committed_profiles_match_the_kernel_code():
+    """The traffic the bench reports comes from ncu summaries taken on the
+    current wave-kernel code."""
+    for workload in ("attributed_1000", "large_4000"):
+        assert bench.ncu_traffic_per_launch("pdb_kernel", workload, 1000) is not None
+
+
+def test_params_per_mode():
+    p = bench.params(F, 1.0)
+    assert p.precision == F.FP32 and p.algorithm == F.ALG_FASTPFP and p.alpha == 0.5
+    p = bench.params(F, 1.0, precision="fp8")
+    assert p.precision == F.FP8 and p.refine_iters == 30 and p.switch_tol == 1e-3
+    p = bench.params(F, 1.0, pg_alpha=0.01)
+    assert p.algorithm == F.ALG_PG and p.normalize_max == 0 and abs(p.alpha - 0.01) < 1e-9
+
+
+def test_pg_step_is_one_over_the_lipschitz_constant():
+    g = synth.graph_pair(30, p=0.3, sigma=0.0, seed=1)
+    L = np.linalg.norm(g.A.astype(np.float64), 2) * np.linalg.norm(g.A2.astype(np.float64), 2)
+    assert bench.pg_step([g]) == pytest.approx(1.0 / L, rel=1e-6)
+
+
+def test_single_thread_oracle_units_are_positive():
+    g = synth.graph_pair(40, p=0.3, sigma=0.02, k=2, seed=2)
+    u = bench.oracle_single_thread_units(g, rounds=2)
+    assert all(v > 0 for v in u.values())
+    assert isinstance(bench.cpu_model(), str)
