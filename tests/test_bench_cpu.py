@@ -25,11 +25,20 @@ def test_code_hash_ignores_comments_but_not_code():
     assert bench.code_hash('const char* s = "//x";') != bench.code_hash('const char* s = "";')
 
 
-def test_committed_profiles_match_the_kernel_code():
-    """The traffic the bench reports comes from ncu summaries taken on the
-    current wave-kernel code."""
-    for workload in ("attributed_1000", "large_4000"):
-        assert bench.ncu_traffic_per_launch("pdb_kernel", workload, 1000) is not None
+def test_profile_traffic_needs_a_matching_code_hash(tmp_path, monkeypatch):
+    """The traffic field is read from a summary only while its recorded hash
+    is the kernel's current code hash (and the round count matches)."""
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    h = bench.source_hash("pdb_kernel")
+    (prof / "pdb_kernel_attributed_1000.md").write_text(
+        f"source_sha256_16: {h}\ndram_bytes_per_launch: 1234\nrounds_per_launch: 1000\n")
+    (prof / "pdb_kernel_large_4000.md").write_text(
+        "source_sha256_16: 0000000000000000\ndram_bytes_per_launch: 1234\nrounds_per_launch: 1000\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.ncu_traffic_per_launch("pdb_kernel", "attributed_1000", 1000) == 1234
+    assert bench.ncu_traffic_per_launch("pdb_kernel", "attributed_1000", 500) is None
+    assert bench.ncu_traffic_per_launch("pdb_kernel", "large_4000", 1000) is None
 
 
 def test_params_per_mode():
