@@ -221,17 +221,19 @@ def make_pairs(workload: str, rank: int, batch: int):
     raise ValueError(workload)
 
 
-def params(F, lam, profile=0, precision="fp32", loop_mode=0, pg_alpha=None):
+def params(F, lam, profile=0, precision="fp32", loop_mode=0, pg_alpha=None, **override):
     """The workload's parameters.  bf16: tensor-core products until
     max|dX| < 1e-3, then FP32 iterations (at most 30) to convergence.
     pg_alpha: the projected gradient method of Eq. (pg) with that step and
-    no normalisation instead of FastPFP."""
+    no normalisation instead of FastPFP.  override: any other field."""
     low = {"bf16": F.BF16, "fp8": F.FP8}.get(precision)
     extra = dict(precision=low, refine_iters=30, switch_tol=1e-3) if low is not None else {}
     solver = dict(SOLVER)
     if pg_alpha is not None:
         solver.update(alpha=pg_alpha)
         extra.update(algorithm=F.ALG_PG, normalize_max=0)
+    solver.update({k: v for k, v in override.items() if k in solver})
+    extra.update({k: v for k, v in override.items() if k not in solver})
     return F.default_params(lam=lam, profile=profile, loop_mode=loop_mode, **solver, **extra)
 
 
@@ -295,6 +297,63 @@ def cpu_oracle_sample(g, budget_s=12.0):
     sample = (f"1 pair (N={N}, m={m}): 1 gradient of {ng}x{mg} ({t_grad:.2f}s) + {rounds} "
               f"projection rounds ({t_round * 1e3:.2f} ms/round) + 1 blend")
     return unit, sample, t_grad + rounds * t_round + t_blend
+
+
+def oracle_solve_kwargs(lam, pg_alpha=None):
+    """The oracle's arguments for the workload's solve (FastPFP, or the
+    projected gradient method with step pg_alpha and no normalisation)."""
+    kw = dict(SOLVER, lam=lam)
+    if pg_alpha is not None:
+        kw.update(alpha=pg_alpha, algorithm="pg", normalize_max=False)
+    return kw
+
+
+def oracle_timed_solves(pairs, budget_s, pg_alpha=None):
+    """The oracle as it stands (Algorithm 1 and the greedy, FP64, on every
+    host core) solving the step's pairs one after another from the first,
+    each solve timed whole, until budget_s has been spent (at least one
+    pair).  Returns (pairs solved, seconds)."""
+    import oracle
+    done, spent = 0, 0.0
+    for g in pairs:
+        t0 = time.perf_counter()
+        oracle.solve(g.A, g.A2, g.B, g.B2, **oracle_solve_kwargs(g.lam, pg_alpha))
+        spent += time.perf_counter() - t0
+        done += 1
+        if spent >= budget_s:
+            break
+    return done, spent
+
+
+def oracle_error(F, solver, dpairs, pairs, prm, p_switch, pg_alpha=None):
+    """Error of the GPU's result for pair 0 of the batch against the FP64
+    oracle.  The batch is solved once more (untimed, the same bits as a
+    timed step: the solve is reproducible) with its X; the oracle replays
+    pair 0's inner counts.  After a BF16 / E4M3 phase the oracle runs the
+    FP32 refinement from the X at the switch, which the same batch stopped
+    there (p_switch(L): no refinement, I_0 = L) returns.  dpairs may carry
+    each pair's start X(0) as a fifth entry (the learned start)."""
+    import oracle
+    outs = solver.match_batched(dpairs, params=prm, want_X=True)
+    inner, _ = solver.last_trace(pair=0)
+    st = outs[0].stats
+    g = pairs[0]
+    L, T = st.lowp_iters, st.outer_iters
+    X0 = dpairs[0][4].cpu().numpy() if len(dpairs[0]) > 4 else None   # a learned start
+    if L > 0:
+        X0 = solver.match_batched(dpairs, params=p_switch(L), want_X=True)[0].X.cpu().numpy()
+    t0 = time.perf_counter()
+    ref = oracle.solve(g.A, g.A2, g.B, g.B2, X0=X0, replay_inner=inner[L:], replay_outer=T - L,
+                       **oracle_solve_kwargs(g.lam, pg_alpha))
+    Xg = outs[0].X.cpu().numpy()
+    return {"pair": 0, "max_abs_X": float(np.abs(Xg - ref["X"]).max()),
+            "objective_rel": abs(st.objective - ref["objective"]) / abs(ref["objective"]),
+            "perm_equal": bool((outs[0].perm.cpu().numpy() == ref["perm"]).all()),
+            "outer": T, "lowp_iters": L,
+            "how": ("oracle replays the GPU's inner counts of every outer iteration" if L == 0 else
+                    f"oracle runs the {T - L} FP32 refinement iterations from the X the GPU's "
+                    f"{L} low-precision iterations reached, replaying the GPU's inner counts"),
+            "oracle_seconds": round(time.perf_counter() - t0, 2)}
 
 
 def cpu_model() -> str:
@@ -392,40 +451,36 @@ def train_warm_start(F, torch, dev, local, count, seed):
 
 def run_reference(args, rank, world):
     """--impl reference: the FP64 CPU oracle as it stands, on the host cores.
-    Each step is a bounded sample of the n = 1000 workload, extrapolated with
-    the oracle's own iteration counts of its full solve of seed 0."""
+    Every step is one whole oracle solve (Algorithm 1 and the greedy) of the
+    workload's first pair, timed.  At n = 4000 a whole solve takes about half
+    an hour, so that workload has no reference arm."""
     import oracle
     if rank != 0:
         return
-    if args.workload != "attributed_1000":
+    if args.workload == "large_4000":
         print(json.dumps({"impl": "reference", "unavailable":
-                          "the oracle's own iteration counts are stored for attributed_1000 only"}))
+                          "one whole FP64 oracle solve at n = 4000 takes about half an hour on the host cores"}))
         return
-    golden = os.path.join(ROOT, "tests", "golden", "attributed_1000_seed0.json")
-    with open(golden) as f:
-        gold = json.load(f)
-    outer = gold["outer_iters"]
-    inner = sum(gold["inner"])
-    g = make_pairs("attributed_1000", 0, 1)[0]
+    g = make_pairs(args.workload, 0, 1)[0]
     N, m = canon_shape(g)
-    vals, samples = [], []
+    times = []
     for i in range(args.warmup + args.steps):
-        unit, sample, _ = cpu_oracle_sample(g, budget_s=args.ref_budget)
+        _, t = oracle_timed_solves([g], 0.0)
         if i >= args.warmup:
-            vals.append(1.0 / oracle_solve_seconds(unit, N, m, outer, inner))
-            samples.append(sample)
-    value = float(np.median(vals))
-    wl = {k: v for k, v in WORKLOADS["attributed_1000"].items() if k not in ("metric", "batch")}
+            times.append(t)
+    value = len(times) / float(sum(times))
+    wl = WORKLOADS[args.workload]
+    cfg = {k: v for k, v in wl.items() if k not in ("metric", "batch")}
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+        "impl": "reference", "metric": wl["metric"], "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(sum(times)) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": dict(workload="attributed_1000", **wl, **SOLVER, pairs_per_step=1),
+        "config": dict(workload=args.workload, **cfg, **SOLVER, pairs_per_step=1),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
-                         "kind": "oracle", "cpu_model": cpu_model(), "sample": samples[-1] +
-                         f", extrapolated to the oracle's own full solve of seed 0 "
-                         f"({outer} outer, {inner} inner iterations)"},
+                         "kind": "oracle", "cpu_model": cpu_model(),
+                         "sample": f"every step one whole oracle solve of the workload's first pair "
+                                   f"(N={N}, m={m}), timed; nothing extrapolated"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -439,7 +494,8 @@ def main():
     ap.add_argument("--workload", default="attributed_1000", choices=sorted(WORKLOADS))
     ap.add_argument("--batch", type=int, default=None, help="pairs per step and rank")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--ref-budget", type=float, default=10.0, dest="ref_budget")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, dest="cpu_budget",
+                    help="seconds of whole oracle solves timed for the cpu_baseline field")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"],
                     help="gradient products: plain FP32, or BF16 / E4M3 tensor cores + FP32 refinement")
@@ -561,23 +617,40 @@ def main():
     achieved = alg_bytes / (ms_proj / 1e3) / 1e9 if ms_proj > 0 else None
     hbm_peak, hbm_kind = peaks()
     kernel = "pdb_kernel" if flat[0].wave_pairs > 0 else "pd_kernel"
-    # the memory level that holds Y during the rounds bounds their traffic:
-    # shared memory for a wave (and for a lone pair whose band fits), L2 for
-    # a streamed band of up to ~100 MB, HBM beyond
+    # the memory level that holds Y during the rounds bounds their traffic.
+    # The wave kernel keeps a wave's slacked matrices on chip: the first rows
+    # of every CTA's band in tensor memory (all 512 columns of the SM), the
+    # rest in shared memory.  Its bound is the time to move a round's bytes
+    # through both at their measured bandwidths, with the wave's bytes split
+    # as the capacities fill: tensor memory first.  A lone pair too large for
+    # a wave streams its band through L2 (up to ~100 MB) or HBM.
     Nmax = max(N for N, _ in shapes)
     y_bytes = 4.0 * Nmax * Nmax
-    if kernel == "pdb_kernel" or Nmax <= 2900:
-        level, bound, sweeps = 0, "smem", 20000
+    split = None
+    if kernel == "pdb_kernel":
+        smem_gbs = F.bandwidth_probe(0, sweeps=20000, device=local)
+        tmem_gbs = F.bandwidth_probe(3, sweeps=2000, device=local)
+        n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+        wave = float(np.mean([max(s.wave_pairs, 1) for s in flat]))
+        wave_y = wave * float(np.mean([4.0 * N * N for N, _ in shapes]))
+        f_tmem = min(1.0, n_sms * 512 * 128 * 4.0 / wave_y)
+        peak = 1.0 / (f_tmem / tmem_gbs + (1.0 - f_tmem) / smem_gbs)
+        bound = "on-chip (tmem + smem)"
+        split = {"tmem_gbs": tmem_gbs, "smem_gbs": smem_gbs, "tmem_share_of_bytes": f_tmem,
+                 "wave_pairs": wave, "wave_y_bytes": wave_y}
+        peak_kind = ("measured live by fastpfp_bandwidth_probe (read + write sweeps of every SM's tensor "
+                     "memory and shared memory), combined as 1 / (f / tmem + (1 - f) / smem) with f the "
+                     "share of a wave's slacked matrices that fits in tensor memory")
+    elif Nmax <= 2900:
+        peak = F.bandwidth_probe(0, sweeps=20000, device=local)
+        bound = "smem"
+        peak_kind = "measured live by fastpfp_bandwidth_probe: read + write sweeps of every SM's shared memory"
     elif y_bytes <= 100e6:
-        level, bound, sweeps = 1, "l2", 2000
+        peak = F.bandwidth_probe(1, sweeps=2000, device=local)
+        bound = "l2"
+        peak_kind = "measured live by fastpfp_bandwidth_probe: read + write sweeps of a 64 MB L2-resident buffer"
     else:
-        level, bound, sweeps = 2, "hbm", 0
-    if level < 2:
-        peak = F.bandwidth_probe(level, sweeps=sweeps, device=local)
-        peak_kind = ("measured live by fastpfp_bandwidth_probe: read + write sweeps of "
-                     + ("every SM's shared memory" if level == 0 else "a 64 MB L2-resident buffer"))
-    else:
-        peak, peak_kind = hbm_peak, hbm_kind
+        peak, peak_kind, bound = hbm_peak, hbm_kind, "hbm"
     # one projection launch per outer iteration of a wave (or of a lone pair)
     # and, about, as many rounds per launch as the wave's slowest pair runs
     proj_launches, wave_rounds = 0, 0
@@ -630,19 +703,39 @@ def main():
 
     flat_t = [s for step in stats_all for s in step]
     cpu = None
+    err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
-        unit, sample, _ = cpu_oracle_sample(pairs[0])
         last = stats_all[-1]
-        t_cpu = sum(oracle_solve_seconds(unit, N, m, s_.outer_iters, s_.inner_iters_total)
-                    for s_, (N, m) in zip(last, shapes))
+        if args.workload != "large_4000":
+            done, spent = oracle_timed_solves(pairs, args.cpu_budget, pg_alpha)
+            N0, m0 = shapes[0]
+            cpu = {"value": done / spent, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                   "cpu_model": cpu_model(),
+                   "sample": f"{done} whole oracle solve(s) of the step's first pair(s) (first N={N0}, "
+                             f"m={m0}), each timed from start to end: {spent:.1f} s; nothing extrapolated"}
+        else:
+            # a whole solve at n = 4000 takes about half an hour: per-unit
+            # costs of a bounded sample, extrapolated with the GPU's counts
+            unit, sample, _ = cpu_oracle_sample(pairs[0])
+            t_cpu = sum(oracle_solve_seconds(unit, N, m, s_.outer_iters, s_.inner_iters_total)
+                        for s_, (N, m) in zip(last, shapes))
+            cpu = {"value": len(last) / t_cpu, "unit": UNIT, "cores": oracle.num_threads(),
+                   "kind": "oracle (extrapolated)", "cpu_model": cpu_model(),
+                   "sample": sample + f", per-unit costs extrapolated to the {len(last)} pair(s) of one "
+                                      f"step with the GPU's per-pair iteration counts"}
         unit1 = oracle_single_thread_units(pairs[0])
         t_cpu1 = sum(oracle_solve_seconds(unit1, N, m, s_.outer_iters, s_.inner_iters_total)
                      for s_, (N, m) in zip(last, shapes))
-        cpu = {"value": len(last) / t_cpu, "unit": UNIT, "cores": oracle.num_threads(),
-               "kind": "oracle", "cpu_model": cpu_model(), "value_1_thread": len(last) / t_cpu1,
-               "sample": sample + f", per-unit costs extrapolated to the {len(last)} pairs of one "
-                                  f"step with the GPU's per-pair iteration counts"}
+        cpu["value_1_thread_extrapolated"] = len(last) / t_cpu1
+        if args.workload != "large_4000":
+            p_switch = lambda L: params(F, lam, precision=args.precision, loop_mode=loop_mode,  # noqa: E731
+                                        pg_alpha=pg_alpha, refine_iters=0, max_outer=L)
+            with_x0 = dpairs if mlp is None else [dp + (solver.warmstart(*dp, mlp, iters=20),) for dp in dpairs]
+            err = oracle_error(F, solver, with_x0, pairs, p_plain, p_switch, pg_alpha)
+        else:
+            err = {"not_replayed": "a whole oracle solve at n = 4000 takes about half an hour; the GPU "
+                                   "tests replay two outer iterations of this workload"}
 
     if rank == 0:
         cfg = {k: v for k, v in wl.items() if k not in ("metric", "batch")}
@@ -668,8 +761,9 @@ def main():
                          "hbm_peak": hbm_peak, "hbm_frac": (achieved / hbm_peak) if achieved else None,
                          "traffic": traffic,
                          "alg_bytes_per_launch": alg_bytes / max(proj_launches, 1),
-                         "launches": proj_launches, "timing": timing},
+                         "launches": proj_launches, "timing": timing, "on_chip_split": split},
             "gemm_probe": gemm,
+            "oracle_error": err,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -202,10 +202,9 @@ int fastpfp_match_batched_host(fastpfp_t h, void* stream, int count, const fastp
 /* Copies the per-outer-iteration trace of a pair of the last call on this
  * handle: inner_counts[t] = P1/P2 rounds of outer iteration t, deltas[t] =
  * max|X(t+1) - X(t)|.  `pair` is 0 after fastpfp_match / _host, and after
- * fastpfp_match_batched the index within that call of a pair of its last
- * wave.  Either array may be NULL.  Returns the number of outer iterations
- * (at most cap entries are written), or ERR_ARG for a pair whose trace is no
- * longer held. */
+ * fastpfp_match_batched (or _host) the index of any pair within that call.
+ * Either array may be NULL.  Returns the number of outer iterations (at most
+ * cap entries are written), or ERR_ARG for an index outside the last call. */
 int fastpfp_last_trace(fastpfp_t h, int pair, int* inner_counts, double* deltas, int cap);
 
 /* ---- single steps of Algorithm 1, for step-by-step checking ------------ */
@@ -286,24 +285,24 @@ int fastpfp_warmstart_train_step(fastpfp_t h, void* stream, const float* A, int 
 
 /* ---- entry point for callers that cannot allocate -------------------------
  * The paper has no counterpart to this call; it exists for callers that are
- * not allowed to call cudaMalloc -- for example code running inside a host
- * application's fixed device-memory arena, inside a region being captured
- * into a CUDA graph, or under a real-time rule that forbids allocation after
- * start-up.  Such callers cannot create a handle, because fastpfp_create
- * allocates.
+ * not allowed to call cudaMalloc -- for example a plugin that a host
+ * application hands a fixed device-memory arena (the application accounts
+ * for every byte and refuses allocations made behind its back), or a
+ * real-time loop that forbids allocation after start-up (cudaMalloc can
+ * block and synchronise the device for an unbounded time).  Such callers
+ * cannot create a handle, because fastpfp_create allocates.
  *
  * fastpfp_project_noalloc runs the same successive projection as
  * fastpfp_project, in place on the caller's N x N device matrix Y (row-major,
  * leading dimension N), on the CUDA device that is current.  It allocates
  * nothing: the projection's own scratch (column-sum accumulators, FP64
  * totals, round maxima, barrier and control words) is one file-scope device
- * array of about 100 KB that every GPU which loads this library holds until
+ * array of about 130 KB that every GPU which loads this library holds until
  * the process exits.
  *   - N must be a multiple of 4 with 4 <= N <= 4096 and Y 16-byte aligned;
  *     larger N returns FASTPFP_ERR_SIZE, other shapes FASTPFP_ERR_ARG.
  *   - The first call on a device resolves the array's device address and sets
- *     the kernel's attributes for that device; make that first call before
- *     any stream capture.
+ *     the kernel's attributes for that device.
  *   - Every call on a device shares the one array: the call clears what must
  *     start at zero, but two calls whose work overlaps on the GPU (different
  *     streams, or different host threads) race on it and give wrong results.
@@ -318,10 +317,13 @@ int fastpfp_project_noalloc(void* stream, float* Y, int N, double tol, int max_i
  * per sweep, 16-byte accesses):
  *   level 0  shared memory, every SM sweeping ~225 KB of its own;
  *   level 1  L2, one 64 MB buffer (the size of Y at N = 4000);
- *   level 2  HBM, one 2 GB buffer.
+ *   level 2  HBM, one 2 GB buffer;
+ *   level 3  tensor memory, every SM sweeping all 512 columns x 128 lanes
+ *            (256 KB) of its own with 16-column tcgen05.ld / tcgen05.st
+ *            accesses, the wave kernel's band storage.
  * sweeps >= 1 timed sweeps after one warm-up sweep.  *gbs receives the
  * measured read + write bandwidth in GB/s.  Allocates and frees a scratch
- * buffer (levels 1, 2); synchronises the device.  Errors: ERR_ARG (bad level
+ * buffer (levels 1, 2, 3); synchronises the device.  Errors: ERR_ARG (bad level
  * or sweeps, gbs == NULL), ERR_CUDA. */
 int fastpfp_bandwidth_probe(int device, int level, int sweeps, double* gbs);
 

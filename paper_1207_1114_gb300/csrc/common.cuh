@@ -10,6 +10,7 @@
 namespace fpfp {
 
 constexpr int kMaxOuterTrace = 4096;  // per-solve trace capacity (outer iterations)
+constexpr int kObjBlocks = 256;       // blocks of the objective kernel
 
 // Device control block of one solve.  Zeroed (except the fields the host
 // sets) before the first outer iteration.
@@ -31,8 +32,10 @@ struct Ctrl {
     unsigned bar;          // grid-barrier arrival counter (grows within a solve)
     unsigned bar_base;     // counter value at the start of the next cooperative launch
     int matched;           // discretisation: columns matched so far
+    unsigned obj_ticket;   // objective: blocks that have stored their partial sum
     int inner_trace[kMaxOuterTrace];
     double delta_trace[kMaxOuterTrace];
+    double obj_part[kObjBlocks];   // objective: one partial sum per block, folded in block order
 };
 
 // ---------------------------------------------------------------- ordering
@@ -101,6 +104,54 @@ __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, 
                  "f"(b), "f"(c), "f"(d)
                  : "memory");
 }
+
+// Reduction-add of one double into global memory.
+__device__ __forceinline__ void red_add_f64(double* p, double v) {
+    asm volatile("red.relaxed.gpu.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+// ------------------------------------------------------- order-free sums
+// The column sums and totals of the projection rounds are added across CTAs
+// by atomics, in an order that changes from run to run.  They are made exact
+// -- and so independent of that order -- by rounding every contribution to a
+// multiple of a power-of-two quantum q chosen from a bound that every CTA
+// computes identically before it adds: if every partial sum stays below
+// 2^24 q (FP32) or 2^53 q (FP64), every addition is exact.  The rounding
+// error of one contribution is at most q/2, about one unit in the last place
+// of the bound.
+//
+// FP32: scales of the quantum for a bound b >= 1 (finite): with
+// E = floor(log2 b), b < 2^(E+1) = 2^24 q for q = 2^(E-23); dn = 1/q, up = q.
+struct Quant32 {
+    float dn, up;
+};
+__device__ __forceinline__ Quant32 quant32_for(float bound) {
+    int E = ((__float_as_int(bound) >> 23) & 0xff) - 127;
+    E = E < 0 ? 0 : (E > 100 ? 100 : E);
+    return Quant32{__int_as_float((127 + 23 - E) << 23), __int_as_float((127 - 23 + E) << 23)};
+}
+__device__ __forceinline__ float quant32(float v, Quant32 q) { return rintf(v * q.dn) * q.up; }
+__device__ __forceinline__ float4 quant32x4(float4 v, Quant32 a, Quant32 b, Quant32 c, Quant32 d) {
+    return make_float4(quant32(v.x, a), quant32(v.y, b), quant32(v.z, c), quant32(v.w, d));
+}
+// Margin on every bound: covers the FP32 rounding of the bound itself and of
+// the updates it bounds.
+constexpr float kBoundMargin = 1.0f + 1.0f / 1024.0f;
+
+// FP64: the quantum q = 2^(E-52) for a bound b, E = floor(log2 b), so
+// b < 2^(E+1) = 2^53 q; b <= 0 (only zeros to add) takes q = 1.
+struct Quant64 {
+    double dn, up;
+};
+__device__ __forceinline__ Quant64 quant64_for(double bound) {
+    if (!(bound > 0.0)) return Quant64{1.0, 1.0};
+    int E;
+    frexp(bound, &E);   // bound = f 2^E with f in [0.5, 1)
+    E -= 1;
+    E = E > 900 ? 900 : (E < -900 ? -900 : E);
+    return Quant64{ldexp(1.0, 52 - E), ldexp(1.0, E - 52)};
+}
+__device__ __forceinline__ double quant64(double v, Quant64 q) { return rint(v * q.dn) * q.up; }
 
 // Asynchronous 16-byte global -> shared copy through L2 only (the source is
 // written by other CTAs' reductions, so L1 must not hold a stale copy), and

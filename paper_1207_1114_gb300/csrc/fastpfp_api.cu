@@ -50,10 +50,6 @@ constexpr long long kMinElemsPerCta = 8192;       // smallest band worth a CTA o
 // column quads per thread (pdb_shape): measured +7 % at 112 rows per CTA
 // (17 pairs of n = 1000), -25 % at 7 (one pair of n = 1000).
 constexpr int kTwoQuadRowsPerCta = 32;
-// Two interleaved pair groups per wave (one group's barrier hidden behind the
-// other's round).  Measured slower on GB300 at n = 1000 (17.3 vs 11.8 us per
-// 7-pair round): a round's fixed cost is serial latency, not barrier waiting.
-constexpr bool kInterleaveGroups = false;
 
 inline int round4(int x) { return (x + 3) & ~3; }
 inline int round8(int x) { return (x + 7) & ~7; }   // BF16 rows: 16-byte TMA strides
@@ -226,9 +222,9 @@ int enqueue_setup(const Slot& sl, cudaStream_t s, const Problem& q, const fastpf
     const int ldy = round4(q.N), ldx = round4(q.m);
     const bool lowp = p->precision != FASTPFP_FP32;   // a BF16 or FP8 phase
     FP_CUDA(cudaMemsetAsync(sl.ctrl, 0, kCtrlHeader, s));
-    FP_CUDA(cudaMemsetAsync(sl.colbuf, 0, 3 * (size_t)ld * sizeof(float), s));
+    FP_CUDA(cudaMemsetAsync(sl.colbuf, 0, colbuf_bytes(ld), s));
     FP_CUDA(cudaMemsetAsync(sl.sbuf, 0, 3 * sizeof(double), s));
-    FP_CUDA(cudaMemsetAsync(sl.dbuf, 0, 3 * sizeof(unsigned), s));
+    FP_CUDA(cudaMemsetAsync(sl.dbuf, 0, kDbufWords * sizeof(unsigned), s));
     FP_CUDA(cudaMemsetAsync(sl.Y, 0, (size_t)q.N * ldy * sizeof(float), s));
     FP_CUDA(init_ctrl(sl.ctrl, lowp ? 1 : 0, s));
     int nl = 2;
@@ -590,10 +586,10 @@ int fill_stats(const Ctrl& c, int transposed, int launches, int wave_pairs, fast
 // ---- waves of the batched path ---------------------------------------------
 
 struct Wave {
-    int first = 0, count = 0, split = 0, grid = 0;
+    int first = 0, count = 0, grid = 0;
     size_t smem = 0;
     PdbLayout layout{};
-    std::vector<int> band;   // 2 x (grid + 1) boundaries: group 0, then group 1
+    std::vector<int> band;   // grid + 1 row boundaries
 };
 
 struct BandStats {
@@ -659,12 +655,10 @@ int cut_rows(const std::vector<Problem>& qs, int first, int count, long long C, 
 // Cuts pairs [first, first + count) into at most G bands minimising the
 // largest band cost (binary search on the cost bound over cut_rows).
 // band[0..used] holds the row boundaries, band[used..G] = total rows.
-// tcol[b] (G entries) holds the TMEM columns band b's CTA has already given
-// to earlier segments — the kernel places group 1's segments after group
-// 0's — and receives the columns used after this group.  Returns the number
-// of bands used.
-int split_group(const std::vector<Problem>& qs, int first, int count, int G, long long seg_cost,
-                int two_quad_ties, int* band, std::vector<BandStats>& st, std::vector<int>& tcol) {
+// Returns the number of bands used and, per band, its rows, columns, floats
+// left in shared memory and segments in st.
+int split_rows(const std::vector<Problem>& qs, int first, int count, int G, long long seg_cost,
+               int two_quad_ties, int* band, std::vector<BandStats>& st) {
     long long lo = 1, hi = 0;
     int rows = 0;
     for (int i = 0; i < count; ++i) {
@@ -686,7 +680,7 @@ int split_group(const std::vector<Problem>& qs, int first, int count, int G, lon
     // per-band statistics; the first rows of every row group go to TMEM
     // (pdb_tmem_rows, segments in pair order as the kernel places them), so
     // elems counts the floats left in shared memory
-    tcol.resize(G, 0);
+    std::vector<int> tcol(G, 0);
     int b = 0, gr = 0;
     for (int i = 0; i < count; ++i) {
         const int N = qs[first + i].N, ldy = round4(N);
@@ -708,27 +702,15 @@ int split_group(const std::vector<Problem>& qs, int first, int count, int G, lon
     return used;
 }
 
-// Plans one wave of pairs [first, first + count): two groups of about equal
-// entry counts (group 1 one half-step behind group 0; with kInterleaveGroups
-// off group 1 is empty), each cut into at most num_sms cost-balanced bands;
-// a CTA holds one band of each group.  Bands first try to respect the
-// per-segment cost (pair-aligned where possible), then fall back to pure
+// Plans one wave of pairs [first, first + count): their rows cut into at
+// most num_sms cost-balanced bands, one per CTA.  Bands first try to respect
+// the per-segment cost (pair-aligned where possible), then fall back to pure
 // entry balance if that does not fit in shared memory.  Returns false when a
-// CTA's bands would not fit.
+// CTA's band would not fit.
 bool plan_bands(const std::vector<Problem>& qs, int first, int count, int num_sms, Wave* w,
                 int max_level = 3) {
     long long E = 0;
     for (int i = 0; i < count; ++i) E += (long long)qs[first + i].N * round4(qs[first + i].N);
-    int split = count;
-    if (kInterleaveGroups && count > 1) {
-        long long pre = 0;
-        split = 1;
-        for (int i = 0; i < count - 1; ++i) {
-            pre += (long long)qs[first + i].N * round4(qs[first + i].N);
-            split = i + 1;
-            if (2 * pre >= E) break;
-        }
-    }
     const long long gl = (E + kMinElemsPerCta - 1) / kMinElemsPerCta;
     const int Gmax = (int)std::min<long long>(num_sms, std::max<long long>(1, gl));
     long long rows = 0;
@@ -740,33 +722,25 @@ bool plan_bands(const std::vector<Problem>& qs, int first, int count, int num_sm
     const long long levels[4] = {kSegCost, kSegCost / 2, kSegCost / 4, 0ll};
     for (int lv = 0; lv <= max_level && lv < 4; ++lv) {
         const long long seg_cost = levels[lv];
-        std::vector<int> b0(Gmax + 1), b1(Gmax + 1);
-        std::vector<BandStats> s0, s1;
-        std::vector<int> tcol(Gmax, 0);   // TMEM columns per CTA, group 0's segments first
-        const int u0 = split_group(qs, first, split, Gmax, seg_cost, t2, b0.data(), s0, tcol);
-        const int u1 = split_group(qs, first + split, count - split, Gmax, seg_cost, t2, b1.data(), s1, tcol);
-        const int G = std::max(1, std::max(u0, u1));
+        std::vector<int> b0(Gmax + 1);
+        std::vector<BandStats> s0;
+        const int G = std::max(1, split_rows(qs, first, count, Gmax, seg_cost, t2, b0.data(), s0));
         PdbLayout L{0, 0, 0, 1, t2, 1, count};
         for (int i = 0; i < count; ++i)
             L.rp_stride = std::max(L.rp_stride, pdb_row_warps(round4(qs[first + i].N), kPdbThreads, t2));
         bool ok = true;
         for (int b = 0; b < G; ++b) {
-            L.max_band_rows = std::max(L.max_band_rows, s0[b].rows + s1[b].rows);
-            L.max_band_cols = std::max(L.max_band_cols, s0[b].cols + s1[b].cols);
-            L.max_band_elems = std::max(L.max_band_elems, s0[b].elems + s1[b].elems);
-            L.max_segs = std::max(L.max_segs, s0[b].segs + s1[b].segs);
-            if (s0[b].segs + s1[b].segs > kMaxSeg) ok = false;
+            L.max_band_rows = std::max(L.max_band_rows, s0[b].rows);
+            L.max_band_cols = std::max(L.max_band_cols, s0[b].cols);
+            L.max_band_elems = std::max(L.max_band_elems, s0[b].elems);
+            L.max_segs = std::max(L.max_segs, s0[b].segs);
+            if (s0[b].segs > kMaxSeg) ok = false;
         }
         const size_t smem = pdb_smem_bytes(L, kPdbThreads);
         if (!ok || smem > (size_t)kPdMaxSmem) continue;
-        w->band.assign(2 * (G + 1), 0);
-        for (int c = 0; c <= G; ++c) {
-            w->band[c] = b0[c];
-            w->band[G + 1 + c] = b1[c];
-        }
+        w->band.assign(b0.begin(), b0.begin() + G + 1);
         w->first = first;
         w->count = count;
-        w->split = split;
         w->grid = G;
         w->layout = L;
         w->smem = smem;
@@ -818,14 +792,13 @@ int write_wave_tables(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& q
         d.m = q.m;
         d.ldx = round4(q.m);
         d.ldxt = round8(q.N);
-        if (i == w.split) row0 = 0;   // rows are counted per group
         d.row0 = row0;
         row0 += q.N;
         h->h_pairs[i] = d;
     }
-    for (int b = 0; b < 2 * (w.grid + 1); ++b) h->h_band[b] = w.band[b];
+    for (int b = 0; b <= w.grid; ++b) h->h_band[b] = w.band[b];
     FP_CUDA(cudaMemcpyAsync(h->d_pairs, h->h_pairs, sizeof(PairDesc) * mem.size(), cudaMemcpyHostToDevice, s));
-    FP_CUDA(cudaMemcpyAsync(h->d_band, h->h_band, sizeof(int) * 2 * (w.grid + 1), cudaMemcpyHostToDevice, s));
+    FP_CUDA(cudaMemcpyAsync(h->d_band, h->h_band, sizeof(int) * (w.grid + 1), cudaMemcpyHostToDevice, s));
     FP_CUDA(cudaMemsetAsync(h->d_wave, 0, sizeof(WaveCtrl), s));
     return 0;
 }
@@ -834,7 +807,6 @@ PdbParams wave_params(fastpfp_t h, const Wave& w, int npairs, const fastpfp_para
     PdbParams P{};
     P.pairs = h->d_pairs;
     P.npairs = npairs;
-    P.split = w.split;
     P.band_row = h->d_band;
     P.wave = h->d_wave;
     P.layout = w.layout;
@@ -1018,8 +990,8 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     for (auto& o : so) {
         o.Y = take(f32mat); o.X = take(f32mat); o.T = take(f32mat); o.K = take(f32mat);
         o.A16 = take(b16mat); o.A216 = take(b16mat); o.Xt16 = take(b16mat); o.T16 = take(b16mat);
-        o.col = take(3 * ld * sizeof(float)); o.s = take(3 * sizeof(double));
-        o.d = take(3 * sizeof(unsigned)); o.ctrl = take(sizeof(Ctrl));
+        o.col = take(colbuf_bytes((int)ld)); o.s = take(3 * sizeof(double));
+        o.d = take(kDbufWords * sizeof(unsigned)); o.ctrl = take(sizeof(Ctrl));
         o.rm = take(n * 4); o.cm = take(n * 4); o.rb = take(n * 8); o.cb = take(2 * n * 8);
         o.sA = take(n * n * 4); o.sA2 = take(n * n * 4); o.sB = take(n * kMaxK * 4);
         o.sB2 = take(n * kMaxK * 4); o.sX0 = take(n * n * 4); o.sXo = take(n * n * 4); o.sp = take(n * 4);
@@ -1499,7 +1471,7 @@ int solve_batch(fastpfp_t h, cudaStream_t s, int count, const fastpfp_pair* pair
 extern "C" {
 
 int fastpfp_bandwidth_probe(int device, int level, int sweeps, double* gbs) {
-    if (!gbs || sweeps < 1 || level < 0 || level > 2) return FASTPFP_ERR_ARG;
+    if (!gbs || sweeps < 1 || level < 0 || level > 3) return FASTPFP_ERR_ARG;
     if (cudaSetDevice(device) != cudaSuccess) return FASTPFP_ERR_CUDA;
     int num_sms = 0;
     if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
@@ -1508,6 +1480,7 @@ int fastpfp_bandwidth_probe(int device, int level, int sweeps, double* gbs) {
     double bytes = 0.0;
     cudaError_t e;
     if (level == 0) e = probe_smem(num_sms, sweeps, 0, &ms, &bytes);
+    else if (level == 3) e = probe_tmem(num_sms, sweeps, 0, &ms, &bytes);
     else e = probe_gmem(level == 1 ? (size_t)64 << 20 : (size_t)2 << 30, num_sms, sweeps, 0, &ms, &bytes);
     if (e != cudaSuccess || ms <= 0.f) return FASTPFP_ERR_CUDA;
     *gbs = bytes / ((double)ms * 1e-3) / 1e9;
@@ -1771,9 +1744,9 @@ int fastpfp_project(fastpfp_t h, void* stream, float* Y, int N, double tol, int 
     const Slot& sl = h->slots[0];
     const int ldy = round4(N);
     FP_CUDA(cudaMemsetAsync(sl.ctrl, 0, kCtrlHeader, s));
-    FP_CUDA(cudaMemsetAsync(sl.colbuf, 0, 3 * (size_t)h->ld * sizeof(float), s));
+    FP_CUDA(cudaMemsetAsync(sl.colbuf, 0, colbuf_bytes(h->ld), s));
     FP_CUDA(cudaMemsetAsync(sl.sbuf, 0, 3 * sizeof(double), s));
-    FP_CUDA(cudaMemsetAsync(sl.dbuf, 0, 3 * sizeof(unsigned), s));
+    FP_CUDA(cudaMemsetAsync(sl.dbuf, 0, kDbufWords * sizeof(unsigned), s));
     FP_CUDA(cudaMemsetAsync(sl.Y, 0, (size_t)N * ldy * sizeof(float), s));
     FP_CUDA(cudaMemcpy2DAsync(sl.Y, (size_t)ldy * 4, Y, (size_t)N * 4, (size_t)N * 4, N,
                               cudaMemcpyDeviceToDevice, s));

@@ -12,6 +12,19 @@ namespace fpfp {
 struct Ctrl;
 
 // ------------------------------------------------------------ projection
+// Column-sum scratch of one pair whose slacked rows hold ldy floats: three
+// rotating FP32 accumulators of the rounds (3 x ldy floats), then the FP64
+// column sums of the launch's input (ldy doubles, 16-byte aligned since ldy
+// is a multiple of 4).  The round maxima take kDbufWords words: three
+// rotating max|dY|, then max|y| of the launch's input.
+constexpr int kDbufWords = 4;
+__host__ __device__ inline size_t colbuf_bytes(int ldy) {
+    return (size_t)ldy * (3 * sizeof(float) + sizeof(double));
+}
+__host__ __device__ inline double* colbuf64(float* colbuf, int ldy) {
+    return reinterpret_cast<double*>(colbuf + 3 * (size_t)ldy);
+}
+
 constexpr int kPdOuterStep = 1;     // P_D rounds + blend/normalise + loop control
 constexpr int kPdProjectOnly = 0;   // P_D rounds only (fastpfp_project)
 constexpr int kPdMaxSmem = 226 * 1024;   // dynamic shared memory per CTA (the opt-in limit is 227 KB)
@@ -33,9 +46,9 @@ struct PdParams {
     int max_outer;
     int refine_iters;
     double switch_tol;
-    float* colbuf;      // 3 x ldy rotating column-sum accumulators, zero between launches
+    float* colbuf;      // colbuf_bytes(ldy) of column sums, zero between launches
     double* sbuf;       // 3 rotating totals
-    unsigned* dbuf;     // 3 rotating max|dY| (float bits)
+    unsigned* dbuf;     // kDbufWords words: 3 rotating max|dY|, max|y| of the input (float bits)
     Ctrl* ctrl;
     long long timeout_ns;
     int rpc;            // rows per CTA
@@ -65,21 +78,21 @@ struct PairDesc {
     float* Y;             // N x ldy slacked matrix
     float* X;             // N x ldx master X
     __nv_bfloat16* Xt16;  // nullable BF16 copy of X^T (m x ldxt)
-    float* colbuf;        // 3 x ldy column-sum accumulators
+    float* colbuf;        // colbuf_bytes(ldy) of column sums
     double* sbuf;         // 3 totals
-    unsigned* dbuf;       // 3 round maxima
+    unsigned* dbuf;       // kDbufWords round maxima
     Ctrl* ctrl;           // the pair's control block
     int N, ldy, m, ldx, ldxt;
-    int row0;             // first row of the pair in its group's concatenated rows
+    int row0;             // first row of the pair in the wave's concatenated rows
 };
 
-// Wave-level state: error word, "every pair done", and one grid-barrier
-// counter per pair group (the two groups' rounds are interleaved).
+// Wave-level state: error word, "every pair done", the grid-barrier counter
+// (it only grows within a call) and its value when the next launch starts.
 struct WaveCtrl {
     int error;
     int all_done;
-    unsigned bar[2];
-    unsigned bar_base[2];
+    unsigned bar;
+    unsigned bar_base;
 };
 
 // Shared-memory sizing of the batched kernel (maxima over the CTAs' bands).
@@ -155,8 +168,7 @@ __host__ __device__ inline int pdb_tmem_rows(int nrows, int ldy, int nthr, int c
 struct PdbParams {
     const PairDesc* pairs;
     int npairs;
-    int split;            // pairs [0, split) form group 0, [split, npairs) group 1
-    const int* band_row;  // 2 x (grid + 1) row boundaries, per group, in its concatenated rows
+    const int* band_row;  // grid + 1 row boundaries in the wave's concatenated rows
     WaveCtrl* wave;
     PdbLayout layout;
     float alpha;
@@ -273,6 +285,9 @@ cudaError_t gemm_f32t_group(const GemmF32TGroup& g, cudaStream_t s);
 // *ms = elapsed time of the timed sweeps, *bytes = bytes they moved.
 cudaError_t probe_smem(int num_sms, int sweeps, cudaStream_t s, float* ms, double* bytes);
 cudaError_t probe_gmem(size_t buf_bytes, int num_sms, int sweeps, cudaStream_t s, float* ms, double* bytes);
+// Read + write sweeps of every SM's tensor memory (all 512 columns) with
+// the wave kernel's 16-column tcgen05.ld / tcgen05.st accesses.
+cudaError_t probe_tmem(int num_sms, int sweeps, cudaStream_t s, float* ms, double* bytes);
 // Best time of one n x n x n product C = A B^T on the solver's kernels
 // (FP32 SIMT, BF16 or E4M3 tensor cores) over reps timed launches.
 cudaError_t probe_gemm(int precision, int n, int reps, cudaStream_t s, float* best_ms);

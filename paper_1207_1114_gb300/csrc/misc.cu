@@ -155,6 +155,8 @@ __global__ void x_out_kernel(const float* X, int N, int m, int ldx, int transpos
 }
 
 // 1/2 sum_{j,l} A[r(j), r(l)] A2[l, j] + lambda sum_j K[r(j), j], in FP64.
+// Every block stores its partial sum; the last block to finish adds them in
+// block order, so the result does not depend on the blocks' timing.
 __global__ void objective_kernel(const float* A, int N, const float* A2, int m, const float* K,
                                  int ldk, float lambda, const int32_t* row_of_col, Ctrl* ctrl) {
     double acc = 0.0;
@@ -174,10 +176,21 @@ __global__ void objective_kernel(const float* A, int N, const float* A2, int m, 
     acc = warp_sum_d(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
+    __shared__ int last;
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        atomicAdd(&ctrl->objective, t);
+        ctrl->obj_part[blockIdx.x] = t;
+        __threadfence();
+        last = atomicAdd(&ctrl->obj_ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double t = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(&ctrl->obj_part[b]);
+        ctrl->objective = t;
+        ctrl->obj_ticket = 0u;
     }
 }
 
@@ -292,8 +305,8 @@ cudaError_t write_outputs(const int32_t* row_of_col, int N, int m, int transpose
 cudaError_t objective(const float* A, int N, const float* A2, int m, const float* K, int ldk,
                       float lambda, const int32_t* row_of_col, Ctrl* ctrl, cudaStream_t s) {
     const size_t total = (size_t)m * m;
-    objective_kernel<<<grid_for(total, 256, 1024), 256, 0, s>>>(A, N, A2, m, K, ldk, lambda,
-                                                                row_of_col, ctrl);
+    objective_kernel<<<grid_for(total, 256, kObjBlocks), 256, 0, s>>>(A, N, A2, m, K, ldk, lambda,
+                                                                      row_of_col, ctrl);
     return cudaGetLastError();
 }
 

@@ -1,11 +1,13 @@
 // noalloc.cu -- fastpfp_project_noalloc: the successive projection of
 // fastpfp_project for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code that runs inside a host
-// application's fixed device-memory arena, inside a region being captured
-// into a CUDA graph, or under a real-time rule that forbids allocation after
-// start-up.  They cannot create a handle (fastpfp_create allocates), so this
-// entry point needs none.  The caller passes the matrix Y in and gets it
+// Some callers cannot call cudaMalloc at all: a plugin that a host
+// application hands a fixed device-memory arena (the application accounts
+// for every byte on the GPU and refuses allocations made behind its back),
+// or a real-time loop that forbids allocation after start-up (cudaMalloc can
+// block and synchronise the device for an unbounded time).  They cannot
+// create a handle (fastpfp_create allocates), so this entry point needs
+// none.  The caller passes the matrix Y in and gets it
 // back in place; the only scratch the projection kernel needs beyond Y (its
 // rotating column-sum accumulators, the FP64 totals, the round maxima and
 // the barrier/control words) lives in one file-scope device array of fixed
@@ -25,7 +27,7 @@ namespace {
 constexpr int kNoallocMaxN = 4096;   // largest N this entry point accepts
 constexpr int kMaxDevices = 64;
 constexpr size_t kCtrlBytes = (sizeof(Ctrl) + 255) & ~size_t(255);
-constexpr size_t kColBytes = 3 * (size_t)kNoallocMaxN * sizeof(float);
+constexpr size_t kColBytes = (size_t)kNoallocMaxN * (3 * sizeof(float) + sizeof(double));   // colbuf_bytes
 constexpr size_t kScratchBytes = kCtrlBytes + kColBytes + 256 + 256;
 
 // The shared scratch.  Host code must not use this name as a device address:
@@ -83,9 +85,9 @@ extern "C" int fastpfp_project_noalloc(void* stream, float* Y, int N, double tol
     unsigned* dbuf = reinterpret_cast<unsigned*>(d->scratch + kCtrlBytes + kColBytes + 256);
     // the previous call's contents stay in the array: clear what must start at zero
     if (cudaMemsetAsync(ctrl, 0, offsetof(Ctrl, inner_trace), s) != cudaSuccess ||
-        cudaMemsetAsync(colbuf, 0, 3 * (size_t)N * sizeof(float), s) != cudaSuccess ||
+        cudaMemsetAsync(colbuf, 0, colbuf_bytes(N), s) != cudaSuccess ||
         cudaMemsetAsync(sbuf, 0, 3 * sizeof(double), s) != cudaSuccess ||
-        cudaMemsetAsync(dbuf, 0, 3 * sizeof(unsigned), s) != cudaSuccess)
+        cudaMemsetAsync(dbuf, 0, kDbufWords * sizeof(unsigned), s) != cudaSuccess)
         return FASTPFP_ERR_CUDA;
 
     PdLaunch L;

@@ -33,6 +33,55 @@ __global__ void __launch_bounds__(kProbeThreads, 1) smem_probe_kernel(int floats
     if (threadIdx.x == 0) sink[blockIdx.x] = buf[0].x + buf[q - 1].w;
 }
 
+// Tensor memory used as plain storage, as the wave kernel holds band rows:
+// every CTA (one per SM) allocates all 512 TMEM columns, and each warp
+// sweeps its 32-lane quarter of one 128-column block with 16-column
+// tcgen05.ld / tcgen05.st accesses (64 bytes per thread per access, the
+// wave kernel's x16 form), adding one to every word.
+__global__ void __launch_bounds__(kProbeThreads, 1) tmem_probe_kernel(int sweeps, float* sink) {
+    __shared__ uint32_t s_tmem;
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (unsigned)__cvta_generic_to_shared(&s_tmem)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t t = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(128 * (warp >> 2));
+    float acc = 0.f;
+    for (int s = 0; s < sweeps; ++s) {
+        for (int c = 0; c < 128; c += 16) {
+            uint32_t r[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(t + c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) + 1.0f);
+            asm volatile(
+                "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                ::"r"(t + c), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+                  "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+                : "memory");
+            acc += __uint_as_float(r[0]);
+        }
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(512) : "memory");
+    if ((threadIdx.x & 31) == 0) sink[blockIdx.x * (kProbeThreads / 32) + warp] = acc;
+}
+
 // Global memory: the grid sweeps `bytes` of one buffer (L2-resident when it
 // is small enough), each sweep a read-modify-write of every float4.
 __global__ void __launch_bounds__(kProbeThreads) gmem_probe_kernel(float4* buf, size_t q, int sweeps) {
@@ -146,6 +195,35 @@ cudaError_t probe_smem(int num_sms, int sweeps, cudaStream_t s, float* ms, doubl
     if (e == cudaSuccess) {
         cudaEventElapsedTime(ms, a, b);
         *bytes = 8.0 * (double)floats * (double)num_sms * (double)sweeps;   // read + write
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    return e;
+}
+
+cudaError_t probe_tmem(int num_sms, int sweeps, cudaStream_t s, float* ms, double* bytes) {
+    // more than half an SM's shared memory per CTA: one CTA (one 512-column
+    // TMEM allocation) per SM
+    const int one_per_sm = 120 * 1024;
+    cudaError_t e = cudaFuncSetAttribute((const void*)tmem_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         one_per_sm);
+    if (e != cudaSuccess) return e;
+    float* sink = nullptr;
+    if ((e = cudaMalloc(&sink, sizeof(float) * num_sms * (kProbeThreads / 32))) != cudaSuccess) return e;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    tmem_probe_kernel<<<num_sms, kProbeThreads, one_per_sm, s>>>(1, sink);   // warm
+    cudaEventRecord(a, s);
+    tmem_probe_kernel<<<num_sms, kProbeThreads, one_per_sm, s>>>(sweeps, sink);
+    cudaEventRecord(b, s);
+    e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        cudaEventElapsedTime(ms, a, b);
+        // 128 lanes x 512 columns x 4 bytes per SM, read and written per sweep
+        *bytes = 2.0 * 128.0 * 512.0 * 4.0 * (double)num_sms * (double)sweeps;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);

@@ -7,7 +7,10 @@
 // c = Y^T 1 and the total s = 1^T Y 1 are the only cross-CTA quantities:
 // each round every CTA adds its column partials into one of three rotating
 // global accumulators (vector red.add) and its FP64 share of s, then one
-// bounded grid barrier ends the round.  Round u reads the sums of round u-1,
+// bounded grid barrier ends the round.  Every partial is rounded first to a
+// power-of-two quantum from a bound all CTAs share (common.cuh), so the sums
+// are exact whatever order the atomics land in; the input's sums are taken
+// in FP64 the same way after a first barrier that agrees on max|y|.  Round u reads the sums of round u-1,
 // applies Eq. (P1) elementwise
 //      y <- y + 1/N + s/N^2 - r_i/N - c_j/N
 // then Eq. (P2) y <- max(y, 0), measures max|dy|, and accumulates the sums
@@ -30,8 +33,9 @@ struct Smem {
     float* rowpart;    // rpc x 32 per-warp row partials
     double* dred;      // 32 doubles of block-reduction scratch
     float* fred;       // 32 floats of block-reduction scratch
-    int* ictl;         // [0] non-finite total, [1] stop the rounds
-    float* fctl;       // [0] max|dY| of the last round
+    int* ictl;         // [0] non-finite total, [1] stop the rounds, [2] bound mode of the next pass
+    float* fctl;       // [0] max|dY| of the last round, [1] bound of the next pass's column sums
+    double* qd;        // [0], [1] quantum (dn, up) of the next pass's share of s
 };
 
 // Shared-memory layout; pd_smem_bytes() below must mirror it.
@@ -54,6 +58,8 @@ __device__ __forceinline__ Smem carve(char* base, int rpc, int Q, bool res) {
     s.ictl = reinterpret_cast<int*>(base + off);
     off += 4 * sizeof(int);
     s.fctl = reinterpret_cast<float*>(base + off);
+    off += 4 * sizeof(float);
+    s.qd = reinterpret_cast<double*>(base + off);
     return s;
 }
 
@@ -121,11 +127,13 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
 
     // ---- prologue: optional slack reset, band load, sums of the input Y.
     const bool reset_slack = (P.mode == kPdOuterStep) && P.slack_reset && P.m < N;
+    float ym = 0.f;   // max|y| of the band, for the quanta of the exact input sums
     for (int rr = 0; rr < nr; ++rr) {
         float4* src = Yg + (size_t)(r0 + rr) * Q;
         float4* dst = row_ptr(rr);
         for (int q = tid; q < Q; q += nthr) {
             float4 v = src[q];
+            ym = fmaxf(ym, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
             if (reset_slack) {
                 // keep columns < m, zero the slack columns m..N-1
                 const int c0 = 4 * q;
@@ -147,6 +155,21 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
             P.sbuf[1] = 0.0;
             P.dbuf[1] = 0u;
         }
+    }
+    {
+        const float bm = block_max_f(ym, S.fred);
+        if (tid == 0 && bm > 0.f) atomicMax(P.dbuf + 3, __float_as_uint(bm));
+    }
+    if (!grid_barrier(&C->bar, bar_base + G * (gen + 1), err, P.timeout_ns)) return;
+    ++gen;
+    // quanta of the input's sums: every column partial is at most N max|y|,
+    // the total at most N^2 max|y|
+    const float ymax = __uint_as_float(__ldcg(P.dbuf + 3));
+    const Quant64 q_in = quant64_for((double)N * (double)ymax * (double)kBoundMargin);
+    if (tid == 0) {
+        const Quant64 qs = quant64_for((double)N * (double)N * (double)ymax * (double)kBoundMargin);
+        S.qd[0] = qs.dn;
+        S.qd[1] = qs.up;
     }
     __syncthreads();
 
@@ -175,15 +198,46 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
             float bm = lane < (nthr >> 5) ? S.fred[lane] : 0.f;
             bm = warp_max(bm);
             if (lane == 0) {
-                atomicAdd(&P.sbuf[cur], sp);
+                atomicAdd(&P.sbuf[cur], quant64(sp, Quant64{S.qd[0], S.qd[1]}));
                 if (bm > 0.f) atomicMax(&P.dbuf[cur], __float_as_uint(bm));
             }
         }
         float* ccur = P.colbuf + (size_t)cur * ldy;
+        double* cin = colbuf64(P.colbuf, ldy);
+        if (u == 0) {
+            // the input's column sums, FP64
 #pragma unroll
-        for (int k = 0; k < kQpt; ++k) {
-            const int q = tid + k * nthr;
-            if (q < Q) red_add_v4(ccur + 4 * q, cpart[k].x, cpart[k].y, cpart[k].z, cpart[k].w);
+            for (int k = 0; k < kQpt; ++k) {
+                const int q = tid + k * nthr;
+                if (q < Q) {
+                    red_add_f64(cin + 4 * q + 0, quant64((double)cpart[k].x, q_in));
+                    red_add_f64(cin + 4 * q + 1, quant64((double)cpart[k].y, q_in));
+                    red_add_f64(cin + 4 * q + 2, quant64((double)cpart[k].z, q_in));
+                    red_add_f64(cin + 4 * q + 3, quant64((double)cpart[k].w, q_in));
+                }
+            }
+        } else {
+            // this pass's output is >= 0: column j's sum is at most
+            // c_j + 1 + s/N (previous c_j, s; cN holds c_j / N) or, after the
+            // input round, the one bound in fctl[1]
+            const bool one = S.ictl[2] != 0;
+            const float cb = S.fctl[1], Nf = (float)N;
+#pragma unroll
+            for (int k = 0; k < kQpt; ++k) {
+                const int q = tid + k * nthr;
+                if (q < Q) {
+                    float4 v = cpart[k];
+                    if (one) {
+                        const Quant32 a = quant32_for(cb);
+                        v = quant32x4(v, a, a, a, a);
+                    } else {
+                        const float m = kBoundMargin * Nf;
+                        v = quant32x4(v, quant32_for(fmaf(cN[k].x, m, cb)), quant32_for(fmaf(cN[k].y, m, cb)),
+                                      quant32_for(fmaf(cN[k].z, m, cb)), quant32_for(fmaf(cN[k].w, m, cb)));
+                    }
+                    red_add_v4(ccur + 4 * q, v.x, v.y, v.z, v.w);
+                }
+            }
         }
         if (!grid_barrier(&C->bar, bar_base + G * (gen + 1), err, P.timeout_ns, arrive)) return false;
         ++gen;
@@ -193,7 +247,14 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
         for (int k = 0; k < kQpt; ++k) {
             const int q = tid + k * nthr;
             if (q < Q) {
-                const float4 c = __ldcg(reinterpret_cast<const float4*>(ccur) + q);
+                float4 c;
+                if (u == 0) {
+                    const double2 a = __ldcg(reinterpret_cast<const double2*>(cin) + 2 * q);
+                    const double2 b = __ldcg(reinterpret_cast<const double2*>(cin) + 2 * q + 1);
+                    c = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+                } else {
+                    c = __ldcg(reinterpret_cast<const float4*>(ccur) + q);
+                }
                 cN[k] = make_float4(c.x * invN, c.y * invN, c.z * invN, c.w * invN);
             }
         }
@@ -207,6 +268,25 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
                 S.ictl[0] = isfinite(s) ? 0 : 1;
                 S.ictl[1] = (u > 0 && ((double)d < P.tol_inner || u >= P.max_inner)) ? 1 : 0;
                 S.fctl[0] = d;
+                // bounds of the next pass's sums: after the input every column
+                // sum is at most 4 N max|y| + 1 (input, row offsets and column
+                // offset of P1 each at most N max|y| per column); after a round
+                // column j's at most c_j + 1 + s/N, the total at most 2 s + N
+                const double mg = (double)kBoundMargin, Nd = (double)N;
+                double sb;
+                if (u == 0) {
+                    const double b1 = (4.0 * Nd * (double)ymax + 1.0) * mg;
+                    S.ictl[2] = 1;
+                    S.fctl[1] = (float)b1;
+                    sb = b1 * Nd * mg;
+                } else {
+                    S.ictl[2] = 0;
+                    S.fctl[1] = (float)((1.0 + s * invN_d) * mg);
+                    sb = (2.0 * s + Nd) * mg * mg;
+                }
+                const Quant64 qs = quant64_for(sb);
+                S.qd[0] = qs.dn;
+                S.qd[1] = qs.up;
             }
         }
         __syncthreads();
@@ -236,6 +316,26 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
         if (tid == 0) atomicCAS(err, 0, FASTPFP_ERR_NONFINITE);
         return;
     }
+
+    // Zeroes every accumulator of the launch (after its last cross-CTA read):
+    // the rotating column sums, totals and maxima, the FP64 input sums and
+    // the input's max|y|.
+    auto clear_sums = [&]() {
+        for (int b = 0; b < 3; ++b) {
+            float* cb = P.colbuf + (size_t)b * ldy;
+            for (int q = blockIdx.x * nthr + tid; q < Q; q += G * nthr)
+                reinterpret_cast<float4*>(cb)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        double2* c64 = reinterpret_cast<double2*>(colbuf64(P.colbuf, ldy));
+        for (int q = blockIdx.x * nthr + tid; q < Q; q += G * nthr) {
+            c64[2 * q] = make_double2(0.0, 0.0);
+            c64[2 * q + 1] = make_double2(0.0, 0.0);
+        }
+        if (blockIdx.x == 0 && tid == 0) {
+            for (int b = 0; b < 3; ++b) { P.sbuf[b] = 0.0; P.dbuf[b] = 0u; }
+            P.dbuf[3] = 0u;
+        }
+    };
 
     // ---- P1/P2 rounds (cN holds c/N of the previous pass, S.arow its a_i)
     int u = 0;
@@ -307,13 +407,8 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
         }
         if (!grid_barrier(&C->bar, bar_base + G * (gen + 1), err, P.timeout_ns)) return;
         ++gen;
-        for (int b = 0; b < 3; ++b) {
-            float* cb = P.colbuf + (size_t)b * ldy;
-            for (int q = blockIdx.x * nthr + tid; q < Q; q += G * nthr)
-                reinterpret_cast<float4*>(cb)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+        clear_sums();
         if (blockIdx.x == 0 && tid == 0) {
-            for (int b = 0; b < 3; ++b) { P.sbuf[b] = 0.0; P.dbuf[b] = 0u; }
             C->last_inner = u;
             C->last_delta = (double)delta;
             C->bar_base = bar_base + G * gen;
@@ -387,13 +482,8 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
     ++gen;
 
     // all cross-CTA reads of this launch are done: clear the accumulators
-    for (int b = 0; b < 3; ++b) {
-        float* cb = P.colbuf + (size_t)b * ldy;
-        for (int q = blockIdx.x * nthr + tid; q < Q; q += G * nthr)
-            reinterpret_cast<float4*>(cb)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    clear_sums();
     if (blockIdx.x == 0 && tid == 0) {
-        for (int b = 0; b < 3; ++b) { P.sbuf[b] = 0.0; P.dbuf[b] = 0u; }
         const double d = __longlong_as_double((long long)__ldcg(&C->dx_bits));
         if (!isfinite(d)) atomicCAS(err, 0, FASTPFP_ERR_NONFINITE);
         C->dx_bits = 0ull;
@@ -440,7 +530,7 @@ size_t pd_smem_bytes(int rpc, int Q, bool res) {
     off += (size_t)rpc * 4 * 2;
     off += (size_t)rpc * 32 * 4;
     off = (off + 15) & ~size_t(15);
-    off += 32 * 8 + 32 * 4 + 4 * 4 + 4 * 4;
+    off += 32 * 8 + 32 * 4 + 4 * 4 + 4 * 4 + 2 * 8;
     return off;
 }
 

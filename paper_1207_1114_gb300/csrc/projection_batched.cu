@@ -3,20 +3,19 @@
 // Algorithm 1 for a whole wave of graph pairs at once.
 //
 // The projection rounds are bound by grid-synchronisation latency, not by
-// bandwidth.  A wave therefore shares every barrier between many pairs.  The
-// kernel can also split a wave into two groups with their own barrier
-// counters and compute one group's round while the other's barrier completes
-//     arrive(A,u) -> wait(B,u-1) -> round B(u) -> arrive(B,u) -> wait(A,u) -> round A(u+1) ...
-// (the host chooses; with one group, group 1 is empty).
-// Within a group all rows of all pairs are concatenated and cut into one band
+// bandwidth.  A wave therefore shares every barrier between many pairs.
+// All rows of all pairs are concatenated and cut into one band
 // per CTA of about the same cost (entries plus a measured cost per pair the
 // band spans); a band may span several pairs ("segments") and stays on chip
 // for all rounds: the first rows of every thread in tensor memory (all 512
 // columns of the SM, used as storage through tcgen05.ld/st), the rest in
 // shared memory.  A round
-// applies Eq. (P1) and Eq. (P2) elementwise to every segment of the group,
+// applies Eq. (P1) and Eq. (P2) elementwise to every segment of the band,
 // measures max|dY|, and publishes the pairs' column partials (vector
-// red.add), FP64 shares of the totals s and round maxima.  After the group's
+// red.add), FP64 shares of the totals s and round maxima.  Every partial is
+// first rounded to a power-of-two quantum (common.cuh) from a bound all CTAs
+// share, so the sums are exact and do not depend on the order in which the
+// atomics land: a solve gives the same bits every run.  After the grid
 // barrier every CTA reads every pair's round maximum, so all CTAs take the
 // same stop decision for each pair (max|dY| < eps_2 or I_1 rounds) and leave
 // the loop together.  Pairs whose outer loop has finished are skipped.
@@ -30,7 +29,6 @@ namespace {
 
 struct Seg {
     int pair;       // index into the wave's pair table
-    int group;      // 0 or 1
     int lr0;        // first row of the segment inside its pair
     int nrows;      // rows of the segment
     int brow0;      // first row of the segment inside the band (rsum/rowpart index)
@@ -51,20 +49,23 @@ struct PairS {
     double s;       // total of the last finished pass
     int N, ldy;
     float abase;    // 1/N + s/N^2 of the last finished pass (the row offset is abase - r_i/N)
-    int pad;
+    int bmode;      // quanta of the next pass's column partials: 0 per column, 1 one for the pair
     double invN;    // 1/N
+    float cb;       // bmode 0: column j's bound is c_j * margin + cb; bmode 1: every column's bound
+    float ymax;     // max|y| of the launch's input
+    Quant64 sq;     // quantum of the next pass's contributions to s
 };
 
-static_assert(sizeof(Seg) == 48, "pdb_smem_bytes assumes 48-byte segments");
-static_assert(sizeof(PairS) == 56, "pdb_smem_bytes assumes 56-byte pair records");
+static_assert(sizeof(Seg) == 44, "pdb_smem_bytes assumes 44-byte segments");
+static_assert(sizeof(PairS) == 80, "pair records are 80 bytes");
 
 struct Shared {
     Seg* seg;            // L.max_segs
     PairS* pair;         // L.npairs
     int* pstate;         // L.npairs: bit0 active this launch, bit1 stopped
     int* pstop;          // L.npairs: round at which the pair stopped
-    int* ictl;           // [2] n segments, [3] non-finite, [4],[5] running pairs of group 0 / 1
-    int* qpref;          // 2 x (L.npairs + 1): per group, prefix sums of the pairs' column quads
+    int* ictl;           // [2] n segments, [3] non-finite, [4] running pairs
+    int* qpref;          // L.npairs + 1: prefix sums of the pairs' column quads
     float* fred;         // L.max_segs x 32 per-warp maxima
     float* rsum;         // band rows
     float* rowpart;      // band rows x rp_stride per-warp row partials
@@ -85,7 +86,7 @@ __device__ __forceinline__ Shared carve_b(char* base, const PdbLayout& L, int nt
     s.pstate = reinterpret_cast<int*>(take(sizeof(int) * L.npairs));
     s.pstop = reinterpret_cast<int*>(take(sizeof(int) * L.npairs));
     s.ictl = reinterpret_cast<int*>(take(sizeof(int) * 8));
-    s.qpref = reinterpret_cast<int*>(take(sizeof(int) * 2 * (L.npairs + 1)));
+    s.qpref = reinterpret_cast<int*>(take(sizeof(int) * (L.npairs + 1)));
     s.fred = reinterpret_cast<float*>(take(sizeof(float) * L.max_segs * 32));
     s.rsum = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_rows));
     s.rowpart = reinterpret_cast<float*>(take(sizeof(float) * L.max_band_rows * L.rp_stride));
@@ -429,52 +430,44 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     const unsigned G = gridDim.x;
     Shared S = carve_b(smem_raw, P.layout, nthr);
     int* err = &W->error;
-    const unsigned base0 = W->bar_base[0], base1 = W->bar_base[1];
-    unsigned gen[2] = {0u, 0u};
-    const int npairs = P.npairs, split = P.split;
+    const unsigned base = W->bar_base;
+    unsigned gen = 0u;
+    const int npairs = P.npairs;
     const int RPS = P.layout.rp_stride;
     // testing only (debug_flags bit 0): CTA 0 skips its first arrival of the
     // first launch of a solve, so every wait of that launch runs out
     bool skip_first = P.skip_arrive && blockIdx.x == 0 && ld_relaxed_i32(&P.pairs[0].ctrl->outer) == 0;
 
-    // ---- bands of both groups -> segments, pair states and per-pair fields
+    // ---- the band -> segments, pair states and per-pair fields
     if (tid == 0) {
         int nseg = 0, brow = 0, soff = 0, coff = 0, tcol = 0;
-        for (int g = 0; g < 2; ++g) {
-            const int* band = P.band_row + g * (G + 1);
-            const int b0 = band[blockIdx.x], b1 = band[blockIdx.x + 1];
-            const int p0 = g == 0 ? 0 : split, p1 = g == 0 ? split : npairs;
-            for (int p = p0; p < p1 && nseg < P.layout.max_segs; ++p) {
-                const PairDesc& d = P.pairs[p];
-                const int lo = max(b0, d.row0), hi = min(b1, d.row0 + d.N);
-                if (lo >= hi) continue;
-                Seg s;
-                s.pair = p;
-                s.group = g;
-                s.lr0 = lo - d.row0;
-                s.nrows = hi - lo;
-                s.brow0 = brow;
-                s.soff = soff;
-                s.coff = coff;
-                s.tcol = tcol;
-                s.tm = pdb_tmem_rows(s.nrows, d.ldy, nthr, tcol, &s.ntm, &tcol, P.layout.two_quad_ties);
-                const PdbShape sh = pdb_shape(d.ldy, nthr, P.layout.two_quad_ties);
-                s.qpg = sh.qpg;
-                s.rpkq = 4 * sh.rp + sh.kq;
-                S.seg[nseg++] = s;
-                brow += s.nrows;
-                soff += (s.nrows - s.ntm) * d.ldy;
-                coff += d.ldy;
-            }
+        const int b0 = P.band_row[blockIdx.x], b1 = P.band_row[blockIdx.x + 1];
+        for (int p = 0; p < npairs && nseg < P.layout.max_segs; ++p) {
+            const PairDesc& d = P.pairs[p];
+            const int lo = max(b0, d.row0), hi = min(b1, d.row0 + d.N);
+            if (lo >= hi) continue;
+            Seg s;
+            s.pair = p;
+            s.lr0 = lo - d.row0;
+            s.nrows = hi - lo;
+            s.brow0 = brow;
+            s.soff = soff;
+            s.coff = coff;
+            s.tcol = tcol;
+            s.tm = pdb_tmem_rows(s.nrows, d.ldy, nthr, tcol, &s.ntm, &tcol, P.layout.two_quad_ties);
+            const PdbShape sh = pdb_shape(d.ldy, nthr, P.layout.two_quad_ties);
+            s.qpg = sh.qpg;
+            s.rpkq = 4 * sh.rp + sh.kq;
+            S.seg[nseg++] = s;
+            brow += s.nrows;
+            soff += (s.nrows - s.ntm) * d.ldy;
+            coff += d.ldy;
         }
         S.ictl[2] = nseg;
         S.ictl[3] = 0;
-        for (int g = 0; g < 2; ++g) {
-            const int p0 = g == 0 ? 0 : split, p1 = g == 0 ? split : npairs;
-            int* qp = S.qpref + g * (P.layout.npairs + 1);
-            qp[0] = 0;
-            for (int p = p0; p < p1; ++p) qp[p - p0 + 1] = qp[p - p0] + (P.pairs[p].ldy >> 2);
-        }
+        int* qp = S.qpref;
+        qp[0] = 0;
+        for (int p = 0; p < npairs; ++p) qp[p + 1] = qp[p] + (P.pairs[p].ldy >> 2);
     }
     for (int p = tid; p < npairs; p += nthr) {
         const PairDesc& d = P.pairs[p];
@@ -489,8 +482,11 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         ps.N = d.N;
         ps.ldy = d.ldy;
         ps.abase = 0.f;
-        ps.pad = 0;
+        ps.bmode = 0;
         ps.invN = 1.0 / (double)d.N;
+        ps.cb = 0.f;
+        ps.ymax = 0.f;
+        ps.sq = Quant64{1.0, 1.0};
         S.pair[p] = ps;
     }
     __syncthreads();
@@ -521,11 +517,14 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         return v;
     };
 
-    // ---- prologue: load the band (optional slack reset)
+    // ---- prologue: load the band (optional slack reset), with max|y| of
+    // every segment for the quanta of the exact input sums below
     for (int si = 0; si < nseg; ++si) {
         const Seg sg = S.seg[si];
         const PairDesc& d = P.pairs[sg.pair];
         if (!(S.pstate[sg.pair] & 1)) continue;
+        float ym = 0.f;
+        auto absmax = [&ym](float4 v) { ym = fmaxf(ym, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)))); };
         const int Q = d.ldy >> 2, m = d.m;
         const bool reset = P.slack_reset && m < d.N;
         const float4* src = reinterpret_cast<const float4*>(d.Y) + (size_t)sg.lr0 * Q;
@@ -541,6 +540,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                         if (r < sg.nrows && q < Q) {
                             v = src[(size_t)r * Q + q];
                             if (reset) v = slack_mask(v, 4 * q, m);
+                            absmax(v);
                         }
                         tm_st4(tme + sg.tcol + 4 * (mp.kq * k + j), v);
                     }
@@ -553,20 +553,32 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         for (int e = tid; e < (sg.nrows - sg.ntm) * Q; e += nthr) {
             float4 v = src2[e];
             if (reset) v = slack_mask(v, 4 * (e % Q), m);
+            absmax(v);
             dst[e] = v;
         }
+        ym = warp_max(ym);
+        if (lane == 0) S.fred[si * 32 + warp] = ym;
     }
     tm_wait_st();
     __syncthreads();
+    if (warp < 2) {
+        for (int si = warp; si < nseg; si += 2) {
+            const Seg sg = S.seg[si];
+            if (!(S.pstate[sg.pair] & 1)) continue;
+            float bm = lane < (nthr >> 5) ? S.fred[si * 32 + lane] : 0.f;
+            bm = warp_max(bm);
+            if (lane == 0 && bm > 0.f) atomicMax(S.pair[sg.pair].dbuf + 3, __float_as_uint(bm));
+        }
+    }
+    grid_arrive(&W->bar);   // waited for at the start of body()
 
-    // One pass over the active segments of group g.  UPDATE = false only sums.
-    // Row partials go to rowpart, per-segment maxima to fred, column partials
-    // to the pairs' accumulator `cur`.
-    auto pass = [&](int g, auto update_tag, int cur) {
+    // One pass over the active segments.  UPDATE = false only sums.  Row
+    // partials go to rowpart, per-segment maxima to fred, column partials to
+    // the pairs' accumulator `cur`.
+    auto pass = [&](auto update_tag, int cur) {
         constexpr bool UPDATE = decltype(update_tag)::value;
         for (int si = 0; si < nseg; ++si) {
             const Seg sg = S.seg[si];
-            if (sg.group != g) continue;
             const int pst = S.pstate[sg.pair];
             if (!(pst & 1) || (pst & 2)) continue;   // inactive or stopped pair
             const PairS pr = S.pair[sg.pair];
@@ -612,20 +624,54 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             if (UPDATE) tm_wait_st();
             dmax = warp_max(dmax);
             if (lane == 0) S.fred[si * 32 + warp] = dmax;
-            // column partials: every row group adds its own, one red.v4 per
-            // quad (L2 folds the row groups; no block-wide fold, no barrier)
-            float* acc = pr.colbuf + (size_t)cur * pr.ldy;
-            if (in_grp) {
-                if (mp.q0 < Q) red_add_v4(acc + 4 * mp.q0, cp0.x, cp0.y, cp0.z, cp0.w);
-                if (mp.kq > 1 && mp.q0 + mp.QP < Q)
+            // column partials: every row group adds its own (L2 folds the row
+            // groups; no block-wide fold, no barrier), rounded to the column's
+            // quantum so that the sums are exact in any order
+            if (UPDATE && in_grp) {
+                // the pass's output is >= 0, so column j's new sum is at most
+                // c_j + 1 + s/N (previous round's c_j, s) or, after the input
+                // round, the pair's bound cb (set in wait_post)
+                const float4* cNq = reinterpret_cast<const float4*>(S.cN + sg.coff);
+                auto qz = [&](float4 v, int q) {
+                    if (pr.bmode) {
+                        const Quant32 u = quant32_for(pr.cb);
+                        return quant32x4(v, u, u, u, u);
+                    }
+                    const float4 c = cNq[q];
+                    return quant32x4(v, quant32_for(fmaf(c.x, kBoundMargin, pr.cb)),
+                                     quant32_for(fmaf(c.y, kBoundMargin, pr.cb)),
+                                     quant32_for(fmaf(c.z, kBoundMargin, pr.cb)),
+                                     quant32_for(fmaf(c.w, kBoundMargin, pr.cb)));
+                };
+                float* acc = pr.colbuf + (size_t)cur * pr.ldy;
+                if (mp.q0 < Q) {
+                    cp0 = qz(cp0, mp.q0);
+                    red_add_v4(acc + 4 * mp.q0, cp0.x, cp0.y, cp0.z, cp0.w);
+                }
+                if (mp.kq > 1 && mp.q0 + mp.QP < Q) {
+                    cp1 = qz(cp1, mp.q0 + mp.QP);
                     red_add_v4(acc + 4 * (mp.q0 + mp.QP), cp1.x, cp1.y, cp1.z, cp1.w);
+                }
+            } else if (in_grp) {
+                // the input's column sums in FP64: every partial is at most
+                // N max|y| in magnitude
+                const Quant64 q0 = quant64_for((double)N * (double)pr.ymax * (double)kBoundMargin);
+                double* acc = colbuf64(pr.colbuf, pr.ldy);
+                auto add4 = [&](float4 v, int q) {
+                    double* a = acc + 4 * (size_t)q;
+                    red_add_f64(a + 0, quant64((double)v.x, q0));
+                    red_add_f64(a + 1, quant64((double)v.y, q0));
+                    red_add_f64(a + 2, quant64((double)v.z, q0));
+                    red_add_f64(a + 3, quant64((double)v.w, q0));
+                };
+                if (mp.q0 < Q) add4(cp0, mp.q0);
+                if (mp.kq > 1 && mp.q0 + mp.QP < Q) add4(cp1, mp.q0 + mp.QP);
             }
         }
-        // the row sums of the group's segments, once every warp's partials are in
+        // the row sums of the segments, once every warp's partials are in
         __syncthreads();
         for (int si = 0; si < nseg; ++si) {
             const Seg sg = S.seg[si];
-            if (sg.group != g) continue;
             const int pst = S.pstate[sg.pair];
             if (!(pst & 1) || (pst & 2)) continue;
             const int nw = pdb_row_warps(S.pair[sg.pair].ldy, nthr, P.layout.two_quad_ties);
@@ -638,12 +684,13 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         }
     };
 
-    // Zero accumulator `which` of group g's pairs with threads t of nt.  The
-    // group's column quads are numbered consecutively over its pairs and
-    // dealt round-robin over the CTAs, so every CTA zeroes about the same few.
-    auto clear_acc = [&](int g, int which, int t, int nt) {
-        const int p0 = g == 0 ? 0 : split, np = (g == 0 ? split : npairs) - p0;
-        const int* qp = S.qpref + g * (P.layout.npairs + 1);
+    // Zero accumulator `which` of the wave's pairs with threads t of nt
+    // (which == 3: the FP64 input sums and the input's max|y|).  The column
+    // quads are numbered consecutively over the pairs and dealt round-robin
+    // over the CTAs, so every CTA zeroes about the same few.
+    auto clear_acc = [&](int which, int t, int nt) {
+        const int np = npairs;
+        const int* qp = S.qpref;
         const int total = qp[np];
         for (int f = t * (int)G + (int)blockIdx.x; f < total; f += nt * (int)G) {
             int lo = 0, hi = np;   // the pair whose quads hold f: qp[lo] <= f < qp[lo + 1]
@@ -651,8 +698,15 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 const int mid = (lo + hi) >> 1;
                 if (qp[mid] <= f) lo = mid; else hi = mid;
             }
-            const PairS& pr = S.pair[p0 + lo];
+            const PairS& pr = S.pair[lo];
             const int q = f - qp[lo];
+            if (which == 3) {
+                double2* a = reinterpret_cast<double2*>(colbuf64(pr.colbuf, pr.ldy)) + 2 * (size_t)q;
+                a[0] = make_double2(0.0, 0.0);
+                a[1] = make_double2(0.0, 0.0);
+                if (q == 0) pr.dbuf[3] = 0u;
+                continue;
+            }
             reinterpret_cast<float4*>(pr.colbuf + (size_t)which * pr.ldy)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (q == 0) {
                 pr.sbuf[which] = 0.0;
@@ -661,19 +715,18 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         }
     };
 
-    // End of group g's pass: warps 0 and 1 publish the segments' totals and
-    // round maxima (alternate segments) while warps 2.. zero accumulator
-    // `clear_which` (>= 0) of the group's pairs; all of it precedes the
+    // End of a pass: warps 0 and 1 publish the segments' totals and round
+    // maxima (alternate segments) while warps 2.. zero accumulator
+    // `clear_which` (>= 0) of the wave's pairs; all of it precedes the
     // arrival, so the zeros are visible before any CTA's next-round
     // reductions.  A band's total (at most a few dozen FP32 row sums) is
     // added in FP32 and accumulated over the CTAs in FP64.
-    auto publish = [&](int g, int cur, int clear_which) {
+    auto publish = [&](int cur, int clear_which) {
         __syncthreads();
-        if (tid == 0) S.ictl[4 + g] = 0;   // the running-pair count of wait_post
+        if (tid == 0) S.ictl[4] = 0;   // the running-pair count of wait_post
         if (warp < 2) {
             for (int si = warp; si < nseg; si += 2) {
                 const Seg sg = S.seg[si];
-                if (sg.group != g) continue;
                 const int pst = S.pstate[sg.pair];
                 if (!(pst & 1) || (pst & 2)) continue;
                 float sp = 0.f;
@@ -683,46 +736,53 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 bm = warp_max(bm);
                 if (lane == 0) {
                     const PairS& pr = S.pair[sg.pair];
-                    atomicAdd(pr.sbuf + cur, (double)sp);
+                    atomicAdd(pr.sbuf + cur, quant64((double)sp, pr.sq));
                     if (bm > 0.f) atomicMax(pr.dbuf + cur, __float_as_uint(bm));
                 }
             }
         } else if (clear_which >= 0) {
-            clear_acc(g, clear_which, tid - 64, nthr - 64);
+            clear_acc(clear_which, tid - 64, nthr - 64);
         }
         if (skip_first) {   // fault-injection test: this arrival is lost
             skip_first = false;
             __syncthreads();
         } else {
-            grid_arrive(&W->bar[g]);
+            grid_arrive(&W->bar);
         }
     };
 
-    // Wait for group g's barrier of pass `cur` (round u), then take every
-    // stop decision of the group's pairs (identical in every CTA), load the
-    // column sums c_j of its segments and turn the new totals into the next
-    // row-offset bases 1/N + s/N^2.
-    auto wait_post = [&](int g, int cur, int u, bool check_stop) -> bool {
-        const unsigned target = (g == 0 ? base0 : base1) + G * (gen[g] + 1u);
-        if (!grid_wait(&W->bar[g], target, err, P.timeout_ns)) return false;
-        ++gen[g];
+    // Wait for the barrier of pass `cur` (round u), then take every pair's
+    // stop decision (identical in every CTA), load the column sums c_j of the
+    // segments and turn the new totals into the next row-offset bases
+    // 1/N + s/N^2.
+    auto wait_post = [&](int cur, int u, bool check_stop) -> bool {
+        const unsigned target = base + G * (gen + 1u);
+        if (!grid_wait(&W->bar, target, err, P.timeout_ns)) return false;
+        ++gen;
         // every segment's column sums in flight at once (copied, not loaded
-        // and stored, so no segment waits for the previous one's latency)
+        // and stored, so no segment waits for the previous one's latency);
+        // the input's sums (u = 0) are FP64 and converted here
         for (int si = 0; si < nseg; ++si) {
             const Seg sg = S.seg[si];
-            if (sg.group != g) continue;
             const int pst = S.pstate[sg.pair];
             if (!(pst & 1) || (pst & 2)) continue;
             const PairS pr = S.pair[sg.pair];
-            const float4* c = reinterpret_cast<const float4*>(pr.colbuf + (size_t)cur * pr.ldy);
             float4* dst = reinterpret_cast<float4*>(S.cN + sg.coff);
+            if (u == 0) {
+                const double2* c = reinterpret_cast<const double2*>(colbuf64(pr.colbuf, pr.ldy));
+                for (int q = tid; q < (pr.ldy >> 2); q += nthr) {
+                    const double2 a = __ldcg(c + 2 * q), b = __ldcg(c + 2 * q + 1);
+                    dst[q] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+                }
+                continue;
+            }
+            const float4* c = reinterpret_cast<const float4*>(pr.colbuf + (size_t)cur * pr.ldy);
             for (int q = tid; q < (pr.ldy >> 2); q += nthr) cp_async_cg16(dst + q, c + q);
         }
-        // the group's pairs, one per thread of the first four warps (their
-        // totals come from L2: one round trip for up to 128 pairs)
-        const int p0 = g == 0 ? 0 : split, p1 = g == 0 ? split : npairs;
+        // the pairs, one per thread of the first four warps (their totals
+        // come from L2: one round trip for up to 128 pairs)
         int any = 0;
-        for (int p = p0 + tid; p < p1 && tid < 128; p += 128) {
+        for (int p = tid; p < npairs && tid < 128; p += 128) {
             int ps = S.pstate[p];
             if ((ps & 1) && !(ps & 2)) {
                 PairS& pr = S.pair[p];
@@ -732,6 +792,22 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 pr.s = s;
                 pr.abase = (float)(invN + s * invN * invN);
                 if (!isfinite(s)) S.ictl[3] = 1;
+                // bounds of the next pass's sums (its output is >= 0): after
+                // the input, every column sum is at most 4 N max|y| + 1 (the
+                // input, the row offsets and the column offset of P1 are each
+                // at most N max|y| per column); after a round, column j's at
+                // most c_j + 1 + s/N and the total at most 2 s + N
+                const double mg = (double)kBoundMargin;
+                if (u == 0) {
+                    const double b1 = (4.0 * (double)pr.N * (double)pr.ymax + 1.0) * mg;
+                    pr.bmode = 1;
+                    pr.cb = (float)b1;
+                    pr.sq = quant64_for(b1 * (double)pr.N * mg);
+                } else {
+                    pr.bmode = 0;
+                    pr.cb = (float)((1.0 + s * invN) * mg);
+                    pr.sq = quant64_for((2.0 * s + (double)pr.N) * mg * mg);
+                }
                 if (check_stop && ((double)dd < P.tol_inner || u >= P.max_inner)) {
                     ps |= 2;
                     S.pstop[p] = u;
@@ -740,9 +816,9 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 any |= !(ps & 2);
             }
         }
-        // ictl[4 + g] counts the group's pairs still running (zeroed in publish)
+        // ictl[4] counts the warps that still have a running pair (zeroed in publish)
         any = __any_sync(0xffffffffu, any);
-        if (warp < 4 && lane == 0 && any) atomicAdd(&S.ictl[4 + g], 1);
+        if (warp < 4 && lane == 0 && any) atomicAdd(&S.ictl[4], 1);
         cp_async_wait_all();
         __syncthreads();
         return true;
@@ -751,44 +827,35 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     // Everything from here until the tensor memory is released; a timeout or
     // a non-finite total leaves it early (all threads of the CTA together).
     auto body = [&]() {
-    // ---- sums of the input of both groups
-    const bool has1 = split < npairs;
-    pass(0, std::false_type{}, 0);
-    publish(0, 0, -1);
-    if (has1) {
-        pass(1, std::false_type{}, 0);
-        publish(1, 0, -1);
+    // ---- max|y| of every pair's input (the prologue's barrier), the
+    // quantum of the input's total, then the exact sums of the input
+    if (!grid_wait(&W->bar, base + G * (gen + 1u), err, P.timeout_ns)) return;
+    ++gen;
+    for (int p = tid; p < npairs; p += nthr) {
+        if (!(S.pstate[p] & 1)) continue;
+        PairS& pr = S.pair[p];
+        pr.ymax = __uint_as_float(__ldcg(pr.dbuf + 3));
+        const double N = (double)pr.N;
+        pr.sq = quant64_for(N * N * (double)pr.ymax * (double)kBoundMargin);   // |s| <= N^2 max|y|
     }
-    if (!wait_post(0, 0, 0, false)) return;
-    if (has1 && !wait_post(1, 0, 0, false)) return;
+    __syncthreads();
+    pass(std::false_type{}, 0);
+    publish(0, -1);
+    if (!wait_post(0, 0, false)) return;
     if (S.ictl[3]) {
         if (tid == 0) atomicCAS(err, 0, FASTPFP_ERR_NONFINITE);
         return;
     }
-    bool act0 = S.ictl[4] != 0, act1 = has1 && S.ictl[5] != 0, pend1 = false;
+    bool act = S.ictl[4] != 0;
 
-    // ---- the rounds, group 1 one half-step behind group 0
+    // ---- the rounds
     int u = 0;
-    while (act0 || act1 || pend1) {
+    while (act) {
         ++u;
-        if (act0) {
-            pass(0, std::true_type{}, u % 3);
-            publish(0, u % 3, (u + 1) % 3);
-        }
-        if (pend1) {
-            if (!wait_post(1, (u - 1) % 3, u - 1, true)) return;
-            act1 = S.ictl[5] != 0;
-            pend1 = false;
-        }
-        if (act1) {
-            pass(1, std::true_type{}, u % 3);
-            publish(1, u % 3, (u + 1) % 3);
-            pend1 = true;
-        }
-        if (act0) {
-            if (!wait_post(0, u % 3, u, true)) return;
-            act0 = S.ictl[4] != 0;
-        }
+        pass(std::true_type{}, u % 3);
+        publish(u % 3, (u + 1) % 3);
+        if (!wait_post(u % 3, u, true)) return;
+        act = S.ictl[4] != 0;
     }
 
     // ---- the band back to Y, every column: the slack columns carry over to
@@ -818,7 +885,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     }
     __syncthreads();
 
-    // ---- blend and normalise every active pair (barriers on counter 0)
+    // ---- blend and normalise every active pair
     const float alpha = P.alpha, beta = 1.0f - P.alpha;
     if (P.normalize) {
         for (int si = 0; si < nseg; ++si) {
@@ -851,9 +918,9 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 if (lane == 0) atomicMax(&P.pairs[sg.pair].ctrl->xmax_bits, float_to_ordered(bm));
             }
         }
-        grid_arrive(&W->bar[0]);
-        if (!grid_wait(&W->bar[0], base0 + G * (gen[0] + 1u), err, P.timeout_ns)) return;
-        ++gen[0];
+        grid_arrive(&W->bar);
+        if (!grid_wait(&W->bar, base + G * (gen + 1u), err, P.timeout_ns)) return;
+        ++gen;
     }
     for (int si = 0; si < nseg; ++si) {
         const Seg sg = S.seg[si];
@@ -893,15 +960,12 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         dx = warp_max_d(dx);
         if (lane == 0 && dx > 0.0) atomicMax(&d.ctrl->dx_bits, (unsigned long long)__double_as_longlong(dx));
     }
-    grid_arrive(&W->bar[0]);
-    if (!grid_wait(&W->bar[0], base0 + G * (gen[0] + 1u), err, P.timeout_ns)) return;
-    ++gen[0];
+    grid_arrive(&W->bar);
+    if (!grid_wait(&W->bar, base + G * (gen + 1u), err, P.timeout_ns)) return;
+    ++gen;
 
     // ---- per-pair loop control, accumulator clean-up
-    for (int b = 0; b < 3; ++b) {
-        clear_acc(0, b, tid, nthr);
-        clear_acc(1, b, tid, nthr);
-    }
+    for (int b = 0; b < 4; ++b) clear_acc(b, tid, nthr);
     if (blockIdx.x == 0) {
         for (int p = tid; p < npairs; p += nthr) {
             if (!(S.pstate[p] & 1)) continue;
@@ -948,8 +1012,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             int all = 1;
             for (int p = 0; p < npairs; ++p) all &= (P.pairs[p].ctrl->done != 0);
             W->all_done = all;
-            W->bar_base[0] = base0 + G * gen[0];
-            W->bar_base[1] = base1 + G * gen[1];
+            W->bar_base = base + G * gen;
         }
     }
     };
@@ -969,12 +1032,12 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
 size_t pdb_smem_bytes(const PdbLayout& L, int nthr) {
     size_t off = 0;
     auto take = [&](size_t bytes) { off = (off + bytes + 15) & ~size_t(15); };
-    take(48 * (size_t)L.max_segs);    // Seg is twelve ints
-    take(56 * (size_t)L.npairs);      // PairS: three pointers, a double, two ints, a float, pad, a double
+    take(sizeof(Seg) * (size_t)L.max_segs);
+    take(sizeof(PairS) * (size_t)L.npairs);
     take(4 * (size_t)L.npairs);
     take(4 * (size_t)L.npairs);
     take(4 * 8);
-    take(4 * 2 * ((size_t)L.npairs + 1));
+    take(4 * ((size_t)L.npairs + 1));
     take(4 * (size_t)L.max_segs * 32);
     take(4 * (size_t)L.max_band_rows);
     take(4 * (size_t)L.max_band_rows * L.rp_stride);

@@ -118,8 +118,8 @@ def lib():
 
 
 def bandwidth_probe(level: int, sweeps: int = 200, device: int = 0) -> float:
-    """GB/s of shared memory (0), L2 (1) or HBM (2) under the projection
-    rounds' read + write pattern (fastpfp_bandwidth_probe)."""
+    """GB/s of shared memory (0), L2 (1), HBM (2) or tensor memory (3) under
+    the projection rounds' read + write pattern (fastpfp_bandwidth_probe)."""
     out = C.c_double(0.0)
     _check(lib().fastpfp_bandwidth_probe(int(device), int(level), int(sweeps), C.byref(out)),
            "fastpfp_bandwidth_probe")
@@ -330,7 +330,7 @@ class Solver:
 
     def last_trace(self, pair: int = 0, cap: int = 4096):
         """(inner counts, max|dX|) per outer iteration of pair `pair` of the
-        last call (0 after match; a pair of the last wave after a batch)."""
+        last call (0 after match; any pair's index after a batch)."""
         inner = np.zeros(cap, dtype=np.int32)
         delta = np.zeros(cap, dtype=np.float64)
         n = lib().fastpfp_last_trace(self._h, int(pair), C.c_void_p(inner.ctypes.data),

@@ -50,6 +50,26 @@ def test_params_per_mode():
     assert p.algorithm == F.ALG_PG and p.normalize_max == 0 and abs(p.alpha - 0.01) < 1e-9
 
 
+def test_params_override_and_switch_point():
+    """The parameters of the X-at-the-switch rerun: the same mode with no
+    refinement and I_0 cut to the low-precision iteration count."""
+    p = bench.params(F, 1.0, precision="bf16", refine_iters=0, max_outer=7)
+    assert p.precision == F.BF16 and p.refine_iters == 0 and p.max_outer == 7
+    assert p.switch_tol == 1e-3 and p.max_inner == 1000
+
+
+def test_oracle_timed_solves_are_whole_solves():
+    """The cpu_baseline's oracle timing: whole solves, at least one pair, in
+    order, stopping once the budget is spent."""
+    pairs = [synth.graph_pair(20, p=0.3, sigma=0.02, k=2, lam=0.5, seed=s) for s in range(3)]
+    done, spent = bench.oracle_timed_solves(pairs, 0.0)
+    assert done == 1 and spent > 0
+    done, spent = bench.oracle_timed_solves(pairs, 1e9)
+    assert done == 3
+    kw = bench.oracle_solve_kwargs(0.5, pg_alpha=0.1)
+    assert kw["algorithm"] == "pg" and kw["alpha"] == 0.1 and kw["normalize_max"] is False
+
+
 def test_pg_step_is_one_over_the_lipschitz_constant():
     g = synth.graph_pair(30, p=0.3, sigma=0.0, seed=1)
     L = np.linalg.norm(g.A.astype(np.float64), 2) * np.linalg.norm(g.A2.astype(np.float64), 2)

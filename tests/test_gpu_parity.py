@@ -218,18 +218,17 @@ def test_warm_start_x0_matches_oracle(solver):
 
 
 def _same_solve(a, b, Xa, Xb):
-    """Two runs of one solve (different entry points or loop control) agree
-    up to FP32 reduction order: the column sums are accumulated by atomics
-    in any order, so a stop test that lands on an epsilon boundary may move
-    by one iteration.  Same permutation and objective; the same X when the
-    iteration counts agree."""
+    """Two runs of one solve (different entry points or loop control) give
+    the same bits: the projection's cross-CTA sums are exact, so the order in
+    which the atomics land does not matter.  Same permutation, iteration
+    counts, objective and X."""
     np.testing.assert_array_equal(a.perm.cpu().numpy() if hasattr(a.perm, "cpu") else a.perm,
                                   b.perm.cpu().numpy() if hasattr(b.perm, "cpu") else b.perm)
-    assert abs(a.stats.objective - b.stats.objective) <= 1e-5 * abs(b.stats.objective)
-    assert abs(a.stats.outer_iters - b.stats.outer_iters) <= 1
-    assert abs(a.stats.lowp_iters - b.stats.lowp_iters) <= 1
-    if a.stats.outer_iters == b.stats.outer_iters and a.stats.lowp_iters == b.stats.lowp_iters:
-        assert np.abs(Xa - Xb).max() <= 1e-4
+    assert a.stats.objective == b.stats.objective
+    assert a.stats.outer_iters == b.stats.outer_iters
+    assert a.stats.inner_iters_total == b.stats.inner_iters_total
+    assert a.stats.lowp_iters == b.stats.lowp_iters
+    np.testing.assert_array_equal(np.asarray(Xa), np.asarray(Xb))
 
 
 def test_host_entry_point_equals_device_entry_point(solver):
@@ -353,8 +352,8 @@ def stream_solver_wide():
 def test_bf16_phase_then_fp32_refinement(solver):
     """Precision policy: BF16 tensor-core products until max|dX| < switch_tol,
     then FP32 iterations.  The refined result matches the plain FP32 solve's
-    permutation and objective; the refinement's X matches the oracle replaying
-    the FP32 iterations from the X the BF16 phase reached."""
+    permutation and objective, and its X the plain solve's to 1e-3 (the
+    oracle replay of the refinement is in test_gpu_solve_parity.py)."""
     g = synth.attributed_1000(seed=1)
     A, A2, B, B2 = cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)
     p32 = F.default_params(lam=1.0)
@@ -471,16 +470,18 @@ def test_streamed_mixed_batch_of_120(stream_solver):
 
 
 def test_bandwidth_probe_orders_the_memory_levels():
-    """The probe behind the roofline denominators: shared memory (all SMs)
-    is faster than L2, which is faster than HBM; all are plausible for one
-    GB300 (HBM within the measured copy figure's ballpark)."""
+    """The probe behind the roofline denominators: tensor memory (all SMs)
+    is faster than shared memory, which is faster than L2, which is faster
+    than HBM; all are plausible for one GB300 (HBM within the measured copy
+    figure's ballpark)."""
+    tmem = F.bandwidth_probe(3, sweeps=2000)
     smem = F.bandwidth_probe(0, sweeps=2000)
     l2 = F.bandwidth_probe(1, sweeps=200)
     hbm = F.bandwidth_probe(2, sweeps=5)
-    assert smem > l2 > hbm > 1000.0
+    assert tmem > smem > l2 > hbm > 1000.0
     assert hbm < 10000.0
     with pytest.raises(F.FastPFPError):
-        F.bandwidth_probe(3)
+        F.bandwidth_probe(4)
 
 
 # ------------------------------------------------------------ errors / faults

@@ -142,7 +142,7 @@ def test_reference_arm_under_torchrun_prints_one_line():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
            os.path.join(root, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1",
-           "--warmup", "0", "--ref-budget", "1"]
+           "--warmup", "0"]
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=root)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [json.loads(l) for l in out.stdout.splitlines() if l.startswith("{")]
@@ -150,4 +150,6 @@ def test_reference_arm_under_torchrun_prints_one_line():
     line = lines[0]
     assert line["impl"] == "reference" and line["n_gpus"] == 2
     assert line["cpu_baseline"]["kind"] == "oracle" and line["value"] > 0
+    assert "nothing extrapolated" in line["cpu_baseline"]["sample"]
+    assert line["ms_per_step"] == pytest.approx(1e3 / line["value"])
     assert line["e2e"]["h2d_bytes_per_step"] == 0

@@ -1,8 +1,10 @@
 """fastpfp_project_noalloc -- the projection entry point for callers that
-may not allocate device memory (a fixed arena owned by the host application,
-a region under CUDA graph capture, a real-time no-allocation rule).  It must
-give what the handle-based fastpfp_project gives on the same input, call
-after call, although every call reuses the same static scratch array.
+may not allocate device memory (a plugin handed a fixed device-memory arena
+by its host application, a real-time loop that forbids allocation after
+start-up).  It must give what the handle-based fastpfp_project gives on the
+same input, call after call, although every call reuses the same static
+scratch array, and both must match the FP64 oracle's successive projection
+(Section 4.3) run for the same number of rounds.
 
 This file is collected last so that a failure here comes after every other
 test has run; it also passes when run alone in a fresh process."""
@@ -15,6 +17,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
+import oracle
 from paper_1207_1114_gb300 import fastpfp as F
 
 pytestmark = pytest.mark.gpu
@@ -31,8 +34,11 @@ def _noalloc_raw(Y, tol, max_iter):
     return rc, it.value, d.value
 
 
-@pytest.mark.parametrize("N,tol,rounds", [(1000, 0.0, 60), (256, 1e-5, 3000), (4, 0.0, 10)])
-def test_noalloc_matches_handle_projection_twice(N, tol, rounds):
+# N = 3200: the band no longer fits in shared memory and the kernel streams
+# it through L2 (the N range (2900, 4096] of this entry point)
+@pytest.mark.parametrize("N,tol,rounds", [(1000, 0.0, 60), (256, 1e-5, 3000), (4, 0.0, 10),
+                                          (3200, 0.0, 6)])
+def test_noalloc_matches_handle_projection_and_oracle_twice(N, tol, rounds):
     rng = np.random.default_rng(N)
     with F.Solver(max_n=N) as s:
         for call in range(2):   # the second call starts from the first call's leftovers
@@ -45,6 +51,8 @@ def test_noalloc_matches_handle_projection_twice(N, tol, rounds):
             assert it == it_ref
             assert abs(d - d_ref) <= 2e-5
             assert (got - ref).abs().max().item() <= 2e-5
+            want, _, _ = oracle.pd(Y0, fixed_iters=it)
+            assert np.abs(got.cpu().numpy() - want).max() <= 2e-5
 
 
 def test_noalloc_rejects_sizes_beyond_its_limit():
