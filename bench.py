@@ -208,17 +208,50 @@ def whole_job_rate(units_per_rank: int, seconds: float, device) -> float:
     return units_per_rank * world / max_over_ranks(seconds, device)
 
 
-def make_pairs(workload: str, rank: int, batch: int):
+def global_shapes(workload: str, count: int):
+    """(n_a, n_b) of every pair of the whole job's batch (all ranks), drawn
+    without generating the graphs."""
     from paper_1207_1114_gb300 import synth
     if workload == "attributed_1000":
-        return [synth.attributed_1000(seed=rank * 1000 + b) for b in range(batch)]
+        return [(1000, 1000)] * count
     if workload == "partial_1000_1200":
-        return [synth.partial_1000_1200(seed=rank * 1000 + b) for b in range(batch)]
+        return [(1000, 1200)] * count
     if workload == "batch_mixed_512":
-        return synth.batch_mixed(count=batch, seed=rank + 1)
+        return [(n, n + o) for n, o in synth.batch_mixed_sizes(count, seed=1)]
     if workload == "large_4000":
-        return [synth.large_4000(seed=rank * 1000 + b) for b in range(batch)]
+        return [(4000, 4000)] * count
     raise ValueError(workload)
+
+
+def make_pair(workload: str, i: int, count: int):
+    """Pair i of the whole job's batch of `count` pairs (seeded by i)."""
+    from paper_1207_1114_gb300 import synth
+    if workload == "attributed_1000":
+        return synth.attributed_1000(seed=i)
+    if workload == "partial_1000_1200":
+        return synth.partial_1000_1200(seed=i)
+    if workload == "batch_mixed_512":
+        n, o = synth.batch_mixed_sizes(count, seed=1)[i]
+        return synth.batch_mixed_pair(i, n, o, seed=1)
+    if workload == "large_4000":
+        return synth.large_4000(seed=i)
+    raise ValueError(workload)
+
+
+def rank_share(workload: str, rank: int, world: int, batch: int):
+    """This rank's pairs: the whole job carries world x batch pairs (weak
+    scaling: each rank's work stays fixed as ranks are added), split by the
+    cost-balanced partition of paper_1207_1114_gb300/shard.py, computed the
+    same on every rank with no communication.  Returns (indices, pairs)."""
+    from paper_1207_1114_gb300 import shard
+    shapes = global_shapes(workload, world * batch)
+    shares = shard.partition([shard.pair_cost(a, b) for a, b in shapes], world)
+    mine = shares[rank]
+    return mine, [make_pair(workload, i, world * batch) for i in mine]
+
+
+def make_pairs(workload: str, rank: int, batch: int, world: int = 1):
+    return rank_share(workload, rank, world, batch)[1]
 
 
 def params(F, lam, profile=0, precision="fp32", loop_mode=0, pg_alpha=None, **override):
@@ -530,7 +563,9 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    pairs = make_pairs(args.workload, rank, args.batch)
+    per_rank = args.batch
+    pairs = make_pairs(args.workload, rank, per_rank, world)
+    args.batch = len(pairs)   # this rank's share of the cost-balanced split
     shapes = [canon_shape(g) for g in pairs]
     max_n = max(max(g.A.shape[0], g.A2.shape[0]) for g in pairs)
     lam = pairs[0].lam
@@ -750,7 +785,8 @@ def main():
                            precision=args.precision, loop=args.loop, init=args.init,
                            gemm_tiles=dict(tiles, source="default" if args.no_autotune else "autotuned"),
                            l2="flushed (512 MB write) before every timed step",
-                           parallelism=f"pairs sharded over {world} rank(s)"),
+                           parallelism=f"{world} rank(s), the job's {world} x {per_rank} pairs split by the "
+                                       f"cost-balanced partition (shard.partition)"),
             "accuracy": float(np.mean(accs)),
             "iterations": {"outer_per_pair": sum(s.outer_iters for s in flat_t) / len(flat_t),
                            "inner_per_pair": sum(s.inner_iters_total for s in flat_t) / len(flat_t)},

@@ -123,6 +123,8 @@ typedef struct {
     float ms_gemm;          /* profile = 1: summed time of the gradient products             */
     float ms_proj;          /* profile = 1: summed time of the projection launches           */
     float ms_disc;          /* profile = 1: time of the discretisation                       */
+    int host_syncs;         /* host synchronisations the call made (stream or event waits) while
+                               its work was in flight; the same for every pair of a batch     */
 } fastpfp_stats;
 
 /* One graph pair of a batch; all pointers are device pointers. */
@@ -144,9 +146,10 @@ void fastpfp_default_params(fastpfp_params* p);
 
 /* Creates a solver on CUDA device `device` for graphs of up to max_n nodes.
  * All device scratch (the slacked N x N matrix Y of Section 4.3, X, K, the
- * products, the reduction buffers) is allocated here, sized for max_n;
- * max_batch bounds the pairs of one fastpfp_match_batched call.  Nothing is
- * allocated by the solve calls.  Errors: ERR_ARG (max_n < 1, max_batch < 1,
+ * products, the reduction buffers) is allocated here, sized for max_n, one
+ * slot of it for each of the max_batch pairs one fastpfp_match_batched call
+ * may carry (about 30 max_n^2 bytes per slot).  Nothing is allocated by the
+ * solve calls.  Errors: ERR_ARG (max_n < 1, max_batch < 1,
  * out == NULL), ERR_CUDA (bad device, out of memory). */
 int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch);
 
@@ -185,11 +188,16 @@ int fastpfp_match_host(fastpfp_t h, void* stream,
 /* Solves `count` independent pairs with the same parameters (Algorithm 1
  * per pair).  pairs[] is a host array of device-pointer descriptors; st is
  * a nullable host array of `count` statistics.  Pairs are solved in waves:
- * consecutive pairs whose slacked matrices fit in shared memory together
- * (N <= 4096 each, at most 64 and at most max_batch per wave) share one
- * projection launch per outer iteration; with profile = 1 a wave's phase
- * times are split equally between its pairs.  Synchronises `stream`.
- * Errors as fastpfp_match, plus ERR_ARG when count > max_batch. */
+ * pairs whose slacked matrices fit on chip together (tensor memory plus
+ * shared memory of all SMs; N <= 4096 each, at most 128 per wave) share one
+ * projection launch per outer iteration.  A batch larger than one wave is
+ * streamed: pairs that stopped leave the wave, waiting pairs join it in
+ * batch order.  With loop_mode 0 (and profile 0) the waves are planned on
+ * the device and the whole batch runs as one CUDA graph launch with one
+ * host synchronisation; otherwise the host plans them between outer
+ * iterations (the same plans, so the same results).  With profile = 1 a
+ * wave's phase times are split equally between its pairs.  Synchronises
+ * `stream`.  Errors as fastpfp_match, plus ERR_ARG when count > max_batch. */
 int fastpfp_match_batched(fastpfp_t h, void* stream, int count, const fastpfp_pair* pairs,
                           const fastpfp_params* p, fastpfp_stats* st);
 

@@ -238,6 +238,10 @@ def solve(A, A2, B=None, B2=None, lam=0.0, alpha=0.5, tol_outer=1e-6, tol_inner=
     rip = None
     if replay_inner is not None:
         replay_inner = np.ascontiguousarray(replay_inner, dtype=np.int32)
+        need = int(replay_outer) if int(replay_outer) > 0 else int(max_outer)
+        if len(replay_inner) < need or (replay_inner[:need] < 1).any():
+            raise ValueError("replay_inner needs a positive inner count for every outer iteration "
+                             "the replay runs")
         rip = replay_inner.ctypes.data_as(_I)
     perm = np.empty(n_a, dtype=np.int32)
     X = np.empty((n_a, n_b))

@@ -1,0 +1,215 @@
+// band_plan.cuh -- the band planner of the wave kernel (pdb_kernel).
+//
+// A wave's pairs have their slacked rows concatenated and cut into one
+// band per CTA, each kept on chip (tensor memory + shared memory) for every
+// P1/P2 round of an outer iteration.  The same code plans a wave on the host
+// (between launches) and on the device (the planner kernel of a batch
+// streamed inside one CUDA graph), so a wave is cut identically on either
+// side and the two give bit-identical results.
+#pragma once
+
+#include "internal.h"
+
+namespace fpfp {
+
+// Band cost model of pdb_kernel, in entry equivalents: a band costs its
+// entries plus kSegCost for every pair it spans (a segment brings its own
+// loop tails, reductions and read-back; measured on GB300 by clock stamps
+// at 2500-2750 cycles against 0.07-0.09 cycles per entry of a pass).
+constexpr long long kSegCost = 32768;
+constexpr long long kMinElemsPerCta = 8192;   // smallest band worth a CTA of its own
+// Waves with at least this many rows per CTA lay out tied pairs with two
+// column quads per thread (pdb_shape): measured +7 % at 112 rows per CTA
+// (17 pairs of n = 1000), -25 % at 7 (one pair of n = 1000).
+constexpr int kTwoQuadRowsPerCta = 32;
+// Pairs join a streamed wave only while its bands can still be cut with at
+// least this segment-cost level (0 = kSegCost, 1 = half of it, ...): a wave
+// filled until only pure entry balance fits leaves the CTAs that span
+// several pairs slower than the rest, and every grid barrier waits for them.
+// Measured: level 0 gives the 512-pair mixed batch 451 pair-solves/s against
+// 405 with no limit, and streamed n = 1000 batches 153 against 148.  A batch
+// that fits in one wave as a whole takes any plan instead: splitting it
+// would leave a tail wave of a few pairs (17 pairs of n = 1000: 117 against
+// 146 pair-solves/s).
+constexpr int kAdmitLevel = 0;
+constexpr int kMaxBands = 256;   // CTAs of one wave (one per SM)
+constexpr int kSegBytes = 44;    // a segment record of pdb_kernel's shared-memory tables
+constexpr int kPairBytes = 80;   // a pair record of the same
+
+__host__ __device__ inline int bp_round4(int x) { return (x + 3) & ~3; }
+
+// Shared memory pdb_kernel carves for a wave with layout L (its tables, then
+// the band storage), 16-byte aligned pieces.
+__host__ __device__ inline size_t pdb_smem_bytes(const PdbLayout& L, int nthr) {
+    (void)nthr;
+    size_t off = 0;
+    auto take = [&off](size_t bytes) { off = (off + bytes + 15) & ~size_t(15); };
+    take((size_t)kSegBytes * L.max_segs);
+    take((size_t)kPairBytes * L.npairs);
+    take(4 * (size_t)L.npairs);
+    take(4 * (size_t)L.npairs);
+    take(4 * 8);
+    take(4 * ((size_t)L.npairs + 1));
+    take(4 * (size_t)L.max_segs * 32);
+    take(4 * (size_t)L.max_band_rows);
+    take(4 * (size_t)L.max_band_rows * L.rp_stride);
+    take(4 * (size_t)L.max_band_cols);
+    take(4 * (size_t)L.max_band_elems);
+    return off;
+}
+
+// Greedy cut of the concatenated rows of pairs with row counts Ns[0..count)
+// into consecutive bands of cost at most C: each band takes as many rows as
+// fit.  Writes the boundaries to band[0..] (when band != nullptr) and returns
+// the number of bands, or max_bands + 1 as soon as more would be needed.  For
+// a cost that only grows as rows are added, the greedy uses the fewest bands,
+// and the count never grows with C.
+__host__ __device__ inline int cut_rows(const int* Ns, int count, long long C, long long seg_cost, int max_bands,
+                                        int* band) {
+    int b = 0, gr = 0, rows_in = 0, last = -1;
+    long long cur = 0;
+    if (band) band[0] = 0;
+    for (int i = 0; i < count; ++i) {
+        const int N = Ns[i];
+        const long long ldy = bp_round4(N);
+        int r = 0;
+        while (r < N) {
+            const long long seg = last != i ? seg_cost : 0;
+            const long long avail = C - cur - seg;
+            long long k = avail >= ldy ? ((long long)(N - r) < avail / ldy ? (long long)(N - r) : avail / ldy) : 0;
+            if (k == 0) {
+                if (rows_in > 0) {
+                    if (++b >= max_bands) return max_bands + 1;
+                    if (band) band[b] = gr;
+                    cur = 0;
+                    rows_in = 0;
+                    last = -1;
+                    continue;
+                }
+                k = 1;   // C below one row's cost: the row goes alone
+            }
+            cur += seg + k * ldy;
+            rows_in += (int)k;
+            r += (int)k;
+            gr += (int)k;
+            last = i;
+        }
+    }
+    return rows_in > 0 || b == 0 ? b + 1 : b;
+}
+
+// The search interval of the smallest band cost bound: every row fits in a
+// band ([lo]), one band holds everything ([hi]).
+__host__ __device__ inline void cut_interval(const int* Ns, int count, long long seg_cost, long long* lo,
+                                             long long* hi) {
+    *lo = 1;
+    *hi = 0;
+    for (int i = 0; i < count; ++i) {
+        const long long ldy = bp_round4(Ns[i]);
+        if (seg_cost + ldy > *lo) *lo = seg_cost + ldy;
+        *hi += (long long)Ns[i] * ldy + seg_cost;
+    }
+}
+
+// A planned wave: `grid` CTAs (bands), their row boundaries (band[grid] =
+// the wave's rows; a launch on more CTAs gives the extra ones empty bands)
+// and the shared-memory layout.
+struct WavePlan {
+    int grid;
+    int band[kMaxBands + 1];
+    PdbLayout layout;
+    unsigned smem;
+};
+
+// Wave-level choices before the cut: the largest CTA count worth using and
+// the thread-layout tie rule.
+__host__ __device__ inline void wave_shape(const int* Ns, int count, int num_sms, int* Gmax, int* t2) {
+    long long E = 0, rows = 0;
+    for (int i = 0; i < count; ++i) {
+        E += (long long)Ns[i] * bp_round4(Ns[i]);
+        rows += Ns[i];
+    }
+    long long g = (E + kMinElemsPerCta - 1) / kMinElemsPerCta;
+    if (g < 1) g = 1;
+    if (g > num_sms) g = num_sms;
+    if (g > kMaxBands) g = kMaxBands;
+    *Gmax = (int)g;
+    *t2 = rows >= (long long)kTwoQuadRowsPerCta * g ? 1 : 0;
+}
+
+__host__ __device__ inline long long seg_cost_of_level(int lv) {
+    return lv == 0 ? kSegCost : lv == 1 ? kSegCost / 2 : lv == 2 ? kSegCost / 4 : 0ll;
+}
+
+// Per-band statistics of the cut at bound C into w->band / w->grid, and the
+// wave's layout: the first rows of every row group of a segment go to tensor
+// memory (pdb_tmem_rows, a band's segments in pair order as the kernel places
+// them), the rest to shared memory.  False when a CTA's band would not fit
+// (more than kMaxSeg segments, or more shared memory than a CTA has).
+__host__ __device__ inline bool finish_plan(const int* Ns, int count, long long C, long long seg_cost, int Gmax,
+                                            int t2, WavePlan* w) {
+    int rows = 0;
+    for (int i = 0; i < count; ++i) rows += Ns[i];
+    const int used = cut_rows(Ns, count, C, seg_cost, Gmax, w->band);
+    for (int c = used; c <= Gmax; ++c) w->band[c] = rows;
+    const int G = used > 1 ? used : 1;
+    PdbLayout L{0, 0, 0, 1, t2, 1, count};
+    for (int i = 0; i < count; ++i) {
+        const int rw = pdb_row_warps(bp_round4(Ns[i]), kPdbThreads, t2);
+        if (rw > L.rp_stride) L.rp_stride = rw;
+    }
+    int p = 0, p0 = 0;   // the pair holding row band[b], and its first row
+    for (int b = 0; b < G; ++b) {
+        const int lo = w->band[b], hi = w->band[b + 1];
+        while (p < count && p0 + Ns[p] <= lo) p0 += Ns[p++];
+        int brows = 0, bcols = 0, belems = 0, segs = 0, tcol = 0;
+        for (int q = p, q0 = p0; q < count && q0 < hi; q0 += Ns[q++]) {
+            const int s0 = lo > q0 ? lo : q0, s1 = hi < q0 + Ns[q] ? hi : q0 + Ns[q];
+            if (s0 >= s1) continue;
+            const int nr = s1 - s0, ldy = bp_round4(Ns[q]);
+            int ntm = 0, next = 0;
+            pdb_tmem_rows(nr, ldy, kPdbThreads, tcol, &ntm, &next, t2);
+            tcol = next;
+            brows += nr;
+            bcols += ldy;
+            belems += (nr - ntm) * ldy;
+            ++segs;
+        }
+        if (segs > kMaxSeg) return false;
+        if (brows > L.max_band_rows) L.max_band_rows = brows;
+        if (bcols > L.max_band_cols) L.max_band_cols = bcols;
+        if (belems > L.max_band_elems) L.max_band_elems = belems;
+        if (segs > L.max_segs) L.max_segs = segs;
+    }
+    const size_t smem = pdb_smem_bytes(L, kPdbThreads);
+    if (smem > (size_t)kPdMaxSmem) return false;
+    w->grid = G;
+    w->layout = L;
+    w->smem = (unsigned)smem;
+    return true;
+}
+
+// Plans a wave of pairs with row counts Ns[0..count) on at most num_sms
+// CTAs: for the measured segment cost first, then cheaper ones (levels up to
+// max_level) when that plan does not fit on chip (pair-aligned bands hold
+// more entries), finally pure entry balance; at each level the smallest
+// bound whose greedy cut needs at most Gmax bands (binary search).  False
+// when no level fits.  Sequential: the host's planner.
+inline bool plan_bands_seq(const int* Ns, int count, int num_sms, int max_level, WavePlan* w) {
+    int Gmax = 1, t2 = 0;
+    wave_shape(Ns, count, num_sms, &Gmax, &t2);
+    for (int lv = 0; lv <= max_level && lv < 4; ++lv) {
+        const long long seg_cost = seg_cost_of_level(lv);
+        long long lo, hi;
+        cut_interval(Ns, count, seg_cost, &lo, &hi);
+        while (lo < hi) {
+            const long long mid = lo + (hi - lo) / 2;
+            if (cut_rows(Ns, count, mid, seg_cost, Gmax, nullptr) <= Gmax) hi = mid;
+            else lo = mid + 1;
+        }
+        if (finish_plan(Ns, count, lo, seg_cost, Gmax, t2, w)) return true;
+    }
+    return false;
+}
+
+}  // namespace fpfp

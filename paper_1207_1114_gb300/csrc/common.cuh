@@ -33,6 +33,9 @@ struct Ctrl {
     unsigned bar_base;     // counter value at the start of the next cooperative launch
     int matched;           // discretisation: columns matched so far
     unsigned obj_ticket;   // objective: blocks that have stored their partial sum
+    int idle;              // 1 while a streamed batch keeps this pair out of the running wave:
+                           // its product and projection launches skip it
+    int wave_pairs;        // largest wave the pair ran in (device-planned waves)
     int inner_trace[kMaxOuterTrace];
     double delta_trace[kMaxOuterTrace];
     double obj_part[kObjBlocks];   // objective: one partial sum per block, folded in block order

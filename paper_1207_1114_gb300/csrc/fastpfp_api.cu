@@ -31,6 +31,7 @@
 #include <new>
 #include <vector>
 
+#include "band_plan.cuh"
 #include "common.cuh"
 #include "internal.h"
 
@@ -45,11 +46,6 @@ constexpr int kProfIters = 128;                   // outer iterations timed when
 constexpr int kProfEvents = 2 * kProfIters + 3;   // iteration boundaries + discretisation
 constexpr int kChunk = 4;                         // outer iterations enqueued between checks
 constexpr size_t kTraceBytes = (size_t)kMaxOuterTrace * (sizeof(int) + sizeof(double));
-constexpr long long kMinElemsPerCta = 8192;       // smallest band worth a CTA of its own
-// Waves with at least this many rows per CTA lay out tied pairs with two
-// column quads per thread (pdb_shape): measured +7 % at 112 rows per CTA
-// (17 pairs of n = 1000), -25 % at 7 (one pair of n = 1000).
-constexpr int kTwoQuadRowsPerCta = 32;
 
 inline int round4(int x) { return (x + 3) & ~3; }
 inline int round8(int x) { return (x + 7) & ~7; }   // BF16 rows: 16-byte TMA strides
@@ -96,6 +92,13 @@ struct fastpfp_s {
     char* trace_store = nullptr; // device, max_batch x kTraceBytes: per-pair inner counts and deltas
     int* d_flags = nullptr;      // device, kMaxWavePairs + 1 stop/error words of a streamed wave
     int* h_flags = nullptr;      // pinned copy of d_flags
+    // a batch streamed inside one graph: per-pair wave-table templates and
+    // the device planner's state (device), with pinned staging
+    PairDesc* d_tmpl = nullptr;
+    PairDesc* h_tmpl = nullptr;
+    StreamState* d_stream = nullptr;
+    StreamState* h_stream = nullptr;
+    int host_syncs = 0;          // host synchronisations of the current call
 
     cudaEvent_t ev[kProfEvents] = {};
     cudaEvent_t chunk_ev[2] = {};
@@ -477,6 +480,7 @@ int run_outer(fastpfp_t h, cudaStream_t s, const fastpfp_params* p, const int* d
         FP_CUDA(cudaEventRecord(h->chunk_ev[slot], s));
         if (chunk >= 1) {
             FP_CUDA(cudaEventSynchronize(h->chunk_ev[slot ^ 1]));
+            h->host_syncs += 1;
             const int* w = &h->h_done[4 * (slot ^ 1)];
             if (w[done_idx] || w[err_idx]) break;
         }
@@ -564,9 +568,11 @@ void read_profile(fastpfp_t h, int outer, float share, fastpfp_stats* st) {
     st->ms_disc = d * share;
 }
 
-int fill_stats(const Ctrl& c, int transposed, int launches, int wave_pairs, fastpfp_stats* st) {
+int fill_stats(const Ctrl& c, int transposed, int launches, int wave_pairs, fastpfp_stats* st,
+               int host_syncs = 0) {
     const int status = c.error != 0 ? c.error : FASTPFP_OK;
     if (st) {
+        st->host_syncs = host_syncs;
         st->launches = launches;
         st->wave_pairs = wave_pairs;
         st->ms_gemm = st->ms_proj = st->ms_disc = 0.f;
@@ -592,161 +598,21 @@ struct Wave {
     std::vector<int> band;   // grid + 1 row boundaries
 };
 
-struct BandStats {
-    int rows = 0, cols = 0, elems = 0, segs = 0;
-};
-
-// Band cost model of pdb_kernel, in entry equivalents: a band costs its
-// entries plus kSegCost for every pair it spans (a segment brings its own
-// loop tails, reductions and read-back; measured on GB300 by clock stamps
-// at 2500-2750 cycles against 0.07-0.09 cycles per entry of a pass).
-constexpr long long kSegCost = 32768;
-
-// Pairs join a wave only while its bands can still be cut with at least
-// this segment-cost level (0 = kSegCost, 1 = half of it, ...): a wave filled
-// until only pure entry balance fits leaves the CTAs that span several pairs
-// slower than the rest, and every grid barrier waits for them.  Measured:
-// level 0 gives the 512-pair mixed batch 451 pair-solves/s against 405 with
-// no limit, and streamed n = 1000 batches 153 against 148.  A batch that
-// fits in one wave as a whole (plan_wave) takes any plan instead: splitting
-// it would leave a tail wave of a few pairs (17 pairs of n = 1000: 117
-// against 146 pair-solves/s).
-constexpr int kAdmitLevel = 0;
-
-// Greedy cut of the concatenated rows of pairs [first, first + count) into
-// consecutive bands of cost at most C: each band takes as many rows as fit.
-// Writes the boundaries to band[0..] (when band != nullptr) and returns the
-// number of bands, or max_bands + 1 as soon as more would be needed.  For a
-// cost that only grows as rows are added, the greedy uses the fewest bands.
-int cut_rows(const std::vector<Problem>& qs, int first, int count, long long C, long long seg_cost,
-             int max_bands, int* band) {
-    int b = 0, gr = 0, rows_in = 0, last = -1;
-    long long cur = 0;
-    if (band) band[0] = 0;
-    for (int i = 0; i < count; ++i) {
-        const int N = qs[first + i].N;
-        const long long ldy = round4(N);
-        int r = 0;
-        while (r < N) {
-            const long long seg = last != i ? seg_cost : 0;
-            const long long avail = C - cur - seg;
-            long long k = avail >= ldy ? std::min<long long>(N - r, avail / ldy) : 0;
-            if (k == 0) {
-                if (rows_in > 0) {
-                    if (++b >= max_bands) return max_bands + 1;
-                    if (band) band[b] = gr;
-                    cur = 0;
-                    rows_in = 0;
-                    last = -1;
-                    continue;
-                }
-                k = 1;   // C below one row's cost: the row goes alone
-            }
-            cur += seg + k * ldy;
-            rows_in += (int)k;
-            r += (int)k;
-            gr += (int)k;
-            last = i;
-        }
-    }
-    return rows_in > 0 || b == 0 ? b + 1 : b;
-}
-
-// Cuts pairs [first, first + count) into at most G bands minimising the
-// largest band cost (binary search on the cost bound over cut_rows).
-// band[0..used] holds the row boundaries, band[used..G] = total rows.
-// Returns the number of bands used and, per band, its rows, columns, floats
-// left in shared memory and segments in st.
-int split_rows(const std::vector<Problem>& qs, int first, int count, int G, long long seg_cost,
-               int two_quad_ties, int* band, std::vector<BandStats>& st) {
-    long long lo = 1, hi = 0;
-    int rows = 0;
-    for (int i = 0; i < count; ++i) {
-        const long long ldy = round4(qs[first + i].N);
-        lo = std::max(lo, seg_cost + ldy);
-        hi += (long long)qs[first + i].N * ldy + seg_cost;
-        rows += qs[first + i].N;
-    }
-    for (int c = 0; c <= G; ++c) band[c] = rows;
-    st.assign(G, BandStats{});
-    if (count == 0) return 0;
-    while (lo < hi) {
-        const long long mid = lo + (hi - lo) / 2;
-        if (cut_rows(qs, first, count, mid, seg_cost, G, nullptr) <= G) hi = mid;
-        else lo = mid + 1;
-    }
-    const int used = cut_rows(qs, first, count, lo, seg_cost, G, band);
-    for (int c = used; c <= G; ++c) band[c] = rows;
-    // per-band statistics; the first rows of every row group go to TMEM
-    // (pdb_tmem_rows, segments in pair order as the kernel places them), so
-    // elems counts the floats left in shared memory
-    std::vector<int> tcol(G, 0);
-    int b = 0, gr = 0;
-    for (int i = 0; i < count; ++i) {
-        const int N = qs[first + i].N, ldy = round4(N);
-        while (b + 1 < used && band[b + 1] <= gr) ++b;
-        for (int bb = b; bb < used && band[bb] < gr + N; ++bb) {
-            const int lo = std::max(band[bb], gr), hi = std::min(band[bb + 1], gr + N);
-            if (lo >= hi) continue;
-            const int nr = hi - lo;
-            int ntm = 0, next = 0;
-            pdb_tmem_rows(nr, ldy, kPdbThreads, tcol[bb], &ntm, &next, two_quad_ties);
-            tcol[bb] = next;
-            st[bb].rows += nr;
-            st[bb].cols += ldy;
-            ++st[bb].segs;
-            st[bb].elems += (nr - ntm) * ldy;
-        }
-        gr += N;
-    }
-    return used;
-}
-
-// Plans one wave of pairs [first, first + count): their rows cut into at
-// most num_sms cost-balanced bands, one per CTA.  Bands first try to respect
-// the per-segment cost (pair-aligned where possible), then fall back to pure
-// entry balance if that does not fit in shared memory.  Returns false when a
-// CTA's band would not fit.
+// A wave planned by the shared band planner (band_plan.cuh) for pairs
+// [first, first + count) of qs.
 bool plan_bands(const std::vector<Problem>& qs, int first, int count, int num_sms, Wave* w,
                 int max_level = 3) {
-    long long E = 0;
-    for (int i = 0; i < count; ++i) E += (long long)qs[first + i].N * round4(qs[first + i].N);
-    const long long gl = (E + kMinElemsPerCta - 1) / kMinElemsPerCta;
-    const int Gmax = (int)std::min<long long>(num_sms, std::max<long long>(1, gl));
-    long long rows = 0;
-    for (int i = 0; i < count; ++i) rows += qs[first + i].N;
-    const int t2 = rows >= (long long)kTwoQuadRowsPerCta * Gmax ? 1 : 0;
-    // the measured segment cost first, then cheaper ones when that plan does
-    // not fit on chip (pair-aligned bands hold more entries), finally pure
-    // entry balance
-    const long long levels[4] = {kSegCost, kSegCost / 2, kSegCost / 4, 0ll};
-    for (int lv = 0; lv <= max_level && lv < 4; ++lv) {
-        const long long seg_cost = levels[lv];
-        std::vector<int> b0(Gmax + 1);
-        std::vector<BandStats> s0;
-        const int G = std::max(1, split_rows(qs, first, count, Gmax, seg_cost, t2, b0.data(), s0));
-        PdbLayout L{0, 0, 0, 1, t2, 1, count};
-        for (int i = 0; i < count; ++i)
-            L.rp_stride = std::max(L.rp_stride, pdb_row_warps(round4(qs[first + i].N), kPdbThreads, t2));
-        bool ok = true;
-        for (int b = 0; b < G; ++b) {
-            L.max_band_rows = std::max(L.max_band_rows, s0[b].rows);
-            L.max_band_cols = std::max(L.max_band_cols, s0[b].cols);
-            L.max_band_elems = std::max(L.max_band_elems, s0[b].elems);
-            L.max_segs = std::max(L.max_segs, s0[b].segs);
-            if (s0[b].segs > kMaxSeg) ok = false;
-        }
-        const size_t smem = pdb_smem_bytes(L, kPdbThreads);
-        if (!ok || smem > (size_t)kPdMaxSmem) continue;
-        w->band.assign(b0.begin(), b0.begin() + G + 1);
-        w->first = first;
-        w->count = count;
-        w->grid = G;
-        w->layout = L;
-        w->smem = smem;
-        return true;
-    }
-    return false;
+    std::vector<int> Ns(count);
+    for (int i = 0; i < count; ++i) Ns[i] = qs[first + i].N;
+    WavePlan wp;
+    if (!plan_bands_seq(Ns.data(), count, num_sms, max_level, &wp)) return false;
+    w->band.assign(wp.band, wp.band + wp.grid + 1);
+    w->first = first;
+    w->count = count;
+    w->grid = wp.grid;
+    w->layout = wp.layout;
+    w->smem = wp.smem;
+    return true;
 }
 
 // Largest wave starting at `first` (at least one pair when it fits at all).
@@ -773,25 +639,30 @@ struct Member {
 // Wave tables of members mem (pair table in member order, band table of w)
 // staged through pinned memory, the wave control word cleared.  The pinned
 // staging is reused by the next wave, so callers synchronise in between.
+// The wave-table entry of problem q in slot sl (row0 left 0).
+PairDesc pair_desc(const Slot& sl, const Problem& q, bool lowp) {
+    PairDesc d{};
+    d.Y = sl.Y;
+    d.X = sl.X;
+    d.Xt16 = lowp ? sl.Xt16 : nullptr;
+    d.colbuf = sl.colbuf;
+    d.sbuf = sl.sbuf;
+    d.dbuf = sl.dbuf;
+    d.ctrl = sl.ctrl;
+    d.N = q.N;
+    d.ldy = round4(q.N);
+    d.m = q.m;
+    d.ldx = round4(q.m);
+    d.ldxt = round8(q.N);
+    return d;
+}
+
 int write_wave_tables(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs,
                       const std::vector<Member>& mem, const Wave& w, bool lowp) {
     int row0 = 0;
     for (int i = 0; i < (int)mem.size(); ++i) {
         const Problem& q = qs[mem[i].pair];
-        const Slot& sl = h->slots[mem[i].slot];
-        PairDesc d{};
-        d.Y = sl.Y;
-        d.X = sl.X;
-        d.Xt16 = lowp ? sl.Xt16 : nullptr;
-        d.colbuf = sl.colbuf;
-        d.sbuf = sl.sbuf;
-        d.dbuf = sl.dbuf;
-        d.ctrl = sl.ctrl;
-        d.N = q.N;
-        d.ldy = round4(q.N);
-        d.m = q.m;
-        d.ldx = round4(q.m);
-        d.ldxt = round8(q.N);
+        PairDesc d = pair_desc(h->slots[mem[i].slot], q, lowp);
         d.row0 = row0;
         row0 += q.N;
         h->h_pairs[i] = d;
@@ -963,7 +834,7 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     h->max_n = max_n;
     h->max_batch = max_batch;
     h->ld = round4(max_n);
-    h->nslots = std::min(max_batch, kMaxWavePairs);
+    h->nslots = max_batch;   // one slot per pair of a batch: a batch streams inside one graph
     for (int c = 0; c < FASTPFP_TUNE_SIZES; ++c)
         for (int k = 0; k < FASTPFP_TUNE_COUNTS; ++k) {
             h->tile_f32[c][k] = 128;
@@ -1000,6 +871,8 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
         o.scA = take(n * 4); o.scA2 = take(n * 4); o.scX = take(n * 4); o.scT = take(n * 4);
     }
     const size_t opairs = take(sizeof(PairDesc) * kMaxWavePairs);
+    const size_t otmpl = take(sizeof(PairDesc) * (size_t)max_batch);
+    const size_t ostream = take(sizeof(StreamState));
     const size_t oband = take(sizeof(int) * 2 * (h->num_sms + 1));
     const size_t owave = take(sizeof(WaveCtrl));
     const size_t oloop = take(sizeof(int));
@@ -1023,6 +896,8 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
         if (h->h_band) cudaFreeHost(h->h_band);
         if (h->h_done) cudaFreeHost(h->h_done);
         if (h->h_flags) cudaFreeHost(h->h_flags);
+        if (h->h_tmpl) cudaFreeHost(h->h_tmpl);
+        if (h->h_stream) cudaFreeHost(h->h_stream);
         if (h->cap) cudaStreamDestroy(h->cap);
         if (h->pool) cudaFree(h->pool);
         delete h;
@@ -1034,6 +909,8 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
         cudaMallocHost(&h->h_band, sizeof(int) * 2 * (h->num_sms + 1)) != cudaSuccess ||
         cudaMallocHost(&h->h_done, sizeof(int) * 8) != cudaSuccess ||
         cudaMallocHost(&h->h_flags, sizeof(int) * (kMaxWavePairs + 1)) != cudaSuccess ||
+        cudaMallocHost(&h->h_tmpl, sizeof(PairDesc) * (size_t)max_batch) != cudaSuccess ||
+        cudaMallocHost(&h->h_stream, sizeof(StreamState)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
         return fail(FASTPFP_ERR_CUDA);
     char* b = h->pool;
@@ -1076,6 +953,8 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
         sl.sperm = (int32_t*)(b + o.sp);
     }
     h->d_pairs = (PairDesc*)(b + opairs);
+    h->d_tmpl = (PairDesc*)(b + otmpl);
+    h->d_stream = (StreamState*)(b + ostream);
     h->d_band = (int*)(b + oband);
     h->d_wave = (WaveCtrl*)(b + owave);
     h->d_loop = (int*)(b + oloop);
@@ -1126,6 +1005,8 @@ void fastpfp_destroy(fastpfp_t h) {
     if (h->h_band) cudaFreeHost(h->h_band);
     if (h->h_done) cudaFreeHost(h->h_done);
     if (h->h_flags) cudaFreeHost(h->h_flags);
+    if (h->h_tmpl) cudaFreeHost(h->h_tmpl);
+    if (h->h_stream) cudaFreeHost(h->h_stream);
     if (h->cap) cudaStreamDestroy(h->cap);
     if (h->pool) cudaFree(h->pool);
     delete h;
@@ -1213,6 +1094,122 @@ int stage_out(fastpfp_t h, cudaStream_t s, const fastpfp_pair& x, int slot) {
     return 0;
 }
 
+// A batch larger than one wave, streamed inside one CUDA graph.  Every pair
+// is set up in its own slot; the planner kernel (wave_stream.cu) chooses each
+// outer iteration's wave on the device (stopped pairs leave, waiting pairs
+// join while the band plan fits, the same plans the host would make), the
+// grouped products run over every pair of the batch and skip the idle ones,
+// and the projection launch takes the wave the planner wrote.  The while
+// node ends once every pair has stopped; then every pair is discretised and
+// its outputs written.  One graph launch and one host synchronisation per
+// call.  Returns the worst status.
+int solve_graph_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, const fastpfp_pair* pairs,
+                       const fastpfp_params* p, fastpfp_stats* st, bool host) {
+    const int count = (int)qs.size();
+    const bool lowp = p->precision != FASTPFP_FP32;   // a BF16 or FP8 phase
+    int nl = 0;
+    auto fail = [&](int code) {
+        cudaStreamSynchronize(s);
+        release_graphs(h);
+        return code;
+    };
+    for (int i = 0; i < count; ++i) {
+        if (host) {
+            const int r = stage_in(h, s, pairs[i], p, i, &qs[i]);
+            if (r < 0) return fail(r);
+        }
+        const int r = enqueue_setup(h->slots[i], s, qs[i], p, h->ld);
+        if (r < 0) return fail(r);
+        nl += r;
+        h->h_tmpl[i] = pair_desc(h->slots[i], qs[i], lowp);
+    }
+    StreamState init{};
+    init.count = count;
+    init.first = 1;
+    init.num_sms = h->num_sms;
+    *h->h_stream = init;
+    if (cudaMemcpyAsync(h->d_tmpl, h->h_tmpl, sizeof(PairDesc) * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->d_stream, h->h_stream, sizeof(StreamState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(h->d_wave, 0, sizeof(WaveCtrl), s) != cudaSuccess ||
+        cudaMemsetAsync(h->d_band, 0, sizeof(int) * (h->num_sms + 1), s) != cudaSuccess)
+        return fail(FASTPFP_ERR_CUDA);
+    // the products of every pair (idle and stopped pairs skip theirs)
+    std::vector<Member> all(count);
+    for (int i = 0; i < count; ++i) all[i] = Member{i, i};
+    std::vector<GemmF32TGroup> f32a, f32b;
+    f32_groups(h, qs, all, p, f32a, f32b);
+    TcPlan tc;
+    if (lowp && !plan_tc(h, qs.data(), count, p, &tc)) return fail(FASTPFP_ERR_UNSUPPORTED);
+    Wave none;
+    PdbParams P = wave_params(h, none, 0, p);
+    P.dyn = 1;
+    // the first wave, then the loop: products, projection, next wave
+    if (wave_plan(h->d_stream, h->d_tmpl, h->d_pairs, h->d_band, h->d_wave, s) != cudaSuccess)
+        return fail(FASTPFP_ERR_CUDA);
+    nl += 1;
+    const int cap = count * std::max(1, p->max_outer);   // each iteration advances every pair of a wave
+    static_assert(offsetof(StreamState, done) == 0 && offsetof(StreamState, error) == 4, "StreamState head");
+    const int r = run_outer_graph(h, s, reinterpret_cast<const int*>(h->d_stream), 0, 1, cap,
+                                  [&](int, cudaStream_t cs) -> int {
+        int n = 0;
+        if (lowp) {
+            n = enqueue_tc(tc, cs);
+            if (n < 0) return n;
+        }
+        for (const GemmF32TGroup& g : f32a) FP_CUDA(gemm_f32t_group(g, cs));   // T^T = X^T A
+        for (const GemmF32TGroup& g : f32b) FP_CUDA(gemm_f32t_group(g, cs));   // Y = T A' + lambda K
+        n += (int)(f32a.size() + f32b.size());
+        FP_CUDA(pdb_launch(P, h->num_sms, (size_t)kPdMaxSmem, cs));
+        FP_CUDA(wave_plan(h->d_stream, h->d_tmpl, h->d_pairs, h->d_band, h->d_wave, cs));
+        return n + 2;
+    });
+    if (r < 0) return fail(r);
+    for (int i = 0; i < count; ++i) {
+        const int f = enqueue_finish(h->slots[i], s, qs[i], p, h->num_sms, &h->host_ctrl[i]);
+        if (f < 0) return fail(f);
+        nl += f;
+        if (save_trace(h, s, i, i, p->max_outer) < 0) return fail(FASTPFP_ERR_CUDA);
+        if (host && stage_out(h, s, pairs[i], i) < 0) return fail(FASTPFP_ERR_CUDA);
+    }
+    const cudaError_t es = cudaStreamSynchronize(s);
+    h->host_syncs += 1;
+    int loop_iters = 0;
+    StreamState fin{};
+    if (es == cudaSuccess) {
+        FP_CUDA(cudaMemcpy(&loop_iters, h->d_loop, sizeof(int), cudaMemcpyDeviceToHost));
+        FP_CUDA(cudaMemcpy(&fin, h->d_stream, offsetof(StreamState, act), cudaMemcpyDeviceToHost));
+    }
+    release_graphs(h);
+    if (es != cudaSuccess) return FASTPFP_ERR_CUDA;
+    nl += 1 + h->loop_body * loop_iters;   // loop_init + iterations
+    int worst = FASTPFP_OK;
+    for (int i = 0; i < count; ++i) {
+        Ctrl& c = h->host_ctrl[i];
+        // an error of a shared launch belongs to every pair it left unfinished
+        if (fin.error != 0 && c.error == 0 && !c.done) c.error = fin.error;
+        const int rc = fill_stats(c, qs[i].transposed, nl / count + (i < nl % count ? 1 : 0), c.wave_pairs,
+                                  st ? &st[i] : nullptr, h->host_syncs);
+        if (rc != FASTPFP_OK && worst == FASTPFP_OK) worst = rc;
+    }
+    h->last_count = count;
+    return worst;
+}
+
+// True when a batch can stream inside one graph: the graph loop is asked
+// for, every pair has its own slot, and every pair fits in a wave alone.
+bool graph_streamable(fastpfp_t h, const std::vector<Problem>& qs, const fastpfp_params* p) {
+    if (p->loop_mode != 0 || p->profile || (int)qs.size() > h->nslots) return false;
+    std::vector<int> seen;
+    for (const Problem& q : qs) {
+        if (q.N > kPdbMaxN) return false;
+        if (std::find(seen.begin(), seen.end(), q.N) != seen.end()) continue;
+        Wave w;
+        if (!plan_bands(qs, (int)(&q - qs.data()), 1, h->num_sms, &w)) return false;
+        seen.push_back(q.N);
+    }
+    return true;
+}
+
 // Continuous batching for batches that do not fit in one wave.  A wave is
 // kept full: after every outer iteration (one pdb_kernel launch over the
 // wave's active pairs and their grouped products) the host reads the pairs'
@@ -1286,6 +1283,7 @@ int solve_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, const fa
             if (save_trace(h, s, slot, next, p->max_outer) < 0) return fail(FASTPFP_ERR_CUDA);
             if (host && stage_out(h, s, pairs[next], slot) < 0) return fail(FASTPFP_ERR_CUDA);
             if (cudaStreamSynchronize(s) != cudaSuccess) return FASTPFP_ERR_CUDA;
+            h->host_syncs += 1;
             if (h->loop_body > 0) {
                 int it = 0;
                 FP_CUDA(cudaMemcpy(&it, h->d_loop, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1352,6 +1350,7 @@ int solve_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, const fa
             return fail(FASTPFP_ERR_CUDA);
         kl += 2;   // the flag gather and the pdb launch
         if (cudaStreamSynchronize(s) != cudaSuccess) return FASTPFP_ERR_CUDA;
+        h->host_syncs += 1;
         float tg = 0.f, tp = 0.f;
         if (prof) {
             cudaEventElapsedTime(&tg, h->ev[0], h->ev[1]);
@@ -1386,11 +1385,12 @@ int solve_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, const fa
         act.swap(keep);
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return FASTPFP_ERR_CUDA;
+    h->host_syncs += 1;
     int worst = FASTPFP_OK;
     for (int b = 0; b < count; ++b) {
         if (werr_of[b] != 0 && h->host_ctrl[b].error == 0) h->host_ctrl[b].error = werr_of[b];
         fastpfp_stats* sb = st ? &st[b] : nullptr;
-        const int rc = fill_stats(h->host_ctrl[b], qs[b].transposed, nl[b], wave_of[b], sb);
+        const int rc = fill_stats(h->host_ctrl[b], qs[b].transposed, nl[b], wave_of[b], sb, h->host_syncs);
         if (sb && prof) {
             sb->ms_gemm = ms_g[b];
             sb->ms_proj = ms_p[b];
@@ -1404,6 +1404,7 @@ int solve_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, const fa
 
 int solve_batch(fastpfp_t h, cudaStream_t s, int count, const fastpfp_pair* pairs,
                 const fastpfp_params* p, fastpfp_stats* st, bool host) {
+    h->host_syncs = 0;
     std::vector<Problem> qs(count);
     for (int b = 0; b < count; ++b) {
         const fastpfp_pair& x = pairs[b];
@@ -1416,7 +1417,9 @@ int solve_batch(fastpfp_t h, cudaStream_t s, int count, const fastpfp_pair* pair
     // no wave runs through pd_kernel
     Wave w;
     const bool batched = plan_wave(qs, 0, h->nslots, h->num_sms, &w);
-    if (count > 1 && (!batched || w.count < count)) return solve_stream(h, s, qs, pairs, p, st, host);
+    if (count > 1 && (!batched || w.count < count))
+        return graph_streamable(h, qs, p) ? solve_graph_stream(h, s, qs, pairs, p, st, host)
+                                          : solve_stream(h, s, qs, pairs, p, st, host);
     const int cnt = batched ? w.count : 1;
     if (host)
         for (int i = 0; i < cnt; ++i) {
@@ -1438,6 +1441,7 @@ int solve_batch(fastpfp_t h, cudaStream_t s, int count, const fastpfp_pair* pair
         for (int i = 0; i < cnt; ++i)
             if (stage_out(h, s, pairs[i], i) < 0) return FASTPFP_ERR_CUDA;
     const cudaError_t es = cudaStreamSynchronize(s);
+    h->host_syncs += 1;
     int loop_iters = 0;
     if (es == cudaSuccess && h->loop_body > 0)
         FP_CUDA(cudaMemcpy(&loop_iters, h->d_loop, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1458,7 +1462,7 @@ int solve_batch(fastpfp_t h, cudaStream_t s, int count, const fastpfp_pair* pair
     for (int i = 0; i < cnt; ++i) {
         const int launches = nl / cnt + (i == 0 ? nl % cnt : 0);
         const int rc = fill_stats(h->host_ctrl[i], qs[i].transposed, launches, batched ? cnt : 0,
-                                  st ? &st[i] : nullptr);
+                                  st ? &st[i] : nullptr, h->host_syncs);
         if (st && p->profile) read_profile(h, outer, 1.0f / (float)cnt, &st[i]);
         if (rc != FASTPFP_OK && worst == FASTPFP_OK) worst = rc;
     }

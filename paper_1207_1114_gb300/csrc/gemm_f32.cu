@@ -17,7 +17,9 @@ __global__ void __launch_bounds__(kThreads) gemm_f32_kernel(const __grid_constan
     const GemmF32Args& g = grp.a[blockIdx.z];
     if ((int)blockIdx.y * BM >= g.M || (int)blockIdx.x * BN >= g.Nc) return;
     if (g.ctrl) {
-        if (ld_relaxed_i32(&g.ctrl->done) != 0 || ld_relaxed_i32(&g.ctrl->error) != 0) return;
+        if (ld_relaxed_i32(&g.ctrl->done) != 0 || ld_relaxed_i32(&g.ctrl->error) != 0 ||
+            ld_relaxed_i32(&g.ctrl->idle) != 0)
+            return;
         if (ld_relaxed_i32(&g.ctrl->lowp) != 0) return;
     }
     __shared__ __align__(16) float As[2][BK][BM];
@@ -143,7 +145,9 @@ __global__ void __launch_bounds__(kThreads) gemm_f32t_kernel(const __grid_consta
     const GemmF32TArgs& g = grp.a[blockIdx.z];
     if ((int)blockIdx.y * BMT >= g.M || (int)blockIdx.x * BN >= g.Nc) return;
     if (g.ctrl) {
-        if (ld_relaxed_i32(&g.ctrl->done) != 0 || ld_relaxed_i32(&g.ctrl->error) != 0) return;
+        if (ld_relaxed_i32(&g.ctrl->done) != 0 || ld_relaxed_i32(&g.ctrl->error) != 0 ||
+            ld_relaxed_i32(&g.ctrl->idle) != 0)
+            return;
         if (ld_relaxed_i32(&g.ctrl->lowp) != 0) return;
     }
     extern __shared__ __align__(16) float tsm[];

@@ -163,7 +163,9 @@ __device__ __forceinline__ bool tile_of(const TcGroup& G, int t, int* g, int* m0
     *n0 = (local % G.ntn[p]) * BN;
     const TcProblem& pr = G.prob[p];
     if (pr.ctrl) {
-        if (ld_relaxed_i32(&pr.ctrl->done) != 0 || ld_relaxed_i32(&pr.ctrl->error) != 0) return false;
+        if (ld_relaxed_i32(&pr.ctrl->done) != 0 || ld_relaxed_i32(&pr.ctrl->error) != 0 ||
+            ld_relaxed_i32(&pr.ctrl->idle) != 0)
+            return false;
         if (ld_relaxed_i32(&pr.ctrl->lowp) == 0) return false;
     }
     return true;

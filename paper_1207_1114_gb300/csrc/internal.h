@@ -86,15 +86,6 @@ struct PairDesc {
     int row0;             // first row of the pair in the wave's concatenated rows
 };
 
-// Wave-level state: error word, "every pair done", the grid-barrier counter
-// (it only grows within a call) and its value when the next launch starts.
-struct WaveCtrl {
-    int error;
-    int all_done;
-    unsigned bar;
-    unsigned bar_base;
-};
-
 // Shared-memory sizing of the batched kernel (maxima over the CTAs' bands).
 struct PdbLayout {
     int max_band_rows;    // rows of the largest band
@@ -104,6 +95,19 @@ struct PdbLayout {
     int two_quad_ties;    // pdb_shape's tie rule for this wave (1: two quads per thread)
     int max_segs;         // segments of the band that spans the most pairs (<= kMaxSeg)
     int npairs;           // pairs of the wave: the per-pair tables are sized for this many
+};
+
+// Wave-level state: error word, "every pair done", the grid-barrier counter
+// (it only grows within a call) and its value when the next launch starts.
+// A wave planned on the device (dyn launches) also finds its pair count and
+// layout here.
+struct WaveCtrl {
+    int error;
+    int all_done;
+    unsigned bar;
+    unsigned bar_base;
+    int npairs;
+    PdbLayout layout;
 };
 
 // Warps sharing one row of a pair whose slacked rows hold ldy floats, in a
@@ -181,11 +185,33 @@ struct PdbParams {
     double switch_tol;
     long long timeout_ns;
     int skip_arrive;      // testing only: CTA 0 does not arrive at the first barrier of a solve's first launch
+    int dyn;              // 1: npairs and layout come from the wave control block (a device-planned wave)
 };
 
 cudaError_t pdb_configure();
-size_t pdb_smem_bytes(const PdbLayout& L, int nthr);
 cudaError_t pdb_launch(const PdbParams& P, int grid, size_t smem, cudaStream_t s);
+
+// A batch streamed through waves inside one CUDA graph (wave_stream.cu):
+// pair p of the batch has the wave-table template tmpl[p] (row0 unset); the
+// planner kernel keeps the current wave in act[0..nact) and admits pairs
+// from `next` on.  Words 0 and 1 are the loop's stop and error words.
+struct StreamState {
+    int done;      // 1 once every pair of the batch has stopped, or after an error
+    int error;     // the wave's error word, copied by the planner
+    int count;     // pairs of the batch
+    int next;      // first pair not yet admitted
+    int nact;      // pairs of the current wave
+    int first;     // 1 until the first plan
+    int num_sms;   // CTAs of a wave launch (bands past the plan's are empty)
+    int waves;     // plans made
+    int act[kMaxWavePairs];
+};
+// One planning step (after an outer iteration, or before the first): the
+// wave's stopped pairs leave, waiting pairs join while the band plan fits;
+// writes wave[0..n) and band[0..num_sms], W->npairs / layout / all_done and
+// every pair's idle word.
+cudaError_t wave_plan(StreamState* st, const PairDesc* tmpl, PairDesc* wave, int* band, WaveCtrl* W,
+                      cudaStream_t s);
 
 // ------------------------------------------------- tensor-core products
 constexpr int kTcMaxGroup = 32;      // problems of one grouped launch (a whole wave)
@@ -203,7 +229,8 @@ struct TcProblem {
     const float* Kmat;    // FP32 mode: nullable lambda * K addend, leading dimension ldk
     int ldk;
     float lambda;
-    const Ctrl* ctrl;     // nullable: skip unless the solve runs its low-precision phase
+    const Ctrl* ctrl;     // nullable: skip unless the solve runs (not stopped, no error, not idle)
+                          // in its low-precision phase
     int* err;             // nullable: receives FASTPFP_ERR_TIMEOUT
     const float* rs;      // nullable: per-row output scale (M entries)
     const float* cs;      // nullable: per-column output scale (N entries)
@@ -238,8 +265,8 @@ cudaError_t tc_gemm(const TcGroup& G, cudaStream_t s);
 
 // ----------------------------------------------------------------- GEMM
 // C[M x Nc] = Aop[M x K] * Bop[K x Nc] (+ lambda * Kmat), row-major FP32.
-// When ctrl is set the kernel does nothing unless the solve is running and
-// its precision phase is `phase` (0 FP32, 1 BF16).
+// When ctrl is set the kernel does nothing unless the solve is running (not
+// stopped, no error, not idle) and its precision phase is FP32.
 struct GemmF32Args {
     const float* A; int lda;
     const float* B; int ldb;

@@ -72,7 +72,9 @@ __global__ void __launch_bounds__(256) quant_fp8_kernel(const __grid_constant__ 
     const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (row >= q.rows) return;
     if (q.ctrl) {
-        if (ld_relaxed_i32(&q.ctrl->done) != 0 || ld_relaxed_i32(&q.ctrl->error) != 0) return;
+        if (ld_relaxed_i32(&q.ctrl->done) != 0 || ld_relaxed_i32(&q.ctrl->error) != 0 ||
+            ld_relaxed_i32(&q.ctrl->idle) != 0)
+            return;
         if (ld_relaxed_i32(&q.ctrl->lowp) == 0) return;
     }
     const float* f = q.src_bf16 ? nullptr : reinterpret_cast<const float*>(q.src) + (size_t)row * q.lds;

@@ -21,6 +21,7 @@
 // the loop together.  Pairs whose outer loop has finished are skipped.
 #include <type_traits>
 
+#include "band_plan.cuh"
 #include "common.cuh"
 #include "internal.h"
 
@@ -56,8 +57,8 @@ struct PairS {
     Quant64 sq;     // quantum of the next pass's contributions to s
 };
 
-static_assert(sizeof(Seg) == 44, "pdb_smem_bytes assumes 44-byte segments");
-static_assert(sizeof(PairS) == 80, "pair records are 80 bytes");
+static_assert(sizeof(Seg) == kSegBytes, "pdb_smem_bytes sizes the segment table");
+static_assert(sizeof(PairS) == kPairBytes, "pdb_smem_bytes sizes the pair table");
 
 struct Shared {
     Seg* seg;            // L.max_segs
@@ -419,21 +420,26 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     extern __shared__ __align__(16) char smem_raw[];
     WaveCtrl* W = P.wave;
     if (ld_relaxed_i32(&W->all_done) != 0 || ld_relaxed_i32(&W->error) != 0) return;
-    // the per-pair tables are sized for layout.npairs pairs: a launch with more
-    // would overrun them, so every CTA leaves (the same decision everywhere,
-    // before any barrier)
-    if (P.npairs > P.layout.npairs || P.layout.max_segs < 1) {
+    // a wave planned on the device (dyn) finds its pair count and layout in
+    // the wave control block, written by the planner kernel before the launch
+    const int npairs = P.dyn ? W->npairs : P.npairs;
+    const PdbLayout Lay = P.dyn ? W->layout : P.layout;
+    // the per-pair tables are sized for layout.npairs pairs and the layout
+    // for the launch's shared memory: a launch outside them would overrun,
+    // so every CTA leaves (the same decision everywhere, before any barrier)
+    unsigned dyn_smem;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
+    if (npairs > Lay.npairs || Lay.max_segs < 1 || pdb_smem_bytes(Lay, kPdbThreads) > dyn_smem) {
         if (threadIdx.x == 0 && blockIdx.x == 0) atomicCAS(&W->error, 0, FASTPFP_ERR_ARG);
         return;
     }
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const unsigned G = gridDim.x;
-    Shared S = carve_b(smem_raw, P.layout, nthr);
+    Shared S = carve_b(smem_raw, Lay, nthr);
     int* err = &W->error;
     const unsigned base = W->bar_base;
     unsigned gen = 0u;
-    const int npairs = P.npairs;
-    const int RPS = P.layout.rp_stride;
+    const int RPS = Lay.rp_stride;
     // testing only (debug_flags bit 0): CTA 0 skips its first arrival of the
     // first launch of a solve, so every wait of that launch runs out
     bool skip_first = P.skip_arrive && blockIdx.x == 0 && ld_relaxed_i32(&P.pairs[0].ctrl->outer) == 0;
@@ -442,7 +448,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     if (tid == 0) {
         int nseg = 0, brow = 0, soff = 0, coff = 0, tcol = 0;
         const int b0 = P.band_row[blockIdx.x], b1 = P.band_row[blockIdx.x + 1];
-        for (int p = 0; p < npairs && nseg < P.layout.max_segs; ++p) {
+        for (int p = 0; p < npairs && nseg < Lay.max_segs; ++p) {
             const PairDesc& d = P.pairs[p];
             const int lo = max(b0, d.row0), hi = min(b1, d.row0 + d.N);
             if (lo >= hi) continue;
@@ -454,8 +460,8 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             s.soff = soff;
             s.coff = coff;
             s.tcol = tcol;
-            s.tm = pdb_tmem_rows(s.nrows, d.ldy, nthr, tcol, &s.ntm, &tcol, P.layout.two_quad_ties);
-            const PdbShape sh = pdb_shape(d.ldy, nthr, P.layout.two_quad_ties);
+            s.tm = pdb_tmem_rows(s.nrows, d.ldy, nthr, tcol, &s.ntm, &tcol, Lay.two_quad_ties);
+            const PdbShape sh = pdb_shape(d.ldy, nthr, Lay.two_quad_ties);
             s.qpg = sh.qpg;
             s.rpkq = 4 * sh.rp + sh.kq;
             S.seg[nseg++] = s;
@@ -674,7 +680,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             const Seg sg = S.seg[si];
             const int pst = S.pstate[sg.pair];
             if (!(pst & 1) || (pst & 2)) continue;
-            const int nw = pdb_row_warps(S.pair[sg.pair].ldy, nthr, P.layout.two_quad_ties);
+            const int nw = pdb_row_warps(S.pair[sg.pair].ldy, nthr, Lay.two_quad_ties);
             for (int r = tid; r < sg.nrows; r += nthr) {
                 const float* rpp = S.rowpart + (size_t)(sg.brow0 + r) * RPS;
                 float t = 0.f;
@@ -1028,23 +1034,6 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
 }
 
 }  // namespace
-
-size_t pdb_smem_bytes(const PdbLayout& L, int nthr) {
-    size_t off = 0;
-    auto take = [&](size_t bytes) { off = (off + bytes + 15) & ~size_t(15); };
-    take(sizeof(Seg) * (size_t)L.max_segs);
-    take(sizeof(PairS) * (size_t)L.npairs);
-    take(4 * (size_t)L.npairs);
-    take(4 * (size_t)L.npairs);
-    take(4 * 8);
-    take(4 * ((size_t)L.npairs + 1));
-    take(4 * (size_t)L.max_segs * 32);
-    take(4 * (size_t)L.max_band_rows);
-    take(4 * (size_t)L.max_band_rows * L.rp_stride);
-    take(4 * (size_t)L.max_band_cols);
-    take(4 * (size_t)L.max_band_elems);
-    return off;
-}
 
 cudaError_t pdb_configure() {
     return cudaFuncSetAttribute((const void*)pdb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -1,0 +1,194 @@
+// wave_stream.cu -- the planner of a batch streamed through waves inside one
+// CUDA graph.
+//
+// A batch larger than one wave keeps a wave full: pairs that stopped leave,
+// waiting pairs join while the wave's band plan still fits on chip.  This
+// kernel takes those decisions on the device after every outer iteration
+// (one CTA): it reads the stop words of the wave's pairs, admits waiting
+// pairs in batch order, cuts the new wave into bands with the shared band
+// planner (band_plan.cuh; its binary search on the band cost bound runs as
+// rounds of candidate bounds evaluated by all threads at once, and finds the
+// same bound as the host's search), and writes the wave tables pdb_kernel
+// reads.  The products run over every pair of the batch and skip the pairs
+// that are idle (not in the wave), so no launch depends on host decisions
+// and the whole repeat loop is one graph launch.
+#include "band_plan.cuh"
+#include "common.cuh"
+#include "internal.h"
+
+namespace fpfp {
+namespace {
+
+constexpr int kPlanThreads = 512;
+
+struct PlanShared {
+    int list[kMaxWavePairs + 1];   // pair indices of the wave being planned, in admission order
+    int Ns[kMaxWavePairs + 1];     // their canonical row counts
+    int n;                         // pairs in list
+    int best;                      // smallest candidate index whose cut fits
+    long long lo, hi;              // search interval of the band cost bound
+    int Gmax, t2, ok;
+    WavePlan plan;                 // the last plan that fit
+    WavePlan trial;
+};
+
+// The smallest band cost bound whose greedy cut needs at most Gmax bands, for
+// the pairs Ns[0..n): rounds in which every thread tests one of kPlanThreads
+// bounds spread over the interval; the interval shrinks to the step between
+// the last bound that did not fit and the first that did.  Block-wide.
+__device__ long long search_bound(PlanShared& S, const int* Ns, int n, long long seg_cost, int Gmax) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    if (tid == 0) cut_interval(Ns, n, seg_cost, &S.lo, &S.hi);
+    __syncthreads();
+    while (true) {
+        const long long lo = S.lo, hi = S.hi;
+        if (lo >= hi) break;   // every thread reads the same interval
+        __syncthreads();
+        if (tid == 0) S.best = nthr;
+        __syncthreads();
+        const long long C = lo + ((hi - lo) * (long long)(tid + 1)) / nthr;   // thread nthr - 1 tests hi
+        if (cut_rows(Ns, n, C, seg_cost, Gmax, nullptr) <= Gmax) atomicMin(&S.best, tid);
+        __syncthreads();
+        if (tid == 0) {
+            const int t = S.best < nthr ? S.best : nthr - 1;   // hi always fits (one band holds all)
+            S.hi = lo + ((hi - lo) * (long long)(t + 1)) / nthr;
+            S.lo = t == 0 ? lo : lo + ((hi - lo) * (long long)t) / nthr + 1;
+        }
+        __syncthreads();
+    }
+    return S.lo;
+}
+
+// plan_bands_seq of band_plan.cuh with the bound search spread over the
+// block; the result (into *w) is the same.  Block-wide; returns S.ok.
+__device__ bool plan_bands_par(PlanShared& S, const int* Ns, int n, int num_sms, int max_level, WavePlan* w) {
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        wave_shape(Ns, n, num_sms, &S.Gmax, &S.t2);
+        S.ok = 0;
+    }
+    __syncthreads();
+    for (int lv = 0; lv <= max_level && lv < 4; ++lv) {
+        const long long seg_cost = seg_cost_of_level(lv);
+        const long long C = search_bound(S, Ns, n, seg_cost, S.Gmax);
+        if (tid == 0) S.ok = finish_plan(Ns, n, C, seg_cost, S.Gmax, S.t2, w) ? 1 : 0;
+        __syncthreads();
+        if (S.ok) break;
+    }
+    return S.ok != 0;
+}
+
+__global__ void __launch_bounds__(kPlanThreads, 1)
+    wave_plan_kernel(StreamState* st, const PairDesc* tmpl, PairDesc* wave, int* band, WaveCtrl* W) {
+    __shared__ PlanShared S;
+    __shared__ int s_go, s_first, s_next, s_try;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    if (tid == 0) {
+        s_go = 1;
+        s_first = st->first;
+        st->error = ld_relaxed_i32(&W->error);
+        if (st->error != 0) {
+            st->done = 1;
+            s_go = 0;
+        } else {
+            // the wave's pairs that are still running stay, in order
+            int n = 0, left = 0;
+            for (int i = 0; i < st->nact; ++i) {
+                const int p = st->act[i];
+                const Ctrl* c = tmpl[p].ctrl;
+                if (ld_relaxed_i32(&c->done) != 0 || ld_relaxed_i32(&c->error) != 0) {
+                    ++left;
+                    continue;
+                }
+                S.list[n] = p;
+                S.Ns[n] = tmpl[p].N;
+                ++n;
+            }
+            S.n = n;
+            // nothing changes until a pair stops (the wave and its plan stay)
+            if (!s_first && left == 0) s_go = 0;
+        }
+    }
+    __syncthreads();
+    if (!s_go) return;
+    if (s_first) {   // every pair of the batch waits until it is admitted
+        for (int p = tid; p < st->count; p += nthr) tmpl[p].ctrl->idle = 1;
+        __syncthreads();
+    }
+    // admit waiting pairs in batch order while the plan with the next one
+    // still fits: at the admission level once the wave has pairs, at any
+    // level for its first pair
+    bool have = false;
+    while (true) {
+        if (tid == 0) {
+            s_next = st->next;
+            s_try = s_next < st->count && S.n < kMaxWavePairs && tmpl[s_next].N <= kPdbMaxN;
+            if (s_try) {
+                S.list[S.n] = s_next;
+                S.Ns[S.n] = tmpl[s_next].N;
+            }
+        }
+        __syncthreads();
+        if (!s_try) break;
+        const int lvl = S.n == 0 ? 3 : kAdmitLevel;
+        if (!plan_bands_par(S, S.Ns, S.n + 1, st->num_sms, lvl, &S.trial)) break;
+        if (tid == 0) {
+            S.plan = S.trial;
+            S.n += 1;
+            st->next = s_next + 1;
+        }
+        have = true;
+        __syncthreads();
+    }
+    // no admission: the remaining pairs, at any level; if even that does not
+    // fit, the longest prefix of them that does (the others wait)
+    if (!have) {
+        while (S.n > 0 && !plan_bands_par(S, S.Ns, S.n, st->num_sms, 3, &S.plan)) {
+            if (tid == 0) S.n -= 1;
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    // the wave tables: pairs (rows numbered through the wave), bands (the
+    // launch's extra CTAs get empty bands), layout and the idle words
+    const int n = S.n;
+    for (int i = tid; i < st->nact; i += nthr) tmpl[st->act[i]].ctrl->idle = 1;
+    __syncthreads();
+    if (tid == 0) {
+        int row0 = 0;
+        for (int i = 0; i < n; ++i) {
+            PairDesc d = tmpl[S.list[i]];
+            d.row0 = row0;
+            row0 += d.N;
+            wave[i] = d;
+            Ctrl* c = d.ctrl;
+            c->idle = 0;
+            if (n > c->wave_pairs) c->wave_pairs = n;
+            st->act[i] = S.list[i];
+        }
+        st->nact = n;
+        const int G = n > 0 ? S.plan.grid : 0;
+        for (int c = 0; c <= st->num_sms; ++c) band[c] = c <= G && n > 0 ? S.plan.band[c] : row0;
+        W->npairs = n;
+        W->layout = S.plan.layout;
+        W->all_done = n == 0 ? 1 : 0;
+        st->first = 0;
+        st->done = (n == 0 && st->next >= st->count) ? 1 : 0;
+        st->waves += 1;
+        if (n == 0 && st->next < st->count) {   // a waiting pair fits in no wave
+            atomicCAS(&W->error, 0, FASTPFP_ERR_UNSUPPORTED);
+            st->error = FASTPFP_ERR_UNSUPPORTED;
+            st->done = 1;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t wave_plan(StreamState* st, const PairDesc* tmpl, PairDesc* wave, int* band, WaveCtrl* W,
+                      cudaStream_t s) {
+    wave_plan_kernel<<<1, kPlanThreads, 0, s>>>(st, tmpl, wave, band, W);
+    return cudaGetLastError();
+}
+
+}  // namespace fpfp

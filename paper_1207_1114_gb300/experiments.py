@@ -61,7 +61,7 @@ def lipschitz_step(A: np.ndarray, A2: np.ndarray, iters: int = 60) -> float:
     return 1.0 / L if L > 0 else 1.0
 
 
-def _solve_timed(solver, g, params, dev):
+def _solve_timed(solver, g, params, dev, want_X=False):
     import torch
     A = torch.as_tensor(g.A, device=dev)
     A2 = torch.as_tensor(g.A2, device=dev)
@@ -70,14 +70,17 @@ def _solve_timed(solver, g, params, dev):
     solver.match(A, A2, B, B2, params=params)          # warm-up (graph capture, caches)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    r = solver.match(A, A2, B, B2, params=params)
+    r = solver.match(A, A2, B, B2, params=params, want_X=want_X)
     torch.cuda.synchronize()
     return r, time.perf_counter() - t0
 
 
 def e1_sweep(sizes=E1_SIZES, cases="abcd", seeds=(0,), algorithms=("fastpfp", "pg"), device: int = 0,
-             max_outer: int = 100, max_inner: int = 1000):
-    """Rows of the Section 5.1 sweep (one per size, case, seed, algorithm)."""
+             max_outer: int = 100, max_inner: int = 1000, detail: bool = False):
+    """Rows of the Section 5.1 sweep (one per size, case, seed, algorithm).
+    detail: each row also carries the solve's permutation, its inner-count
+    trace, its soft assignment X and its parameters (for checking against
+    the oracle)."""
     import torch
     dev = torch.device("cuda", device)
     solver = F.Solver(max_n=max(sizes), max_batch=1, device=device)
@@ -96,7 +99,7 @@ def e1_sweep(sizes=E1_SIZES, cases="abcd", seeds=(0,), algorithms=("fastpfp", "p
                         else:
                             alpha = 0.5
                             p = F.default_params(lam=0.0, alpha=alpha, max_outer=max_outer, max_inner=max_inner)
-                        r, sec = _solve_timed(solver, g, p, dev)
+                        r, sec = _solve_timed(solver, g, p, dev, want_X=detail)
                         perm = r.perm.cpu().numpy()
                         inl = g.gt >= 0
                         rows.append(dict(n=n, case=case, seed=seed, algorithm=alg, alpha=alpha,
@@ -104,14 +107,19 @@ def e1_sweep(sizes=E1_SIZES, cases="abcd", seeds=(0,), algorithms=("fastpfp", "p
                                          converged=bool(r.stats.converged),
                                          error=matching_error(g.A, g.A2, perm) - err_gt,
                                          accuracy=float((perm[inl] == g.gt[inl]).mean())))
+                        if detail:
+                            rows[-1].update(perm=perm, inner=solver.last_trace()[0], X=r.X.cpu().numpy(),
+                                            objective=float(r.stats.objective),
+                                            max_outer=max_outer, max_inner=max_inner)
     finally:
         solver.close()
     return rows
 
 
-def alpha_sweep(alphas=ALPHAS, seeds=(0, 1, 2), device: int = 0, n: int = 1000):
+def alpha_sweep(alphas=ALPHAS, seeds=(0, 1, 2), device: int = 0, n: int = 1000, detail: bool = False):
     """Rows of the step-size sweep on attributed n-node pairs (one per alpha
-    and seed)."""
+    and seed).  detail: each row also carries the permutation, the
+    inner-count trace and the soft assignment X."""
     import torch
     dev = torch.device("cuda", device)
     solver = F.Solver(max_n=n, max_batch=1, device=device)
@@ -121,11 +129,13 @@ def alpha_sweep(alphas=ALPHAS, seeds=(0, 1, 2), device: int = 0, n: int = 1000):
             g = synth.attributed_1000(seed=seed, n=n)
             for a in alphas:
                 p = F.default_params(lam=g.lam, alpha=float(a))
-                r, sec = _solve_timed(solver, g, p, dev)
+                r, sec = _solve_timed(solver, g, p, dev, want_X=detail)
                 perm = r.perm.cpu().numpy()
                 rows.append(dict(alpha=float(a), seed=seed, seconds=sec, outer=int(r.stats.outer_iters),
                                  converged=bool(r.stats.converged), objective=float(r.stats.objective),
                                  accuracy=float((perm == g.gt).mean())))
+                if detail:
+                    rows[-1].update(perm=perm, inner=solver.last_trace()[0], X=r.X.cpu().numpy())
     finally:
         solver.close()
     return rows

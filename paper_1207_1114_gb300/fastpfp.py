@@ -53,7 +53,7 @@ class fastpfp_stats(C.Structure):
                 ("transposed", C.c_int), ("status", C.c_int), ("launches", C.c_int),
                 ("wave_pairs", C.c_int),
                 ("final_delta", C.c_double), ("objective", C.c_double), ("ms_gemm", C.c_float),
-                ("ms_proj", C.c_float), ("ms_disc", C.c_float)]
+                ("ms_proj", C.c_float), ("ms_disc", C.c_float), ("host_syncs", C.c_int)]
 
 
 class fastpfp_pair(C.Structure):

@@ -111,15 +111,28 @@ def partial_1000_1200(seed: int = 0, n: int = 1000, n_out: int = 200) -> GraphPa
     return graph_pair(n, p=0.1, sigma=0.03, k=16, attr_sigma=0.05, n_out=n_out, lam=0.5, seed=seed)
 
 
+def batch_mixed_sizes(count: int = 512, seed: int = 0, n_lo: int = 50, n_hi: int = 600,
+                      out_hi: int = 100) -> list[tuple[int, int]]:
+    """(n, outliers) of every pair of batch_mixed(count, seed, ...), drawn
+    without generating the graphs."""
+    rng = np.random.default_rng(seed)
+    ns = rng.integers(n_lo, n_hi + 1, size=count)
+    outs = rng.integers(0, out_hi + 1, size=count)
+    return [(int(ns[b]), int(outs[b])) for b in range(count)]
+
+
+def batch_mixed_pair(b: int, n: int, n_out: int, seed: int = 0) -> GraphPair:
+    """Pair b of batch_mixed(..., seed) given its drawn (n, outliers)."""
+    return graph_pair(n, p=0.15, sigma=0.03, k=8, attr_sigma=0.05, n_out=n_out, lam=0.5,
+                      seed=seed * 100003 + b + 1)
+
+
 def batch_mixed(count: int = 512, seed: int = 0, n_lo: int = 50, n_hi: int = 600,
                 out_hi: int = 100) -> list[GraphPair]:
     """Batch of pairs with n ~ U{n_lo..n_hi}, n' = n + U{0..out_hi} outliers,
     p = 0.15, noise 0.03, 8-dim attributes, lambda = 0.5."""
-    rng = np.random.default_rng(seed)
-    ns = rng.integers(n_lo, n_hi + 1, size=count)
-    outs = rng.integers(0, out_hi + 1, size=count)
-    return [graph_pair(int(ns[b]), p=0.15, sigma=0.03, k=8, attr_sigma=0.05, n_out=int(outs[b]),
-                       lam=0.5, seed=seed * 100003 + b + 1) for b in range(count)]
+    sizes = batch_mixed_sizes(count, seed, n_lo, n_hi, out_hi)
+    return [batch_mixed_pair(b, n, o, seed) for b, (n, o) in enumerate(sizes)]
 
 
 def large_4000(seed: int = 0, n: int = 4000) -> GraphPair:

@@ -58,10 +58,13 @@ def test_default_params_and_error_strings(built):
 def test_struct_layouts_match_header():
     """The ctypes mirrors have the size the C compiler gives the header's structs."""
     src = r'''
+#include <stddef.h>
 #include <stdio.h>
 #include "fastpfp.h"
 int main(void) {
   printf("%zu %zu %zu\n", sizeof(fastpfp_params), sizeof(fastpfp_stats), sizeof(fastpfp_pair));
+  printf("%zu %zu %zu\n", offsetof(fastpfp_stats, wave_pairs), offsetof(fastpfp_stats, ms_disc),
+         offsetof(fastpfp_stats, host_syncs));
   printf("%d %d %d %d %d %d %d\n", FASTPFP_FP32, FASTPFP_BF16, FASTPFP_FP8, FASTPFP_ALG_FASTPFP,
          FASTPFP_ALG_PG, FASTPFP_TUNE_SIZES, FASTPFP_TUNE_COUNTS);
   return 0;
@@ -76,5 +79,8 @@ int main(void) {
     sizes = [int(x) for x in lines[0].split()]
     assert sizes == [C.sizeof(F.fastpfp_params), C.sizeof(F.fastpfp_stats),
                      C.sizeof(F.fastpfp_pair)]
-    consts = [int(x) for x in lines[1].split()]
+    offs = [int(x) for x in lines[1].split()]
+    assert offs == [F.fastpfp_stats.wave_pairs.offset, F.fastpfp_stats.ms_disc.offset,
+                    F.fastpfp_stats.host_syncs.offset]
+    consts = [int(x) for x in lines[2].split()]
     assert consts == [F.FP32, F.BF16, F.FP8, F.ALG_FASTPFP, F.ALG_PG, F.TUNE_SIZES, F.TUNE_COUNTS]

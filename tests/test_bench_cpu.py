@@ -70,6 +70,26 @@ def test_oracle_timed_solves_are_whole_solves():
     assert kw["algorithm"] == "pg" and kw["alpha"] == 0.1 and kw["normalize_max"] is False
 
 
+def test_rank_shares_split_the_job_by_cost():
+    """Under torchrun every rank takes its share of the whole job's
+    world x batch pairs from shard.partition: the shares are disjoint and
+    complete, equal-size pairs split evenly, and one rank's share is the
+    job's first pairs (the same pairs as before the split existed)."""
+    world, batch = 2, 6
+    shapes = bench.global_shapes("batch_mixed_512", world * batch)
+    shares = [bench.rank_share("batch_mixed_512", r, world, batch)[0] for r in range(world)]
+    assert sorted(shares[0] + shares[1]) == list(range(world * batch))
+    from paper_1207_1114_gb300 import shard
+    cost = [sum(shard.pair_cost(*shapes[i]) for i in sh) for sh in shares]
+    assert max(cost) <= 1.5 * min(cost)
+    idx, pairs = bench.rank_share("batch_mixed_512", 1, world, batch)
+    for i, g in zip(idx, pairs):
+        assert (g.A.shape[0], g.A2.shape[0]) == shapes[i]
+    eq = [bench.rank_share("attributed_1000", r, 2, 2)[0] for r in range(2)]
+    assert sorted(eq[0] + eq[1]) == [0, 1, 2, 3] and len(eq[0]) == len(eq[1]) == 2
+    assert bench.rank_share("attributed_1000", 0, 1, 3)[0] == [0, 1, 2]
+
+
 def test_pg_step_is_one_over_the_lipschitz_constant():
     g = synth.graph_pair(30, p=0.3, sigma=0.0, seed=1)
     L = np.linalg.norm(g.A.astype(np.float64), 2) * np.linalg.norm(g.A2.astype(np.float64), 2)

@@ -44,7 +44,7 @@ def dev_pair(g):
 
 @pytest.fixture(scope="module")
 def solver():
-    s = F.Solver(max_n=1000, max_batch=24)
+    s = F.Solver(max_n=1000, max_batch=40)
     yield s
     s.close()
 
@@ -145,9 +145,11 @@ def _check_lowp_batch(solver, pairs, precision, lam, **kw):
     dev = [dev_pair(g) for g in pairs]
     p = F.default_params(lam=lam, precision=precision, refine_iters=40, **kw)
     outs = solver.match_batched(dev, params=p, want_X=True)
+    # every pair's trace now: the reruns at the switch points replace them
+    traces = [solver.last_trace(pair=i)[0] for i in range(len(pairs))]
     errs = []
     for i, (g, o) in enumerate(zip(pairs, outs)):
-        inner, _ = solver.last_trace(pair=i)
+        inner = traces[i]
         st = o.stats
         L, T = st.lowp_iters, st.outer_iters
         assert st.status == 0 and 1 <= L < T and st.converged == 1
@@ -232,3 +234,68 @@ def test_attributed_1000_free_run_matches_stored_oracle_solve(solver):
     assert gold["outer_iters"] <= st.outer_iters <= gold["outer_iters"] + 1
     for t, d in enumerate(gold["delta"][:5]):   # well above the FP32 noise floor
         assert abs(deltas[t] - d) <= 1e-3 * d + 1e-6, (t, deltas[t], d)
+
+
+# ------------------------------------------- a streamed batch in one graph
+
+def _pairs_24():
+    rng = np.random.default_rng(46)
+    return [synth.graph_pair(int(rng.integers(850, 1001)), p=0.1, sigma=0.05, k=8, lam=0.5, seed=900 + i)
+            for i in range(24)]
+
+
+def test_graph_streamed_batch_equals_host_streamed_batch(solver):
+    """A batch larger than one wave with the graph loop (loop_mode 0) runs as
+    one CUDA graph whose planner kernel chooses every wave on the device; with
+    loop_mode 1 the host plans the same waves between outer iterations.  The
+    two give the same bits, and the graph form synchronises the host once."""
+    pairs = _pairs_24()
+    dev = [dev_pair(g) for g in pairs]
+    kw = dict(lam=0.5, max_outer=12, max_inner=80, tol_outer=1e-3)
+    g = solver.match_batched(dev, params=F.default_params(loop_mode=0, **kw), want_X=True)
+    tg = [solver.last_trace(pair=i)[0] for i in range(len(pairs))]
+    h = solver.match_batched(dev, params=F.default_params(loop_mode=1, **kw), want_X=True)
+    assert 0 < max(o.stats.wave_pairs for o in g) < len(pairs)
+    assert len({o.stats.outer_iters for o in g}) > 1        # pairs left at different times
+    assert all(o.stats.host_syncs == 1 for o in g)
+    assert all(o.stats.host_syncs > 1 for o in h)
+    for i, (a, b) in enumerate(zip(g, h)):
+        _same_bits(a, b)
+        assert a.stats.wave_pairs == b.stats.wave_pairs
+        np.testing.assert_array_equal(tg[i], solver.last_trace(pair=i)[0])
+
+
+def test_graph_streamed_batch_matches_oracle(solver):
+    """Every pair of the graph-streamed batch against the oracle replaying
+    its own inner counts (X max-abs 1e-4, greedy bit-exact, objective)."""
+    pairs = _pairs_24()
+    dev = [dev_pair(g) for g in pairs]
+    kw = dict(max_outer=12, max_inner=80, tol_outer=1e-3)
+    outs = solver.match_batched(dev, params=F.default_params(lam=0.5, **kw), want_X=True)
+    for i, (g, o) in enumerate(zip(pairs, outs)):
+        inner, _ = solver.last_trace(pair=i)
+        assert o.stats.status == 0 and len(inner) == o.stats.outer_iters
+        ref = oracle.solve(g.A, g.A2, g.B, g.B2, lam=0.5, replay_inner=inner,
+                           replay_outer=o.stats.outer_iters, **kw)
+        Xg = o.X.cpu().numpy()
+        assert np.abs(Xg - ref["X"]).max() <= 1e-4
+        roc, obj, _ = _greedy_objective(g, Xg, 0.5)
+        np.testing.assert_array_equal(np.argsort(roc), o.perm.cpu().numpy())
+        assert abs(o.stats.objective - obj) <= 1e-5 * abs(obj)
+
+
+def test_graph_streamed_bf16_batch_of_uneven_pairs(solver):
+    """A mixed batch of 40 uneven pairs (outliers on either side) with the
+    BF16 phase, streamed in one graph: identical to the host-planned stream,
+    and every pair ends at the plain FP32 solve's objective."""
+    pairs = synth.batch_mixed(count=40, seed=47, n_lo=300, n_hi=900, out_hi=100)
+    dev = [dev_pair(g) for g in pairs]
+    kw = dict(lam=0.5, precision=F.BF16, refine_iters=30, max_inner=200)
+    g = solver.match_batched(dev, params=F.default_params(loop_mode=0, **kw), want_X=True)
+    h = solver.match_batched(dev, params=F.default_params(loop_mode=1, **kw), want_X=True)
+    assert max(o.stats.wave_pairs for o in g) < len(pairs) and g[0].stats.host_syncs == 1
+    p32 = solver.match_batched(dev, params=F.default_params(lam=0.5, max_inner=200))
+    for a, b, c in zip(g, h, p32):
+        _same_bits(a, b)
+        assert a.stats.status == 0 and a.stats.lowp_iters >= 1
+        assert abs(a.stats.objective - c.stats.objective) <= 1e-4 * abs(c.stats.objective)

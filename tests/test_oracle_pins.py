@@ -414,3 +414,15 @@ def test_pg_is_equivariant_under_relabelling():
     rq = oracle.solve(g.A, g.A2[q][:, q], g.B, g.B2[q], **kw)
     np.testing.assert_allclose(rq["X"], r["X"][:, q], atol=1e-10)
     np.testing.assert_allclose(rq["delta"], r["delta"], rtol=1e-8, atol=1e-12)
+
+
+def test_replay_rejects_a_trace_shorter_than_the_replay():
+    """A replay needs one positive inner count per outer iteration it runs;
+    a shorter or zero trace is an error, not a read past its end."""
+    g = synth.plain_100(0)
+    with pytest.raises(ValueError):
+        oracle.solve(g.A, g.A2, replay_inner=[3, 3], replay_outer=3)
+    with pytest.raises(ValueError):
+        oracle.solve(g.A, g.A2, replay_inner=[3, 0, 3], replay_outer=3)
+    r = oracle.solve(g.A, g.A2, replay_inner=[3, 3, 3, 9], replay_outer=3)
+    assert list(r["inner"]) == [3, 3, 3]
