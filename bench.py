@@ -76,12 +76,16 @@ def peaks():
 def gemm_probe_line(F, device: int, n: int = 4096):
     """The product kernels timed alone at n^3 (fastpfp_gemm_probe) against
     their peaks: BF16 against the measured cuBLAS burst, E4M3 against twice
-    that (the nominal FP8:BF16 ratio), FP32 SIMT against its derived peak."""
+    that (the nominal FP8:BF16 ratio), split TF32 against a sixth of it,
+    FP32 SIMT against its derived peak."""
     bf16_peak = float(load_peaks().get("bf16_tflops") or 1900.0)   # the fallback burst figure
     f32_peak = F32_SIMT_TFLOPS
     out = {"n": n, "timing": "best of 10 launches, CUDA events, after one warm-up"}
     for name, prec, peak, kind in (
-            ("f32", F.FP32, f32_peak, "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"),
+            ("f32_tc", F.FP32, bf16_peak / 6.0,
+             "split TF32 (3 MMAs per product term) against the measured BF16 burst / 6 (TF32 runs at half "
+             "the BF16 rate, nominal dense ratio; three MMAs)"),
+            ("f32_simt", F.FP32_SIMT, f32_peak, "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"),
             ("bf16", F.BF16, bf16_peak, "measured cuBLAS BF16 burst (MEASURED_PEAKS.json)"),
             ("fp8", F.FP8, 2.0 * bf16_peak, "2 x measured BF16 burst (nominal dense FP8:BF16 ratio)")):
         t = F.gemm_probe(prec, n=n, reps=10, device=device)
@@ -441,44 +445,43 @@ def oracle_solve_seconds(unit, N, m, outer, inner):
             + inner * unit["round"] * N * N)
 
 
-def train_warm_start(F, torch, dev, local, count, seed):
-    """The learned warm start of the large workload: `count` pairs shaped
-    like the partial workload (n in 200..800, up to n/5 outliers, 15-dim
-    attributes) are solved by the plain FP32 solver; their matchings are
-    the targets of one Adam pass (row + column softmax cross-entropy of
-    the similarity S, all on the GPU through fastpfp_warmstart_train_step).
-    Returns the trained parameters and a summary."""
+def train_warm_start(F, torch, dev, local, count, seed, max_n):
+    """The learned warm start of the large workload: `count` pairs shaped like
+    the partial workload (n in 200..800, up to n/5 outliers, 15-dim
+    attributes) are drawn on the GPU, solved by the plain FP32 solver 64 at a
+    time, and their matchings are the targets of one Adam pass (row + column
+    softmax cross-entropy of the similarity S, all on the GPU through
+    fastpfp_warmstart_train_step).  Returns the trained parameters and a
+    summary."""
     from paper_1207_1114_gb300 import synth
-    t0 = time.perf_counter()
-    train = synth.warm_start_train(count, seed=seed)
-    t_gen = time.perf_counter() - t0
-    max_n = max(max(g.A.shape[0], g.A2.shape[0]) for g in train)
-    ts = F.Solver(max_n=max_n, max_batch=64, device=local)
+    ts = F.Solver(max_n=max(max_n, 960), max_batch=64, device=local)
     prm = F.default_params(lam=0.5, **SOLVER)
-    t0 = time.perf_counter()
-    solved = []
-    for c in range(0, count, 64):
-        chunk = train[c:c + 64]
-        dev_chunk = [(torch.as_tensor(g.A, device=dev), torch.as_tensor(g.A2, device=dev),
-                      torch.as_tensor(g.B, device=dev), torch.as_tensor(g.B2, device=dev)) for g in chunk]
-        outs = ts.match_batched(dev_chunk, params=prm)
-        solved += [(d, o.perm) for d, o in zip(dev_chunk, outs)]
-    torch.cuda.synchronize()
-    t_solve = time.perf_counter() - t0
     params = torch.as_tensor(F.init_mlp_params(seed), device=dev)
     m = torch.zeros(F.MLP_NPARAMS, device=dev)
     v = torch.zeros(F.MLP_NPARAMS, device=dev)
-    t0 = time.perf_counter()
-    losses = []
-    for step, (d, perm) in enumerate(solved, start=1):
-        loss, _ = ts.train_step(*d, perm, params, m, v, step=step, lr=3e-3)
-        losses.append(loss)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
+    gen = synth.warm_start_train_torch(count, seed=seed, device=dev)
+    t_gen = t_solve = t_train = 0.0
+    losses, step, chunk = [], 0, 64
+    while step < count:
+        t0 = time.perf_counter()
+        batch = [next(gen) for _ in range(min(chunk, count - step))]
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        outs = ts.match_batched([b[:4] for b in batch], params=prm)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        for b, o in zip(batch, outs):
+            step += 1
+            loss, _ = ts.train_step(*b[:4], o.perm, params, m, v, step=step, lr=3e-3)
+            losses.append(loss)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        t_gen, t_solve, t_train = t_gen + t1 - t0, t_solve + t2 - t1, t_train + t3 - t2
     ts.close()
     k = max(1, min(50, len(losses) // 10))
-    return params, {"train_pairs": count, "train_shape": "n in 200..800, up to n/5 outliers, k=15, lambda=0.5",
-                    "seconds": {"generate_cpu": t_gen, "solve_gpu": t_solve, "train_gpu": t_train},
+    return params, {"train_pairs": count, "train_shape": "n in 200..800, up to n/5 outliers, k=15, lambda=0.5, "
+                                                         "drawn on the GPU (synth.warm_start_train_torch)",
+                    "seconds": {"generate_gpu": t_gen, "solve_gpu": t_solve, "train_gpu": t_train},
                     "loss_first": float(np.mean(losses[:k])), "loss_last": float(np.mean(losses[-k:]))}
 
 
@@ -535,7 +538,7 @@ def main():
     ap.add_argument("--init", default="uniform", choices=["uniform", "learned"],
                     help="X(0): the paper's uniform start, or the learned warm start (trained first, "
                          "on --train-pairs pairs solved by the plain solver)")
-    ap.add_argument("--train-pairs", type=int, default=2000, dest="train_pairs")
+    ap.add_argument("--train-pairs", type=int, default=20000, dest="train_pairs")
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="outer loop: CUDA-graph while node (default) or host-polled chunks")
     ap.add_argument("--algorithm", default="fastpfp", choices=["fastpfp", "pg"],
@@ -591,7 +594,7 @@ def main():
     # then every step computes X(0) for its pairs before solving them
     ws_info, mlp = None, None
     if args.init == "learned":
-        mlp, ws_info = train_warm_start(F, torch, dev, local, args.train_pairs, seed=rank + 11)
+        mlp, ws_info = train_warm_start(F, torch, dev, local, args.train_pairs, seed=rank + 11, max_n=max_n)
 
     def solve(prm):
         if mlp is None:
@@ -717,24 +720,40 @@ def main():
     e2e_value = whole_job_rate(args.batch * e2e_steps, time.perf_counter() - t0, dev)
 
     if ws_info is not None:
-        # the same pairs from the uniform start, same timing rules
+        # the same pairs from the uniform start with the plain FP32 solver,
+        # same timing rules
+        p_fp32 = params(F, lam, loop_mode=loop_mode)
+        solver.match_batched(dpairs, params=p_fp32)   # warm
         u_ms, u_outer, u_acc = [], [], []
         for _ in range(args.steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            uo = solver.match_batched(dpairs, params=p_plain)
+            uo = solver.match_batched(dpairs, params=p_fp32)
             e1.record(stream)
             e1.synchronize()
             u_ms.append(e0.elapsed_time(e1))
             u_outer += [o.stats.outer_iters for o in uo]
             u_acc += [float((o.perm.cpu().numpy() == g.gt).mean()) for o, g in zip(uo, pairs)]
-        ws_info["uniform"] = {"value": whole_job_rate(args.batch * args.steps, sum(u_ms) / 1e3, dev),
-                              "outer_per_pair": float(np.mean(u_outer)), "accuracy": float(np.mean(u_acc))}
-        ws_info["learned"] = {"value": value,
+        ws_info["uniform_fp32"] = {"value": whole_job_rate(args.batch * args.steps, sum(u_ms) / 1e3, dev),
+                                   "ms_per_step": float(np.mean(u_ms)), "precision": "fp32",
+                                   "outer_per_pair": float(np.mean(u_outer)), "accuracy": float(np.mean(u_acc))}
+        # the learned start's own cost (features, MLP, S, Sinkhorn) per step
+        x_ms = []
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for dp in dpairs:
+                solver.warmstart(*dp, mlp, iters=20)
+            e1.record(stream)
+            e1.synchronize()
+            x_ms.append(e0.elapsed_time(e1))
+        ws_info["x0_ms_per_step"] = float(np.mean(x_ms))
+        ws_info["learned"] = {"value": value, "ms_per_step": total_ms / args.steps, "precision": args.precision,
                               "outer_per_pair": float(np.mean([s.outer_iters for st in stats_all for s in st])),
-                              "accuracy": float(np.mean(accs))}
+                              "accuracy": float(np.mean(accs)), "includes": "X(0) computed inside every timed step"}
 
     flat_t = [s for step in stats_all for s in step]
     cpu = None

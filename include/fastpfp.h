@@ -51,14 +51,20 @@ extern "C" {
 #define FASTPFP_MAX_N 16384          /* largest graph a handle can be created for         */
 #define FASTPFP_MAX_K 256            /* largest attribute dimension k                     */
 
-/* Precision of the A X A' products (FP32 accumulation throughout).  BF16:
- * both operands of both products rounded to BF16.  FP8: both operands E4M3
+/* Precision of the A X A' products (FP32 accumulation throughout).  FP32:
+ * the products of FP32 operands on the tensor cores, every operand split
+ * into its TF32 part (rounded to 10 mantissa bits) and its FP32 remainder
+ * and multiplied as hi*hi + hi*lo + lo*hi (relative error about 2^-21 per
+ * product term, below the FP32 accumulation's own).  FP32_SIMT: the same
+ * products on the FP32 FMA pipes (exact FP32 arithmetic).  BF16: both
+ * operands of both products rounded to BF16.  FP8: both operands E4M3
  * (round to nearest even, saturating) with one power-of-two scale per
  * operand row, chosen so the row's largest magnitude maps to at most 448,
  * and both scales applied to the FP32 accumulator: A and A' are quantised
  * once per solve, X^T (through a BF16 copy) and T = A X (through its BF16
- * result) before each product. */
-enum { FASTPFP_FP32 = 0, FASTPFP_BF16 = 1, FASTPFP_FP8 = 2 };
+ * result) before each product.  BF16 and FP8 runs end with FP32
+ * iterations (the FP32 products above). */
+enum { FASTPFP_FP32 = 0, FASTPFP_BF16 = 1, FASTPFP_FP8 = 2, FASTPFP_FP32_SIMT = 3 };
 enum { FASTPFP_ALG_FASTPFP = 0, FASTPFP_ALG_PG = 1 };
 
 typedef struct fastpfp_s* fastpfp_t;
@@ -74,7 +80,8 @@ typedef struct {
     double tol_inner;      /* eps_2: stop P_D when max|Y(u+1) - Y(u)| < eps_2 (Section 5)     */
     int max_outer;         /* I_0: at most this many outer iterations, >= 1                   */
     int max_inner;         /* I_1: at most this many P1/P2 rounds per outer iteration, >= 1   */
-    int precision;         /* FASTPFP_FP32, FASTPFP_BF16 or FASTPFP_FP8 for the A X A' products */
+    int precision;         /* FASTPFP_FP32, FASTPFP_BF16, FASTPFP_FP8 or FASTPFP_FP32_SIMT for the
+                              A X A' products                                                */
     int refine_iters;      /* BF16 / FP8: FP32 outer iterations run after the low-precision
                               phase                                                          */
     double switch_tol;     /* BF16 / FP8: the low-precision phase ends once max|dX| <
@@ -221,8 +228,9 @@ int fastpfp_last_trace(fastpfp_t h, int pair, int* inner_counts, double* deltas,
  *   Y[i, j] = sum_l (sum_q A[i,q] X[q,l]) A2[l,j] + lambda * K[i,j]
  * for i < N, j < m; Y has leading dimension ldy >= m.  A is N x N, X is
  * N x m, A2 is m x m, K is N x m (nullable when lambda == 0).  precision
- * selects FP32, BF16 or FP8 products (FP32 accumulation; FP8 quantises as
- * the solve does, T through a BF16 copy).  Device pointers;
+ * selects FP32 (split TF32 on the tensor cores), FP32_SIMT, BF16 or FP8
+ * products (FP32 accumulation; each quantises as the solve does, FP8's T
+ * through a BF16 copy).  Device pointers;
  * asynchronous on `stream`.  Errors: ERR_ARG, ERR_SIZE, ERR_CUDA. */
 int fastpfp_gradient(fastpfp_t h, void* stream, const float* A, const float* X, const float* A2,
                      const float* K, float lambda, int N, int m, float* Y, int ldy, int precision);
@@ -337,9 +345,10 @@ int fastpfp_bandwidth_probe(int device, int level, int sweeps, double* gbs);
 
 /* Throughput of the gradient's product kernels on CUDA device `device`: one
  * n x n x n product C = A B^T (both operands K-major, values pseudo-random
- * in [-1, 1)) with the kernel `precision` selects (FASTPFP_FP32: the SIMT
- * kernel; FASTPFP_BF16 / FASTPFP_FP8: the tensor-core kernel, 128 x 256
- * tiles, E4M3 with per-row scales), timed alone with CUDA events after one
+ * in [-1, 1)) with the kernel `precision` selects (FASTPFP_FP32: the
+ * tensor-core kernel on split-TF32 operands, three MMAs per product term;
+ * FASTPFP_FP32_SIMT: the SIMT kernel; FASTPFP_BF16 / FASTPFP_FP8: the
+ * tensor-core kernel, 128 x 256 tiles, E4M3 with per-row scales), timed alone with CUDA events after one
  * warm-up launch; *tflops = 2 n^3 / (best of reps) in TFLOP/s.  n a multiple
  * of 16 in [256, 16384], reps in [1, 1000].  Allocates and frees about
  * 16 n^2 bytes; synchronises the device.  Errors: ERR_ARG, ERR_CUDA. */

@@ -76,7 +76,12 @@ __host__ __device__ inline int cut_rows(const int* Ns, int count, long long C, l
         while (r < N) {
             const long long seg = last != i ? seg_cost : 0;
             const long long avail = C - cur - seg;
-            long long k = avail >= ldy ? ((long long)(N - r) < avail / ldy ? (long long)(N - r) : avail / ldy) : 0;
+            long long k = 0;
+            if (avail >= ldy) {   // 32-bit division when the values fit (the device planner's common case)
+                const long long fit = avail <= 0x7fffffffll ? (long long)((unsigned)avail / (unsigned)ldy)
+                                                            : avail / ldy;
+                k = (long long)(N - r) < fit ? (long long)(N - r) : fit;
+            }
             if (k == 0) {
                 if (rows_in > 0) {
                     if (++b >= max_bands) return max_bands + 1;
@@ -141,11 +146,46 @@ __host__ __device__ inline long long seg_cost_of_level(int lv) {
     return lv == 0 ? kSegCost : lv == 1 ? kSegCost / 2 : lv == 2 ? kSegCost / 4 : 0ll;
 }
 
+// Statistics of band [lo, hi) of the concatenated rows (pair p holds rows
+// [p0, p0 + Ns[p]) and is the pair holding row lo): its rows, columns (the
+// sum of its segments' row lengths), floats kept in shared memory and
+// segments.  The first rows of every row group of a segment go to tensor
+// memory (pdb_tmem_rows, the band's segments in pair order as the kernel
+// places them), the rest to shared memory.
+struct BandStat {
+    int rows, cols, elems, segs;
+};
+__host__ __device__ inline BandStat band_stat(const int* Ns, int count, int p, int p0, int lo, int hi, int t2) {
+    BandStat st{0, 0, 0, 0};
+    int tcol = 0;
+    for (int q = p, q0 = p0; q < count && q0 < hi; q0 += Ns[q++]) {
+        const int s0 = lo > q0 ? lo : q0, s1 = hi < q0 + Ns[q] ? hi : q0 + Ns[q];
+        if (s0 >= s1) continue;
+        const int nr = s1 - s0, ldy = bp_round4(Ns[q]);
+        int ntm = 0, next = 0;
+        pdb_tmem_rows(nr, ldy, kPdbThreads, tcol, &ntm, &next, t2);
+        tcol = next;
+        st.rows += nr;
+        st.cols += ldy;
+        st.elems += (nr - ntm) * ldy;
+        ++st.segs;
+    }
+    return st;
+}
+
+// The wave's layout from its bands' statistics (maxima over the bands, the
+// pairs' row-partial stride); false when a CTA's band would not fit (more
+// than kMaxSeg segments, or more shared memory than a CTA has).
+__host__ __device__ inline bool layout_fits(PdbLayout* L, unsigned* smem) {
+    if (L->max_segs > kMaxSeg) return false;
+    const size_t b = pdb_smem_bytes(*L, kPdbThreads);
+    if (b > (size_t)kPdMaxSmem) return false;
+    *smem = (unsigned)b;
+    return true;
+}
+
 // Per-band statistics of the cut at bound C into w->band / w->grid, and the
-// wave's layout: the first rows of every row group of a segment go to tensor
-// memory (pdb_tmem_rows, a band's segments in pair order as the kernel places
-// them), the rest to shared memory.  False when a CTA's band would not fit
-// (more than kMaxSeg segments, or more shared memory than a CTA has).
+// wave's layout (band_stat per band, layout_fits).
 __host__ __device__ inline bool finish_plan(const int* Ns, int count, long long C, long long seg_cost, int Gmax,
                                             int t2, WavePlan* w) {
     int rows = 0;
@@ -153,7 +193,7 @@ __host__ __device__ inline bool finish_plan(const int* Ns, int count, long long 
     const int used = cut_rows(Ns, count, C, seg_cost, Gmax, w->band);
     for (int c = used; c <= Gmax; ++c) w->band[c] = rows;
     const int G = used > 1 ? used : 1;
-    PdbLayout L{0, 0, 0, 1, t2, 1, count};
+    PdbLayout L{0, 0, 0, 1, t2, 0, count};
     for (int i = 0; i < count; ++i) {
         const int rw = pdb_row_warps(bp_round4(Ns[i]), kPdbThreads, t2);
         if (rw > L.rp_stride) L.rp_stride = rw;
@@ -162,30 +202,16 @@ __host__ __device__ inline bool finish_plan(const int* Ns, int count, long long 
     for (int b = 0; b < G; ++b) {
         const int lo = w->band[b], hi = w->band[b + 1];
         while (p < count && p0 + Ns[p] <= lo) p0 += Ns[p++];
-        int brows = 0, bcols = 0, belems = 0, segs = 0, tcol = 0;
-        for (int q = p, q0 = p0; q < count && q0 < hi; q0 += Ns[q++]) {
-            const int s0 = lo > q0 ? lo : q0, s1 = hi < q0 + Ns[q] ? hi : q0 + Ns[q];
-            if (s0 >= s1) continue;
-            const int nr = s1 - s0, ldy = bp_round4(Ns[q]);
-            int ntm = 0, next = 0;
-            pdb_tmem_rows(nr, ldy, kPdbThreads, tcol, &ntm, &next, t2);
-            tcol = next;
-            brows += nr;
-            bcols += ldy;
-            belems += (nr - ntm) * ldy;
-            ++segs;
-        }
-        if (segs > kMaxSeg) return false;
-        if (brows > L.max_band_rows) L.max_band_rows = brows;
-        if (bcols > L.max_band_cols) L.max_band_cols = bcols;
-        if (belems > L.max_band_elems) L.max_band_elems = belems;
-        if (segs > L.max_segs) L.max_segs = segs;
+        const BandStat st = band_stat(Ns, count, p, p0, lo, hi, t2);
+        if (st.rows > L.max_band_rows) L.max_band_rows = st.rows;
+        if (st.cols > L.max_band_cols) L.max_band_cols = st.cols;
+        if (st.elems > L.max_band_elems) L.max_band_elems = st.elems;
+        if (st.segs > L.max_segs) L.max_segs = st.segs;
     }
-    const size_t smem = pdb_smem_bytes(L, kPdbThreads);
-    if (smem > (size_t)kPdMaxSmem) return false;
+    if (L.max_segs < 1) L.max_segs = 1;
+    if (!layout_fits(&L, &w->smem)) return false;
     w->grid = G;
     w->layout = L;
-    w->smem = (unsigned)smem;
     return true;
 }
 

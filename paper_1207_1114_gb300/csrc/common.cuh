@@ -142,17 +142,24 @@ __device__ __forceinline__ float4 quant32x4(float4 v, Quant32 a, Quant32 b, Quan
 constexpr float kBoundMargin = 1.0f + 1.0f / 1024.0f;
 
 // FP64: the quantum q = 2^(E-52) for a bound b, E = floor(log2 b), so
-// b < 2^(E+1) = 2^53 q; b <= 0 (only zeros to add) takes q = 1.
+// b < 2^(E+1) = 2^53 q; b <= 0 (only zeros to add) takes q = 1.  The
+// scales are built from the exponent bits (FP64 arithmetic is slow here).
 struct Quant64 {
     double dn, up;
 };
+__device__ __forceinline__ Quant64 quant64_from_exp(int E) {
+    E = E > 900 ? 900 : (E < -900 ? -900 : E);
+    return Quant64{__longlong_as_double((long long)(1023 + 52 - E) << 52),
+                   __longlong_as_double((long long)(1023 - 52 + E) << 52)};
+}
 __device__ __forceinline__ Quant64 quant64_for(double bound) {
     if (!(bound > 0.0)) return Quant64{1.0, 1.0};
-    int E;
-    frexp(bound, &E);   // bound = f 2^E with f in [0.5, 1)
-    E -= 1;
-    E = E > 900 ? 900 : (E < -900 ? -900 : E);
-    return Quant64{ldexp(1.0, 52 - E), ldexp(1.0, E - 52)};
+    return quant64_from_exp((int)((__double_as_longlong(bound) >> 52) & 0x7ff) - 1023);
+}
+// The same from a float bound (positive, finite).
+__device__ __forceinline__ Quant64 quant64_for_f(float bound) {
+    if (!(bound > 0.f)) return Quant64{1.0, 1.0};
+    return quant64_from_exp(((__float_as_int(bound) >> 23) & 0xff) - 127);
 }
 __device__ __forceinline__ double quant64(double v, Quant64 q) { return rint(v * q.dn) * q.up; }
 

@@ -71,6 +71,10 @@ struct Slot {
     // round16 of the row length) and their per-row scales
     uint8_t *qA, *qA2, *qXt, *qT;
     float *scA, *scA2, *scX, *scT;
+    // FP32 products on the tensor cores: TF32 parts and FP32 remainders of
+    // A, A' (once per solve), X^T (per iteration) and T (the first product's
+    // output), rows padded to multiples of 4 floats
+    float *Ahi, *Alo, *A2hi, *A2lo, *Xthi, *Xtlo, *Thi, *Tlo;
 };
 
 }  // namespace
@@ -151,13 +155,22 @@ bool params_ok(const fastpfp_params* p) {
     if (p->max_outer < 1 || p->max_inner < 1) return false;
     if (p->max_outer > kMaxOuterTrace) return false;
     if (!(p->tol_outer >= 0.0) || !(p->tol_inner >= 0.0)) return false;
-    if (p->precision != FASTPFP_FP32 && p->precision != FASTPFP_BF16 && p->precision != FASTPFP_FP8)
+    if (p->precision != FASTPFP_FP32 && p->precision != FASTPFP_BF16 && p->precision != FASTPFP_FP8 &&
+        p->precision != FASTPFP_FP32_SIMT)
         return false;
     if (p->refine_iters < 0) return false;
     if (p->loop_mode != 0 && p->loop_mode != 1) return false;
     if (p->algorithm != FASTPFP_ALG_FASTPFP && p->algorithm != FASTPFP_ALG_PG) return false;
     return true;
 }
+
+// A BF16 or FP8 phase before the FP32 iterations.
+inline bool lowp_of(const fastpfp_params* p) {
+    return p->precision == FASTPFP_BF16 || p->precision == FASTPFP_FP8;
+}
+// The FP32 phase's products on the FP32 FMA pipes instead of split TF32 on
+// the tensor cores.
+inline bool simt_of(const fastpfp_params* p) { return p->precision == FASTPFP_FP32_SIMT; }
 
 long long timeout_ns(const fastpfp_params* p) {
     const int ms = (p && p->timeout_ms > 0) ? p->timeout_ms : 2000;
@@ -223,7 +236,7 @@ inline const float* f32_operand(const float* A, int n, float* padded, int* ld) {
 int enqueue_setup(const Slot& sl, cudaStream_t s, const Problem& q, const fastpfp_params* p,
                   int ld) {
     const int ldy = round4(q.N), ldx = round4(q.m);
-    const bool lowp = p->precision != FASTPFP_FP32;   // a BF16 or FP8 phase
+    const bool lowp = lowp_of(p);   // a BF16 or FP8 phase
     FP_CUDA(cudaMemsetAsync(sl.ctrl, 0, kCtrlHeader, s));
     FP_CUDA(cudaMemsetAsync(sl.colbuf, 0, colbuf_bytes(ld), s));
     FP_CUDA(cudaMemsetAsync(sl.sbuf, 0, 3 * sizeof(double), s));
@@ -243,6 +256,15 @@ int enqueue_setup(const Slot& sl, cudaStream_t s, const Problem& q, const fastpf
     if (!rows16(q.A2, q.m))
         FP_CUDA(cudaMemcpy2DAsync(sl.A232, (size_t)round4(q.m) * 4, q.A2, (size_t)q.m * 4, (size_t)q.m * 4, q.m,
                                   cudaMemcpyDeviceToDevice, s));
+    if (!simt_of(p)) {
+        // TF32 parts and remainders of A and A' for the FP32 products
+        SplitGroup g{};
+        g.count = 2;
+        g.q[0] = SplitRows{q.A, q.N, q.N, q.N, sl.Ahi, sl.Alo, round4(q.N), 0, nullptr};
+        g.q[1] = SplitRows{q.A2, q.m, q.m, q.m, sl.A2hi, sl.A2lo, round4(q.m), 0, nullptr};
+        FP_CUDA(split_tf32_group(g, s));
+        ++nl;
+    }
     if (p->precision == FASTPFP_BF16) {
         // BF16 operand copies of A and A' for the tensor-core products
         FP_CUDA(to_bf16(q.A, q.N, q.N, q.N, sl.A16, round8(q.N), s));
@@ -299,9 +321,74 @@ int enqueue_gradient(const Slot& sl, cudaStream_t s, const Problem& q, const fas
 // quantised per row just before the product that reads them (qx, qt), A and
 // A' once at set-up, and the epilogues scale by the two operands' row scales.
 struct TcPlan {
-    std::vector<TcGroup> g1, g2;
+    std::vector<TcGroup> g1, g2;          // low-precision phase: BF16 or E4M3 products
     std::vector<QuantGroup> qx, qt;
+    std::vector<SplitGroup> sx;           // FP32 phase: X^T split, then the split-TF32 products
+    std::vector<TcGroup> f1, f2;
 };
+
+// The FP32 phase's products of problems qs[0..count) (slot slot_of[i], or
+// i) on the tensor cores, split TF32: per iteration X^T is split from the
+// blend's X, then T = A X (written as its TF32 part and remainder) and
+// Y[:, :m] = T A' + lambda K; every launch skips solves outside their FP32
+// phase.
+bool plan_split(fastpfp_t h, const Problem* qs, int count, const fastpfp_params* p, TcPlan* plan,
+                const int* slot_of = nullptr) {
+    plan->sx.clear();
+    plan->f1.clear();
+    plan->f2.clear();
+    for (int b = 0; b < count; b += kTcMaxGroup) {
+        TcGroup a{}, c{};
+        SplitGroup sx{};
+        const int n = std::min(kTcMaxGroup, count - b);
+        int nmax = 0;
+        for (int i = 0; i < n; ++i) nmax = std::max(nmax, qs[b + i].N);
+        (void)nmax;
+        const int bn = kTcSplitBN;
+        a.count = c.count = sx.count = n;
+        a.mode = kTcOutSplit;
+        c.mode = kTcOutF32;
+        a.bn = c.bn = bn;
+        a.kind = c.kind = kTcTf32x3;
+        a.phase = c.phase = 1;
+        for (int i = 0; i < n; ++i) {
+            const Problem& q = qs[b + i];
+            const Slot& sl = h->slots[slot_of ? slot_of[b + i] : b + i];
+            const int l4N = round4(q.N), l4m = round4(q.m);
+            if (!tc_make_map(&a.map_a[i], sl.Ahi, q.N, q.N, l4N, kTcTileM, kTcTf32x3) ||
+                !tc_make_map(&a.map_a_lo[i], sl.Alo, q.N, q.N, l4N, kTcTileM, kTcTf32x3) ||
+                !tc_make_map(&a.map_b[i], sl.Xthi, q.m, q.N, l4N, bn, kTcTf32x3) ||
+                !tc_make_map(&a.map_b_lo[i], sl.Xtlo, q.m, q.N, l4N, bn, kTcTf32x3) ||
+                !tc_make_map(&c.map_a[i], sl.Thi, q.N, q.m, l4m, kTcTileM, kTcTf32x3) ||
+                !tc_make_map(&c.map_a_lo[i], sl.Tlo, q.N, q.m, l4m, kTcTileM, kTcTf32x3) ||
+                !tc_make_map(&c.map_b[i], sl.A2hi, q.m, q.m, l4m, bn, kTcTf32x3) ||
+                !tc_make_map(&c.map_b_lo[i], sl.A2lo, q.m, q.m, l4m, bn, kTcTf32x3))
+                return false;
+            sx.q[i] = SplitRows{sl.X, q.N, q.m, l4m, sl.Xthi, sl.Xtlo, l4N, 1, sl.ctrl};
+            a.prob[i] = TcProblem{q.N, q.m, q.N, sl.Thi, l4m, nullptr, 0, 0.f, sl.ctrl, &sl.ctrl->error};
+            a.prob[i].out_lo = sl.Tlo;
+            c.prob[i] = TcProblem{q.N, q.m, q.m, sl.Y, l4N, q.k ? sl.K : nullptr, l4m, q.k ? (float)p->lambda : 0.f,
+                                  sl.ctrl, &sl.ctrl->error};
+            if (p->algorithm == FASTPFP_ALG_PG) {   // Y[:, :m] = X + alpha (T A' + lambda K), Eq. (pg)
+                c.prob[i].addend = sl.X;
+                c.prob[i].ld_add = l4m;
+                c.prob[i].scale = p->alpha;
+                c.prob[i].lambda *= p->alpha;
+            }
+        }
+        plan->sx.push_back(sx);
+        plan->f1.push_back(a);
+        plan->f2.push_back(c);
+    }
+    return true;
+}
+
+int enqueue_fp32(const TcPlan& plan, cudaStream_t s) {
+    for (const SplitGroup& g : plan.sx) FP_CUDA(split_tf32_group(g, s));
+    for (const TcGroup& g : plan.f1) FP_CUDA(tc_gemm(g, s));
+    for (const TcGroup& g : plan.f2) FP_CUDA(tc_gemm(g, s));
+    return (int)(plan.sx.size() + plan.f1.size() + plan.f2.size());
+}
 
 bool plan_tc(fastpfp_t h, const Problem* qs, int count, const fastpfp_params* p, TcPlan* plan,
              const int* slot_of = nullptr) {
@@ -321,7 +408,7 @@ bool plan_tc(fastpfp_t h, const Problem* qs, int count, const fastpfp_params* p,
         a.mode = kTcOutBf16;
         c.mode = kTcOutF32;
         a.bn = c.bn = bn;
-        a.fp8 = c.fp8 = fp8 ? 1 : 0;
+        a.kind = c.kind = fp8 ? kTcE4m3 : kTcBf16;
         qx.count = qt.count = fp8 ? n : 0;
         for (int i = 0; i < n; ++i) {
             const Problem& q = qs[b + i];
@@ -329,10 +416,10 @@ bool plan_tc(fastpfp_t h, const Problem* qs, int count, const fastpfp_params* p,
             const int l16N = round8(q.N), l16m = round8(q.m);
             if (fp8) {
                 const int l8N = round16(q.N), l8m = round16(q.m);
-                if (!tc_make_map(&a.map_a[i], sl.qA, q.N, q.N, l8N, kTcTileM, true) ||
-                    !tc_make_map(&a.map_b[i], sl.qXt, q.m, q.N, l8N, bn, true) ||
-                    !tc_make_map(&c.map_a[i], sl.qT, q.N, q.m, l8m, kTcTileM, true) ||
-                    !tc_make_map(&c.map_b[i], sl.qA2, q.m, q.m, l8m, bn, true))
+                if (!tc_make_map(&a.map_a[i], sl.qA, q.N, q.N, l8N, kTcTileM, kTcE4m3) ||
+                    !tc_make_map(&a.map_b[i], sl.qXt, q.m, q.N, l8N, bn, kTcE4m3) ||
+                    !tc_make_map(&c.map_a[i], sl.qT, q.N, q.m, l8m, kTcTileM, kTcE4m3) ||
+                    !tc_make_map(&c.map_b[i], sl.qA2, q.m, q.m, l8m, bn, kTcE4m3))
                     return false;
                 qx.q[i] = QuantRows{sl.Xt16, 1, q.m, q.N, l16N, sl.qXt, l8N, sl.scX, sl.ctrl};
                 qt.q[i] = QuantRows{sl.T16, 1, q.N, q.m, l16m, sl.qT, l8m, sl.scT, sl.ctrl};
@@ -494,9 +581,11 @@ int enqueue_single(fastpfp_t h, cudaStream_t s, const Slot& sl, const Problem& q
                    const fastpfp_params* p, Ctrl* host_slot) {
     const int N = q.N, m = q.m;
     const int ldy = round4(N), ldx = round4(m);
-    const bool lowp = p->precision != FASTPFP_FP32;   // a BF16 or FP8 phase
+    const bool lowp = lowp_of(p);   // a BF16 or FP8 phase
     TcPlan tc;
     if (lowp && !plan_tc(h, &q, 1, p, &tc)) return FASTPFP_ERR_UNSUPPORTED;
+    const int slot = (int)(&sl - h->slots.data());
+    if (!simt_of(p) && !plan_split(h, &q, 1, p, &tc, &slot)) return FASTPFP_ERR_UNSUPPORTED;
     int nl = enqueue_setup(sl, s, q, p, h->ld);
     if (nl < 0) return nl;
     PdLaunch L;
@@ -537,7 +626,7 @@ int enqueue_single(fastpfp_t h, cudaStream_t s, const Slot& sl, const Problem& q
             g = enqueue_tc(tc, st);
             if (g < 0) return g;
         }
-        const int g32 = enqueue_gradient(sl, st, q, p, f32_tile(h, q.N, 1));
+        const int g32 = simt_of(p) ? enqueue_gradient(sl, st, q, p, f32_tile(h, q.N, 1)) : enqueue_fp32(tc, st);
         if (g32 < 0) return g32;
         if (pt) FP_CUDA(cudaEventRecord(h->ev[2 * t + 1], st));
         FP_CUDA(pd_launch(L, P, st));
@@ -701,6 +790,7 @@ void f32_groups(fastpfp_t h, const std::vector<Problem>& qs, const std::vector<M
                 const fastpfp_params* p, std::vector<GemmF32TGroup>& ga_out, std::vector<GemmF32TGroup>& gb_out) {
     ga_out.clear();
     gb_out.clear();
+    if (!simt_of(p)) return;   // the FP32 products run on the tensor cores (plan_split)
     for (int b = 0; b < (int)mem.size(); b += kF32MaxGroup) {
         GemmF32TGroup ga{}, gb{};
         ga.count = gb.count = std::min(kF32MaxGroup, (int)mem.size() - b);
@@ -732,11 +822,12 @@ int save_trace(fastpfp_t h, cudaStream_t s, int slot, int pair, int max_outer) {
 int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, const Wave& w,
                  const fastpfp_params* p, Ctrl* host_slots) {
     int nl = 0;
-    const bool lowp = p->precision != FASTPFP_FP32;   // a BF16 or FP8 phase
+    const bool lowp = lowp_of(p);   // a BF16 or FP8 phase
     std::vector<Member> mem(w.count);
     for (int i = 0; i < w.count; ++i) mem[i] = Member{w.first + i, i};
     TcPlan tc;
     if (lowp && !plan_tc(h, &qs[w.first], w.count, p, &tc)) return FASTPFP_ERR_UNSUPPORTED;
+    if (!simt_of(p) && !plan_split(h, &qs[w.first], w.count, p, &tc)) return FASTPFP_ERR_UNSUPPORTED;
     for (int i = 0; i < w.count; ++i) {
         const int r = enqueue_setup(h->slots[i], s, qs[w.first + i], p, h->ld);
         if (r < 0) return r;
@@ -759,6 +850,9 @@ int enqueue_wave(fastpfp_t h, cudaStream_t s, const std::vector<Problem>& qs, co
             n = enqueue_tc(tc, st);
             if (n < 0) return n;
         }
+        const int f = enqueue_fp32(tc, st);   // split-TF32 FP32 products (none with SIMT)
+        if (f < 0) return f;
+        n += f;
         for (const GemmF32TGroup& g : f32a) FP_CUDA(gemm_f32t_group(g, st));   // T^T = X^T A
         for (const GemmF32TGroup& g : f32b) FP_CUDA(gemm_f32t_group(g, st));   // Y = T A' + lambda K
         n += (int)(f32a.size() + f32b.size());
@@ -855,7 +949,8 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
     auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
     struct SlotOff {
         size_t Y, X, T, K, A16, A216, Xt16, T16, col, s, d, ctrl, rm, cm, rb, cb, sA, sA2, sB, sB2, sX0,
-            sXo, sp, A32, A232, qA, qA2, qXt, qT, scA, scA2, scX, scT;
+            sXo, sp, A32, A232, qA, qA2, qXt, qT, scA, scA2, scX, scT, Ahi, Alo, A2hi, A2lo, Xthi, Xtlo, Thi,
+            Tlo;
     };
     std::vector<SlotOff> so(h->nslots);
     for (auto& o : so) {
@@ -869,6 +964,8 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
         o.A32 = take(f32mat); o.A232 = take(f32mat);
         o.qA = take(f8mat); o.qA2 = take(f8mat); o.qXt = take(f8mat); o.qT = take(f8mat);
         o.scA = take(n * 4); o.scA2 = take(n * 4); o.scX = take(n * 4); o.scT = take(n * 4);
+        o.Ahi = take(f32mat); o.Alo = take(f32mat); o.A2hi = take(f32mat); o.A2lo = take(f32mat);
+        o.Xthi = take(f32mat); o.Xtlo = take(f32mat); o.Thi = take(f32mat); o.Tlo = take(f32mat);
     }
     const size_t opairs = take(sizeof(PairDesc) * kMaxWavePairs);
     const size_t otmpl = take(sizeof(PairDesc) * (size_t)max_batch);
@@ -951,6 +1048,14 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
         sl.scX = (float*)(b + o.scX);
         sl.scT = (float*)(b + o.scT);
         sl.sperm = (int32_t*)(b + o.sp);
+        sl.Ahi = (float*)(b + o.Ahi);
+        sl.Alo = (float*)(b + o.Alo);
+        sl.A2hi = (float*)(b + o.A2hi);
+        sl.A2lo = (float*)(b + o.A2lo);
+        sl.Xthi = (float*)(b + o.Xthi);
+        sl.Xtlo = (float*)(b + o.Xtlo);
+        sl.Thi = (float*)(b + o.Thi);
+        sl.Tlo = (float*)(b + o.Tlo);
     }
     h->d_pairs = (PairDesc*)(b + opairs);
     h->d_tmpl = (PairDesc*)(b + otmpl);
@@ -1106,7 +1211,7 @@ int stage_out(fastpfp_t h, cudaStream_t s, const fastpfp_pair& x, int slot) {
 int solve_graph_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, const fastpfp_pair* pairs,
                        const fastpfp_params* p, fastpfp_stats* st, bool host) {
     const int count = (int)qs.size();
-    const bool lowp = p->precision != FASTPFP_FP32;   // a BF16 or FP8 phase
+    const bool lowp = lowp_of(p);   // a BF16 or FP8 phase
     int nl = 0;
     auto fail = [&](int code) {
         cudaStreamSynchronize(s);
@@ -1140,6 +1245,7 @@ int solve_graph_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, co
     f32_groups(h, qs, all, p, f32a, f32b);
     TcPlan tc;
     if (lowp && !plan_tc(h, qs.data(), count, p, &tc)) return fail(FASTPFP_ERR_UNSUPPORTED);
+    if (!simt_of(p) && !plan_split(h, qs.data(), count, p, &tc)) return fail(FASTPFP_ERR_UNSUPPORTED);
     Wave none;
     PdbParams P = wave_params(h, none, 0, p);
     P.dyn = 1;
@@ -1156,6 +1262,9 @@ int solve_graph_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, co
             n = enqueue_tc(tc, cs);
             if (n < 0) return n;
         }
+        const int f = enqueue_fp32(tc, cs);   // split-TF32 FP32 products (none with SIMT)
+        if (f < 0) return f;
+        n += f;
         for (const GemmF32TGroup& g : f32a) FP_CUDA(gemm_f32t_group(g, cs));   // T^T = X^T A
         for (const GemmF32TGroup& g : f32b) FP_CUDA(gemm_f32t_group(g, cs));   // Y = T A' + lambda K
         n += (int)(f32a.size() + f32b.size());
@@ -1221,7 +1330,7 @@ bool graph_streamable(fastpfp_t h, const std::vector<Problem>& qs, const fastpfp
 int solve_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, const fastpfp_pair* pairs,
                  const fastpfp_params* p, fastpfp_stats* st, bool host) {
     const int count = (int)qs.size();
-    const bool lowp = p->precision != FASTPFP_FP32;   // a BF16 or FP8 phase
+    const bool lowp = lowp_of(p);   // a BF16 or FP8 phase
     const bool prof = p->profile != 0;
     std::vector<int> free_slots;
     for (int i = h->nslots - 1; i >= 0; --i) free_slots.push_back(i);
@@ -1324,11 +1433,18 @@ int solve_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, const fa
         const PdbParams P = wave_params(h, w, n, p);
         TcPlan tc;
         if (lowp && !plan_tc(h, cand.data(), n, p, &tc, cand_slots.data())) return fail(FASTPFP_ERR_UNSUPPORTED);
+        if (!simt_of(p) && !plan_split(h, cand.data(), n, p, &tc, cand_slots.data()))
+            return fail(FASTPFP_ERR_UNSUPPORTED);
         f32_groups(h, qs, run, p, f32a, f32b);
         int kl = 0;
         if (prof && cudaEventRecord(h->ev[0], s) != cudaSuccess) return fail(FASTPFP_ERR_CUDA);
         if (lowp) {
             const int r = enqueue_tc(tc, s);
+            if (r < 0) return fail(r);
+            kl += r;
+        }
+        {
+            const int r = enqueue_fp32(tc, s);   // split-TF32 FP32 products (none with SIMT)
             if (r < 0) return fail(r);
             kl += r;
         }
@@ -1493,7 +1609,9 @@ int fastpfp_bandwidth_probe(int device, int level, int sweeps, double* gbs) {
 
 int fastpfp_gemm_probe(int device, int precision, int n, int reps, double* tflops) {
     if (!tflops || reps < 1 || reps > 1000 || n < 256 || n > 16384 || (n % 16) != 0) return FASTPFP_ERR_ARG;
-    if (precision != FASTPFP_FP32 && precision != FASTPFP_BF16 && precision != FASTPFP_FP8) return FASTPFP_ERR_ARG;
+    if (precision != FASTPFP_FP32 && precision != FASTPFP_BF16 && precision != FASTPFP_FP8 &&
+        precision != FASTPFP_FP32_SIMT)
+        return FASTPFP_ERR_ARG;
     if (cudaSetDevice(device) != cudaSuccess) return FASTPFP_ERR_CUDA;
     if (tc_configure() != cudaSuccess || gemm_f32t_configure() != cudaSuccess) return FASTPFP_ERR_CUDA;
     float ms = 0.f;
@@ -1636,11 +1754,52 @@ int fastpfp_gradient(fastpfp_t h, void* stream, const float* A, const float* X, 
     if (!h || !A || !X || !A2 || !Y || N < 1 || m < 1 || m > N || ldy < m) return FASTPFP_ERR_ARG;
     if (lambda != 0.f && !K) return FASTPFP_ERR_ARG;
     if (N > h->max_n) return FASTPFP_ERR_SIZE;
-    if (precision != FASTPFP_FP32 && precision != FASTPFP_BF16 && precision != FASTPFP_FP8)
+    if (precision != FASTPFP_FP32 && precision != FASTPFP_BF16 && precision != FASTPFP_FP8 &&
+        precision != FASTPFP_FP32_SIMT)
         return FASTPFP_ERR_ARG;
     if (cudaSetDevice(h->device) != cudaSuccess) return FASTPFP_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     const Slot& sl = h->slots[0];
+    if (precision == FASTPFP_FP32) {
+        // split-TF32 products on the tensor cores: A, A' and X^T split into
+        // TF32 parts and remainders in the slot, T written split, Y and K
+        // through the slot's padded FP32 buffers (16-byte aligned rows)
+        const int l4N = round4(N), l4m = round4(m);
+        SplitGroup g{};
+        g.count = 3;
+        g.q[0] = SplitRows{A, N, N, N, sl.Ahi, sl.Alo, l4N, 0, nullptr};
+        g.q[1] = SplitRows{A2, m, m, m, sl.A2hi, sl.A2lo, l4m, 0, nullptr};
+        g.q[2] = SplitRows{X, N, m, m, sl.Xthi, sl.Xtlo, l4N, 1, nullptr};
+        FP_CUDA(split_tf32_group(g, s));
+        if (lambda != 0.f)
+            FP_CUDA(cudaMemcpy2DAsync(sl.K, (size_t)l4m * 4, K, (size_t)m * 4, (size_t)m * 4, N,
+                                      cudaMemcpyDeviceToDevice, s));
+        TcGroup a{}, c{};
+        a.count = c.count = 1;
+        a.mode = kTcOutSplit;
+        c.mode = kTcOutF32;
+        a.kind = c.kind = kTcTf32x3;
+        a.phase = c.phase = 1;
+        const int bn = kTcSplitBN;
+        a.bn = c.bn = bn;
+        if (!tc_make_map(&a.map_a[0], sl.Ahi, N, N, l4N, kTcTileM, kTcTf32x3) ||
+            !tc_make_map(&a.map_a_lo[0], sl.Alo, N, N, l4N, kTcTileM, kTcTf32x3) ||
+            !tc_make_map(&a.map_b[0], sl.Xthi, m, N, l4N, bn, kTcTf32x3) ||
+            !tc_make_map(&a.map_b_lo[0], sl.Xtlo, m, N, l4N, bn, kTcTf32x3) ||
+            !tc_make_map(&c.map_a[0], sl.Thi, N, m, l4m, kTcTileM, kTcTf32x3) ||
+            !tc_make_map(&c.map_a_lo[0], sl.Tlo, N, m, l4m, kTcTileM, kTcTf32x3) ||
+            !tc_make_map(&c.map_b[0], sl.A2hi, m, m, l4m, bn, kTcTf32x3) ||
+            !tc_make_map(&c.map_b_lo[0], sl.A2lo, m, m, l4m, bn, kTcTf32x3))
+            return FASTPFP_ERR_UNSUPPORTED;
+        a.prob[0] = TcProblem{N, m, N, sl.Thi, l4m, nullptr, 0, 0.f, nullptr, nullptr};
+        a.prob[0].out_lo = sl.Tlo;
+        c.prob[0] = TcProblem{N, m, m, sl.Y, l4m, lambda != 0.f ? sl.K : nullptr, l4m, lambda, nullptr, nullptr};
+        FP_CUDA(tc_gemm(a, s));
+        FP_CUDA(tc_gemm(c, s));
+        FP_CUDA(cudaMemcpy2DAsync(Y, (size_t)ldy * 4, sl.Y, (size_t)l4m * 4, (size_t)m * 4, N,
+                                  cudaMemcpyDeviceToDevice, s));
+        return FASTPFP_OK;
+    }
     if (precision == FASTPFP_FP8) {
         // E4M3 copies with per-row scales: A, A' and X^T (through the BF16
         // transpose the solve's blend writes), then T between the products
@@ -1659,13 +1818,13 @@ int fastpfp_gradient(fastpfp_t h, void* stream, const float* A, const float* X, 
         a.count = c.count = 1;
         a.mode = kTcOutBf16;
         c.mode = kTcOutF32;
-        a.fp8 = c.fp8 = 1;
+        a.kind = c.kind = kTcE4m3;
         const int bn = tc_tile(h, N, 1);
         a.bn = c.bn = bn;
-        if (!tc_make_map(&a.map_a[0], sl.qA, N, N, l8N, kTcTileM, true) ||
-            !tc_make_map(&a.map_b[0], sl.qXt, m, N, l8N, bn, true) ||
-            !tc_make_map(&c.map_a[0], sl.qT, N, m, l8m, kTcTileM, true) ||
-            !tc_make_map(&c.map_b[0], sl.qA2, m, m, l8m, bn, true))
+        if (!tc_make_map(&a.map_a[0], sl.qA, N, N, l8N, kTcTileM, kTcE4m3) ||
+            !tc_make_map(&a.map_b[0], sl.qXt, m, N, l8N, bn, kTcE4m3) ||
+            !tc_make_map(&c.map_a[0], sl.qT, N, m, l8m, kTcTileM, kTcE4m3) ||
+            !tc_make_map(&c.map_b[0], sl.qA2, m, m, l8m, bn, kTcE4m3))
             return FASTPFP_ERR_UNSUPPORTED;
         a.prob[0] = TcProblem{N, m, N, sl.T16, l16m, nullptr, 0, 0.f, nullptr, nullptr, sl.scA, sl.scX};
         c.prob[0] = TcProblem{N, m, m, sl.Y, l4m, lambda != 0.f ? sl.K : nullptr, l4m, lambda, nullptr, nullptr,

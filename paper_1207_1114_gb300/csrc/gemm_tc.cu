@@ -1,12 +1,23 @@
 // gemm_tc.cu -- low-precision products of the gradient (Section 4.1) on the
 // sm_103a tensor cores: tcgen05.mma with the accumulator in tensor memory,
 // operands staged into shared memory by TMA (cp.async.bulk.tensor, 128-byte
-// swizzle).  Operands are BF16 (kind::f16, K = 16 per MMA) or E4M3
+// swizzle).  Operands are BF16 (kind::f16, K = 16 per MMA), E4M3
 // (kind::f8f6f4, K = 32 per MMA) with one scale per operand row, applied to
-// the accumulator in the epilogue.  Either way a K stage is 128 bytes per
-// row, so the shared-memory layout, the descriptors and the ring are the
-// same; only the element count per stage (64 or 128) and the instruction
-// differ.
+// the accumulator in the epilogue, or FP32 split in two (kind::tf32, K = 8
+// per MMA): every operand is stored as its TF32 part (the value rounded to
+// 10 mantissa bits, low 13 bits zero) and the FP32 remainder, and each K
+// step issues hi*hi into one FP32 accumulator and hi*lo + lo*hi into a
+// second one, added in the epilogue -- the dropped lo*lo term and the tensor
+// core's truncation of the remainders to TF32 leave about 2^-21 of each
+// product, so these are the FP32 products of the solve at tensor-core speed.
+// (Keeping the small terms apart matters: each MMA's addition into its
+// accumulator loses about 2^-26 of it on average, always downwards, which
+// over the ~3 K/8 additions of one accumulator came to 1.2e-5 of the result
+// at K = 1000; the main accumulator now takes a third of them.)  Every kind's K stage is 128 bytes per
+// row (and an MMA's K step 32 bytes), so the shared-memory layout, the
+// descriptors and the ring are the same; the element count per stage (64,
+// 128 or 32), the instruction and, for the split kind, the two operand
+// parts per stage differ.
 //
 // Both products are "TN": C[i, j] = sum_k A[i, k] * B[j, k] with A and B
 // stored K-major (row-major with the reduction index contiguous):
@@ -14,8 +25,9 @@
 //   Y = T A' + lK  A: T (N x m),         B: A' itself (m x m) -- A' is
 //                  symmetric, so its rows are the K-major columns and no
 //                  transpose is ever formed.
-// FP32 accumulation in TMEM; the epilogue writes T as BF16 for the second
-// product, or Y as FP32 with lambda K added.
+// FP32 accumulation in TMEM; the epilogue writes T as BF16 (or, for the
+// split kind, as its TF32 part and remainder) for the second product, or Y
+// as FP32 with lambda K added.
 //
 // Persistent: one CTA per SM walks the 128 x BN output tiles of every
 // problem of the group.  BN = 256 (the default) halves the shared-memory
@@ -38,24 +50,35 @@
 namespace fpfp {
 namespace {
 
-constexpr int BM = kTcTileM, STAGES = 4;
+constexpr int BM = kTcTileM;
 constexpr int kRowBytes = 128;                 // bytes of one operand row per K stage
 constexpr int kTileBytesA = BM * kRowBytes;
 constexpr int kThreads = 192;
-// Shapes that depend on the tile width BN (128 or 256) and the operand type.
-template <int BN, bool F8>
+// Shapes that depend on the tile width BN (128 or 256) and the operand kind.
+template <int BN, int KIND>
 struct TcShape {
-    static constexpr int BK = F8 ? 128 : 64;       // K elements per stage
+    static constexpr bool kSplit = KIND == kTcTf32x3;
+    static constexpr int BK = KIND == kTcE4m3 ? 128 : KIND == kTcTf32x3 ? 32 : 64;   // K elements per stage
     static constexpr int kTileBytesB = BN * kRowBytes;
-    static constexpr int kStageBytes = kTileBytesA + kTileBytesB;
-    static constexpr uint32_t kTmemCols = 2 * BN;   // two BN-column FP32 accumulators
+    static constexpr int kPartBytes = kTileBytesA + kTileBytesB;   // the A and B tiles of one part
+    // a split stage holds both parts: [A hi][B hi][A lo][B lo]
+    static constexpr int kStageBytes = kSplit ? 2 * kPartBytes : kPartBytes;
+    static constexpr int kStages = kSplit ? (BN == 256 ? 2 : 3) : 4;
+    // two tiles' accumulators (double buffering); a split tile has two, the
+    // products of the TF32 parts and the corrections
+    static constexpr uint32_t kAccCols = kSplit ? 2 * BN : BN;
+    static constexpr uint32_t kTmemCols = 2 * kAccCols;
+    static_assert(kTmemCols <= 512, "tensor memory has 512 columns");
     // Instruction descriptor: FP32 accumulate (bits 4-5), A and B types
-    // (bits 7-9, 10-12: BF16 = 1 for kind::f16, E4M3 = 0 for kind::f8f6f4),
-    // both K-major, N >> 3 (bits 17-22), M >> 4 (bits 24-28).
-    static constexpr uint32_t kIdesc = (1u << 4) | (F8 ? 0u : (1u << 7) | (1u << 10)) |
-                                       ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    // (bits 7-9, 10-12: BF16 = 1 and TF32 = 2 for kind::f16 / kind::tf32,
+    // E4M3 = 0 for kind::f8f6f4), both K-major, N >> 3 (bits 17-22),
+    // M >> 4 (bits 24-28).
+    static constexpr uint32_t kFmt = KIND == kTcBf16 ? 1u : KIND == kTcTf32x3 ? 2u : 0u;
+    static constexpr uint32_t kIdesc = (1u << 4) | (kFmt << 7) | (kFmt << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                       ((uint32_t)(BM >> 4) << 24);
 };
 constexpr long long kWaitNs = 2000ll * 1000000ll;
+static_assert(sizeof(TcGroup) <= 32000, "a TcGroup is passed as one kernel parameter (at most 32 KB)");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -112,10 +135,17 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     d |= (uint64_t)2 << 61;                     // 128-byte swizzle
     return d;
 }
-template <bool F8>
+template <int KIND>
 __device__ __forceinline__ void mma_issue(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t acc) {
-    if (F8)
+    if (KIND == kTcTf32x3)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
+    else if (KIND == kTcE4m3)
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"
@@ -151,8 +181,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 // Output tile t of the group: problem g, tile row / column, or false when
-// the solve that owns the problem is not in its BF16 phase (every role of
-// every CTA decides the same way: the flags do not change during a launch).
+// the solve that owns the problem is not running in the group's phase (its
+// low-precision phase, or its FP32 phase for the split products; every role
+// of every CTA decides the same way: the flags do not change during a
+// launch).
 template <int BN>
 __device__ __forceinline__ bool tile_of(const TcGroup& G, int t, int* g, int* m0, int* n0) {
     int p = 0;
@@ -166,22 +198,52 @@ __device__ __forceinline__ bool tile_of(const TcGroup& G, int t, int* g, int* m0
         if (ld_relaxed_i32(&pr.ctrl->done) != 0 || ld_relaxed_i32(&pr.ctrl->error) != 0 ||
             ld_relaxed_i32(&pr.ctrl->idle) != 0)
             return false;
-        if (ld_relaxed_i32(&pr.ctrl->lowp) == 0) return false;
+        if ((ld_relaxed_i32(&pr.ctrl->lowp) != 0) != (G.phase == 0)) return false;
     }
     return true;
 }
 
+// The TF32 part of an FP32 value: rounded to 10 mantissa bits (to nearest,
+// ties away from zero), low 13 bits zero.
+__device__ __forceinline__ float tf32_hi(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // Epilogue of one tile: warp `quarter` of the four epilogue warps drains TMEM
-// lanes 32 * quarter .. + 31 (tile rows) of accumulator column base `tcol`.
+// lanes 32 * quarter .. + 31 (tile rows) of accumulator column base `tcol`
+// (and adds the correction accumulator `BN` columns after it when `split`).
 template <int BN>
 __device__ __forceinline__ void drain_tile(const TcGroup& G, const TcProblem& pr, uint32_t tmem, uint32_t tcol,
-                                           int quarter, int lane, int m0, int n0) {
+                                           int quarter, int lane, int m0, int n0, bool split) {
     const int row = m0 + quarter * 32 + lane;
     const float rsc = (pr.rs && row < pr.M) ? __ldg(pr.rs + row) : 1.f;
 #pragma unroll 1
     for (int c = 0; c < BN; c += 32) {
         uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + tcol + (uint32_t)c, r);
+        const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + tcol + (uint32_t)c;
+        tmem_ld32(ta, r);
+        if (split) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t q[16];
+                tmem_ld16(ta + (uint32_t)BN + (uint32_t)(16 * h), q);
+#pragma unroll
+                for (int v = 0; v < 16; ++v)
+                    r[16 * h + v] = __float_as_uint(__uint_as_float(r[16 * h + v]) + __uint_as_float(q[v]));
+            }
+        }
         const int col = n0 + c;
         if (row >= pr.M || col >= pr.N) continue;
         const int nv = min(32, pr.N - col);
@@ -210,6 +272,25 @@ __device__ __forceinline__ void drain_tile(const TcGroup& G, const TcProblem& pr
                 }
             } else {
                 for (int v = 0; v < nv; ++v) out[v] = __float2bfloat16_rn(__uint_as_float(r[v]));
+            }
+        } else if (G.mode == kTcOutSplit) {
+            float* hi = reinterpret_cast<float*>(pr.out) + (size_t)row * pr.ldo + col;
+            float* lo = pr.out_lo + (size_t)row * pr.ldo + col;
+            if (nv == 32) {
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    const float4 x = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                                                 __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
+                    const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+                    reinterpret_cast<float4*>(hi)[v] = h;
+                    reinterpret_cast<float4*>(lo)[v] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+                }
+            } else {
+                for (int v = 0; v < nv; ++v) {
+                    const float x = __uint_as_float(r[v]), h = tf32_hi(x);
+                    hi[v] = h;
+                    lo[v] = x - h;
+                }
             }
         } else {
             float* out = reinterpret_cast<float*>(pr.out) + (size_t)row * pr.ldo + col;
@@ -245,10 +326,11 @@ __device__ __forceinline__ void drain_tile(const TcGroup& G, const TcProblem& pr
     }
 }
 
-template <int BN, bool F8>
+template <int BN, int KIND>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcGroup G) {
-    using S = TcShape<BN, F8>;
+    using S = TcShape<BN, KIND>;
     constexpr int BK = S::BK;
+    constexpr int STAGES = S::kStages;
     constexpr int kStageBytes = S::kStageBytes;
     constexpr uint32_t kTmemCols = S::kTmemCols;
     const int ntiles = G.tile0[G.count];
@@ -307,6 +389,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 mbar_expect_tx(&full[s], kStageBytes);
                 tma_load_2d(a, &G.map_a[g], kb * BK, m0, &full[s]);
                 tma_load_2d(b, &G.map_b[g], kb * BK, n0, &full[s]);
+                if (S::kSplit) {
+                    tma_load_2d(a + S::kPartBytes, &G.map_a_lo[g], kb * BK, m0, &full[s]);
+                    tma_load_2d(b + S::kPartBytes, &G.map_b_lo[g], kb * BK, n0, &full[s]);
+                }
             }
         }
     } else if (warp == 1 && lane == 0) {
@@ -319,7 +405,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             const uint32_t buf = tc & 1u, aph = (tc >> 1) & 1u;
             if (!mbar_wait(&acc_empty[buf], aph ^ 1u, abort)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t acc = tmem + buf * (uint32_t)BN;
+            const uint32_t acc = tmem + buf * S::kAccCols;
             bool ok = true;
             for (int kb = 0; kb < nk; ++kb, ++it) {
                 const int s = it % STAGES;
@@ -332,10 +418,23 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 const uint32_t a = smem_u32(tiles + s * kStageBytes);
                 const uint32_t b = a + kTileBytesA;
                 const uint64_t ad = smem_desc(a), bd = smem_desc(b);
+                if (S::kSplit) {
+                    const uint64_t adl = smem_desc(a + S::kPartBytes), bdl = smem_desc(b + S::kPartBytes);
+                    const uint32_t corr = acc + (uint32_t)BN;   // the correction accumulator
 #pragma unroll
-                for (int j = 0; j < 4; ++j)   // 32 bytes of K per MMA (16 BF16 or 32 E4M3)
-                    mma_issue<F8>(acc, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), S::kIdesc,
-                                  (kb > 0 || j > 0) ? 1u : 0u);
+                    for (int j = 0; j < 4; ++j) {   // 32 bytes of K per MMA (8 TF32)
+                        const uint64_t o = (uint64_t)(2 * j);
+                        const uint32_t first = (kb > 0 || j > 0) ? 1u : 0u;
+                        mma_issue<KIND>(corr, ad + o, bdl + o, S::kIdesc, first);   // hi * lo
+                        mma_issue<KIND>(corr, adl + o, bd + o, S::kIdesc, 1u);      // lo * hi
+                        mma_issue<KIND>(acc, ad + o, bd + o, S::kIdesc, first);     // hi * hi
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)   // 32 bytes of K per MMA (16 BF16 or 32 E4M3)
+                        mma_issue<KIND>(acc, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), S::kIdesc,
+                                        (kb > 0 || j > 0) ? 1u : 0u);
+                }
                 mma_commit(&empty[s]);
             }
             if (!ok) break;
@@ -355,7 +454,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             if (lane == 0) okl = mbar_wait(&acc_full[buf], aph, abort) ? 1 : 0;
             if (__shfl_sync(0xffffffffu, okl, 0) == 0) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            drain_tile<BN>(G, G.prob[g], tmem, buf * (uint32_t)BN, quarter, lane, m0, n0);
+            drain_tile<BN>(G, G.prob[g], tmem, buf * S::kAccCols, quarter, lane, m0, n0, S::kSplit);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) {
@@ -393,9 +492,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-size_t tc_smem_bytes(int bn) {
-    return (size_t)STAGES * (bn == 128 ? TcShape<128, false>::kStageBytes : TcShape<256, false>::kStageBytes) +
-           1024 + 256;
+template <int BN, int KIND>
+constexpr size_t tc_smem_of() {
+    return (size_t)TcShape<BN, KIND>::kStages * TcShape<BN, KIND>::kStageBytes + 1024 + 256;
+}
+
+size_t tc_smem_bytes(int bn, int kind) {
+    if (kind == kTcTf32x3) return tc_smem_of<128, kTcTf32x3>();
+    if (kind == kTcE4m3) return bn == 128 ? tc_smem_of<128, kTcE4m3>() : tc_smem_of<256, kTcE4m3>();
+    return bn == 128 ? tc_smem_of<128, kTcBf16>() : tc_smem_of<256, kTcBf16>();
 }
 
 static int g_tc_sms = 0;
@@ -405,30 +510,34 @@ cudaError_t tc_configure() {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const void* fns[4] = {(const void*)tc_gemm_kernel<256, false>, (const void*)tc_gemm_kernel<128, false>,
-                          (const void*)tc_gemm_kernel<256, true>, (const void*)tc_gemm_kernel<128, true>};
-    for (int i = 0; i < 4; ++i) {
+    const void* fns[6] = {(const void*)tc_gemm_kernel<256, kTcBf16>,   (const void*)tc_gemm_kernel<128, kTcBf16>,
+                          (const void*)tc_gemm_kernel<256, kTcE4m3>,   (const void*)tc_gemm_kernel<128, kTcE4m3>,
+                          (const void*)tc_gemm_kernel<128, kTcTf32x3>, (const void*)tc_gemm_kernel<128, kTcTf32x3>};
+    for (int i = 0; i < 6; ++i) {
         e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tc_smem_bytes((i & 1) ? 128 : 256));
+                                 (int)tc_smem_bytes((i & 1) ? 128 : 256, i / 2));
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
 // rows x cols matrix, row-major with leading dimension ld elements (BF16,
-// ld a multiple of 8; or E4M3 bytes, ld a multiple of 16), read as boxes of
-// 128 bytes along K by box_rows rows (128 for the A operand, the group's
-// tile width for B) with 128-byte swizzle.
-bool tc_make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int box_rows, bool fp8) {
+// ld a multiple of 8; E4M3 bytes, ld a multiple of 16; FP32, ld a multiple
+// of 4), read as boxes of 128 bytes along K by box_rows rows (128 for the A
+// operand, the group's tile width for B) with 128-byte swizzle.
+bool tc_make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int box_rows, int kind) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
-    const int esize = fp8 ? 1 : 2;
+    const int esize = kind == kTcE4m3 ? 1 : kind == kTcTf32x3 ? 4 : 2;
     if (!fn || ((size_t)ld * esize) % 16 != 0 || (reinterpret_cast<uintptr_t>(ptr) & 15) != 0) return false;
     if (box_rows != 128 && box_rows != 256) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * esize};
     const cuuint32_t box[2] = {(cuuint32_t)(kRowBytes / esize), (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = fn(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+    const CUtensorMapDataType dt = kind == kTcE4m3   ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                   : kind == kTcTf32x3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                       : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const CUresult r = fn(map, dt, 2,
                           const_cast<void*>(ptr), dims,
                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -438,6 +547,9 @@ bool tc_make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, 
 cudaError_t tc_gemm(const TcGroup& G0, cudaStream_t s) {
     if (G0.count <= 0) return cudaSuccess;
     TcGroup G = G0;
+    // split products keep two accumulators per tile: 128-column tiles only
+    // (their B tensor maps carry a 128-row box)
+    if (G.kind == kTcTf32x3 && G.bn != 128) return cudaErrorInvalidValue;
     const int bn = G.bn == 128 ? 128 : 256;
     G.tile0[0] = 0;
     for (int i = 0; i < G.count; ++i) {
@@ -447,15 +559,16 @@ cudaError_t tc_gemm(const TcGroup& G0, cudaStream_t s) {
     const int ntiles = G.tile0[G.count];
     if (ntiles <= 0) return cudaSuccess;
     const int grid = min(ntiles, g_tc_sms > 0 ? g_tc_sms : 148);
-    if (G.fp8) {
-        if (bn == 128)
-            tc_gemm_kernel<128, true><<<grid, kThreads, tc_smem_bytes(128), s>>>(G);
-        else
-            tc_gemm_kernel<256, true><<<grid, kThreads, tc_smem_bytes(256), s>>>(G);
+    const size_t smem = tc_smem_bytes(bn, G.kind);
+    if (G.kind == kTcTf32x3) {
+        tc_gemm_kernel<128, kTcTf32x3><<<grid, kThreads, smem, s>>>(G);
+    } else if (G.kind == kTcE4m3) {
+        if (bn == 128) tc_gemm_kernel<128, kTcE4m3><<<grid, kThreads, smem, s>>>(G);
+        else tc_gemm_kernel<256, kTcE4m3><<<grid, kThreads, smem, s>>>(G);
     } else if (bn == 128) {
-        tc_gemm_kernel<128, false><<<grid, kThreads, tc_smem_bytes(128), s>>>(G);
+        tc_gemm_kernel<128, kTcBf16><<<grid, kThreads, smem, s>>>(G);
     } else {
-        tc_gemm_kernel<256, false><<<grid, kThreads, tc_smem_bytes(256), s>>>(G);
+        tc_gemm_kernel<256, kTcBf16><<<grid, kThreads, smem, s>>>(G);
     }
     return cudaGetLastError();
 }

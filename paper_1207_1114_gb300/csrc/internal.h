@@ -217,6 +217,11 @@ cudaError_t wave_plan(StreamState* st, const PairDesc* tmpl, PairDesc* wave, int
 constexpr int kTcMaxGroup = 32;      // problems of one grouped launch (a whole wave)
 constexpr int kTcOutBf16 = 0;        // epilogue writes BF16 (T = A X)
 constexpr int kTcOutF32 = 1;         // epilogue writes FP32 + lambda K (Y = T A' + lambda K)
+constexpr int kTcOutSplit = 2;       // epilogue writes T as its TF32 part and the FP32 remainder
+// Operand kinds: BF16 (kind::f16), E4M3 with per-row scales (kind::f8f6f4),
+// or FP32 split into a TF32 part and its FP32 remainder, multiplied as
+// hi*hi + hi*lo + lo*hi (three kind::tf32 MMAs; the FP32 products).
+constexpr int kTcBf16 = 0, kTcE4m3 = 1, kTcTf32x3 = 2;
 
 // C[M x N] = A[M x K] B[N x K]^T, both operands K-major (tensor maps),
 // both BF16 or both E4M3 (the group's fp8 flag).  With rs / cs set the
@@ -239,28 +244,38 @@ struct TcProblem {
     const float* addend;
     int ld_add;
     float scale;
+    float* out_lo;        // split mode: the FP32 remainder of the output (out holds its TF32 part)
 };
 struct TcGroup {
     CUtensorMap map_a[kTcMaxGroup];
     CUtensorMap map_b[kTcMaxGroup];
+    CUtensorMap map_a_lo[kTcMaxGroup];   // kTcTf32x3: the FP32 remainders of A and B
+    CUtensorMap map_b_lo[kTcMaxGroup];
     TcProblem prob[kTcMaxGroup];
     int count;
     int mode;
-    int bn;   // output tile columns: 256 (0 reads as 256) or 128; map_b's box has bn rows
-    int fp8;  // operands E4M3 (kind::f8f6f4, 128-element K stages) instead of BF16
+    int bn;    // output tile columns: 256 (0 reads as 256) or 128; map_b's box has bn rows
+    int kind;  // kTcBf16, kTcE4m3 (128-element K stages) or kTcTf32x3 (32-element K stages)
+    int phase; // problems with ctrl run while their solve is in its low-precision phase (0) or
+               // in its FP32 phase (1)
     // filled by tc_gemm: output tiles of problems before i (tile0[count] =
     // all tiles) and tiles per row of tiles of problem i
     int tile0[kTcMaxGroup + 1];
     int ntn[kTcMaxGroup];
 };
 constexpr int kTcTileM = 128;   // output tile rows of tc_gemm (the A operand's box)
-size_t tc_smem_bytes(int bn);
+// Output tile columns of the split FP32 products (kTcTf32x3): each tile keeps
+// two FP32 accumulators in tensor memory, so only 128-column tiles fit two
+// tiles' worth (double buffering) in its 512 columns.
+constexpr int kTcSplitBN = 128;
+size_t tc_smem_bytes(int bn, int kind);
 cudaError_t tc_configure();
-// TMA map of a rows x cols operand for tc_gemm, BF16 (ld elements, a
-// multiple of 8) or E4M3 bytes (fp8; ld a multiple of 16), read in boxes of
-// 128 bytes along K by box_rows rows: kTcTileM for an A operand, the group's
-// bn for a B operand.  False if the layout does not suit TMA.
-bool tc_make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int box_rows, bool fp8 = false);
+// TMA map of a rows x cols operand for tc_gemm of operand kind `kind`: BF16
+// (ld elements, a multiple of 8), E4M3 bytes (ld a multiple of 16) or FP32
+// (either part of a split operand; ld a multiple of 4), read in boxes of 128
+// bytes along K by box_rows rows: kTcTileM for an A operand, the group's bn
+// for a B operand.  False if the layout does not suit TMA.
+bool tc_make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int box_rows, int kind = kTcBf16);
 cudaError_t tc_gemm(const TcGroup& G, cudaStream_t s);
 
 // ----------------------------------------------------------------- GEMM
@@ -378,6 +393,27 @@ cudaError_t quant_fp8_group(const QuantGroup& g, cudaStream_t s);
 
 cudaError_t transpose_to_bf16(const float* src, int r, int c, int lds, __nv_bfloat16* dst, int ldd,
                               cudaStream_t s);
+
+// The split operands of the FP32 products (kTcTf32x3): dst = src (rows x
+// cols, leading dimension lds) or its transpose, every value as its TF32
+// part in hi and FP32 remainder in lo (leading dimension ldd, pad columns
+// zero).  Up to kTcMaxGroup matrices per launch; an entry with ctrl set
+// does nothing unless that solve runs (not stopped, no error, not idle) in
+// its FP32 phase.
+struct SplitRows {
+    const float* src;
+    int rows, cols, lds;
+    float* hi;
+    float* lo;
+    int ldd;
+    int transpose;
+    const Ctrl* ctrl;
+};
+struct SplitGroup {
+    SplitRows q[kTcMaxGroup];
+    int count;
+};
+cudaError_t split_tf32_group(const SplitGroup& g, cudaStream_t s);
 
 // Caller-orientation outputs from the canonical result.
 cudaError_t write_outputs(const int32_t* row_of_col, int N, int m, int transposed, int32_t* perm_out,

@@ -122,6 +122,46 @@ __global__ void transpose_bf16_kernel(const float* src, int r, int c, int lds, _
     }
 }
 
+// The FP32 products' operands on the tensor cores: every value split into
+// its TF32 part (rounded to 10 mantissa bits, low 13 bits zero) and the FP32
+// remainder.  One 32 x 32 tile of one matrix of the group (blockIdx.z) per
+// block, through shared memory when the matrix is transposed; pad columns
+// of the destination are written as zero.  A matrix with ctrl set is split
+// only while its solve runs its FP32 phase.
+__device__ __forceinline__ void split_tf32(float x, float* hi, float* lo) {
+    const float h = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+    *hi = h;
+    *lo = x - h;
+}
+__global__ void split_tf32_kernel(const __grid_constant__ SplitGroup G) {
+    if ((int)blockIdx.z >= G.count) return;
+    const SplitRows& q = G.q[blockIdx.z];
+    if (q.ctrl) {
+        if (ld_relaxed_i32(&q.ctrl->done) != 0 || ld_relaxed_i32(&q.ctrl->error) != 0 ||
+            ld_relaxed_i32(&q.ctrl->idle) != 0 || ld_relaxed_i32(&q.ctrl->lowp) != 0)
+            return;
+    }
+    // destination extent: rows x ldd (pad columns zero)
+    const int drows = q.transpose ? q.cols : q.rows, dcols = q.transpose ? q.rows : q.cols;
+    const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
+    if (bi >= drows || bj >= q.ldd) return;
+    __shared__ float tile[32][33];
+    if (q.transpose) {
+        for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+            const int i = bj + y, j = bi + threadIdx.x;   // source row bj + y, column bi + x
+            tile[y][threadIdx.x] = (i < q.rows && j < q.cols) ? q.src[(size_t)i * q.lds + j] : 0.f;
+        }
+        __syncthreads();
+    }
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int i = bi + y, j = bj + threadIdx.x;
+        if (i >= drows || j >= q.ldd) continue;
+        float x = 0.f;
+        if (j < dcols) x = q.transpose ? tile[threadIdx.x][y] : q.src[(size_t)i * q.lds + j];
+        split_tf32(x, q.hi + (size_t)i * q.ldd + j, q.lo + (size_t)i * q.ldd + j);
+    }
+}
+
 __global__ void perm_fill_kernel(int32_t* perm, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) perm[i] = -1;
@@ -273,6 +313,17 @@ cudaError_t to_bf16(const float* src, int r, int c, int lds, __nv_bfloat16* dst,
                     cudaStream_t s) {
     const size_t total = (size_t)r * ldd;
     to_bf16_kernel<<<grid_for(total, 256), 256, 0, s>>>(src, r, c, lds, dst, ldd);
+    return cudaGetLastError();
+}
+
+cudaError_t split_tf32_group(const SplitGroup& g, cudaStream_t s) {
+    int rows = 0, cols = 0;
+    for (int i = 0; i < g.count; ++i) {
+        rows = max(rows, g.q[i].transpose ? g.q[i].cols : g.q[i].rows);
+        cols = max(cols, g.q[i].ldd);
+    }
+    if (g.count <= 0 || rows <= 0 || cols <= 0) return cudaSuccess;
+    split_tf32_kernel<<<dim3((cols + 31) / 32, (rows + 31) / 32, g.count), dim3(32, 8), 0, s>>>(g);
     return cudaGetLastError();
 }
 

@@ -133,9 +133,32 @@ cudaError_t probe_gemm(int precision, int n, int reps, cudaStream_t s, float* be
     // one product C = A B^T (TN, both K-major) of the precision under test
     TcGroup g{};
     GemmF32TGroup f{};
-    if (e == cudaSuccess && precision == FASTPFP_FP32) {
+    float *alo = nullptr, *blo = nullptr;
+    if (e == cudaSuccess && precision == FASTPFP_FP32_SIMT) {
         f.count = 1;
         f.a[0] = GemmF32TArgs{a, n, b, n, c, n, nullptr, 0, 0.f, n, n, n, nullptr};
+    } else if (e == cudaSuccess && precision == FASTPFP_FP32) {
+        // split TF32: a and b become their TF32 parts, alo / blo the remainders
+        check(cudaMalloc(&alo, nn * 4));
+        check(cudaMalloc(&blo, nn * 4));
+        if (e == cudaSuccess) {
+            SplitGroup sg{};
+            sg.count = 2;
+            sg.q[0] = SplitRows{a, n, n, n, a, alo, n, 0, nullptr};
+            sg.q[1] = SplitRows{b, n, n, n, b, blo, n, 0, nullptr};
+            check(split_tf32_group(sg, s));
+        }
+        g.count = 1;
+        g.mode = kTcOutF32;
+        g.bn = kTcSplitBN;
+        g.kind = kTcTf32x3;
+        if (e == cudaSuccess &&
+            (!tc_make_map(&g.map_a[0], a, n, n, n, kTcTileM, kTcTf32x3) ||
+             !tc_make_map(&g.map_a_lo[0], alo, n, n, n, kTcTileM, kTcTf32x3) ||
+             !tc_make_map(&g.map_b[0], b, n, n, n, kTcSplitBN, kTcTf32x3) ||
+             !tc_make_map(&g.map_b_lo[0], blo, n, n, n, kTcSplitBN, kTcTf32x3)))
+            e = cudaErrorInvalidValue;
+        g.prob[0] = TcProblem{n, n, n, c, n, nullptr, 0, 0.f, nullptr, nullptr};
     } else if (e == cudaSuccess) {
         const bool fp8 = precision == FASTPFP_FP8;
         if (fp8) {
@@ -151,14 +174,14 @@ cudaError_t probe_gemm(int precision, int n, int reps, cudaStream_t s, float* be
         g.count = 1;
         g.mode = kTcOutF32;
         g.bn = 256;
-        g.fp8 = fp8 ? 1 : 0;
-        if (!tc_make_map(&g.map_a[0], a16, n, n, n, kTcTileM, fp8) ||
-            !tc_make_map(&g.map_b[0], b16, n, n, n, 256, fp8))
+        g.kind = fp8 ? kTcE4m3 : kTcBf16;
+        if (!tc_make_map(&g.map_a[0], a16, n, n, n, kTcTileM, g.kind) ||
+            !tc_make_map(&g.map_b[0], b16, n, n, n, 256, g.kind))
             e = cudaErrorInvalidValue;
         g.prob[0] = TcProblem{n, n, n, c, n, nullptr, 0, 0.f, nullptr, nullptr, fp8 ? sa : nullptr,
                               fp8 ? sb : nullptr};
     }
-    auto launch = [&]() { return precision == FASTPFP_FP32 ? gemm_f32t_group(f, s) : tc_gemm(g, s); };
+    auto launch = [&]() { return precision == FASTPFP_FP32_SIMT ? gemm_f32t_group(f, s) : tc_gemm(g, s); };
     if (e == cudaSuccess) check(launch());   // warm-up
     *best_ms = 0.f;
     for (int r = 0; r < reps && e == cudaSuccess; ++r) {
@@ -173,6 +196,8 @@ cudaError_t probe_gemm(int precision, int n, int reps, cudaStream_t s, float* be
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(a); cudaFree(b); cudaFree(c); cudaFree(a16); cudaFree(b16); cudaFree(sa); cudaFree(sb);
+    if (alo) cudaFree(alo);
+    if (blo) cudaFree(blo);
     return e;
 }
 

@@ -227,14 +227,10 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
                 const int q = tid + k * nthr;
                 if (q < Q) {
                     float4 v = cpart[k];
-                    if (one) {
-                        const Quant32 a = quant32_for(cb);
-                        v = quant32x4(v, a, a, a, a);
-                    } else {
-                        const float m = kBoundMargin * Nf;
-                        v = quant32x4(v, quant32_for(fmaf(cN[k].x, m, cb)), quant32_for(fmaf(cN[k].y, m, cb)),
-                                      quant32_for(fmaf(cN[k].z, m, cb)), quant32_for(fmaf(cN[k].w, m, cb)));
-                    }
+                    // one quantum for the quad, from the largest of its bounds
+                    const float cm = fmaxf(fmaxf(cN[k].x, cN[k].y), fmaxf(cN[k].z, cN[k].w));
+                    const Quant32 a = quant32_for(one ? cb : fmaf(cm, kBoundMargin * Nf, cb));
+                    v = quant32x4(v, a, a, a, a);
                     red_add_v4(ccur + 4 * q, v.x, v.y, v.z, v.w);
                 }
             }
@@ -272,19 +268,19 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
                 // sum is at most 4 N max|y| + 1 (input, row offsets and column
                 // offset of P1 each at most N max|y| per column); after a round
                 // column j's at most c_j + 1 + s/N, the total at most 2 s + N
-                const double mg = (double)kBoundMargin, Nd = (double)N;
-                double sb;
+                const float mg = kBoundMargin, Nf = (float)N, sf = (float)s;
+                float sb;
                 if (u == 0) {
-                    const double b1 = (4.0 * Nd * (double)ymax + 1.0) * mg;
+                    const float b1 = fmaf(4.0f * Nf, ymax, 1.0f) * mg;
                     S.ictl[2] = 1;
-                    S.fctl[1] = (float)b1;
-                    sb = b1 * Nd * mg;
+                    S.fctl[1] = b1;
+                    sb = b1 * Nf * mg;
                 } else {
                     S.ictl[2] = 0;
-                    S.fctl[1] = (float)((1.0 + s * invN_d) * mg);
-                    sb = (2.0 * s + Nd) * mg * mg;
+                    S.fctl[1] = fmaf(sf, invN, 1.0f) * mg;
+                    sb = fmaf(2.0f, sf, Nf) * (mg * mg);
                 }
-                const Quant64 qs = quant64_for(sb);
+                const Quant64 qs = quant64_for_f(sb);
                 S.qd[0] = qs.dn;
                 S.qd[1] = qs.up;
             }

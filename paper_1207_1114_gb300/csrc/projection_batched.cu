@@ -636,26 +636,30 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             if (UPDATE && in_grp) {
                 // the pass's output is >= 0, so column j's new sum is at most
                 // c_j + 1 + s/N (previous round's c_j, s) or, after the input
-                // round, the pair's bound cb (set in wait_post)
-                const float4* cNq = reinterpret_cast<const float4*>(S.cN + sg.coff);
-                auto qz = [&](float4 v, int q) {
-                    if (pr.bmode) {
-                        const Quant32 u = quant32_for(pr.cb);
-                        return quant32x4(v, u, u, u, u);
+                // round, the pair's bound cb (set in wait_post); one quantum
+                // serves the thread's columns, from the largest of their bounds
+                float bnd = pr.cb;
+                if (!pr.bmode) {
+                    const float4* cNq = reinterpret_cast<const float4*>(S.cN + sg.coff);
+                    float cm = 0.f;
+                    if (mp.q0 < Q) {
+                        const float4 c = cNq[mp.q0];
+                        cm = fmaxf(fmaxf(c.x, c.y), fmaxf(c.z, c.w));
                     }
-                    const float4 c = cNq[q];
-                    return quant32x4(v, quant32_for(fmaf(c.x, kBoundMargin, pr.cb)),
-                                     quant32_for(fmaf(c.y, kBoundMargin, pr.cb)),
-                                     quant32_for(fmaf(c.z, kBoundMargin, pr.cb)),
-                                     quant32_for(fmaf(c.w, kBoundMargin, pr.cb)));
-                };
+                    if (mp.kq > 1 && mp.q0 + mp.QP < Q) {
+                        const float4 c = cNq[mp.q0 + mp.QP];
+                        cm = fmaxf(cm, fmaxf(fmaxf(c.x, c.y), fmaxf(c.z, c.w)));
+                    }
+                    bnd = fmaf(cm, kBoundMargin, pr.cb);
+                }
+                const Quant32 u = quant32_for(bnd);
                 float* acc = pr.colbuf + (size_t)cur * pr.ldy;
                 if (mp.q0 < Q) {
-                    cp0 = qz(cp0, mp.q0);
+                    cp0 = quant32x4(cp0, u, u, u, u);
                     red_add_v4(acc + 4 * mp.q0, cp0.x, cp0.y, cp0.z, cp0.w);
                 }
                 if (mp.kq > 1 && mp.q0 + mp.QP < Q) {
-                    cp1 = qz(cp1, mp.q0 + mp.QP);
+                    cp1 = quant32x4(cp1, u, u, u, u);
                     red_add_v4(acc + 4 * (mp.q0 + mp.QP), cp1.x, cp1.y, cp1.z, cp1.w);
                 }
             } else if (in_grp) {
@@ -803,16 +807,17 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 // input, the row offsets and the column offset of P1 are each
                 // at most N max|y| per column); after a round, column j's at
                 // most c_j + 1 + s/N and the total at most 2 s + N
-                const double mg = (double)kBoundMargin;
+                // (FP32 bounds: the margin covers their rounding)
+                const float mg = kBoundMargin, Nf = (float)pr.N, sf = (float)s;
                 if (u == 0) {
-                    const double b1 = (4.0 * (double)pr.N * (double)pr.ymax + 1.0) * mg;
+                    const float b1 = fmaf(4.0f * Nf, pr.ymax, 1.0f) * mg;
                     pr.bmode = 1;
-                    pr.cb = (float)b1;
-                    pr.sq = quant64_for(b1 * (double)pr.N * mg);
+                    pr.cb = b1;
+                    pr.sq = quant64_for_f(b1 * Nf * mg);
                 } else {
                     pr.bmode = 0;
-                    pr.cb = (float)((1.0 + s * invN) * mg);
-                    pr.sq = quant64_for((2.0 * s + (double)pr.N) * mg * mg);
+                    pr.cb = fmaf(sf, (float)invN, 1.0f) * mg;
+                    pr.sq = quant64_for_f(fmaf(2.0f, sf, Nf) * (mg * mg));
                 }
                 if (check_stop && ((double)dd < P.tol_inner || u >= P.max_inner)) {
                     ps |= 2;

@@ -28,6 +28,10 @@ struct PlanShared {
     int best;                      // smallest candidate index whose cut fits
     long long lo, hi;              // search interval of the band cost bound
     int Gmax, t2, ok;
+    int G;                         // bands of the cut being finished
+    int pre[kMaxWavePairs + 2];    // prefix sums of Ns: pair p holds rows [pre[p], pre[p + 1])
+    int mx[4];                     // maxima over the bands: rows, columns, shared-memory floats, segments
+    int rp;                        // the most row-partial slots a pair needs
     WavePlan plan;                 // the last plan that fit
     WavePlan trial;
 };
@@ -37,7 +41,8 @@ struct PlanShared {
 // bounds spread over the interval; the interval shrinks to the step between
 // the last bound that did not fit and the first that did.  Block-wide.
 __device__ long long search_bound(PlanShared& S, const int* Ns, int n, long long seg_cost, int Gmax) {
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tid = threadIdx.x;
+    constexpr int nthr = kPlanThreads;   // the launch's block size (a power of two: shifts, not divisions)
     if (tid == 0) cut_interval(Ns, n, seg_cost, &S.lo, &S.hi);
     __syncthreads();
     while (true) {
@@ -59,8 +64,53 @@ __device__ long long search_bound(PlanShared& S, const int* Ns, int n, long long
     return S.lo;
 }
 
-// plan_bands_seq of band_plan.cuh with the bound search spread over the
-// block; the result (into *w) is the same.  Block-wide; returns S.ok.
+// finish_plan of band_plan.cuh with the bands' statistics spread over the
+// block (one band per thread; the maxima are order-free, so the layout is
+// the same).  Block-wide; returns S.ok.
+__device__ bool finish_plan_par(PlanShared& S, const int* Ns, int n, long long C, long long seg_cost, int Gmax,
+                                int t2, WavePlan* w) {
+    const int tid = threadIdx.x;
+    constexpr int nthr = kPlanThreads;
+    if (tid == 0) {
+        S.pre[0] = 0;
+        for (int i = 0; i < n; ++i) S.pre[i + 1] = S.pre[i] + Ns[i];
+        const int used = cut_rows(Ns, n, C, seg_cost, Gmax, w->band);
+        for (int c = used; c <= Gmax; ++c) w->band[c] = S.pre[n];
+        S.G = used > 1 ? used : 1;
+        S.mx[0] = S.mx[1] = S.mx[2] = S.mx[3] = 0;
+        S.rp = 1;
+    }
+    __syncthreads();
+    for (int b = tid; b < S.G; b += nthr) {
+        const int lo = w->band[b], hi = w->band[b + 1];
+        int a = 0, z = n - 1;   // the first pair whose rows end after lo
+        while (a < z) {
+            const int mid = (a + z) >> 1;
+            if (S.pre[mid + 1] > lo) z = mid; else a = mid + 1;
+        }
+        const BandStat st = band_stat(Ns, n, a, S.pre[a], lo, hi, t2);
+        atomicMax(&S.mx[0], st.rows);
+        atomicMax(&S.mx[1], st.cols);
+        atomicMax(&S.mx[2], st.elems);
+        atomicMax(&S.mx[3], st.segs);
+    }
+    for (int i = tid; i < n; i += nthr) atomicMax(&S.rp, pdb_row_warps(bp_round4(Ns[i]), kPdbThreads, t2));
+    __syncthreads();
+    if (tid == 0) {
+        PdbLayout L{S.mx[0], S.mx[1], S.mx[2], S.rp, t2, S.mx[3] > 1 ? S.mx[3] : 1, n};
+        S.ok = layout_fits(&L, &w->smem) ? 1 : 0;
+        if (S.ok) {
+            w->grid = S.G;
+            w->layout = L;
+        }
+    }
+    __syncthreads();
+    return S.ok != 0;
+}
+
+// plan_bands_seq of band_plan.cuh with the bound search and the bands'
+// statistics spread over the block; the result (into *w) is the same.
+// Block-wide; returns S.ok.
 __device__ bool plan_bands_par(PlanShared& S, const int* Ns, int n, int num_sms, int max_level, WavePlan* w) {
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -71,9 +121,7 @@ __device__ bool plan_bands_par(PlanShared& S, const int* Ns, int n, int num_sms,
     for (int lv = 0; lv <= max_level && lv < 4; ++lv) {
         const long long seg_cost = seg_cost_of_level(lv);
         const long long C = search_bound(S, Ns, n, seg_cost, S.Gmax);
-        if (tid == 0) S.ok = finish_plan(Ns, n, C, seg_cost, S.Gmax, S.t2, w) ? 1 : 0;
-        __syncthreads();
-        if (S.ok) break;
+        if (finish_plan_par(S, Ns, n, C, seg_cost, S.Gmax, S.t2, w)) break;
     }
     return S.ok != 0;
 }

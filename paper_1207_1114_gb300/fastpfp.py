@@ -23,7 +23,7 @@ FASTPFP_ERR_CUDA = -3
 FASTPFP_ERR_TIMEOUT = -4
 FASTPFP_ERR_NONFINITE = -5
 FASTPFP_ERR_UNSUPPORTED = -6
-FP32, BF16, FP8 = 0, 1, 2
+FP32, BF16, FP8, FP32_SIMT = 0, 1, 2, 3
 ALG_FASTPFP, ALG_PG = 0, 1
 
 # Every symbol include/fastpfp.h declares.
@@ -127,8 +127,8 @@ def bandwidth_probe(level: int, sweeps: int = 200, device: int = 0) -> float:
 
 
 def gemm_probe(precision: int, n: int = 4096, reps: int = 10, device: int = 0) -> float:
-    """TFLOP/s of one n^3 product on the solver's FP32, BF16 or FP8 kernel
-    (fastpfp_gemm_probe)."""
+    """TFLOP/s of one n^3 product on the solver's FP32 (split TF32 on the
+    tensor cores), BF16, FP8 or FP32_SIMT kernel (fastpfp_gemm_probe)."""
     out = C.c_double(0.0)
     _check(lib().fastpfp_gemm_probe(int(device), int(precision), int(n), int(reps), C.byref(out)),
            "fastpfp_gemm_probe")

@@ -182,3 +182,55 @@ def e1_pair(n: int, case: str, seed: int = 0) -> GraphPair:
     gt = np.full(n, -1, dtype=np.int32)
     gt[keep] = label
     return GraphPair(A, A2p, np.zeros((n, 0), np.float32), np.zeros((m, 0), np.float32), gt, 0.0)
+
+
+def graph_pair_torch(n: int, *, p: float, sigma: float, k: int, attr_sigma: float, n_out: int,
+                     generator, device):
+    """graph_pair's recipe drawn with torch on `device` (for the learned warm
+    start's training pairs, which are generated, solved and consumed on the
+    GPU in chunks; never compared with the oracle).  Returns float32 tensors
+    (A, A2, B, B2) and the int32 ground truth gt."""
+    import torch
+    kw = dict(generator=generator, device=device)
+
+    def rgraph(m, pp):
+        up = torch.triu((torch.rand((m, m), **kw) < pp).float() * torch.rand((m, m), **kw), 1)
+        return up + up.T
+
+    A = rgraph(n, p)
+    noise = torch.triu(torch.randn((n, n), **kw) * sigma, 1)
+    noise = (noise + noise.T) * (A != 0)
+    n2 = n + n_out
+    M = torch.zeros((n2, n2), device=device)
+    M[:n, :n] = A + noise
+    if n_out > 0:
+        O = rgraph(n2, p)
+        M[n:, :] = O[n:, :]
+        M[:, n:] = O[:, n:]
+    perm2 = torch.randperm(n2, **kw)
+    A2 = torch.zeros((n2, n2), device=device)
+    A2[perm2[:, None], perm2[None, :]] = M
+    B = torch.randn((n, k), **kw)
+    MB = torch.empty((n2, k), device=device)
+    MB[:n] = B + torch.randn((n, k), **kw) * attr_sigma
+    if n_out > 0:
+        MB[n:] = torch.randn((n_out, k), **kw)
+    B2 = torch.empty((n2, k), device=device)
+    B2[perm2] = MB
+    return A.contiguous(), A2.contiguous(), B.contiguous(), B2.contiguous(), perm2[:n].to(torch.int32)
+
+
+def warm_start_train_torch(count: int, seed: int, device, n_lo: int = 200, n_hi: int = 800):
+    """Yields the `count` training pairs of the learned warm start (shaped like
+    warm_start_train: n ~ U{n_lo..n_hi} inliers plus up to n/5 outliers,
+    p = 0.1, sigma = 0.03, 15-dim attributes), drawn on `device` one at a
+    time from a seeded torch generator."""
+    import torch
+    rng = np.random.default_rng(seed)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    for _ in range(count):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        n_out = int(rng.integers(0, n // 5 + 1))
+        yield graph_pair_torch(n, p=0.1, sigma=0.03, k=15, attr_sigma=0.05, n_out=n_out,
+                               generator=gen, device=device)

@@ -65,8 +65,8 @@ int main(void) {
   printf("%zu %zu %zu\n", sizeof(fastpfp_params), sizeof(fastpfp_stats), sizeof(fastpfp_pair));
   printf("%zu %zu %zu\n", offsetof(fastpfp_stats, wave_pairs), offsetof(fastpfp_stats, ms_disc),
          offsetof(fastpfp_stats, host_syncs));
-  printf("%d %d %d %d %d %d %d\n", FASTPFP_FP32, FASTPFP_BF16, FASTPFP_FP8, FASTPFP_ALG_FASTPFP,
-         FASTPFP_ALG_PG, FASTPFP_TUNE_SIZES, FASTPFP_TUNE_COUNTS);
+  printf("%d %d %d %d %d %d %d %d\n", FASTPFP_FP32, FASTPFP_BF16, FASTPFP_FP8, FASTPFP_FP32_SIMT,
+         FASTPFP_ALG_FASTPFP, FASTPFP_ALG_PG, FASTPFP_TUNE_SIZES, FASTPFP_TUNE_COUNTS);
   return 0;
 }'''
     import tempfile
@@ -83,4 +83,5 @@ int main(void) {
     assert offs == [F.fastpfp_stats.wave_pairs.offset, F.fastpfp_stats.ms_disc.offset,
                     F.fastpfp_stats.host_syncs.offset]
     consts = [int(x) for x in lines[2].split()]
-    assert consts == [F.FP32, F.BF16, F.FP8, F.ALG_FASTPFP, F.ALG_PG, F.TUNE_SIZES, F.TUNE_COUNTS]
+    assert consts == [F.FP32, F.BF16, F.FP8, F.FP32_SIMT, F.ALG_FASTPFP, F.ALG_PG, F.TUNE_SIZES,
+                      F.TUNE_COUNTS]

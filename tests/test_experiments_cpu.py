@@ -49,3 +49,25 @@ def test_lipschitz_step_of_a_complete_graph():
     n = 30
     A = np.ones((n, n)) - np.eye(n)
     assert lipschitz_step(A, A) == pytest.approx(1.0 / (n - 1) ** 2, rel=1e-9)
+
+
+def test_torch_training_pairs_follow_the_recipe():
+    """The learned warm start's training pairs drawn with torch (on the CPU
+    here): symmetric zero-diagonal graphs, graph 2 a relabelled noisy copy of
+    graph 1 plus outliers, attributes copied with small noise; seeded, so the
+    same seed gives the same pairs."""
+    torch = pytest.importorskip("torch")
+    a = list(synth.warm_start_train_torch(3, seed=4, device="cpu", n_lo=20, n_hi=40))
+    b = list(synth.warm_start_train_torch(3, seed=4, device="cpu", n_lo=20, n_hi=40))
+    for (A, A2, B, B2, gt), (A_, _, _, _, gt_) in zip(a, b):
+        assert torch.equal(A, A_) and torch.equal(gt, gt_)
+        n, n2 = A.shape[0], A2.shape[0]
+        assert 20 <= n <= 40 and n <= n2 <= n + n // 5 and B.shape == (n, 15) and B2.shape == (n2, 15)
+        for M in (A, A2):
+            assert torch.equal(M, M.T) and (M.diagonal() == 0).all()
+        g = gt.long()
+        assert len(set(g.tolist())) == n and int(g.max()) < n2
+        back = A2[g][:, g]
+        assert ((back != 0) == (A != 0)).all()                 # noise only on existing edges
+        assert float((back - A).abs().max()) < 0.3               # sigma = 0.03
+        assert float((B2[g] - B).abs().max()) < 0.5              # attr sigma = 0.05

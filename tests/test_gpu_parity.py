@@ -54,18 +54,36 @@ def test_affinity_matches_oracle(solver, N, m, k):
     assert (np.abs(K - ref) <= 1e-6 * bound + 1e-30).all()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp32_simt"])
 @pytest.mark.parametrize("N,m", [(1, 1), (5, 3), (129, 100), (300, 300), (1200, 1000)])
-def test_gradient_matches_oracle(solver, N, m):
+def test_gradient_matches_oracle(solver, N, m, precision):
+    """The FP32 products, on the tensor cores (split TF32) and on the FMA
+    pipes, against the oracle.
+
+    FMA pipes: round-to-nearest FP32 sums, well inside 1e-5 * |A||X||A'|.
+    Split TF32: each product term loses at most 3 * 2^-22 of itself (the
+    dropped lo*lo and the remainders read as TF32), and each tcgen05.mma's
+    addition into its FP32 accumulator may drop up to one unit in the last
+    place of the running sum (2^-23 of it, at most the bound) -- one such
+    addition per 8 terms of K, ceil(N / 8) in A*X and ceil(m / 8) in T*A'.
+    The correction terms accumulate apart (2^-11 smaller), so
+    |err| <= ((ceil(N/8) + ceil(m/8)) * 2^-23 + 6 * 2^-22 + 2^-23) * bound."""
     rng = np.random.default_rng(N * 3 + m)
     A = synth.random_graph(rng, N, 0.2).astype(np.float32)
     A2 = synth.random_graph(rng, m, 0.2).astype(np.float32)
     X = rng.random((N, m)).astype(np.float32)
     K = rng.normal(size=(N, m)).astype(np.float32)
     lam = 0.7
-    G = solver.gradient(cu(A), cu(X), cu(A2), cu(K), lam).cpu().numpy()
+    prec = F.FP32 if precision == "fp32" else F.FP32_SIMT
+    G = solver.gradient(cu(A), cu(X), cu(A2), cu(K), lam, precision=prec).cpu().numpy()
     ref = oracle.gradient(A, X, A2, K, lam)
     bound = np.abs(A) @ np.abs(X).astype(np.float64) @ np.abs(A2) + lam * np.abs(K)
-    assert (np.abs(G - ref) <= 1e-5 * bound + 1e-30).all()
+    if precision == "fp32":
+        tol = (-(-N // 8) - (-m // 8)) * 2.0**-23 + 6 * 2.0**-22 + 2.0**-23
+    else:
+        tol = 1e-5
+    err = np.abs(G - ref) / (bound + 1e-30)
+    assert err.max() <= tol, (err.max(), tol, float(np.mean((G - ref) / (bound + 1e-30))))
 
 
 def _bf16(a):
@@ -570,16 +588,19 @@ def test_gradient_tiles_give_identical_products(solver, N, m):
     args = (cu(A), cu(X), cu(A2), cu(K), lam)
     try:
         assert solver.get_tiles(N, 1) == (128, 256)
-        g128 = solver.gradient(*args).cpu().numpy()
+        g128 = solver.gradient(*args, precision=F.FP32_SIMT).cpu().numpy()
         t256 = solver.gradient(*args, precision=F.BF16).cpu().numpy()
+        s256 = solver.gradient(*args).cpu().numpy()
         solver.set_tiles(64, 128, n=N, count=1)
         assert solver.get_tiles(N, 1) == (64, 128)
-        g64 = solver.gradient(*args).cpu().numpy()
+        g64 = solver.gradient(*args, precision=F.FP32_SIMT).cpu().numpy()
         t128 = solver.gradient(*args, precision=F.BF16).cpu().numpy()
+        s128 = solver.gradient(*args).cpu().numpy()
     finally:
         solver.set_tiles(128, 256)
     np.testing.assert_array_equal(g64, g128)
     assert (np.abs(t128 - t256) <= 1e-6 * bound + 1e-30).all()
+    assert (np.abs(s128 - s256) <= 1e-6 * bound + 1e-30).all()
     ref16 = oracle.gradient(_bf16(A), _bf16(X), _bf16(A2), K, lam)
     assert (np.abs(t128 - ref16) <= 3e-3 * bound + 1e-30).all()
 
@@ -714,11 +735,13 @@ def test_gemm_probe_orders_the_product_kernels():
     """The GEMM throughput probe behind the bench's product fractions: every
     kernel does real work (FP32 well above 1 TFLOP/s), the tensor cores beat
     the SIMT kernel, and nothing exceeds its nominal dense peak (FP32 80.5,
-    BF16 2250, FP8 4500 TFLOP/s)."""
-    f32 = F.gemm_probe(F.FP32, n=2048, reps=3)
+    split TF32 375, BF16 2250, FP8 4500 TFLOP/s)."""
+    f32 = F.gemm_probe(F.FP32_SIMT, n=2048, reps=3)
+    tf32 = F.gemm_probe(F.FP32, n=2048, reps=3)
     bf16 = F.gemm_probe(F.BF16, n=2048, reps=3)
     fp8 = F.gemm_probe(F.FP8, n=2048, reps=3)
     assert 1.0 < f32 < 80.5
+    assert f32 < tf32 < 1125.0 / 3      # three TF32 MMAs per product term, TF32 at half the BF16 rate
     assert f32 < bf16 < 2250.0
     assert 1.0 < fp8 < 4500.0
     with pytest.raises(F.FastPFPError):

@@ -299,3 +299,24 @@ def test_graph_streamed_bf16_batch_of_uneven_pairs(solver):
         _same_bits(a, b)
         assert a.stats.status == 0 and a.stats.lowp_iters >= 1
         assert abs(a.stats.objective - c.stats.objective) <= 1e-4 * abs(c.stats.objective)
+
+
+def test_fp32_products_on_tensor_cores_match_the_simt_solve(solver):
+    """The FP32 solve with its products on the tensor cores (split TF32)
+    and on the FMA pipes: the same permutation, iteration counts within one
+    and X within 1e-5 when the counts agree; each against the oracle's
+    replay of its own counts."""
+    g = synth.attributed_1000(seed=3)
+    args = dev_pair(g)
+    outs = {}
+    for prec in (F.FP32, F.FP32_SIMT):
+        r = solver.match(*args, params=F.default_params(lam=1.0, precision=prec), want_X=True)
+        inner, _ = solver.last_trace()
+        ref = oracle.solve(g.A, g.A2, g.B, g.B2, lam=1.0, replay_inner=inner, replay_outer=r.stats.outer_iters)
+        assert r.stats.status == 0 and np.abs(r.X.cpu().numpy() - ref["X"]).max() <= 1e-4
+        outs[prec] = r
+    a, b = outs[F.FP32], outs[F.FP32_SIMT]
+    np.testing.assert_array_equal(a.perm.cpu().numpy(), b.perm.cpu().numpy())
+    assert abs(a.stats.outer_iters - b.stats.outer_iters) <= 1 and a.stats.lowp_iters == 0
+    if a.stats.outer_iters == b.stats.outer_iters:
+        assert (a.X - b.X).abs().max().item() <= 1e-5
