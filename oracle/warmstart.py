@@ -16,8 +16,12 @@ more nodes on the rows).  Only tests/ may import this module.
             zscore over the graph's nodes with the population std + 1e-6
   MLP       H = relu(F W1 + b1) (128), E = H W2 + b2 (64), shared weights
   S         E_big E_small^T / 8
-  X(0)      K = exp(S - max S), then `iters` times: rows / row sums, columns /
-            column sums
+  X(0)      K = max(exp(S - rowmax S), 2^-100), then `iters` times: rows /
+            row sums, columns / column sums, each result floored at 2^-100
+            (shifting each row by its own maximum is the same start as one
+            global shift once rows are normalised; the floor keeps every row
+            and column positive when a trained S is so peaked that whole
+            columns would underflow -- it moves no entry above 2^-100)
   loss      t(j) = row matched to column j;
             L = -(1/m) sum_j [S[t(j),j] - logsumexp_i S[i,j]]
                 -(1/m) sum_j [S[t(j),j] - logsumexp_j' S[t(j),j']]
@@ -85,11 +89,14 @@ def similarity(E, E2):
     return E @ E2.T / 8.0
 
 
+FLOOR = 2.0 ** -100
+
+
 def sinkhorn(S, iters=20):
-    K = np.exp(S - S.max())
+    K = np.maximum(np.exp(S - S.max(axis=1, keepdims=True)), FLOOR)
     for _ in range(iters):
-        K = K / K.sum(axis=1, keepdims=True)
-        K = K / K.sum(axis=0, keepdims=True)
+        K = np.maximum(K / K.sum(axis=1, keepdims=True), FLOOR)
+        K = np.maximum(K / K.sum(axis=0, keepdims=True), FLOOR)
     return K
 
 

@@ -59,46 +59,58 @@ __host__ __device__ inline size_t pdb_smem_bytes(const PdbLayout& L, int nthr) {
 }
 
 // Greedy cut of the concatenated rows of pairs with row counts Ns[0..count)
-// into consecutive bands of cost at most C: each band takes as many rows as
-// fit.  Writes the boundaries to band[0..] (when band != nullptr) and returns
-// the number of bands, or max_bands + 1 as soon as more would be needed.  For
-// a cost that only grows as rows are added, the greedy uses the fewest bands,
-// and the count never grows with C.
+// into consecutive bands of cost at most C: row by row, a row joins the open
+// band while the band's cost stays within C (a row of pair i costs its row
+// length, plus the segment cost when the band holds no row of pair i yet),
+// else it opens the next band (alone when even that exceeds C).  Writes the
+// boundaries to band[0..] (when band != nullptr) and returns the number of
+// bands, or max_bands + 1 as soon as more would be needed.  For a cost that
+// only grows as rows are added, the greedy uses the fewest bands, and the
+// count never grows with C.
+//
+// Within one pair every fresh band takes the same number of rows, so the
+// cut is taken a pair at a time: the rows that still fit in the open band,
+// then whole fresh bands of that many rows, the last one left open -- O(count)
+// steps to count the bands (the bound search runs this for hundreds of
+// candidate bounds), O(bands) more to write their boundaries.
+__host__ __device__ inline long long bp_div(long long a, long long b) {
+    return a <= 0x7fffffffll ? (long long)((unsigned)a / (unsigned)b) : a / b;   // 32-bit division when it fits
+}
 __host__ __device__ inline int cut_rows(const int* Ns, int count, long long C, long long seg_cost, int max_bands,
                                         int* band) {
-    int b = 0, gr = 0, rows_in = 0, last = -1;
-    long long cur = 0;
+    int b = 0, gr = 0, rows_in = 0;   // the open band b, the rows before it or in it, its rows
+    long long cur = 0;                // the open band's cost
     if (band) band[0] = 0;
+    const long long room = C - seg_cost;   // a fresh band's budget for its rows of one pair
     for (int i = 0; i < count; ++i) {
         const int N = Ns[i];
+        if (N <= 0) continue;
         const long long ldy = bp_round4(N);
         int r = 0;
-        while (r < N) {
-            const long long seg = last != i ? seg_cost : 0;
-            const long long avail = C - cur - seg;
-            long long k = 0;
-            if (avail >= ldy) {   // 32-bit division when the values fit (the device planner's common case)
-                const long long fit = avail <= 0x7fffffffll ? (long long)((unsigned)avail / (unsigned)ldy)
-                                                            : avail / ldy;
-                k = (long long)(N - r) < fit ? (long long)(N - r) : fit;
+        if (rows_in > 0) {   // rows of pair i that still fit in the open band (a new segment of it)
+            const long long avail = C - cur - seg_cost;
+            if (avail >= ldy) {
+                const long long fit = bp_div(avail, ldy);
+                r = fit < (long long)N ? (int)fit : N;
+                cur += seg_cost + r * ldy;
+                rows_in += r;
+                gr += r;
+                if (r == N) continue;
             }
-            if (k == 0) {
-                if (rows_in > 0) {
-                    if (++b >= max_bands) return max_bands + 1;
-                    if (band) band[b] = gr;
-                    cur = 0;
-                    rows_in = 0;
-                    last = -1;
-                    continue;
-                }
-                k = 1;   // C below one row's cost: the row goes alone
-            }
-            cur += seg + k * ldy;
-            rows_in += (int)k;
-            r += (int)k;
-            gr += (int)k;
-            last = i;
+            if (++b >= max_bands) return max_bands + 1;   // the band is closed
+            if (band) band[b] = gr;
+            rows_in = 0;
         }
+        // the rest in fresh bands of kk rows each (one row when a row alone exceeds C)
+        const int rest = N - r;
+        const long long kk = room >= ldy ? bp_div(room, ldy) : 1;
+        const long long nb = kk >= rest ? 1 : (long long)(((unsigned)rest + (unsigned)kk - 1u) / (unsigned)kk);
+        if ((long long)b + nb - 1 >= (long long)max_bands) return max_bands + 1;
+        for (long long t = 1; band && t < nb; ++t) band[b + t] = gr + (int)(t * kk);
+        b += (int)(nb - 1);
+        rows_in = rest - (int)((nb - 1) * kk);
+        gr += rest;
+        cur = seg_cost + rows_in * ldy;
     }
     return rows_in > 0 || b == 0 ? b + 1 : b;
 }

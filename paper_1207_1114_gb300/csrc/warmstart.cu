@@ -4,7 +4,9 @@
 //
 //   features  F_i = [zscore(deg)_i, hist_i[0..15], zscore(B)_i[0..14]]
 //   MLP       H = relu(F W1 + b1), E = H W2 + b2     (32 -> 128 -> 64, shared)
-//   S         E_big E_small^T / 8,  X(0) = Sinkhorn(exp(S - max S))
+//   S         E_big E_small^T / 8,  X(0) = Sinkhorn(max(exp(S - rowmax S), 2^-100))
+//             (every normalised entry floored at 2^-100 too: a trained S can
+//             be so peaked that whole columns would underflow to zero)
 //   training  row + column softmax cross-entropy of S against a solved
 //             matching; analytic backward through S and the MLP; Adam.
 //
@@ -135,35 +137,20 @@ __global__ void transpose_kernel(const float* src, int r, int c, int lds, float*
     }
 }
 
-// Global maximum of an r x c matrix (single block, fixed order).
-__global__ void max_kernel(const float* S, int r, int c, int ld, float* out) {
-    __shared__ float red[32];
-    float mx = -INFINITY;
-    for (size_t e = threadIdx.x; e < (size_t)r * c; e += blockDim.x) {
-        const int i = (int)(e / c), j = (int)(e % c);
-        mx = fmaxf(mx, S[(size_t)i * ld + j]);
-    }
-    mx = warp_max(mx);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = red[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
-        *out = t;
-    }
+constexpr float kSinkFloor = 0x1p-100f;   // positivity floor of the Sinkhorn iterates
+
+// S <- max(exp(S - max of its row), kSinkFloor); one warp per row.
+__global__ void row_exp_kernel(float* S, int r, int c, int ld) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= r) return;
+    float* row = S + (size_t)warp * ld;
+    float m = -INFINITY;
+    for (int j = lane; j < c; j += 32) m = fmaxf(m, row[j]);
+    m = warp_max(m);
+    for (int j = lane; j < c; j += 32) row[j] = fmaxf(expf(row[j] - m), kSinkFloor);
 }
 
-__global__ void exp_shift_kernel(float* S, int r, int c, int ld, const float* mx) {
-    const float m = *mx;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)r * c;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e / c), j = (int)(e % c);
-        float& v = S[(size_t)i * ld + j];
-        v = expf(v - m);
-    }
-}
-
-// Each row divided by its sum; one warp per row.
+// Each row divided by its sum (floored); one warp per row.
 __global__ void row_normalize_kernel(float* S, int r, int c, int ld) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= r) return;
@@ -172,7 +159,7 @@ __global__ void row_normalize_kernel(float* S, int r, int c, int ld) {
     for (int j = lane; j < c; j += 32) s += row[j];
     s = warp_sum(s);
     const float inv = 1.0f / s;
-    for (int j = lane; j < c; j += 32) row[j] *= inv;
+    for (int j = lane; j < c; j += 32) row[j] = fmaxf(row[j] * inv, kSinkFloor);
 }
 
 // Column partial sums over row chunks: part[chunk][j].
@@ -193,7 +180,7 @@ __global__ void col_normalize_kernel(float* S, int r, int c, int ld, const float
     for (int ch = 0; ch < nch; ++ch) s += part[(size_t)ch * c + j];
     const float inv = 1.0f / s;
     const int i0 = blockIdx.y * kChunkRows, i1 = min(r, i0 + kChunkRows);
-    for (int i = i0; i < i1; ++i) S[(size_t)i * ld + j] *= inv;
+    for (int i = i0; i < i1; ++i) S[(size_t)i * ld + j] = fmaxf(S[(size_t)i * ld + j] * inv, kSinkFloor);
 }
 
 // Column log-sum-exp of S: phase 1, per chunk (max, sum exp) with an online update.
@@ -364,9 +351,8 @@ cudaError_t ws_scale(float* x, size_t n, float v, cudaStream_t s) {
 
 cudaError_t ws_sinkhorn(float* S, int r, int c, int ld, int iters, float* part, float* scalar,
                         cudaStream_t s) {
-    max_kernel<<<1, 1024, 0, s>>>(S, r, c, ld, scalar);
-    WS_CHECK();
-    exp_shift_kernel<<<blocks_for((size_t)r * c, 256), 256, 0, s>>>(S, r, c, ld, scalar);
+    (void)scalar;
+    row_exp_kernel<<<(r + 7) / 8, 256, 0, s>>>(S, r, c, ld);
     WS_CHECK();
     const int nch = (r + kChunkRows - 1) / kChunkRows;
     for (int it = 0; it < iters; ++it) {

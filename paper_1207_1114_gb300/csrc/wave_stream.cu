@@ -129,48 +129,65 @@ __device__ bool plan_bands_par(PlanShared& S, const int* Ns, int n, int num_sms,
 __global__ void __launch_bounds__(kPlanThreads, 1)
     wave_plan_kernel(StreamState* st, const PairDesc* tmpl, PairDesc* wave, int* band, WaveCtrl* W) {
     __shared__ PlanShared S;
-    __shared__ int s_go, s_first, s_next, s_try;
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    __shared__ int s_first, s_err, s_nact, s_count, s_next, s_try, s_left;
+    __shared__ int s_warp[kMaxWavePairs / 32];
+    __shared__ int s_row0[kMaxWavePairs + 1];
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
-        s_go = 1;
         s_first = st->first;
-        st->error = ld_relaxed_i32(&W->error);
-        if (st->error != 0) {
-            st->done = 1;
-            s_go = 0;
-        } else {
-            // the wave's pairs that are still running stay, in order
-            int n = 0, left = 0;
-            for (int i = 0; i < st->nact; ++i) {
-                const int p = st->act[i];
-                const Ctrl* c = tmpl[p].ctrl;
-                if (ld_relaxed_i32(&c->done) != 0 || ld_relaxed_i32(&c->error) != 0) {
-                    ++left;
-                    continue;
-                }
-                S.list[n] = p;
-                S.Ns[n] = tmpl[p].N;
-                ++n;
-            }
-            S.n = n;
-            // nothing changes until a pair stops (the wave and its plan stay)
-            if (!s_first && left == 0) s_go = 0;
-        }
+        s_err = ld_relaxed_i32(&W->error);
+        s_nact = st->nact;
+        s_count = st->count;
+        st->error = s_err;
+        if (s_err != 0) st->done = 1;
     }
     __syncthreads();
-    if (!s_go) return;
+    if (s_err != 0) return;
+    // the wave's pairs that are still running stay, in order (one thread per
+    // pair reads its stop words; a ballot per warp keeps the order)
+    const int nact = s_nact;
+    int keep = 0, p = 0, N = 0;
+    unsigned bal = 0;
+    if (tid < nact) {
+        p = st->act[tid];
+        const Ctrl* c = tmpl[p].ctrl;
+        N = tmpl[p].N;
+        keep = ld_relaxed_i32(&c->done) == 0 && ld_relaxed_i32(&c->error) == 0;
+    }
+    if (warp < kMaxWavePairs / 32) {   // warp-uniform
+        bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) s_warp[warp] = __popc(bal);
+    }
+    __syncthreads();
+    if (keep) {
+        int pos = __popc(bal & ((1u << lane) - 1u));
+        for (int w = 0; w < warp; ++w) pos += s_warp[w];
+        S.list[pos] = p;
+        S.Ns[pos] = N;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int kept = 0;
+        for (int w = 0; w < kMaxWavePairs / 32; ++w) kept += s_warp[w];
+        S.n = kept;
+        s_left = nact - kept;
+    }
+    __syncthreads();
+    // nothing changes until a pair stops (the wave and its plan stay)
+    if (!s_first && s_left == 0) return;
     if (s_first) {   // every pair of the batch waits until it is admitted
-        for (int p = tid; p < st->count; p += nthr) tmpl[p].ctrl->idle = 1;
+        for (int p = tid; p < s_count; p += nthr) tmpl[p].ctrl->idle = 1;
         __syncthreads();
     }
     // admit waiting pairs in batch order while the plan with the next one
     // still fits: at the admission level once the wave has pairs, at any
     // level for its first pair
     bool have = false;
+    if (tid == 0) s_next = st->next;
+    __syncthreads();
     while (true) {
         if (tid == 0) {
-            s_next = st->next;
-            s_try = s_next < st->count && S.n < kMaxWavePairs && tmpl[s_next].N <= kPdbMaxN;
+            s_try = s_next < s_count && S.n < kMaxWavePairs && tmpl[s_next].N <= kPdbMaxN;
             if (s_try) {
                 S.list[S.n] = s_next;
                 S.Ns[S.n] = tmpl[s_next].N;
@@ -183,7 +200,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
         if (tid == 0) {
             S.plan = S.trial;
             S.n += 1;
-            st->next = s_next + 1;
+            s_next += 1;
         }
         have = true;
         __syncthreads();
@@ -200,30 +217,33 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
     // the wave tables: pairs (rows numbered through the wave), bands (the
     // launch's extra CTAs get empty bands), layout and the idle words
     const int n = S.n;
-    for (int i = tid; i < st->nact; i += nthr) tmpl[st->act[i]].ctrl->idle = 1;
-    __syncthreads();
+    for (int i = tid; i < nact; i += nthr) tmpl[st->act[i]].ctrl->idle = 1;
     if (tid == 0) {
-        int row0 = 0;
-        for (int i = 0; i < n; ++i) {
-            PairDesc d = tmpl[S.list[i]];
-            d.row0 = row0;
-            row0 += d.N;
-            wave[i] = d;
-            Ctrl* c = d.ctrl;
-            c->idle = 0;
-            if (n > c->wave_pairs) c->wave_pairs = n;
-            st->act[i] = S.list[i];
-        }
+        s_row0[0] = 0;
+        for (int i = 0; i < n; ++i) s_row0[i + 1] = s_row0[i] + S.Ns[i];
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += nthr) {
+        PairDesc d = tmpl[S.list[i]];
+        d.row0 = s_row0[i];
+        wave[i] = d;
+        Ctrl* c = d.ctrl;
+        c->idle = 0;
+        if (n > c->wave_pairs) c->wave_pairs = n;
+        st->act[i] = S.list[i];
+    }
+    const int G = n > 0 ? S.plan.grid : 0, rows = s_row0[n];
+    for (int c = tid; c <= st->num_sms; c += nthr) band[c] = c <= G && n > 0 ? S.plan.band[c] : rows;
+    if (tid == 0) {
         st->nact = n;
-        const int G = n > 0 ? S.plan.grid : 0;
-        for (int c = 0; c <= st->num_sms; ++c) band[c] = c <= G && n > 0 ? S.plan.band[c] : row0;
+        st->next = s_next;
         W->npairs = n;
         W->layout = S.plan.layout;
         W->all_done = n == 0 ? 1 : 0;
         st->first = 0;
-        st->done = (n == 0 && st->next >= st->count) ? 1 : 0;
+        st->done = (n == 0 && s_next >= s_count) ? 1 : 0;
         st->waves += 1;
-        if (n == 0 && st->next < st->count) {   // a waiting pair fits in no wave
+        if (n == 0 && s_next < s_count) {   // a waiting pair fits in no wave
             atomicCAS(&W->error, 0, FASTPFP_ERR_UNSUPPORTED);
             st->error = FASTPFP_ERR_UNSUPPORTED;
             st->done = 1;

@@ -30,6 +30,22 @@ DRIVER = r'''
 #include "band_plan.cuh"
 using namespace fpfp;
 int main(int argc, char** argv) {
+    int mode = 0;
+    if (scanf("%d", &mode) != 1) return 1;
+    if (mode == 1) {   // one greedy cut: C seg max_bands count Ns...
+        long long C = 0, seg = 0;
+        int max_bands = 0, count = 0;
+        if (scanf("%lld %lld %d %d", &C, &seg, &max_bands, &count) != 4) return 1;
+        std::vector<int> Ns(count);
+        for (int& n : Ns) if (scanf("%d", &n) != 1) return 1;
+        std::vector<int> band(max_bands + 2, -1);
+        const int used = cut_rows(Ns.data(), count, C, seg, max_bands, band.data());
+        const int counted = cut_rows(Ns.data(), count, C, seg, max_bands, nullptr);
+        printf("{\"used\": %d, \"counted\": %d, \"band\": [", used, counted);
+        for (int b = 0; b < used && b <= max_bands; ++b) printf("%s%d", b ? ", " : "", band[b]);
+        printf("]}\n");
+        return 0;
+    }
     int num_sms = 0, count = 0, level = 3;
     if (scanf("%d %d %d", &num_sms, &level, &count) != 3) return 1;
     std::vector<int> Ns(count);
@@ -78,11 +94,38 @@ def planner():
     subprocess.run(["g++", "-std=c++17", "-O1", "-I", CSRC, "-I", CUDA_INC, "-I", os.path.join(ROOT, "include"),
                     src, "-o", exe], check=True)
 
-    def run(Ns, num_sms=152, level=3):
-        inp = f"{num_sms} {level} {len(Ns)} " + " ".join(map(str, Ns))
+    def run(Ns, num_sms=152, level=3, cut=None):
+        if cut is not None:   # (C, seg_cost, max_bands): one greedy cut
+            inp = "1 {} {} {} {} ".format(*cut, len(Ns)) + " ".join(map(str, Ns))
+        else:
+            inp = f"0 {num_sms} {level} {len(Ns)} " + " ".join(map(str, Ns))
         out = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True).stdout
         return json.loads(out)
     return run
+
+
+def _greedy_by_rows(Ns, C, seg_cost, max_bands):
+    """The greedy cut by its definition, one row at a time: a row of pair i
+    costs its row length plus the segment cost when the open band holds no
+    row of pair i; it joins the open band while the band stays within C,
+    else opens the next band (alone when even that exceeds C).  Returns
+    (bands, starts) or (max_bands + 1, None) once more bands are needed."""
+    starts, cur, pairs_in, rows_in, g = [0], 0, set(), 0, 0
+    for i, n in enumerate(Ns):
+        ldy = (n + 3) & ~3
+        for _ in range(n):
+            cost = ldy + (seg_cost if i not in pairs_in else 0)
+            if rows_in > 0 and cur + cost > C:
+                if len(starts) >= max_bands:
+                    return max_bands + 1, None
+                starts.append(g)
+                cur, pairs_in, rows_in = 0, set(), 0
+                cost = ldy + seg_cost
+            cur += cost
+            pairs_in.add(i)
+            rows_in += 1
+            g += 1
+    return len(starts), starts
 
 
 def _band_costs(Ns, band, seg_cost):
@@ -126,3 +169,25 @@ def test_a_wave_of_seventeen_pairs_of_1000_fits_and_eighteen_at_level_0_does_not
     the full segment cost (the measured wave size), 18 do not."""
     assert planner([1000] * 17, level=0)["ok"] == 1
     assert planner([1000] * 18, level=0)["ok"] == 0
+
+
+def test_cut_matches_the_row_by_row_greedy(planner):
+    """The planner's cut takes a pair at a time (whole fresh bands in closed
+    form); on random waves and bounds it gives the row-by-row greedy's bands
+    exactly, including the bound where a row alone exceeds C and the early
+    stop once more than max_bands bands would be needed."""
+    rng = np.random.default_rng(11)
+    cases = [([1000] * 17, 111_000, 32768, 152), ([1000] * 17, 1000 + 32768, 32768, 152),
+             ([7], 10, 32768, 4), ([5, 9, 1, 13], 40, 8, 3), ([4000], 2_000_000, 0, 152)]
+    for _ in range(300):
+        Ns = list(rng.integers(1, 300, size=rng.integers(1, 9)))
+        seg = int(rng.choice([0, 16, 256, 4096]))
+        tot = sum(n * ((n + 3) & ~3) for n in Ns) + seg * len(Ns)
+        C = int(rng.integers(1, tot + 2))
+        cases.append((Ns, C, seg, int(rng.integers(1, 40))))
+    for Ns, C, seg, mb in cases:
+        want, starts = _greedy_by_rows(Ns, C, seg, mb)
+        got = planner(Ns, cut=(C, seg, mb))
+        assert got["used"] == want and got["counted"] == want, (Ns, C, seg, mb, got, want)
+        if starts is not None:
+            assert got["band"] == starts, (Ns, C, seg, mb)

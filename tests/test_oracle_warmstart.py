@@ -82,6 +82,32 @@ def test_sinkhorn_converges_to_doubly_stochastic():
     assert r1 == pytest.approx(r2, rel=1e-10)
 
 
+def test_sinkhorn_of_peaked_or_far_apart_rows_stays_finite():
+    """Rows far below the global maximum (a trained S can span thousands):
+    shifting by each row's own maximum keeps them; the result is the same
+    doubly stochastic matrix a plain global shift gives where that does not
+    underflow."""
+    K = ws.sinkhorn(np.array([[0.0, 0.0], [-2000.0, -2000.0]]), iters=3)
+    np.testing.assert_array_equal(K, np.full((2, 2), 0.5))
+    # a very peaked similarity: the permutation it encodes, off entries at the floor
+    perm = np.array([2, 0, 3, 1])
+    S = np.full((4, 4), -1.0)
+    S[np.arange(4), perm] = 1e4
+    K = ws.sinkhorn(S, iters=20)
+    assert np.isfinite(K).all()
+    np.testing.assert_allclose(K[np.arange(4), perm], 1.0, rtol=1e-12)
+    off = np.ones((4, 4), bool)
+    off[np.arange(4), perm] = False
+    assert (K[off] <= 2.0 ** -99).all() and (K[off] > 0).all()
+    # where nothing underflows the row shift changes nothing
+    S = np.random.default_rng(5).normal(size=(6, 5))
+    E = np.exp(S - S.max())
+    for _ in range(4):
+        E = E / E.sum(1, keepdims=True)
+        E = E / E.sum(0, keepdims=True)
+    np.testing.assert_allclose(ws.sinkhorn(S, iters=4), E, rtol=1e-13)
+
+
 def test_adam_first_step_moves_by_lr_times_sign():
     p = np.array([1.0, -2.0, 0.5])
     g = np.array([0.3, -7.0, 1e-3])
