@@ -206,6 +206,36 @@ __device__ __forceinline__ void tm_st16(uint32_t taddr, const float4 (&q)[4]) {
           "r"(__float_as_uint(q[3].w))
         : "memory");
 }
+// Two 16-column loads behind one wait (the wait names their registers, so
+// no use of them can be scheduled before it): half the load round trips of
+// one wait per load.
+__device__ __forceinline__ void tm_ld16x2(uint32_t ta, uint32_t tb, float4 (&q)[8]) {
+    uint32_t a[16], b[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]),
+          "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15])
+        : "r"(ta));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]),
+          "=r"(b[8]), "=r"(b[9]), "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15])
+        : "r"(tb));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
+                   "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]), "+r"(a[14]),
+                   "+r"(a[15]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]),
+                   "+r"(b[6]), "+r"(b[7]), "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]),
+                   "+r"(b[13]), "+r"(b[14]), "+r"(b[15])
+                 :: "memory");
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        q[j] = make_float4(__uint_as_float(a[4 * j]), __uint_as_float(a[4 * j + 1]), __uint_as_float(a[4 * j + 2]),
+                           __uint_as_float(a[4 * j + 3]));
+        q[4 + j] = make_float4(__uint_as_float(b[4 * j]), __uint_as_float(b[4 * j + 1]),
+                               __uint_as_float(b[4 * j + 2]), __uint_as_float(b[4 * j + 3]));
+    }
+}
 __device__ __forceinline__ float4 tm_ld4(uint32_t taddr) {
     uint32_t r[4];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
@@ -250,6 +280,32 @@ __device__ __forceinline__ void seg_rows_tmem(uint32_t taddr, int tm, int nrows,
     const bool h0 = mp.q0 < Q;
     const int RP = mp.RP;
     int k = 0;
+    // eight thread-rows per wait
+    for (; k + 7 < tm; k += 8) {
+        float4 q[8];
+        tm_ld16x2(taddr + 4 * k, taddr + 4 * k + 16, q);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float s[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int r = mp.grp + RP * (k + 4 * h + j);
+                s[j] = 0.f;
+                if (r < nrows && h0) {
+                    const float a = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
+                    s[j] = quad_upd<UPDATE>(q[4 * h + j], a, c0v, cp0, dmax);
+                }
+            }
+            const float z = sum4_rows(s, lane);
+            const int rj = mp.grp + RP * (k + 4 * h + 2 * (lane >> 4) + ((lane >> 3) & 1));
+            if ((lane & 7) == 0 && rj < nrows) rowpart[(size_t)rj * rps] = z;
+        }
+        if (UPDATE) {
+            const float4 qa[4] = {q[0], q[1], q[2], q[3]}, qb[4] = {q[4], q[5], q[6], q[7]};
+            tm_st16(taddr + 4 * k, qa);
+            tm_st16(taddr + 4 * k + 16, qb);
+        }
+    }
     for (; k + 3 < tm; k += 4) {
         float4 q[4];
         tm_ld16(taddr + 4 * k, q);
@@ -294,6 +350,30 @@ __device__ __forceinline__ void seg_rows_tmem2(uint32_t taddr, int tm, int nrows
     const bool h0 = mp.q0 < Q, h1 = q1 < Q;
     const int RP = mp.RP;
     int k = 0;
+    // four thread-rows per wait, their four row sums in one shuffle tree
+    for (; k + 3 < tm; k += 4) {
+        float4 q[8];   // row k + j: quads 0, 1 at q[2 j], q[2 j + 1]
+        tm_ld16x2(taddr + 8 * k, taddr + 8 * k + 16, q);
+        float s[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = mp.grp + RP * (k + j);
+            s[j] = 0.f;
+            if (r < nrows) {
+                const float a = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
+                if (h0) s[j] += quad_upd<UPDATE>(q[2 * j], a, c0v, cp0, dmax);
+                if (h1) s[j] += quad_upd<UPDATE>(q[2 * j + 1], a, c1v, cp1, dmax);
+            }
+        }
+        if (UPDATE) {
+            const float4 qa[4] = {q[0], q[1], q[2], q[3]}, qb[4] = {q[4], q[5], q[6], q[7]};
+            tm_st16(taddr + 8 * k, qa);
+            tm_st16(taddr + 8 * k + 16, qb);
+        }
+        const float z = sum4_rows(s, lane);
+        const int rj = mp.grp + RP * (k + 2 * (lane >> 4) + ((lane >> 3) & 1));
+        if ((lane & 7) == 0 && rj < nrows) rowpart[(size_t)rj * rps] = z;
+    }
     for (; k + 1 < tm; k += 2) {
         float4 q[4];   // row k: quads 0, 1; row k + 1: quads 0, 1
         tm_ld16(taddr + 8 * k, q);
