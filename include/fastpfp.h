@@ -65,7 +65,7 @@ extern "C" {
  * result) before each product.  BF16 and FP8 runs end with FP32
  * iterations (the FP32 products above). */
 enum { FASTPFP_FP32 = 0, FASTPFP_BF16 = 1, FASTPFP_FP8 = 2, FASTPFP_FP32_SIMT = 3 };
-enum { FASTPFP_ALG_FASTPFP = 0, FASTPFP_ALG_PG = 1 };
+enum { FASTPFP_ALG_FASTPFP = 0, FASTPFP_ALG_PG = 1, FASTPFP_ALG_FASTGA = 2 };
 
 typedef struct fastpfp_s* fastpfp_t;
 
@@ -110,7 +110,17 @@ typedef struct {
                               X <- (1 - alpha) X + alpha P_d(A X A' + lambda K);
                               FASTPFP_ALG_PG: the projected gradient method of Eq. (pg),
                               X <- P_d(X + alpha (A X A' + lambda K)) (normalize_max applies to
-                              both)                                                          */
+                              both);
+                              FASTPFP_ALG_FASTGA: graduated assignment with C = A (x) A'
+                              (Appendix, Eqs. GAO3/GAO4) at a fixed beta, the comparison method
+                              of Section 5: X <- Y[:, :m] of Sinkhorn normalisation (rows, then
+                              columns, to eps_2 or I_1) applied to exp(beta (A X A' + lambda K))
+                              over the slacked N x N matrix (slack columns 0), to eps_1 or I_0;
+                              precision FP32 or FP32_SIMT only; pairs of a batch run one after
+                              another; alpha and normalize_max do not apply                   */
+    float beta;            /* FASTPFP_ALG_FASTGA: the fixed inverse temperature beta > 0 of the
+                              soft-assignment (the paper gives no value or schedule; default
+                              10)                                                            */
 } fastpfp_params;
 
 /* Statistics of one solve (in the canonical orientation). */

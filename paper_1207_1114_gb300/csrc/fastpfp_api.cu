@@ -103,6 +103,8 @@ struct fastpfp_s {
     StreamState* d_stream = nullptr;
     StreamState* h_stream = nullptr;
     int host_syncs = 0;          // host synchronisations of the current call
+    // FastGA: the N x N scratch of its normalisation (allocated on first use)
+    float* ga_z = nullptr;
 
     cudaEvent_t ev[kProfEvents] = {};
     cudaEvent_t chunk_ev[2] = {};
@@ -160,7 +162,13 @@ bool params_ok(const fastpfp_params* p) {
         return false;
     if (p->refine_iters < 0) return false;
     if (p->loop_mode != 0 && p->loop_mode != 1) return false;
-    if (p->algorithm != FASTPFP_ALG_FASTPFP && p->algorithm != FASTPFP_ALG_PG) return false;
+    if (p->algorithm != FASTPFP_ALG_FASTPFP && p->algorithm != FASTPFP_ALG_PG &&
+        p->algorithm != FASTPFP_ALG_FASTGA)
+        return false;
+    if (p->algorithm == FASTPFP_ALG_FASTGA) {   // FP32 products; a positive, finite beta
+        if (p->precision != FASTPFP_FP32 && p->precision != FASTPFP_FP32_SIMT) return false;
+        if (!(p->beta > 0.f) || !isfinite(p->beta)) return false;
+    }
     return true;
 }
 
@@ -642,6 +650,53 @@ int enqueue_single(fastpfp_t h, cudaStream_t s, const Slot& sl, const Problem& q
     return nl + f;
 }
 
+// One pair through FastGA (fastga.cu): the gradient products of FastPFP
+// (FP32: split TF32 on the tensor cores, or SIMT), then one ga_kernel launch
+// per outer iteration; the same setup, loop control and finish as a
+// single-pair FastPFP solve.
+int enqueue_ga(fastpfp_t h, cudaStream_t s, const Slot& sl, const Problem& q, const fastpfp_params* p,
+               Ctrl* host_slot) {
+    const int N = q.N, m = q.m;
+    const int slot = (int)(&sl - h->slots.data());
+    TcPlan tc;
+    if (!simt_of(p) && !plan_split(h, &q, 1, p, &tc, &slot)) return FASTPFP_ERR_UNSUPPORTED;
+    if (!h->ga_z) FP_CUDA(cudaMalloc(&h->ga_z, (size_t)h->max_n * round4(h->max_n) * sizeof(float)));
+    int nl = enqueue_setup(sl, s, q, p, h->ld);
+    if (nl < 0) return nl;
+    // the slot's column-sum buffer holds the two integer accumulators: 16
+    // bytes per column of the 20 it has
+    static_assert(2 * sizeof(unsigned long long) <= 3 * sizeof(float) + sizeof(double), "acc in colbuf");
+    GaParams P{};
+    P.Y = sl.Y;
+    P.Z = h->ga_z;
+    P.X = sl.X;
+    P.acc = reinterpret_cast<unsigned long long*>(sl.colbuf);
+    P.dbuf = sl.dbuf;
+    P.ctrl = sl.ctrl;
+    P.N = N;
+    P.m = m;
+    P.ldy = round4(N);
+    P.ldx = round4(m);
+    P.rpc = ga_rows_per_cta(N, h->num_sms);
+    P.beta = p->beta;
+    P.tol_inner = p->tol_inner;
+    P.tol_outer = p->tol_outer;
+    P.max_inner = p->max_inner;
+    P.max_outer = p->max_outer;
+    P.timeout_ns = timeout_ns(p);
+    const int r = run_outer(h, s, p, &sl.ctrl->done, 0, 2, [&](int, cudaStream_t st) -> int {
+        const int g32 = simt_of(p) ? enqueue_gradient(sl, st, q, p, f32_tile(h, q.N, 1)) : enqueue_fp32(tc, st);
+        if (g32 < 0) return g32;
+        FP_CUDA(ga_launch(P, st));
+        return g32 + 1;
+    });
+    if (r < 0) return r;
+    nl += r;
+    const int f = enqueue_finish(sl, s, q, p, h->num_sms, host_slot);
+    if (f < 0) return f;
+    return nl + f;
+}
+
 // Per-phase times of the last profiled solve (after the stream synced).
 void read_profile(fastpfp_t h, int outer, float share, fastpfp_stats* st) {
     if (!st) return;
@@ -901,6 +956,7 @@ void fastpfp_default_params(fastpfp_params* p) {
     p->loop_mode = 0;
     p->debug_flags = 0;
     p->algorithm = FASTPFP_ALG_FASTPFP;
+    p->beta = 10.f;
 }
 
 const char* fastpfp_error_string(int code) {
@@ -936,6 +992,7 @@ int fastpfp_create(fastpfp_t* out, int device, int max_n, int max_batch) {
         }
     if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         pd_configure() != cudaSuccess || pdb_configure() != cudaSuccess || tc_configure() != cudaSuccess ||
+        ga_configure() != cudaSuccess ||
         gemm_f32t_configure() != cudaSuccess ||
         disc_configure() != cudaSuccess) {
         delete h;
@@ -1112,6 +1169,7 @@ void fastpfp_destroy(fastpfp_t h) {
     if (h->h_flags) cudaFreeHost(h->h_flags);
     if (h->h_tmpl) cudaFreeHost(h->h_tmpl);
     if (h->h_stream) cudaFreeHost(h->h_stream);
+    if (h->ga_z) cudaFree(h->ga_z);
     if (h->cap) cudaStreamDestroy(h->cap);
     if (h->pool) cudaFree(h->pool);
     delete h;
@@ -1518,6 +1576,44 @@ int solve_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, const fa
     return worst;
 }
 
+// FastGA over a batch: the pairs one after another on the stream (slot i
+// for pair i), one synchronisation at the end.
+int solve_ga(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, const fastpfp_pair* pairs,
+             const fastpfp_params* p, fastpfp_stats* st, bool host) {
+    const int count = (int)qs.size();
+    std::vector<int> nl(count, 0), body(count, 0);
+    for (int i = 0; i < count; ++i) {
+        if (host) {
+            const int r = stage_in(h, s, pairs[i], p, i, &qs[i]);
+            if (r < 0) return r;
+        }
+        int r = enqueue_ga(h, s, h->slots[i], qs[i], p, &h->host_ctrl[i]);
+        if (r >= 0 && save_trace(h, s, i, i, p->max_outer) < 0) r = FASTPFP_ERR_CUDA;
+        if (r >= 0 && host && stage_out(h, s, pairs[i], i) < 0) r = FASTPFP_ERR_CUDA;
+        if (r < 0) {
+            cudaStreamSynchronize(s);
+            release_graphs(h);
+            return r;
+        }
+        nl[i] = r;
+        body[i] = h->loop_body;
+    }
+    const cudaError_t es = cudaStreamSynchronize(s);
+    h->host_syncs += 1;
+    release_graphs(h);
+    if (es != cudaSuccess) return FASTPFP_ERR_CUDA;
+    int worst = FASTPFP_OK;
+    for (int i = 0; i < count; ++i) {
+        // graph mode: a loop-init kernel plus one body per outer iteration run
+        const int launches = nl[i] + (body[i] > 0 ? 1 + body[i] * h->host_ctrl[i].outer : 0);
+        const int rc = fill_stats(h->host_ctrl[i], qs[i].transposed, launches, 0, st ? &st[i] : nullptr,
+                                  h->host_syncs);
+        if (rc != FASTPFP_OK && worst == FASTPFP_OK) worst = rc;
+    }
+    h->last_count = count;
+    return worst;
+}
+
 int solve_batch(fastpfp_t h, cudaStream_t s, int count, const fastpfp_pair* pairs,
                 const fastpfp_params* p, fastpfp_stats* st, bool host) {
     h->host_syncs = 0;
@@ -1526,6 +1622,7 @@ int solve_batch(fastpfp_t h, cudaStream_t s, int count, const fastpfp_pair* pair
         const fastpfp_pair& x = pairs[b];
         qs[b] = canonical(x.A, x.n_a, x.A2, x.n_b, x.B, x.B2, x.k, p->lambda, x.X0, x.perm_out, x.X_out);
     }
+    if (p->algorithm == FASTPFP_ALG_FASTGA) return solve_ga(h, s, qs, pairs, p, st, host);
     // a batch that fits in one wave runs as one wave (its loop on the
     // device), a lone pair included: its slacked matrix then stays on chip
     // (TMEM + shared memory) instead of streaming through L2; a larger batch

@@ -263,6 +263,26 @@ struct TcGroup {
     int tile0[kTcMaxGroup + 1];
     int ntn[kTcMaxGroup];
 };
+// FastGA (fastga.cu): one cooperative launch per outer iteration over one
+// pair's slacked matrix, after the gradient products.
+constexpr int kGaThreads = 512;
+struct GaParams {
+    float* Y;                 // N x ldy: the products in columns 0..m-1, then Y of the normalisation
+    float* Z;                 // N x ldy scratch (rows normalised)
+    float* X;                 // N x ldx master X
+    unsigned long long* acc;  // 2 x ldy column sums in units of 2^-40 (zero between launches)
+    unsigned* dbuf;           // 2 words: a step's max|dY| (zero between launches)
+    Ctrl* ctrl;
+    int N, m, ldy, ldx, rpc;
+    float beta;
+    double tol_inner, tol_outer;
+    int max_inner, max_outer;
+    long long timeout_ns;
+};
+int ga_rows_per_cta(int N, int num_sms);
+cudaError_t ga_configure();
+cudaError_t ga_launch(const GaParams& P, cudaStream_t s);
+
 constexpr int kTcTileM = 128;   // output tile rows of tc_gemm (the A operand's box)
 // Output tile columns of the split FP32 products (kTcTf32x3): each tile keeps
 // two FP32 accumulators in tensor memory, so only 128-column tiles fit two

@@ -24,7 +24,7 @@ FASTPFP_ERR_TIMEOUT = -4
 FASTPFP_ERR_NONFINITE = -5
 FASTPFP_ERR_UNSUPPORTED = -6
 FP32, BF16, FP8, FP32_SIMT = 0, 1, 2, 3
-ALG_FASTPFP, ALG_PG = 0, 1
+ALG_FASTPFP, ALG_PG, ALG_FASTGA = 0, 1, 2
 
 # Every symbol include/fastpfp.h declares.
 EXPORTS = ("fastpfp_default_params", "fastpfp_create", "fastpfp_destroy", "fastpfp_match",
@@ -44,7 +44,7 @@ class fastpfp_params(C.Structure):
                 ("precision", C.c_int), ("refine_iters", C.c_int), ("switch_tol", C.c_double),
                 ("normalize_max", C.c_int), ("slack_policy", C.c_int), ("timeout_ms", C.c_int),
                 ("profile", C.c_int), ("loop_mode", C.c_int), ("debug_flags", C.c_int),
-                ("algorithm", C.c_int)]
+                ("algorithm", C.c_int), ("beta", C.c_float)]
 
 
 class fastpfp_stats(C.Structure):

@@ -50,7 +50,7 @@ def test_default_params_and_error_strings(built):
     assert p.alpha == 0.5 and p.max_outer == 100 and p.max_inner == 1000
     assert p.tol_outer == 1e-6 and p.tol_inner == 1e-6 and p.normalize_max == 1
     assert p.slack_policy == 0 and p.precision == F.FP32 and p.debug_flags == 0
-    assert p.algorithm == F.ALG_FASTPFP
+    assert p.algorithm == F.ALG_FASTPFP and p.beta == 10.0
     for code in (0, -1, -2, -3, -4, -5, -6):
         assert F.error_string(code) != "unknown error"
 
@@ -63,10 +63,10 @@ def test_struct_layouts_match_header():
 #include "fastpfp.h"
 int main(void) {
   printf("%zu %zu %zu\n", sizeof(fastpfp_params), sizeof(fastpfp_stats), sizeof(fastpfp_pair));
-  printf("%zu %zu %zu\n", offsetof(fastpfp_stats, wave_pairs), offsetof(fastpfp_stats, ms_disc),
-         offsetof(fastpfp_stats, host_syncs));
-  printf("%d %d %d %d %d %d %d %d\n", FASTPFP_FP32, FASTPFP_BF16, FASTPFP_FP8, FASTPFP_FP32_SIMT,
-         FASTPFP_ALG_FASTPFP, FASTPFP_ALG_PG, FASTPFP_TUNE_SIZES, FASTPFP_TUNE_COUNTS);
+  printf("%zu %zu %zu %zu\n", offsetof(fastpfp_stats, wave_pairs), offsetof(fastpfp_stats, ms_disc),
+         offsetof(fastpfp_stats, host_syncs), offsetof(fastpfp_params, beta));
+  printf("%d %d %d %d %d %d %d %d %d\n", FASTPFP_FP32, FASTPFP_BF16, FASTPFP_FP8, FASTPFP_FP32_SIMT,
+         FASTPFP_ALG_FASTPFP, FASTPFP_ALG_PG, FASTPFP_ALG_FASTGA, FASTPFP_TUNE_SIZES, FASTPFP_TUNE_COUNTS);
   return 0;
 }'''
     import tempfile
@@ -81,7 +81,7 @@ int main(void) {
                      C.sizeof(F.fastpfp_pair)]
     offs = [int(x) for x in lines[1].split()]
     assert offs == [F.fastpfp_stats.wave_pairs.offset, F.fastpfp_stats.ms_disc.offset,
-                    F.fastpfp_stats.host_syncs.offset]
+                    F.fastpfp_stats.host_syncs.offset, F.fastpfp_params.beta.offset]
     consts = [int(x) for x in lines[2].split()]
-    assert consts == [F.FP32, F.BF16, F.FP8, F.FP32_SIMT, F.ALG_FASTPFP, F.ALG_PG, F.TUNE_SIZES,
-                      F.TUNE_COUNTS]
+    assert consts == [F.FP32, F.BF16, F.FP8, F.FP32_SIMT, F.ALG_FASTPFP, F.ALG_PG, F.ALG_FASTGA,
+                      F.TUNE_SIZES, F.TUNE_COUNTS]
