@@ -114,13 +114,14 @@ typedef struct {
                               FASTPFP_ALG_FASTGA: graduated assignment with C = A (x) A'
                               (Appendix, Eqs. GAO3/GAO4) at a fixed beta, the comparison method
                               of Section 5: X <- Y[:, :m] of Sinkhorn normalisation (rows, then
-                              columns, to eps_2 or I_1) applied to exp(beta (A X A' + lambda K))
-                              over the slacked N x N matrix (slack columns 0), to eps_1 or I_0;
+                              columns, to eps_2 or I_1) applied to exp(beta Q / max|Q|),
+                              Q = A X A' + lambda K over the slacked N x N matrix (slack columns
+                              0), to eps_1 or I_0;
                               precision FP32 or FP32_SIMT only; pairs of a batch run one after
                               another; alpha and normalize_max do not apply                   */
     float beta;            /* FASTPFP_ALG_FASTGA: the fixed inverse temperature beta > 0 of the
-                              soft-assignment (the paper gives no value or schedule; default
-                              10)                                                            */
+                              soft-assignment, applied to Q scaled by its largest magnitude (the
+                              paper gives no value or schedule; default 100)                  */
 } fastpfp_params;
 
 /* Statistics of one solve (in the canonical orientation). */

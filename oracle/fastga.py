@@ -11,13 +11,17 @@ the normalisation (inner) loop when max|Y(k+1) - Y(k)| < eps_2 or after I_1
 iterations; the result is discretised by the same greedy rule.
 
 The paper gives neither beta nor an annealing schedule.  Reading used here
-(and by the CUDA path): beta is fixed for a solve (a parameter), the start
-is FastPFP's uniform X, and graphs of different sizes are handled as in
-FastPFP's slacked projection -- the larger graph's N nodes are the rows, the
-smaller graph's m nodes the first m of N columns, and the N - m slack
-columns (dummy nodes) take Q = 0.  One outer iteration:
+(and by the CUDA path): beta is fixed for a solve (a parameter) and applies
+to Q divided by its largest magnitude, so that one beta serves graphs whose
+products differ in scale (Q grows with n and the edge density; an absolute
+beta that suits weighted sparse pairs leaves dense unweighted ones with no
+soft-assignment at all); the start is FastPFP's uniform X, and graphs of
+different sizes are handled as in FastPFP's slacked projection -- the larger
+graph's N nodes are the rows, the smaller graph's m nodes the first m of N
+columns, and the N - m slack columns (dummy nodes) take Q = 0.  One outer
+iteration, with s = max |Q| (1 if Q = 0):
 
-  Y(0)   = max(exp(beta (Q - rowmax Q)), 2^-100)        over the N x N Q
+  Y(0)   = max(exp(beta (Q/s - rowmax Q/s)), 2^-100)    over the N x N Q
            (a per-row factor does not change the normalised result; the
            floor keeps every row and column positive where exp underflows)
   Y(k+1) = C(R(Y(k))),  R: rows divided by their sums, C: columns divided
@@ -39,8 +43,10 @@ FLOOR = 2.0 ** -100
 
 def soft_assign(Q, beta):
     """Y(0) of the inner loop from the N x N argument Q (slack columns
-    included)."""
+    included), scaled by its largest magnitude."""
     Q = np.asarray(Q, dtype=np.float64)
+    s = float(np.abs(Q).max())
+    Q = Q / (s if s > 0 else 1.0)
     return np.maximum(np.exp(beta * (Q - Q.max(axis=1, keepdims=True))), FLOOR)
 
 
@@ -66,7 +72,7 @@ def normalise(Y, tol=1e-6, max_iter=1000, fixed_iters=0):
     return Y, k, d
 
 
-def solve(A, A2, B=None, B2=None, lam=0.0, beta=10.0, tol_outer=1e-6, tol_inner=1e-6,
+def solve(A, A2, B=None, B2=None, lam=0.0, beta=100.0, tol_outer=1e-6, tol_inner=1e-6,
           max_outer=100, max_inner=1000, X0=None, replay_inner=None):
     """FastGA end to end in the caller's orientation; the same dict as
     oracle.solve (perm, X, inner / delta traces, stats).  replay_inner:

@@ -4,20 +4,24 @@
 //
 // One outer iteration is the gradient products (the same launches FastPFP
 // uses, Y[:, :m] = A X A' + lambda K) followed by one cooperative launch of
-// ga_kernel over the pair's N x N slacked matrix (slack columns Q = 0):
+// ga_kernel over the pair's N x N slacked matrix (slack columns Q = 0),
+// with beta acting on Q scaled by its largest magnitude s (one beta for
+// pairs whose products differ in scale; the paper gives no beta):
 //
-//   Y(0)   = max(exp(beta (Q - rowmax Q)), 2^-100)
+//   Y(0)   = max(exp(beta (Q/s - rowmax Q/s)), 2^-100)
 //   repeat: Z = R(Y) rows to unit sums, Y' = C(Z) columns to unit sums (each
 //           floored at 2^-100), until max|Y' - Y| < eps_2 or I_1 steps
 //   X      = Y[:, :m], max|dX| for the outer stop (eps_1, I_0).
 //
 // A CTA owns a contiguous block of rows; Y and Z stay in global memory (an
 // N x N FP32 matrix of N <= 4096 is L2-resident).  Row sums are warp sums in
-// a fixed order.  Column sums are exact: every entry of Z (<= 1) is rounded
-// to a multiple of 2^-40 and the CTAs' partials are added as 64-bit integers
-// (order-free, no FP64 arithmetic, which is slow on this part), so every run
-// gives the same bits.  Two grid barriers per normalisation step: after the
-// column sums, after the step's max|dY|.
+// a fixed order.  Column sums are two-stage, in a fixed order: every CTA
+// stores the partial of its rows per column, then (after a grid barrier)
+// CTA c adds up all CTAs' partials of its block of columns, so every run
+// gives the same bits (and a column whose entries all sit at the floor still
+// sums to a positive number).  Three grid barriers per normalisation step:
+// after the partials, after the sums, after the step's max|dY|; one more per
+// launch for s.
 #include "common.cuh"
 #include "internal.h"
 
@@ -25,19 +29,6 @@ namespace fpfp {
 namespace {
 
 constexpr float kGaFloor = 0x1p-100f;   // positivity floor of the normalised iterates
-
-// round(z * 2^40) for 0 <= z <= 2^20 from the bits (integer operations only):
-// z = M 2^(e - 150) with the 24-bit significand M and biased exponent e.
-__device__ __forceinline__ unsigned long long units_2m40(float z) {
-    const unsigned b = __float_as_uint(z) & 0x7fffffffu;
-    if (b < 0x00800000u) return 0ull;   // zero or subnormal: below half a unit
-    const int e = (int)(b >> 23);
-    const unsigned long long M = (unsigned long long)((b & 0x007fffffu) | 0x00800000u);
-    const int sh = e - 110;   // z 2^40 = M 2^(e - 110)
-    if (sh >= 0) return M << sh;
-    if (sh < -24) return 0ull;
-    return (M + (1ull << (-sh - 1))) >> -sh;   // round half up
-}
 
 __device__ __forceinline__ float block_max(float v, float* red) {
     v = warp_max(v);
@@ -75,27 +66,47 @@ __global__ void __launch_bounds__(kGaThreads, 1) ga_kernel(const GaParams P) {
     int* err = &C->error;
     float* Y = P.Y;
     float* Z = P.Z;
-    unsigned long long* acc = P.acc;   // 2 x ldy column sums in units of 2^-40, by step parity
-    unsigned* dmax = P.dbuf;           // [0], [1]: the step's max|dY| (float bits), by parity
+    float* part = P.part;   // G x ldy: the CTAs' column partials of the running step
+    float* csum = P.csum;   // ldy: the step's column sums
+    unsigned* dmax = P.dbuf;           // [0], [1]: the step's max|dY| (float bits), by parity;
+                                       // [2]: max|Q| of the launch (float bits)
 
-    // ---- Y(0): exp of beta Q shifted by the row maximum (slack columns
+    // ---- s = max|Q| over the pair (slack columns hold Q = 0)
+    float qa = 0.f;
+    for (int i = r0 + warp; i < r1; i += nwarp) {
+        const float* y = Y + (size_t)i * ldy;
+        for (int j = lane; j < m; j += 32) qa = fmaxf(qa, fabsf(y[j]));
+    }
+    qa = block_max(qa, s_red);
+    if (tid == 0 && r1 > r0 && qa > 0.f) atomicMax(dmax + 2, __float_as_uint(qa));
+    if (!grid_barrier(&C->bar, bar_base + G * (gen + 1), err, P.timeout_ns)) return;
+    ++gen;
+    float sq = __uint_as_float(__ldcg(dmax + 2));
+    if (!isfinite(sq)) {
+        if (blockIdx.x == 0 && tid == 0) atomicCAS(err, 0, FASTPFP_ERR_NONFINITE);
+        return;
+    }
+    if (!(sq > 0.f)) sq = 1.f;
+
+    // ---- Y(0): exp of beta Q/s shifted by the row maximum (slack columns
     // hold Q = 0 whatever Y stores there), floored; padding columns 0
     for (int i = r0 + warp; i < r1; i += nwarp) {
         float* y = Y + (size_t)i * ldy;
         float mx = m < N ? 0.f : -INFINITY;
-        for (int j = lane; j < m; j += 32) mx = fmaxf(mx, y[j]);
+        for (int j = lane; j < m; j += 32) mx = fmaxf(mx, y[j] / sq);
         mx = warp_max(mx);
         for (int j = lane; j < ldy; j += 32) {
-            const float q = j < m ? y[j] : 0.f;
+            const float q = j < m ? y[j] / sq : 0.f;
             y[j] = j < N ? fmaxf(expf(P.beta * (q - mx)), kGaFloor) : 0.f;
         }
     }
 
     // ---- the normalisation loop
+    const int cb = (N + (int)G - 1) / (int)G;   // columns summed by each CTA
+    const int c0 = (int)blockIdx.x * cb, c1 = min(N, c0 + cb);
     int k = 0;
     while (true) {
         const int par = k & 1;
-        unsigned long long* a = acc + (size_t)par * ldy;
         // rows to unit sums (Y -> Z)
         for (int i = r0 + warp; i < r1; i += nwarp) {
             const float* y = Y + (size_t)i * ldy;
@@ -106,24 +117,27 @@ __global__ void __launch_bounds__(kGaThreads, 1) ga_kernel(const GaParams P) {
             for (int j = lane; j < N; j += 32) z[j] = fmaxf(y[j] / s, kGaFloor);
         }
         __syncthreads();   // the block's Z rows are in before its column pass reads them
-        // the block's column partials, exact 64-bit integer sums
-        if (r1 > r0) {
-            for (int j = tid; j < N; j += nthr) {
-                unsigned long long c = 0ull;
-                for (int i = r0; i < r1; ++i) c += units_2m40(Z[(size_t)i * ldy + j]);
-                atomicAdd(a + j, c);
-            }
+        // the block's column partials, its rows in order
+        for (int j = tid; j < N; j += nthr) {
+            float c = 0.f;
+            for (int i = r0; i < r1; ++i) c += Z[(size_t)i * ldy + j];
+            part[(size_t)blockIdx.x * ldy + j] = c;
         }
         if (!grid_barrier(&C->bar, bar_base + G * (gen + 1), err, P.timeout_ns)) return;
         ++gen;
-        // every CTA converts the same sums the same way
-        for (int j = tid; j < N; j += nthr) cN[j] = (float)((double)__ldcg(a + j) * 0x1p-40);
-        // step k - 1's accumulators (the other parity) were read by every CTA
-        // before it arrived at this step's first barrier; step k + 1 adds to
-        // them after this step's second barrier, which these zeros precede
-        unsigned long long* other = acc + (size_t)(par ^ 1) * ldy;
-        for (int j = (int)blockIdx.x * nthr + tid; j < ldy; j += (int)G * nthr) other[j] = 0ull;
+        // this CTA's block of column sums, the CTAs' partials in order
+        for (int j = c0 + tid; j < c1; j += nthr) {
+            float c = 0.f;
+            for (unsigned g = 0; g < G; ++g) c += __ldcg(part + (size_t)g * ldy + j);
+            csum[j] = c;
+        }
+        // step k - 1's maximum (the other parity) was read by every CTA before
+        // it arrived at this step's first barrier; step k + 1 raises it after
+        // this step's third barrier, which this zero precedes
         if (blockIdx.x == 0 && tid == 0) dmax[par ^ 1] = 0u;
+        if (!grid_barrier(&C->bar, bar_base + G * (gen + 1), err, P.timeout_ns)) return;
+        ++gen;
+        for (int j = tid; j < N; j += nthr) cN[j] = __ldcg(csum + j);
         __syncthreads();
         // columns to unit sums (Z -> Y) and the step's max|dY|
         float dm = 0.f;
@@ -165,12 +179,12 @@ __global__ void __launch_bounds__(kGaThreads, 1) ga_kernel(const GaParams P) {
     if (!grid_barrier(&C->bar, bar_base + G * (gen + 1), err, P.timeout_ns)) return;
     ++gen;
 
-    // ---- no CTA reads the accumulators any more: zero them for the next
-    // launch; loop control of Algorithm 1's repeat loop (CTA 0)
-    for (int j = (int)blockIdx.x * nthr + tid; j < 2 * ldy; j += (int)G * nthr) acc[j] = 0ull;
+    // ---- no CTA reads the maxima any more: zero them for the next launch;
+    // loop control of Algorithm 1's repeat loop (CTA 0)
     if (blockIdx.x == 0 && tid == 0) {
         dmax[0] = 0u;
         dmax[1] = 0u;
+        dmax[2] = 0u;
         const double d = __longlong_as_double((long long)__ldcg(&C->dx_bits));
         if (!isfinite(d)) atomicCAS(err, 0, FASTPFP_ERR_NONFINITE);
         C->dx_bits = 0ull;

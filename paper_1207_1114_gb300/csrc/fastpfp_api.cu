@@ -660,17 +660,17 @@ int enqueue_ga(fastpfp_t h, cudaStream_t s, const Slot& sl, const Problem& q, co
     const int slot = (int)(&sl - h->slots.data());
     TcPlan tc;
     if (!simt_of(p) && !plan_split(h, &q, 1, p, &tc, &slot)) return FASTPFP_ERR_UNSUPPORTED;
-    if (!h->ga_z) FP_CUDA(cudaMalloc(&h->ga_z, (size_t)h->max_n * round4(h->max_n) * sizeof(float)));
+    // scratch: Z (max_n x ld), the CTAs' column partials (num_sms x ld), the column sums (ld)
+    const size_t ld = (size_t)round4(h->max_n);
+    if (!h->ga_z) FP_CUDA(cudaMalloc(&h->ga_z, ((size_t)h->max_n + h->num_sms + 1) * ld * sizeof(float)));
     int nl = enqueue_setup(sl, s, q, p, h->ld);
     if (nl < 0) return nl;
-    // the slot's column-sum buffer holds the two integer accumulators: 16
-    // bytes per column of the 20 it has
-    static_assert(2 * sizeof(unsigned long long) <= 3 * sizeof(float) + sizeof(double), "acc in colbuf");
     GaParams P{};
     P.Y = sl.Y;
     P.Z = h->ga_z;
     P.X = sl.X;
-    P.acc = reinterpret_cast<unsigned long long*>(sl.colbuf);
+    P.part = h->ga_z + (size_t)h->max_n * ld;
+    P.csum = P.part + (size_t)h->num_sms * ld;
     P.dbuf = sl.dbuf;
     P.ctrl = sl.ctrl;
     P.N = N;
@@ -956,7 +956,7 @@ void fastpfp_default_params(fastpfp_params* p) {
     p->loop_mode = 0;
     p->debug_flags = 0;
     p->algorithm = FASTPFP_ALG_FASTPFP;
-    p->beta = 10.f;
+    p->beta = 100.f;
 }
 
 const char* fastpfp_error_string(int code) {

@@ -270,8 +270,9 @@ struct GaParams {
     float* Y;                 // N x ldy: the products in columns 0..m-1, then Y of the normalisation
     float* Z;                 // N x ldy scratch (rows normalised)
     float* X;                 // N x ldx master X
-    unsigned long long* acc;  // 2 x ldy column sums in units of 2^-40 (zero between launches)
-    unsigned* dbuf;           // 2 words: a step's max|dY| (zero between launches)
+    float* part;              // (grid) x ldy scratch: the CTAs' column partials
+    float* csum;              // ldy scratch: column sums
+    unsigned* dbuf;           // 3 words: a step's max|dY| by parity, max|Q| (zero between launches)
     Ctrl* ctrl;
     int N, m, ldy, ldx, rpc;
     float beta;

@@ -4,8 +4,10 @@
   from 100 to 1500, matched in four cases (isomorphic; n edge editions; 10 %
   node deletion; both).  Each row records the runtime of one solve and the
   matching error ||A - X A' X^T||_F^2 - ||A - X_GT A' X_GT^T||_F^2 of the
-  discrete result, for FastPFP (alpha = 0.5) and the projected gradient
-  method of Eq. (pg) (step 1 / L, L = ||A||_2 ||A'||_2).
+  discrete result, for FastPFP (alpha = 0.5), the projected gradient
+  method of Eq. (pg) (step 1 / L, L = ||A||_2 ||A'||_2) and FastGA
+  (Appendix; fixed beta on Q / max|Q|, default 100), the paper's three
+  O(n^3) methods.
 * ``alpha``: Section 6's step-size sensitivity — FastPFP on attributed
   n = 1000 pairs for alpha from 0.1 to 1: outer iterations, runtime,
   accuracy and objective.
@@ -75,8 +77,8 @@ def _solve_timed(solver, g, params, dev, want_X=False):
     return r, time.perf_counter() - t0
 
 
-def e1_sweep(sizes=E1_SIZES, cases="abcd", seeds=(0,), algorithms=("fastpfp", "pg"), device: int = 0,
-             max_outer: int = 100, max_inner: int = 1000, detail: bool = False):
+def e1_sweep(sizes=E1_SIZES, cases="abcd", seeds=(0,), algorithms=("fastpfp", "pg", "fastga"), device: int = 0,
+             max_outer: int = 100, max_inner: int = 1000, detail: bool = False, beta: float = 100.0):
     """Rows of the Section 5.1 sweep (one per size, case, seed, algorithm).
     detail: each row also carries the solve's permutation, its inner-count
     trace, its soft assignment X and its parameters (for checking against
@@ -95,6 +97,10 @@ def e1_sweep(sizes=E1_SIZES, cases="abcd", seeds=(0,), algorithms=("fastpfp", "p
                         if alg == "pg":
                             alpha = lipschitz_step(g.A, g.A2)
                             p = F.default_params(lam=0.0, alpha=alpha, algorithm=F.ALG_PG, normalize_max=0,
+                                                 max_outer=max_outer, max_inner=max_inner)
+                        elif alg == "fastga":
+                            alpha = float("nan")   # no step size: the soft-assignment replaces X
+                            p = F.default_params(lam=0.0, algorithm=F.ALG_FASTGA, beta=beta,
                                                  max_outer=max_outer, max_inner=max_inner)
                         else:
                             alpha = 0.5

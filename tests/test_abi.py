@@ -50,7 +50,7 @@ def test_default_params_and_error_strings(built):
     assert p.alpha == 0.5 and p.max_outer == 100 and p.max_inner == 1000
     assert p.tol_outer == 1e-6 and p.tol_inner == 1e-6 and p.normalize_max == 1
     assert p.slack_policy == 0 and p.precision == F.FP32 and p.debug_flags == 0
-    assert p.algorithm == F.ALG_FASTPFP and p.beta == 10.0
+    assert p.algorithm == F.ALG_FASTPFP and p.beta == 100.0
     for code in (0, -1, -2, -3, -4, -5, -6):
         assert F.error_string(code) != "unknown error"
 

@@ -18,6 +18,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 import oracle
+from oracle import fastga as oracle_fastga
 from paper_1207_1114_gb300 import experiments, synth
 
 pytestmark = pytest.mark.gpu
@@ -52,7 +53,8 @@ def test_e1_rows_match_the_oracle():
     and the projected gradient method) against the oracle replaying the
     GPU's counts; the oracle's free run gives the same matching error when
     both converge."""
-    rows = experiments.e1_sweep(sizes=(100, 160), cases="abcd", max_outer=60, max_inner=400, detail=True)
+    rows = experiments.e1_sweep(sizes=(100, 160), cases="abcd", algorithms=("fastpfp", "pg"), max_outer=60,
+                                max_inner=400, detail=True)
     assert len(rows) == 16
     for r in rows:
         g = synth.e1_pair(r["n"], r["case"], seed=r["seed"])
@@ -65,6 +67,22 @@ def test_e1_rows_match_the_oracle():
     # the paper's observation on isomorphic graphs: FastPFP recovers them
     for r in rows:
         if r["case"] == "a" and r["algorithm"] == "fastpfp":
+            assert r["error"] == 0.0 and r["accuracy"] == 1.0
+
+
+def test_e1_fastga_rows_match_the_oracle():
+    """FastGA's rows of the E1 sweep (n = 100, cases a-d) against the FastGA
+    oracle replaying the GPU's inner counts (X max-abs 1e-4, the same
+    permutation); the isomorphic case is recovered."""
+    rows = experiments.e1_sweep(sizes=(100,), cases="abcd", algorithms=("fastga",), max_outer=60,
+                                max_inner=400, detail=True)
+    assert len(rows) == 4
+    for r in rows:
+        g = synth.e1_pair(r["n"], r["case"], seed=r["seed"])
+        rep = oracle_fastga.solve(g.A, g.A2, max_outer=r["outer"], max_inner=400, replay_inner=r["inner"])
+        assert np.abs(r["X"] - rep["X"]).max() <= 1e-4
+        np.testing.assert_array_equal(r["perm"], rep["perm"])
+        if r["case"] == "a":
             assert r["error"] == 0.0 and r["accuracy"] == 1.0
 
 

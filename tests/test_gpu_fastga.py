@@ -2,9 +2,9 @@
 oracle (oracle/fastga.py).
 
 Tolerances.  The products are FP32 (|err| <~ 3e-5 of |A||X||A'|, the
-split-TF32 bound), so beta Q carries ~1e-4 absolute error at beta = 10 and
-Q ~ 3; exp turns it into ~1e-4 relative error of Y(0), which the
-normalisation keeps relative.  X entries are at most 1, so X is compared at
+split-TF32 bound), so beta Q / max|Q| carries up to ~3e-3 absolute error at
+beta = 100; exp turns it into that relative error of Y(0) at worst, which
+the normalisation keeps relative (typical errors are ~100 times smaller).  X entries are at most 1, so X is compared at
 the FP32 X bound of FastPFP's tests, max-abs 1e-4, after a few replayed
 outer iterations (errors do not grow: each outer iteration starts from the
 normalised soft assignment; measured on GB300 ~2e-6), with the GPU's inner
@@ -41,7 +41,7 @@ def solver():
 
 
 def ga_params(**kw):
-    base = dict(algorithm=F.ALG_FASTGA, beta=10.0, max_outer=100, max_inner=1000)
+    base = dict(algorithm=F.ALG_FASTGA, beta=100.0, max_outer=100, max_inner=1000)
     base.update(kw)
     return F.default_params(**base)
 
@@ -63,7 +63,7 @@ def test_fastga_matches_oracle_replay(solver, case, precision):
     inner, _ = solver.last_trace()
     t = r.stats.outer_iters
     assert 1 <= t <= 5 and (inner[:t] >= 1).all()
-    ref = oga.solve(A, A2, B if g.k else None, B2 if g.k else None, lam=g.lam, beta=10.0,
+    ref = oga.solve(A, A2, B if g.k else None, B2 if g.k else None, lam=g.lam, beta=100.0,
                     max_outer=t, max_inner=400, replay_inner=inner[:t])
     X = r.X.cpu().numpy()
     err = np.abs(X - ref["X"]).max()
@@ -78,7 +78,7 @@ def test_fastga_free_run_recovers_the_ground_truth_like_the_oracle(solver):
     for seed in range(3):
         g = synth.graph_pair(80, p=0.3, sigma=0.0, k=0, seed=seed)
         r = solver.match(*dev_pair(g), params=ga_params())
-        ref = oga.solve(g.A, g.A2, beta=10.0)
+        ref = oga.solve(g.A, g.A2, beta=100.0)
         perm = r.perm.cpu().numpy()
         np.testing.assert_array_equal(ref["perm"], g.gt)
         np.testing.assert_array_equal(perm, g.gt)
