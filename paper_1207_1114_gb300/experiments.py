@@ -11,11 +11,15 @@
 * ``alpha``: Section 6's step-size sensitivity — FastPFP on attributed
   n = 1000 pairs for alpha from 0.1 to 1: outer iterations, runtime,
   accuracy and objective.
+* ``wave``: one wave of attributed pairs (one batched call, outer loop
+  enqueued by the host so every kernel is a plain launch): the small,
+  fixed case the kernel profiles are captured on.
 
 Usage::
 
     python -m paper_1207_1114_gb300.experiments e1 [--sizes 100,300,...] [--json out.json]
     python -m paper_1207_1114_gb300.experiments alpha [--seeds 0,1,2] [--json out.json]
+    python -m paper_1207_1114_gb300.experiments wave [--pairs 17] [--n 1000] [--max-outer 1]
 
 Every solve runs on the CUDA path (``Solver.match``); the host only draws
 the inputs (``synth``) and scores the discrete results.
@@ -147,6 +151,27 @@ def alpha_sweep(alphas=ALPHAS, seeds=(0, 1, 2), device: int = 0, n: int = 1000, 
     return rows
 
 
+def wave(pairs: int = 17, n: int = 1000, max_outer: int = 1, precision: str = "fp32", device: int = 0):
+    """One batched solve of `pairs` attributed n-node pairs (seeds 0..) with
+    the host-enqueued outer loop and at most max_outer outer iterations;
+    returns (seconds, stats of pair 0)."""
+    import torch
+    dev = torch.device("cuda", device)
+    prec = {"fp32": F.FP32, "bf16": F.BF16, "fp8": F.FP8, "fp32_simt": F.FP32_SIMT}[precision]
+    solver = F.Solver(max_n=n, max_batch=pairs, device=device)
+    try:
+        gs = [synth.attributed_1000(seed=i, n=n) for i in range(pairs)]
+        d = [tuple(torch.as_tensor(a, device=dev) for a in (g.A, g.A2, g.B, g.B2)) for g in gs]
+        p = F.default_params(lam=gs[0].lam, max_outer=max_outer, loop_mode=1, precision=prec)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        out = solver.match_batched(d, params=p)
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t0, out[0].stats
+    finally:
+        solver.close()
+
+
 def _table(rows, keys):
     out = ["| " + " | ".join(keys) + " |", "|" + "---|" * len(keys)]
     for r in rows:
@@ -156,7 +181,11 @@ def _table(rows, keys):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("which", choices=["e1", "alpha"])
+    ap.add_argument("which", choices=["e1", "alpha", "wave"])
+    ap.add_argument("--pairs", type=int, default=17)
+    ap.add_argument("--n", type=int, default=1000)
+    ap.add_argument("--max-outer", type=int, default=1, dest="max_outer")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8", "fp32_simt"])
     ap.add_argument("--sizes", default=",".join(map(str, E1_SIZES)))
     ap.add_argument("--cases", default="abcd")
     ap.add_argument("--seeds", default="0")
@@ -164,6 +193,11 @@ def main(argv=None):
     ap.add_argument("--json", default=None, help="also write the rows to this file")
     a = ap.parse_args(argv)
     seeds = tuple(int(s) for s in a.seeds.split(","))
+    if a.which == "wave":
+        sec, st = wave(a.pairs, a.n, a.max_outer, a.precision, device=a.device)
+        print(f"wave of {a.pairs} pairs of n = {a.n}: {sec * 1e3:.1f} ms, outer {st.outer_iters}, "
+              f"inner {st.inner_iters_total}, wave_pairs {st.wave_pairs}")
+        return
     if a.which == "e1":
         rows = e1_sweep(tuple(int(s) for s in a.sizes.split(",")), a.cases, seeds, device=a.device)
         print(_table(rows, ["n", "case", "algorithm", "seconds", "outer", "converged", "error", "accuracy"]))

@@ -793,13 +793,15 @@ def test_pg_bf16_phase_then_fp32_refinement(solver):
 
 
 def test_e1_sweep_recovers_isomorphisms():
-    """The Section 5.1 driver on small graphs: FastPFP finds the hidden
-    isomorphism (case a: zero error, accuracy 1) and every row is complete."""
+    """The Section 5.1 driver on small graphs (FastPFP, PG and FastGA):
+    FastPFP and FastGA find the hidden isomorphism (case a: zero error,
+    accuracy 1) and every row is complete."""
     from paper_1207_1114_gb300 import experiments
     rows = experiments.e1_sweep(sizes=(60,), cases="abcd", max_outer=60, max_inner=400)
-    assert len(rows) == 8
-    a = [r for r in rows if r["case"] == "a" and r["algorithm"] == "fastpfp"][0]
-    assert a["error"] == 0.0 and a["accuracy"] == 1.0
+    assert len(rows) == 12
+    for alg in ("fastpfp", "fastga"):
+        a = [r for r in rows if r["case"] == "a" and r["algorithm"] == alg][0]
+        assert a["error"] == 0.0 and a["accuracy"] == 1.0
     for r in rows:
         assert r["seconds"] > 0 and r["outer"] >= 1
 
