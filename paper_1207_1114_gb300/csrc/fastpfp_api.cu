@@ -1232,17 +1232,37 @@ namespace {
 // and the outputs copied back before the next wave).
 // Host-memory inputs of pair x staged into `slot`; *q is rewritten to
 // point at the staged copies (caller orientation preserved).
+// One host input buffer into the device: appended to `L` (copied later by
+// one gather kernel, see gather_copy) when the GPU can read it in place --
+// pinned host memory with a device address, 16-byte aligned, the list not
+// full -- otherwise an ordinary copy on the stream (pageable memory).
+int stage_copy(CopyList* L, void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (L && L->count < kMaxCopySegs && bytes % 4 == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, src) == cudaSuccess && a.type == cudaMemoryTypeHost &&
+            a.devicePointer && (reinterpret_cast<uintptr_t>(a.devicePointer) & 15) == 0) {
+            L->seg[L->count++] = CopySeg{a.devicePointer, dst, (unsigned long long)bytes};
+            return 0;
+        }
+        cudaGetLastError();   // a pageable pointer is not an error
+    }
+    FP_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+    return 0;
+}
+
+// The pair's host inputs into its slot's staging buffers (through `L` when
+// given: the caller launches gather_copy before anything reads them).
 int stage_in(fastpfp_t h, cudaStream_t s, const fastpfp_pair& x, const fastpfp_params* p, int slot,
-             Problem* q) {
+             Problem* q, CopyList* L = nullptr) {
     const Slot& sl = h->slots[slot];
     const int kk = (x.k > 0 && p->lambda != 0.f) ? x.k : 0;
-    FP_CUDA(cudaMemcpyAsync(sl.sA, x.A, (size_t)x.n_a * x.n_a * 4, cudaMemcpyHostToDevice, s));
-    FP_CUDA(cudaMemcpyAsync(sl.sA2, x.A2, (size_t)x.n_b * x.n_b * 4, cudaMemcpyHostToDevice, s));
-    if (kk) {
-        FP_CUDA(cudaMemcpyAsync(sl.sB, x.B, (size_t)x.n_a * kk * 4, cudaMemcpyHostToDevice, s));
-        FP_CUDA(cudaMemcpyAsync(sl.sB2, x.B2, (size_t)x.n_b * kk * 4, cudaMemcpyHostToDevice, s));
-    }
-    if (x.X0) FP_CUDA(cudaMemcpyAsync(sl.sX0, x.X0, (size_t)x.n_a * x.n_b * 4, cudaMemcpyHostToDevice, s));
+    if (stage_copy(L, sl.sA, x.A, (size_t)x.n_a * x.n_a * 4, s) < 0 ||
+        stage_copy(L, sl.sA2, x.A2, (size_t)x.n_b * x.n_b * 4, s) < 0)
+        return FASTPFP_ERR_CUDA;
+    if (kk && (stage_copy(L, sl.sB, x.B, (size_t)x.n_a * kk * 4, s) < 0 ||
+               stage_copy(L, sl.sB2, x.B2, (size_t)x.n_b * kk * 4, s) < 0))
+        return FASTPFP_ERR_CUDA;
+    if (x.X0 && stage_copy(L, sl.sX0, x.X0, (size_t)x.n_a * x.n_b * 4, s) < 0) return FASTPFP_ERR_CUDA;
     *q = canonical(sl.sA, x.n_a, sl.sA2, x.n_b, kk ? sl.sB : nullptr, kk ? sl.sB2 : nullptr, kk, p->lambda,
                    x.X0 ? sl.sX0 : nullptr, sl.sperm, x.X_out ? sl.sXout : nullptr);
     return 0;
@@ -1276,11 +1296,20 @@ int solve_graph_stream(fastpfp_t h, cudaStream_t s, std::vector<Problem>& qs, co
         release_graphs(h);
         return code;
     };
-    for (int i = 0; i < count; ++i) {
-        if (host) {
-            const int r = stage_in(h, s, pairs[i], p, i, &qs[i]);
+    if (host) {   // every pair's inputs, pinned ones by one gather launch
+        CopyList L;
+        L.count = 0;
+        for (int i = 0; i < count; ++i) {
+            if (L.count + 5 > kMaxCopySegs) {
+                FP_CUDA(gather_copy(L, s));
+                L.count = 0;
+            }
+            const int r = stage_in(h, s, pairs[i], p, i, &qs[i], &L);
             if (r < 0) return fail(r);
         }
+        FP_CUDA(gather_copy(L, s));
+    }
+    for (int i = 0; i < count; ++i) {
         const int r = enqueue_setup(h->slots[i], s, qs[i], p, h->ld);
         if (r < 0) return fail(r);
         nl += r;
@@ -1634,11 +1663,19 @@ int solve_batch(fastpfp_t h, cudaStream_t s, int count, const fastpfp_pair* pair
         return graph_streamable(h, qs, p) ? solve_graph_stream(h, s, qs, pairs, p, st, host)
                                           : solve_stream(h, s, qs, pairs, p, st, host);
     const int cnt = batched ? w.count : 1;
-    if (host)
+    if (host) {   // pinned inputs by one gather launch
+        CopyList L;
+        L.count = 0;
         for (int i = 0; i < cnt; ++i) {
-            const int r = stage_in(h, s, pairs[i], p, i, &qs[i]);
+            if (L.count + 5 > kMaxCopySegs) {
+                FP_CUDA(gather_copy(L, s));
+                L.count = 0;
+            }
+            const int r = stage_in(h, s, pairs[i], p, i, &qs[i], &L);
             if (r < 0) return r;
         }
+        FP_CUDA(gather_copy(L, s));
+    }
     int nl = batched ? enqueue_wave(h, s, qs, w, p, h->host_ctrl)
                      : enqueue_single(h, s, h->slots[0], qs[0], p, &h->host_ctrl[0]);
     if (nl >= 0 && !batched) {

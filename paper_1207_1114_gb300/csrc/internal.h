@@ -436,6 +436,25 @@ struct SplitGroup {
 };
 cudaError_t split_tf32_group(const SplitGroup& g, cudaStream_t s);
 
+// Host-to-device staging of a batch by one kernel: pinned host memory is
+// addressable by the GPU (over NVLink-C2C on this part), and one launch
+// reading every input buffer of a batch runs at the link's rate, where a
+// separate DMA copy per buffer of a few MB pays a fixed cost apiece (measured
+// on GB300: 520 MB in 256 copies 30.5 ms, one 512 MB copy 2.6 ms).  Every
+// segment's source and destination are 16-byte aligned device addresses and
+// its size a multiple of 4 bytes.
+constexpr int kMaxCopySegs = 640;
+struct CopySeg {
+    const void* src;
+    void* dst;
+    unsigned long long bytes;
+};
+struct CopyList {
+    CopySeg seg[kMaxCopySegs];
+    int count;
+};
+cudaError_t gather_copy(const CopyList& L, cudaStream_t s);
+
 // Caller-orientation outputs from the canonical result.
 cudaError_t write_outputs(const int32_t* row_of_col, int N, int m, int transposed, int32_t* perm_out,
                           const float* X, int ldx, float* X_out, cudaStream_t s);

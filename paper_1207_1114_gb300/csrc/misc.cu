@@ -273,6 +273,39 @@ inline int grid_for(size_t total, int block, int cap = 4096) {
 
 }  // namespace
 
+// Segment blockIdx.y of the list, 16 bytes per thread and step (four in
+// flight), the last bytes of a size that is not a multiple of 16 in words.
+constexpr int kCopyThreads = 256, kCopyBlocksPerSeg = 16;
+__global__ void __launch_bounds__(kCopyThreads) gather_copy_kernel(const __grid_constant__ CopyList L) {
+    const CopySeg sg = L.seg[blockIdx.y];
+    const size_t n16 = sg.bytes / 16;
+    const float4* src = reinterpret_cast<const float4*>(sg.src);
+    float4* dst = reinterpret_cast<float4*>(sg.dst);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n16; i += 4 * stride) {
+        const float4 a = src[i], b = src[i + stride], c = src[i + 2 * stride], d = src[i + 3 * stride];
+        dst[i] = a;
+        dst[i + stride] = b;
+        dst[i + 2 * stride] = c;
+        dst[i + 3 * stride] = d;
+    }
+    for (; i < n16; i += stride) dst[i] = src[i];
+    if (blockIdx.x == 0) {
+        const size_t w0 = n16 * 4, nw = sg.bytes / 4;
+        const float* s4 = reinterpret_cast<const float*>(sg.src);
+        float* d4 = reinterpret_cast<float*>(sg.dst);
+        for (size_t w = w0 + threadIdx.x; w < nw; w += blockDim.x) d4[w] = s4[w];
+    }
+}
+
+cudaError_t gather_copy(const CopyList& L, cudaStream_t s) {
+    if (L.count <= 0) return cudaSuccess;
+    if (L.count > kMaxCopySegs) return cudaErrorInvalidValue;
+    gather_copy_kernel<<<dim3(kCopyBlocksPerSeg, L.count), kCopyThreads, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
 cudaError_t init_ctrl(Ctrl* c, int lowp, cudaStream_t s) {
     init_ctrl_kernel<<<1, 1, 0, s>>>(c, lowp);
     return cudaGetLastError();

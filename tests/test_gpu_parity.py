@@ -269,6 +269,30 @@ def test_batched_host_entry_point_equals_device_batch(solver):
         _same_solve(a, b, a.X.cpu().numpy(), b.X)
 
 
+@pytest.mark.parametrize("count", [3, 24])
+def test_pinned_host_inputs_gathered_by_one_kernel_equal_device_batch(count):
+    """Pinned host inputs are read in place by one gather kernel (pageable
+    ones are copied as before); a batch mixing both — one wave (3 pairs) and
+    a streamed batch (24 pairs, the graph path) — gives what the device entry
+    point gives on the same pairs, bit for bit, including odd sizes whose
+    byte counts are not multiples of 16."""
+    pairs = synth.batch_mixed(count=count, seed=31 + count, n_lo=41, n_hi=333, out_hi=17)
+    p = F.default_params(lam=0.5, max_outer=12, max_inner=200)
+    solver = F.Solver(max_n=350, max_batch=count)
+    dev = [(cu(g.A), cu(g.A2), cu(g.B), cu(g.B2)) for g in pairs]
+    d = solver.match_batched(dev, params=p, want_X=True)
+    host = []
+    for i, g in enumerate(pairs):
+        arrs = (g.A, g.A2, g.B, g.B2)
+        if i % 3 != 2:   # two of every three pairs pinned, the third pageable
+            arrs = tuple(torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).pin_memory() for a in arrs)
+        host.append(arrs)
+    h = solver.match_batched_host(host, params=p, want_X=True)
+    solver.close()
+    for a, b in zip(d, h):
+        _same_solve(a, b, a.X.cpu().numpy(), b.X)
+
+
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_graph_loop_equals_host_loop_single(solver, precision):
     """Algorithm 1's repeat loop as a CUDA-graph while node (loop_mode 0)
