@@ -115,17 +115,34 @@ __host__ __device__ inline int cut_rows(const int* Ns, int count, long long C, l
     return rows_in > 0 || b == 0 ? b + 1 : b;
 }
 
-// The search interval of the smallest band cost bound: every row fits in a
-// band ([lo]), one band holds everything ([hi]).
-__host__ __device__ inline void cut_interval(const int* Ns, int count, long long seg_cost, long long* lo,
+// The search interval [lo, hi] of the smallest band cost bound that fits
+// Gmax bands.  lo: every row fits in a band alone (seg + its row length),
+// and no bound below (E + count seg) / Gmax fits -- with no row costing more
+// than the bound every band costs at most it, and the bands together cost at
+// least the entries E plus one segment cost per pair.  hi: one band holding
+// everything, or, if smaller, (E + (count + Gmax) seg) / Gmax + seg + the
+// longest row, which always fits -- every band the greedy closes costs more
+// than the bound less one row and its segment, and Gmax such bands would
+// cost more than the cut's at most E + (count + Gmax) seg.  Since the band
+// count never grows with the bound, the smallest fitting bound in [lo, hi]
+// is the smallest at or above the row lower bound: the interval only saves
+// search rounds.
+__host__ __device__ inline void cut_interval(const int* Ns, int count, long long seg_cost, int Gmax, long long* lo,
                                              long long* hi) {
-    *lo = 1;
-    *hi = 0;
+    long long rowmax = 1, E = 0, ldymax = 0;
     for (int i = 0; i < count; ++i) {
         const long long ldy = bp_round4(Ns[i]);
-        if (seg_cost + ldy > *lo) *lo = seg_cost + ldy;
-        *hi += (long long)Ns[i] * ldy + seg_cost;
+        if (seg_cost + ldy > rowmax) rowmax = seg_cost + ldy;
+        if (ldy > ldymax) ldymax = ldy;
+        E += (long long)Ns[i] * ldy;
     }
+    const long long g = Gmax > 0 ? Gmax : 1;
+    const long long all = E + (long long)count * seg_cost;   // one band holds everything
+    const long long avg = (E + (long long)count * seg_cost + g - 1) / g;
+    *lo = rowmax > avg ? rowmax : avg;
+    long long h = (E + ((long long)count + g) * seg_cost + g - 1) / g + seg_cost + ldymax;
+    if (h > all) h = all;
+    *hi = h > *lo ? h : *lo;
 }
 
 // A planned wave: `grid` CTAs (bands), their row boundaries (band[grid] =
@@ -239,7 +256,7 @@ inline bool plan_bands_seq(const int* Ns, int count, int num_sms, int max_level,
     for (int lv = 0; lv <= max_level && lv < 4; ++lv) {
         const long long seg_cost = seg_cost_of_level(lv);
         long long lo, hi;
-        cut_interval(Ns, count, seg_cost, &lo, &hi);
+        cut_interval(Ns, count, seg_cost, Gmax, &lo, &hi);
         while (lo < hi) {
             const long long mid = lo + (hi - lo) / 2;
             if (cut_rows(Ns, count, mid, seg_cost, Gmax, nullptr) <= Gmax) hi = mid;

@@ -43,7 +43,7 @@ struct PlanShared {
 __device__ long long search_bound(PlanShared& S, const int* Ns, int n, long long seg_cost, int Gmax) {
     const int tid = threadIdx.x;
     constexpr int nthr = kPlanThreads;   // the launch's block size (a power of two: shifts, not divisions)
-    if (tid == 0) cut_interval(Ns, n, seg_cost, &S.lo, &S.hi);
+    if (tid == 0) cut_interval(Ns, n, seg_cost, Gmax, &S.lo, &S.hi);
     __syncthreads();
     while (true) {
         const long long lo = S.lo, hi = S.hi;
@@ -126,10 +126,99 @@ __device__ bool plan_bands_par(PlanShared& S, const int* Ns, int n, int num_sms,
     return S.ok != 0;
 }
 
+// Admission candidates planned side by side: group g of kAdmitGroups (each
+// kPlanThreads / kAdmitGroups threads) plans the wave of the first n + g + 1
+// pairs of the list at the admission level -- the plans the sequential
+// admission loop would make one after another, so the first that does not
+// fit decides the same admissions.  Each group's search and finish are those
+// of plan_bands_par with fewer candidate bounds per round (the same
+// smallest bound: the band count never grows with the bound).
+constexpr int kAdmitGroups = 8;
+constexpr int kGroupThreads = kPlanThreads / kAdmitGroups;
+struct GroupPlan {
+    long long lo, hi;
+    int best, Gmax, t2, ok, G, live;
+    int mx[4];
+    int rp;
+    WavePlan w;
+};
+
+// Block-wide: groups 0..K-1 plan n + 1 .. n + K pairs at segment cost
+// seg_cost (S.pre must hold the prefix sums of S.Ns up to n + K).
+__device__ void plan_candidates(PlanShared& S, GroupPlan* gp, int n, int K, int num_sms, long long seg_cost) {
+    const int tid = threadIdx.x, g = tid / kGroupThreads, t = tid % kGroupThreads;
+    GroupPlan& P = gp[g];
+    const int cnt = n + g + 1;
+    if (t == 0) {
+        P.live = g < K;
+        P.ok = 0;
+        if (P.live) {
+            wave_shape(S.Ns, cnt, num_sms, &P.Gmax, &P.t2);
+            cut_interval(S.Ns, cnt, seg_cost, P.Gmax, &P.lo, &P.hi);
+        }
+    }
+    __syncthreads();
+    // the bound searches, all groups in step
+    while (__syncthreads_or(P.live && P.lo < P.hi)) {
+        const bool go = P.live && P.lo < P.hi;
+        const long long lo = P.lo, hi = P.hi;
+        if (go && t == 0) P.best = kGroupThreads;
+        __syncthreads();
+        if (go) {
+            const long long C = lo + ((hi - lo) * (long long)(t + 1)) / kGroupThreads;
+            if (cut_rows(S.Ns, cnt, C, seg_cost, P.Gmax, nullptr) <= P.Gmax) atomicMin(&P.best, t);
+        }
+        __syncthreads();
+        if (go && t == 0) {
+            const int b = P.best < kGroupThreads ? P.best : kGroupThreads - 1;   // hi always fits
+            P.hi = lo + ((hi - lo) * (long long)(b + 1)) / kGroupThreads;
+            P.lo = b == 0 ? lo : lo + ((hi - lo) * (long long)b) / kGroupThreads + 1;
+        }
+        __syncthreads();
+    }
+    // the cuts at the bounds found and their bands' statistics
+    if (P.live && t == 0) {
+        const int used = cut_rows(S.Ns, cnt, P.lo, seg_cost, P.Gmax, P.w.band);
+        for (int c = used; c <= P.Gmax; ++c) P.w.band[c] = S.pre[cnt];
+        P.G = used > 1 ? used : 1;
+        P.mx[0] = P.mx[1] = P.mx[2] = P.mx[3] = 0;
+        P.rp = 1;
+    }
+    __syncthreads();
+    if (P.live) {
+        for (int b = t; b < P.G; b += kGroupThreads) {
+            const int lo = P.w.band[b], hi = P.w.band[b + 1];
+            int a = 0, z = cnt - 1;   // the first pair whose rows end after lo
+            while (a < z) {
+                const int mid = (a + z) >> 1;
+                if (S.pre[mid + 1] > lo) z = mid; else a = mid + 1;
+            }
+            const BandStat st = band_stat(S.Ns, cnt, a, S.pre[a], lo, hi, P.t2);
+            atomicMax(&P.mx[0], st.rows);
+            atomicMax(&P.mx[1], st.cols);
+            atomicMax(&P.mx[2], st.elems);
+            atomicMax(&P.mx[3], st.segs);
+        }
+        for (int i = t; i < cnt; i += kGroupThreads)
+            atomicMax(&P.rp, pdb_row_warps(bp_round4(S.Ns[i]), kPdbThreads, P.t2));
+    }
+    __syncthreads();
+    if (P.live && t == 0) {
+        PdbLayout L{P.mx[0], P.mx[1], P.mx[2], P.rp, P.t2, P.mx[3] > 1 ? P.mx[3] : 1, cnt};
+        P.ok = layout_fits(&L, &P.w.smem) ? 1 : 0;
+        if (P.ok) {
+            P.w.grid = P.G;
+            P.w.layout = L;
+        }
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kPlanThreads, 1)
     wave_plan_kernel(StreamState* st, const PairDesc* tmpl, PairDesc* wave, int* band, WaveCtrl* W) {
     __shared__ PlanShared S;
-    __shared__ int s_first, s_err, s_nact, s_count, s_next, s_try, s_left;
+    __shared__ GroupPlan gp[kAdmitGroups];
+    __shared__ int s_first, s_err, s_nact, s_count, s_next, s_try, s_left, s_more;
     __shared__ int s_warp[kMaxWavePairs / 32];
     __shared__ int s_row0[kMaxWavePairs + 1];
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
@@ -180,30 +269,59 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
         __syncthreads();
     }
     // admit waiting pairs in batch order while the plan with the next one
-    // still fits: at the admission level once the wave has pairs, at any
-    // level for its first pair
+    // still fits: at the admission level once the wave has pairs (up to
+    // kAdmitGroups candidates planned at once), at any level for its first
+    // pair
     bool have = false;
     if (tid == 0) s_next = st->next;
     __syncthreads();
     while (true) {
         if (tid == 0) {
-            s_try = s_next < s_count && S.n < kMaxWavePairs && tmpl[s_next].N <= kPdbMaxN;
-            if (s_try) {
-                S.list[S.n] = s_next;
-                S.Ns[S.n] = tmpl[s_next].N;
+            int K = 0;
+            while (K < kAdmitGroups) {
+                const int j = s_next + K;
+                if (j >= s_count || S.n + K >= kMaxWavePairs || tmpl[j].N > kPdbMaxN) break;
+                S.list[S.n + K] = j;
+                S.Ns[S.n + K] = tmpl[j].N;
+                ++K;
             }
+            if (S.n == 0 && K > 1) K = 1;   // a wave's first pair alone (any level)
+            s_try = K;
+            S.pre[0] = 0;
+            for (int i = 0; i < S.n + K; ++i) S.pre[i + 1] = S.pre[i] + S.Ns[i];
         }
         __syncthreads();
-        if (!s_try) break;
-        const int lvl = S.n == 0 ? 3 : kAdmitLevel;
-        if (!plan_bands_par(S, S.Ns, S.n + 1, st->num_sms, lvl, &S.trial)) break;
+        const int K = s_try;
+        if (K == 0) break;
+        if (S.n == 0) {
+            if (!plan_bands_par(S, S.Ns, 1, st->num_sms, 3, &S.trial)) break;
+            if (tid == 0) {
+                S.plan = S.trial;
+                S.n = 1;
+                s_next += 1;
+            }
+            have = true;
+            __syncthreads();
+            continue;
+        }
+        plan_candidates(S, gp, S.n, K, st->num_sms, seg_cost_of_level(kAdmitLevel));
         if (tid == 0) {
-            S.plan = S.trial;
-            S.n += 1;
-            s_next += 1;
+            int f = 0;   // candidates that fit before the first that does not
+            while (f < K && gp[f].ok) ++f;
+            if (f > 0) {
+                S.plan = gp[f - 1].w;
+                S.n += f;
+                s_next += f;
+            }
+            s_more = f == K;
+            s_try = f;
         }
-        have = true;
         __syncthreads();
+        const int admitted = s_try;
+        const bool more = s_more != 0;
+        __syncthreads();   // read by every thread before the next round writes them
+        if (admitted > 0) have = true;
+        if (!more) break;
     }
     // no admission: the remaining pairs, at any level; if even that does not
     // fit, the longest prefix of them that does (the others wait)

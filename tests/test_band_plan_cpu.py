@@ -32,6 +32,32 @@ using namespace fpfp;
 int main(int argc, char** argv) {
     int mode = 0;
     if (scanf("%d", &mode) != 1) return 1;
+    if (mode == 2) {   // smallest fitting bound: from the row bound up to one band, and in cut_interval's interval
+        long long seg = 0;
+        int Gmax = 0, count = 0;
+        if (scanf("%lld %d %d", &seg, &Gmax, &count) != 3) return 1;
+        std::vector<int> Ns(count);
+        for (int& n : Ns) if (scanf("%d", &n) != 1) return 1;
+        long long lo = 1, hi = 0;
+        for (int i = 0; i < count; ++i) {
+            const long long ldy = bp_round4(Ns[i]);
+            if (seg + ldy > lo) lo = seg + ldy;
+            hi += (long long)Ns[i] * ldy + seg;
+        }
+        while (lo < hi) {
+            const long long mid = lo + (hi - lo) / 2;
+            if (cut_rows(Ns.data(), count, mid, seg, Gmax, nullptr) <= Gmax) hi = mid; else lo = mid + 1;
+        }
+        long long l2 = 0, h2 = 0;
+        cut_interval(Ns.data(), count, seg, Gmax, &l2, &h2);
+        const int hi_fits = cut_rows(Ns.data(), count, h2, seg, Gmax, nullptr) <= Gmax;
+        while (l2 < h2) {
+            const long long mid = l2 + (h2 - l2) / 2;
+            if (cut_rows(Ns.data(), count, mid, seg, Gmax, nullptr) <= Gmax) h2 = mid; else l2 = mid + 1;
+        }
+        printf("{\"wide\": %lld, \"narrow\": %lld, \"hi_fits\": %d}\n", lo, l2, hi_fits);
+        return 0;
+    }
     if (mode == 1) {   // one greedy cut: C seg max_bands count Ns...
         long long C = 0, seg = 0;
         int max_bands = 0, count = 0;
@@ -65,7 +91,7 @@ int main(int argc, char** argv) {
         for (int lv = 0; lv < 4; ++lv) {
             const long long seg = seg_cost_of_level(lv);
             long long lo, hi;
-            cut_interval(Ns.data(), count, seg, &lo, &hi);
+            cut_interval(Ns.data(), count, seg, Gmax, &lo, &hi);
             while (lo < hi) {
                 const long long mid = lo + (hi - lo) / 2;
                 if (cut_rows(Ns.data(), count, mid, seg, Gmax, nullptr) <= Gmax) hi = mid; else lo = mid + 1;
@@ -94,8 +120,10 @@ def planner():
     subprocess.run(["g++", "-std=c++17", "-O1", "-I", CSRC, "-I", CUDA_INC, "-I", os.path.join(ROOT, "include"),
                     src, "-o", exe], check=True)
 
-    def run(Ns, num_sms=152, level=3, cut=None):
-        if cut is not None:   # (C, seg_cost, max_bands): one greedy cut
+    def run(Ns, num_sms=152, level=3, cut=None, bound=None):
+        if bound is not None:   # (seg_cost, Gmax): the smallest fitting bound two ways
+            inp = "2 {} {} {} ".format(*bound, len(Ns)) + " ".join(map(str, Ns))
+        elif cut is not None:   # (C, seg_cost, max_bands): one greedy cut
             inp = "1 {} {} {} {} ".format(*cut, len(Ns)) + " ".join(map(str, Ns))
         else:
             inp = f"0 {num_sms} {level} {len(Ns)} " + " ".join(map(str, Ns))
@@ -191,3 +219,15 @@ def test_cut_matches_the_row_by_row_greedy(planner):
         assert got["used"] == want and got["counted"] == want, (Ns, C, seg, mb, got, want)
         if starts is not None:
             assert got["band"] == starts, (Ns, C, seg, mb)
+
+
+def test_search_interval_keeps_the_smallest_fitting_bound(planner):
+    """cut_interval's interval (a provable lower bound from the total cost, a
+    provable upper bound that always fits) gives the same smallest fitting
+    bound as the search from one row up to one band holding everything."""
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        Ns = list(rng.integers(1, 1100 if rng.random() < 0.5 else 300, size=rng.integers(1, 60)))
+        seg = int(rng.choice([0, 8192, 32768]))
+        r = planner(Ns, bound=(seg, int(rng.integers(1, 153))))
+        assert r["hi_fits"] == 1 and r["narrow"] == r["wide"], (Ns, seg, r)
