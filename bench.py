@@ -808,7 +808,14 @@ def main():
                                        f"cost-balanced partition (shard.partition)"),
             "accuracy": float(np.mean(accs)),
             "iterations": {"outer_per_pair": sum(s.outer_iters for s in flat_t) / len(flat_t),
-                           "inner_per_pair": sum(s.inner_iters_total for s in flat_t) / len(flat_t)},
+                           "inner_per_pair": sum(s.inner_iters_total for s in flat_t) / len(flat_t),
+                           # eps_2 = 1e-6 is rarely reached: the P_D rounds of an outer
+                           # iteration then run to the cap I_1 (the paper gives no I_1)
+                           "inner_per_outer": (sum(s.inner_iters_total for s in flat_t)
+                                               / max(1, sum(s.outer_iters for s in flat_t))),
+                           "inner_cap": SOLVER["max_inner"],
+                           "every_outer_at_inner_cap": all(s.inner_iters_total == s.outer_iters * SOLVER["max_inner"]
+                                                           for s in flat_t)},
             "phase_ms_instrumented": {"gemm": ms_gemm, "projection": ms_proj, "discretize": ms_disc},
             "roofline": {"kernel": f"{kernel} (projection rounds + blend)", "bound": bound,
                          "achieved": achieved, "peak": peak, "peak_kind": peak_kind,

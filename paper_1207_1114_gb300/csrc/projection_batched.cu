@@ -758,20 +758,8 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 if (mp.kq > 1 && mp.q0 + mp.QP < Q) add4(cp1, mp.q0 + mp.QP);
             }
         }
-        // the row sums of the segments, once every warp's partials are in
+        // every warp's partials are in (publish folds them)
         __syncthreads();
-        for (int si = 0; si < nseg; ++si) {
-            const Seg sg = S.seg[si];
-            const int pst = S.pstate[sg.pair];
-            if (!(pst & 1) || (pst & 2)) continue;
-            const int nw = pdb_row_warps(S.pair[sg.pair].ldy, nthr, Lay.two_quad_ties);
-            for (int r = tid; r < sg.nrows; r += nthr) {
-                const float* rpp = S.rowpart + (size_t)(sg.brow0 + r) * RPS;
-                float t = 0.f;
-                for (int w = 0; w < nw; ++w) t += rpp[w];
-                S.rsum[sg.brow0 + r] = t;
-            }
-        }
     };
 
     // Zero accumulator `which` of the wave's pairs with threads t of nt
@@ -805,22 +793,32 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         }
     };
 
-    // End of a pass: warps 0 and 1 publish the segments' totals and round
-    // maxima (alternate segments) while warps 2.. zero accumulator
+    // The row sum of band row r: its row group's per-warp partials, in order.
+    auto row_sum = [&](const Seg& sg, int nw, int r) {
+        const float* rpp = S.rowpart + (size_t)(sg.brow0 + r) * RPS;
+        float t = 0.f;
+        for (int w = 0; w < nw; ++w) t += rpp[w];
+        return t;
+    };
+
+    // End of a pass (every warp's partials in): warps 0 and 1 publish the
+    // segments' totals and round maxima (alternate segments) while warps
+    // 2.. fold the row sums for the next pass and zero accumulator
     // `clear_which` (>= 0) of the wave's pairs; all of it precedes the
     // arrival, so the zeros are visible before any CTA's next-round
-    // reductions.  A band's total (at most a few dozen FP32 row sums) is
-    // added in FP32 and accumulated over the CTAs in FP64.
+    // reductions.  A band's total (at most a few dozen FP32 row sums, each
+    // folded as the next pass's row sum is) is added in FP32 and accumulated
+    // over the CTAs in FP64.
     auto publish = [&](int cur, int clear_which) {
-        __syncthreads();
         if (tid == 0) S.ictl[4] = 0;   // the running-pair count of wait_post
         if (warp < 2) {
             for (int si = warp; si < nseg; si += 2) {
                 const Seg sg = S.seg[si];
                 const int pst = S.pstate[sg.pair];
                 if (!(pst & 1) || (pst & 2)) continue;
+                const int nw = pdb_row_warps(S.pair[sg.pair].ldy, nthr, Lay.two_quad_ties);
                 float sp = 0.f;
-                for (int r = lane; r < sg.nrows; r += 32) sp += S.rsum[sg.brow0 + r];
+                for (int r = lane; r < sg.nrows; r += 32) sp += row_sum(sg, nw, r);
                 sp = warp_sum(sp);
                 float bm = lane < (nthr >> 5) ? S.fred[si * 32 + lane] : 0.f;
                 bm = warp_max(bm);
@@ -830,8 +828,15 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                     if (bm > 0.f) atomicMax(pr.dbuf + cur, __float_as_uint(bm));
                 }
             }
-        } else if (clear_which >= 0) {
-            clear_acc(clear_which, tid - 64, nthr - 64);
+        } else {
+            for (int si = 0; si < nseg; ++si) {
+                const Seg sg = S.seg[si];
+                const int pst = S.pstate[sg.pair];
+                if (!(pst & 1) || (pst & 2)) continue;
+                const int nw = pdb_row_warps(S.pair[sg.pair].ldy, nthr, Lay.two_quad_ties);
+                for (int r = tid - 64; r < sg.nrows; r += nthr - 64) S.rsum[sg.brow0 + r] = row_sum(sg, nw, r);
+            }
+            if (clear_which >= 0) clear_acc(clear_which, tid - 64, nthr - 64);
         }
         if (skip_first) {   // fault-injection test: this arrival is lost
             skip_first = false;
