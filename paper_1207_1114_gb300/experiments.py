@@ -11,6 +11,10 @@
 * ``alpha``: Section 6's step-size sensitivity — FastPFP on attributed
   n = 1000 pairs for alpha from 0.1 to 1: outer iterations, runtime,
   accuracy and objective.
+* ``compare``: FastPFP, PG and FastGA on the same single pairs of the
+  synthetic workloads (plain weighted n = 300 and 1000, attributed n = 1000,
+  partial 1000 into 1200): time per solve, outer iterations, accuracy —
+  the paper's runtime comparisons (Sections 5.1-5.4) on synthetic inputs.
 * ``wave``: one wave of attributed pairs (one batched call, outer loop
   enqueued by the host so every kernel is a plain launch): the small,
   fixed case the kernel profiles are captured on.
@@ -19,6 +23,7 @@ Usage::
 
     python -m paper_1207_1114_gb300.experiments e1 [--sizes 100,300,...] [--json out.json]
     python -m paper_1207_1114_gb300.experiments alpha [--seeds 0,1,2] [--json out.json]
+    python -m paper_1207_1114_gb300.experiments compare [--seeds 0,1,2] [--json out.json]
     python -m paper_1207_1114_gb300.experiments wave [--pairs 17] [--n 1000] [--max-outer 1]
 
 Every solve runs on the CUDA path (``Solver.match``); the host only draws
@@ -151,6 +156,46 @@ def alpha_sweep(alphas=ALPHAS, seeds=(0, 1, 2), device: int = 0, n: int = 1000, 
     return rows
 
 
+COMPARE_CASES = (
+    ("plain_300", lambda seed: synth.graph_pair(300, p=0.3, sigma=0.02, k=0, seed=seed)),
+    ("plain_1000", lambda seed: synth.graph_pair(1000, p=0.1, sigma=0.02, k=0, seed=seed)),
+    ("attributed_1000", lambda seed: synth.attributed_1000(seed=seed)),
+    ("partial_1000_1200", lambda seed: synth.partial_1000_1200(seed=seed)),
+)
+
+
+def compare(seeds=(0,), device: int = 0, beta: float = 100.0, cases=COMPARE_CASES):
+    """Rows of the method comparison: one per case, seed and method (FastPFP
+    alpha = 0.5, PG with step 1/L, FastGA with the fixed beta), each a timed
+    single-pair solve after an untimed one."""
+    import torch
+    dev = torch.device("cuda", device)
+    solver = F.Solver(max_n=1200, max_batch=1, device=device)
+    rows = []
+    try:
+        for name, make in cases:
+            for seed in seeds:
+                g = make(seed)
+                for alg in ("fastpfp", "pg", "fastga"):
+                    if alg == "pg":
+                        p = F.default_params(lam=g.lam, alpha=lipschitz_step(g.A, g.A2), algorithm=F.ALG_PG,
+                                             normalize_max=0)
+                    elif alg == "fastga":
+                        p = F.default_params(lam=g.lam, algorithm=F.ALG_FASTGA, beta=beta)
+                    else:
+                        p = F.default_params(lam=g.lam)
+                    r, sec = _solve_timed(solver, g, p, dev)
+                    perm = r.perm.cpu().numpy()
+                    inl = g.gt >= 0
+                    rows.append(dict(case=name, seed=seed, algorithm=alg, seconds=sec,
+                                     outer=int(r.stats.outer_iters), inner=int(r.stats.inner_iters_total),
+                                     converged=bool(r.stats.converged), objective=float(r.stats.objective),
+                                     accuracy=float((perm[inl] == g.gt[inl]).mean())))
+    finally:
+        solver.close()
+    return rows
+
+
 def wave(pairs: int = 17, n: int = 1000, max_outer: int = 1, precision: str = "fp32", device: int = 0):
     """One batched solve of `pairs` attributed n-node pairs (seeds 0..) with
     the host-enqueued outer loop and at most max_outer outer iterations;
@@ -181,7 +226,7 @@ def _table(rows, keys):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("which", choices=["e1", "alpha", "wave"])
+    ap.add_argument("which", choices=["e1", "alpha", "wave", "compare"])
     ap.add_argument("--pairs", type=int, default=17)
     ap.add_argument("--n", type=int, default=1000)
     ap.add_argument("--max-outer", type=int, default=1, dest="max_outer")
@@ -197,6 +242,13 @@ def main(argv=None):
         sec, st = wave(a.pairs, a.n, a.max_outer, a.precision, device=a.device)
         print(f"wave of {a.pairs} pairs of n = {a.n}: {sec * 1e3:.1f} ms, outer {st.outer_iters}, "
               f"inner {st.inner_iters_total}, wave_pairs {st.wave_pairs}")
+        return
+    if a.which == "compare":
+        rows = compare(seeds=seeds, device=a.device)
+        print(_table(rows, ["case", "seed", "algorithm", "seconds", "outer", "inner", "converged", "accuracy"]))
+        if a.json:
+            with open(a.json, "w") as f:
+                json.dump(rows, f, indent=1)
         return
     if a.which == "e1":
         rows = e1_sweep(tuple(int(s) for s in a.sizes.split(",")), a.cases, seeds, device=a.device)

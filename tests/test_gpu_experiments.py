@@ -86,6 +86,19 @@ def test_e1_fastga_rows_match_the_oracle():
             assert r["error"] == 0.0 and r["accuracy"] == 1.0
 
 
+def test_method_comparison_rows():
+    """The comparison driver (FastPFP, PG, FastGA on the same single pairs):
+    every row complete; FastPFP and FastGA recover a noisy plain 300-node
+    pair."""
+    cases = (("plain_300", lambda seed: synth.graph_pair(300, p=0.3, sigma=0.02, k=0, seed=seed)),)
+    rows = experiments.compare(seeds=(0,), cases=cases)
+    assert [r["algorithm"] for r in rows] == ["fastpfp", "pg", "fastga"]
+    for r in rows:
+        assert r["seconds"] > 0 and r["outer"] >= 1 and r["inner"] >= r["outer"]
+        if r["algorithm"] != "pg":
+            assert r["converged"] and r["accuracy"] == 1.0
+
+
 def test_alpha_sweep_rows_match_the_oracle():
     """Section 6's step-size sweep on attributed 200-node pairs: for every
     alpha the GPU's solve against the oracle's replay of its counts, and the
