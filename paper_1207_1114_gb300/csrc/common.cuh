@@ -73,6 +73,44 @@ __device__ __forceinline__ double warp_max_d(double v) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
+
+// --------------------------------------------------- exact max |v - x|
+// The maximum over elements of |v - x| rounded once to FP64 (what
+// fabs((double)v - (double)x) gives), with FP32 arithmetic per element: the
+// FP64 units of this part run at a small fraction of the FP32 rate.  Knuth's
+// TwoSum splits v - x exactly into s + t (s = fl(v - x), |t| <= ulp(s)/2);
+// then |v - x| = |s| + sign(s) t, and the pairs (|s|, sign(s) t) order like
+// the exact differences under lexicographic comparison (rounding is
+// monotone), so the running maximum is kept as a pair and rounded to FP64
+// once.  A difference that overflows FP32 (s or t not finite) takes the
+// FP64 path; NaN differences are ignored, as fmax ignores them.
+struct AbsDiffMax {
+    float hi = 0.f, lo = 0.f;   // the largest |v - x| so far, exactly hi + lo
+    double big = 0.0;           // the FP64 maximum of the differences FP32 cannot hold
+    __device__ __forceinline__ void add(float v, float x) {
+        const float s = v - x;
+        const float vr = s + x;            // TwoSum of v and -x
+        const float xr = s - vr;
+        const float t = (v - vr) - (x + xr);
+        const float as = fabsf(s), at = s < 0.f ? -t : t;
+        if (as > hi || (as == hi && at > lo)) {
+            if (isfinite(as) && isfinite(at)) {
+                hi = as;
+                lo = at;
+            } else {
+                big = fmax(big, fabs((double)v - (double)x));
+            }
+        }
+    }
+    __device__ __forceinline__ void add4(float4 v, float4 x) {
+        add(v.x, x.x);
+        add(v.y, x.y);
+        add(v.z, x.z);
+        add(v.w, x.w);
+    }
+    __device__ __forceinline__ double value() const { return fmax(big, (double)hi + (double)lo); }
+};
+
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

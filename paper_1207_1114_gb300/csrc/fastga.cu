@@ -164,17 +164,17 @@ __global__ void __launch_bounds__(kGaThreads, 1) ga_kernel(const GaParams P) {
     }
 
     // ---- X(t+1) = Y[:, :m] and max|dX| (FP64, like FastPFP's)
-    double dx = 0.0;
+    AbsDiffMax dxm;
     for (int i = r0 + warp; i < r1; i += nwarp) {
         const float* y = Y + (size_t)i * ldy;
         float* x = P.X + (size_t)i * ldx;
         for (int j = lane; j < ldx; j += 32) {
             const float v = j < m ? y[j] : 0.f;
-            dx = fmax(dx, fabs((double)v - (double)x[j]));
+            dxm.add(v, x[j]);
             x[j] = v;
         }
     }
-    dx = block_max_dbl(dx, s_dred);
+    const double dx = block_max_dbl(dxm.value(), s_dred);
     if (tid == 0 && r1 > r0) atomicMax(&C->dx_bits, (unsigned long long)__double_as_longlong(dx));
     if (!grid_barrier(&C->bar, bar_base + G * (gen + 1), err, P.timeout_ns)) return;
     ++gen;

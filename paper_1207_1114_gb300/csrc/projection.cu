@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
         ++gen;
         mx = ordered_to_float(__ldcg(&C->xmax_bits));
     }
-    double dx = 0.0;
+    AbsDiffMax dxm;   // max|dX| in FP64, as the oracle takes it
     const bool write16 = (P.Xt16 != nullptr);
     for (int rr = 0; rr < nr; ++rr) {
         const int i = r0 + rr;
@@ -451,8 +451,7 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
                                    beta * x.z + alpha * y.z, beta * x.w + alpha * y.w);
             if (P.normalize) { v.x /= mx; v.y /= mx; v.z /= mx; v.w /= mx; }
             v = mask_cols(v, q, m);
-            dx = fmax(dx, fmax(fmax(fabs((double)v.x - (double)x.x), fabs((double)v.y - (double)x.y)),
-                               fmax(fabs((double)v.z - (double)x.z), fabs((double)v.w - (double)x.w))));
+            dxm.add4(v, x);
             xr[q] = v;
             if (write16) {
                 const int c0 = 4 * q;
@@ -472,7 +471,7 @@ __global__ void __launch_bounds__(1024, 1) pd_kernel(const PdParams P) {
             for (int q = qs + tid; q < Q; q += nthr) dst[q] = src[q];
         }
     }
-    const double bdx = block_max_d(dx, S.dred);
+    const double bdx = block_max_d(dxm.value(), S.dred);
     if (tid == 0 && nr > 0) atomicMax(&C->dx_bits, (unsigned long long)__double_as_longlong(bdx));
     if (!grid_barrier(&C->bar, bar_base + G * (gen + 1), err, P.timeout_ns)) return;
     ++gen;

@@ -117,6 +117,11 @@ __device__ __forceinline__ Map make_map(int qpg, int rpkq, int tid) {
 // their update max(a_i - kPadB, -0) is -0 (finite: no infinity enters).
 constexpr float kPadB = 1.0e30f;
 
+// float4 loads of X and of Y each thread issues before it uses any in the
+// blend: with one CTA of 16 warps per SM, one load pair per thread leaves
+// the blend latency-bound far below the HBM rate.
+constexpr int kBlendLoads = 4;
+
 // Two-lane FP32 arithmetic (sm_100 packed f32x2): one instruction updates
 // two floats held in a register pair.
 __device__ __forceinline__ unsigned long long pk(float a, float b) {
@@ -992,14 +997,28 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             const float4* Yg = reinterpret_cast<const float4*>(d.Y) + (size_t)sg.lr0 * Qy;
             const float4* X = reinterpret_cast<const float4*>(d.X) + (size_t)sg.lr0 * Qx;
             float lmax = -INFINITY;
-            for (int e = tid; e < sg.nrows * Qx; e += nthr) {
-                const int r = e / Qx, q = e % Qx;
-                const float4 x = X[(size_t)r * Qx + q], y = Yg[(size_t)r * Qy + q];
-                const int c0 = 4 * q;
-                lmax = fmaxf(lmax, beta * x.x + alpha * y.x);
-                if (c0 + 1 < m) lmax = fmaxf(lmax, beta * x.y + alpha * y.y);
-                if (c0 + 2 < m) lmax = fmaxf(lmax, beta * x.z + alpha * y.z);
-                if (c0 + 3 < m) lmax = fmaxf(lmax, beta * x.w + alpha * y.w);
+            const int dr = nthr / Qx, dq = nthr % Qx;
+            int r = tid / Qx, q = tid % Qx;
+            while (r < sg.nrows) {
+                int qk[kBlendLoads];
+                float4 xk[kBlendLoads], yk[kBlendLoads];
+#pragma unroll
+                for (int k = 0; k < kBlendLoads; ++k) {
+                    qk[k] = r < sg.nrows ? q : -1;
+                    if (r < sg.nrows) { xk[k] = X[(size_t)r * Qx + q]; yk[k] = Yg[(size_t)r * Qy + q]; }
+                    r += dr; q += dq;
+                    if (q >= Qx) { q -= Qx; ++r; }
+                }
+#pragma unroll
+                for (int k = 0; k < kBlendLoads; ++k) {
+                    if (qk[k] < 0) break;
+                    const float4 x = xk[k], y = yk[k];
+                    const int c0 = 4 * qk[k];
+                    lmax = fmaxf(lmax, beta * x.x + alpha * y.x);
+                    if (c0 + 1 < m) lmax = fmaxf(lmax, beta * x.y + alpha * y.y);
+                    if (c0 + 2 < m) lmax = fmaxf(lmax, beta * x.z + alpha * y.z);
+                    if (c0 + 3 < m) lmax = fmaxf(lmax, beta * x.w + alpha * y.w);
+                }
             }
             lmax = warp_max(lmax);
             if (lane == 0) S.fred[si * 32 + warp] = lmax;
@@ -1028,32 +1047,47 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         float4* X = reinterpret_cast<float4*>(d.X) + (size_t)sg.lr0 * Qx;
         __nv_bfloat16* Xt16 = d.Xt16;
         const int ldxt = d.ldxt;
-        double dx = 0.0;
-        for (int e = tid; e < sg.nrows * Qx; e += nthr) {
-            const int r = e / Qx, q = e % Qx;
-            const float4 x = X[(size_t)r * Qx + q], y = Yg[(size_t)r * Qy + q];
-            float4 v = make_float4(beta * x.x + alpha * y.x, beta * x.y + alpha * y.y,
-                                   beta * x.z + alpha * y.z, beta * x.w + alpha * y.w);
-            if (P.normalize) { v.x /= mx; v.y /= mx; v.z /= mx; v.w /= mx; }
-            const int c0 = 4 * q;
-            if (c0 + 4 > m) {
-                if (c0 + 1 >= m) v.y = 0.f;
-                if (c0 + 2 >= m) v.z = 0.f;
-                if (c0 + 3 >= m) v.w = 0.f;
+        AbsDiffMax dxm;   // max|dX| in FP64, as the oracle takes it
+        const int dr = nthr / Qx, dq = nthr % Qx;
+        int rn = tid / Qx, qn = tid % Qx;
+        while (rn < sg.nrows) {
+            int rk[kBlendLoads], qk[kBlendLoads];
+            float4 xk[kBlendLoads], yk[kBlendLoads];
+#pragma unroll
+            for (int k = 0; k < kBlendLoads; ++k) {
+                rk[k] = rn;
+                qk[k] = qn;
+                if (rn < sg.nrows) { xk[k] = X[(size_t)rn * Qx + qn]; yk[k] = Yg[(size_t)rn * Qy + qn]; }
+                rn += dr; qn += dq;
+                if (qn >= Qx) { qn -= Qx; ++rn; }
             }
-            dx = fmax(dx, fmax(fmax(fabs((double)v.x - (double)x.x), fabs((double)v.y - (double)x.y)),
-                               fmax(fabs((double)v.z - (double)x.z), fabs((double)v.w - (double)x.w))));
-            X[(size_t)r * Qx + q] = v;
-            if (Xt16) {
-                const int i = sg.lr0 + r;
-                Xt16[(size_t)c0 * ldxt + i] = __float2bfloat16_rn(v.x);
-                if (c0 + 1 < m) Xt16[(size_t)(c0 + 1) * ldxt + i] = __float2bfloat16_rn(v.y);
-                if (c0 + 2 < m) Xt16[(size_t)(c0 + 2) * ldxt + i] = __float2bfloat16_rn(v.z);
-                if (c0 + 3 < m) Xt16[(size_t)(c0 + 3) * ldxt + i] = __float2bfloat16_rn(v.w);
+#pragma unroll
+            for (int k = 0; k < kBlendLoads; ++k) {
+                const int r = rk[k], q = qk[k];
+                if (r >= sg.nrows) break;
+                const float4 x = xk[k], y = yk[k];
+                float4 v = make_float4(beta * x.x + alpha * y.x, beta * x.y + alpha * y.y,
+                                       beta * x.z + alpha * y.z, beta * x.w + alpha * y.w);
+                if (P.normalize) { v.x /= mx; v.y /= mx; v.z /= mx; v.w /= mx; }
+                const int c0 = 4 * q;
+                if (c0 + 4 > m) {
+                    if (c0 + 1 >= m) v.y = 0.f;
+                    if (c0 + 2 >= m) v.z = 0.f;
+                    if (c0 + 3 >= m) v.w = 0.f;
+                }
+                dxm.add4(v, x);
+                X[(size_t)r * Qx + q] = v;
+                if (Xt16) {
+                    const int i = sg.lr0 + r;
+                    Xt16[(size_t)c0 * ldxt + i] = __float2bfloat16_rn(v.x);
+                    if (c0 + 1 < m) Xt16[(size_t)(c0 + 1) * ldxt + i] = __float2bfloat16_rn(v.y);
+                    if (c0 + 2 < m) Xt16[(size_t)(c0 + 2) * ldxt + i] = __float2bfloat16_rn(v.z);
+                    if (c0 + 3 < m) Xt16[(size_t)(c0 + 3) * ldxt + i] = __float2bfloat16_rn(v.w);
+                }
             }
         }
         // per-warp max|dX| of the segment, folded at L2 by the atomic
-        dx = warp_max_d(dx);
+        const double dx = warp_max_d(dxm.value());
         if (lane == 0 && dx > 0.0) atomicMax(&d.ctrl->dx_bits, (unsigned long long)__double_as_longlong(dx));
     }
     grid_arrive(&W->bar);

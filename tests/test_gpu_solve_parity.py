@@ -320,3 +320,50 @@ def test_fp32_products_on_tensor_cores_match_the_simt_solve(solver):
     assert abs(a.stats.outer_iters - b.stats.outer_iters) <= 1 and a.stats.lowp_iters == 0
     if a.stats.outer_iters == b.stats.outer_iters:
         assert (a.X - b.X).abs().max().item() <= 1e-5
+
+
+# ------------------------------------------- the outer stop's max|dX| exactly
+def _tiny_start(n, seed):
+    """A start whose entries sit ~2^-40 below the iterate's: every change
+    |X(1) - X(0)| then needs more than FP64's 53 bits, so its FP64 rounding
+    (the oracle's max|dX|) differs from a rounding through FP32."""
+    rng = np.random.default_rng(seed)
+    return (rng.uniform(1.0, 2.0, (n, n)) * 2.0 ** -40).astype(np.float32)
+
+
+def _exact_delta(X1, X0):
+    return float(np.abs(X1.astype(np.float64) - X0.astype(np.float64)).max())
+
+
+@pytest.mark.parametrize("algorithm", [F.ALG_FASTPFP, F.ALG_FASTGA])
+def test_outer_delta_is_the_fp64_max_change_in_a_wave(solver, algorithm):
+    """max|dX| of Algorithm 1's outer stop, taken per element in FP32 (exact
+    TwoSum pairs) and rounded to FP64 once, equals the FP64 maximum of the
+    changes of X the solve returns, bit for bit; wave kernel (three pairs in
+    one wave) and FastGA's kernel."""
+    gs = [synth.graph_pair(n, p=0.2, sigma=0.02, k=0, seed=40 + n) for n in (90, 150, 61)]
+    X0s = [_tiny_start(g.n, g.n) for g in gs]
+    prm = F.default_params(algorithm=algorithm, beta=100.0, max_outer=1, max_inner=30)
+    res = solver.match_batched([dev_pair(g)[:2] + (None, None, cu(X0)) for g, X0 in zip(gs, X0s)],
+                               params=prm, want_X=True)
+    for i, (r, X0) in enumerate(zip(res, X0s)):
+        _, deltas = solver.last_trace(pair=i)
+        want = _exact_delta(r.X.cpu().numpy(), X0)
+        assert float(np.float32(want)) != want   # the case needs the exact low part
+        assert deltas[0] == want, (i, deltas[0], want)
+
+
+def test_outer_delta_is_the_fp64_max_change_alone():
+    """The same bit-exact max|dX| from pd_kernel, which runs a pair too wide
+    for any wave (N > 4096) alone."""
+    n = 4100
+    g = synth.graph_pair(n, p=0.01, sigma=0.0, k=0, seed=2)
+    X0 = _tiny_start(n, 5)
+    with F.Solver(max_n=n) as s:
+        r = s.match(cu(g.A), cu(g.A2), X0=cu(X0), params=F.default_params(max_outer=1, max_inner=10),
+                    want_X=True)
+        _, deltas = s.last_trace()
+    assert r.stats.wave_pairs == 0
+    want = _exact_delta(r.X.cpu().numpy(), X0)
+    assert float(np.float32(want)) != want
+    assert deltas[0] == want
