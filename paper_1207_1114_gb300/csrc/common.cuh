@@ -200,6 +200,24 @@ __device__ __forceinline__ Quant64 quant64_for_f(float bound) {
     return quant64_from_exp(((__float_as_int(bound) >> 23) & 0xff) - 127);
 }
 __device__ __forceinline__ double quant64(double v, Quant64 q) { return rint(v * q.dn) * q.up; }
+// quant64 of an FP32 value without FP64 arithmetic, the same bits.  For a
+// quantum 2^e with -126 <= e <= 104 and |v| < 2^(e+23), |v| + 2^(e+23) lies
+// in [2^(e+23), 2^(e+24)], where floats are 2^e apart, so the addition
+// rounds |v| to the nearest multiple of 2^e (ties to an even multiple, as
+// rint does) and the subtraction is exact; a float |v| >= 2^(e+23) already
+// is a multiple of 2^e.  The result is 0 or a normal float, widened to FP64
+// by its bits.  Other quanta, and infinite or NaN v, take the FP64 route.
+__device__ __forceinline__ double quant64_of_f32(float v, Quant64 q) {
+    const int e = (int)((__double_as_longlong(q.up) >> 52) & 0x7ff) - 1023;
+    const float a = fabsf(v);
+    if (e < -126 || e > 104 || !(a <= 3.402823466e38f)) return quant64((double)v, q);
+    const float C = __int_as_float((127 + 23 + e) << 23);
+    const unsigned b = __float_as_uint(a < C ? (a + C) - C : a) | (__float_as_uint(v) & 0x80000000u);
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    if ((b & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(((b >> 23) & 0xffu) + 896u) << 52) |
+                                            ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
 
 // Asynchronous 16-byte global -> shared copy through L2 only (the source is
 // written by other CTAs' reductions, so L1 must not hold a stale copy), and

@@ -24,6 +24,7 @@
 // the GPU never idles, whether every pair has stopped; launches after a
 // pair's stop return at once.
 #include <algorithm>
+#include <cmath>
 #include <cstddef>
 #include <cstdio>
 #include <cstdlib>
@@ -48,6 +49,13 @@ constexpr int kChunk = 4;                         // outer iterations enqueued b
 constexpr size_t kTraceBytes = (size_t)kMaxOuterTrace * (sizeof(int) + sizeof(double));
 
 inline int round4(int x) { return (x + 3) & ~3; }
+// The least float >= t (t itself when it is a float; +inf above the float
+// range; NaN stays NaN): a float d is below it exactly when d < t in FP64.
+inline float float_at_least(double t) {
+    float f = (float)t;
+    if ((double)f < t) f = std::nextafter(f, INFINITY);
+    return f;
+}
 inline int round8(int x) { return (x + 7) & ~7; }   // BF16 rows: 16-byte TMA strides
 inline int round16(int x) { return (x + 15) & ~15; }   // E4M3 rows: 16-byte TMA strides
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -829,6 +837,7 @@ PdbParams wave_params(fastpfp_t h, const Wave& w, int npairs, const fastpfp_para
     P.normalize = p->normalize_max ? 1 : 0;
     P.slack_reset = p->slack_policy == 1 ? 1 : 0;
     P.tol_inner = p->tol_inner;
+    P.tol_inner_f = float_at_least(p->tol_inner);
     P.max_inner = p->max_inner;
     P.tol_outer = p->tol_outer;
     P.max_outer = p->max_outer;

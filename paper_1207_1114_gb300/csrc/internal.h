@@ -178,6 +178,7 @@ struct PdbParams {
     float alpha;
     int normalize, slack_reset;
     double tol_inner;
+    float tol_inner_f;    // the least float >= tol_inner: for a float d, d < tol_inner_f iff d < tol_inner
     int max_inner;
     double tol_outer;
     int max_outer;

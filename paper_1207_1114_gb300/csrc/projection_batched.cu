@@ -802,6 +802,16 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     auto row_sum = [&](const Seg& sg, int nw, int r) {
         const float* rpp = S.rowpart + (size_t)(sg.brow0 + r) * RPS;
         float t = 0.f;
+        if ((RPS & 3) == 0) {   // float4 loads (rows 16-byte aligned), the same order of additions
+            for (int w = 0; w < nw; w += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(rpp + w);
+                t += v.x;
+                if (w + 1 < nw) t += v.y;
+                if (w + 2 < nw) t += v.z;
+                if (w + 3 < nw) t += v.w;
+            }
+            return t;
+        }
         for (int w = 0; w < nw; ++w) t += rpp[w];
         return t;
     };
@@ -821,7 +831,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 const Seg sg = S.seg[si];
                 const int pst = S.pstate[sg.pair];
                 if (!(pst & 1) || (pst & 2)) continue;
-                const int nw = pdb_row_warps(S.pair[sg.pair].ldy, nthr, Lay.two_quad_ties);
+                const int nw = sg.qpg >> 5;   // warps sharing a row
                 float sp = 0.f;
                 for (int r = lane; r < sg.nrows; r += 32) sp += row_sum(sg, nw, r);
                 sp = warp_sum(sp);
@@ -829,7 +839,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 bm = warp_max(bm);
                 if (lane == 0) {
                     const PairS& pr = S.pair[sg.pair];
-                    atomicAdd(pr.sbuf + cur, quant64((double)sp, pr.sq));
+                    atomicAdd(pr.sbuf + cur, quant64_of_f32(sp, pr.sq));
                     if (bm > 0.f) atomicMax(pr.dbuf + cur, __float_as_uint(bm));
                 }
             }
@@ -838,7 +848,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 const Seg sg = S.seg[si];
                 const int pst = S.pstate[sg.pair];
                 if (!(pst & 1) || (pst & 2)) continue;
-                const int nw = pdb_row_warps(S.pair[sg.pair].ldy, nthr, Lay.two_quad_ties);
+                const int nw = sg.qpg >> 5;
                 for (int r = tid - 64; r < sg.nrows; r += nthr - 64) S.rsum[sg.brow0 + r] = row_sum(sg, nw, r);
             }
             if (clear_which >= 0) clear_acc(clear_which, tid - 64, nthr - 64);
@@ -909,7 +919,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                     pr.cb = fmaf(sf, (float)invN, 1.0f) * mg;
                     pr.sq = quant64_for_f(fmaf(2.0f, sf, Nf) * (mg * mg));
                 }
-                if (check_stop && ((double)dd < P.tol_inner || u >= P.max_inner)) {
+                if (check_stop && (dd < P.tol_inner_f || u >= P.max_inner)) {
                     ps |= 2;
                     S.pstop[p] = u;
                 }
