@@ -58,6 +58,7 @@ struct PairS {
 };
 
 static_assert(sizeof(Seg) == kSegBytes, "pdb_smem_bytes sizes the segment table");
+static_assert(kPdbThreads <= 16 * 32, "a segment's fred slots hold 16 warps' maxima and 16 warps' totals");
 static_assert(sizeof(PairS) == kPairBytes, "pdb_smem_bytes sizes the pair table");
 
 struct Shared {
@@ -67,7 +68,7 @@ struct Shared {
     int* pstop;          // L.npairs: round at which the pair stopped
     int* ictl;           // [2] n segments, [3] non-finite, [4] running pairs
     int* qpref;          // L.npairs + 1: prefix sums of the pairs' column quads
-    float* fred;         // L.max_segs x 32 per-warp maxima
+    float* fred;         // L.max_segs x 32: per-warp maxima (0 .. 15), per-warp row-partial totals (16 .. 31)
     float* rsum;         // band rows
     float* rowpart;      // band rows x rp_stride per-warp row partials
     float* cN;           // sum over segments of ldy floats: the column sums c_j of the last round
@@ -281,7 +282,7 @@ template <bool UPDATE>
 __device__ __forceinline__ void seg_rows_tmem(uint32_t taddr, int tm, int nrows, int Q, int N, const Map& mp,
                                               int lane, const float* __restrict__ rsum, float abase,
                                               float* __restrict__ rowpart, int rps, float4 c0v, float ninvN,
-                                              float4& cp0, float& dmax) {
+                                              float4& cp0, float& dmax, float& tot) {
     const bool h0 = mp.q0 < Q;
     const int RP = mp.RP;
     int k = 0;
@@ -303,7 +304,7 @@ __device__ __forceinline__ void seg_rows_tmem(uint32_t taddr, int tm, int nrows,
             }
             const float z = sum4_rows(s, lane);
             const int rj = mp.grp + RP * (k + 4 * h + 2 * (lane >> 4) + ((lane >> 3) & 1));
-            if ((lane & 7) == 0 && rj < nrows) rowpart[(size_t)rj * rps] = z;
+            if ((lane & 7) == 0 && rj < nrows) { rowpart[(size_t)rj * rps] = z; tot += z; }
         }
         if (UPDATE) {
             const float4 qa[4] = {q[0], q[1], q[2], q[3]}, qb[4] = {q[4], q[5], q[6], q[7]};
@@ -327,7 +328,7 @@ __device__ __forceinline__ void seg_rows_tmem(uint32_t taddr, int tm, int nrows,
         if (UPDATE) tm_st16(taddr + 4 * k, q);
         const float z = sum4_rows(s, lane);
         const int rj = mp.grp + RP * (k + 2 * (lane >> 4) + ((lane >> 3) & 1));
-        if ((lane & 7) == 0 && rj < nrows) rowpart[(size_t)rj * rps] = z;
+        if ((lane & 7) == 0 && rj < nrows) { rowpart[(size_t)rj * rps] = z; tot += z; }
     }
     for (; k < tm; ++k) {
         const int r = mp.grp + RP * k;
@@ -339,7 +340,7 @@ __device__ __forceinline__ void seg_rows_tmem(uint32_t taddr, int tm, int nrows,
         }
         if (UPDATE) tm_st4(taddr + 4 * k, y);
         s0 = warp_sum(s0);
-        if (lane == 0 && r < nrows) rowpart[(size_t)r * rps] = s0;
+        if (lane == 0 && r < nrows) { rowpart[(size_t)r * rps] = s0; tot += s0; }
     }
 }
 
@@ -350,7 +351,7 @@ template <bool UPDATE>
 __device__ __forceinline__ void seg_rows_tmem2(uint32_t taddr, int tm, int nrows, int Q, int N, const Map& mp,
                                                int lane, const float* __restrict__ rsum, float abase,
                                                float* __restrict__ rowpart, int rps, float4 c0v, float4 c1v,
-                                               float ninvN, float4& cp0, float4& cp1, float& dmax) {
+                                               float ninvN, float4& cp0, float4& cp1, float& dmax, float& tot) {
     const int q1 = mp.q0 + mp.QP;
     const bool h0 = mp.q0 < Q, h1 = q1 < Q;
     const int RP = mp.RP;
@@ -377,7 +378,7 @@ __device__ __forceinline__ void seg_rows_tmem2(uint32_t taddr, int tm, int nrows
         }
         const float z = sum4_rows(s, lane);
         const int rj = mp.grp + RP * (k + 2 * (lane >> 4) + ((lane >> 3) & 1));
-        if ((lane & 7) == 0 && rj < nrows) rowpart[(size_t)rj * rps] = z;
+        if ((lane & 7) == 0 && rj < nrows) { rowpart[(size_t)rj * rps] = z; tot += z; }
     }
     for (; k + 1 < tm; k += 2) {
         float4 q[4];   // row k: quads 0, 1; row k + 1: quads 0, 1
@@ -402,8 +403,8 @@ __device__ __forceinline__ void seg_rows_tmem2(uint32_t taddr, int tm, int nrows
         keep += __shfl_xor_sync(0xffffffffu, keep, 2);
         keep += __shfl_xor_sync(0xffffffffu, keep, 1);
         const int r0 = mp.grp + RP * k, r1 = r0 + RP;
-        if (lane == 0 && r0 < nrows) rowpart[(size_t)r0 * rps] = keep;
-        if (lane == 16 && r1 < nrows) rowpart[(size_t)r1 * rps] = keep;
+        if (lane == 0 && r0 < nrows) { rowpart[(size_t)r0 * rps] = keep; tot += keep; }
+        if (lane == 16 && r1 < nrows) { rowpart[(size_t)r1 * rps] = keep; tot += keep; }
     }
     if (k < tm) {
         const int r = mp.grp + RP * k;
@@ -419,7 +420,7 @@ __device__ __forceinline__ void seg_rows_tmem2(uint32_t taddr, int tm, int nrows
             tm_st4(taddr + 8 * k + 4, y1);
         }
         s0 = warp_sum(s0);
-        if (lane == 0 && r < nrows) rowpart[(size_t)r * rps] = s0;
+        if (lane == 0 && r < nrows) { rowpart[(size_t)r * rps] = s0; tot += s0; }
     }
 }
 
@@ -433,7 +434,7 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
                                          const Map& mp, int nthr, int lane,
                                          const float* __restrict__ rsum, float abase,
                                          float* __restrict__ rowpart, int rps, float4 c0v, float4 c1v, float ninvN,
-                                         float4& cp0, float4& cp1, float& dmax) {
+                                         float4& cp0, float4& cp1, float& dmax, float& tot) {
     const bool h0 = mp.q0 < Q;
     const int q1 = mp.q0 + mp.QP;   // the second quad (kq = 2)
     const bool h1 = KQ > 1 && q1 < Q;
@@ -465,7 +466,7 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
             }
         }
         const float z = sum4_rows(s, lane);
-        if ((lane & 7) == 0) rowpart[(size_t)(r + (2 * (lane >> 4) + ((lane >> 3) & 1)) * RP) * rps] = z;
+        if ((lane & 7) == 0) { rowpart[(size_t)(r + (2 * (lane >> 4) + ((lane >> 3) & 1)) * RP) * rps] = z; tot += z; }
     }
     for (; r + RP < nrows; r += 2 * RP, p += 2 * stride) {
         const float a0 = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
@@ -488,8 +489,8 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
         keep += __shfl_xor_sync(0xffffffffu, keep, 4);
         keep += __shfl_xor_sync(0xffffffffu, keep, 2);
         keep += __shfl_xor_sync(0xffffffffu, keep, 1);
-        if (lane == 0) rowpart[(size_t)r * rps] = keep;
-        if (lane == 16) rowpart[(size_t)(r + RP) * rps] = keep;
+        if (lane == 0) { rowpart[(size_t)r * rps] = keep; tot += keep; }
+        if (lane == 16) { rowpart[(size_t)(r + RP) * rps] = keep; tot += keep; }
     }
     if (r < nrows) {
         const float a0 = UPDATE ? fmaf(ninvN, rsum[r], abase) : 0.f;
@@ -497,7 +498,7 @@ __device__ __forceinline__ void seg_rows(float4* __restrict__ band, int nrows, i
         if (h0) s0 += quad_step<UPDATE>(p, a0, c0v, cp0, dmax);
         if (KQ > 1 && h1) s0 += quad_step<UPDATE>(p + mp.QP, a0, c1v, cp1, dmax);
         s0 = warp_sum(s0);
-        if (lane == 0) rowpart[(size_t)r * rps] = s0;
+        if (lane == 0) { rowpart[(size_t)r * rps] = s0; tot += s0; }
     }
 }
 
@@ -664,8 +665,8 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     grid_arrive(&W->bar);   // waited for at the start of body()
 
     // One pass over the active segments.  UPDATE = false only sums.  Row
-    // partials go to rowpart, per-segment maxima to fred, column partials to
-    // the pairs' accumulator `cur`.
+    // partials go to rowpart, per-segment per-warp maxima and totals of the
+    // row partials to fred, column partials to the pairs' accumulator `cur`.
     auto pass = [&](auto update_tag, int cur) {
         constexpr bool UPDATE = decltype(update_tag)::value;
         for (int si = 0; si < nseg; ++si) {
@@ -691,6 +692,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             }
             float4 cp0 = make_float4(0.f, 0.f, 0.f, 0.f), cp1 = cp0;
             float dmax = 0.f;
+            float tot = 0.f;   // this lane's share of the warp's row partials of the segment
             if (in_grp) {
                 const int wig = (tid % mp.QP) >> 5;
                 float4* bp = reinterpret_cast<float4*>(S.band + sg.soff);
@@ -699,22 +701,26 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 const float ninvN = -1.0f / (float)N;
                 if (sg.tm > 0 && mp.kq == 1)
                     seg_rows_tmem<UPDATE>(tme + sg.tcol, sg.tm, sg.nrows, Q, N, mp, lane, rs, pr.abase, rp, RPS,
-                                          c0v, ninvN, cp0, dmax);
+                                          c0v, ninvN, cp0, dmax, tot);
                 else if (sg.tm > 0)
                     seg_rows_tmem2<UPDATE>(tme + sg.tcol, sg.tm, sg.nrows, Q, N, mp, lane, rs, pr.abase, rp, RPS,
-                                           c0v, c1v, ninvN, cp0, cp1, dmax);
+                                           c0v, c1v, ninvN, cp0, cp1, dmax, tot);
                 // rows ntm .. nrows - 1 (ntm is a multiple of RP, so row groups line up)
                 const int ns = sg.nrows - sg.ntm;
                 if (mp.kq == 1)
                     seg_rows<UPDATE, 1>(bp, ns, Q, N, mp, nthr, lane, rs + sg.ntm, pr.abase,
-                                        rp + (size_t)sg.ntm * RPS, RPS, c0v, c1v, ninvN, cp0, cp1, dmax);
+                                        rp + (size_t)sg.ntm * RPS, RPS, c0v, c1v, ninvN, cp0, cp1, dmax, tot);
                 else
                     seg_rows<UPDATE, 2>(bp, ns, Q, N, mp, nthr, lane, rs + sg.ntm, pr.abase,
-                                        rp + (size_t)sg.ntm * RPS, RPS, c0v, c1v, ninvN, cp0, cp1, dmax);
+                                        rp + (size_t)sg.ntm * RPS, RPS, c0v, c1v, ninvN, cp0, cp1, dmax, tot);
             }
             if (UPDATE) tm_wait_st();
             dmax = warp_max(dmax);
-            if (lane == 0) S.fred[si * 32 + warp] = dmax;
+            tot = warp_sum(tot);
+            if (lane == 0) {
+                S.fred[si * 32 + warp] = dmax;
+                S.fred[si * 32 + 16 + warp] = tot;
+            }
             // column partials: every row group adds its own (L2 folds the row
             // groups; no block-wide fold, no barrier), rounded to the column's
             // quantum so that the sums are exact in any order
@@ -821,9 +827,9 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     // 2.. fold the row sums for the next pass and zero accumulator
     // `clear_which` (>= 0) of the wave's pairs; all of it precedes the
     // arrival, so the zeros are visible before any CTA's next-round
-    // reductions.  A band's total (at most a few dozen FP32 row sums, each
-    // folded as the next pass's row sum is) is added in FP32 and accumulated
-    // over the CTAs in FP64.
+    // reductions.  A band's total is the sum, in a fixed order, of the
+    // per-warp totals of the row partials the pass stored (FP32), and is
+    // accumulated over the CTAs in FP64.
     auto publish = [&](int cur, int clear_which) {
         if (tid == 0) S.ictl[4] = 0;   // the running-pair count of wait_post
         if (warp < 2) {
@@ -831,11 +837,9 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 const Seg sg = S.seg[si];
                 const int pst = S.pstate[sg.pair];
                 if (!(pst & 1) || (pst & 2)) continue;
-                const int nw = sg.qpg >> 5;   // warps sharing a row
-                float sp = 0.f;
-                for (int r = lane; r < sg.nrows; r += 32) sp += row_sum(sg, nw, r);
-                sp = warp_sum(sp);
+                float sp = lane < (nthr >> 5) ? S.fred[si * 32 + 16 + lane] : 0.f;
                 float bm = lane < (nthr >> 5) ? S.fred[si * 32 + lane] : 0.f;
+                sp = warp_sum(sp);
                 bm = warp_max(bm);
                 if (lane == 0) {
                     const PairS& pr = S.pair[sg.pair];
