@@ -219,6 +219,24 @@ __device__ __forceinline__ double quant64_of_f32(float v, Quant64 q) {
                                             ((unsigned long long)(b & 0x7fffffu) << 29)));
 }
 
+// (float)d by integer operations (round to nearest, ties to even), for
+// results in the normal float range; zero, results below it, overflow,
+// infinities and NaN take the conversion instruction.  A carry out of the
+// fraction moves into the exponent, as rounding does (to infinity from the
+// top binade).
+__device__ __forceinline__ float f64_to_f32_rn(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex < 1023 - 126 || ex > 1023 + 127) return (float)d;
+    const unsigned long long rest = b & 0x1fffffffull;   // the 29 fraction bits dropped
+    unsigned bits = ((unsigned)(ex - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffull);
+    if (rest > 0x10000000ull || (rest == 0x10000000ull && (bits & 1u))) bits += 1u;
+    return __uint_as_float(bits | ((unsigned)(b >> 63) << 31));
+}
+__device__ __forceinline__ bool f64_is_finite(double d) {
+    return ((__double_as_longlong(d) >> 52) & 0x7ff) != 0x7ff;
+}
+
 // Asynchronous 16-byte global -> shared copy through L2 only (the source is
 // written by other CTAs' reductions, so L1 must not hold a stale copy), and
 // the wait for all of this thread's copies.  Both addresses 16-byte aligned.

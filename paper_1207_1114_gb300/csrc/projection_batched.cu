@@ -824,13 +824,10 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
 
     // End of a pass (every warp's partials in): warps 0 and 1 publish the
     // segments' totals and round maxima (alternate segments) while warps
-    // 2.. fold the row sums for the next pass and zero accumulator
-    // `clear_which` (>= 0) of the wave's pairs; all of it precedes the
-    // arrival, so the zeros are visible before any CTA's next-round
-    // reductions.  A band's total is the sum, in a fixed order, of the
+    // 2.. fold the row sums for the next pass.  A band's total is the sum, in a fixed order, of the
     // per-warp totals of the row partials the pass stored (FP32), and is
     // accumulated over the CTAs in FP64.
-    auto publish = [&](int cur, int clear_which) {
+    auto publish = [&](int cur) {
         if (tid == 0) S.ictl[4] = 0;   // the running-pair count of wait_post
         if (warp < 2) {
             for (int si = warp; si < nseg; si += 2) {
@@ -855,7 +852,6 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 const int nw = sg.qpg >> 5;
                 for (int r = tid - 64; r < sg.nrows; r += nthr - 64) S.rsum[sg.brow0 + r] = row_sum(sg, nw, r);
             }
-            if (clear_which >= 0) clear_acc(clear_which, tid - 64, nthr - 64);
         }
         if (skip_first) {   // fault-injection test: this arrival is lost
             skip_first = false;
@@ -905,14 +901,14 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 const double invN = pr.invN;
                 pr.s = s;
                 pr.abase = (float)(invN + s * invN * invN);
-                if (!isfinite(s)) S.ictl[3] = 1;
+                if (!f64_is_finite(s)) S.ictl[3] = 1;
                 // bounds of the next pass's sums (its output is >= 0): after
                 // the input, every column sum is at most 4 N max|y| + 1 (the
                 // input, the row offsets and the column offset of P1 are each
                 // at most N max|y| per column); after a round, column j's at
                 // most c_j + 1 + s/N and the total at most 2 s + N
                 // (FP32 bounds: the margin covers their rounding)
-                const float mg = kBoundMargin, Nf = (float)pr.N, sf = (float)s;
+                const float mg = kBoundMargin, Nf = (float)pr.N, sf = f64_to_f32_rn(s);
                 if (u == 0) {
                     const float b1 = fmaf(4.0f * Nf, pr.ymax, 1.0f) * mg;
                     pr.bmode = 1;
@@ -931,6 +927,13 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                 any |= !(ps & 2);
             }
         }
+        // Accumulator (u + 2) % 3, which round u + 2 adds into, was last read
+        // (column sums, total, maximum) in every CTA's wait_post of round
+        // u - 1, before its arrival at the barrier just passed: the threads
+        // the pair loop leaves idle zero it now, so the stores are done long
+        // before this CTA's next arrival (a release, which would wait for
+        // them) and visible before any CTA's round u + 2 reductions.
+        if (tid >= 128) clear_acc((u + 2) % 3, tid - 128, nthr - 128);
         // ictl[4] counts the warps that still have a running pair (zeroed in publish)
         any = __any_sync(0xffffffffu, any);
         if (warp < 4 && lane == 0 && any) atomicAdd(&S.ictl[4], 1);
@@ -955,7 +958,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     }
     __syncthreads();
     pass(std::false_type{}, 0);
-    publish(0, -1);
+    publish(0);
     if (!wait_post(0, 0, false)) return;
     if (S.ictl[3]) {
         if (tid == 0) atomicCAS(err, 0, FASTPFP_ERR_NONFINITE);
@@ -968,7 +971,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
     while (act) {
         ++u;
         pass(std::true_type{}, u % 3);
-        publish(u % 3, (u + 1) % 3);
+        publish(u % 3);
         if (!wait_post(u % 3, u, true)) return;
         act = S.ictl[4] != 0;
     }
