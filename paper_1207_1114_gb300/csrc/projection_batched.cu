@@ -47,12 +47,12 @@ struct PairS {
     float* colbuf;
     double* sbuf;
     unsigned* dbuf;
-    double s;       // total of the last finished pass
+    float invNf;    // (float)(1/N), for the FP32 bounds
+    int bmode;      // quanta of the next pass's column partials: 0 per column, 1 one for the pair
     int N, ldy;
     float abase;    // 1/N + s/N^2 of the last finished pass (the row offset is abase - r_i/N)
-    int bmode;      // quanta of the next pass's column partials: 0 per column, 1 one for the pair
-    double invN;    // 1/N
     float cb;       // bmode 0: column j's bound is c_j * margin + cb; bmode 1: every column's bound
+    double invN;    // 1/N
     float ymax;     // max|y| of the launch's input
     Quant64 sq;     // quantum of the next pass's contributions to s
 };
@@ -570,12 +570,12 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         ps.colbuf = d.colbuf;
         ps.sbuf = d.sbuf;
         ps.dbuf = d.dbuf;
-        ps.s = 0.0;
         ps.N = d.N;
         ps.ldy = d.ldy;
         ps.abase = 0.f;
         ps.bmode = 0;
         ps.invN = 1.0 / (double)d.N;
+        ps.invNf = (float)ps.invN;
         ps.cb = 0.f;
         ps.ymax = 0.f;
         ps.sq = Quant64{1.0, 1.0};
@@ -621,20 +621,29 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         const bool reset = P.slack_reset && m < d.N;
         const float4* src = reinterpret_cast<const float4*>(d.Y) + (size_t)sg.lr0 * Q;
         // TMEM rows: thread-row k of the row group is band row grp + RP k
+        // (eight float4 loads in flight per thread before any is used)
         if (sg.tm > 0) {
             const Map mp = make_map(sg.qpg, sg.rpkq, tid);
             if (mp.grp < mp.RP) {
-                for (int k = 0; k < sg.tm; ++k) {
-                    const int r = mp.grp + mp.RP * k;
-                    for (int j = 0; j < mp.kq; ++j) {   // the thread's quads of its k-th row
-                        const int q = mp.q0 + j * mp.QP;
-                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int k0 = 0; k0 < sg.tm; k0 += 4) {
+                    float4 v[8];   // thread-rows k0 .. k0 + 3, quads j = 0, 1
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int k = k0 + (i >> 1), j = i & 1;
+                        const int r = mp.grp + mp.RP * k, q = mp.q0 + j * mp.QP;
+                        v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (k < sg.tm && j < mp.kq && r < sg.nrows && q < Q) v[i] = src[(size_t)r * Q + q];
+                    }
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int k = k0 + (i >> 1), j = i & 1;
+                        if (k >= sg.tm || j >= mp.kq) continue;   // warp-uniform
+                        const int r = mp.grp + mp.RP * k, q = mp.q0 + j * mp.QP;
                         if (r < sg.nrows && q < Q) {
-                            v = src[(size_t)r * Q + q];
-                            if (reset) v = slack_mask(v, 4 * q, m);
-                            absmax(v);
+                            if (reset) v[i] = slack_mask(v[i], 4 * q, m);
+                            absmax(v[i]);
                         }
-                        tm_st4(tme + sg.tcol + 4 * (mp.kq * k + j), v);
+                        tm_st4(tme + sg.tcol + 4 * (mp.kq * k + j), v[i]);
                     }
                 }
             }
@@ -642,11 +651,20 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         // shared-memory rows ntm .. nrows - 1
         const float4* src2 = src + (size_t)sg.ntm * Q;
         float4* dst = reinterpret_cast<float4*>(S.band + sg.soff);
-        for (int e = tid; e < (sg.nrows - sg.ntm) * Q; e += nthr) {
-            float4 v = src2[e];
-            if (reset) v = slack_mask(v, 4 * (e % Q), m);
-            absmax(v);
-            dst[e] = v;
+        const int ne = (sg.nrows - sg.ntm) * Q;
+        for (int e0 = tid; e0 < ne; e0 += 4 * nthr) {
+            float4 v[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (e0 + i * nthr < ne) v[i] = src2[e0 + i * nthr];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int e = e0 + i * nthr;
+                if (e >= ne) break;
+                if (reset) v[i] = slack_mask(v[i], 4 * (e % Q), m);
+                absmax(v[i]);
+                dst[e] = v[i];
+            }
         }
         ym = warp_max(ym);
         if (lane == 0) S.fred[si * 32 + warp] = ym;
@@ -869,6 +887,17 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
         const unsigned target = base + G * (gen + 1u);
         if (!grid_wait(&W->bar, target, err, P.timeout_ns)) return false;
         ++gen;
+        // the running pairs' totals and maxima first (one pair per thread of
+        // the first four warps): their L2 round trip heads the chain below
+        double s_pre = 0.0;
+        unsigned d_pre = 0u;
+        if (tid < 128 && tid < npairs) {
+            const int ps = S.pstate[tid];
+            if ((ps & 1) && !(ps & 2)) {
+                s_pre = __ldcg(S.pair[tid].sbuf + cur);
+                d_pre = __ldcg(S.pair[tid].dbuf + cur);
+            }
+        }
         // every segment's column sums in flight at once (copied, not loaded
         // and stored, so no segment waits for the previous one's latency);
         // the input's sums (u = 0) are FP64 and converted here
@@ -889,17 +918,16 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
             const float4* c = reinterpret_cast<const float4*>(pr.colbuf + (size_t)cur * pr.ldy);
             for (int q = tid; q < (pr.ldy >> 2); q += nthr) cp_async_cg16(dst + q, c + q);
         }
-        // the pairs, one per thread of the first four warps (their totals
-        // come from L2: one round trip for up to 128 pairs)
+        // the pairs, one per thread of the first four warps (totals and
+        // maxima loaded above)
         int any = 0;
         for (int p = tid; p < npairs && tid < 128; p += 128) {
             int ps = S.pstate[p];
             if ((ps & 1) && !(ps & 2)) {
                 PairS& pr = S.pair[p];
-                const double s = __ldcg(pr.sbuf + cur);
-                const float dd = __uint_as_float(__ldcg(pr.dbuf + cur));
+                const double s = p == tid ? s_pre : __ldcg(pr.sbuf + cur);
+                const float dd = __uint_as_float(p == tid ? d_pre : __ldcg(pr.dbuf + cur));
                 const double invN = pr.invN;
-                pr.s = s;
                 pr.abase = (float)(invN + s * invN * invN);
                 if (!f64_is_finite(s)) S.ictl[3] = 1;
                 // bounds of the next pass's sums (its output is >= 0): after
@@ -916,7 +944,7 @@ __global__ void __launch_bounds__(kPdbThreads, 1) pdb_kernel(const PdbParams P) 
                     pr.sq = quant64_for_f(b1 * Nf * mg);
                 } else {
                     pr.bmode = 0;
-                    pr.cb = fmaf(sf, (float)invN, 1.0f) * mg;
+                    pr.cb = fmaf(sf, pr.invNf, 1.0f) * mg;
                     pr.sq = quant64_for_f(fmaf(2.0f, sf, Nf) * (mg * mg));
                 }
                 if (check_stop && (dd < P.tol_inner_f || u >= P.max_inner)) {
