@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "../../include/fastpfp.h"
+#include "exact.cuh"
 
 namespace fpfp {
 
@@ -73,43 +74,6 @@ __device__ __forceinline__ double warp_max_d(double v) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
-
-// --------------------------------------------------- exact max |v - x|
-// The maximum over elements of |v - x| rounded once to FP64 (what
-// fabs((double)v - (double)x) gives), with FP32 arithmetic per element: the
-// FP64 units of this part run at a small fraction of the FP32 rate.  Knuth's
-// TwoSum splits v - x exactly into s + t (s = fl(v - x), |t| <= ulp(s)/2);
-// then |v - x| = |s| + sign(s) t, and the pairs (|s|, sign(s) t) order like
-// the exact differences under lexicographic comparison (rounding is
-// monotone), so the running maximum is kept as a pair and rounded to FP64
-// once.  A difference that overflows FP32 (s or t not finite) takes the
-// FP64 path; NaN differences are ignored, as fmax ignores them.
-struct AbsDiffMax {
-    float hi = 0.f, lo = 0.f;   // the largest |v - x| so far, exactly hi + lo
-    double big = 0.0;           // the FP64 maximum of the differences FP32 cannot hold
-    __device__ __forceinline__ void add(float v, float x) {
-        const float s = v - x;
-        const float vr = s + x;            // TwoSum of v and -x
-        const float xr = s - vr;
-        const float t = (v - vr) - (x + xr);
-        const float as = fabsf(s), at = s < 0.f ? -t : t;
-        if (as > hi || (as == hi && at > lo)) {
-            if (isfinite(as) && isfinite(at)) {
-                hi = as;
-                lo = at;
-            } else {
-                big = fmax(big, fabs((double)v - (double)x));
-            }
-        }
-    }
-    __device__ __forceinline__ void add4(float4 v, float4 x) {
-        add(v.x, x.x);
-        add(v.y, x.y);
-        add(v.z, x.z);
-        add(v.w, x.w);
-    }
-    __device__ __forceinline__ double value() const { return fmax(big, (double)hi + (double)lo); }
-};
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
 #pragma unroll
@@ -179,63 +143,7 @@ __device__ __forceinline__ float4 quant32x4(float4 v, Quant32 a, Quant32 b, Quan
 // the updates it bounds.
 constexpr float kBoundMargin = 1.0f + 1.0f / 1024.0f;
 
-// FP64: the quantum q = 2^(E-52) for a bound b, E = floor(log2 b), so
-// b < 2^(E+1) = 2^53 q; b <= 0 (only zeros to add) takes q = 1.  The
-// scales are built from the exponent bits (FP64 arithmetic is slow here).
-struct Quant64 {
-    double dn, up;
-};
-__device__ __forceinline__ Quant64 quant64_from_exp(int E) {
-    E = E > 900 ? 900 : (E < -900 ? -900 : E);
-    return Quant64{__longlong_as_double((long long)(1023 + 52 - E) << 52),
-                   __longlong_as_double((long long)(1023 - 52 + E) << 52)};
-}
-__device__ __forceinline__ Quant64 quant64_for(double bound) {
-    if (!(bound > 0.0)) return Quant64{1.0, 1.0};
-    return quant64_from_exp((int)((__double_as_longlong(bound) >> 52) & 0x7ff) - 1023);
-}
-// The same from a float bound (positive, finite).
-__device__ __forceinline__ Quant64 quant64_for_f(float bound) {
-    if (!(bound > 0.f)) return Quant64{1.0, 1.0};
-    return quant64_from_exp(((__float_as_int(bound) >> 23) & 0xff) - 127);
-}
-__device__ __forceinline__ double quant64(double v, Quant64 q) { return rint(v * q.dn) * q.up; }
-// quant64 of an FP32 value without FP64 arithmetic, the same bits.  For a
-// quantum 2^e with -126 <= e <= 104 and |v| < 2^(e+23), |v| + 2^(e+23) lies
-// in [2^(e+23), 2^(e+24)], where floats are 2^e apart, so the addition
-// rounds |v| to the nearest multiple of 2^e (ties to an even multiple, as
-// rint does) and the subtraction is exact; a float |v| >= 2^(e+23) already
-// is a multiple of 2^e.  The result is 0 or a normal float, widened to FP64
-// by its bits.  Other quanta, and infinite or NaN v, take the FP64 route.
-__device__ __forceinline__ double quant64_of_f32(float v, Quant64 q) {
-    const int e = (int)((__double_as_longlong(q.up) >> 52) & 0x7ff) - 1023;
-    const float a = fabsf(v);
-    if (e < -126 || e > 104 || !(a <= 3.402823466e38f)) return quant64((double)v, q);
-    const float C = __int_as_float((127 + 23 + e) << 23);
-    const unsigned b = __float_as_uint(a < C ? (a + C) - C : a) | (__float_as_uint(v) & 0x80000000u);
-    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
-    if ((b & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);
-    return __longlong_as_double((long long)(sign | ((unsigned long long)(((b >> 23) & 0xffu) + 896u) << 52) |
-                                            ((unsigned long long)(b & 0x7fffffu) << 29)));
-}
-
-// (float)d by integer operations (round to nearest, ties to even), for
-// results in the normal float range; zero, results below it, overflow,
-// infinities and NaN take the conversion instruction.  A carry out of the
-// fraction moves into the exponent, as rounding does (to infinity from the
-// top binade).
-__device__ __forceinline__ float f64_to_f32_rn(double d) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-    const int ex = (int)((b >> 52) & 0x7ff);
-    if (ex < 1023 - 126 || ex > 1023 + 127) return (float)d;
-    const unsigned long long rest = b & 0x1fffffffull;   // the 29 fraction bits dropped
-    unsigned bits = ((unsigned)(ex - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7fffffull);
-    if (rest > 0x10000000ull || (rest == 0x10000000ull && (bits & 1u))) bits += 1u;
-    return __uint_as_float(bits | ((unsigned)(b >> 63) << 31));
-}
-__device__ __forceinline__ bool f64_is_finite(double d) {
-    return ((__double_as_longlong(d) >> 52) & 0x7ff) != 0x7ff;
-}
+// FP64: Quant64 and its helpers (exact.cuh), shared with host builds.
 
 // Asynchronous 16-byte global -> shared copy through L2 only (the source is
 // written by other CTAs' reductions, so L1 must not hold a stale copy), and
