@@ -116,6 +116,16 @@ FPFP_HD float f64_to_f32_rn(double d) {
 }
 FPFP_HD bool f64_is_finite(double d) { return ((f64_bits(d) >> 52) & 0x7ff) != 0x7ff; }
 
+// The least float >= t (t itself when it is a float; +inf above the float
+// range; NaN stays NaN): a float d is below it exactly when d < t in FP64, so
+// a stop test of an FP32 quantity against an FP64 tolerance compares in FP32.
+// Host only (the threshold is formed once per launch).
+inline float float_at_least(double t) {
+    float f = (float)t;
+    if ((double)f < t) f = nextafterf(f, INFINITY);
+    return f;
+}
+
 // --------------------------------------------------- exact max |v - x|
 // The maximum over elements of |v - x| rounded once to FP64 (what
 // fabs((double)v - (double)x) gives), with FP32 arithmetic per element: the

@@ -49,13 +49,6 @@ constexpr int kChunk = 4;                         // outer iterations enqueued b
 constexpr size_t kTraceBytes = (size_t)kMaxOuterTrace * (sizeof(int) + sizeof(double));
 
 inline int round4(int x) { return (x + 3) & ~3; }
-// The least float >= t (t itself when it is a float; +inf above the float
-// range; NaN stays NaN): a float d is below it exactly when d < t in FP64.
-inline float float_at_least(double t) {
-    float f = (float)t;
-    if ((double)f < t) f = std::nextafter(f, INFINITY);
-    return f;
-}
 inline int round8(int x) { return (x + 7) & ~7; }   // BF16 rows: 16-byte TMA strides
 inline int round16(int x) { return (x + 15) & ~15; }   // E4M3 rows: 16-byte TMA strides
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }

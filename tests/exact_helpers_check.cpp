@@ -3,6 +3,7 @@
 //   quant64_of_f32(v, q) == rint((double)v / q) * q   for quanta q = 2^e
 //   f64_to_f32_rn(d)     == (float)d
 //   AbsDiffMax           == the FP64 maximum of fabs((double)v - (double)x)
+//   d < float_at_least(t) (FP32) == d < t (FP64), for floats d
 // on random bit patterns, scaled values, exact ties and the edges of each
 // helper's range.  Prints the counts and exits non-zero on any mismatch.
 #include <math.h>
@@ -75,6 +76,32 @@ int main(int argc, char** argv) {
         if (fpfp::f64_is_finite(d) != (bool)isfinite(d)) ++bad_c;
     }
 
+    // float_at_least: d < t in FP64 exactly when d < float_at_least(t) in FP32
+    long bad_t = 0;
+    for (long i = 0; i < n; ++i) {
+        double t;
+        switch (i % 5) {
+            case 0: t = (double)f32_from_bits((unsigned)g()); break;                  // t a float
+            case 1: t = ldexp(u01(g), (int)(g() % 300) - 150); break;                 // between floats
+            case 2: t = f64_from_bits(g()); break;                                    // any double
+            case 3: t = ldexp(1.0 + u01(g), 127 + (int)(g() % 3)); break;             // the top of the range
+            default: t = ldexp(u01(g), -149 - (int)(g() % 4)); break;                 // below the subnormals
+        }
+        const float th = fpfp::float_at_least(t);
+        for (int k = 0; k < 4; ++k) {
+            float d;
+            if (k == 0) d = th;
+            else if (k == 1) d = nextafterf(th, -INFINITY);
+            else if (k == 2) d = (float)t;
+            else d = f32_from_bits((unsigned)g());
+            if (((double)d < t) != (d < th)) {
+                if (bad_t < 5) printf("float_at_least(%a) = %a: d = %a\n", t, th, d);
+                ++bad_t;
+            }
+        }
+    }
+    bad_c += bad_t;
+
     // AbsDiffMax against the FP64 maximum, on runs of 1 to 256 elements
     for (long i = 0; i < n / 16; ++i) {
         fpfp::AbsDiffMax m;
@@ -109,7 +136,7 @@ int main(int argc, char** argv) {
     }
 
     printf("quant64_of_f32 mismatches %ld of %ld\n", bad_q, n);
-    printf("f64_to_f32_rn / f64_is_finite mismatches %ld of %ld\n", bad_c, n);
+    printf("f64_to_f32_rn / f64_is_finite / float_at_least mismatches %ld of %ld\n", bad_c, n);
     printf("AbsDiffMax mismatches %ld of %ld runs\n", bad_m, n / 16);
     return (bad_q || bad_c || bad_m) ? 1 : 0;
 }
